@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark of the DLMCOL hot path on GB300: batched TabuCol moves per second.
+
+Workload (one step): TabuCol on G(n=500, p=0.5), k = 48, population 4096 per GPU, 10^5
+iterations per individual, random start colourings (Philox seed 0), through the C-ABI call
+dlm_tabucol_batch. value = tabu moves (iterations that moved) of all GPUs / device time.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank runs its own 4096 individuals (weak scaling, no data-path collective).
+--impl reference times the CPU oracle (the plain C++ statement of the method) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, P_EDGE, K, POP, ITERS, SEED = 500, 0.5, 48, 4096, 100_000, 0
+METRIC = "tabu moves/s at n=500,k=48"
+UNIT = "moves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--pop", type=int, default=POP)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def config(args, extra=None):
+    c = {"workload": f"batched TabuCol G(n={N}, p={P_EDGE}), k={K}, population {args.pop} per GPU, "
+                     f"{args.iters} iterations per individual, random starts (Philox seed {SEED})",
+         "n": N, "k": K, "edge_p": P_EDGE, "population_per_gpu": args.pop, "iters": args.iters,
+         "tenure": "U{0..9} + floor(0.6 f)", "parallelism": f"population sharded over {args.gpus} GPU(s)",
+         "l2": "flushed between timed steps (256 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ------------------------------------------------------------------------------------------------
+def _oracle_job(args):
+    import oracle
+    from paper_2109_05948_gb300 import inputs
+
+    ind, iters = args
+    adj = inputs.edges_to_adj(N, inputs.gnp(N, P_EDGE, SEED))
+    col = oracle.init_colors(N, K, 1, SEED, ind_base=ind)[0]
+    t = time.perf_counter()
+    r = oracle.tabucol(adj, K, col, iters, seed=SEED, ind=ind)
+    return r["moves"], time.perf_counter() - t
+
+
+def oracle_sample(n_ind: int, iters: int):
+    """Runs n_ind individuals of the workload through the oracle, one process per host core
+    (spawned); returns (moves, wall seconds, processes, cpu seconds)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    procs = min(n_ind, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_job, [(0, 10)] * procs)  # start-up outside the timing
+        t = time.perf_counter()
+        res = pool.map(_oracle_job, [(i, iters) for i in range(n_ind)])
+        wall = time.perf_counter() - t
+    return sum(r[0] for r in res), wall, procs, sum(r[1] for r in res)
+
+
+def cpu_baseline(args):
+    n_ind = min(16, os.cpu_count() or 1)
+    moves, wall, procs, cpu_s = oracle_sample(n_ind, args.iters)
+    return {"value": moves / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{n_ind} individuals x {args.iters} iterations of the same workload, one spawned "
+                      f"process per individual on {procs} host cores ({cpu_s:.1f} s of CPU work)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_ind = min(16, os.cpu_count() or 1)
+    iters = max(1000, min(args.iters, 20_000))
+    for _ in range(args.warmup):
+        oracle_sample(n_ind, iters)
+    moves = 0
+    wall = 0.0
+    cpu = 0.0
+    for _ in range(args.steps):
+        mv, w, procs, c = oracle_sample(n_ind, iters)
+        moves += mv
+        wall += w
+        cpu += c
+    v = moves / wall
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16/int32",
+           "data": "synthetic", "config": config(args, {"reference_sample": f"{n_ind} individuals x {iters} iterations per step"}),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                            "sample": f"{n_ind} individuals x {iters} iterations per step, {cpu:.1f} s CPU"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_2109_05948_gb300 import build as libbuild
+    from paper_2109_05948_gb300 import dlmcol, inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+    ctx = dlmcol.Context(local)
+    dev = torch.device("cuda", local)
+    e = inputs.gnp(N, P_EDGE, SEED)
+    g = dlmcol.Graph(ctx, N, torch.from_numpy(e).to(dev))
+    pop, iters = args.pop, args.iters
+    base = rank * pop
+    col0 = torch.empty((pop, N), dtype=torch.int16, device=dev)
+    dlmcol.dlm_init_colors(ctx, N, K, pop, SEED, base, col0)
+    col = torch.empty_like(col0)
+    best_f = torch.empty(pop, dtype=torch.int64, device=dev)
+    moves = torch.zeros((max(1, args.steps), pop), dtype=torch.int64, device=dev)
+    work = torch.zeros((max(1, args.steps), pop, 2), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    smem_gbps = dlmcol.dlm_probe_smem_bandwidth(ctx)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(s, timed):
+        col.copy_(col0)
+        flush.fill_(s & 0xFF)
+        if timed:
+            kev[s][0].record(stream)
+        dlmcol.dlm_tabucol_batch_ex(ctx, g, K, pop, col, best_f, moves[s if timed else 0], iters, dlmcol.COL_TENURE,
+                                    SEED, 0, base, 0, None, work[s if timed else 0])
+        if timed:
+            kev[s][1].record(stream)
+
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for w in range(args.warmup):
+        step(w, False)
+    ctx.sync()
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(args.steps):
+        step(s, True)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.sync()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop() if rank == 0 else None
+    ms = t0.elapsed_time(t1)
+    kms = [a.elapsed_time(b) for a, b in kev]
+    tot_moves = int(moves[: args.steps].sum().item())
+    wk = work[: args.steps].sum(dim=(0, 1)).tolist()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        m = torch.tensor([tot_moves], dtype=torch.int64, device=dev)
+        dist.all_reduce(m)
+        tot_moves = int(m.item())
+    value = tot_moves / (ms / 1e3)
+
+    # algorithmic shared-memory bytes of the tabu kernel (per launch): every conflicting row
+    # scanned reads k gamma + k tabu entries (4k B); every neighbour of a moved vertex costs two
+    # u16 read-modify-writes of its gamma row (8 B) plus its colour byte (1 B)
+    alg_bytes = (4 * K * wk[0] + 9 * wk[1]) / args.steps
+    kmean = sum(kms) / len(kms)
+    achieved = alg_bytes / (kmean / 1e3) / 1e9
+    roofline = {"bound": "smem", "achieved": achieved, "peak": smem_gbps, "unit": "GB/s",
+                "frac": achieved / smem_gbps, "traffic": None,
+                "kernel": "tabucol_batch_kernel", "kernel_ms": kmean,
+                "peak_source": "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads)",
+                "work": {"rows_scanned_per_launch": wk[0] / args.steps,
+                         "neighbour_updates_per_launch": wk[1] / args.steps}}
+    traffic_file = os.path.join(ROOT, "profiles", "tabucol_C2_traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            roofline["traffic"] = json.load(open(traffic_file)).get("dram_bytes_per_launch")
+        except Exception:
+            pass
+
+    e2e = None
+    if not args.no_e2e:
+        # the same metric through the C-ABI with host buffers: start colourings copied in from
+        # pinned host memory and best colourings, conflicts and moves copied back every step
+        h_col0 = col0.cpu().pin_memory()
+        h_col = torch.empty_like(h_col0).pin_memory()
+        h_bf = torch.empty(pop, dtype=torch.int64).pin_memory()
+        h_mv = torch.empty(pop, dtype=torch.int64).pin_memory()
+        mvd = torch.zeros(pop, dtype=torch.int64, device=dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = time.perf_counter()
+        emoves = 0
+        for s in range(args.steps):
+            col.copy_(h_col0, non_blocking=True)
+            dlmcol.dlm_tabucol_batch(ctx, g, K, pop, col, best_f, mvd, iters, dlmcol.COL_TENURE, SEED, 0, base)
+            h_col.copy_(col, non_blocking=True)
+            h_bf.copy_(best_f, non_blocking=True)
+            h_mv.copy_(mvd, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            emoves += int(h_mv.sum())
+        el = time.perf_counter() - e0
+        ctx.sync()
+        if world > 1:
+            t = torch.tensor([el], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+            m = torch.tensor([emoves], dtype=torch.int64, device=dev)
+            dist.all_reduce(m)
+            emoves = int(m.item())
+        e2e = {"value": emoves / el, "unit": UNIT, "h2d_bytes_per_step": pop * N * 2,
+               "d2h_bytes_per_step": pop * N * 2 + 2 * pop * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "int16/int32", "data": "synthetic",
+               "config": config(args, {"smem_probe_gbps": smem_gbps}), "roofline": roofline,
+               "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": args.steps,
+               "moves": tot_moves}
+        print(json.dumps(out), flush=True)
+    g.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,675 @@
+// Population-wide TabuCol for k-COL (paper: section "Adaptations of the algorithm for the vertex
+// coloring problem" -- TabuCOL of Hertz & de Werra in the implementation of Galinier & Hao, run
+// on every offspring; Table params-COL for alpha = 0.6 and the 128|V| depth).
+//
+// GB300 design (differs from the paper's one-thread-per-individual Numba kernel):
+//  * one CTA of W warps per individual; its whole search state lives in shared memory:
+//      gam[n][ks] u16  conflict table gamma (row stride ks u16, ks/2 odd words so that the
+//                      scattered row updates of one warp spread over the banks)
+//      tab[n][ks] u16  tabu expiry iteration modulo 2^16 (kept within +-2^15 of the iteration
+//                      counter by a sweep every 2^14 iterations)
+//      col[n], best[n] u8 current and best colouring; cv[] u32 bitmap of conflicting vertices;
+//      rowres[n] u32   (row minimum, tie count) of each conflicting row of the current scan.
+//  * scan: warps take the conflicting rows round-robin; a warp reads one row with one u32 (two
+//    colours) per lane and reduces (min delta, #ties) with redux.sync -- no shared atomics.
+//  * selection: warp 0 combines the warp results, draws the iteration's Philox block and walks the
+//    per-row tie counts (warp prefix sums) to the j-th tied move in (v, c) order, then rescans that
+//    one row with ballots.
+//  * update: the adjacency bit row of the moved vertex (prefetched into L1 during the scan) is
+//    split across all threads; each neighbour costs two u16 read-modify-writes of its gamma row
+//    and, when its conflict status flips, one shared atomic on the bitmap.
+//  Three CTA barriers per iteration.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dlm {
+
+struct TabuJob {
+  int32_t n, k, ks, words;
+  const uint32_t* bits;  // [n][words]
+  int16_t* col;          // [n] in: start, out: best
+  int64_t* best_f;       // -> one int64
+  int64_t* moves;        // -> one int64 or null
+  int32_t* trace;        // [iters][4] or null
+  int64_t* work;         // [2] or null: sum of conflicting rows scanned, sum of degrees of moved vertices
+  const int32_t* off;    // CSR offsets (degrees for the work counter)
+  int64_t iters;
+  uint32_t ind;          // Philox stream id of this individual
+};
+
+struct TabuRule {
+  uint32_t L1;           // L_max + 1
+  int32_t an, ad;        // alpha = an / ad
+  uint64_t seed;
+  uint32_t gen;
+  int32_t* status;
+};
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int kNone16 = 0x7FFF;
+
+__host__ __device__ inline int tabu_row_stride(int k) {
+  int kw = (k + 1) / 2;
+  if ((kw & 1) == 0) kw += 1;
+  return 2 * kw;
+}
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct TabuSmem {
+  size_t gam, tab, col, best, rowres, cv, red, total;
+};
+
+__host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps) {
+  TabuSmem s;
+  const int ks = tabu_row_stride(k);
+  size_t o = 0;
+  s.gam = o; o += align16((size_t)n * ks * 2);
+  s.tab = o; o += align16((size_t)n * ks * 2);
+  s.col = o; o += align16(n);
+  s.best = o; o += align16(n);
+  s.rowres = o; o += align16((size_t)n * 4);
+  s.cv = o; o += 64 * 4;
+  s.red = o; o += align16((size_t)warps * 8 + 64);
+  s.total = o;
+  return s;
+}
+
+// position of the r-th (0-based) set bit of x (x has more than r set bits)
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int r) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const int c = __popc(x & ((1u << s) - 1u));
+    if (r >= c) { r -= c; x >>= s; pos += s; }
+  }
+  return pos;
+}
+
+// Warp view of the conflicting-vertex bitmap: lane l owns bitmap words 2l and 2l+1 (vertices
+// 64l .. 64l+63), its popcount and the exclusive prefix over lanes (= rank of its first vertex).
+struct CvView {
+  uint64_t w;
+  int cnt, excl, total;
+};
+
+__device__ __forceinline__ CvView cv_view(const uint32_t* cv, int nwords, int lane) {
+  CvView c;
+  const uint32_t lo = (2 * lane < nwords) ? cv[2 * lane] : 0u;
+  const uint32_t hi = (2 * lane + 1 < nwords) ? cv[2 * lane + 1] : 0u;
+  c.w = ((uint64_t)hi << 32) | lo;
+  c.cnt = __popcll(c.w);
+  int incl = c.cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += t;
+  }
+  c.excl = incl - c.cnt;
+  c.total = __shfl_sync(FULL, incl, 31);
+  return c;
+}
+
+// vertex id of the i-th conflicting vertex (0 <= i < total); warp-collective
+__device__ __forceinline__ int cv_select(const CvView& c, int i, int lane) {
+  const unsigned bal = __ballot_sync(FULL, i >= c.excl && i < c.excl + c.cnt);
+  const int L = __ffs(bal) - 1;
+  int v = 0;
+  if (lane == L) {
+    const int r = i - c.excl;
+    const uint32_t lo = (uint32_t)c.w, hi = (uint32_t)(c.w >> 32);
+    const int pl = __popc(lo);
+    v = 64 * lane + (r < pl ? nth_set_bit(lo, r) : 32 + nth_set_bit(hi, r - pl));
+  }
+  return __shfl_sync(FULL, v, L);
+}
+
+// key of one (v, c) entry: delta if the move is admissible, INT_MAX otherwise
+__device__ __forceinline__ int move_key(int c, int k, int colv, int gc, int te, int g0, int it16, int f, int best_f) {
+  const int d = gc - g0;
+  const bool tabu = (int16_t)(uint16_t)(te - it16) > 0;
+  const bool adm = (c < k) && (c != colv) && (!tabu || f + d < best_f);
+  return adm ? d : INT_MAX;
+}
+
+template <int W>
+__device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t* smem) {
+  constexpr int NT = 32 * W;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = J.n, k = J.k, ks = J.ks, kw = ks / 2, nwords = J.words;
+  const TabuSmem L = tabu_smem_layout(n, k, W);
+  uint16_t* gam = (uint16_t*)(smem + L.gam);
+  uint16_t* tab = (uint16_t*)(smem + L.tab);
+  uint8_t* colS = smem + L.col;
+  uint8_t* bestS = smem + L.best;
+  uint32_t* rowres = (uint32_t*)(smem + L.rowres);
+  uint32_t* cv = (uint32_t*)(smem + L.cv);
+  int32_t* red = (int32_t*)(smem + L.red);   // [W] min, [W] count
+  int32_t* sc = red + 2 * W;                 // scalars
+  // sc[0] moved vertex (-1 none), sc[1] old colour, sc[2] new colour, sc[3] f after,
+  // sc[4] improved, sc[5] error, sc[6] bad input
+
+  // ---- set-up: zero the tables, load the start colouring ------------------------------------
+  {
+    uint32_t* g32 = (uint32_t*)gam;
+    uint32_t* t32 = (uint32_t*)tab;
+    const int nw32 = n * kw;
+    for (int i = tid; i < nw32; i += NT) { g32[i] = 0u; t32[i] = 0u; }
+    if (tid < 8) sc[tid] = 0;
+    for (int i = tid; i < 64; i += NT) cv[i] = 0u;
+  }
+  __syncthreads();
+  for (int v = tid; v < n; v += NT) {
+    const int c = J.col[v];
+    if (c < 0 || c >= k) sc[6] = 1;
+    const uint8_t cc = (uint8_t)(c < 0 ? 0 : (c >= k ? 0 : c));
+    colS[v] = cc;
+    bestS[v] = cc;
+  }
+  __syncthreads();
+  if (sc[6]) {
+    if (tid == 0) raise_status(R.status, DLM_EINVAL);
+    return;
+  }
+  // gamma rows: one thread per row, neighbours from the bit rows
+  for (int v = tid; v < n; v += NT) {
+    const uint32_t* brow = J.bits + (size_t)v * nwords;
+    uint16_t* grow = gam + (size_t)v * ks;
+    for (int w = 0; w < nwords; ++w) {
+      uint32_t m = __ldg(brow + w);
+      while (m) {
+        const int u = 32 * w + __ffs(m) - 1;
+        m &= m - 1;
+        grow[colS[u]]++;
+      }
+    }
+  }
+  __syncthreads();
+  int f;
+  {
+    int part = 0;
+    for (int v0 = warp * 32; v0 < n; v0 += NT) {
+      const int v = v0 + lane;
+      int g = 0;
+      if (v < n) g = gam[(size_t)v * ks + colS[v]];
+      part += g;
+      const unsigned b = __ballot_sync(FULL, g > 0);
+      if (lane == 0) cv[v0 >> 5] = b;
+    }
+    part = __reduce_add_sync(FULL, part);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    int tot = 0;
+    for (int w = 0; w < W; ++w) tot += red[w];
+    f = tot / 2;
+    __syncthreads();
+  }
+  int best_f = f;
+  int64_t moves = 0;
+  int64_t it = 0;
+  int64_t work_rows = 0, work_deg = 0;  // kept by thread 0 only
+
+  // per-thread slice of a bit row for the gamma update
+  int per = (n + NT - 1) / NT;
+  {
+    int p2 = 1;
+    while (p2 < per) p2 <<= 1;
+    per = p2 > 32 ? 32 : p2;
+  }
+  const uint32_t slice_mask = per == 32 ? 0xFFFFFFFFu : ((1u << per) - 1u);
+
+  for (it = 0; it < J.iters; ++it) {
+    if (f == 0) break;
+    const int it16 = (int)(it & 0xFFFF);
+    // ---- phase 1: scan of the conflicting rows --------------------------------------------
+    const CvView view = cv_view(cv, nwords, lane);
+    const int ncv = view.total;
+    if (tid == 0) work_rows += ncv;
+    int wmin = INT_MAX, wcnt = 0;
+    for (int i = warp; i < ncv; i += W) {
+      const int v = cv_select(view, i, lane);
+      if (lane == 0) {  // the moved vertex's bit row is needed in phase 3: pull it into L1
+        const char* p = (const char*)(J.bits + (size_t)v * nwords);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(p + nwords * 4 - 4));
+      }
+      const int colv = colS[v];
+      const uint16_t* grow = gam + (size_t)v * ks;
+      const uint32_t* g32 = (const uint32_t*)grow;
+      const uint32_t* t32 = (const uint32_t*)(tab + (size_t)v * ks);
+      const int g0 = grow[colv];
+      int lm = INT_MAX, lc = 0;
+      for (int wd = lane; wd < kw; wd += 32) {
+        const uint32_t gw = g32[wd], tw = t32[wd];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int key = move_key(2 * wd + h, k, colv, (gw >> (16 * h)) & 0xFFFF, (tw >> (16 * h)) & 0xFFFF, g0,
+                                   it16, f, best_f);
+          if (key < lm) { lm = key; lc = 1; }
+          else if (key == lm && key != INT_MAX) lc++;
+        }
+      }
+      const int m = __reduce_min_sync(FULL, lm);
+      const int c = (int)__reduce_add_sync(FULL, (m != INT_MAX && lm == m) ? (unsigned)lc : 0u);
+      if (lane == 0) rowres[i] = ((uint32_t)(uint16_t)(m == INT_MAX ? kNone16 : m) << 16) | (uint32_t)c;
+      if (m < wmin) { wmin = m; wcnt = c; }
+      else if (m == wmin && m != INT_MAX) wcnt += c;
+    }
+    if (lane == 0) { red[warp] = wmin; red[W + warp] = wcnt; }
+    __syncthreads();
+    // ---- phase 2: selection and move (warp 0) -------------------------------------------------
+    if (warp == 0) {
+      const U4 r = rng(R.seed, (uint32_t)it, R.gen, J.ind, kTagTabu);
+      const int key = lane < W ? red[lane] : INT_MAX;
+      const int cntw = lane < W ? red[W + lane] : 0;
+      const int dstar = __reduce_min_sync(FULL, key);
+      const int T = (int)__reduce_add_sync(FULL, (dstar != INT_MAX && key == dstar) ? (unsigned)cntw : 0u);
+      int mv = -1, mc = -1;
+      if (T > 0) {
+        const uint32_t j = below(r.x, (uint32_t)T);
+        uint32_t base = 0;
+        int irow = -1;
+        uint32_t jj = 0;
+        for (int i0 = 0; i0 < ncv; i0 += 32) {
+          const int i = i0 + lane;
+          const uint32_t rr = i < ncv ? rowres[i] : ((uint32_t)kNone16 << 16);
+          const int rm = (int16_t)(rr >> 16);
+          const int cc = rm == dstar ? (int)(rr & 0xFFFF) : 0;
+          int incl = cc;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += t;
+          }
+          const uint32_t tot = (uint32_t)__shfl_sync(FULL, incl, 31);
+          if (j < base + tot) {
+            const unsigned bal = __ballot_sync(FULL, j < base + (uint32_t)incl);
+            const int Lr = __ffs(bal) - 1;
+            irow = i0 + Lr;
+            jj = j - base - (uint32_t)__shfl_sync(FULL, incl - cc, Lr);
+            break;
+          }
+          base += tot;
+        }
+        if (irow < 0) {  // tie counts inconsistent with the scan: refuse to move
+          if (lane == 0) sc[5] = 2;
+          irow = 0;
+        }
+        mv = cv_select(view, irow, lane);
+        const int colv = colS[mv];
+        const uint16_t* grow = gam + (size_t)mv * ks;
+        const uint32_t* g32 = (const uint32_t*)grow;
+        const uint32_t* t32 = (const uint32_t*)(tab + (size_t)mv * ks);
+        const int g0 = grow[colv];
+        for (int wd0 = 0; wd0 < kw; wd0 += 32) {
+          const int wd = wd0 + lane;
+          int b0 = 0, b1 = 0;
+          if (wd < kw) {
+            const uint32_t gw = g32[wd], tw = t32[wd];
+            b0 = move_key(2 * wd, k, colv, gw & 0xFFFF, tw & 0xFFFF, g0, it16, f, best_f) == dstar;
+            b1 = move_key(2 * wd + 1, k, colv, gw >> 16, tw >> 16, g0, it16, f, best_f) == dstar;
+          }
+          const int cc = b0 + b1;
+          int incl = cc;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += t;
+          }
+          const uint32_t tot = (uint32_t)__shfl_sync(FULL, incl, 31);
+          if (jj < tot) {
+            const unsigned bal = __ballot_sync(FULL, jj < (uint32_t)incl);
+            const int Lc = __ffs(bal) - 1;
+            int cpick = 0;
+            if (lane == Lc) {
+              const uint32_t before = (uint32_t)(incl - cc);
+              cpick = (b0 && jj == before) ? 2 * wd : 2 * wd + 1;
+            }
+            mc = __shfl_sync(FULL, cpick, Lc);
+            break;
+          }
+          jj -= tot;
+        }
+      }
+      if (lane == 0 && mv >= 0 && (mc < 0 || mc >= k)) { sc[5] = 2; mv = -1; }
+      if (lane == 0) {
+        if (mv >= 0 && sc[5] == 0) {
+          const int old = colS[mv];
+          colS[mv] = (uint8_t)mc;
+          const int fn = f + dstar;
+          const int64_t tt = (int64_t)below(r.y, R.L1) + ((int64_t)R.an * fn) / R.ad;
+          if (tt > 32766) sc[5] = 1;
+          tab[(size_t)mv * ks + old] = (uint16_t)((it + 1 + tt) & 0xFFFF);
+          const uint32_t bit = 1u << (mv & 31);
+          if (gam[(size_t)mv * ks + mc] > 0) cv[mv >> 5] |= bit;
+          else cv[mv >> 5] &= ~bit;
+          sc[0] = mv; sc[1] = old; sc[2] = mc; sc[3] = fn; sc[4] = fn < best_f;
+          if (J.trace) {
+            int4 t4 = make_int4(mv, mc, dstar, T);
+            reinterpret_cast<int4*>(J.trace)[it] = t4;
+          }
+        } else {
+          sc[0] = -1;
+          if (J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(-1, -1, 0, 0);
+        }
+      }
+    }
+    __syncthreads();
+    if (sc[5]) break;
+    // ---- phase 3: gamma update over the neighbours of the moved vertex ------------------------
+    const int mv = sc[0];
+    if (mv >= 0) {
+      const int old = sc[1], nw = sc[2];
+      f = sc[3];
+      ++moves;
+      if (tid == 0 && J.work) work_deg += __ldg(J.off + mv + 1) - __ldg(J.off + mv);
+      const uint32_t* brow = J.bits + (size_t)mv * nwords;
+      for (int b0 = tid * per; b0 < n; b0 += NT * per) {
+        uint32_t m = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
+        while (m) {
+          const int u = b0 + __ffs(m) - 1;
+          m &= m - 1;
+          uint16_t* grow = gam + (size_t)u * ks;
+          const int go = grow[old] - 1;
+          grow[old] = (uint16_t)go;
+          const int gn = grow[nw] + 1;
+          grow[nw] = (uint16_t)gn;
+          const int cu = colS[u];
+          if (cu == old && go == 0) atomicAnd(cv + (u >> 5), ~(1u << (u & 31)));
+          else if (cu == nw && gn == 1) atomicOr(cv + (u >> 5), 1u << (u & 31));
+        }
+      }
+      if (sc[4]) {
+        best_f = f;
+        const uint32_t* s32 = (const uint32_t*)colS;
+        uint32_t* d32 = (uint32_t*)bestS;
+        for (int i = tid; i < (n + 3) / 4; i += NT) d32[i] = s32[i];
+      }
+    }
+    if (((it + 1) & 0x3FFF) == 0) {
+      // keep every expiry within 2^15 of the counter: expired entries are reset to "now"
+      const uint32_t now = (uint32_t)((it + 1) & 0xFFFF);
+      uint32_t* t32 = (uint32_t*)tab;
+      for (int i = tid; i < n * kw; i += NT) {
+        uint32_t w = t32[i];
+        uint32_t lo = w & 0xFFFF, hi = w >> 16;
+        if ((int16_t)(uint16_t)(lo - now) <= 0) lo = now;
+        if ((int16_t)(uint16_t)(hi - now) <= 0) hi = now;
+        t32[i] = lo | (hi << 16);
+      }
+    }
+    __syncthreads();
+  }
+  if (sc[5]) {
+    if (tid == 0) raise_status(R.status, sc[5] == 1 ? DLM_EUNSUPPORTED : DLM_ECUDA);
+  }
+  __syncthreads();
+  for (int v = tid; v < n; v += NT) J.col[v] = (int16_t)bestS[v];
+  if (tid == 0) {
+    *J.best_f = best_f;
+    if (J.moves) *J.moves = moves;
+    if (J.work) { J.work[0] = work_rows; J.work[1] = work_deg; }
+  }
+}
+
+struct TabuBatchArgs {
+  int32_t n, k, ks, words, pop;
+  const uint32_t* bits;
+  const int32_t* off;
+  int16_t* col;
+  int64_t* best_f;
+  int64_t* moves;
+  int32_t* trace;
+  int64_t* work;
+  int64_t iters;
+  uint32_t ind_base;
+  TabuRule rule;
+};
+
+template <int W>
+__global__ void __launch_bounds__(W * 32) tabucol_batch_kernel(TabuBatchArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int i = blockIdx.x;
+  TabuJob J;
+  J.n = a.n; J.k = a.k; J.ks = a.ks; J.words = a.words; J.bits = a.bits;
+  J.col = a.col + (size_t)i * a.n;
+  J.best_f = a.best_f + i;
+  J.moves = a.moves ? a.moves + i : nullptr;
+  J.trace = a.trace ? a.trace + (size_t)i * a.iters * 4 : nullptr;
+  J.work = a.work ? a.work + 2 * (size_t)i : nullptr;
+  J.off = a.off;
+  J.iters = a.iters;
+  J.ind = a.ind_base + (uint32_t)i;
+  tabucol_individual<W>(J, a.rule, smem);
+}
+
+// ---- uneven batch: persistent CTAs pull individuals from a device queue ----------------------
+struct MultiJob {
+  int32_t n, k, ks, words;
+  const uint32_t* bits;
+  int16_t* col;
+  int64_t* best_f;
+  int64_t* moves;
+  int64_t iters;
+  uint32_t ind;
+};
+
+template <int W>
+__global__ void __launch_bounds__(W * 32) tabucol_multi_kernel(const MultiJob* jobs, int32_t njobs,
+                                                               int32_t* queue, TabuRule rule) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int32_t next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+    __syncthreads();
+    const int j = next;
+    __syncthreads();
+    if (j >= njobs) break;
+    const MultiJob& M = jobs[j];
+    TabuJob J;
+    J.n = M.n; J.k = M.k; J.ks = M.ks; J.words = M.words; J.bits = M.bits; J.col = M.col;
+    J.best_f = M.best_f; J.moves = M.moves; J.trace = nullptr; J.work = nullptr; J.off = nullptr;
+    J.iters = M.iters; J.ind = M.ind;
+    tabucol_individual<W>(J, rule, smem);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+template <int W>
+static dlm_status launch_batch(dlm_ctx* ctx, const TabuBatchArgs& a, size_t smem) {
+  auto kfn = tabucol_batch_kernel<W>;
+  DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kfn<<<a.pop, W * 32, smem, ctx->stream>>>(a);
+  return launch_check(ctx, "tabucol_batch_kernel");
+}
+
+static int lookup_tune(const dlm_ctx* ctx, int n, int k) {
+  for (int i = 0; i < ctx->n_tune; ++i)
+    if (ctx->tune[i].n == n && ctx->tune[i].k == k) return ctx->tune[i].warps;
+  return 0;
+}
+
+// default when not tuned: enough threads to cover a row scan and a neighbour update in few steps
+static int default_warps(int n, int k) {
+  (void)k;
+  if (n <= 160) return 1;
+  if (n <= 400) return 2;
+  return 4;
+}
+
+static dlm_status tabucol_check(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,
+                                dlm_tenure t) {
+  if (!ctx || !g) return fail(ctx, DLM_EINVAL, "null context or graph");
+  if (k < 2 || k > 128) return fail(ctx, DLM_EUNSUPPORTED, "tabucol: k must be in 2..128");
+  if (pop < 0 || iters < 0) return fail(ctx, DLM_EINVAL, "tabucol: negative population or budget");
+  if (iters > INT32_MAX) return fail(ctx, DLM_EINVAL, "tabucol: budget above 2^31");
+  if (t.L_max < 0 || t.alpha_num < 0 || t.alpha_den <= 0) return fail(ctx, DLM_EINVAL, "tabucol: bad tenure");
+  return DLM_OK;
+}
+
+static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                              int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
+                              uint32_t generation, uint32_t ind_base, int warps, int32_t* trace,
+                              int64_t* work) {
+  DLM_TRY(tabucol_check(ctx, g, k, pop, iters, tenure));
+  if (pop == 0) return DLM_OK;
+  if (!col || !best_f) return fail(ctx, DLM_EINVAL, "tabucol: null col or best_f");
+  if (warps == 0) warps = lookup_tune(ctx, g->n, k);
+  if (warps == 0) warps = default_warps(g->n, k);
+  if (warps != 1 && warps != 2 && warps != 4 && warps != 8)
+    return fail(ctx, DLM_EINVAL, "tabucol: warps per individual must be 1, 2, 4 or 8");
+  const TabuSmem L = tabu_smem_layout(g->n, k, warps);
+  if (L.total > ctx->smem_optin)
+    return fail(ctx, DLM_EUNSUPPORTED, "tabucol: per-individual state (" + std::to_string(L.total) +
+                                           " B) exceeds shared memory per block");
+  TabuBatchArgs a;
+  a.n = g->n; a.k = k; a.ks = tabu_row_stride(k); a.words = g->words; a.pop = pop;
+  a.bits = g->d_bits; a.off = g->d_off; a.col = col; a.best_f = best_f; a.moves = moves; a.trace = trace;
+  a.work = work; a.iters = iters;
+  a.ind_base = ind_base;
+  a.rule = TabuRule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status};
+  switch (warps) {
+    case 1: return launch_batch<1>(ctx, a, L.total);
+    case 2: return launch_batch<2>(ctx, a, L.total);
+    case 4: return launch_batch<4>(ctx, a, L.total);
+    default: return launch_batch<8>(ctx, a, L.total);
+  }
+}
+
+}  // namespace dlm
+
+using namespace dlm;
+
+extern "C" dlm_status dlm_tabucol_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                        int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure,
+                                        uint64_t seed, uint32_t generation, uint32_t ind_base) {
+  return tabucol_run(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base, 0, nullptr,
+                     nullptr);
+}
+
+extern "C" dlm_status dlm_tabucol_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                           int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure,
+                                           uint64_t seed, uint32_t generation, uint32_t ind_base,
+                                           int32_t warps_per_individual, int32_t* trace, int64_t* work) {
+  return tabucol_run(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base,
+                     warps_per_individual, trace, work);
+}
+
+extern "C" dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,
+                                           int32_t* best) {
+  if (!ctx || !g || pop <= 0 || iters <= 0) return fail(ctx, DLM_EINVAL, "autotune: bad arguments");
+  const size_t col_bytes = align16((size_t)pop * g->n * sizeof(int16_t));
+  uint8_t* ws = nullptr;
+  DLM_TRY(ctx_workspace(ctx, col_bytes + (size_t)pop * sizeof(int64_t), (void**)&ws));
+  int16_t* col = (int16_t*)ws;
+  int64_t* bf = (int64_t*)(ws + col_bytes);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  int best_w = default_warps(g->n, k);
+  const int cand[4] = {1, 2, 4, 8};
+  dlm_status st = DLM_OK;
+  for (int c = 0; c < 4 && st == DLM_OK; ++c) {
+    const TabuSmem L = tabu_smem_layout(g->n, k, cand[c]);
+    if (L.total > ctx->smem_optin) continue;
+    float ms_sum = 0.f;
+    for (int rep = 0; rep < 2 && st == DLM_OK; ++rep) {
+      st = dlm_init_colors(ctx, g->n, k, pop, 0x7u, 0u, col);
+      if (st != DLM_OK) break;
+      cudaEventRecord(e0, ctx->stream);
+      st = tabucol_run(ctx, g, k, pop, col, bf, nullptr, iters, dlm_tenure{9, 6, 10}, 1u, 0u, 0u, cand[c], nullptr,
+                       nullptr);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 1) ms_sum += ms;  // first repetition warms up
+    }
+    if (st == DLM_OK && ms_sum < best_ms) { best_ms = ms_sum; best_w = cand[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DLM_OK) return st;
+  int slot = -1;
+  for (int i = 0; i < ctx->n_tune; ++i)
+    if (ctx->tune[i].n == g->n && ctx->tune[i].k == k) slot = i;
+  if (slot < 0 && ctx->n_tune < 64) slot = ctx->n_tune++;
+  if (slot >= 0) ctx->tune[slot] = dlm_ctx::TuneEntry{g->n, k, best_w};
+  if (best) *best = best_w;
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dlm_graph* const* graphs,
+                                        const int32_t* k, const int32_t* pop, int16_t* const* col,
+                                        int64_t* const* best_f, int64_t* const* moves, const int64_t* iters,
+                                        dlm_tenure tenure, uint64_t seed, uint32_t generation, uint32_t ind_base) {
+  if (!ctx || n_graphs <= 0 || !graphs || !k || !pop || !col || !best_f || !iters)
+    return fail(ctx, DLM_EINVAL, "tabucol_multi: bad arguments");
+  // one launch: the block size is the largest tuned/default warp count, shared memory the largest
+  // per-individual state; individuals sorted by decreasing work (n * k * iters) go to a queue
+  int warps = 1;
+  size_t smem = 0;
+  size_t njobs = 0;
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    DLM_TRY(tabucol_check(ctx, graphs[gi], k[gi], pop[gi], iters[gi], tenure));
+    if (pop[gi] > 0 && (!col[gi] || !best_f[gi])) return fail(ctx, DLM_EINVAL, "tabucol_multi: null output");
+    int w = lookup_tune(ctx, graphs[gi]->n, k[gi]);
+    if (w == 0) w = default_warps(graphs[gi]->n, k[gi]);
+    warps = w > warps ? w : warps;
+    njobs += (size_t)pop[gi];
+  }
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    const TabuSmem L = tabu_smem_layout(graphs[gi]->n, k[gi], warps);
+    smem = L.total > smem ? L.total : smem;
+  }
+  if (smem > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi: a graph's state exceeds shared memory");
+  if (njobs == 0) return DLM_OK;
+  std::vector<MultiJob> jobs;
+  jobs.reserve(njobs);
+  uint32_t id = ind_base;
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    const dlm_graph* g = graphs[gi];
+    for (int j = 0; j < pop[gi]; ++j) {
+      MultiJob M;
+      M.n = g->n; M.k = k[gi]; M.ks = tabu_row_stride(k[gi]); M.words = g->words; M.bits = g->d_bits;
+      M.col = col[gi] + (size_t)j * g->n; M.best_f = best_f[gi] + j; M.moves = moves && moves[gi] ? moves[gi] + j : nullptr;
+      M.iters = iters[gi]; M.ind = id++;
+      jobs.push_back(M);
+    }
+  }
+  std::stable_sort(jobs.begin(), jobs.end(), [](const MultiJob& a, const MultiJob& b) {
+    return (double)a.n * a.k * a.iters > (double)b.n * b.k * b.iters;
+  });
+  const size_t job_bytes = align16(jobs.size() * sizeof(MultiJob));
+  uint8_t* ws = nullptr;
+  DLM_TRY(ctx_workspace(ctx, job_bytes + 16, (void**)&ws));
+  MultiJob* d_jobs = (MultiJob*)ws;
+  int32_t* d_queue = (int32_t*)(ws + job_bytes);
+  DLM_CUDA(ctx, cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(MultiJob), cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int32_t), ctx->stream));
+  const TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status};
+  int per_sm = 0;
+  dlm_status st = DLM_OK;
+  auto go = [&](auto kfn) -> dlm_status {
+    DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DLM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int grid = (int)std::min<size_t>((size_t)per_sm * ctx->num_sms, jobs.size());
+    kfn<<<grid, warps * 32, smem, ctx->stream>>>(d_jobs, (int32_t)jobs.size(), d_queue, rule);
+    return launch_check(ctx, "tabucol_multi_kernel");
+  };
+  switch (warps) {
+    case 1: st = go(tabucol_multi_kernel<1>); break;
+    case 2: st = go(tabucol_multi_kernel<2>); break;
+    case 4: st = go(tabucol_multi_kernel<4>); break;
+    default: st = go(tabucol_multi_kernel<8>); break;
+  }
+  return st;
+}

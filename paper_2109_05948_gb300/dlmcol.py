@@ -1,0 +1,329 @@
+"""Thin ctypes binding of ``libdlmcol.so`` (C-ABI in ``include/dlmcol.h``).
+
+The functions keep the C names. They only marshal arguments: torch tensors are passed by their
+device pointers, streams by their CUDA handles. Every step of the computation runs in the CUDA
+library; importing this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdlmcol.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "dlmcol.h")
+
+DLM_OK, DLM_EINVAL, DLM_ENOMEM, DLM_ECUDA, DLM_ETIMEOUT, DLM_ECANCELLED, DLM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "DLM_OK", -1: "DLM_EINVAL", -2: "DLM_ENOMEM", -3: "DLM_ECUDA", -4: "DLM_ETIMEOUT",
+                -5: "DLM_ECANCELLED", -6: "DLM_EUNSUPPORTED"}
+
+
+class DlmError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+
+
+class Tenure(ctypes.Structure):
+    _fields_ = [("L_max", ctypes.c_int32), ("alpha_num", ctypes.c_int32), ("alpha_den", ctypes.c_int32)]
+
+
+class MemeticParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("p", ctypes.c_int32), ("K", ctypes.c_int32), ("iters", ctypes.c_int64),
+                ("tenure", Tenure), ("use_scorer", ctypes.c_int32), ("epochs", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+COL_TENURE = Tenure(9, 6, 10)    # Table params-COL: alpha = 0.6, L in 0..9
+WVCP_TENURE = Tenure(9, 2, 10)   # Table params-WVCP: alpha = 0.2 (times |V|), L in 0..9
+
+_P = ctypes.c_void_p
+_i32, _i64, _u32, _u64, _f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "dlm_create": (_i32, [_PP, _i32, _P]),
+    "dlm_destroy": (None, [_P]),
+    "dlm_set_stream": (_i32, [_P, _P]),
+    "dlm_last_error": (ctypes.c_char_p, [_P]),
+    "dlm_sync": (_i32, [_P]),
+    "dlm_graph_create": (_i32, [_P, _i32, _i64, _P, _P, _PP]),
+    "dlm_graph_destroy": (None, [_P]),
+    "dlm_graph_n": (_i32, [_P]),
+    "dlm_graph_m": (_i64, [_P]),
+    "dlm_graph_export": (_i32, [_P, _P, _P, _P, _P]),
+    "dlm_init_colors": (_i32, [_P, _i32, _i32, _i32, _u64, _u32, _P]),
+    "dlm_gamma": (_i32, [_P, _P, _i32, _i32, _P, _P, _P]),
+    "dlm_tabucol_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, Tenure, _u64, _u32, _u32]),
+    "dlm_tabucol_batch_ex": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, Tenure, _u64, _u32, _u32, _i32, _P, _P]),
+    "dlm_tabucol_multi": (_i32, [_P, _i32, _P, _P, _P, _P, _P, _P, _P, Tenure, _u64, _u32, _u32]),
+    "dlm_tabucol_autotune": (_i32, [_P, _P, _i32, _i32, _i64, _P]),
+    "dlm_gpx_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _P, _i32, _P, _u64, _u32]),
+    "dlm_distance_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32]),
+    "dlm_pool_update": (_i32, [_P, _i32, _i32, _P, _P, _P]),
+    "dlm_knn": (_i32, [_P, _i32, _P, _i32, _P]),
+    "dlm_scorer_create": (_i32, [_P, _i32, _i32, _u64, _PP]),
+    "dlm_scorer_destroy": (None, [_P]),
+    "dlm_scorer_nparams": (_i64, [_P]),
+    "dlm_scorer_get_params": (_i32, [_P, _P, _P]),
+    "dlm_scorer_set_params": (_i32, [_P, _P, _P]),
+    "dlm_score_offspring": (_i32, [_P, _P, _P, _i32, _P]),
+    "dlm_scorer_loss_grad": (_i32, [_P, _P, _P, _P, _i32, _P, _P, _P]),
+    "dlm_scorer_train": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32, _f32, _u64, _u32]),
+    "dlm_memetic_create": (_i32, [_P, _P, _P, _PP]),
+    "dlm_memetic_destroy": (None, [_P]),
+    "dlm_memetic_step": (_i32, [_P, _P, _P]),
+    "dlm_memetic_get": (_i32, [_P, _P, _i32, _P]),
+    "dlm_memetic_set": (_i32, [_P, _P, _i32, _P]),
+    "dlm_probe_smem_bandwidth": (_i32, [_P, _P]),
+    "dlm_wvcp_tabu_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises when it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2109_05948_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(L, name):
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_symbols():
+    """Names of the entry points declared in include/dlmcol.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(dlm_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Context:
+    """dlm_ctx on one device and stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        st = lib().dlm_create(ctypes.byref(h), device, _stream_handle(stream))
+        if st != DLM_OK:
+            raise DlmError(st, "dlm_create")
+        self.h = h
+
+    def check(self, st, what=""):
+        if st != DLM_OK:
+            raise DlmError(st, f"{what}: {lib().dlm_last_error(self.h).decode()}")
+
+    def set_stream(self, stream):
+        self.check(lib().dlm_set_stream(self.h, _stream_handle(stream)), "dlm_set_stream")
+
+    def sync(self):
+        self.check(lib().dlm_sync(self.h), "dlm_sync")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dlm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """dlm_graph built on the GPU from a device edge list [m][2] int32 (and weights [n] int32)."""
+
+    def __init__(self, ctx: Context, n: int, edges, weights=None):
+        h = ctypes.c_void_p()
+        m = 0 if edges is None else int(edges.shape[0])
+        ctx.check(lib().dlm_graph_create(ctx.h, n, m, _ptr(edges), _ptr(weights), ctypes.byref(h)), "dlm_graph_create")
+        self.h, self.n = h, n
+        self.m = int(lib().dlm_graph_m(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dlm_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------------------
+# entry points (same names as the C ABI); tensors are device tensors of the documented dtype
+# ------------------------------------------------------------------------------------------------
+def dlm_graph_export(ctx, g, off, idx, bits):
+    ctx.check(lib().dlm_graph_export(ctx.h, g.h, _ptr(off), _ptr(idx), _ptr(bits)), "dlm_graph_export")
+
+
+def dlm_init_colors(ctx, n, k, pop, seed, ind_base, col):
+    ctx.check(lib().dlm_init_colors(ctx.h, n, k, pop, seed, ind_base, _ptr(col)), "dlm_init_colors")
+
+
+def dlm_gamma(ctx, g, k, pop, col, gamma, f):
+    ctx.check(lib().dlm_gamma(ctx.h, g.h, k, pop, _ptr(col), _ptr(gamma), _ptr(f)), "dlm_gamma")
+
+
+def dlm_tabucol_batch(ctx, g, k, pop, col, best_f, moves, iters, tenure=COL_TENURE, seed=0, generation=0,
+                      ind_base=0):
+    ctx.check(lib().dlm_tabucol_batch(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_f), _ptr(moves), iters, tenure,
+                                      seed, generation, ind_base), "dlm_tabucol_batch")
+
+
+def dlm_tabucol_batch_ex(ctx, g, k, pop, col, best_f, moves, iters, tenure=COL_TENURE, seed=0, generation=0,
+                         ind_base=0, warps=0, trace=None, work=None):
+    ctx.check(lib().dlm_tabucol_batch_ex(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_f), _ptr(moves), iters, tenure,
+                                         seed, generation, ind_base, warps, _ptr(trace), _ptr(work)),
+              "dlm_tabucol_batch_ex")
+
+
+def dlm_tabucol_multi(ctx, graphs, ks, pops, cols, best_fs, moves, iters, tenure=COL_TENURE, seed=0, generation=0,
+                      ind_base=0):
+    G = len(graphs)
+    arr_g = (ctypes.c_void_p * G)(*[g.h.value for g in graphs])
+    arr_k = (ctypes.c_int32 * G)(*ks)
+    arr_p = (ctypes.c_int32 * G)(*pops)
+    arr_c = (ctypes.c_void_p * G)(*[c.data_ptr() for c in cols])
+    arr_b = (ctypes.c_void_p * G)(*[b.data_ptr() for b in best_fs])
+    arr_m = (ctypes.c_void_p * G)(*[(m.data_ptr() if m is not None else 0) for m in moves]) if moves else None
+    arr_i = (ctypes.c_int64 * G)(*iters)
+    ctx.check(lib().dlm_tabucol_multi(ctx.h, G, arr_g, arr_k, arr_p, arr_c, arr_b, arr_m, arr_i, tenure, seed,
+                                      generation, ind_base), "dlm_tabucol_multi")
+
+
+def dlm_tabucol_autotune(ctx, g, k, pop, iters):
+    best = ctypes.c_int32(0)
+    ctx.check(lib().dlm_tabucol_autotune(ctx.h, g.h, k, pop, iters, ctypes.byref(best)), "dlm_tabucol_autotune")
+    return best.value
+
+
+def dlm_gpx_batch(ctx, n, k, parents, pop, pairs, child_id, m, children, seed, generation):
+    ctx.check(lib().dlm_gpx_batch(ctx.h, n, k, _ptr(parents), pop, _ptr(pairs), _ptr(child_id), m, _ptr(children),
+                                  seed, generation), "dlm_gpx_batch")
+
+
+def dlm_distance_batch(ctx, n, k, X, a, Y, b, D, ldD, upper=0):
+    ctx.check(lib().dlm_distance_batch(ctx.h, n, k, _ptr(X), a, _ptr(Y), b, _ptr(D), ldD, upper),
+              "dlm_distance_batch")
+
+
+def dlm_pool_update(ctx, p, n, fit, D, sel):
+    ctx.check(lib().dlm_pool_update(ctx.h, p, n, _ptr(fit), _ptr(D), _ptr(sel)), "dlm_pool_update")
+
+
+def dlm_knn(ctx, p, D, K, nbr):
+    ctx.check(lib().dlm_knn(ctx.h, p, _ptr(D), K, _ptr(nbr)), "dlm_knn")
+
+
+class Scorer:
+    def __init__(self, ctx: Context, n: int, k: int, seed: int):
+        h = ctypes.c_void_p()
+        ctx.check(lib().dlm_scorer_create(ctx.h, n, k, seed, ctypes.byref(h)), "dlm_scorer_create")
+        self.h, self.n, self.k = h, n, k
+        self.nparams = int(lib().dlm_scorer_nparams(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dlm_scorer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dlm_scorer_get_params(ctx, s, params):
+    ctx.check(lib().dlm_scorer_get_params(ctx.h, s.h, _ptr(params)), "dlm_scorer_get_params")
+
+
+def dlm_scorer_set_params(ctx, s, params):
+    ctx.check(lib().dlm_scorer_set_params(ctx.h, s.h, _ptr(params)), "dlm_scorer_set_params")
+
+
+def dlm_score_offspring(ctx, s, col, c, out):
+    ctx.check(lib().dlm_score_offspring(ctx.h, s.h, _ptr(col), c, _ptr(out)), "dlm_score_offspring")
+
+
+def dlm_scorer_loss_grad(ctx, s, col, y, B, grad, out, loss):
+    ctx.check(lib().dlm_scorer_loss_grad(ctx.h, s.h, _ptr(col), _ptr(y), B, _ptr(grad), _ptr(out), _ptr(loss)),
+              "dlm_scorer_loss_grad")
+
+
+def dlm_scorer_train(ctx, s, cols, fvals, p, epochs, b, lr, seed, generation):
+    ctx.check(lib().dlm_scorer_train(ctx.h, s.h, _ptr(cols), _ptr(fvals), p, epochs, b, lr, seed, generation),
+              "dlm_scorer_train")
+
+
+class Memetic:
+    def __init__(self, ctx: Context, g: Graph, params: MemeticParams):
+        h = ctypes.c_void_p()
+        ctx.check(lib().dlm_memetic_create(ctx.h, g.h, ctypes.byref(params), ctypes.byref(h)), "dlm_memetic_create")
+        self.h, self.params = h, params
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dlm_memetic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dlm_memetic_step(ctx, mm):
+    best = ctypes.c_int64(0)
+    ctx.check(lib().dlm_memetic_step(ctx.h, mm.h, ctypes.byref(best)), "dlm_memetic_step")
+    return best.value
+
+
+def dlm_memetic_get(ctx, mm, which, dst):
+    ctx.check(lib().dlm_memetic_get(ctx.h, mm.h, which, _ptr(dst)), "dlm_memetic_get")
+
+
+def dlm_memetic_set(ctx, mm, which, src):
+    ctx.check(lib().dlm_memetic_set(ctx.h, mm.h, which, _ptr(src)), "dlm_memetic_set")
+
+
+def dlm_probe_smem_bandwidth(ctx):
+    g = ctypes.c_double(0.0)
+    ctx.check(lib().dlm_probe_smem_bandwidth(ctx.h, ctypes.byref(g)), "dlm_probe_smem_bandwidth")
+    return g.value
+
+
+def dlm_wvcp_tabu_batch(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure=WVCP_TENURE, phi=0, seed=0,
+                        generation=0, ind_base=0):
+    ctx.check(lib().dlm_wvcp_tabu_batch(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_g), _ptr(best_fc), _ptr(moves),
+                                        iters, tenure, phi, seed, generation, ind_base), "dlm_wvcp_tabu_batch")

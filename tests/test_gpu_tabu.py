@@ -1,0 +1,193 @@
+"""GPU parity of graph build, initialisation, conflict table and batched TabuCol against the
+oracle, through the C-ABI. TabuCol must match bit for bit: the move of every iteration (trace),
+the best colouring, its conflicts and the number of moves."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_05948_gb300 import dlmcol, inputs
+
+from gpu_util import device_graph, gnp_case, oracle_tabu_many
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2109_05948_gb300 import build
+
+    build.build()
+    c = dlmcol.Context(0)
+    yield c
+    c.close()
+
+
+def _run_gpu(ctx, g, k, col_np, iters, seed=0, gen=0, ind_base=0, warps=0, trace=False):
+    pop, n = col_np.shape
+    col = torch.from_numpy(col_np.copy()).cuda()
+    bf = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    mv = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    tr = torch.full((pop, iters, 4), -7, dtype=torch.int32, device="cuda") if trace else None
+    dlmcol.dlm_tabucol_batch_ex(ctx, g, k, pop, col, bf, mv, iters, dlmcol.COL_TENURE, seed, gen, ind_base, warps, tr)
+    ctx.sync()
+    out = dict(col=col.cpu().numpy(), best_f=bf.cpu().numpy(), moves=mv.cpu().numpy())
+    if trace:
+        out["trace"] = tr.cpu().numpy()
+    return out
+
+
+def test_graph_build_matches_oracle(ctx):
+    for n, p, s in [(125, 0.5, 0), (500, 0.5, 0), (97, 0.1, 3), (1000, 0.9, 1), (33, 1.0, 0)]:
+        e, adj = gnp_case(n, p, s)
+        g = device_graph(ctx, n, e)
+        off, idx, bits = oracle.graph_csr(adj)
+        assert g.m == len(e)
+        doff = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+        didx = torch.zeros(max(1, 2 * g.m), dtype=torch.int32, device="cuda")
+        dbits = torch.zeros((n, (n + 31) // 32), dtype=torch.int32, device="cuda")
+        dlmcol.dlm_graph_export(ctx, g, doff, didx, dbits)
+        ctx.sync()
+        assert np.array_equal(doff.cpu().numpy(), off)
+        assert np.array_equal(didx.cpu().numpy()[: 2 * g.m], idx)
+        assert np.array_equal(dbits.cpu().numpy().view(np.uint32), bits)
+
+
+def test_graph_rejects_bad_edges(ctx):
+    with pytest.raises(dlmcol.DlmError):
+        device_graph(ctx, 5, np.array([[0, 1], [2, 5]], np.int32))
+    with pytest.raises(dlmcol.DlmError):
+        device_graph(ctx, 5, np.array([[3, 3]], np.int32))
+
+
+def test_init_colors_matches_oracle(ctx):
+    for n, k, pop, seed, base in [(125, 17, 8, 0, 0), (500, 48, 64, 5, 3), (1000, 100, 3, 2**40 + 7, 11)]:
+        col = torch.zeros((pop, n), dtype=torch.int16, device="cuda")
+        dlmcol.dlm_init_colors(ctx, n, k, pop, seed, base, col)
+        ctx.sync()
+        assert np.array_equal(col.cpu().numpy(), oracle.init_colors(n, k, pop, seed, base))
+
+
+def test_gamma_matches_oracle(ctx):
+    n, k, pop = 300, 23, 5
+    e, adj = gnp_case(n, 0.3, 2)
+    g = device_graph(ctx, n, e)
+    cols = inputs.random_colorings(pop, n, k, seed=4)
+    gam = torch.zeros((pop, n, k), dtype=torch.int32, device="cuda")
+    f = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    dlmcol.dlm_gamma(ctx, g, k, pop, torch.from_numpy(cols).cuda(), gam, f)
+    ctx.sync()
+    for i in range(pop):
+        g_ref, f_ref = oracle.gamma(adj, k, cols[i])
+        assert np.array_equal(gam[i].cpu().numpy(), g_ref) and f[i].item() == f_ref
+
+
+@pytest.mark.parametrize("warps", [1, 2, 4, 8])
+def test_tabucol_small_random_graph_trace_bitexact(ctx, warps):
+    """8 individuals on G(125, 0.5), k = 17, 10^4 iterations, seed 0 (gamma is exact in u16 for n < 65536): every
+    iteration's move, the best colouring, best f and moves equal the oracle's."""
+    n, k, pop, iters = 125, 17, 8, 10_000
+    e, adj = gnp_case(n, 0.5, 0)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, pop, 0)
+    gpu = _run_gpu(ctx, g, k, start, iters, seed=0, warps=warps, trace=True)
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 0, i, 0, True) for i in range(pop)])
+    for i, r in enumerate(refs):
+        T = r["iters"]
+        assert np.array_equal(gpu["trace"][i, :T], r["trace"]), f"individual {i}: first divergence at " \
+            f"{int(np.argmax(np.any(gpu['trace'][i, :T] != r['trace'], axis=1)))}"
+        assert gpu["best_f"][i] == r["best_f"] and gpu["moves"][i] == r["moves"]
+        assert np.array_equal(gpu["col"][i], r["best_col"])
+
+
+@pytest.mark.parametrize("n,k,p,iters,pop,seed", [
+    (64, 5, 0.3, 3000, 7, 1),      # n a multiple of 32, odd k
+    (101, 9, 0.2, 2000, 5, 2),     # ragged n
+    (260, 100, 0.9, 1500, 3, 3),   # k > 64: several words per lane
+    (700, 30, 0.5, 1000, 2, 4),    # n > 512: two bitmap words per lane
+    (2, 2, 1.0, 50, 3, 5),         # a single edge
+])
+def test_tabucol_shapes_bitexact(ctx, n, k, p, iters, pop, seed):
+    e, adj = gnp_case(n, p, seed)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, pop, seed)
+    gpu = _run_gpu(ctx, g, k, start, iters, seed=seed, gen=3, ind_base=10, trace=True)
+    refs = oracle_tabu_many([(adj, k, start[i], iters, seed, 10 + i, 3, True) for i in range(pop)])
+    for i, r in enumerate(refs):
+        assert np.array_equal(gpu["trace"][i, :r["iters"]], r["trace"])
+        assert gpu["best_f"][i] == r["best_f"] and gpu["moves"][i] == r["moves"]
+        assert np.array_equal(gpu["col"][i], r["best_col"])
+
+
+def test_tabucol_planted_early_stop_and_legal_start(ctx):
+    n, k = 200, 8
+    e, part = inputs.planted(n, k, 0.5, seed=2)
+    adj = inputs.edges_to_adj(n, e)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, 4, 1)
+    start[3] = part  # already legal: no iteration runs
+    gpu = _run_gpu(ctx, g, k, start, 50_000, seed=1, trace=False)
+    refs = oracle_tabu_many([(adj, k, start[i], 50_000, 1, i, 0, False) for i in range(4)])
+    for i, r in enumerate(refs):
+        assert gpu["best_f"][i] == r["best_f"] == 0 and gpu["moves"][i] == r["moves"]
+        assert np.array_equal(gpu["col"][i], r["best_col"])
+    assert gpu["moves"][3] == 0
+
+
+def test_tabucol_long_run_crosses_tabu_sweeps(ctx):
+    """70 000 iterations cross the 2^14 sweep of the 16-bit tabu expiries four times and wrap 2^16."""
+    n, k, pop, iters = 150, 15, 2, 70_000
+    e, adj = gnp_case(n, 0.5, 7)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, pop, 7)
+    gpu = _run_gpu(ctx, g, k, start, iters, seed=7)
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 7, i, 0, False) for i in range(pop)])
+    for i, r in enumerate(refs):
+        assert gpu["best_f"][i] == r["best_f"] and gpu["moves"][i] == r["moves"]
+        assert np.array_equal(gpu["col"][i], r["best_col"])
+
+
+def test_tabucol_rejects_bad_input(ctx):
+    n, k = 50, 4
+    e, adj = gnp_case(n, 0.3, 1)
+    g = device_graph(ctx, n, e)
+    col = torch.zeros((2, n), dtype=torch.int16, device="cuda")
+    col[1, 7] = 4  # colour outside 0..k-1
+    bf = torch.zeros(2, dtype=torch.int64, device="cuda")
+    dlmcol.dlm_tabucol_batch(ctx, g, k, 2, col, bf, None, 10)
+    with pytest.raises(dlmcol.DlmError):
+        ctx.sync()
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_tabucol_batch(ctx, g, 200, 2, col, bf, None, 10)  # k above 128
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_tabucol_batch_ex(ctx, g, k, 2, col, bf, None, 10, warps=3)
+    dlmcol.dlm_tabucol_batch(ctx, g, k, 0, col, bf, None, 10)  # empty population is a no-op
+    ctx.sync()
+
+
+def test_tabucol_full_size_sampled(ctx):
+    """The benchmarked launch: G(500, 0.5), k = 48, population 4096, 10^5 iterations, random
+    starts from seed 0. 12 sampled individuals are replayed by the oracle; for all 4096 the best
+    conflicts equal the recount of the returned colouring."""
+    n, k, pop, iters = 500, 48, 4096, 100_000
+    e, adj = gnp_case(n, 0.5, 0)
+    g = device_graph(ctx, n, e)
+    col = torch.zeros((pop, n), dtype=torch.int16, device="cuda")
+    dlmcol.dlm_init_colors(ctx, n, k, pop, 0, 0, col)
+    start = col.cpu().numpy()
+    bf = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    mv = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    dlmcol.dlm_tabucol_batch(ctx, g, k, pop, col, bf, mv, iters, dlmcol.COL_TENURE, 0, 0, 0)
+    f2 = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    dlmcol.dlm_gamma(ctx, g, k, pop, col, None, f2)
+    ctx.sync()
+    assert torch.equal(bf, f2)
+    sample = [0, 1, 2, 511, 1024, 2047, 2048, 3000, 3333, 4000, 4094, 4095]
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 0, i, 0, False) for i in sample])
+    colh, bfh, mvh = col.cpu().numpy(), bf.cpu().numpy(), mv.cpu().numpy()
+    for i, r in zip(sample, refs):
+        assert bfh[i] == r["best_f"] and mvh[i] == r["moves"], i
+        assert np.array_equal(colh[i], r["best_col"]), i
