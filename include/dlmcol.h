@@ -140,6 +140,40 @@ dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
                                 int32_t* best);
 
 /* ---------------------------------------------------------------------------------------------
+ * GPX crossover (Galinier & Hao 1999; section "Parent matching and selection of crossovers").
+ * For child t with parents A = parents[pairs[t][0]], B = parents[pairs[t][1]]: for l = 0..k-1 the
+ * child gives label l to the largest class (smallest colour on ties) not yet inherited of A (l even)
+ * or B (l odd); those vertices leave both parents. Vertices left over get the label high word of
+ * r0 * k, r = Philox(a = v, b = generation, c = child_id[t], tag = GPX).
+ *   parents  device [pop][n] int16;  pairs device [m][2] int32;  child_id device [m] uint32 or
+ *   NULL (child_id = t);  children device [m][n] int16 out.  Limits: k <= 128, n <= 2048.
+ * ------------------------------------------------------------------------------------------- */
+dlm_status dlm_gpx_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* parents, int32_t pop,
+                         const int32_t* pairs, const uint32_t* child_id, int32_t m, int16_t* children,
+                         uint64_t seed, uint32_t generation);
+
+/* ---------------------------------------------------------------------------------------------
+ * Approximate set-theoretic partition distance (section "Distance computation"): with
+ * M[c][c'] = |A_c intersect B_c'|, D = n - min(sum_c max_c' M, sum_c' max_c M), a symmetric lower
+ * bound of the exact (Hungarian) distance, exact when the best-match map is injective.
+ *   X device [a][n], Y device [b][n] int16 colourings; D device out, D[i * ldD + j] = D(X_i, Y_j).
+ *   upper != 0 with X == Y computes only j > i (and writes those entries). Limits: k <= 128.
+ * ------------------------------------------------------------------------------------------- */
+dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a, const int16_t* Y,
+                              int32_t b, int16_t* D, int64_t ldD, int32_t upper);
+
+/* Distance-and-quality pool update (section "Population update"): the 2p candidates (index < p:
+ * the population, >= p: the improved individuals) are visited by increasing fit, ties by lower
+ * index; a candidate is kept when its distance to every candidate kept so far is > n / 10; if
+ * fewer than p are kept the best remaining ones (same order) fill the population.
+ *   fit device [2p] int64;  D device [2p][2p] int16;  sel device [p] int32 out (in keep order). */
+dlm_status dlm_pool_update(dlm_ctx* ctx, int32_t p, int32_t n, const int64_t* fit, const int16_t* D, int32_t* sel);
+
+/* Parent matching (section "Parent matching ..."): the K nearest j != i of every i by D (device
+ * [p][p] int16), nearest first, ties by lower index. nbr device [p][K] int32 out. K <= 64. */
+dlm_status dlm_knn(dlm_ctx* ctx, int32_t p, const int16_t* D, int32_t K, int32_t* nbr);
+
+/* ---------------------------------------------------------------------------------------------
  * Measurement utility (no counterpart in the paper): streams conflict-free 16-byte shared-memory
  * loads on every SM and returns the achieved bandwidth in GB/s (host double). It is the
  * denominator of the tabu kernel's roofline, whose state is held in shared memory.

@@ -1,0 +1,234 @@
+// Population management: approximate partition distances (section "Distance computation"),
+// the distance-and-quality pool update (section "Population update") and the K-nearest-neighbour
+// parent matching (section "Parent matching and selection of crossovers").
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace dlm {
+
+// ------------------------------------------------------------------------------------------------
+// Distances. One CTA holds one row X_i in shared memory; each warp owns a k x k overlap table and
+// handles pairs (i, j). Per pair: count M[a][b] over the vertices (shared atomics), then row and
+// column maxima of the touched entries, then reset only the touched entries -- O(n) per pair.
+// ------------------------------------------------------------------------------------------------
+constexpr int kDistWarpsMax = 8;
+constexpr int kDistCols = 64;  // Y rows handled by one CTA
+
+__global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, const int16_t* X, int a, const int16_t* Y,
+                                                              int b, int16_t* D, int64_t ldD, int upper,
+                                                              int32_t* status) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int i = blockIdx.y;
+  const int j0 = blockIdx.x * kDistCols;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* xi = smem;                                    // [n]
+  const size_t xoff = (n + 15) & ~15;
+  // per warp: k*k u16 counters (padded to a word boundary), then k + k u32 maxima
+  const size_t kk2 = (size_t)((k * k + 1) & ~1);
+  uint16_t* M = (uint16_t*)((uint8_t*)smem + xoff + (size_t)warp * (kk2 * 2 + (size_t)k * 8));
+  uint32_t* rmax = (uint32_t*)(M + kk2);
+  uint32_t* cmax = rmax + k;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    int c = X[(size_t)i * n + v];
+    if (c < 0 || c >= k) { raise_status(status, DLM_EINVAL); c = 0; }
+    xi[v] = (uint8_t)c;
+  }
+  for (int q = lane; q < (int)kk2; q += 32) M[q] = 0;
+  for (int q = lane; q < 2 * k; q += 32) rmax[q] = 0u;
+  __syncthreads();
+  uint32_t* M32 = (uint32_t*)M;  // 16-bit counters updated through their 32-bit word
+  const int nwarps = blockDim.x >> 5;
+  for (int jj = warp; jj < kDistCols; jj += nwarps) {
+    const int j = j0 + jj;
+    if (j >= b) break;
+    if (upper && j <= i) continue;
+    const int16_t* y = Y + (size_t)j * n;
+    for (int v = lane; v < n; v += 32) {
+      int c2 = y[v];
+      if (c2 < 0 || c2 >= k) { raise_status(status, DLM_EINVAL); c2 = 0; }
+      const int q = xi[v] * k + c2;
+      atomicAdd(M32 + (q >> 1), 1u << (16 * (q & 1)));
+    }
+    __syncwarp();
+    for (int v = lane; v < n; v += 32) {
+      int c2 = y[v];
+      c2 = (c2 < 0 || c2 >= k) ? 0 : c2;
+      const int c1 = xi[v];
+      const unsigned cnt = M[c1 * k + c2];
+      atomicMax(rmax + c1, cnt);
+      atomicMax(cmax + c2, cnt);
+    }
+    __syncwarp();
+    int sr = 0, scl = 0;
+    for (int c = lane; c < k; c += 32) { sr += (int)rmax[c]; scl += (int)cmax[c]; }
+    sr = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)sr);
+    scl = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)scl);
+    if (lane == 0) D[(size_t)i * ldD + j] = (int16_t)(n - (sr < scl ? sr : scl));
+    __syncwarp();
+    for (int v = lane; v < n; v += 32) {
+      int c2 = y[v];
+      c2 = (c2 < 0 || c2 >= k) ? 0 : c2;
+      M[xi[v] * k + c2] = 0;
+    }
+    for (int c = lane; c < k; c += 32) { rmax[c] = 0u; cmax[c] = 0u; }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Pool update: one CTA. Candidates are sorted by (f, index) with a shared-memory bitonic sort of
+// 64-bit keys; then the greedy pass admits a candidate when no admitted member is within n/10
+// (the check of the admitted list is split across the threads, one barrier per candidate).
+// ------------------------------------------------------------------------------------------------
+constexpr int kPoolThreads = 1024;
+
+__global__ void __launch_bounds__(kPoolThreads) k_pool_update(int p, int n, const int64_t* fit, const int16_t* D,
+                                                              int32_t* sel, int32_t* status) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int m = 2 * p;
+  int mp = 1;
+  while (mp < m) mp <<= 1;
+  uint64_t* key = (uint64_t*)smem;             // [mp]
+  int32_t* adm = (int32_t*)(key + mp);          // [p] admitted, in order
+  uint8_t* chosen = (uint8_t*)(adm + p);        // [m]
+  __shared__ int cnt;
+  __shared__ int reject;
+  const int t = threadIdx.x;
+  for (int q = t; q < mp; q += blockDim.x) {
+    if (q < m) {
+      int64_t f = fit[q];
+      if (f < 0 || f >= ((int64_t)1 << 43)) { raise_status(status, DLM_EINVAL); f = 0; }
+      key[q] = ((uint64_t)f << 20) | (uint64_t)q;
+    } else {
+      key[q] = ~0ull;
+    }
+  }
+  for (int q = t; q < m; q += blockDim.x) chosen[q] = 0;
+  if (t == 0) cnt = 0;
+  __syncthreads();
+  for (int size = 2; size <= mp; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = t; q < mp; q += blockDim.x) {
+        const int r = q ^ stride;
+        if (r > q) {
+          const bool up = (q & size) == 0;
+          const uint64_t x = key[q], y = key[r];
+          if ((x > y) == up) { key[q] = y; key[r] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  const int64_t lim = n;  // admitted when 10 * D > n
+  for (int s = 0; s < m; ++s) {
+    const int c = cnt;  // uniform (written before the last barrier)
+    if (c >= p) break;
+    const int x = (int)(key[s] & 0xFFFFF);
+    if (t == 0) reject = 0;
+    __syncthreads();
+    int bad = 0;
+    const int16_t* row = D + (size_t)x * m;
+    for (int q = t; q < c; q += blockDim.x)
+      if (10 * (int64_t)row[adm[q]] <= lim) bad = 1;
+    bad = __syncthreads_or(bad);
+    if (t == 0 && !bad) { adm[c] = x; chosen[x] = 1; cnt = c + 1; }
+    __syncthreads();
+  }
+  // fill with the best remaining candidates when fewer than p were spaced
+  if (t == 0) {
+    int c = cnt;
+    for (int s = 0; s < m && c < p; ++s) {
+      const int x = (int)(key[s] & 0xFFFFF);
+      if (!chosen[x]) { adm[c++] = x; chosen[x] = 1; }
+    }
+    cnt = c;
+  }
+  __syncthreads();
+  for (int q = t; q < p; q += blockDim.x) sel[q] = adm[q];
+}
+
+// ------------------------------------------------------------------------------------------------
+// K nearest neighbours: one warp per row; the row's keys (D << 16 | j) sit in shared memory and
+// K rounds of redux.sync min pick them in increasing order.
+// ------------------------------------------------------------------------------------------------
+constexpr int kKnnWarps = 4;
+
+__global__ void __launch_bounds__(32 * kKnnWarps) k_knn(int p, const int16_t* D, int K, int32_t* nbr) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* keys = (uint32_t*)smem + (size_t)warp * p;
+  for (int i = blockIdx.x * kKnnWarps + warp; i < p; i += gridDim.x * kKnnWarps) {
+    for (int j = lane; j < p; j += 32) {
+      const int d = D[(size_t)i * p + j];
+      keys[j] = j == i ? 0xFFFFFFFFu : (((uint32_t)(d < 0 ? 0 : d) << 16) | (uint32_t)j);
+    }
+    __syncwarp();
+    uint32_t last = 0;
+    bool first = true;
+    for (int r = 0; r < K; ++r) {
+      uint32_t best = 0xFFFFFFFFu;
+      for (int j = lane; j < p; j += 32) {
+        const uint32_t x = keys[j];
+        if ((first || x > last) && x < best) best = x;
+      }
+      best = __reduce_min_sync(0xFFFFFFFFu, best);
+      if (lane == 0) nbr[(size_t)i * K + r] = (int32_t)(best & 0xFFFF);
+      last = best;
+      first = false;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace dlm
+
+using namespace dlm;
+
+extern "C" dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
+                                         const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper) {
+  if (!ctx) return DLM_EINVAL;
+  if (n < 1 || n > 2048 || k < 1 || a < 0 || b < 0 || ldD < b) return fail(ctx, DLM_EINVAL, "distance: bad sizes");
+  if (k > 128) return fail(ctx, DLM_EUNSUPPORTED, "distance: k must be <= 128");
+  if (a == 0 || b == 0) return DLM_OK;
+  if (!X || !Y || !D) return fail(ctx, DLM_EINVAL, "distance: null pointer");
+  if (a > 65535) return fail(ctx, DLM_EUNSUPPORTED, "distance: at most 65535 rows");
+  // as many warps (overlap tables) as shared memory allows, up to 8
+  const size_t per_warp = (size_t)((k * k + 1) & ~1) * 2 + (size_t)k * 8;
+  const size_t head = ((n + 15) & ~15) + 16;
+  int warps = kDistWarpsMax;
+  while (warps > 1 && head + warps * per_warp > ctx->smem_optin) --warps;
+  const size_t smem = head + warps * per_warp;
+  if (smem > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "distance: shared memory");
+  DLM_CUDA(ctx, cudaFuncSetAttribute(k_distance, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((b + kDistCols - 1) / kDistCols, a);
+  k_distance<<<grid, 32 * warps, smem, ctx->stream>>>(n, k, X, a, Y, b, D, ldD, upper, ctx->d_status);
+  return launch_check(ctx, "k_distance");
+}
+
+extern "C" dlm_status dlm_pool_update(dlm_ctx* ctx, int32_t p, int32_t n, const int64_t* fit, const int16_t* D,
+                                      int32_t* sel) {
+  if (!ctx) return DLM_EINVAL;
+  if (p < 1 || n < 1) return fail(ctx, DLM_EINVAL, "pool_update: bad sizes");
+  if (!fit || !D || !sel) return fail(ctx, DLM_EINVAL, "pool_update: null pointer");
+  const int m = 2 * p;
+  int mp = 1;
+  while (mp < m) mp <<= 1;
+  const size_t smem = (size_t)mp * 8 + (size_t)p * 4 + m + 16;
+  if (smem > ctx->smem_optin || m > (1 << 20)) return fail(ctx, DLM_EUNSUPPORTED, "pool_update: p too large");
+  DLM_CUDA(ctx, cudaFuncSetAttribute(k_pool_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_pool_update<<<1, kPoolThreads, smem, ctx->stream>>>(p, n, fit, D, sel, ctx->d_status);
+  return launch_check(ctx, "k_pool_update");
+}
+
+extern "C" dlm_status dlm_knn(dlm_ctx* ctx, int32_t p, const int16_t* D, int32_t K, int32_t* nbr) {
+  if (!ctx) return DLM_EINVAL;
+  if (p < 2 || K < 1 || K > p - 1 || K > 64) return fail(ctx, DLM_EINVAL, "knn: need 1 <= K <= min(64, p - 1)");
+  if (p > 65535) return fail(ctx, DLM_EUNSUPPORTED, "knn: p must be < 65536");
+  if (!D || !nbr) return fail(ctx, DLM_EINVAL, "knn: null pointer");
+  const size_t smem = (size_t)kKnnWarps * p * 4;
+  if (smem > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "knn: p too large for shared memory");
+  DLM_CUDA(ctx, cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::min((p + kKnnWarps - 1) / kKnnWarps, ctx->num_sms * 4);
+  k_knn<<<grid, 32 * kKnnWarps, smem, ctx->stream>>>(p, D, K, nbr);
+  return launch_check(ctx, "k_knn");
+}

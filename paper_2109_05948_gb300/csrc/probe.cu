@@ -12,12 +12,17 @@ __global__ void __launch_bounds__(1024) k_smem_probe(int reps, uint4* sink) {
     buf[i] = make_uint4(i, i * 3u, i * 5u, i * 7u);
   __syncthreads();
   uint4 acc = make_uint4(0, 0, 0, 0);
-  int idx = threadIdx.x;
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
+  uint32_t idx = threadIdx.x;
 #pragma unroll 4
   for (int r = 0; r < reps; ++r) {
-    const uint4 v = buf[idx];
+    uint4 v;
+    // volatile: every iteration really reads shared memory
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(base + 16u * idx));
     acc.x ^= v.x; acc.y += v.y; acc.z ^= v.z; acc.w += v.w;
-    idx = (idx + 1024) & 2047;
+    idx = (idx + 1024u + (uint32_t)(r & 1)) & 2047u;
   }
   if (acc.x == 0x12345678u && acc.y == 0x9abcdef0u) sink[blockIdx.x] = acc;
 }

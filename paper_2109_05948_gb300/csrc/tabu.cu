@@ -4,21 +4,22 @@
 //
 // GB300 design (differs from the paper's one-thread-per-individual Numba kernel):
 //  * one CTA of W warps per individual; its whole search state lives in shared memory:
-//      gam[n][ks] u16  conflict table gamma (row stride ks u16, ks/2 odd words so that the
-//                      scattered row updates of one warp spread over the banks)
+//      gam[n][ks] u16  conflict table gamma (row stride ks u16 with ks/2 odd, so that the
+//                      scattered row updates of a warp spread over the banks)
 //      tab[n][ks] u16  tabu expiry iteration modulo 2^16 (kept within +-2^15 of the iteration
 //                      counter by a sweep every 2^14 iterations)
 //      col[n], best[n] u8 current and best colouring; cv[] u32 bitmap of conflicting vertices;
-//      rowres[n] u32   (row minimum, tie count) of each conflicting row of the current scan.
-//  * scan: warps take the conflicting rows round-robin; a warp reads one row with one u32 (two
-//    colours) per lane and reduces (min delta, #ties) with redux.sync -- no shared atomics.
-//  * selection: warp 0 combines the warp results, draws the iteration's Philox block and walks the
-//    per-row tie counts (warp prefix sums) to the j-th tied move in (v, c) order, then rescans that
-//    one row with ballots.
+//      rowres[n] u32   (row minimum delta, tie count) of each conflicting row of the scan.
+//  * scan: each warp compacts the bitmap into its own list of conflicting vertices; thread t
+//    scans a contiguous block of rows (two colours per 32-bit word, no warp collectives inside a
+//    row), so threads run their rows in parallel and the order of rows follows the thread order.
+//  * selection: block minimum of delta, then a block prefix sum of the per-thread tie counts;
+//    the thread holding the j-th tied move (j drawn from the iteration's Philox block) applies it,
+//    using the tie mask of the row it scanned last.
 //  * update: the adjacency bit row of the moved vertex (prefetched into L1 during the scan) is
 //    split across all threads; each neighbour costs two u16 read-modify-writes of its gamma row
 //    and, when its conflict status flips, one shared atomic on the bitmap.
-//  Three CTA barriers per iteration.
+//  Four CTA barriers per iteration.
 #include <algorithm>
 #include <climits>
 #include <vector>
@@ -60,7 +61,7 @@ __host__ __device__ inline int tabu_row_stride(int k) {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct TabuSmem {
-  size_t gam, tab, col, best, rowres, cv, red, total;
+  size_t gam, tab, col, best, rowres, deg, cvl, cv, red, total;
 };
 
 __host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps) {
@@ -72,6 +73,8 @@ __host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps) {
   s.col = o; o += align16(n);
   s.best = o; o += align16(n);
   s.rowres = o; o += align16((size_t)n * 4);
+  s.deg = o; o += align16((size_t)n * 2);
+  s.cvl = o; o += align16((size_t)warps * n * 2);
   s.cv = o; o += 64 * 4;
   s.red = o; o += align16((size_t)warps * 8 + 64);
   s.total = o;
@@ -87,6 +90,12 @@ __device__ __forceinline__ int nth_set_bit(uint32_t x, int r) {
     if (r >= c) { r -= c; x >>= s; pos += s; }
   }
   return pos;
+}
+
+__device__ __forceinline__ int nth_set_bit64(uint64_t x, int r) {
+  const uint32_t lo = (uint32_t)x;
+  const int pl = __popc(lo);
+  return r < pl ? nth_set_bit(lo, r) : 32 + nth_set_bit((uint32_t)(x >> 32), r - pl);
 }
 
 // Warp view of the conflicting-vertex bitmap: lane l owns bitmap words 2l and 2l+1 (vertices
@@ -113,28 +122,62 @@ __device__ __forceinline__ CvView cv_view(const uint32_t* cv, int nwords, int la
   return c;
 }
 
-// vertex id of the i-th conflicting vertex (0 <= i < total); warp-collective
-__device__ __forceinline__ int cv_select(const CvView& c, int i, int lane) {
-  const unsigned bal = __ballot_sync(FULL, i >= c.excl && i < c.excl + c.cnt);
-  const int L = __ffs(bal) - 1;
-  int v = 0;
-  if (lane == L) {
-    const int r = i - c.excl;
-    const uint32_t lo = (uint32_t)c.w, hi = (uint32_t)(c.w >> 32);
-    const int pl = __popc(lo);
-    v = 64 * lane + (r < pl ? nth_set_bit(lo, r) : 32 + nth_set_bit(hi, r - pl));
+// Scan of one conflicting row v by one thread. The key of colour c is gamma[v][c] when the move
+// (v, c) is admissible (not tabu, or tabu but f + delta < best_f, i.e. gamma < thr with
+// thr = best_f - f + gamma[v][col v]) and 0xFFFF otherwise; the current colour and the padding
+// columns carry gamma = 0xFFFF. Returns the row's minimum key and the columns reaching it.
+struct RowScan {
+  unsigned kmin;
+  uint64_t m0, m1;  // colours 0..63, 64..127 reaching kmin
+};
+
+__device__ __forceinline__ RowScan scan_row(const uint16_t* gam, const uint16_t* tab, int ks, int kw, int v, int colv,
+                                            int thr, int it16) {
+  const uint32_t* g32 = (const uint32_t*)(gam + (size_t)v * ks);
+  const uint32_t* t32 = (const uint32_t*)(tab + (size_t)v * ks);
+  const int killw = colv >> 1;
+  const uint32_t killm = 0xFFFFu << (16 * (colv & 1));
+  RowScan r{0xFFFFu, 0ull, 0ull};
+  const int wlo = kw < 32 ? kw : 32;
+#pragma unroll 4
+  for (int w = 0; w < wlo; ++w) {
+    uint32_t gw = g32[w];
+    const uint32_t tw = t32[w];
+    if (w == killw) gw |= killm;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = (gw >> (16 * h)) & 0xFFFF;
+      const int te = (tw >> (16 * h)) & 0xFFFF;
+      const bool tabu = (int16_t)(uint16_t)(te - it16) > 0;
+      const unsigned key = (!tabu || g < thr) ? (unsigned)g : 0xFFFFu;
+      const uint64_t bit = 1ull << (2 * w + h);
+      if (key < r.kmin) { r.kmin = key; r.m0 = 0ull; }
+      if (key == r.kmin) r.m0 |= bit;
+    }
   }
-  return __shfl_sync(FULL, v, L);
+  for (int w = 32; w < kw; ++w) {
+    uint32_t gw = g32[w];
+    const uint32_t tw = t32[w];
+    if (w == killw) gw |= killm;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = (gw >> (16 * h)) & 0xFFFF;
+      const int te = (tw >> (16 * h)) & 0xFFFF;
+      const bool tabu = (int16_t)(uint16_t)(te - it16) > 0;
+      const unsigned key = (!tabu || g < thr) ? (unsigned)g : 0xFFFFu;
+      const uint64_t bit = 1ull << ((2 * w + h) & 63);
+      if (key < r.kmin) { r.kmin = key; r.m0 = 0ull; r.m1 = 0ull; }
+      if (key == r.kmin) r.m1 |= bit;
+    }
+  }
+  return r;
 }
 
-// key of one (v, c) entry: delta if the move is admissible, INT_MAX otherwise
-__device__ __forceinline__ int move_key(int c, int k, int colv, int gc, int te, int g0, int it16, int f, int best_f) {
-  const int d = gc - g0;
-  const bool tabu = (int16_t)(uint16_t)(te - it16) > 0;
-  const bool adm = (c < k) && (c != colv) && (!tabu || f + d < best_f);
-  return adm ? d : INT_MAX;
-}
-
+// One individual, one CTA of W warps.
+// Per iteration: (1) every warp compacts the conflicting-vertex bitmap into its own list; thread
+// t scans rows [tC, tC + C) of that list (C = ceil(|CV| / threads)), keeping per-row (min delta,
+// #ties) and its own aggregate; (2) block min of delta; (3) block prefix of the tie counts: the
+// thread holding the j-th tie applies the move; (4) all threads update gamma on the neighbours.
 template <int W>
 __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t* smem) {
   constexpr int NT = 32 * W;
@@ -146,19 +189,25 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   uint8_t* colS = smem + L.col;
   uint8_t* bestS = smem + L.best;
   uint32_t* rowres = (uint32_t*)(smem + L.rowres);
+  uint16_t* degS = (uint16_t*)(smem + L.deg);
+  uint16_t* cvl = (uint16_t*)(smem + L.cvl) + (size_t)warp * n;
   uint32_t* cv = (uint32_t*)(smem + L.cv);
-  int32_t* red = (int32_t*)(smem + L.red);   // [W] min, [W] count
+  int32_t* red = (int32_t*)(smem + L.red);   // [W] warp minima, [W] warp tie totals
   int32_t* sc = red + 2 * W;                 // scalars
   // sc[0] moved vertex (-1 none), sc[1] old colour, sc[2] new colour, sc[3] f after,
-  // sc[4] improved, sc[5] error, sc[6] bad input
+  // sc[4] improved, sc[5] error, sc[6] bad input, sc[7] r0, sc[8] r1
 
-  // ---- set-up: zero the tables, load the start colouring ------------------------------------
+  // ---- set-up: zero the tables (padding colours of gamma = 0xFFFF), load the start colouring --
   {
     uint32_t* g32 = (uint32_t*)gam;
     uint32_t* t32 = (uint32_t*)tab;
     const int nw32 = n * kw;
-    for (int i = tid; i < nw32; i += NT) { g32[i] = 0u; t32[i] = 0u; }
-    if (tid < 8) sc[tid] = 0;
+    for (int i = tid; i < nw32; i += NT) {
+      const int c0 = 2 * (i % kw);
+      g32[i] = (c0 >= k ? 0xFFFFu : 0u) | (c0 + 1 >= k ? 0xFFFF0000u : 0u);
+      t32[i] = 0u;
+    }
+    if (tid < 16) sc[tid] = 0;
     for (int i = tid; i < 64; i += NT) cv[i] = 0u;
   }
   __syncthreads();
@@ -178,14 +227,17 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   for (int v = tid; v < n; v += NT) {
     const uint32_t* brow = J.bits + (size_t)v * nwords;
     uint16_t* grow = gam + (size_t)v * ks;
+    int dv = 0;
     for (int w = 0; w < nwords; ++w) {
       uint32_t m = __ldg(brow + w);
+      dv += __popc(m);
       while (m) {
         const int u = 32 * w + __ffs(m) - 1;
         m &= m - 1;
         grow[colS[u]]++;
       }
     }
+    degS[v] = (uint16_t)dv;
   }
   __syncthreads();
   int f;
@@ -224,139 +276,109 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   for (it = 0; it < J.iters; ++it) {
     if (f == 0) break;
     const int it16 = (int)(it & 0xFFFF);
-    // ---- phase 1: scan of the conflicting rows --------------------------------------------
+    // ---- phase 1: conflicting-vertex list of this warp, scan of this thread's rows -----------
     const CvView view = cv_view(cv, nwords, lane);
+    {
+      uint64_t wb = view.w;
+      int pos = view.excl;
+      while (wb) {
+        cvl[pos++] = (uint16_t)(64 * lane + __ffsll(wb) - 1);
+        wb &= wb - 1;
+      }
+    }
+    __syncwarp();
     const int ncv = view.total;
-    if (tid == 0) work_rows += ncv;
-    int wmin = INT_MAX, wcnt = 0;
-    for (int i = warp; i < ncv; i += W) {
-      const int v = cv_select(view, i, lane);
-      if (lane == 0) {  // the moved vertex's bit row is needed in phase 3: pull it into L1
+    if (tid == 0) {
+      work_rows += ncv;
+      const U4 r = rng(R.seed, (uint32_t)it, R.gen, J.ind, kTagTabu);
+      sc[7] = (int32_t)r.x;
+      sc[8] = (int32_t)r.y;
+    }
+    const int C = (ncv + NT - 1) / NT;
+    const int i0 = tid * C;
+    const int i1 = min(i0 + C, ncv);
+    int tmin = INT_MAX, tcnt = 0;
+    RowScan last{0xFFFFu, 0ull, 0ull};
+    for (int i = i0; i < i1; ++i) {
+      const int v = cvl[i];
+      {
         const char* p = (const char*)(J.bits + (size_t)v * nwords);
         asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
         asm volatile("prefetch.global.L1 [%0];" ::"l"(p + nwords * 4 - 4));
       }
       const int colv = colS[v];
-      const uint16_t* grow = gam + (size_t)v * ks;
-      const uint32_t* g32 = (const uint32_t*)grow;
-      const uint32_t* t32 = (const uint32_t*)(tab + (size_t)v * ks);
-      const int g0 = grow[colv];
-      int lm = INT_MAX, lc = 0;
-      for (int wd = lane; wd < kw; wd += 32) {
-        const uint32_t gw = g32[wd], tw = t32[wd];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int key = move_key(2 * wd + h, k, colv, (gw >> (16 * h)) & 0xFFFF, (tw >> (16 * h)) & 0xFFFF, g0,
-                                   it16, f, best_f);
-          if (key < lm) { lm = key; lc = 1; }
-          else if (key == lm && key != INT_MAX) lc++;
-        }
+      const int g0 = gam[(size_t)v * ks + colv];
+      last = scan_row(gam, tab, ks, kw, v, colv, best_f - f + g0, it16);
+      const int rc = last.kmin == 0xFFFFu ? 0 : __popcll(last.m0) + __popcll(last.m1);
+      const int dm = last.kmin == 0xFFFFu ? kNone16 : (int)last.kmin - g0;
+      rowres[i] = ((uint32_t)(uint16_t)dm << 16) | (uint32_t)rc;
+      if (rc > 0) {
+        if (dm < tmin) { tmin = dm; tcnt = rc; }
+        else if (dm == tmin) tcnt += rc;
       }
-      const int m = __reduce_min_sync(FULL, lm);
-      const int c = (int)__reduce_add_sync(FULL, (m != INT_MAX && lm == m) ? (unsigned)lc : 0u);
-      if (lane == 0) rowres[i] = ((uint32_t)(uint16_t)(m == INT_MAX ? kNone16 : m) << 16) | (uint32_t)c;
-      if (m < wmin) { wmin = m; wcnt = c; }
-      else if (m == wmin && m != INT_MAX) wcnt += c;
     }
-    if (lane == 0) { red[warp] = wmin; red[W + warp] = wcnt; }
+    const int wm = __reduce_min_sync(FULL, tmin);
+    if (lane == 0) red[warp] = wm;
     __syncthreads();
-    // ---- phase 2: selection and move (warp 0) -------------------------------------------------
-    if (warp == 0) {
-      const U4 r = rng(R.seed, (uint32_t)it, R.gen, J.ind, kTagTabu);
-      const int key = lane < W ? red[lane] : INT_MAX;
-      const int cntw = lane < W ? red[W + lane] : 0;
-      const int dstar = __reduce_min_sync(FULL, key);
-      const int T = (int)__reduce_add_sync(FULL, (dstar != INT_MAX && key == dstar) ? (unsigned)cntw : 0u);
-      int mv = -1, mc = -1;
-      if (T > 0) {
-        const uint32_t j = below(r.x, (uint32_t)T);
-        uint32_t base = 0;
-        int irow = -1;
-        uint32_t jj = 0;
-        for (int i0 = 0; i0 < ncv; i0 += 32) {
-          const int i = i0 + lane;
-          const uint32_t rr = i < ncv ? rowres[i] : ((uint32_t)kNone16 << 16);
-          const int rm = (int16_t)(rr >> 16);
-          const int cc = rm == dstar ? (int)(rr & 0xFFFF) : 0;
-          int incl = cc;
+    // ---- phase 2: minimum delta, tie ranks, move ---------------------------------------------
+    int dstar = INT_MAX;
 #pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const int t = __shfl_up_sync(FULL, incl, d);
-            if (lane >= d) incl += t;
-          }
-          const uint32_t tot = (uint32_t)__shfl_sync(FULL, incl, 31);
-          if (j < base + tot) {
-            const unsigned bal = __ballot_sync(FULL, j < base + (uint32_t)incl);
-            const int Lr = __ffs(bal) - 1;
-            irow = i0 + Lr;
-            jj = j - base - (uint32_t)__shfl_sync(FULL, incl - cc, Lr);
-            break;
-          }
-          base += tot;
-        }
-        if (irow < 0) {  // tie counts inconsistent with the scan: refuse to move
-          if (lane == 0) sc[5] = 2;
-          irow = 0;
-        }
-        mv = cv_select(view, irow, lane);
-        const int colv = colS[mv];
-        const uint16_t* grow = gam + (size_t)mv * ks;
-        const uint32_t* g32 = (const uint32_t*)grow;
-        const uint32_t* t32 = (const uint32_t*)(tab + (size_t)mv * ks);
-        const int g0 = grow[colv];
-        for (int wd0 = 0; wd0 < kw; wd0 += 32) {
-          const int wd = wd0 + lane;
-          int b0 = 0, b1 = 0;
-          if (wd < kw) {
-            const uint32_t gw = g32[wd], tw = t32[wd];
-            b0 = move_key(2 * wd, k, colv, gw & 0xFFFF, tw & 0xFFFF, g0, it16, f, best_f) == dstar;
-            b1 = move_key(2 * wd + 1, k, colv, gw >> 16, tw >> 16, g0, it16, f, best_f) == dstar;
-          }
-          const int cc = b0 + b1;
-          int incl = cc;
+    for (int w = 0; w < W; ++w) dstar = min(dstar, red[w]);
+    const int ct = (dstar != INT_MAX && tmin == dstar) ? tcnt : 0;
+    int incl = ct;
 #pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const int t = __shfl_up_sync(FULL, incl, d);
-            if (lane >= d) incl += t;
-          }
-          const uint32_t tot = (uint32_t)__shfl_sync(FULL, incl, 31);
-          if (jj < tot) {
-            const unsigned bal = __ballot_sync(FULL, jj < (uint32_t)incl);
-            const int Lc = __ffs(bal) - 1;
-            int cpick = 0;
-            if (lane == Lc) {
-              const uint32_t before = (uint32_t)(incl - cc);
-              cpick = (b0 && jj == before) ? 2 * wd : 2 * wd + 1;
-            }
-            mc = __shfl_sync(FULL, cpick, Lc);
-            break;
-          }
-          jj -= tot;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (lane == 31) red[W + warp] = incl;
+    if (tid == 0) sc[0] = -1;
+    __syncthreads();
+    int T = 0, pre = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const int x = red[W + w];
+      T += x;
+      pre += w < warp ? x : 0;
+    }
+    if (T > 0 && ct > 0) {
+      const uint32_t j = below((uint32_t)sc[7], (uint32_t)T);
+      const int lo = pre + incl - ct;
+      if ((int)j >= lo && (int)j < lo + ct) {  // this thread holds the j-th tied move
+        int jj = (int)j - lo;
+        int mv = -1, mc = -1;
+        for (int i = i0; i < i1; ++i) {
+          const uint32_t rr = rowres[i];
+          const int rm = (int16_t)(rr >> 16), rcn = (int)(rr & 0xFFFF);
+          if (rm != dstar || rcn == 0) continue;
+          if (jj >= rcn) { jj -= rcn; continue; }
+          const int v = cvl[i];
+          const int colv = colS[v];
+          RowScan rs = last;
+          if (i != i1 - 1) rs = scan_row(gam, tab, ks, kw, v, colv, best_f - f + gam[(size_t)v * ks + colv], it16);
+          const int p0 = __popcll(rs.m0);
+          mv = v;
+          mc = jj < p0 ? nth_set_bit64(rs.m0, jj) : 64 + nth_set_bit64(rs.m1, jj - p0);
+          break;
         }
-      }
-      if (lane == 0 && mv >= 0 && (mc < 0 || mc >= k)) { sc[5] = 2; mv = -1; }
-      if (lane == 0) {
-        if (mv >= 0 && sc[5] == 0) {
+        if (mv >= 0 && mc >= 0 && mc < k) {
           const int old = colS[mv];
           colS[mv] = (uint8_t)mc;
           const int fn = f + dstar;
-          const int64_t tt = (int64_t)below(r.y, R.L1) + ((int64_t)R.an * fn) / R.ad;
+          const int64_t tt = (int64_t)below((uint32_t)sc[8], R.L1) + ((int64_t)R.an * fn) / R.ad;
           if (tt > 32766) sc[5] = 1;
           tab[(size_t)mv * ks + old] = (uint16_t)((it + 1 + tt) & 0xFFFF);
           const uint32_t bit = 1u << (mv & 31);
-          if (gam[(size_t)mv * ks + mc] > 0) cv[mv >> 5] |= bit;
-          else cv[mv >> 5] &= ~bit;
+          if (gam[(size_t)mv * ks + mc] > 0) atomicOr(cv + (mv >> 5), bit);
+          else atomicAnd(cv + (mv >> 5), ~bit);
           sc[0] = mv; sc[1] = old; sc[2] = mc; sc[3] = fn; sc[4] = fn < best_f;
-          if (J.trace) {
-            int4 t4 = make_int4(mv, mc, dstar, T);
-            reinterpret_cast<int4*>(J.trace)[it] = t4;
-          }
+          if (J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(mv, mc, dstar, T);
         } else {
-          sc[0] = -1;
-          if (J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(-1, -1, 0, 0);
+          sc[5] = 2;  // tie counts inconsistent with the scan: refuse to move
         }
       }
     }
+    if (T == 0 && tid == 0 && J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(-1, -1, 0, 0);
     __syncthreads();
     if (sc[5]) break;
     // ---- phase 3: gamma update over the neighbours of the moved vertex ------------------------
@@ -365,7 +387,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       const int old = sc[1], nw = sc[2];
       f = sc[3];
       ++moves;
-      if (tid == 0 && J.work) work_deg += __ldg(J.off + mv + 1) - __ldg(J.off + mv);
+      if (tid == 0) work_deg += degS[mv];
       const uint32_t* brow = J.bits + (size_t)mv * nwords;
       for (int b0 = tid * per; b0 < n; b0 += NT * per) {
         uint32_t m = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
@@ -485,6 +507,7 @@ template <int W>
 static dlm_status launch_batch(dlm_ctx* ctx, const TabuBatchArgs& a, size_t smem) {
   auto kfn = tabucol_batch_kernel<W>;
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   kfn<<<a.pop, W * 32, smem, ctx->stream>>>(a);
   return launch_check(ctx, "tabucol_batch_kernel");
 }
@@ -659,6 +682,7 @@ extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dl
   dlm_status st = DLM_OK;
   auto go = [&](auto kfn) -> dlm_status {
     DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     DLM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem));
     if (per_sm < 1) per_sm = 1;
     const int grid = (int)std::min<size_t>((size_t)per_sm * ctx->num_sms, jobs.size());

@@ -1,0 +1,131 @@
+"""GPU parity of GPX, distances, pool update and K-nearest-neighbour matching against the oracle,
+through the C-ABI (all integer work: bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_05948_gb300 import dlmcol, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2109_05948_gb300 import build
+
+    build.build()
+    c = dlmcol.Context(0)
+    yield c
+    c.close()
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n,k,pop,m", [(300, 20, 50, 200), (1000, 48, 64, 300), (97, 101, 9, 40), (2048, 7, 4, 8),
+                                       (1, 3, 2, 3)])
+def test_gpx_matches_oracle(ctx, n, k, pop, m):
+    rng = np.random.default_rng(n + k)
+    parents = inputs.random_colorings(pop, n, k, seed=n)
+    pairs = rng.integers(0, pop, size=(m, 2)).astype(np.int32)
+    pairs[: min(m, 3), 1] = pairs[: min(m, 3), 0]  # identical parents
+    cid = rng.integers(0, 2**32, size=m, dtype=np.uint64).astype(np.uint32)
+    out = torch.zeros((m, n), dtype=torch.int16, device="cuda")
+    dlmcol.dlm_gpx_batch(ctx, n, k, _cuda(parents), pop, _cuda(pairs), _cuda(cid), m, out, 77, 5)
+    ctx.sync()
+    got = out.cpu().numpy()
+    for t in range(m):
+        ref = oracle.gpx(k, parents[pairs[t, 0]], parents[pairs[t, 1]], seed=77, child_id=int(cid[t]), gen=5)
+        assert np.array_equal(got[t], ref), t
+
+
+def test_gpx_default_child_ids_and_bad_pairs(ctx):
+    n, k, pop = 120, 9, 6
+    parents = inputs.random_colorings(pop, n, k, seed=1)
+    pairs = np.array([[0, 1], [2, 3], [5, 4]], np.int32)
+    out = torch.zeros((3, n), dtype=torch.int16, device="cuda")
+    dlmcol.dlm_gpx_batch(ctx, n, k, _cuda(parents), pop, _cuda(pairs), None, 3, out, 1, 0)
+    ctx.sync()
+    for t in range(3):
+        assert np.array_equal(out[t].cpu().numpy(), oracle.gpx(k, parents[pairs[t, 0]], parents[pairs[t, 1]], 1, t, 0))
+    bad = np.array([[0, 6]], np.int32)
+    dlmcol.dlm_gpx_batch(ctx, n, k, _cuda(parents), pop, _cuda(bad), None, 1, out, 1, 0)
+    with pytest.raises(dlmcol.DlmError):
+        ctx.sync()
+
+
+@pytest.mark.parametrize("n,k,a,b", [(257, 33, 40, 70), (1000, 48, 17, 130), (64, 128, 5, 9), (3, 2, 4, 4)])
+def test_distance_matches_oracle(ctx, n, k, a, b):
+    X = inputs.random_colorings(a, n, k, seed=a)
+    Y = inputs.random_colorings(b, n, k, seed=b + 1)
+    Y[0] = X[0]  # a zero distance
+    ld = b + 3
+    D = torch.full((a, ld), -1, dtype=torch.int16, device="cuda")
+    dlmcol.dlm_distance_batch(ctx, n, k, _cuda(X), a, _cuda(Y), b, D, ld, 0)
+    ctx.sync()
+    got = D.cpu().numpy()
+    assert np.array_equal(got[:, :b], oracle.distance_matrix(k, X, Y))
+    assert np.all(got[:, b:] == -1)
+
+
+def test_distance_upper_triangle(ctx):
+    n, k, a = 200, 12, 50
+    X = inputs.random_colorings(a, n, k, seed=3)
+    D = torch.full((a, a), -1, dtype=torch.int16, device="cuda")
+    dlmcol.dlm_distance_batch(ctx, n, k, _cuda(X), a, _cuda(X), a, D, a, 1)
+    ctx.sync()
+    got = D.cpu().numpy()
+    ref = oracle.distance_matrix(k, X, X)
+    iu = np.triu_indices(a, 1)
+    assert np.array_equal(got[iu], ref[iu])
+    assert np.all(got[np.tril_indices(a)] == -1)
+
+
+def _random_pool_case(p, n, seed, spread):
+    rng = np.random.default_rng(seed)
+    m = 2 * p
+    D = rng.integers(0, spread, size=(m, m))
+    D = np.triu(D, 1)
+    D = (D + D.T).astype(np.int16)
+    fit = rng.integers(0, 30, size=m).astype(np.int64)
+    return fit, D
+
+
+@pytest.mark.parametrize("p,n,seed,spread", [(64, 100, 0, 25), (300, 500, 1, 120), (33, 50, 2, 6), (1, 10, 3, 5),
+                                             (8192, 1000, 4, 300)])
+def test_pool_update_matches_oracle(ctx, p, n, seed, spread):
+    fit, D = _random_pool_case(p, n, seed, spread)
+    sel = torch.zeros(p, dtype=torch.int32, device="cuda")
+    dlmcol.dlm_pool_update(ctx, p, n, _cuda(fit), _cuda(D), sel)
+    ctx.sync()
+    assert np.array_equal(sel.cpu().numpy(), oracle.pool_update(p, n, fit, D))
+
+
+@pytest.mark.parametrize("p,K,seed", [(300, 16, 0), (40, 39, 1), (8192, 32, 2), (2, 1, 3)])
+def test_knn_matches_oracle(ctx, p, K, seed):
+    rng = np.random.default_rng(seed)
+    D = rng.integers(0, 60, size=(p, p))
+    D = (np.triu(D, 1) + np.triu(D, 1).T).astype(np.int16)
+    nbr = torch.zeros((p, K), dtype=torch.int32, device="cuda")
+    dlmcol.dlm_knn(ctx, p, _cuda(D), K, nbr)
+    ctx.sync()
+    got = nbr.cpu().numpy()
+    if p <= 300:
+        assert np.array_equal(got, oracle.knn(D, K))
+    else:  # the full-size matrix: sampled rows against a library sort
+        for i in [0, 1, p // 2, p - 1]:
+            js = np.array([j for j in range(p) if j != i])
+            ref = js[np.argsort(D[i, js], kind="stable")][:K]
+            assert np.array_equal(got[i], ref)
+
+
+def test_knn_rejects_bad_k(ctx):
+    D = torch.zeros((4, 4), dtype=torch.int16, device="cuda")
+    nbr = torch.zeros((4, 4), dtype=torch.int32, device="cuda")
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_knn(ctx, 4, D, 4, nbr)
