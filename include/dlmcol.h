@@ -174,6 +174,73 @@ dlm_status dlm_pool_update(dlm_ctx* ctx, int32_t p, int32_t n, const int64_t* fi
 dlm_status dlm_knn(dlm_ctx* ctx, int32_t p, const int16_t* D, int32_t K, int32_t* nbr);
 
 /* ---------------------------------------------------------------------------------------------
+ * Offspring scorer f_theta (section "Deep neural network training"): a colour-permutation
+ * invariant deep-set network. Layer 0 sums the 64-d embedding rows E[v] over each colour class
+ * (plus bias, LeakyReLU 0.2); three layers H' = LeakyReLU_0.2(beta + H Lambda + rho(H) Gamma) of
+ * width 256, rho the mean over the k classes; output = mean over classes of the linear head.
+ * Matrix products run on the tcgen05 tensor cores in BF16 with FP32 accumulation; parameters
+ * are kept in FP32. Flat parameter order: E[n][64], b0[64], for l = 1..3 (din = 64, 256, 256):
+ * Lambda_l[din][256], Gamma_l[din][256], beta_l[256]; then w_head[256], b_head[1].
+ * Limits: k <= 64, n <= 2048.
+ * ------------------------------------------------------------------------------------------- */
+dlm_status dlm_scorer_create(dlm_ctx* ctx, int32_t n, int32_t k, uint64_t seed, dlm_scorer** out);
+void dlm_scorer_destroy(dlm_scorer* s);
+int64_t dlm_scorer_nparams(const dlm_scorer* s);
+/* params: device [nparams] float32 (copy out / copy in; set also resets the Adam state). */
+dlm_status dlm_scorer_get_params(dlm_ctx* ctx, dlm_scorer* s, float* params);
+dlm_status dlm_scorer_set_params(dlm_ctx* ctx, dlm_scorer* s, const float* params);
+/* Scores c colourings: col device [c][n] int16, out device [c] float32. */
+dlm_status dlm_score_offspring(dlm_ctx* ctx, dlm_scorer* s, const int16_t* col, int32_t c, float* out);
+/* Mean squared error of B samples (col device [B][n], y device [B]) and its gradient
+ * (grad device [nparams] float32, out device [B] float32 predictions, loss device [1]). */
+dlm_status dlm_scorer_loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* col, const float* y, int32_t B,
+                                float* grad, float* out, float* loss);
+/* Online training: N epochs of Adam (lr, betas 0.9/0.999, eps 1e-8) over p samples (cols device
+ * [p][n], targets fvals device [p] int64 standardised by their mean and std) in batches of b;
+ * epoch e visits the samples sorted by the keys Philox(a = i, b = e, c = generation,
+ * tag = BATCH).r0 (ties by i). */
+dlm_status dlm_scorer_train(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const int64_t* fvals, int32_t p,
+                            int32_t epochs, int32_t b, float lr, uint64_t seed, uint32_t generation);
+
+/* ---------------------------------------------------------------------------------------------
+ * Memetic loop (Algorithm 1). dlm_memetic_step runs one generation: TabuCol on every offspring,
+ * best-so-far update, scorer training (use_scorer), distances between P and P' and within P',
+ * pool update, K nearest neighbours, and offspring: with use_scorer the best-scored of the K GPX
+ * children of i (parent 2 = its j-th neighbour, child id i*K + j); without, one GPX child with a
+ * neighbour drawn uniformly (Philox(a = i, b = generation, c = 0, tag = SELECT)), the ablation of
+ * section "Benefits of the neural network based crossover selection".
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+  int32_t k, p, K;
+  int64_t iters;          /* tabu iterations per generation (paper: 128 |V|) */
+  dlm_tenure tenure;      /* paper: {9, 6, 10} */
+  int32_t use_scorer;     /* 1 = learned selection, 0 = random GPX */
+  int32_t epochs, batch;  /* paper: 5, 100 */
+  float lr;               /* paper: 1e-3 */
+  uint64_t seed;
+} dlm_memetic_params;
+
+dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const dlm_memetic_params* prm, dlm_memetic** out);
+void dlm_memetic_destroy(dlm_memetic* mm);
+/* One generation; *best_f_host (host, may be NULL) receives f(S*) after it (this waits). */
+dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* best_f_host);
+/* Copies a state array to device memory dst: 0 = P [p][n] int16, 1 = f(P) [p] int64,
+ * 2 = D(P,P) [p][p] int16, 3 = offspring S^O [p][n] int16, 4 = best colouring [n] int16,
+ * 5 = f(S'_i) of the last generation [p] int64, 6 = chosen candidate j [p] int32,
+ * 7 = candidate scores of the last generation [p][K] float32 (use_scorer only),
+ * 8 = scorer parameters [nparams] float32. */
+dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, void* dst);
+/* Overwrites the population state (which = 0..3 as above) from device memory src. */
+dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const void* src);
+
+/* ---------------------------------------------------------------------------------------------
+ * Building block of the scorer, exported for testing: C = A . B^T on the tcgen05 tensor cores.
+ * A: device [M][K] bf16 row-major, B: device [N][K] bf16 row-major, C: device [M][N] float32.
+ * K must be a multiple of 64 and N a multiple of 64; FP32 accumulation.
+ * ------------------------------------------------------------------------------------------- */
+dlm_status dlm_gemm_bf16(dlm_ctx* ctx, const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K);
+
+/* ---------------------------------------------------------------------------------------------
  * Measurement utility (no counterpart in the paper): streams conflict-free 16-byte shared-memory
  * loads on every SM and returns the achieved bandwidth in GB/s (host double). It is the
  * denominator of the tabu kernel's roofline, whose state is held in shared memory.

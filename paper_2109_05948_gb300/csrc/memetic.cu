@@ -1,0 +1,291 @@
+// One generation of the deep-learning-guided memetic framework (Algorithm 1), stream-ordered on
+// the GPU: TabuCol of every offspring -> best-so-far -> scorer training (learned selection) ->
+// distances P x P' and P' x P' -> pool update -> gather of the new population and its distance
+// matrix -> K nearest neighbours -> GPX offspring (best-scored of K, or one random neighbour).
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+
+struct dlm_memetic {
+  const dlm_graph* g = nullptr;
+  dlm_memetic_params prm{};
+  int n = 0;
+  uint32_t gen = 0;
+  // population state
+  int16_t *P = nullptr, *Pn = nullptr, *SO = nullptr, *Sp = nullptr, *best_col = nullptr, *kids = nullptr;
+  int64_t *fP = nullptr, *fPn = nullptr, *fSp = nullptr, *fall = nullptr, *best_f = nullptr, *moves = nullptr;
+  int16_t *DP = nullptr, *Dall = nullptr;
+  int32_t *sel = nullptr, *nbr = nullptr, *pairs = nullptr, *pick = nullptr;
+  uint32_t* cid = nullptr;
+  float* scores = nullptr;
+  int64_t* h_best = nullptr;  // pinned
+  dlm_scorer* scorer = nullptr;
+};
+
+namespace dlm {
+
+__global__ void k_best_of(int p, int n, const int64_t* fSp, const int16_t* Sp, int64_t* best_f, int16_t* best_col) {
+  __shared__ unsigned long long s[32];
+  __shared__ int win;
+  unsigned long long key = ~0ull;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const unsigned long long kk = ((unsigned long long)fSp[i] << 20) | (unsigned)i;
+    key = kk < key ? kk : key;
+  }
+  for (int d = 16; d >= 1; d >>= 1) {
+    const unsigned long long o = __shfl_down_sync(0xFFFFFFFFu, key, d);
+    key = o < key ? o : key;
+  }
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = key;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = ~0ull;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = s[w] < b ? s[w] : b;
+    const int ib = (int)(b & 0xFFFFF);
+    win = -1;
+    if (fSp[ib] < *best_f) { *best_f = fSp[ib]; win = ib; }
+  }
+  __syncthreads();
+  if (win >= 0)
+    for (int v = threadIdx.x; v < n; v += blockDim.x) best_col[v] = Sp[(size_t)win * n + v];
+}
+
+// Dall (2p x 2p): top-left <- DP, mirror of the cross block, mirror + zero diagonal of the P'P' block
+__global__ void k_dall_assemble(int p, const int16_t* DP, int16_t* Dall) {
+  const int m = 2 * p;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * m) return;
+  const int r = (int)(t / m), c = (int)(t % m);
+  int16_t v;
+  if (r < p && c < p) v = DP[(size_t)r * p + c];
+  else if (r >= p && c < p) v = Dall[(size_t)c * m + r];        // cross block computed as rows < p
+  else if (r >= p && c >= p) v = r == c ? 0 : (c > r ? Dall[(size_t)r * m + c] : Dall[(size_t)c * m + r]);
+  else return;  // r < p, c >= p: computed in place
+  Dall[(size_t)r * m + c] = v;
+}
+
+__global__ void k_fit_all(int p, const int64_t* fP, const int64_t* fSp, int64_t* fall) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < p) { fall[t] = fP[t]; fall[p + t] = fSp[t]; }
+}
+
+__global__ void k_gather_pop(int p, int n, const int32_t* sel, const int16_t* P, const int16_t* Sp, const int64_t* fall,
+                             int16_t* Pn, int64_t* fPn) {
+  const int s = blockIdx.x;
+  const int x = sel[s];
+  const int16_t* src = x < p ? P + (size_t)x * n : Sp + (size_t)(x - p) * n;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) Pn[(size_t)s * n + v] = src[v];
+  if (threadIdx.x == 0) fPn[s] = fall[x];
+}
+
+__global__ void k_gather_dist(int p, const int32_t* sel, const int16_t* Dall, int16_t* DP) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p) return;
+  DP[(size_t)s * p + t] = Dall[(size_t)sel[s] * (2 * p) + sel[t]];
+}
+
+// random GPX: one neighbour per individual, drawn from the SELECT stream
+__global__ void k_pairs_random(int p, int K, const int32_t* nbr, uint64_t seed, uint32_t gen, int32_t* pairs,
+                               uint32_t* cid, int32_t* pick) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p) return;
+  const U4 r = rng(seed, (uint32_t)i, gen, 0u, kTagSelect);
+  const int j = (int)below(r.x, (uint32_t)K);
+  pairs[2 * i] = i;
+  pairs[2 * i + 1] = nbr[(size_t)i * K + j];
+  cid[i] = (uint32_t)(i * K + j);
+  pick[i] = j;
+}
+
+// learned selection: all K neighbours
+__global__ void k_pairs_all(int p, int K, const int32_t* nbr, int32_t* pairs, uint32_t* cid) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p * K) return;
+  pairs[2 * t] = t / K;
+  pairs[2 * t + 1] = nbr[t];
+  cid[t] = (uint32_t)t;
+}
+
+// argmin over the K scores of individual i, visiting j in order: the first candidate is taken and
+// only a strictly smaller score replaces it (ties: lowest j); copies that child into S^O_i
+__global__ void k_select_best(int p, int K, int n, const float* scores, const int16_t* kids, int16_t* SO, int32_t* pick) {
+  const int i = blockIdx.x;
+  __shared__ int best;
+  if (threadIdx.x == 0) {
+    int bj = 0;
+    float bv = scores[(size_t)i * K];
+    for (int j = 1; j < K; ++j) {
+      const float sc = scores[(size_t)i * K + j];
+      if (sc < bv) { bv = sc; bj = j; }
+    }
+    best = bj;
+    pick[i] = bj;
+  }
+  __syncthreads();
+  const int16_t* src = kids + ((size_t)i * K + best) * n;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) SO[(size_t)i * n + v] = src[v];
+}
+
+template <typename T>
+static dlm_status alloc(dlm_ctx* ctx, T** p, size_t count) {
+  if (cudaMalloc((void**)p, std::max<size_t>(1, count) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DLM_ENOMEM, "memetic: device allocation failed");
+  }
+  return DLM_OK;
+}
+
+}  // namespace dlm
+
+using namespace dlm;
+
+extern "C" void dlm_memetic_destroy(dlm_memetic* mm) {
+  if (!mm) return;
+  cudaFree(mm->P); cudaFree(mm->Pn); cudaFree(mm->SO); cudaFree(mm->Sp); cudaFree(mm->best_col); cudaFree(mm->kids);
+  cudaFree(mm->fP); cudaFree(mm->fPn); cudaFree(mm->fSp); cudaFree(mm->fall); cudaFree(mm->best_f); cudaFree(mm->moves);
+  cudaFree(mm->DP); cudaFree(mm->Dall); cudaFree(mm->sel); cudaFree(mm->nbr); cudaFree(mm->pairs); cudaFree(mm->pick);
+  cudaFree(mm->cid); cudaFree(mm->scores);
+  if (mm->h_best) cudaFreeHost(mm->h_best);
+  if (mm->scorer) dlm_scorer_destroy(mm->scorer);
+  delete mm;
+}
+
+extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const dlm_memetic_params* prm,
+                                         dlm_memetic** out) {
+  if (!ctx || !g || !prm || !out) return fail(ctx, DLM_EINVAL, "memetic_create: null argument");
+  *out = nullptr;
+  const int p = prm->p, K = prm->K, n = g->n, k = prm->k;
+  if (p < 2 || K < 1 || K > p - 1 || K > 64 || k < 2 || k > 128 || prm->iters < 0)
+    return fail(ctx, DLM_EINVAL, "memetic_create: need p >= 2, 1 <= K <= min(64, p-1), 2 <= k <= 128");
+  if (p > 8192) return fail(ctx, DLM_EUNSUPPORTED, "memetic_create: p must be <= 8192");
+  if (prm->use_scorer && (prm->epochs < 0 || prm->batch < 1)) return fail(ctx, DLM_EINVAL, "memetic_create: bad training parameters");
+  dlm_memetic* mm = new dlm_memetic();
+  mm->g = g;
+  mm->prm = *prm;
+  mm->n = n;
+  const size_t pn = (size_t)p * n;
+  const int nk = prm->use_scorer ? K : 1;
+  dlm_status st = DLM_OK;
+  auto A = [&](auto** ptr, size_t cnt) { if (st == DLM_OK) st = alloc(ctx, ptr, cnt); };
+  A(&mm->P, pn); A(&mm->Pn, pn); A(&mm->SO, pn); A(&mm->Sp, pn); A(&mm->best_col, (size_t)n);
+  A(&mm->kids, pn * nk);
+  A(&mm->fP, (size_t)p); A(&mm->fPn, (size_t)p); A(&mm->fSp, (size_t)p); A(&mm->fall, (size_t)2 * p);
+  A(&mm->best_f, 1); A(&mm->moves, (size_t)p);
+  A(&mm->DP, (size_t)p * p); A(&mm->Dall, (size_t)4 * p * p);
+  A(&mm->sel, (size_t)p); A(&mm->nbr, (size_t)p * K); A(&mm->pairs, (size_t)2 * p * nk); A(&mm->pick, (size_t)p);
+  A(&mm->cid, (size_t)p * nk); A(&mm->scores, (size_t)p * K);
+  if (st == DLM_OK && cudaMallocHost(&mm->h_best, sizeof(int64_t)) != cudaSuccess) st = fail(ctx, DLM_ENOMEM, "pinned");
+  if (st == DLM_OK && prm->use_scorer) st = dlm_scorer_create(ctx, n, k, prm->seed, &mm->scorer);
+  if (st != DLM_OK) { dlm_memetic_destroy(mm); return st; }
+  // initial population: random colourings, their conflicts and their distance matrix
+  const int64_t big = INT64_MAX;
+  st = dlm_init_colors(ctx, n, k, p, prm->seed, 0u, mm->P);
+  if (st == DLM_OK) st = dlm_gamma(ctx, g, k, p, mm->P, nullptr, mm->fP);
+  if (st == DLM_OK) st = dlm_distance_batch(ctx, n, k, mm->P, p, mm->P, p, mm->DP, p, 0);
+  if (st == DLM_OK) st = cuda_check(ctx, cudaMemcpyAsync(mm->SO, mm->P, pn * 2, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+  if (st == DLM_OK) st = cuda_check(ctx, cudaMemcpyAsync(mm->best_f, &big, 8, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  if (st == DLM_OK) st = cuda_check(ctx, cudaMemsetAsync(mm->Dall, 0, (size_t)4 * p * p * 2, ctx->stream), "memset");
+  if (st == DLM_OK) st = cuda_check(ctx, cudaMemsetAsync(mm->best_col, 0, (size_t)n * 2, ctx->stream), "memset");
+  if (st == DLM_OK) st = dlm_sync(ctx);
+  if (st != DLM_OK) { dlm_memetic_destroy(mm); return st; }
+  *out = mm;
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* best_f_host) {
+  if (!ctx || !mm) return fail(ctx, DLM_EINVAL, "memetic_step: null argument");
+  const dlm_memetic_params& q = mm->prm;
+  const int p = q.p, K = q.K, n = mm->n, k = q.k, m = 2 * p;
+  const size_t pn = (size_t)p * n;
+  cudaStream_t s = ctx->stream;
+  // 1. local search of every offspring: S'_i <- TabuCol(S^O_i)
+  DLM_CUDA(ctx, cudaMemcpyAsync(mm->Sp, mm->SO, pn * 2, cudaMemcpyDeviceToDevice, s));
+  DLM_TRY(dlm_tabucol_batch(ctx, mm->g, k, p, mm->Sp, mm->fSp, mm->moves, q.iters, q.tenure, q.seed, mm->gen, 0u));
+  // 2. best so far
+  k_best_of<<<1, 1024, 0, s>>>(p, n, mm->fSp, mm->Sp, mm->best_f, mm->best_col);
+  DLM_TRY(launch_check(ctx, "k_best_of"));
+  // 3. training on {(S^O_i, f(S'_i))}
+  if (q.use_scorer)
+    DLM_TRY(dlm_scorer_train(ctx, mm->scorer, mm->SO, mm->fSp, p, q.epochs, q.batch, q.lr, q.seed, mm->gen));
+  // 4. distances: P x P' (rows < p, columns >= p) and P' x P' (upper triangle), then assemble
+  DLM_TRY(dlm_distance_batch(ctx, n, k, mm->P, p, mm->Sp, p, mm->Dall + p, m, 0));
+  DLM_TRY(dlm_distance_batch(ctx, n, k, mm->Sp, p, mm->Sp, p, mm->Dall + (size_t)p * m + p, m, 1));
+  {
+    const int64_t tot = (int64_t)m * m;
+    k_dall_assemble<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p, mm->DP, mm->Dall);
+    DLM_TRY(launch_check(ctx, "k_dall_assemble"));
+  }
+  // 5. pool update over P u P'
+  k_fit_all<<<(p + 255) / 256, 256, 0, s>>>(p, mm->fP, mm->fSp, mm->fall);
+  DLM_TRY(launch_check(ctx, "k_fit_all"));
+  DLM_TRY(dlm_pool_update(ctx, p, n, mm->fall, mm->Dall, mm->sel));
+  k_gather_pop<<<p, 128, 0, s>>>(p, n, mm->sel, mm->P, mm->Sp, mm->fall, mm->Pn, mm->fPn);
+  DLM_TRY(launch_check(ctx, "k_gather_pop"));
+  k_gather_dist<<<dim3((p + 255) / 256, p), 256, 0, s>>>(p, mm->sel, mm->Dall, mm->DP);
+  DLM_TRY(launch_check(ctx, "k_gather_dist"));
+  std::swap(mm->P, mm->Pn);
+  std::swap(mm->fP, mm->fPn);
+  // 6. parent matching
+  DLM_TRY(dlm_knn(ctx, p, mm->DP, K, mm->nbr));
+  // 7. offspring
+  if (q.use_scorer) {
+    k_pairs_all<<<(p * K + 255) / 256, 256, 0, s>>>(p, K, mm->nbr, mm->pairs, mm->cid);
+    DLM_TRY(launch_check(ctx, "k_pairs_all"));
+    DLM_TRY(dlm_gpx_batch(ctx, n, k, mm->P, p, mm->pairs, mm->cid, p * K, mm->kids, q.seed, mm->gen));
+    DLM_TRY(dlm_score_offspring(ctx, mm->scorer, mm->kids, p * K, mm->scores));
+    k_select_best<<<p, 128, 0, s>>>(p, K, n, mm->scores, mm->kids, mm->SO, mm->pick);
+    DLM_TRY(launch_check(ctx, "k_select_best"));
+  } else {
+    k_pairs_random<<<(p + 255) / 256, 256, 0, s>>>(p, K, mm->nbr, q.seed, mm->gen, mm->pairs, mm->cid, mm->pick);
+    DLM_TRY(launch_check(ctx, "k_pairs_random"));
+    DLM_TRY(dlm_gpx_batch(ctx, n, k, mm->P, p, mm->pairs, mm->cid, p, mm->SO, q.seed, mm->gen));
+  }
+  mm->gen++;
+  if (best_f_host) {
+    DLM_CUDA(ctx, cudaMemcpyAsync(mm->h_best, mm->best_f, 8, cudaMemcpyDeviceToHost, s));
+    DLM_TRY(dlm_sync(ctx));
+    *best_f_host = *mm->h_best;
+  }
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, void* dst) {
+  if (!ctx || !mm || !dst) return fail(ctx, DLM_EINVAL, "memetic_get: null argument");
+  const int p = mm->prm.p, n = mm->n, K = mm->prm.K;
+  const void* src = nullptr;
+  size_t bytes = 0;
+  switch (which) {
+    case 0: src = mm->P; bytes = (size_t)p * n * 2; break;
+    case 1: src = mm->fP; bytes = (size_t)p * 8; break;
+    case 2: src = mm->DP; bytes = (size_t)p * p * 2; break;
+    case 3: src = mm->SO; bytes = (size_t)p * n * 2; break;
+    case 4: src = mm->best_col; bytes = (size_t)n * 2; break;
+    case 5: src = mm->fSp; bytes = (size_t)p * 8; break;
+    case 6: src = mm->pick; bytes = (size_t)p * 4; break;
+    case 7: if (!mm->prm.use_scorer) return fail(ctx, DLM_EINVAL, "memetic_get: no scores without the scorer");
+            src = mm->scores; bytes = (size_t)p * K * 4; break;
+    case 8: if (!mm->scorer) return fail(ctx, DLM_EINVAL, "memetic_get: no scorer");
+            return dlm_scorer_get_params(ctx, mm->scorer, (float*)dst);
+    default: return fail(ctx, DLM_EINVAL, "memetic_get: unknown array");
+  }
+  DLM_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const void* src) {
+  if (!ctx || !mm || !src) return fail(ctx, DLM_EINVAL, "memetic_set: null argument");
+  const int p = mm->prm.p, n = mm->n;
+  void* dst = nullptr;
+  size_t bytes = 0;
+  switch (which) {
+    case 0: dst = mm->P; bytes = (size_t)p * n * 2; break;
+    case 1: dst = mm->fP; bytes = (size_t)p * 8; break;
+    case 2: dst = mm->DP; bytes = (size_t)p * p * 2; break;
+    case 3: dst = mm->SO; bytes = (size_t)p * n * 2; break;
+    default: return fail(ctx, DLM_EINVAL, "memetic_set: unknown array");
+  }
+  DLM_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return DLM_OK;
+}

@@ -1,0 +1,899 @@
+// Offspring scorer f_theta (section "Deep neural network training"): colour-permutation
+// invariant deep-set network, trained online with Adam, scoring the K GPX candidates of every
+// individual (Eq. select_cross).
+//
+// Network (the sizes of the benchmarked workload): layer 0 sums the 64-d embedding rows E[v]
+// over each colour class (V_i Lambda_0; the rho(S) Gamma_0 term is the same for every partition
+// and is part of beta_0), LeakyReLU_0.2; layers 1..3: H' = LeakyReLU_0.2(beta + H Lambda +
+// rho(H) Gamma) with width 256 and rho the mean over the k classes; output = mean over classes of
+// the linear head. Each candidate occupies R = 64 rows (rows k..63 are zero), so one 128-row
+// tensor-core tile holds two whole candidates.
+//
+// Where the work runs:
+//   tcgen05 BF16 GEMMs (FP32 accumulate in TMEM): H Lambda for layers 1..3 (fused epilogue:
+//     + per-candidate (rho Gamma + beta), LeakyReLU, row mask, bf16 store, head dot product),
+//     the per-candidate rho(H) Gamma terms, the backward dH = dZ Lambda^T (fused: + per-candidate
+//     term, LeakyReLU derivative, row mask) and the weight gradients dLambda = H^T dZ (split-K).
+//   CUDA cores: the class pooling of layer 0 (a gather, not a contraction), per-candidate means
+//     and column sums, the small per-candidate Gamma products of the backward pass (batch of
+//     b = 100 candidates), the embedding gradient (scatter by colour), Adam.
+// All reductions run in a fixed order: results are deterministic run to run.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "tcgemm.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace dlm {
+constexpr int kD0 = 64, kD = 256, kNL = 3, kR = 64;
+}
+
+struct dlm_scorer {
+  int n = 0, k = 0;
+  int64_t np = 0;
+  int64_t t = 0;  // Adam step counter
+  size_t oE = 0, ob0 = 0, olam[4] = {}, ogam[4] = {}, ob[4] = {}, owh = 0, obh = 0;
+  float *theta = nullptr, *am = nullptr, *av = nullptr, *grad = nullptr;
+  bf16* E16 = nullptr;
+  bf16 *LamT[4] = {}, *Lam[4] = {}, *GamT[4] = {};
+  // forward work buffers for up to `cap` candidates
+  int cap = 0;
+  bf16* H[4] = {};
+  bf16* Mb[4] = {};
+  float* Mf[4] = {};
+  float* G[4] = {};
+  float* rowdot = nullptr;
+  // backward buffers for up to `capb` candidates
+  int capb = 0;
+  bf16* Hb[4] = {};
+  bf16* HT[4] = {};
+  bf16* Mbb[4] = {};
+  float* Mfb[4] = {};
+  float* Gbf[4] = {};
+  bf16* dZ[4] = {};
+  bf16* dZT[4] = {};
+  float* S[4] = {};
+  float* Gb = nullptr;
+  float* part = nullptr;  // split-K partial sums
+  float* rowdotb = nullptr;
+  float* outb = nullptr;
+  float* dout = nullptr;
+  float* lossd = nullptr;
+  // training
+  int16_t* bcols = nullptr;   // gathered batch colourings
+  float* y = nullptr;         // standardised targets
+  float* by = nullptr;
+  int32_t* perm = nullptr;
+  int capp = 0;
+};
+
+namespace dlm {
+
+static int din_of(int l) { return l == 1 ? kD0 : kD; }
+
+// ------------------------------------------------------------------------------------------------
+// parameter conversion: fp32 master -> bf16 operands in GEMM layouts
+// ------------------------------------------------------------------------------------------------
+struct ConvArgs {
+  const float* theta;
+  int n;
+  size_t oE, olam[4], ogam[4];
+  bf16* E16;
+  bf16 *LamT[4], *Lam[4], *GamT[4];
+};
+
+__global__ void k_convert(ConvArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nE = (int64_t)a.n * kD0;
+  if (t < nE) { a.E16[t] = __float2bfloat16_rn(a.theta[a.oE + t]); return; }
+  int64_t r = t - nE;
+  for (int l = 1; l <= kNL; ++l) {
+    const int din = l == 1 ? kD0 : kD;
+    const int64_t sz = (int64_t)din * kD;
+    if (r < sz) {
+      const int f = (int)(r / kD), o = (int)(r % kD);
+      const float lam = a.theta[a.olam[l] + r], gam = a.theta[a.ogam[l] + r];
+      a.Lam[l][r] = __float2bfloat16_rn(lam);
+      a.LamT[l][(size_t)o * din + f] = __float2bfloat16_rn(lam);
+      a.GamT[l][(size_t)o * din + f] = __float2bfloat16_rn(gam);
+      return;
+    }
+    r -= sz;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// layer 0: class pooling. One CTA per candidate (grid-stride): a stable counting sort puts the
+// vertices of each class in ascending order, then warp w sums the embedding rows of classes
+// w, w+8, ... with lane = feature pair (fixed summation order).
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols, int c, const bf16* E16, const float* b0,
+                                              bf16* H0, float* Mf0, bf16* Mb0, int32_t* status) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  uint8_t* col = sm;                                        // [n]
+  uint16_t* mem = (uint16_t*)(sm + ((n + 15) & ~15));       // [n]
+  int* cnt = (int*)(mem + ((n + 7) & ~7));                  // [64]
+  int* off = cnt + 64;                                      // [65]
+  int* cur = off + 65;                                      // [64]
+  float* part = (float*)(cur + 64);                         // [8][64]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int cand = blockIdx.x; cand < c; cand += gridDim.x) {
+    const int16_t* cc = cols + (size_t)cand * n;
+    if (tid < 64) cnt[tid] = 0;
+    __syncthreads();
+    for (int v = tid; v < n; v += 256) {
+      int q = cc[v];
+      if (q < 0 || q >= k) { raise_status(status, DLM_EINVAL); q = 0; }
+      col[v] = (uint8_t)q;
+      atomicAdd(cnt + q, 1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int x0 = cnt[lane], x1 = cnt[lane + 32];
+      int i0 = x0, i1 = x1;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int a = __shfl_up_sync(0xFFFFFFFFu, i0, d), b = __shfl_up_sync(0xFFFFFFFFu, i1, d);
+        if (lane >= d) { i0 += a; i1 += b; }
+      }
+      const int tot0 = __shfl_sync(0xFFFFFFFFu, i0, 31);
+      off[lane] = i0 - x0;
+      off[lane + 32] = tot0 + i1 - x1;
+      cur[lane] = i0 - x0;
+      cur[lane + 32] = tot0 + i1 - x1;
+      if (lane == 31) off[64] = tot0 + i1;
+      // stable scatter: chunks of 32 vertices in order, rank among equal colours by lane order
+      for (int v0 = 0; v0 < n; v0 += 32) {
+        const int v = v0 + lane;
+        const int q = v < n ? col[v] : 64 + lane;
+        const unsigned same = __match_any_sync(0xFFFFFFFFu, q);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        int base = 0;
+        if (v < n) base = cur[q];
+        __syncwarp();
+        if (v < n) {
+          mem[base + rank] = (uint16_t)v;
+          if (rank == __popc(same) - 1) cur[q] = base + rank + 1;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    float2 msum = make_float2(0.f, 0.f);
+    const float2 bb = make_float2(b0[2 * lane], b0[2 * lane + 1]);
+    for (int q = warp; q < kR; q += 8) {
+      float2 acc = make_float2(0.f, 0.f);
+      if (q < k) {
+        for (int j = off[q]; j < off[q + 1]; ++j) {
+          const int v = mem[j];
+          const __nv_bfloat162 e = *reinterpret_cast<const __nv_bfloat162*>(E16 + (size_t)v * kD0 + 2 * lane);
+          const float2 ef = __bfloat1622float2(e);
+          acc.x += ef.x;
+          acc.y += ef.y;
+        }
+        float zx = acc.x + bb.x, zy = acc.y + bb.y;
+        acc.x = zx > 0.f ? zx : 0.2f * zx;
+        acc.y = zy > 0.f ? zy : 0.2f * zy;
+        msum.x += acc.x;
+        msum.y += acc.y;
+      }
+      *reinterpret_cast<__nv_bfloat162*>(H0 + ((size_t)cand * kR + q) * kD0 + 2 * lane) = __floats2bfloat162_rn(acc.x, acc.y);
+    }
+    part[warp * 64 + 2 * lane] = msum.x;
+    part[warp * 64 + 2 * lane + 1] = msum.y;
+    __syncthreads();
+    if (tid < 64) {
+      float s = 0.f;
+      for (int w = 0; w < 8; ++w) s += part[w * 64 + tid];
+      s /= (float)k;
+      Mf0[(size_t)cand * kD0 + tid] = s;
+      Mb0[(size_t)cand * kD0 + tid] = __float2bfloat16_rn(s);
+    }
+    __syncthreads();
+  }
+}
+
+// per-candidate mean (or sum) over the k valid rows of a bf16 [c*R][w] matrix; block = w threads
+__global__ void k_segment_reduce(const bf16* X, int w, int k, float scale, float* outf, bf16* outb) {
+  const int cand = blockIdx.x, col = threadIdx.x;
+  const bf16* x = X + (size_t)cand * kR * w + col;
+  float s = 0.f;
+  for (int r = 0; r < k; ++r) s += __bfloat162float(x[(size_t)r * w]);
+  s *= scale;
+  outf[(size_t)cand * w + col] = s;
+  if (outb) outb[(size_t)cand * w + col] = __float2bfloat16_rn(s);
+}
+
+__global__ void k_head_out(int c, int k, const float* rowdot, const float* theta, size_t obh, float* out) {
+  const int cand = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cand >= c) return;
+  float s = 0.f;
+  for (int r = 0; r < k; ++r) s += rowdot[(size_t)cand * kR + r];
+  out[cand] = theta[obh] + s / (float)k;
+}
+
+// 32x32 tiled transpose of a bf16 [rows][cols] matrix into [cols][rows]
+__global__ void k_transpose(const bf16* X, int rows, int cols, bf16* Y) {
+  __shared__ bf16 tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = by + i, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = X[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = bx + i, r = by + threadIdx.x;
+    if (r < rows && c < cols) Y[(size_t)c * rows + r] = tile[threadIdx.x][i];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// GEMM epilogues
+// ------------------------------------------------------------------------------------------------
+struct EpiPlain {  // out[row][col] = alpha * acc + bias[col]
+  float* out;
+  int ld, M;
+  float alpha;
+  const float* bias;
+  __device__ void operator()(int row, int col0, const float (&v)[16]) const {
+    if (row >= M) return;
+    float* o = out + (size_t)row * ld + col0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) o[i] = alpha * v[i] + (bias ? bias[col0 + i] : 0.f);
+  }
+  __device__ void finish(int) const {}
+};
+
+struct EpiPartial {  // split-K slice z: part[z][row][col] = acc
+  float* part;
+  int ld, M;
+  size_t zstride;
+  __device__ void operator()(int row, int col0, const float (&v)[16]) const {
+    if (row >= M) return;
+    float* o = part + blockIdx.z * zstride + (size_t)row * ld + col0;
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  }
+  __device__ void finish(int) const {}
+};
+
+struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optional head dot
+  bf16* H;  // may be null (scoring the last layer)
+  int M, kv;
+  const float* G;
+  const float* wh;
+  float* rowdot;
+  float dot;
+  __device__ void operator()(int row, int col0, const float (&v)[16]) {
+    if (row >= M) return;
+    const int cand = row / kR;
+    const bool valid = (row % kR) < kv;
+    const float* g = G + (size_t)cand * kD + col0;
+    float h[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float z = v[i] + g[i];
+      h[i] = valid ? (z > 0.f ? z : 0.2f * z) : 0.f;
+    }
+    if (wh) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) dot += h[i] * wh[col0 + i];
+    }
+    if (H) {
+      uint4 pk[2];
+      uint32_t* p = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(h[2 * i], h[2 * i + 1]);
+        p[i] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(H + (size_t)row * kD + col0);
+      dst[0] = pk[0];
+      dst[1] = pk[1];
+    }
+  }
+  __device__ void finish(int row) const {
+    if (rowdot && row < M) rowdot[row] = dot;
+  }
+};
+
+struct EpiBwd {  // dZprev[row][col] = mask((acc + Gb[cand][col]) * LeakyReLU'(Hprev[row][col]))
+  bf16* dZ;
+  int ld, M, kv;
+  const float* Gb;
+  const bf16* Hp;
+  __device__ void operator()(int row, int col0, const float (&v)[16]) const {
+    if (row >= M) return;
+    const int cand = row / kR;
+    const bool valid = (row % kR) < kv;
+    const float* g = Gb + (size_t)cand * ld + col0;
+    const uint4* hsrc = reinterpret_cast<const uint4*>(Hp + (size_t)row * ld + col0);
+    uint4 hv[2] = {hsrc[0], hsrc[1]};
+    const bf16* hb = reinterpret_cast<const bf16*>(hv);
+    uint4 pk[2];
+    uint32_t* p = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float d0 = v[2 * i] + g[2 * i], d1 = v[2 * i + 1] + g[2 * i + 1];
+      d0 *= __bfloat162float(hb[2 * i]) > 0.f ? 1.f : 0.2f;
+      d1 *= __bfloat162float(hb[2 * i + 1]) > 0.f ? 1.f : 0.2f;
+      if (!valid) { d0 = 0.f; d1 = 0.f; }
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(d0, d1);
+      p[i] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(dZ + (size_t)row * ld + col0);
+    dst[0] = pk[0];
+    dst[1] = pk[1];
+  }
+  __device__ void finish(int) const {}
+};
+
+// ------------------------------------------------------------------------------------------------
+// backward helpers (batch of B candidates)
+// ------------------------------------------------------------------------------------------------
+__global__ void k_loss(int B, const float* out, const float* y, float* dout, float* loss) {
+  __shared__ float s[256];
+  float l = 0.f;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    const float e = out[i] - y[i];
+    dout[i] = 2.f * e / (float)B;
+    l += e * e;
+  }
+  s[threadIdx.x] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += s[i];
+    *loss = t / (float)B;
+  }
+}
+
+// dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows; block = one candidate row chunk
+__global__ void k_head_back(int B, int k, const float* dout, const float* theta, size_t owh, const bf16* H3, bf16* dZ3) {
+  const int row = blockIdx.x, o = threadIdx.x;
+  const int cand = row / kR;
+  const bool valid = (row % kR) < k;
+  float d = 0.f;
+  if (valid) {
+    d = dout[cand] / (float)k * theta[owh + o];
+    d *= __bfloat162float(H3[(size_t)row * kD + o]) > 0.f ? 1.f : 0.2f;
+  }
+  dZ3[(size_t)row * kD + o] = __float2bfloat16_rn(d);
+}
+
+// grad of the head: wh[o] = sum_cand dout * mean(H3)[cand][o]; bh = sum dout
+__global__ void k_head_grad(int B, const float* dout, const float* Mf3, float* grad, size_t owh, size_t obh) {
+  const int o = threadIdx.x;
+  float s = 0.f;
+  for (int c = 0; c < B; ++c) s += dout[c] * Mf3[(size_t)c * kD + o];
+  grad[owh + o] = s;
+  if (o == 0) {
+    float b = 0.f;
+    for (int c = 0; c < B; ++c) b += dout[c];
+    grad[obh] = b;
+  }
+}
+
+// dGamma[f][o] = sum_cand Mprev[cand][f] * S[cand][o]; dbeta[o] = sum_cand S[cand][o]
+__global__ void k_dgamma(int B, int din, const float* Mprev, const float* S, float* grad, size_t ogam, size_t ob) {
+  const int f = blockIdx.x, o = threadIdx.x;
+  float s = 0.f;
+  for (int c = 0; c < B; ++c) s += Mprev[(size_t)c * din + f] * S[(size_t)c * kD + o];
+  grad[ogam + (size_t)f * kD + o] = s;
+  if (f == 0) {
+    float b = 0.f;
+    for (int c = 0; c < B; ++c) b += S[(size_t)c * kD + o];
+    grad[ob + o] = b;
+  }
+}
+
+// Gb[cand][f] = (1/k) sum_o S[cand][o] * Gamma[f][o]
+__global__ void k_gb(int B, int din, int k, const float* S, const float* theta, size_t ogam, float* Gb) {
+  const int cand = blockIdx.x, f = threadIdx.x;
+  if (f >= din) return;
+  const float* g = theta + ogam + (size_t)f * kD;
+  const float* s = S + (size_t)cand * kD;
+  float acc = 0.f;
+  for (int o = 0; o < kD; ++o) acc += s[o] * g[o];
+  Gb[(size_t)cand * din + f] = acc / (float)k;
+}
+
+// grad[dst + i] = sum_z part[z][i]
+__global__ void k_reduce_splits(int64_t cnt, int splits, const float* part, float* dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  float s = 0.f;
+  for (int z = 0; z < splits; ++z) s += part[(size_t)z * cnt + i];
+  dst[i] = s;
+}
+
+// embedding gradient: dE[v][f] = sum_cand dZ0[cand*R + col_cand[v]][f]; db0[f] = sum_cand S0[cand][f]
+__global__ void k_demb(int n, int B, const int16_t* cols, const bf16* dZ0, const float* S0, float* grad, size_t oE,
+                       size_t ob0) {
+  const int v = blockIdx.x, f = threadIdx.x;  // 64 threads
+  if (v < n) {
+    float s = 0.f;
+    for (int c = 0; c < B; ++c) {
+      const int q = cols[(size_t)c * n + v];
+      s += __bfloat162float(dZ0[((size_t)c * kR + q) * kD0 + f]);
+    }
+    grad[oE + (size_t)v * kD0 + f] = s;
+  } else {
+    float b = 0.f;
+    for (int c = 0; c < B; ++c) b += S0[(size_t)c * kD0 + f];
+    grad[ob0 + f] = b;
+  }
+}
+
+__global__ void k_adam(int64_t np, float* th, float* m, float* v, const float* g, float lr, float bc1, float sbc2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float denom = sqrtf(vi) / sbc2 + 1e-8f;
+  th[i] -= (lr / bc1) * mi / denom;
+}
+
+__global__ void k_init_params(int64_t np, uint64_t seed, float* th, const float* bound_of, const int64_t* seg_end, int nseg) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  int s = 0;
+  while (s < nseg - 1 && i >= seg_end[s]) ++s;
+  const U4 r = rng(seed, (uint32_t)i, 0u, 0u, kTagNnInit);
+  const float u = (float)(r.x >> 8) * (1.0f / 16777216.0f);
+  th[i] = (2.f * u - 1.f) * bound_of[s];
+}
+
+// ---- training data: standardised targets, epoch permutation, batch gather ----------------------
+__global__ void k_standardise(int p, const int64_t* f, float* y) {
+  __shared__ double s1[256], s2[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) a += (double)f[i];
+  s1[threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += s1[i];
+    s1[0] = t / p;
+  }
+  __syncthreads();
+  const double mean = s1[0];
+  double b = 0.0;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) b += ((double)f[i] - mean) * ((double)f[i] - mean);
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += s2[i];
+    double sd = sqrt(t / p);
+    if (!(sd > 1e-12)) sd = 1.0;
+    s2[0] = sd;
+  }
+  __syncthreads();
+  const double sd = s2[0];
+  for (int i = threadIdx.x; i < p; i += blockDim.x) y[i] = (float)(((double)f[i] - mean) / sd);
+}
+
+// one CTA: sort of the 64-bit keys (Philox(i, epoch, gen, BATCH).r0 << 32 | i); p <= 8192
+__global__ void k_epoch_perm(int p, uint64_t seed, uint32_t epoch, uint32_t gen, int32_t* perm) {
+  extern __shared__ __align__(16) uint64_t keys[];
+  int mp = 1;
+  while (mp < p) mp <<= 1;
+  for (int i = threadIdx.x; i < mp; i += blockDim.x) {
+    if (i < p) {
+      const U4 r = rng(seed, (uint32_t)i, epoch, gen, kTagBatch);
+      keys[i] = ((uint64_t)r.x << 32) | (uint32_t)i;
+    } else {
+      keys[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= mp; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = threadIdx.x; q < mp; q += blockDim.x) {
+        const int r = q ^ stride;
+        if (r > q) {
+          const bool up = (q & size) == 0;
+          const uint64_t x = keys[q], y = keys[r];
+          if ((x > y) == up) { keys[q] = y; keys[r] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < p; i += blockDim.x) perm[i] = (int32_t)(keys[i] & 0xFFFFFFFFu);
+}
+
+__global__ void k_gather_batch(int n, int B, const int32_t* perm, int s0, const int16_t* cols, const float* y,
+                               int16_t* bcols, float* by) {
+  const int b = blockIdx.x;
+  const int i = perm[s0 + b];
+  for (int v = threadIdx.x; v < n; v += blockDim.x) bcols[(size_t)b * n + v] = cols[(size_t)i * n + v];
+  if (threadIdx.x == 0) by[b] = y[i];
+}
+
+// ------------------------------------------------------------------------------------------------
+// host plumbing
+// ------------------------------------------------------------------------------------------------
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                              const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+  }
+  return fn;
+}
+
+namespace tc {
+dlm_status make_map_bf16(dlm_ctx* ctx, CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+                         uint32_t box_rows) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return fail(ctx, DLM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  if (((uintptr_t)base & 15) || (ld * 2) % 16) return fail(ctx, DLM_EINVAL, "tensor map: misaligned operand");
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, DLM_ECUDA, "cuTensorMapEncodeTiled failed");
+  return DLM_OK;
+}
+}  // namespace tc
+
+// C[M][N] = A[M][K] . B[N][K]^T through the tcgen05 kernel; kc = 64-wide K chunks per CTA
+template <int BN, class Epi>
+static dlm_status gemm(dlm_ctx* ctx, const bf16* A, int M, int K, int lda, const bf16* B, int N, int ldb, int kc, Epi epi) {
+  constexpr int STAGES = 4;
+  if (M <= 0) return DLM_OK;
+  if (K % tc::BK || N % BN) return fail(ctx, DLM_EINVAL, "gemm: K must be a multiple of 64 and N of the tile");
+  CUtensorMap ma, mb;
+  DLM_TRY(tc::make_map_bf16(ctx, &ma, A, (uint64_t)M, (uint64_t)K, (uint64_t)lda, tc::BM));
+  DLM_TRY(tc::make_map_bf16(ctx, &mb, B, (uint64_t)N, (uint64_t)K, (uint64_t)ldb, BN));
+  auto kfn = tc::gemm_kernel<BN, STAGES, Epi>;
+  constexpr size_t smem = tc::gemm_smem_bytes<BN, STAGES>();
+  static bool attr = false;
+  if (!attr) {
+    DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const int nchunks = K / tc::BK;
+  if (kc <= 0) kc = nchunks;
+  tc::GemmShape sh{M, N, K, kc};
+  dim3 grid((M + tc::BM - 1) / tc::BM, N / BN, (nchunks + kc - 1) / kc);
+  kfn<<<grid, tc::kThreads, smem, ctx->stream>>>(ma, mb, sh, epi, ctx->d_status);
+  return launch_check(ctx, "gemm_kernel");
+}
+
+template <typename T>
+static dlm_status dalloc(dlm_ctx* ctx, T** p, size_t count) {
+  if (cudaMalloc((void**)p, std::max<size_t>(1, count) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DLM_ENOMEM, "scorer: device allocation failed");
+  }
+  return DLM_OK;
+}
+
+static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
+  ConvArgs a;
+  a.theta = s->theta;
+  a.n = s->n;
+  a.oE = s->oE;
+  a.E16 = s->E16;
+  int64_t tot = (int64_t)s->n * kD0;
+  for (int l = 1; l <= kNL; ++l) {
+    a.olam[l] = s->olam[l];
+    a.ogam[l] = s->ogam[l];
+    a.LamT[l] = s->LamT[l];
+    a.Lam[l] = s->Lam[l];
+    a.GamT[l] = s->GamT[l];
+    tot += (int64_t)din_of(l) * kD;
+  }
+  k_convert<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(a);
+  return launch_check(ctx, "k_convert");
+}
+
+static size_t pool_smem(int n) { return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + (64 + 65 + 64) * 4 + 8 * 64 * 4 + 64; }
+
+// forward over c candidates with the given buffers; train = keep every activation (and H3)
+static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int c, float* out, bf16** H, bf16** Mb,
+                          float** Mf, float** G, float* rowdot, bool train) {
+  const int rows = c * kR;
+  const size_t psm = pool_smem(s->n);
+  static bool attr = false;
+  if (!attr) {
+    DLM_CUDA(ctx, cudaFuncSetAttribute(k_pool, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+    attr = true;
+  }
+  const int pgrid = std::min(c, ctx->num_sms * 4);
+  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, cols, c, s->E16, s->theta + s->ob0, H[0], Mf[0], Mb[0],
+                                           ctx->d_status);
+  DLM_TRY(launch_check(ctx, "k_pool"));
+  for (int l = 1; l <= kNL; ++l) {
+    const int din = din_of(l);
+    // per-candidate term rho(H_{l-1}) Gamma_l + beta_l (tensor cores, M = c)
+    DLM_TRY(gemm<256>(ctx, Mb[l - 1], c, din, din, s->GamT[l], kD, din, 0,
+                      EpiPlain{G[l], kD, c, 1.f, s->theta + s->ob[l]}));
+    const bool last = l == kNL;
+    EpiLayer e{(last && !train) ? nullptr : H[l], rows, s->k, G[l], last ? s->theta + s->owh : nullptr,
+               last ? rowdot : nullptr, 0.f};
+    DLM_TRY(gemm<256>(ctx, H[l - 1], rows, din, din, s->LamT[l], kD, din, 0, e));
+    if (!last || train) {
+      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], kD, s->k, 1.f / s->k, Mf[l], Mb[l]);
+      DLM_TRY(launch_check(ctx, "k_segment_reduce"));
+    }
+  }
+  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, rowdot, s->theta, s->obh, out);
+  return launch_check(ctx, "k_head_out");
+}
+
+// forward + backward of one batch; gradient into s->grad (overwritten), predictions into outb
+static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const float* y, int B) {
+  DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Mbb, s->Mfb, s->Gbf, s->rowdotb, true));
+  const int rows = B * kR;
+  k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, s->dout, s->lossd);
+  DLM_TRY(launch_check(ctx, "k_loss"));
+  k_head_grad<<<1, kD, 0, ctx->stream>>>(B, s->dout, s->Mfb[kNL], s->grad, s->owh, s->obh);
+  k_head_back<<<rows, kD, 0, ctx->stream>>>(B, s->k, s->dout, s->theta, s->owh, s->Hb[kNL], s->dZ[kNL]);
+  DLM_TRY(launch_check(ctx, "k_head_back"));
+  for (int l = kNL; l >= 1; --l) {
+    const int din = din_of(l);
+    // column sums of dZ_l per candidate (valid rows are the only nonzero ones)
+    k_segment_reduce<<<B, kD, 0, ctx->stream>>>(s->dZ[l], kD, s->k, 1.f, s->S[l], nullptr);
+    DLM_TRY(launch_check(ctx, "k_segment_reduce"));
+    // transposes for the weight-gradient GEMM
+    dim3 tb(32, 8);
+    k_transpose<<<dim3(kD / 32, (rows + 31) / 32), tb, 0, ctx->stream>>>(s->dZ[l], rows, kD, s->dZT[l]);
+    k_transpose<<<dim3(din / 32, (rows + 31) / 32), tb, 0, ctx->stream>>>(s->Hb[l - 1], rows, din, s->HT[l - 1]);
+    DLM_TRY(launch_check(ctx, "k_transpose"));
+    // dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction)
+    const int nchunks = rows / tc::BK, kc = 4, splits = (nchunks + kc - 1) / kc;
+    DLM_TRY(gemm<256>(ctx, s->HT[l - 1], din, rows, rows, s->dZT[l], kD, rows, kc,
+                      EpiPartial{s->part, kD, din, (size_t)din * kD}));
+    const int64_t cnt = (int64_t)din * kD;
+    k_reduce_splits<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, splits, s->part, s->grad + s->olam[l]);
+    DLM_TRY(launch_check(ctx, "k_reduce_splits"));
+    // dGamma_l, dbeta_l and the per-candidate term of dH_{l-1}
+    k_dgamma<<<din, kD, 0, ctx->stream>>>(B, din, s->Mfb[l - 1], s->S[l], s->grad, s->ogam[l], s->ob[l]);
+    k_gb<<<B, din, 0, ctx->stream>>>(B, din, s->k, s->S[l], s->theta, s->ogam[l], s->Gb);
+    DLM_TRY(launch_check(ctx, "k_gb"));
+    // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
+    EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->Gb, s->Hb[l - 1]};
+    if (din == kD) DLM_TRY(gemm<256>(ctx, s->dZ[l], rows, kD, kD, s->Lam[l], din, kD, 0, e));
+    else DLM_TRY(gemm<64>(ctx, s->dZ[l], rows, kD, kD, s->Lam[l], din, kD, 0, e));
+  }
+  k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], kD0, s->k, 1.f, s->S[0], nullptr);
+  k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, cols, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
+  return launch_check(ctx, "k_demb");
+}
+
+static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
+  if (B <= s->capb) return DLM_OK;
+  if (B > 256) return fail(ctx, DLM_EUNSUPPORTED, "scorer: training batches are limited to 256 samples");
+  const int cb = 256, rows = cb * kR, cpad = cb;
+  for (int l = 0; l <= kNL; ++l) {
+    const int w = l == 0 ? kD0 : kD;
+    DLM_TRY(dalloc(ctx, &s->Hb[l], (size_t)rows * w));
+    DLM_TRY(dalloc(ctx, &s->HT[l], (size_t)rows * w));
+    DLM_TRY(dalloc(ctx, &s->Mbb[l], (size_t)cpad * w));
+    DLM_TRY(dalloc(ctx, &s->Mfb[l], (size_t)cb * w));
+    DLM_TRY(dalloc(ctx, &s->Gbf[l], (size_t)cb * kD));
+    DLM_TRY(dalloc(ctx, &s->dZ[l], (size_t)rows * w));
+    DLM_TRY(dalloc(ctx, &s->dZT[l], (size_t)rows * w));
+    DLM_TRY(dalloc(ctx, &s->S[l], (size_t)cb * w));
+  }
+  DLM_TRY(dalloc(ctx, &s->Gb, (size_t)cb * kD));
+  DLM_TRY(dalloc(ctx, &s->part, (size_t)(rows / tc::BK / 4 + 1) * kD * kD));
+  DLM_TRY(dalloc(ctx, &s->rowdotb, (size_t)rows));
+  DLM_TRY(dalloc(ctx, &s->outb, (size_t)cb));
+  DLM_TRY(dalloc(ctx, &s->dout, (size_t)cb));
+  DLM_TRY(dalloc(ctx, &s->lossd, 1));
+  DLM_TRY(dalloc(ctx, &s->bcols, (size_t)cb * s->n));
+  DLM_TRY(dalloc(ctx, &s->by, (size_t)cb));
+  s->capb = cb;
+  return DLM_OK;
+}
+
+static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
+  if (s->cap) return DLM_OK;
+  const int cap = 8192, rows = cap * kR;
+  for (int l = 0; l <= kNL; ++l) {
+    const int w = l == 0 ? kD0 : kD;
+    if (l < kNL) DLM_TRY(dalloc(ctx, &s->H[l], (size_t)rows * w));
+    DLM_TRY(dalloc(ctx, &s->Mb[l], (size_t)cap * w));
+    DLM_TRY(dalloc(ctx, &s->Mf[l], (size_t)cap * w));
+    DLM_TRY(dalloc(ctx, &s->G[l], (size_t)cap * kD));
+  }
+  DLM_TRY(dalloc(ctx, &s->rowdot, (size_t)rows));
+  s->cap = cap;
+  return DLM_OK;
+}
+
+static dlm_status adam_step(dlm_ctx* ctx, dlm_scorer* s, float lr) {
+  s->t += 1;
+  const double bc1 = 1.0 - std::pow(0.9, (double)s->t), bc2 = 1.0 - std::pow(0.999, (double)s->t);
+  k_adam<<<(unsigned)((s->np + 255) / 256), 256, 0, ctx->stream>>>(s->np, s->theta, s->am, s->av, s->grad, lr, (float)bc1,
+                                                                   (float)std::sqrt(bc2));
+  DLM_TRY(launch_check(ctx, "k_adam"));
+  return convert_params(ctx, s);
+}
+
+}  // namespace dlm
+
+using namespace dlm;
+
+extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
+  if (!s) return;
+  cudaFree(s->theta); cudaFree(s->am); cudaFree(s->av); cudaFree(s->grad); cudaFree(s->E16);
+  for (int l = 0; l <= kNL; ++l) {
+    cudaFree(s->LamT[l]); cudaFree(s->Lam[l]); cudaFree(s->GamT[l]);
+    cudaFree(s->H[l]); cudaFree(s->Mb[l]); cudaFree(s->Mf[l]); cudaFree(s->G[l]);
+    cudaFree(s->Hb[l]); cudaFree(s->HT[l]); cudaFree(s->Mbb[l]); cudaFree(s->Mfb[l]); cudaFree(s->Gbf[l]);
+    cudaFree(s->dZ[l]); cudaFree(s->dZT[l]); cudaFree(s->S[l]);
+  }
+  cudaFree(s->rowdot); cudaFree(s->Gb); cudaFree(s->part); cudaFree(s->rowdotb); cudaFree(s->outb); cudaFree(s->dout);
+  cudaFree(s->lossd); cudaFree(s->bcols); cudaFree(s->y); cudaFree(s->by); cudaFree(s->perm);
+  delete s;
+}
+
+extern "C" dlm_status dlm_scorer_create(dlm_ctx* ctx, int32_t n, int32_t k, uint64_t seed, dlm_scorer** out) {
+  if (!ctx || !out) return fail(ctx, DLM_EINVAL, "scorer_create: null argument");
+  *out = nullptr;
+  if (n < 1 || n > 2048 || k < 1) return fail(ctx, DLM_EINVAL, "scorer_create: bad sizes");
+  if (k > kR) return fail(ctx, DLM_EUNSUPPORTED, "scorer_create: k must be <= 64");
+  dlm_scorer* s = new dlm_scorer();
+  s->n = n;
+  s->k = k;
+  size_t o = 0;
+  s->oE = o; o += (size_t)n * kD0;
+  s->ob0 = o; o += kD0;
+  for (int l = 1; l <= kNL; ++l) {
+    s->olam[l] = o; o += (size_t)din_of(l) * kD;
+    s->ogam[l] = o; o += (size_t)din_of(l) * kD;
+    s->ob[l] = o; o += kD;
+  }
+  s->owh = o; o += kD;
+  s->obh = o; o += 1;
+  s->np = (int64_t)o;
+  dlm_status st = DLM_OK;
+  auto A = [&](auto** p, size_t cnt) { if (st == DLM_OK) st = dalloc(ctx, p, cnt); };
+  A(&s->theta, o); A(&s->am, o); A(&s->av, o); A(&s->grad, o); A(&s->E16, (size_t)n * kD0);
+  for (int l = 1; l <= kNL; ++l) {
+    A(&s->LamT[l], (size_t)din_of(l) * kD); A(&s->Lam[l], (size_t)din_of(l) * kD); A(&s->GamT[l], (size_t)din_of(l) * kD);
+  }
+  if (st != DLM_OK) { dlm_scorer_destroy(s); return st; }
+  // uniform +-1/sqrt(fan_in) per parameter block (fan_in of E and b0: n)
+  std::vector<float> bound;
+  std::vector<int64_t> seg_end;
+  auto seg = [&](size_t end, int fan) { seg_end.push_back((int64_t)end); bound.push_back(1.f / std::sqrt((float)fan)); };
+  seg(s->ob0, n);
+  seg(s->ob0 + kD0, n);
+  for (int l = 1; l <= kNL; ++l) {
+    seg(s->ogam[l], din_of(l));
+    seg(s->ob[l], din_of(l));
+    seg(s->ob[l] + kD, din_of(l));
+  }
+  seg(s->obh, kD);
+  seg(o, kD);
+  float* dbound = nullptr;
+  int64_t* dseg = nullptr;
+  void* ws = nullptr;
+  st = ctx_workspace(ctx, bound.size() * 4 + 64 + seg_end.size() * 8, &ws);
+  if (st == DLM_OK) {
+    dbound = (float*)ws;
+    dseg = (int64_t*)((uint8_t*)ws + ((bound.size() * 4 + 63) & ~(size_t)63));
+    cudaMemcpyAsync(dbound, bound.data(), bound.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dseg, seg_end.data(), seg_end.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
+    k_init_params<<<(unsigned)((o + 255) / 256), 256, 0, ctx->stream>>>((int64_t)o, seed, s->theta, dbound, dseg,
+                                                                          (int)seg_end.size());
+    st = launch_check(ctx, "k_init_params");
+  }
+  if (st == DLM_OK) st = cuda_check(ctx, cudaMemsetAsync(s->am, 0, o * 4, ctx->stream), "memset");
+  if (st == DLM_OK) st = cuda_check(ctx, cudaMemsetAsync(s->av, 0, o * 4, ctx->stream), "memset");
+  if (st == DLM_OK) st = convert_params(ctx, s);
+  if (st == DLM_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  if (st != DLM_OK) { dlm_scorer_destroy(s); return st; }
+  *out = s;
+  return DLM_OK;
+}
+
+extern "C" int64_t dlm_scorer_nparams(const dlm_scorer* s) { return s ? s->np : 0; }
+
+extern "C" dlm_status dlm_scorer_get_params(dlm_ctx* ctx, dlm_scorer* s, float* params) {
+  if (!ctx || !s || !params) return fail(ctx, DLM_EINVAL, "scorer_get_params: null argument");
+  DLM_CUDA(ctx, cudaMemcpyAsync(params, s->theta, (size_t)s->np * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_scorer_set_params(dlm_ctx* ctx, dlm_scorer* s, const float* params) {
+  if (!ctx || !s || !params) return fail(ctx, DLM_EINVAL, "scorer_set_params: null argument");
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->theta, params, (size_t)s->np * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaMemsetAsync(s->am, 0, (size_t)s->np * 4, ctx->stream));
+  DLM_CUDA(ctx, cudaMemsetAsync(s->av, 0, (size_t)s->np * 4, ctx->stream));
+  s->t = 0;
+  return convert_params(ctx, s);
+}
+
+extern "C" dlm_status dlm_score_offspring(dlm_ctx* ctx, dlm_scorer* s, const int16_t* col, int32_t c, float* out) {
+  if (!ctx || !s) return fail(ctx, DLM_EINVAL, "score_offspring: null argument");
+  if (c < 0) return fail(ctx, DLM_EINVAL, "score_offspring: negative count");
+  if (c == 0) return DLM_OK;
+  if (!col || !out) return fail(ctx, DLM_EINVAL, "score_offspring: null pointer");
+  DLM_TRY(ensure_fwd_buffers(ctx, s));
+  for (int c0 = 0; c0 < c; c0 += s->cap) {
+    const int cc = std::min(s->cap, c - c0);
+    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, out + c0, s->H, s->Mb, s->Mf, s->G, s->rowdot, false));
+  }
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_scorer_loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* col, const float* y, int32_t B,
+                                           float* grad, float* out, float* loss) {
+  if (!ctx || !s || !col || !y) return fail(ctx, DLM_EINVAL, "scorer_loss_grad: null argument");
+  if (B < 1) return fail(ctx, DLM_EINVAL, "scorer_loss_grad: empty batch");
+  DLM_TRY(ensure_train_buffers(ctx, s, B));
+  DLM_TRY(loss_grad(ctx, s, col, y, B));
+  if (grad) DLM_CUDA(ctx, cudaMemcpyAsync(grad, s->grad, (size_t)s->np * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (out) DLM_CUDA(ctx, cudaMemcpyAsync(out, s->outb, (size_t)B * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (loss) DLM_CUDA(ctx, cudaMemcpyAsync(loss, s->lossd, 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_scorer_train(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const int64_t* fvals, int32_t p,
+                                       int32_t epochs, int32_t b, float lr, uint64_t seed, uint32_t generation) {
+  if (!ctx || !s || !cols || !fvals) return fail(ctx, DLM_EINVAL, "scorer_train: null argument");
+  if (p < 1 || p > 8192 || epochs < 0 || b < 1) return fail(ctx, DLM_EINVAL, "scorer_train: bad sizes (p <= 8192)");
+  const int bb = std::min(b, p);
+  DLM_TRY(ensure_train_buffers(ctx, s, bb));
+  if (p > s->capp) {
+    cudaFree(s->y);
+    cudaFree(s->perm);
+    s->y = nullptr;
+    s->perm = nullptr;
+    DLM_TRY(dalloc(ctx, &s->y, 8192));
+    DLM_TRY(dalloc(ctx, &s->perm, 8192));
+    s->capp = 8192;
+  }
+  k_standardise<<<1, 256, 0, ctx->stream>>>(p, fvals, s->y);
+  DLM_TRY(launch_check(ctx, "k_standardise"));
+  int mp = 1;
+  while (mp < p) mp <<= 1;
+  static bool attr = false;
+  if (!attr) {
+    DLM_CUDA(ctx, cudaFuncSetAttribute(k_epoch_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
+    attr = true;
+  }
+  for (int ep = 0; ep < epochs; ++ep) {
+    k_epoch_perm<<<1, 1024, (size_t)mp * 8, ctx->stream>>>(p, seed, (uint32_t)ep, generation, s->perm);
+    DLM_TRY(launch_check(ctx, "k_epoch_perm"));
+    for (int s0 = 0; s0 < p; s0 += b) {
+      const int B = std::min(b, p - s0);
+      k_gather_batch<<<B, 128, 0, ctx->stream>>>(s->n, B, s->perm, s0, cols, s->y, s->bcols, s->by);
+      DLM_TRY(launch_check(ctx, "k_gather_batch"));
+      DLM_TRY(loss_grad(ctx, s, s->bcols, s->by, B));
+      DLM_TRY(adam_step(ctx, s, lr));
+    }
+  }
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_gemm_bf16(dlm_ctx* ctx, const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K) {
+  if (!ctx || !A || !B || !C) return fail(ctx, DLM_EINVAL, "gemm_bf16: null argument");
+  if (M < 1 || N < 64 || K < 64 || K % 64 || N % 64) return fail(ctx, DLM_EINVAL, "gemm_bf16: need K, N multiples of 64");
+  if (N % 256 == 0)
+    return gemm<256>(ctx, (const bf16*)A, M, K, K, (const bf16*)B, N, K, 0, EpiPlain{C, N, M, 1.f, nullptr});
+  return gemm<64>(ctx, (const bf16*)A, M, K, K, (const bf16*)B, N, K, 0, EpiPlain{C, N, M, 1.f, nullptr});
+}

@@ -77,6 +77,7 @@ _SIGS = {
     "dlm_memetic_get": (_i32, [_P, _P, _i32, _P]),
     "dlm_memetic_set": (_i32, [_P, _P, _i32, _P]),
     "dlm_probe_smem_bandwidth": (_i32, [_P, _P]),
+    "dlm_gemm_bf16": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32]),
     "dlm_wvcp_tabu_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32]),
 }
 
@@ -315,6 +316,10 @@ def dlm_memetic_get(ctx, mm, which, dst):
 
 def dlm_memetic_set(ctx, mm, which, src):
     ctx.check(lib().dlm_memetic_set(ctx.h, mm.h, which, _ptr(src)), "dlm_memetic_set")
+
+
+def dlm_gemm_bf16(ctx, A, B, C, M, N, K):
+    ctx.check(lib().dlm_gemm_bf16(ctx.h, _ptr(A), _ptr(B), _ptr(C), M, N, K), "dlm_gemm_bf16")
 
 
 def dlm_probe_smem_bandwidth(ctx):

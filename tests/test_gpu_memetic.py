@@ -1,0 +1,104 @@
+"""GPU parity of whole memetic generations (Algorithm 1) against the oracle, through the C-ABI.
+Random-GPX generations are integer work and must match bit for bit; learned generations match bit
+for bit when the oracle selects offspring with the GPU's scores."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_05948_gb300 import dlmcol, inputs
+
+from gpu_util import device_graph
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2109_05948_gb300 import build
+
+    build.build()
+    c = dlmcol.Context(0)
+    yield c
+    c.close()
+
+
+def _get(ctx, mm, which, shape, dtype):
+    t = torch.zeros(shape, dtype=dtype, device="cuda")
+    dlmcol.dlm_memetic_get(ctx, mm, which, t)
+    ctx.sync()
+    return t.cpu().numpy()
+
+
+def _compare(ctx, mm, st, p, n, K, step):
+    assert np.array_equal(_get(ctx, mm, 0, (p, n), torch.int16), st.P), f"P at generation {step}"
+    assert np.array_equal(_get(ctx, mm, 1, (p,), torch.int64), st.fP), f"f(P) at generation {step}"
+    assert np.array_equal(_get(ctx, mm, 2, (p, p), torch.int16), st.DP), f"D(P) at generation {step}"
+    assert np.array_equal(_get(ctx, mm, 3, (p, n), torch.int16), st.SO), f"S^O at generation {step}"
+    assert np.array_equal(_get(ctx, mm, 4, (n,), torch.int16), st.best_col)
+
+
+@pytest.mark.parametrize("n,k,p,K,iters,gens,seed", [(80, 5, 48, 6, 300, 3, 1), (130, 8, 40, 39, 200, 2, 2)])
+def test_memetic_random_gpx_bitexact(ctx, n, k, p, K, iters, gens, seed):
+    e, _ = inputs.planted(n, k, 0.4, seed=seed)
+    adj = inputs.edges_to_adj(n, e)
+    g = device_graph(ctx, n, e)
+    prm = dlmcol.MemeticParams(k=k, p=p, K=K, iters=iters, tenure=dlmcol.COL_TENURE, use_scorer=0, epochs=0, batch=100,
+                               lr=1e-3, seed=seed)
+    mm = dlmcol.Memetic(ctx, g, prm)
+    st = oracle.MemeticState(adj, k, p, K, seed=seed, iters=iters, use_scorer=0)
+    _compare(ctx, mm, st, p, n, K, -1)
+    for gen in range(gens):
+        best = dlmcol.dlm_memetic_step(ctx, mm)
+        fprime, pick = st.generation()
+        assert np.array_equal(_get(ctx, mm, 5, (p,), torch.int64), fprime)
+        assert np.array_equal(_get(ctx, mm, 6, (p,), torch.int32), pick)
+        assert best == st.best_f[0]
+        _compare(ctx, mm, st, p, n, K, gen)
+    mm.close()
+
+
+def test_memetic_learned_selection_bitexact_with_gpu_scores(ctx):
+    n, k, p, K, iters, seed = 60, 5, 32, 4, 200, 3
+    e, _ = inputs.planted(n, k, 0.4, seed=seed)
+    adj = inputs.edges_to_adj(n, e)
+    g = device_graph(ctx, n, e)
+    prm = dlmcol.MemeticParams(k=k, p=p, K=K, iters=iters, tenure=dlmcol.COL_TENURE, use_scorer=1, epochs=1, batch=16,
+                               lr=1e-3, seed=seed)
+    mm = dlmcol.Memetic(ctx, g, prm)
+    st = oracle.MemeticState(adj, k, p, K, seed=seed, iters=iters, use_scorer=1, epochs=1, batch=16)
+    for gen in range(2):
+        dlmcol.dlm_memetic_step(ctx, mm)
+        scores = _get(ctx, mm, 7, (p, K), torch.float32)
+        assert np.all(np.isfinite(scores))
+        fprime, pick = st.generation(ext_scores=scores)
+        assert np.array_equal(_get(ctx, mm, 6, (p,), torch.int32), pick)
+        assert np.array_equal(_get(ctx, mm, 5, (p,), torch.int64), fprime)
+        _compare(ctx, mm, st, p, n, K, gen)
+    mm.close()
+
+
+def test_memetic_scorer_scores_match_oracle_after_training(ctx):
+    """After one learned generation, the GPU's candidate scores equal the oracle network (FP64)
+    evaluated with the GPU's trained parameters, within the scorer tolerance."""
+    n, k, p, K, iters, seed = 60, 5, 32, 4, 150, 4
+    e, _ = inputs.planted(n, k, 0.4, seed=seed)
+    g = device_graph(ctx, n, e)
+    prm = dlmcol.MemeticParams(k=k, p=p, K=K, iters=iters, tenure=dlmcol.COL_TENURE, use_scorer=1, epochs=2, batch=16,
+                               lr=1e-3, seed=seed)
+    mm = dlmcol.Memetic(ctx, g, prm)
+    dlmcol.dlm_memetic_step(ctx, mm)
+    scores = _get(ctx, mm, 7, (p, K), torch.float32)
+    P = _get(ctx, mm, 0, (p, n), torch.int16)
+    nparams = oracle.ScorerDims(n).nparams()
+    th = _get(ctx, mm, 8, (nparams,), torch.float32).astype(np.float64)
+    DP = _get(ctx, mm, 2, (p, p), torch.int16)
+    nbr = oracle.knn(DP, K)
+    kids = np.stack([oracle.gpx(k, P[i], P[nbr[i, j]], seed, i * K + j, 0) for i in range(p) for j in range(K)])
+    ref = oracle.scorer_forward(oracle.ScorerDims(n), k, th, kids).reshape(p, K)
+    rel = np.linalg.norm(scores - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-2
+    mm.close()

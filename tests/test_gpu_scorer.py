@@ -1,0 +1,155 @@
+"""GPU parity of the tcgen05 scorer: the GEMM building block against a plain PyTorch fp32 matmul,
+and the network's forward pass, gradients and Adam training against the FP64 oracle.
+
+Tolerance: the scorer computes in BF16 with FP32 accumulation; results must be within 1e-2
+relative (norm-wise over a batch or a parameter block) of the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_05948_gb300 import dlmcol, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2109_05948_gb300 import build
+
+    build.build()
+    c = dlmcol.Context(0)
+    yield c
+    c.close()
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 256, 256), (1000, 64, 256), (77, 256, 6400), (5, 64, 64)])
+def test_gemm_bf16_matches_torch_fp32(ctx, M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    dlmcol.dlm_gemm_bf16(ctx, A, B, C, M, N, K)
+    ctx.sync()
+    ref = A.float() @ B.float().T
+    err = (C - ref).abs().max().item()
+    assert err <= 1e-4 * max(1.0, ref.abs().max().item()), err
+
+
+def _params(dims, seed, scale):
+    th = oracle.scorer_init(dims, seed) * scale
+    return th
+
+
+def _gpu_scorer(ctx, n, k, th):
+    s = dlmcol.Scorer(ctx, n, k, seed=1)
+    assert s.nparams == th.size
+    dlmcol.dlm_scorer_set_params(ctx, s, torch.from_numpy(th.astype(np.float32)).cuda())
+    return s
+
+
+@pytest.mark.parametrize("n,k,c,scale", [(200, 48, 37, 3.0), (97, 17, 130, 2.0), (64, 64, 9, 4.0), (30, 2, 5, 3.0)])
+def test_scorer_forward_matches_oracle(ctx, n, k, c, scale):
+    dims = oracle.ScorerDims(n)
+    th = _params(dims, seed=n, scale=scale)
+    cols = inputs.random_colorings(c, n, k, seed=c)
+    ref = oracle.scorer_forward(dims, k, th, cols)
+    s = _gpu_scorer(ctx, n, k, th)
+    out = torch.zeros(c, dtype=torch.float32, device="cuda")
+    dlmcol.dlm_score_offspring(ctx, s, torch.from_numpy(cols).cuda(), c, out)
+    ctx.sync()
+    got = out.cpu().numpy()
+    assert _rel(got - th[-1], ref - th[-1]) <= TOL  # the head bias is exact; compare the rest
+    assert _rel(got, ref) <= TOL
+    s.close()
+
+
+def test_scorer_permutation_invariant_on_gpu(ctx):
+    n, k, c = 150, 20, 12
+    dims = oracle.ScorerDims(n)
+    th = _params(dims, seed=3, scale=3.0)
+    cols = inputs.random_colorings(c, n, k, seed=2)
+    sigma = np.random.default_rng(0).permutation(k)
+    s = _gpu_scorer(ctx, n, k, th)
+    a = torch.zeros(c, dtype=torch.float32, device="cuda")
+    b = torch.zeros(c, dtype=torch.float32, device="cuda")
+    dlmcol.dlm_score_offspring(ctx, s, torch.from_numpy(cols).cuda(), c, a)
+    dlmcol.dlm_score_offspring(ctx, s, torch.from_numpy(sigma[cols].astype(np.int16)).cuda(), c, b)
+    ctx.sync()
+    assert torch.allclose(a, b, rtol=1e-5, atol=1e-6)
+    s.close()
+
+
+@pytest.mark.parametrize("n,k,B", [(120, 17, 100), (300, 48, 33)])
+def test_scorer_gradients_match_oracle(ctx, n, k, B):
+    dims = oracle.ScorerDims(n)
+    th = _params(dims, seed=k, scale=3.0)
+    cols = inputs.random_colorings(B, n, k, seed=B)
+    y = np.random.default_rng(1).normal(size=B)
+    loss_ref, g_ref, out_ref = oracle.scorer_loss_grad(dims, k, th, cols, y)
+    s = _gpu_scorer(ctx, n, k, th)
+    grad = torch.zeros(s.nparams, dtype=torch.float32, device="cuda")
+    out = torch.zeros(B, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    dlmcol.dlm_scorer_loss_grad(ctx, s, torch.from_numpy(cols).cuda(), torch.from_numpy(y.astype(np.float32)).cuda(),
+                                B, grad, out, loss)
+    ctx.sync()
+    assert _rel(out.cpu().numpy(), out_ref) <= TOL
+    assert abs(loss.item() - loss_ref) <= TOL * loss_ref
+    g = grad.cpu().numpy()
+    for name, (off, shape) in dims.offsets().items():
+        sz = int(np.prod(shape))
+        e = _rel(g[off:off + sz], g_ref[off:off + sz])
+        assert e <= TOL, (name, e)
+    s.close()
+
+
+def test_scorer_training_matches_oracle(ctx):
+    """Two epochs of Adam (lr 1e-3, b = 100) on p = 250 samples: the parameter change of the
+    GPU run matches the FP64 oracle's within the tolerance."""
+    n, k, p = 80, 9, 250
+    dims = oracle.ScorerDims(n)
+    th0 = _params(dims, seed=5, scale=2.0)
+    cols = inputs.random_colorings(p, n, k, seed=3)
+    fvals = np.random.default_rng(2).integers(0, 40, size=p).astype(np.int64)
+    th = th0.copy()
+    am, av = np.zeros_like(th), np.zeros_like(th)
+    oracle.scorer_train(dims, k, th, am, av, 0, cols, fvals, epochs=2, b=100, lr=1e-3, seed=9, gen=4)
+    s = _gpu_scorer(ctx, n, k, th0)
+    dlmcol.dlm_scorer_train(ctx, s, torch.from_numpy(cols).cuda(), torch.from_numpy(fvals).cuda(), p, 2, 100, 1e-3, 9, 4)
+    got = torch.zeros(s.nparams, dtype=torch.float32, device="cuda")
+    dlmcol.dlm_scorer_get_params(ctx, s, got)
+    ctx.sync()
+    d_gpu = got.cpu().numpy().astype(np.float64) - th0.astype(np.float32).astype(np.float64)
+    d_ref = th - th0
+    assert _rel(d_gpu, d_ref) <= 5 * TOL  # Adam divides by sqrt(v): tiny gradients amplify rounding
+    s.close()
+
+
+def test_scorer_full_size_sampled(ctx):
+    """The scoring launch of the learned memetic workload: n = 1000, k = 48, 8192 x 32 candidates;
+    16 sampled scores against the FP64 oracle."""
+    n, k, c = 1000, 48, 8192 * 32
+    dims = oracle.ScorerDims(n)
+    th = _params(dims, seed=11, scale=3.0)
+    s = _gpu_scorer(ctx, n, k, th)
+    cols = torch.randint(0, k, (c, n), dtype=torch.int16, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    out = torch.zeros(c, dtype=torch.float32, device="cuda")
+    dlmcol.dlm_score_offspring(ctx, s, cols, c, out)
+    ctx.sync()
+    sample = [0, 1, 127, 128, 8191, 8192, 100000, 200000, 262142, 262143, 5, 77, 4096, 65536, 131072, 250000]
+    ref = oracle.scorer_forward(dims, k, th, cols[sample].cpu().numpy())
+    assert _rel(out[sample].cpu().numpy(), ref) <= TOL
+    assert torch.isfinite(out).all()
+    s.close()
