@@ -12,11 +12,13 @@
 // Where the work runs:
 //   tcgen05 BF16 GEMMs (FP32 accumulate in TMEM): H Lambda for layers 1..3 (fused epilogue:
 //     + per-candidate (rho Gamma + beta), LeakyReLU, row mask, bf16 store, head dot product),
-//     the per-candidate rho(H) Gamma terms, the backward dH = dZ Lambda^T (fused: + per-candidate
-//     term, LeakyReLU derivative, row mask) and the weight gradients dLambda = H^T dZ (split-K).
-//   CUDA cores: the class pooling of layer 0 (a gather, not a contraction), per-candidate means
-//     and column sums, the small per-candidate Gamma products of the backward pass (batch of
-//     b = 100 candidates), the embedding gradient (scatter by colour), Adam.
+//     the backward dH = dZ Lambda^T (fused: + per-candidate term, LeakyReLU derivative, row mask)
+//     and the weight gradients dLambda = H^T dZ (split-K). Lambda enters as two bf16 matrices
+//     (hi + lo): two MMAs per K step keep the weights at ~16 mantissa bits, since rounding the
+//     weights to bf16 shifts every row of a layer the same way and dominates the error.
+//   CUDA cores (FP32): the class pooling of layer 0 (a gather, not a contraction), per-candidate
+//     means and column sums, the per-candidate rho(H) Gamma terms (one row per candidate, 1/64 of
+//     the layer's work), the embedding gradient (scatter by colour), Adam.
 // All reductions run in a fixed order: results are deterministic run to run.
 #include <cuda_bf16.h>
 
@@ -39,7 +41,7 @@ struct dlm_scorer {
   size_t oE = 0, ob0 = 0, olam[4] = {}, ogam[4] = {}, ob[4] = {}, owh = 0, obh = 0;
   float *theta = nullptr, *am = nullptr, *av = nullptr, *grad = nullptr;
   bf16* E16 = nullptr;
-  bf16 *LamT[4] = {}, *Lam[4] = {}, *GamT[4] = {};
+  bf16 *LamT[4] = {}, *Lam[4] = {}, *LamTlo[4] = {}, *Lamlo[4] = {};
   // forward work buffers for up to `cap` candidates
   int cap = 0;
   bf16* H[4] = {};
@@ -50,7 +52,9 @@ struct dlm_scorer {
   // backward buffers for up to `capb` candidates
   int capb = 0;
   bf16* Hb[4] = {};
+  bf16* Hblo[4] = {};  // lo parts of the training activations (hi + lo carries ~16 mantissa bits)
   bf16* HT[4] = {};
+  bf16* HTlo[4] = {};
   bf16* Mbb[4] = {};
   float* Mfb[4] = {};
   float* Gbf[4] = {};
@@ -83,7 +87,7 @@ struct ConvArgs {
   int n;
   size_t oE, olam[4], ogam[4];
   bf16* E16;
-  bf16 *LamT[4], *Lam[4], *GamT[4];
+  bf16 *LamT[4], *Lam[4], *LamTlo[4], *Lamlo[4];
 };
 
 __global__ void k_convert(ConvArgs a) {
@@ -96,10 +100,13 @@ __global__ void k_convert(ConvArgs a) {
     const int64_t sz = (int64_t)din * kD;
     if (r < sz) {
       const int f = (int)(r / kD), o = (int)(r % kD);
-      const float lam = a.theta[a.olam[l] + r], gam = a.theta[a.ogam[l] + r];
-      a.Lam[l][r] = __float2bfloat16_rn(lam);
-      a.LamT[l][(size_t)o * din + f] = __float2bfloat16_rn(lam);
-      a.GamT[l][(size_t)o * din + f] = __float2bfloat16_rn(gam);
+      const float lam = a.theta[a.olam[l] + r];
+      const bf16 hi = __float2bfloat16_rn(lam);
+      const bf16 lo = __float2bfloat16_rn(lam - __bfloat162float(hi));
+      a.Lam[l][r] = hi;
+      a.Lamlo[l][r] = lo;
+      a.LamT[l][(size_t)o * din + f] = hi;
+      a.LamTlo[l][(size_t)o * din + f] = lo;
       return;
     }
     r -= sz;
@@ -108,11 +115,11 @@ __global__ void k_convert(ConvArgs a) {
 
 // ------------------------------------------------------------------------------------------------
 // layer 0: class pooling. One CTA per candidate (grid-stride): a stable counting sort puts the
-// vertices of each class in ascending order, then warp w sums the embedding rows of classes
-// w, w+8, ... with lane = feature pair (fixed summation order).
+// vertices of each class in ascending order, then warp w sums the FP32 embedding rows of classes
+// w, w+8, ... with lane = feature pair (fixed summation order; E is read through L1/L2).
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols, int c, const bf16* E16, const float* b0,
-                                              bf16* H0, float* Mf0, bf16* Mb0, int32_t* status) {
+__global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols, int c, const float* E, const float* b0,
+                                              bf16* H0, bf16* H0lo, float* Mf0, bf16* Mb0, int32_t* status) {
   extern __shared__ __align__(16) uint8_t sm[];
   uint8_t* col = sm;                                        // [n]
   uint16_t* mem = (uint16_t*)(sm + ((n + 15) & ~15));       // [n]
@@ -169,8 +176,7 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
       if (q < k) {
         for (int j = off[q]; j < off[q + 1]; ++j) {
           const int v = mem[j];
-          const __nv_bfloat162 e = *reinterpret_cast<const __nv_bfloat162*>(E16 + (size_t)v * kD0 + 2 * lane);
-          const float2 ef = __bfloat1622float2(e);
+          const float2 ef = *reinterpret_cast<const float2*>(E + (size_t)v * kD0 + 2 * lane);
           acc.x += ef.x;
           acc.y += ef.y;
         }
@@ -180,7 +186,13 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
         msum.x += acc.x;
         msum.y += acc.y;
       }
-      *reinterpret_cast<__nv_bfloat162*>(H0 + ((size_t)cand * kR + q) * kD0 + 2 * lane) = __floats2bfloat162_rn(acc.x, acc.y);
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(acc.x, acc.y);
+      *reinterpret_cast<__nv_bfloat162*>(H0 + ((size_t)cand * kR + q) * kD0 + 2 * lane) = hi;
+      if (H0lo) {
+        const float2 hf = __bfloat1622float2(hi);
+        *reinterpret_cast<__nv_bfloat162*>(H0lo + ((size_t)cand * kR + q) * kD0 + 2 * lane) =
+            __floats2bfloat162_rn(acc.x - hf.x, acc.y - hf.y);
+      }
     }
     part[warp * 64 + 2 * lane] = msum.x;
     part[warp * 64 + 2 * lane + 1] = msum.y;
@@ -196,12 +208,40 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
   }
 }
 
+// per-candidate term G[cand][o] = beta[o] + sum_f M[cand][f] Gamma[f][o] in FP32; a block of
+// 256 threads (thread = o) handles 16 candidates, reading each Gamma row once for all 16
+constexpr int kGTile = 16;
+__global__ void __launch_bounds__(256) k_gterm(int c, int din, const float* M, const float* theta, size_t ogam,
+                                               size_t ob, float* G) {
+  __shared__ float ms[kGTile][256];
+  const int c0 = blockIdx.x * kGTile, o = threadIdx.x;
+  for (int i = threadIdx.x; i < kGTile * din; i += 256) {
+    const int cc = i / din, f = i % din;
+    ms[cc][f] = (c0 + cc < c) ? M[(size_t)(c0 + cc) * din + f] : 0.f;
+  }
+  __syncthreads();
+  float acc[kGTile];
+#pragma unroll
+  for (int q = 0; q < kGTile; ++q) acc[q] = 0.f;
+  const float* gam = theta + ogam;
+  for (int f = 0; f < din; ++f) {
+    const float g = gam[(size_t)f * kD + o];
+#pragma unroll
+    for (int q = 0; q < kGTile; ++q) acc[q] += ms[q][f] * g;
+  }
+  const float b = theta[ob + o];
+#pragma unroll
+  for (int q = 0; q < kGTile; ++q)
+    if (c0 + q < c) G[(size_t)(c0 + q) * kD + o] = acc[q] + b;
+}
+
 // per-candidate mean (or sum) over the k valid rows of a bf16 [c*R][w] matrix; block = w threads
-__global__ void k_segment_reduce(const bf16* X, int w, int k, float scale, float* outf, bf16* outb) {
+__global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf, bf16* outb) {
   const int cand = blockIdx.x, col = threadIdx.x;
   const bf16* x = X + (size_t)cand * kR * w + col;
+  const bf16* xl = Xlo ? Xlo + (size_t)cand * kR * w + col : nullptr;
   float s = 0.f;
-  for (int r = 0; r < k; ++r) s += __bfloat162float(x[(size_t)r * w]);
+  for (int r = 0; r < k; ++r) s += __bfloat162float(x[(size_t)r * w]) + (xl ? __bfloat162float(xl[(size_t)r * w]) : 0.f);
   s *= scale;
   outf[(size_t)cand * w + col] = s;
   if (outb) outb[(size_t)cand * w + col] = __float2bfloat16_rn(s);
@@ -261,7 +301,8 @@ struct EpiPartial {  // split-K slice z: part[z][row][col] = acc
 };
 
 struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optional head dot
-  bf16* H;  // may be null (scoring the last layer)
+  bf16* H;    // may be null (scoring the last layer)
+  bf16* Hlo;  // lo part (training) or null
   int M, kv;
   const float* G;
   const float* wh;
@@ -293,6 +334,20 @@ struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optiona
       uint4* dst = reinterpret_cast<uint4*>(H + (size_t)row * kD + col0);
       dst[0] = pk[0];
       dst[1] = pk[1];
+      if (Hlo) {
+        const bf16* hb = reinterpret_cast<const bf16*>(pk);
+        uint4 lk[2];
+        uint32_t* q = reinterpret_cast<uint32_t*>(lk);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const __nv_bfloat162 b2 =
+              __floats2bfloat162_rn(h[2 * i] - __bfloat162float(hb[2 * i]), h[2 * i + 1] - __bfloat162float(hb[2 * i + 1]));
+          q[i] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        uint4* dl = reinterpret_cast<uint4*>(Hlo + (size_t)row * kD + col0);
+        dl[0] = lk[0];
+        dl[1] = lk[1];
+      }
     }
   }
   __device__ void finish(int row) const {
@@ -554,28 +609,46 @@ dlm_status make_map_bf16(dlm_ctx* ctx, CUtensorMap* map, const void* base, uint6
 }
 }  // namespace tc
 
-// C[M][N] = A[M][K] . B[N][K]^T through the tcgen05 kernel; kc = 64-wide K chunks per CTA
+// C[M][N] = (A + A2)[M][K] . (B + B2)[N][K]^T through the tcgen05 kernel, A2 / B2 the lo parts
+// of split operands (or null); kc = 64-wide K chunks per CTA (split-K along grid z)
 template <int BN, class Epi>
-static dlm_status gemm(dlm_ctx* ctx, const bf16* A, int M, int K, int lda, const bf16* B, int N, int ldb, int kc, Epi epi) {
-  constexpr int STAGES = 4;
+static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K, int lda, const bf16* B, const bf16* B2,
+                       int N, int ldb, int kc, Epi epi) {
   if (M <= 0) return DLM_OK;
   if (K % tc::BK || N % BN) return fail(ctx, DLM_EINVAL, "gemm: K must be a multiple of 64 and N of the tile");
-  CUtensorMap ma, mb;
+  CUtensorMap ma, ma2, mb, mb2;
   DLM_TRY(tc::make_map_bf16(ctx, &ma, A, (uint64_t)M, (uint64_t)K, (uint64_t)lda, tc::BM));
   DLM_TRY(tc::make_map_bf16(ctx, &mb, B, (uint64_t)N, (uint64_t)K, (uint64_t)ldb, BN));
-  auto kfn = tc::gemm_kernel<BN, STAGES, Epi>;
-  constexpr size_t smem = tc::gemm_smem_bytes<BN, STAGES>();
-  static bool attr = false;
-  if (!attr) {
-    DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  if (A2) DLM_TRY(tc::make_map_bf16(ctx, &ma2, A2, (uint64_t)M, (uint64_t)K, (uint64_t)lda, tc::BM));
+  else ma2 = ma;
+  if (B2) DLM_TRY(tc::make_map_bf16(ctx, &mb2, B2, (uint64_t)N, (uint64_t)K, (uint64_t)ldb, BN));
+  else mb2 = mb;
   const int nchunks = K / tc::BK;
   if (kc <= 0) kc = nchunks;
   tc::GemmShape sh{M, N, K, kc};
   dim3 grid((M + tc::BM - 1) / tc::BM, N / BN, (nchunks + kc - 1) / kc);
-  kfn<<<grid, tc::kThreads, smem, ctx->stream>>>(ma, mb, sh, epi, ctx->d_status);
-  return launch_check(ctx, "gemm_kernel");
+  auto launch = [&](auto kfn, size_t smem, bool& attr) -> dlm_status {
+    if (!attr) {
+      DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+    kfn<<<grid, tc::kThreads, smem, ctx->stream>>>(ma, ma2, mb, mb2, sh, epi, ctx->d_status);
+    return launch_check(ctx, "gemm_kernel");
+  };
+  if (A2 && B2) {
+    static bool attr = false;
+    return launch(tc::gemm_kernel<BN, 2, 2, 2, Epi>, tc::gemm_smem_bytes<BN, 2, 2, 2>(), attr);
+  }
+  if (A2) {
+    static bool attr = false;
+    return launch(tc::gemm_kernel<BN, 2, 2, 1, Epi>, tc::gemm_smem_bytes<BN, 2, 2, 1>(), attr);
+  }
+  if (B2) {
+    static bool attr = false;
+    return launch(tc::gemm_kernel<BN, 2, 1, 2, Epi>, tc::gemm_smem_bytes<BN, 2, 1, 2>(), attr);
+  }
+  static bool attr = false;
+  return launch(tc::gemm_kernel<BN, 4, 1, 1, Epi>, tc::gemm_smem_bytes<BN, 4, 1, 1>(), attr);
 }
 
 template <typename T>
@@ -599,7 +672,8 @@ static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
     a.ogam[l] = s->ogam[l];
     a.LamT[l] = s->LamT[l];
     a.Lam[l] = s->Lam[l];
-    a.GamT[l] = s->GamT[l];
+    a.LamTlo[l] = s->LamTlo[l];
+    a.Lamlo[l] = s->Lamlo[l];
     tot += (int64_t)din_of(l) * kD;
   }
   k_convert<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(a);
@@ -609,30 +683,25 @@ static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
 static size_t pool_smem(int n) { return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + (64 + 65 + 64) * 4 + 8 * 64 * 4 + 64; }
 
 // forward over c candidates with the given buffers; train = keep every activation (and H3)
-static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int c, float* out, bf16** H, bf16** Mb,
-                          float** Mf, float** G, float* rowdot, bool train) {
+static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int c, float* out, bf16** H, bf16** Hlo,
+                          bf16** Mb, float** Mf, float** G, float* rowdot, bool train) {
   const int rows = c * kR;
-  const size_t psm = pool_smem(s->n);
-  static bool attr = false;
-  if (!attr) {
-    DLM_CUDA(ctx, cudaFuncSetAttribute(k_pool, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-    attr = true;
-  }
+  const size_t psm = pool_smem(s->n);  // < 10 KB for n <= 2048
   const int pgrid = std::min(c, ctx->num_sms * 4);
-  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, cols, c, s->E16, s->theta + s->ob0, H[0], Mf[0], Mb[0],
-                                           ctx->d_status);
+  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, cols, c, s->theta + s->oE, s->theta + s->ob0, H[0],
+                                           Hlo ? Hlo[0] : nullptr, Mf[0], Mb[0], ctx->d_status);
   DLM_TRY(launch_check(ctx, "k_pool"));
   for (int l = 1; l <= kNL; ++l) {
     const int din = din_of(l);
-    // per-candidate term rho(H_{l-1}) Gamma_l + beta_l (tensor cores, M = c)
-    DLM_TRY(gemm<256>(ctx, Mb[l - 1], c, din, din, s->GamT[l], kD, din, 0,
-                      EpiPlain{G[l], kD, c, 1.f, s->theta + s->ob[l]}));
+    // per-candidate term rho(H_{l-1}) Gamma_l + beta_l (FP32, CUDA cores)
+    k_gterm<<<(c + kGTile - 1) / kGTile, 256, 0, ctx->stream>>>(c, din, Mf[l - 1], s->theta, s->ogam[l], s->ob[l], G[l]);
+    DLM_TRY(launch_check(ctx, "k_gterm"));
     const bool last = l == kNL;
-    EpiLayer e{(last && !train) ? nullptr : H[l], rows, s->k, G[l], last ? s->theta + s->owh : nullptr,
-               last ? rowdot : nullptr, 0.f};
-    DLM_TRY(gemm<256>(ctx, H[l - 1], rows, din, din, s->LamT[l], kD, din, 0, e));
+    EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, G[l],
+               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f};
+    DLM_TRY(gemm<256>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din, 0, e));
     if (!last || train) {
-      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], kD, s->k, 1.f / s->k, Mf[l], Mb[l]);
+      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, 1.f / s->k, Mf[l], Mb[l]);
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
@@ -642,7 +711,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
 
 // forward + backward of one batch; gradient into s->grad (overwritten), predictions into outb
 static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const float* y, int B) {
-  DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Mbb, s->Mfb, s->Gbf, s->rowdotb, true));
+  DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mfb, s->Gbf, s->rowdotb, true));
   const int rows = B * kR;
   k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, s->dout, s->lossd);
   DLM_TRY(launch_check(ctx, "k_loss"));
@@ -652,16 +721,17 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
   for (int l = kNL; l >= 1; --l) {
     const int din = din_of(l);
     // column sums of dZ_l per candidate (valid rows are the only nonzero ones)
-    k_segment_reduce<<<B, kD, 0, ctx->stream>>>(s->dZ[l], kD, s->k, 1.f, s->S[l], nullptr);
+    k_segment_reduce<<<B, kD, 0, ctx->stream>>>(s->dZ[l], nullptr, kD, s->k, 1.f, s->S[l], nullptr);
     DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     // transposes for the weight-gradient GEMM
     dim3 tb(32, 8);
     k_transpose<<<dim3(kD / 32, (rows + 31) / 32), tb, 0, ctx->stream>>>(s->dZ[l], rows, kD, s->dZT[l]);
     k_transpose<<<dim3(din / 32, (rows + 31) / 32), tb, 0, ctx->stream>>>(s->Hb[l - 1], rows, din, s->HT[l - 1]);
+    k_transpose<<<dim3(din / 32, (rows + 31) / 32), tb, 0, ctx->stream>>>(s->Hblo[l - 1], rows, din, s->HTlo[l - 1]);
     DLM_TRY(launch_check(ctx, "k_transpose"));
     // dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction)
     const int nchunks = rows / tc::BK, kc = 4, splits = (nchunks + kc - 1) / kc;
-    DLM_TRY(gemm<256>(ctx, s->HT[l - 1], din, rows, rows, s->dZT[l], kD, rows, kc,
+    DLM_TRY(gemm<256>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc,
                       EpiPartial{s->part, kD, din, (size_t)din * kD}));
     const int64_t cnt = (int64_t)din * kD;
     k_reduce_splits<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, splits, s->part, s->grad + s->olam[l]);
@@ -672,10 +742,10 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
     DLM_TRY(launch_check(ctx, "k_gb"));
     // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
     EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->Gb, s->Hb[l - 1]};
-    if (din == kD) DLM_TRY(gemm<256>(ctx, s->dZ[l], rows, kD, kD, s->Lam[l], din, kD, 0, e));
-    else DLM_TRY(gemm<64>(ctx, s->dZ[l], rows, kD, kD, s->Lam[l], din, kD, 0, e));
+    if (din == kD) DLM_TRY(gemm<256>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e));
+    else DLM_TRY(gemm<64>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e));
   }
-  k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], kD0, s->k, 1.f, s->S[0], nullptr);
+  k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, 1.f, s->S[0], nullptr);
   k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, cols, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
   return launch_check(ctx, "k_demb");
 }
@@ -687,7 +757,9 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
   for (int l = 0; l <= kNL; ++l) {
     const int w = l == 0 ? kD0 : kD;
     DLM_TRY(dalloc(ctx, &s->Hb[l], (size_t)rows * w));
+    DLM_TRY(dalloc(ctx, &s->Hblo[l], (size_t)rows * w));
     DLM_TRY(dalloc(ctx, &s->HT[l], (size_t)rows * w));
+    DLM_TRY(dalloc(ctx, &s->HTlo[l], (size_t)rows * w));
     DLM_TRY(dalloc(ctx, &s->Mbb[l], (size_t)cpad * w));
     DLM_TRY(dalloc(ctx, &s->Mfb[l], (size_t)cb * w));
     DLM_TRY(dalloc(ctx, &s->Gbf[l], (size_t)cb * kD));
@@ -739,9 +811,9 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
   if (!s) return;
   cudaFree(s->theta); cudaFree(s->am); cudaFree(s->av); cudaFree(s->grad); cudaFree(s->E16);
   for (int l = 0; l <= kNL; ++l) {
-    cudaFree(s->LamT[l]); cudaFree(s->Lam[l]); cudaFree(s->GamT[l]);
+    cudaFree(s->LamT[l]); cudaFree(s->Lam[l]); cudaFree(s->LamTlo[l]); cudaFree(s->Lamlo[l]);
     cudaFree(s->H[l]); cudaFree(s->Mb[l]); cudaFree(s->Mf[l]); cudaFree(s->G[l]);
-    cudaFree(s->Hb[l]); cudaFree(s->HT[l]); cudaFree(s->Mbb[l]); cudaFree(s->Mfb[l]); cudaFree(s->Gbf[l]);
+    cudaFree(s->Hb[l]); cudaFree(s->Hblo[l]); cudaFree(s->HT[l]); cudaFree(s->HTlo[l]); cudaFree(s->Mbb[l]); cudaFree(s->Mfb[l]); cudaFree(s->Gbf[l]);
     cudaFree(s->dZ[l]); cudaFree(s->dZT[l]); cudaFree(s->S[l]);
   }
   cudaFree(s->rowdot); cudaFree(s->Gb); cudaFree(s->part); cudaFree(s->rowdotb); cudaFree(s->outb); cudaFree(s->dout);
@@ -772,7 +844,8 @@ extern "C" dlm_status dlm_scorer_create(dlm_ctx* ctx, int32_t n, int32_t k, uint
   auto A = [&](auto** p, size_t cnt) { if (st == DLM_OK) st = dalloc(ctx, p, cnt); };
   A(&s->theta, o); A(&s->am, o); A(&s->av, o); A(&s->grad, o); A(&s->E16, (size_t)n * kD0);
   for (int l = 1; l <= kNL; ++l) {
-    A(&s->LamT[l], (size_t)din_of(l) * kD); A(&s->Lam[l], (size_t)din_of(l) * kD); A(&s->GamT[l], (size_t)din_of(l) * kD);
+    A(&s->LamT[l], (size_t)din_of(l) * kD); A(&s->Lam[l], (size_t)din_of(l) * kD);
+    A(&s->LamTlo[l], (size_t)din_of(l) * kD); A(&s->Lamlo[l], (size_t)din_of(l) * kD);
   }
   if (st != DLM_OK) { dlm_scorer_destroy(s); return st; }
   // uniform +-1/sqrt(fan_in) per parameter block (fan_in of E and b0: n)
@@ -835,7 +908,7 @@ extern "C" dlm_status dlm_score_offspring(dlm_ctx* ctx, dlm_scorer* s, const int
   DLM_TRY(ensure_fwd_buffers(ctx, s));
   for (int c0 = 0; c0 < c; c0 += s->cap) {
     const int cc = std::min(s->cap, c - c0);
-    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, out + c0, s->H, s->Mb, s->Mf, s->G, s->rowdot, false));
+    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, out + c0, s->H, nullptr, s->Mb, s->Mf, s->G, s->rowdot, false));
   }
   return DLM_OK;
 }
@@ -894,6 +967,6 @@ extern "C" dlm_status dlm_gemm_bf16(dlm_ctx* ctx, const void* A, const void* B, 
   if (!ctx || !A || !B || !C) return fail(ctx, DLM_EINVAL, "gemm_bf16: null argument");
   if (M < 1 || N < 64 || K < 64 || K % 64 || N % 64) return fail(ctx, DLM_EINVAL, "gemm_bf16: need K, N multiples of 64");
   if (N % 256 == 0)
-    return gemm<256>(ctx, (const bf16*)A, M, K, K, (const bf16*)B, N, K, 0, EpiPlain{C, N, M, 1.f, nullptr});
-  return gemm<64>(ctx, (const bf16*)A, M, K, K, (const bf16*)B, N, K, 0, EpiPlain{C, N, M, 1.f, nullptr});
+    return gemm<256>(ctx, (const bf16*)A, nullptr, M, K, K, (const bf16*)B, nullptr, N, K, 0, EpiPlain{C, N, M, 1.f, nullptr});
+  return gemm<64>(ctx, (const bf16*)A, nullptr, M, K, K, (const bf16*)B, nullptr, N, K, 0, EpiPlain{C, N, M, 1.f, nullptr});
 }

@@ -111,18 +111,23 @@ struct GemmShape {
 };
 
 // Epilogue functors receive (row, col0, v[16]) for 16 consecutive output columns of one row.
-template <int BN, int STAGES, class Epi>
+// NA / NB = 2: the operand is given as two bf16 matrices, the hi and lo parts of an fp32 matrix
+// (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); every K step then issues hi.hi, and hi.lo /
+// lo.hi, into the same accumulator, so the split operand keeps about 16 mantissa bits.
+template <int BN, int STAGES, int NA, int NB, class Epi>
 __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                          const __grid_constant__ CUtensorMap mapB, GemmShape sh,
+                                                          const __grid_constant__ CUtensorMap mapA2,
+                                                          const __grid_constant__ CUtensorMap mapB,
+                                                          const __grid_constant__ CUtensorMap mapB2, GemmShape sh,
                                                           Epi epi, int32_t* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzle atoms
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int A_BYTES = BM * BK * 2;
   constexpr int B_BYTES = BN * BK * 2;
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* full = (uint64_t*)(sB + STAGES * B_BYTES);
+  uint8_t* sA = smem;                          // [STAGES][NA][A_BYTES]
+  uint8_t* sB = smem + STAGES * NA * A_BYTES;  // [STAGES][NB][B_BYTES]
+  uint64_t* full = (uint64_t*)(sB + STAGES * NB * B_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
@@ -157,9 +162,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       for (int i = 0; i < nk; ++i) {
         const int s = i % STAGES;
         if (i >= STAGES && !mbar_wait(empty + s, ((i / STAGES) - 1) & 1)) { *abort_flag = 1; break; }
-        mbar_expect_tx(full + s, A_BYTES + B_BYTES);
-        tma_load_2d(sA + s * A_BYTES, &mapA, (kc0 + i) * BK, m0, full + s);
-        tma_load_2d(sB + s * B_BYTES, &mapB, (kc0 + i) * BK, n0, full + s);
+        mbar_expect_tx(full + s, NA * A_BYTES + NB * B_BYTES);
+        tma_load_2d(sA + (s * NA) * A_BYTES, &mapA, (kc0 + i) * BK, m0, full + s);
+        if (NA == 2) tma_load_2d(sA + (s * NA + 1) * A_BYTES, &mapA2, (kc0 + i) * BK, m0, full + s);
+        tma_load_2d(sB + (s * NB) * B_BYTES, &mapB, (kc0 + i) * BK, n0, full + s);
+        if (NB == 2) tma_load_2d(sB + (s * NB + 1) * B_BYTES, &mapB2, (kc0 + i) * BK, n0, full + s);
       }
     } else if (warp == 1 && lane == 0) {
       // ---- MMA issuer ----
@@ -169,10 +176,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         const int s = i % STAGES;
         if (!mbar_wait(full + s, (i / STAGES) & 1)) { ok = false; break; }
         fence_after_sync();
-        const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+        const uint32_t a0 = smem_u32(sA + (s * NA) * A_BYTES), b0 = smem_u32(sB + (s * NB) * B_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk)
+        for (int kk = 0; kk < BK / 16; ++kk) {
           mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          if (NB == 2) mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + B_BYTES + kk * 32), idesc, 1u);
+          if (NA == 2) mma_bf16(tmem, sw128_desc(a0 + A_BYTES + kk * 32), sw128_desc(b0 + kk * 32), idesc, 1u);
+        }
         mma_commit(empty + s);
       }
       if (!ok) *abort_flag = 1;
@@ -213,9 +223,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   }
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int NA, int NB>
 constexpr size_t gemm_smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + (2 * STAGES + 1) * 8 + 16;
+  return 1024 + (size_t)STAGES * (NA * BM * BK * 2 + NB * BN * BK * 2) + (2 * STAGES + 1) * 8 + 16;
 }
 
 // host: 2-D bf16 tensor map over a row-major [rows][cols] matrix with leading dimension ld
