@@ -1,0 +1,68 @@
+"""GPU parity of the uneven multi-graph persistent TabuCol launch: every individual equals the
+single-graph launch with the same Philox stream, and sampled individuals equal the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_05948_gb300 import dlmcol, inputs
+
+from gpu_util import device_graph, oracle_tabu_many
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2109_05948_gb300 import build
+
+    build.build()
+    c = dlmcol.Context(0)
+    yield c
+    c.close()
+
+
+def _batch(num_graphs, seed, n_hi, pop):
+    specs = inputs.uneven_batch(num_graphs, seed=seed, n_lo=100, n_hi=n_hi)
+    return specs, [pop] * num_graphs
+
+
+def test_multi_matches_single_graph_launches_and_oracle(ctx):
+    specs, pops = _batch(12, seed=3, n_hi=500, pop=6)
+    graphs = [device_graph(ctx, s["n"], s["edges"]) for s in specs]
+    ks = [s["k"] for s in specs]
+    iters = [16 * s["n"] for s in specs]  # a shortened depth (the paper uses 128 |V|)
+    starts = [oracle.init_colors(s["n"], k, p, 5, ind_base=sum(pops[:g])) for g, (s, k, p) in enumerate(zip(specs, ks, pops))]
+    cols = [torch.from_numpy(st.copy()).cuda() for st in starts]
+    bfs = [torch.zeros(p, dtype=torch.int64, device="cuda") for p in pops]
+    mvs = [torch.zeros(p, dtype=torch.int64, device="cuda") for p in pops]
+    dlmcol.dlm_tabucol_multi(ctx, graphs, ks, pops, cols, bfs, mvs, iters, dlmcol.COL_TENURE, 5, 1, 0)
+    ctx.sync()
+    base = 0
+    jobs = []
+    for g, (s, k, p) in enumerate(zip(specs, ks, pops)):
+        col1 = torch.from_numpy(starts[g].copy()).cuda()
+        bf1 = torch.zeros(p, dtype=torch.int64, device="cuda")
+        mv1 = torch.zeros(p, dtype=torch.int64, device="cuda")
+        dlmcol.dlm_tabucol_batch(ctx, graphs[g], k, p, col1, bf1, mv1, iters[g], dlmcol.COL_TENURE, 5, 1, base)
+        ctx.sync()
+        assert torch.equal(col1, cols[g]) and torch.equal(bf1, bfs[g]) and torch.equal(mv1, mvs[g]), g
+        adj = inputs.edges_to_adj(s["n"], s["edges"])
+        jobs.append((adj, k, starts[g][0], iters[g], 5, base, 1, False))
+        base += p
+    refs = oracle_tabu_many(jobs)
+    for g, r in enumerate(refs):
+        assert bfs[g][0].item() == r["best_f"] and mvs[g][0].item() == r["moves"]
+        assert np.array_equal(cols[g][0].cpu().numpy(), r["best_col"])
+
+
+def test_multi_rejects_bad_arguments(ctx):
+    specs, pops = _batch(2, seed=1, n_hi=200, pop=2)
+    graphs = [device_graph(ctx, s["n"], s["edges"]) for s in specs]
+    cols = [torch.zeros((2, s["n"]), dtype=torch.int16, device="cuda") for s in specs]
+    bfs = [torch.zeros(2, dtype=torch.int64, device="cuda") for _ in specs]
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_tabucol_multi(ctx, graphs, [300, 10], pops, cols, bfs, None, [10, 10])
