@@ -134,6 +134,24 @@ dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dlm_graph* co
                              int64_t* const* moves, const int64_t* iters, dlm_tenure tenure, uint64_t seed,
                              uint32_t generation, uint32_t ind_base);
 
+/* dlm_tabucol_multi without any device allocation. The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory -- code on a latency-critical path where
+ * cudaMalloc's implicit device synchronisation is unacceptable, or a process whose device memory
+ * is owned by another allocator (a framework's caching allocator, a fixed memory budget), where a
+ * raw cudaMalloc may fail or fragment the pool. The job list and the work queue of the persistent
+ * kernel live in a file-scope device array of the library (1 MiB plus 256 bytes, held on every GPU
+ * that loads the library until the process exits) instead of the context's workspace.
+ * Arguments and results are those of dlm_tabucol_multi. Limit: at most 16384 individuals in total
+ * per call (DLM_EUNSUPPORTED above, nothing launched). The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. All calls share the one array, which keeps the last call's contents:
+ * the queue counter is cleared by every call, and calls that overlap on the GPU (other streams or
+ * other contexts on the same device) race on it -- serialise them. */
+dlm_status dlm_tabucol_multi_noalloc(dlm_ctx* ctx, int32_t n_graphs, const dlm_graph* const* graphs, const int32_t* k,
+                                     const int32_t* pop, int16_t* const* col, int64_t* const* best_f,
+                                     int64_t* const* moves, const int64_t* iters, dlm_tenure tenure, uint64_t seed,
+                                     uint32_t generation, uint32_t ind_base);
+
 /* Autotuner for the tabu kernel: times warps_per_individual in {1, 2, 4, 8} on a short run of
  * the given problem and caches the fastest for (n, k) in the context; returns it in *best. */
 dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,

@@ -22,6 +22,7 @@
 //  Four CTA barriers per iteration.
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -696,4 +697,111 @@ extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dl
     default: st = go(tabucol_multi_kernel<8>); break;
   }
   return st;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free variant of the uneven-batch launch. Its scratch (the job list and the queue
+// counter of the persistent kernel) lives in a file-scope device array instead of the context's
+// workspace, so the call never allocates device memory.
+// ------------------------------------------------------------------------------------------------
+namespace dlm {
+
+constexpr int kNoAllocMaxJobs = 16384;
+constexpr size_t kNoAllocJobBytes = (size_t)kNoAllocMaxJobs * sizeof(MultiJob);
+constexpr size_t kNoAllocScratchBytes = kNoAllocJobBytes + 256;  // job list, then the queue counter
+
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once with that device current (in
+// host code the symbol itself is only a host-side stand-in, not a device address).
+static void* g_noalloc_addr[128];
+static std::mutex g_noalloc_mu;
+
+static dlm_status noalloc_scratch(dlm_ctx* ctx, uint8_t** out) {
+  if (ctx->device < 0 || ctx->device >= 128) return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi_noalloc: device index");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[ctx->device]) {
+    int cur = -1;
+    DLM_CUDA(ctx, cudaGetDevice(&cur));
+    if (cur != ctx->device) DLM_CUDA(ctx, cudaSetDevice(ctx->device));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (cur != ctx->device) cudaSetDevice(cur);
+    if (e != cudaSuccess || !p) return cuda_check(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+    g_noalloc_addr[ctx->device] = p;
+  }
+  *out = (uint8_t*)g_noalloc_addr[ctx->device];
+  return DLM_OK;
+}
+
+}  // namespace dlm
+
+extern "C" dlm_status dlm_tabucol_multi_noalloc(dlm_ctx* ctx, int32_t n_graphs, const dlm_graph* const* graphs,
+                                                const int32_t* k, const int32_t* pop, int16_t* const* col,
+                                                int64_t* const* best_f, int64_t* const* moves, const int64_t* iters,
+                                                dlm_tenure tenure, uint64_t seed, uint32_t generation,
+                                                uint32_t ind_base) {
+  if (!ctx || n_graphs <= 0 || !graphs || !k || !pop || !col || !best_f || !iters)
+    return fail(ctx, DLM_EINVAL, "tabucol_multi_noalloc: bad arguments");
+  int warps = 1;
+  size_t smem = 0;
+  size_t njobs = 0;
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    DLM_TRY(tabucol_check(ctx, graphs[gi], k[gi], pop[gi], iters[gi], tenure));
+    if (pop[gi] > 0 && (!col[gi] || !best_f[gi])) return fail(ctx, DLM_EINVAL, "tabucol_multi_noalloc: null output");
+    int w = lookup_tune(ctx, graphs[gi]->n, k[gi]);
+    if (w == 0) w = default_warps(graphs[gi]->n, k[gi]);
+    warps = w > warps ? w : warps;
+    njobs += (size_t)pop[gi];
+  }
+  if (njobs > (size_t)kNoAllocMaxJobs)
+    return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi_noalloc: at most " + std::to_string(kNoAllocMaxJobs) +
+                                           " individuals per call (the static scratch array holds that many jobs)");
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    const TabuSmem L = tabu_smem_layout(graphs[gi]->n, k[gi], warps);
+    smem = L.total > smem ? L.total : smem;
+  }
+  if (smem > ctx->smem_optin)
+    return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi_noalloc: a graph's state exceeds shared memory");
+  if (njobs == 0) return DLM_OK;
+  std::vector<MultiJob> jobs;
+  jobs.reserve(njobs);
+  uint32_t id = ind_base;
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    const dlm_graph* g = graphs[gi];
+    for (int j = 0; j < pop[gi]; ++j) {
+      MultiJob M;
+      M.n = g->n; M.k = k[gi]; M.ks = tabu_row_stride(k[gi]); M.words = g->words; M.bits = g->d_bits;
+      M.col = col[gi] + (size_t)j * g->n; M.best_f = best_f[gi] + j; M.moves = moves && moves[gi] ? moves[gi] + j : nullptr;
+      M.iters = iters[gi]; M.ind = id++;
+      jobs.push_back(M);
+    }
+  }
+  std::stable_sort(jobs.begin(), jobs.end(), [](const MultiJob& a, const MultiJob& b) {
+    return (double)a.n * a.k * a.iters > (double)b.n * b.k * b.iters;
+  });
+  uint8_t* scratch = nullptr;
+  DLM_TRY(noalloc_scratch(ctx, &scratch));
+  MultiJob* d_jobs = (MultiJob*)scratch;
+  int32_t* d_queue = (int32_t*)(scratch + kNoAllocJobBytes);
+  DLM_CUDA(ctx, cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(MultiJob), cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int32_t), ctx->stream));  // the queue starts at zero
+  const TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status};
+  auto go = [&](auto kfn) -> dlm_status {
+    int per_sm = 0;
+    DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    DLM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int grid = (int)std::min<size_t>((size_t)per_sm * ctx->num_sms, jobs.size());
+    kfn<<<grid, warps * 32, smem, ctx->stream>>>(d_jobs, (int32_t)jobs.size(), d_queue, rule);
+    return launch_check(ctx, "tabucol_multi_kernel");
+  };
+  switch (warps) {
+    case 1: return go(tabucol_multi_kernel<1>);
+    case 2: return go(tabucol_multi_kernel<2>);
+    case 4: return go(tabucol_multi_kernel<4>);
+    default: return go(tabucol_multi_kernel<8>);
+  }
 }

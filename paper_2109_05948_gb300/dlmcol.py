@@ -58,6 +58,7 @@ _SIGS = {
     "dlm_tabucol_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, Tenure, _u64, _u32, _u32]),
     "dlm_tabucol_batch_ex": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, Tenure, _u64, _u32, _u32, _i32, _P, _P]),
     "dlm_tabucol_multi": (_i32, [_P, _i32, _P, _P, _P, _P, _P, _P, _P, Tenure, _u64, _u32, _u32]),
+    "dlm_tabucol_multi_noalloc": (_i32, [_P, _i32, _P, _P, _P, _P, _P, _P, _P, Tenure, _u64, _u32, _u32]),
     "dlm_tabucol_autotune": (_i32, [_P, _P, _i32, _i32, _i64, _P]),
     "dlm_gpx_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _P, _i32, _P, _u64, _u32]),
     "dlm_distance_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32]),
@@ -205,6 +206,26 @@ def dlm_tabucol_batch_ex(ctx, g, k, pop, col, best_f, moves, iters, tenure=COL_T
     ctx.check(lib().dlm_tabucol_batch_ex(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_f), _ptr(moves), iters, tenure,
                                          seed, generation, ind_base, warps, _ptr(trace), _ptr(work)),
               "dlm_tabucol_batch_ex")
+
+
+def _multi_args(graphs, ks, pops, cols, best_fs, moves, iters):
+    G = len(graphs)
+    arr_g = (ctypes.c_void_p * G)(*[g.h.value for g in graphs])
+    arr_k = (ctypes.c_int32 * G)(*ks)
+    arr_p = (ctypes.c_int32 * G)(*pops)
+    arr_c = (ctypes.c_void_p * G)(*[c.data_ptr() for c in cols])
+    arr_b = (ctypes.c_void_p * G)(*[b.data_ptr() for b in best_fs])
+    arr_m = (ctypes.c_void_p * G)(*[(m.data_ptr() if m is not None else 0) for m in moves]) if moves else None
+    arr_i = (ctypes.c_int64 * G)(*iters)
+    return G, arr_g, arr_k, arr_p, arr_c, arr_b, arr_m, arr_i
+
+
+def dlm_tabucol_multi_noalloc(ctx, graphs, ks, pops, cols, best_fs, moves, iters, tenure=COL_TENURE, seed=0,
+                              generation=0, ind_base=0):
+    """dlm_tabucol_multi for callers that must not allocate device memory (see include/dlmcol.h)."""
+    a = _multi_args(graphs, ks, pops, cols, best_fs, moves, iters)
+    ctx.check(lib().dlm_tabucol_multi_noalloc(ctx.h, *a, tenure, seed, generation, ind_base),
+              "dlm_tabucol_multi_noalloc")
 
 
 def dlm_tabucol_multi(ctx, graphs, ks, pops, cols, best_fs, moves, iters, tenure=COL_TENURE, seed=0, generation=0,
