@@ -93,7 +93,6 @@ __global__ void __launch_bounds__(kPoolThreads) k_pool_update(int p, int n, cons
   int32_t* adm = (int32_t*)(key + mp);          // [p] admitted, in order
   uint8_t* chosen = (uint8_t*)(adm + p);        // [m]
   __shared__ int cnt;
-  __shared__ int reject;
   const int t = threadIdx.x;
   for (int q = t; q < mp; q += blockDim.x) {
     if (q < m) {
@@ -124,7 +123,6 @@ __global__ void __launch_bounds__(kPoolThreads) k_pool_update(int p, int n, cons
     const int c = cnt;  // uniform (written before the last barrier)
     if (c >= p) break;
     const int x = (int)(key[s] & 0xFFFFF);
-    if (t == 0) reject = 0;
     __syncthreads();
     int bad = 0;
     const int16_t* row = D + (size_t)x * m;

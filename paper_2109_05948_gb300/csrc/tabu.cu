@@ -6,20 +6,19 @@
 //  * one CTA of W warps per individual; its whole search state lives in shared memory:
 //      gam[n][ks] u16  conflict table gamma (row stride ks u16 with ks/2 odd, so that the
 //                      scattered row updates of a warp spread over the banks)
-//      tab[n][ks] u16  tabu expiry iteration modulo 2^16 (kept within +-2^15 of the iteration
-//                      counter by a sweep every 2^14 iterations)
+//      tab[n][ks] u16  tabu expiry relative to a base that advances by 2^14 every 2^14
+//                      iterations (one sweep), so a tabu test is a single unsigned compare
 //      col[n], best[n] u8 current and best colouring; cv[] u32 bitmap of conflicting vertices;
 //      rowres[n] u32   (row minimum delta, tie count) of each conflicting row of the scan.
-//  * scan: each warp compacts the bitmap into its own list of conflicting vertices; thread t
-//    scans a contiguous block of rows (two colours per 32-bit word, no warp collectives inside a
-//    row), so threads run their rows in parallel and the order of rows follows the thread order.
-//  * selection: block minimum of delta, then a block prefix sum of the per-thread tie counts;
-//    the thread holding the j-th tied move (j drawn from the iteration's Philox block) applies it,
-//    using the tie mask of the row it scanned last.
-//  * update: the adjacency bit row of the moved vertex (prefetched into L1 during the scan) is
-//    split across all threads; each neighbour costs two u16 read-modify-writes of its gamma row
+//  * scan: each warp compacts the bitmap into its own list of conflicting vertices; rows are cut
+//    into segments so that every thread scans (two colours per 32-bit word, no warp collectives
+//    inside a segment); the order of (row, segment) items follows the thread order.
+//  * selection: per-warp minima and tie counts go through one barrier; every thread derives the
+//    block minimum, the tie total and its rank range, and the thread holding the j-th tied move
+//    (j drawn from the iteration's Philox block) finds its colour and applies the move.
+//  * update: the adjacency bit row of the moved vertex (L2 resident) is split across all threads; each neighbour costs two u16 read-modify-writes of its gamma row
 //    and, when its conflict status flips, one shared atomic on the bitmap.
-//  Four CTA barriers per iteration.
+//  Three CTA barriers per iteration.
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -73,7 +72,7 @@ __host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps) {
   s.tab = o; o += align16((size_t)n * ks * 2);
   s.col = o; o += align16(n);
   s.best = o; o += align16(n);
-  s.rowres = o; o += align16((size_t)n * 4);
+  s.rowres = o; o += align16((size_t)(n > 256 ? n : 256) * 4);
   s.deg = o; o += align16((size_t)n * 2);
   s.cvl = o; o += align16((size_t)warps * n * 2);
   s.cv = o; o += 64 * 4;
@@ -123,62 +122,59 @@ __device__ __forceinline__ CvView cv_view(const uint32_t* cv, int nwords, int la
   return c;
 }
 
-// Scan of one conflicting row v by one thread. The key of colour c is gamma[v][c] when the move
-// (v, c) is admissible (not tabu, or tabu but f + delta < best_f, i.e. gamma < thr with
-// thr = best_f - f + gamma[v][col v]) and 0xFFFF otherwise; the current colour and the padding
-// columns carry gamma = 0xFFFF. Returns the row's minimum key and the columns reaching it.
-struct RowScan {
-  unsigned kmin;
-  uint64_t m0, m1;  // colours 0..63, 64..127 reaching kmin
-};
-
-__device__ __forceinline__ RowScan scan_row(const uint16_t* gam, const uint16_t* tab, int ks, int kw, int v, int colv,
-                                            int thr, int it16) {
-  const uint32_t* g32 = (const uint32_t*)(gam + (size_t)v * ks);
-  const uint32_t* t32 = (const uint32_t*)(tab + (size_t)v * ks);
-  const int killw = colv >> 1;
-  const uint32_t killm = 0xFFFFu << (16 * (colv & 1));
-  RowScan r{0xFFFFu, 0ull, 0ull};
-  const int wlo = kw < 32 ? kw : 32;
+// Scan of words [w0, w1) of a conflicting row by one thread. The key of colour c is gamma[v][c]
+// when the move (v, c) is admissible -- not tabu (relative expiry <= itrel), or tabu but
+// f + delta < best_f, i.e. gamma < thr with thr = best_f - f + gamma[v][col v] -- and 0xFFFF
+// otherwise; the current colour (killed here) and the padding columns carry 0xFFFF. Returns the
+// segment's minimum key and how many colours reach it.
+__device__ __forceinline__ void scan_seg(const uint32_t* g32, const uint32_t* t32, int w0, int w1, int killw,
+                                         uint32_t killm, unsigned itrel, int thr, unsigned& kmin, int& cnt) {
+  unsigned km = 0xFFFFu;
+  int c = 0;
 #pragma unroll 4
-  for (int w = 0; w < wlo; ++w) {
+  for (int w = w0; w < w1; ++w) {
     uint32_t gw = g32[w];
     const uint32_t tw = t32[w];
     if (w == killw) gw |= killm;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int g = (gw >> (16 * h)) & 0xFFFF;
-      const int te = (tw >> (16 * h)) & 0xFFFF;
-      const bool tabu = (int16_t)(uint16_t)(te - it16) > 0;
-      const unsigned key = (!tabu || g < thr) ? (unsigned)g : 0xFFFFu;
-      const uint64_t bit = 1ull << (2 * w + h);
-      if (key < r.kmin) { r.kmin = key; r.m0 = 0ull; }
-      if (key == r.kmin) r.m0 |= bit;
-    }
+    const unsigned ga = gw & 0xFFFFu, gb = gw >> 16;
+    const unsigned k0 = ((tw & 0xFFFFu) <= itrel || (int)ga < thr) ? ga : 0xFFFFu;
+    const unsigned k1 = ((tw >> 16) <= itrel || (int)gb < thr) ? gb : 0xFFFFu;
+    const unsigned m = min(k0, k1);
+    const int cc = (int)(k0 == m) + (int)(k1 == m);
+    if (m < km) { km = m; c = cc; }
+    else if (m == km) c += cc;
   }
-  for (int w = 32; w < kw; ++w) {
+  kmin = km;
+  cnt = c;
+}
+
+// The jj-th (0-based) colour of words [w0, w1) whose key equals kmin, in increasing colour order.
+__device__ __forceinline__ int seg_find(const uint32_t* g32, const uint32_t* t32, int w0, int w1, int killw,
+                                        uint32_t killm, unsigned itrel, int thr, unsigned kmin, int jj) {
+  for (int w = w0; w < w1; ++w) {
     uint32_t gw = g32[w];
     const uint32_t tw = t32[w];
     if (w == killw) gw |= killm;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int g = (gw >> (16 * h)) & 0xFFFF;
-      const int te = (tw >> (16 * h)) & 0xFFFF;
-      const bool tabu = (int16_t)(uint16_t)(te - it16) > 0;
-      const unsigned key = (!tabu || g < thr) ? (unsigned)g : 0xFFFFu;
-      const uint64_t bit = 1ull << ((2 * w + h) & 63);
-      if (key < r.kmin) { r.kmin = key; r.m0 = 0ull; r.m1 = 0ull; }
-      if (key == r.kmin) r.m1 |= bit;
-    }
+    const unsigned ga = gw & 0xFFFFu, gb = gw >> 16;
+    const unsigned k0 = ((tw & 0xFFFFu) <= itrel || (int)ga < thr) ? ga : 0xFFFFu;
+    const unsigned k1 = ((tw >> 16) <= itrel || (int)gb < thr) ? gb : 0xFFFFu;
+    if (k0 == kmin) { if (jj == 0) return 2 * w; --jj; }
+    if (k1 == kmin) { if (jj == 0) return 2 * w + 1; --jj; }
   }
-  return r;
+  return -1;
 }
 
 // One individual, one CTA of W warps.
-// Per iteration: (1) every warp compacts the conflicting-vertex bitmap into its own list; thread
-// t scans rows [tC, tC + C) of that list (C = ceil(|CV| / threads)), keeping per-row (min delta,
-// #ties) and its own aggregate; (2) block min of delta; (3) block prefix of the tie counts: the
-// thread holding the j-th tie applies the move; (4) all threads update gamma on the neighbours.
+// Per iteration: (1) every warp compacts the conflicting-vertex bitmap into its own list; the rows
+// are cut into S contiguous segments (S = threads / |CV| when there are fewer rows than threads)
+// and thread t scans items [tC, tC + C) of the (row, segment) list, keeping per-item (min delta,
+// #ties) and its own aggregate; (2) one barrier publishes the per-warp minima and tie counts:
+// every thread derives the minimum delta, the total T and its own rank range, and the thread that
+// holds the j-th tie (j drawn from the iteration's Philox block) applies the move; (3) all
+// threads update gamma on the neighbours. Three barriers per iteration.
+//
+// Tabu list: u16 expiries relative to a base that advances by 2^14 every 2^14 iterations
+// (t' = expiry - base, 0 = free); a pair is tabu when t' > it - base.
 template <int W>
 __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t* smem) {
   constexpr int NT = 32 * W;
@@ -276,8 +272,8 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
 
   for (it = 0; it < J.iters; ++it) {
     if (f == 0) break;
-    const int it16 = (int)(it & 0xFFFF);
-    // ---- phase 1: conflicting-vertex list of this warp, scan of this thread's rows -----------
+    const unsigned itrel = (unsigned)(it & 0x3FFF);
+    // ---- phase 1: conflicting-vertex list of this warp, scan of this thread's items ----------
     const CvView view = cv_view(cv, nwords, lane);
     {
       uint64_t wb = view.w;
@@ -294,53 +290,57 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       const U4 r = rng(R.seed, (uint32_t)it, R.gen, J.ind, kTagTabu);
       sc[7] = (int32_t)r.x;
       sc[8] = (int32_t)r.y;
+      sc[0] = -1;
     }
-    const int C = (ncv + NT - 1) / NT;
+    const int S = (ncv >= NT || ncv == 0) ? 1 : min(kw, NT / ncv);
+    const int Lw = (kw + S - 1) / S;
+    const int items = ncv * S;
+    const int C = (items + NT - 1) / NT;
     const int i0 = tid * C;
-    const int i1 = min(i0 + C, ncv);
+    const int i1 = min(i0 + C, items);
     int tmin = INT_MAX, tcnt = 0;
-    RowScan last{0xFFFFu, 0ull, 0ull};
     for (int i = i0; i < i1; ++i) {
-      const int v = cvl[i];
-      {
-        const char* p = (const char*)(J.bits + (size_t)v * nwords);
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(p + nwords * 4 - 4));
-      }
+      const int r = i / S, sg = i - r * S;
+      const int v = cvl[r];
       const int colv = colS[v];
-      const int g0 = gam[(size_t)v * ks + colv];
-      last = scan_row(gam, tab, ks, kw, v, colv, best_f - f + g0, it16);
-      const int rc = last.kmin == 0xFFFFu ? 0 : __popcll(last.m0) + __popcll(last.m1);
-      const int dm = last.kmin == 0xFFFFu ? kNone16 : (int)last.kmin - g0;
+      const uint16_t* grow = gam + (size_t)v * ks;
+      const int g0 = grow[colv];
+      const int w0 = sg * Lw, w1 = min(w0 + Lw, kw);
+      unsigned km;
+      int kc;
+      scan_seg((const uint32_t*)grow, (const uint32_t*)(tab + (size_t)v * ks), w0, w1, colv >> 1,
+               0xFFFFu << (16 * (colv & 1)), itrel, best_f - f + g0, km, kc);
+      const int rc = km == 0xFFFFu ? 0 : kc;
+      const int dm = km == 0xFFFFu ? kNone16 : (int)km - g0;
       rowres[i] = ((uint32_t)(uint16_t)dm << 16) | (uint32_t)rc;
       if (rc > 0) {
         if (dm < tmin) { tmin = dm; tcnt = rc; }
         else if (dm == tmin) tcnt += rc;
       }
     }
-    const int wm = __reduce_min_sync(FULL, tmin);
-    if (lane == 0) red[warp] = wm;
+    {
+      const int wm = __reduce_min_sync(FULL, tmin);
+      const int wc = (int)__reduce_add_sync(FULL, (wm != INT_MAX && tmin == wm) ? (unsigned)tcnt : 0u);
+      if (lane == 0) { red[warp] = wm; red[W + warp] = wc; }
+    }
     __syncthreads();
     // ---- phase 2: minimum delta, tie ranks, move ---------------------------------------------
     int dstar = INT_MAX;
 #pragma unroll
     for (int w = 0; w < W; ++w) dstar = min(dstar, red[w]);
+    int T = 0, pre = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const int x = (dstar != INT_MAX && red[w] == dstar) ? red[W + w] : 0;
+      T += x;
+      pre += w < warp ? x : 0;
+    }
     const int ct = (dstar != INT_MAX && tmin == dstar) ? tcnt : 0;
     int incl = ct;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int t = __shfl_up_sync(FULL, incl, d);
       if (lane >= d) incl += t;
-    }
-    if (lane == 31) red[W + warp] = incl;
-    if (tid == 0) sc[0] = -1;
-    __syncthreads();
-    int T = 0, pre = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-      const int x = red[W + w];
-      T += x;
-      pre += w < warp ? x : 0;
     }
     if (T > 0 && ct > 0) {
       const uint32_t j = below((uint32_t)sc[7], (uint32_t)T);
@@ -353,13 +353,15 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           const int rm = (int16_t)(rr >> 16), rcn = (int)(rr & 0xFFFF);
           if (rm != dstar || rcn == 0) continue;
           if (jj >= rcn) { jj -= rcn; continue; }
-          const int v = cvl[i];
+          const int r = i / S, sg = i - r * S;
+          const int v = cvl[r];
           const int colv = colS[v];
-          RowScan rs = last;
-          if (i != i1 - 1) rs = scan_row(gam, tab, ks, kw, v, colv, best_f - f + gam[(size_t)v * ks + colv], it16);
-          const int p0 = __popcll(rs.m0);
+          const uint16_t* grow = gam + (size_t)v * ks;
+          const int g0 = grow[colv];
+          const int w0 = sg * Lw, w1 = min(w0 + Lw, kw);
           mv = v;
-          mc = jj < p0 ? nth_set_bit64(rs.m0, jj) : 64 + nth_set_bit64(rs.m1, jj - p0);
+          mc = seg_find((const uint32_t*)grow, (const uint32_t*)(tab + (size_t)v * ks), w0, w1, colv >> 1,
+                        0xFFFFu << (16 * (colv & 1)), itrel, best_f - f + g0, (unsigned)(dstar + g0), jj);
           break;
         }
         if (mv >= 0 && mc >= 0 && mc < k) {
@@ -368,7 +370,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           const int fn = f + dstar;
           const int64_t tt = (int64_t)below((uint32_t)sc[8], R.L1) + ((int64_t)R.an * fn) / R.ad;
           if (tt > 32766) sc[5] = 1;
-          tab[(size_t)mv * ks + old] = (uint16_t)((it + 1 + tt) & 0xFFFF);
+          tab[(size_t)mv * ks + old] = (uint16_t)(itrel + 1 + tt);
           const uint32_t bit = 1u << (mv & 31);
           if (gam[(size_t)mv * ks + mc] > 0) atomicOr(cv + (mv >> 5), bit);
           else atomicAnd(cv + (mv >> 5), ~bit);
@@ -413,15 +415,12 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       }
     }
     if (((it + 1) & 0x3FFF) == 0) {
-      // keep every expiry within 2^15 of the counter: expired entries are reset to "now"
-      const uint32_t now = (uint32_t)((it + 1) & 0xFFFF);
+      // the base advances by 2^14: relative expiries drop by 2^14, expired ones become 0
       uint32_t* t32 = (uint32_t*)tab;
       for (int i = tid; i < n * kw; i += NT) {
-        uint32_t w = t32[i];
-        uint32_t lo = w & 0xFFFF, hi = w >> 16;
-        if ((int16_t)(uint16_t)(lo - now) <= 0) lo = now;
-        if ((int16_t)(uint16_t)(hi - now) <= 0) hi = now;
-        t32[i] = lo | (hi << 16);
+        const uint32_t w = t32[i];
+        const uint32_t lo = w & 0xFFFF, hi = w >> 16;
+        t32[i] = (lo > 0x4000u ? lo - 0x4000u : 0u) | ((hi > 0x4000u ? hi - 0x4000u : 0u) << 16);
       }
     }
     __syncthreads();
@@ -522,9 +521,9 @@ static int lookup_tune(const dlm_ctx* ctx, int n, int k) {
 // default when not tuned: enough threads to cover a row scan and a neighbour update in few steps
 static int default_warps(int n, int k) {
   (void)k;
-  if (n <= 160) return 1;
-  if (n <= 400) return 2;
-  return 4;
+  if (n <= 128) return 2;
+  if (n <= 300) return 4;
+  return 8;
 }
 
 static dlm_status tabucol_check(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,
