@@ -252,6 +252,42 @@ dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, void* d
 dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const void* src);
 
 /* ---------------------------------------------------------------------------------------------
+ * Weighted vertex colouring (WVCP; Eq. score_WVCP: f(S) = sum over classes of the largest vertex
+ * weight in the class). The graph must carry vertex weights (1..255).
+ *
+ * dlm_wvcp_greedy: randomised greedy initialisation (section "Initialization with a greedy random
+ * algorithm"). Vertices are visited by decreasing weight, then decreasing degree, then increasing
+ * index; vertex number pos of that order takes the colour at index high word of r0 * m among the
+ * m already-opened colours (ascending) that none of its coloured neighbours uses, with
+ * r = Philox(a = pos, b = 0, c = ind_base + i, tag = WINIT), or opens a new colour when m = 0.
+ *   col   device [pop][n] int16 out;  used  device [pop] int32 out (colours opened) or NULL.
+ * More than 255 colours raises DLM_EUNSUPPORTED at dlm_sync. This call waits for its kernel.
+ *
+ * dlm_wvcp_tabu_batch: feasible and infeasible tabu search with a fixed penalty phi (section
+ * "Parallel iterated feasible and infeasible Tabu Search", Eq. AFISA_score; Algorithm 2 with its
+ * last-run setting phi = 2 max w). It minimises g = f + phi * c, c the conflicting edges, over all
+ * one-moves (v, c') of all vertices. A vertex that moves is frozen for
+ * tt = U{0..L_max} + floor(alpha_num * n / alpha_den) iterations (Table params-WVCP: alpha = 0.2);
+ * a move of a frozen vertex is admissible only when g + delta < best g of the run. Iteration it
+ * draws r = Philox(a = it, b = generation, c = ind_base + i, tag = TABU); ties: the j-th admissible
+ * minimum in (v, c') order, j = high word of r0 * (number of ties); U{0..L_max} from r1.
+ *   col      device [pop][n] int16: in start colourings (0..k-1), out the best-g colouring visited
+ *   best_g   device [pop] int64 out;  best_fc  device [pop][2] int64 out (f, c of it) or NULL
+ *   moves    device [pop] int64 out or NULL;  iters  iterations per individual (paper: 10 |V|)
+ * Limits: k <= 255; phi * (max degree + 1) < 2^30; tenure < 2^14. */
+dlm_status dlm_wvcp_greedy(dlm_ctx* ctx, const dlm_graph* g, int32_t pop, uint64_t seed, uint32_t ind_base,
+                           int16_t* col, int32_t* used);
+dlm_status dlm_wvcp_tabu_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                               int64_t* best_g, int64_t* best_fc, int64_t* moves, int64_t iters, dlm_tenure tenure,
+                               int64_t phi, uint64_t seed, uint32_t generation, uint32_t ind_base);
+/* As dlm_wvcp_tabu_batch with a per-iteration trace: device [pop][iters][4] int32 of
+ * (v, c', delta, #ties), (-1, -1, 0, 0) for an iteration without a move. */
+dlm_status dlm_wvcp_tabu_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                  int64_t* best_g, int64_t* best_fc, int64_t* moves, int64_t iters,
+                                  dlm_tenure tenure, int64_t phi, uint64_t seed, uint32_t generation,
+                                  uint32_t ind_base, int32_t* trace);
+
+/* ---------------------------------------------------------------------------------------------
  * Building block of the scorer, exported for testing: C = A . B^T on the tcgen05 tensor cores.
  * A: device [M][K] bf16 row-major, B: device [N][K] bf16 row-major, C: device [M][N] float32.
  * K must be a multiple of 64 and N a multiple of 64; FP32 accumulation.

@@ -1,0 +1,531 @@
+// Weighted vertex colouring (WVCP): randomised greedy initialisation (section "Initialization with
+// a greedy random algorithm") and the feasible/infeasible tabu search on the penalised objective
+// g = f + phi * c (section "Parallel iterated feasible and infeasible Tabu Search", Eq.
+// AFISA_score, Eq. score_WVCP), run on every individual of a population.
+//
+// GB300 design of the tabu search (one CTA per individual, persistent over the population):
+//  * every one-move (v, c) of every vertex is evaluated each iteration (n * k pairs, ~115 000 at
+//    n = 1000): delta = rem(v) + max(0, w_v - max1[c]) + phi (gamma[v][c] - gamma[v][col v]),
+//    rem(v) the drop of v's class maximum when v leaves it;
+//  * gamma is stored transposed, gT[c][v] (u16), so that thread t scanning vertices t, t + 256, ...
+//    reads consecutive addresses across the warp; the first Cs colours live in shared memory, the
+//    rest in an L2-resident slab of global memory owned by the CTA (n * k * 2 bytes exceeds one
+//    SM's shared memory for the benchmarked graphs);
+//  * class maxima are kept exactly by per-class counts per weight level plus a level bitmask, so
+//    max1, its multiplicity and the second largest weight come from two bit scans after a move;
+//  * ties: the j-th admissible minimum in (v ascending, c ascending) order, found by a block
+//    prefix sum over per-vertex tie counts.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dlm {
+
+constexpr int kWThreads = 256;
+constexpr int kWWarps = kWThreads / 32;
+
+struct WvcpLayout {
+  size_t col, best, w, fz, lvl, lmask, info, max1, rmin, rcnt, red, gT, total;
+  int npad, lw, cs;  // vertices padded to 8, mask words per class, colours held in shared memory
+};
+
+__host__ __device__ inline size_t wal16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// as many colours in shared memory as `budget` allows (the rest go to the CTA's global slab)
+__host__ __device__ inline WvcpLayout wvcp_layout(int n, int k, int wmax, size_t budget) {
+  WvcpLayout L;
+  L.npad = (n + 7) & ~7;
+  L.lw = (wmax + 32) / 32;  // levels 0..wmax
+  size_t o = 0;
+  L.col = o; o += wal16(n);
+  L.best = o; o += wal16(n);
+  L.w = o; o += wal16(n);
+  L.fz = o; o += wal16((size_t)n * 2);
+  L.lvl = o; o += wal16((size_t)k * (wmax + 1) * 2);
+  L.lmask = o; o += wal16((size_t)k * L.lw * 4);
+  L.info = o; o += wal16((size_t)k * 4);
+  L.max1 = o; o += wal16((size_t)k);
+  L.rmin = o; o += wal16((size_t)n * 4);
+  L.rcnt = o; o += wal16((size_t)n * 2);
+  L.red = o; o += 512;  // 24 ints, then 24 long longs
+  L.gT = o;
+  const size_t per_col = (size_t)L.npad * 2;
+  size_t cs = budget > o ? (budget - o) / per_col : 0;
+  if (cs > (size_t)k) cs = k;
+  L.cs = (int)cs;
+  o += cs * per_col;
+  L.total = o;
+  return L;
+}
+
+struct WvcpArgs {
+  int32_t n, k, words, pop, wmax;
+  const uint32_t* bits;
+  const int32_t* weight;
+  int16_t* col;
+  int64_t* best_g;
+  int64_t* best_fc;
+  int64_t* moves;
+  int32_t* trace;
+  uint16_t* slab;  // per CTA: (k - cs) * npad u16
+  int64_t iters;
+  int64_t phi;
+  uint32_t L1, ttbase;
+  uint64_t seed;
+  uint32_t gen, ind_base;
+  int32_t* status;
+  size_t smem_budget;
+};
+
+// class c: max1 (largest weight present, 0 if empty), cnt1 (its multiplicity), max2 (next level)
+__device__ __forceinline__ uint32_t class_info(const uint16_t* lvl, const uint32_t* lmask, int lw, int wmax, int c) {
+  const uint32_t* m = lmask + (size_t)c * lw;
+  int m1 = 0, m2 = 0;
+  int w = lw - 1;
+  for (; w >= 0; --w)
+    if (m[w]) { m1 = 32 * w + 31 - __clz(m[w]); break; }
+  if (m1 > 0) {
+    uint32_t rest = m[w] & ~(1u << (m1 & 31));
+    if (rest) m2 = 32 * w + 31 - __clz(rest);
+    else
+      for (int q = w - 1; q >= 0; --q)
+        if (m[q]) { m2 = 32 * q + 31 - __clz(m[q]); break; }
+  }
+  const uint32_t c1 = m1 > 0 ? lvl[(size_t)c * (wmax + 1) + m1] : 0u;
+  return (uint32_t)m1 | ((uint32_t)m2 << 8) | (c1 << 16);
+}
+
+__device__ __forceinline__ void class_add(uint16_t* lvl, uint32_t* lmask, int lw, int wmax, int c, int w, int d) {
+  uint16_t* p = lvl + (size_t)c * (wmax + 1) + w;
+  const int nv = (int)*p + d;
+  *p = (uint16_t)nv;
+  uint32_t* m = lmask + (size_t)c * lw + (w >> 5);
+  if (nv > 0) *m |= 1u << (w & 31);
+  else *m &= ~(1u << (w & 31));
+}
+
+__device__ __forceinline__ void wvcp_scan_key(int c, int o, int wv, int m1c, int base, int64_t phi, int gc, bool frozen,
+                                              int thr, int& km, int& kc) {
+  const int d = base + (wv > m1c ? wv - m1c : 0) + (int)phi * gc;
+  const int key = (c != o && (!frozen || d < thr)) ? d : INT_MAX;
+  if (key < km) { km = key; kc = 1; }
+  else if (key == km && key != INT_MAX) ++kc;
+}
+
+__global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int n = a.n, k = a.k, wmax = a.wmax, nwords = a.words;
+  const WvcpLayout L = wvcp_layout(n, k, wmax, a.smem_budget);
+  const int npad = L.npad, lw = L.lw, cs = L.cs;
+  uint8_t* colS = smem + L.col;
+  uint8_t* bestS = smem + L.best;
+  uint8_t* wS = smem + L.w;
+  uint16_t* fz = (uint16_t*)(smem + L.fz);
+  uint16_t* lvl = (uint16_t*)(smem + L.lvl);
+  uint32_t* lmask = (uint32_t*)(smem + L.lmask);
+  uint32_t* info = (uint32_t*)(smem + L.info);
+  uint8_t* max1s = smem + L.max1;
+  int32_t* rmin = (int32_t*)(smem + L.rmin);
+  uint16_t* rcnt = (uint16_t*)(smem + L.rcnt);
+  int32_t* red = (int32_t*)(smem + L.red);  // [8] warp minima, [8] warp tie totals
+  int32_t* sc = red + 16;                   // mv, old, new, improved, error, bad input, r0, r1
+  long long* sc64 = (long long*)(red + 24); // g, conf, best g, best f, best conf, f, conf partial sums
+  uint16_t* gS = (uint16_t*)(smem + L.gT);
+  uint16_t* gG = a.slab + (size_t)blockIdx.x * (size_t)(k - cs) * npad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t phi = a.phi;
+  int per = (n + kWThreads - 1) / kWThreads;
+  {
+    int p2 = 1;
+    while (p2 < per) p2 <<= 1;
+    per = p2 > 32 ? 32 : p2;
+  }
+  const uint32_t slice_mask = per == 32 ? 0xFFFFFFFFu : ((1u << per) - 1u);
+
+  for (int ind = blockIdx.x; ind < a.pop; ind += gridDim.x) {
+    int16_t* gcol = a.col + (size_t)ind * n;
+    // ---- set-up ---------------------------------------------------------------------------
+    {
+      uint32_t* l32 = (uint32_t*)lvl;
+      for (int i = tid; i < (k * (wmax + 1) + 1) / 2; i += kWThreads) l32[i] = 0u;
+      for (int i = tid; i < k * npad; i += kWThreads) {
+        const int c = i / npad, v = i - c * npad;
+        if (c < cs) gS[(size_t)c * npad + v] = 0;
+        else gG[(size_t)(c - cs) * npad + v] = 0;
+      }
+      if (tid < 8) sc[tid] = 0;
+    }
+    __syncthreads();
+    for (int v = tid; v < n; v += kWThreads) {
+      int c = gcol[v];
+      if (c < 0 || c >= k) { sc[5] = 1; c = 0; }
+      colS[v] = (uint8_t)c;
+      bestS[v] = (uint8_t)c;
+      const int w = a.weight[v];
+      wS[v] = (uint8_t)w;
+      fz[v] = 0;
+      const int q = c * (wmax + 1) + w;
+      atomicAdd((uint32_t*)lvl + (q >> 1), 1u << (16 * (q & 1)));
+    }
+    __syncthreads();
+    if (sc[5]) {
+      if (tid == 0) raise_status(a.status, DLM_EINVAL);
+      __syncthreads();
+      continue;
+    }
+    for (int i = tid; i < k * lw; i += kWThreads) {
+      const int c = i / lw, wd = i - c * lw;
+      uint32_t m = 0;
+      for (int b = 0; b < 32; ++b) {
+        const int lev = 32 * wd + b;
+        if (lev <= wmax && lvl[(size_t)c * (wmax + 1) + lev] > 0) m |= 1u << b;
+      }
+      lmask[i] = m;
+    }
+    // transposed conflict table: the thread of vertex v is the only writer of position v
+    long long cpart = 0;
+    for (int v = tid; v < n; v += kWThreads) {
+      const uint32_t* brow = a.bits + (size_t)v * nwords;
+      for (int wd = 0; wd < nwords; ++wd) {
+        uint32_t m = __ldg(brow + wd);
+        while (m) {
+          const int u = 32 * wd + __ffs(m) - 1;
+          m &= m - 1;
+          const int c = colS[u];
+          if (c < cs) gS[(size_t)c * npad + v]++;
+          else gG[(size_t)(c - cs) * npad + v]++;
+          if (c == colS[v]) ++cpart;
+        }
+      }
+    }
+    __syncthreads();
+    long long fpart = 0;
+    for (int c = tid; c < k; c += kWThreads) {
+      const uint32_t ic = class_info(lvl, lmask, lw, wmax, c);
+      info[c] = ic;
+      max1s[c] = (uint8_t)(ic & 0xFF);
+      fpart += ic & 0xFF;
+    }
+    for (int d = 16; d >= 1; d >>= 1) {
+      cpart += __shfl_down_sync(0xFFFFFFFFu, cpart, d);
+      fpart += __shfl_down_sync(0xFFFFFFFFu, fpart, d);
+    }
+    if (lane == 0) { sc64[8 + warp] = cpart; sc64[16 + warp] = fpart; }
+    __syncthreads();
+    if (tid == 0) {
+      long long ct = 0, ft = 0;
+      for (int w = 0; w < kWWarps; ++w) { ct += sc64[8 + w]; ft += sc64[16 + w]; }
+      const long long conf = ct / 2;
+      sc64[0] = ft + phi * conf;
+      sc64[1] = conf;
+      sc64[2] = ft + phi * conf;
+      sc64[3] = ft;
+      sc64[4] = conf;
+    }
+    __syncthreads();
+    long long g = sc64[0], conf = sc64[1], best_g = sc64[2];
+    int64_t moves = 0;
+    int32_t* trace = a.trace ? a.trace + (size_t)ind * a.iters * 4 : nullptr;
+    for (int64_t it = 0; it < a.iters; ++it) {
+      const unsigned itrel = (unsigned)(it & 0x3FFF);
+      if (tid == 0) {
+        const U4 r = rng(a.seed, (uint32_t)it, a.gen, a.ind_base + (uint32_t)ind, kTagTabu);
+        sc[6] = (int32_t)r.x;
+        sc[7] = (int32_t)r.y;
+        sc[0] = -1;
+      }
+      // ---- phase 1: every one-move of the thread's vertices -----------------------------------
+      const long long thr64 = best_g - g;
+      const int thr = thr64 < (long long)INT_MIN + 1 ? INT_MIN + 1 : (int)thr64;
+      int tmin = INT_MAX;
+      for (int v = tid; v < n; v += kWThreads) {
+        const int o = colS[v], wv = wS[v];
+        const uint32_t io = info[o];
+        const int m1o = io & 0xFF, m2o = (io >> 8) & 0xFF, c1o = io >> 16;
+        const int rem = (wv == m1o && c1o == 1) ? m2o - m1o : 0;
+        const int g0 = o < cs ? gS[(size_t)o * npad + v] : gG[(size_t)(o - cs) * npad + v];
+        const bool frozen = fz[v] > itrel;
+        const int base = rem - (int)phi * g0;
+        int km = INT_MAX, kc = 0;
+#pragma unroll 4
+        for (int c = 0; c < cs; ++c)
+          wvcp_scan_key(c, o, wv, max1s[c], base, phi, gS[(size_t)c * npad + v], frozen, thr, km, kc);
+        for (int c = cs; c < k; ++c)
+          wvcp_scan_key(c, o, wv, max1s[c], base, phi, gG[(size_t)(c - cs) * npad + v], frozen, thr, km, kc);
+        rmin[v] = km;
+        rcnt[v] = (uint16_t)(km == INT_MAX ? 0 : kc);
+        tmin = min(tmin, km);
+      }
+      {
+        const int wm = __reduce_min_sync(0xFFFFFFFFu, tmin);
+        if (lane == 0) red[warp] = wm;
+      }
+      __syncthreads();
+      // ---- phase 2: minimum, tie ranks over vertices in order, move -----------------------------
+      int dstar = INT_MAX;
+#pragma unroll
+      for (int w = 0; w < kWWarps; ++w) dstar = min(dstar, red[w]);
+      const int C2 = (n + kWThreads - 1) / kWThreads;
+      const int v0 = tid * C2, v1 = min(v0 + C2, n);
+      int ct = 0;
+      if (dstar != INT_MAX)
+        for (int v = v0; v < v1; ++v) ct += rmin[v] == dstar ? rcnt[v] : 0;
+      int incl = ct;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+      }
+      if (lane == 31) red[8 + warp] = incl;
+      __syncthreads();
+      int T = 0, pre = 0;
+#pragma unroll
+      for (int w = 0; w < kWWarps; ++w) {
+        T += red[8 + w];
+        pre += w < warp ? red[8 + w] : 0;
+      }
+      if (T > 0 && ct > 0) {
+        const uint32_t j = below((uint32_t)sc[6], (uint32_t)T);
+        const int lo = pre + incl - ct;
+        if ((int)j >= lo && (int)j < lo + ct) {
+          int jj = (int)j - lo, mv = -1, mc = -1;
+          for (int v = v0; v < v1 && mv < 0; ++v) {
+            if (rmin[v] != dstar) continue;
+            if (jj >= rcnt[v]) { jj -= rcnt[v]; continue; }
+            mv = v;
+            const int o = colS[v], wv = wS[v];
+            const uint32_t io = info[o];
+            const int m1o = io & 0xFF, m2o = (io >> 8) & 0xFF, c1o = io >> 16;
+            const int rem = (wv == m1o && c1o == 1) ? m2o - m1o : 0;
+            const int g0 = o < cs ? gS[(size_t)o * npad + v] : gG[(size_t)(o - cs) * npad + v];
+            const bool frozen = fz[v] > itrel;
+            const int base = rem - (int)phi * g0;
+            for (int c = 0; c < k; ++c) {
+              int km = INT_MAX, kc = 0;
+              const int gc = c < cs ? gS[(size_t)c * npad + v] : gG[(size_t)(c - cs) * npad + v];
+              wvcp_scan_key(c, o, wv, max1s[c], base, phi, gc, frozen, thr, km, kc);
+              if (km == dstar) {
+                if (jj == 0) { mc = c; break; }
+                --jj;
+              }
+            }
+          }
+          if (mv >= 0 && mc >= 0) {
+            const int o = colS[mv], wv = wS[mv];
+            const int go = o < cs ? gS[(size_t)o * npad + mv] : gG[(size_t)(o - cs) * npad + mv];
+            const int gn = mc < cs ? gS[(size_t)mc * npad + mv] : gG[(size_t)(mc - cs) * npad + mv];
+            class_add(lvl, lmask, lw, wmax, o, wv, -1);
+            class_add(lvl, lmask, lw, wmax, mc, wv, +1);
+            info[o] = class_info(lvl, lmask, lw, wmax, o);
+            info[mc] = class_info(lvl, lmask, lw, wmax, mc);
+            max1s[o] = (uint8_t)(info[o] & 0xFF);
+            max1s[mc] = (uint8_t)(info[mc] & 0xFF);
+            colS[mv] = (uint8_t)mc;
+            const long long gn64 = g + dstar, cn64 = conf + (gn - go);
+            fz[mv] = (uint16_t)(itrel + 1 + below((uint32_t)sc[7], a.L1) + a.ttbase);
+            sc[0] = mv; sc[1] = o; sc[2] = mc; sc[3] = gn64 < best_g;
+            sc64[0] = gn64;
+            sc64[1] = cn64;
+            if (gn64 < best_g) { sc64[2] = gn64; sc64[3] = gn64 - phi * cn64; sc64[4] = cn64; }
+            if (trace) reinterpret_cast<int4*>(trace)[it] = make_int4(mv, mc, dstar, T);
+          } else {
+            sc[4] = 2;
+          }
+        }
+      }
+      if (T == 0 && tid == 0 && trace) reinterpret_cast<int4*>(trace)[it] = make_int4(-1, -1, 0, 0);
+      __syncthreads();
+      if (sc[4]) break;
+      // ---- phase 3: conflict-table update on the neighbours of the moved vertex ----------------
+      const int mv = sc[0];
+      if (mv >= 0) {
+        g = sc64[0];
+        conf = sc64[1];
+        ++moves;
+        const int old = sc[1], nw = sc[2];
+        const bool improved = sc[3] != 0;
+        if (improved) best_g = sc64[2];
+        uint16_t* po = old < cs ? gS + (size_t)old * npad : gG + (size_t)(old - cs) * npad;
+        uint16_t* pn = nw < cs ? gS + (size_t)nw * npad : gG + (size_t)(nw - cs) * npad;
+        const uint32_t* brow = a.bits + (size_t)mv * nwords;
+        for (int b0 = tid * per; b0 < n; b0 += kWThreads * per) {
+          uint32_t m = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
+          while (m) {
+            const int u = b0 + __ffs(m) - 1;
+            m &= m - 1;
+            po[u]--;
+            pn[u]++;
+          }
+        }
+        if (improved) {
+          const uint32_t* s32 = (const uint32_t*)colS;
+          uint32_t* d32 = (uint32_t*)bestS;
+          for (int i = tid; i < (n + 3) / 4; i += kWThreads) d32[i] = s32[i];
+        }
+      }
+      if (((it + 1) & 0x3FFF) == 0)
+        for (int v = tid; v < n; v += kWThreads) fz[v] = fz[v] > 0x4000 ? (uint16_t)(fz[v] - 0x4000) : 0;
+      __syncthreads();
+    }
+    if (sc[4] && tid == 0) raise_status(a.status, DLM_ECUDA);
+    for (int v = tid; v < n; v += kWThreads) gcol[v] = (int16_t)bestS[v];
+    if (tid == 0) {
+      a.best_g[ind] = sc64[2];
+      if (a.best_fc) { a.best_fc[2 * ind] = sc64[3]; a.best_fc[2 * ind + 1] = sc64[4]; }
+      if (a.moves) a.moves[ind] = moves;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Randomised greedy initialisation: one warp per individual. Vertex order (decreasing weight, then
+// decreasing degree, then increasing index) is shared; vertex pos takes a colour drawn uniformly
+// (Philox(a = pos, b = 0, c = individual, tag = WINIT)) among the opened colours that no coloured
+// neighbour uses, or opens a new colour. The lanes OR their neighbours' colour bits into a 256-bit
+// mask reduced with redux.sync.
+// ------------------------------------------------------------------------------------------------
+constexpr int kGWarps = 4;
+
+__global__ void __launch_bounds__(32 * kGWarps) k_wvcp_greedy(int n, const int32_t* order, const int32_t* off,
+                                                              const uint16_t* idx, int pop, uint64_t seed,
+                                                              uint32_t ind_base, int16_t* col, int32_t* used_out,
+                                                              int32_t* status) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* cw = smem + (size_t)warp * ((n + 15) & ~15);
+  for (int i = blockIdx.x * kGWarps + warp; i < pop; i += gridDim.x * kGWarps) {
+    for (int v = lane; v < n; v += 32) cw[v] = 0xFF;
+    __syncwarp();
+    int used = 0;
+    bool overflow = false;
+    for (int pos = 0; pos < n && !overflow; ++pos) {
+      const int v = order[pos];
+      uint32_t bm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int e = off[v] + lane; e < off[v + 1]; e += 32) {
+        const int c = cw[idx[e]];
+        if (c != 0xFF) bm[c >> 5] |= 1u << (c & 31);
+      }
+      int cnt = 0;
+      uint32_t legal[8];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const uint32_t b = __reduce_or_sync(0xFFFFFFFFu, bm[w]);
+        const int lo = 32 * w;
+        const uint32_t usedm = used >= lo + 32 ? 0xFFFFFFFFu : (used <= lo ? 0u : ((1u << (used - lo)) - 1u));
+        legal[w] = ~b & usedm;
+        cnt += __popc(legal[w]);
+      }
+      int c;
+      if (cnt == 0) {
+        c = used++;
+        if (c > 254) overflow = true;
+      } else {
+        const U4 r = rng(seed, (uint32_t)pos, 0u, ind_base + (uint32_t)i, kTagWInit);
+        int j = (int)below(r.x, (uint32_t)cnt);
+        c = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          const int pc = __popc(legal[w]);
+          if (j >= 0 && j < pc) {
+            uint32_t x = legal[w];
+            for (int q = 0; q < j; ++q) x &= x - 1;
+            c = 32 * w + __ffs(x) - 1;
+          }
+          j -= pc;
+        }
+      }
+      if (lane == 0) cw[v] = (uint8_t)c;
+      __syncwarp();
+    }
+    if (overflow) {
+      if (lane == 0) raise_status(status, DLM_EUNSUPPORTED);
+      continue;
+    }
+    for (int v = lane; v < n; v += 32) col[(size_t)i * n + v] = (int16_t)cw[v];
+    if (lane == 0 && used_out) used_out[i] = used;
+    __syncwarp();
+  }
+}
+
+}  // namespace dlm
+
+using namespace dlm;
+
+extern "C" dlm_status dlm_wvcp_greedy(dlm_ctx* ctx, const dlm_graph* g, int32_t pop, uint64_t seed, uint32_t ind_base,
+                                      int16_t* col, int32_t* used) {
+  if (!ctx || !g) return fail(ctx, DLM_EINVAL, "wvcp_greedy: null argument");
+  if (!g->d_weight) return fail(ctx, DLM_EINVAL, "wvcp_greedy: the graph has no vertex weights");
+  if (pop < 0 || (pop > 0 && !col)) return fail(ctx, DLM_EINVAL, "wvcp_greedy: bad arguments");
+  if (pop == 0) return DLM_OK;
+  const int n = g->n;
+  // vertex order on the host: decreasing weight, decreasing degree, increasing index
+  std::vector<int32_t> w(n), off(n + 1), order(n);
+  DLM_CUDA(ctx, cudaMemcpyAsync(w.data(), g->d_weight, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(off.data(), g->d_off, (size_t)(n + 1) * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int v = 0; v < n; ++v) order[v] = v;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (w[a] != w[b]) return w[a] > w[b];
+    return off[a + 1] - off[a] > off[b + 1] - off[b];
+  });
+  int32_t* d_order = nullptr;
+  DLM_TRY(ctx_workspace(ctx, (size_t)n * 4, (void**)&d_order));
+  DLM_CUDA(ctx, cudaMemcpyAsync(d_order, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice, ctx->stream));
+  const size_t smem = (size_t)kGWarps * ((n + 15) & ~15);
+  const int grid = std::min((pop + kGWarps - 1) / kGWarps, ctx->num_sms * 8);
+  k_wvcp_greedy<<<grid, 32 * kGWarps, smem, ctx->stream>>>(n, d_order, g->d_off, g->d_idx, pop, seed, ind_base, col, used,
+                                                           ctx->d_status);
+  DLM_TRY(launch_check(ctx, "k_wvcp_greedy"));
+  // the order array lives in the workspace: keep it alive until the kernel has read it
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return DLM_OK;
+}
+
+static dlm_status wvcp_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col, int64_t* best_g,
+                           int64_t* best_fc, int64_t* moves, int64_t iters, dlm_tenure tenure, int64_t phi, uint64_t seed,
+                           uint32_t generation, uint32_t ind_base, int32_t* trace) {
+  if (!ctx || !g) return fail(ctx, DLM_EINVAL, "wvcp_tabu: null argument");
+  if (!g->d_weight) return fail(ctx, DLM_EINVAL, "wvcp_tabu: the graph has no vertex weights");
+  if (k < 2 || k > 255) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: k must be in 2..255");
+  if (g->max_weight > 255) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: vertex weights must be <= 255");
+  if (pop < 0 || iters < 0 || iters > INT32_MAX) return fail(ctx, DLM_EINVAL, "wvcp_tabu: bad population or budget");
+  if (phi < 0 || phi * (int64_t)(g->max_degree + 1) >= ((int64_t)1 << 30))
+    return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: phi * (max degree + 1) must stay below 2^30");
+  if (tenure.L_max < 0 || tenure.alpha_num < 0 || tenure.alpha_den <= 0) return fail(ctx, DLM_EINVAL, "wvcp_tabu: bad tenure");
+  const int64_t ttbase = ((int64_t)tenure.alpha_num * g->n) / tenure.alpha_den;
+  if (ttbase + tenure.L_max + 1 >= 0x4000) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: tenure must stay below 2^14");
+  if (pop == 0) return DLM_OK;
+  if (!col || !best_g) return fail(ctx, DLM_EINVAL, "wvcp_tabu: null col or best_g");
+  const WvcpLayout L = wvcp_layout(g->n, k, g->max_weight, ctx->smem_optin);
+  if (L.gT > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: per-individual state exceeds shared memory");
+  const int grid = std::min(pop, ctx->num_sms);
+  uint16_t* slab = nullptr;
+  const size_t slab_cols = (size_t)(k - L.cs);
+  DLM_TRY(ctx_workspace(ctx, std::max<size_t>(16, (size_t)grid * slab_cols * L.npad * 2), (void**)&slab));
+  WvcpArgs a;
+  a.n = g->n; a.k = k; a.words = g->words; a.pop = pop; a.wmax = g->max_weight;
+  a.bits = g->d_bits; a.weight = g->d_weight; a.col = col; a.best_g = best_g; a.best_fc = best_fc; a.moves = moves;
+  a.trace = trace; a.slab = slab; a.iters = iters; a.phi = phi; a.L1 = (uint32_t)tenure.L_max + 1u;
+  a.ttbase = (uint32_t)ttbase; a.seed = seed; a.gen = generation; a.ind_base = ind_base; a.status = ctx->d_status;
+  a.smem_budget = ctx->smem_optin;
+  DLM_CUDA(ctx, cudaFuncSetAttribute(k_wvcp_tabu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  k_wvcp_tabu<<<grid, kWThreads, L.total, ctx->stream>>>(a);
+  return launch_check(ctx, "k_wvcp_tabu");
+}
+
+extern "C" dlm_status dlm_wvcp_tabu_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                          int64_t* best_g, int64_t* best_fc, int64_t* moves, int64_t iters,
+                                          dlm_tenure tenure, int64_t phi, uint64_t seed, uint32_t generation,
+                                          uint32_t ind_base) {
+  return wvcp_run(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure, phi, seed, generation, ind_base, nullptr);
+}
+
+extern "C" dlm_status dlm_wvcp_tabu_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                             int64_t* best_g, int64_t* best_fc, int64_t* moves, int64_t iters,
+                                             dlm_tenure tenure, int64_t phi, uint64_t seed, uint32_t generation,
+                                             uint32_t ind_base, int32_t* trace) {
+  return wvcp_run(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure, phi, seed, generation, ind_base, trace);
+}

@@ -80,6 +80,8 @@ _SIGS = {
     "dlm_probe_smem_bandwidth": (_i32, [_P, _P]),
     "dlm_gemm_bf16": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32]),
     "dlm_wvcp_tabu_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32]),
+    "dlm_wvcp_tabu_batch_ex": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32, _P]),
+    "dlm_wvcp_greedy": (_i32, [_P, _P, _i32, _u64, _u32, _P, _P]),
 }
 
 _lib = None
@@ -353,3 +355,14 @@ def dlm_wvcp_tabu_batch(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenu
                         generation=0, ind_base=0):
     ctx.check(lib().dlm_wvcp_tabu_batch(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_g), _ptr(best_fc), _ptr(moves),
                                         iters, tenure, phi, seed, generation, ind_base), "dlm_wvcp_tabu_batch")
+
+
+def dlm_wvcp_tabu_batch_ex(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure=WVCP_TENURE, phi=0, seed=0,
+                           generation=0, ind_base=0, trace=None):
+    ctx.check(lib().dlm_wvcp_tabu_batch_ex(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_g), _ptr(best_fc), _ptr(moves),
+                                           iters, tenure, phi, seed, generation, ind_base, _ptr(trace)),
+              "dlm_wvcp_tabu_batch_ex")
+
+
+def dlm_wvcp_greedy(ctx, g, pop, seed, ind_base, col, used):
+    ctx.check(lib().dlm_wvcp_greedy(ctx.h, g.h, pop, seed, ind_base, _ptr(col), _ptr(used)), "dlm_wvcp_greedy")

@@ -1,0 +1,154 @@
+"""GPU parity of the weighted vertex colouring path (randomised greedy initialisation and the
+feasible/infeasible tabu search) against the oracle, through the C-ABI (integer work: bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_05948_gb300 import dlmcol, inputs
+
+from gpu_util import device_graph, oracle_pool
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2109_05948_gb300 import build
+
+    build.build()
+    c = dlmcol.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle_greedy(adj, w, seed, ind):
+    n = adj.shape[0]
+    col = np.zeros(n, np.int16)
+    used = oracle.lib().oracle_wvcp_greedy(n, oracle._ptr(adj), oracle._ptr(w), seed, ind, oracle._ptr(col))
+    return col, used
+
+
+def _oracle_tabu(args):
+    import oracle as o
+
+    adj, w, k, col, iters, phi, seed, ind, gen, trace = args
+    n = adj.shape[0]
+    best = np.zeros(n, np.int16)
+    bg, fc, mv = np.zeros(1, np.int64), np.zeros(2, np.int64), np.zeros(1, np.int64)
+    tr = np.full((iters, 4), -7, np.int32) if trace else None
+    rc = o.lib().oracle_wvcp_tabu(n, o._ptr(adj), o._ptr(w), k, o._ptr(col), iters, 9, 2, 10, phi, seed, ind, gen,
+                                  o._ptr(best), o._ptr(bg), o._ptr(fc), o._ptr(mv), o._ptr(tr) if trace else None, 0)
+    assert rc == 0
+    return dict(best_col=best, best_g=int(bg[0]), f=int(fc[0]), c=int(fc[1]), moves=int(mv[0]), trace=tr)
+
+
+def _case(n, p, seed):
+    e = inputs.gnp(n, p, seed)
+    adj = inputs.edges_to_adj(n, e)
+    w = inputs.weights(n, seed)
+    return e, adj, w
+
+
+@pytest.mark.parametrize("n,p,seed,pop", [(60, 0.5, 1, 8), (200, 0.3, 2, 5), (500, 0.5, 3, 3)])
+def test_greedy_matches_oracle(ctx, n, p, seed, pop):
+    e, adj, w = _case(n, p, seed)
+    g = device_graph(ctx, n, e, w)
+    col = torch.zeros((pop, n), dtype=torch.int16, device="cuda")
+    used = torch.zeros(pop, dtype=torch.int32, device="cuda")
+    dlmcol.dlm_wvcp_greedy(ctx, g, pop, seed, 4, col, used)
+    ctx.sync()
+    for i in range(pop):
+        ref, u = _oracle_greedy(adj, w, seed, 4 + i)
+        assert np.array_equal(col[i].cpu().numpy(), ref) and used[i].item() == u
+
+
+def _run_gpu(ctx, g, k, starts, iters, phi, seed, gen, trace=False):
+    pop, n = starts.shape
+    col = torch.from_numpy(starts.copy()).cuda()
+    bg = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    fc = torch.zeros((pop, 2), dtype=torch.int64, device="cuda")
+    mv = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    tr = torch.full((pop, iters, 4), -7, dtype=torch.int32, device="cuda") if trace else None
+    dlmcol.dlm_wvcp_tabu_batch_ex(ctx, g, k, pop, col, bg, fc, mv, iters, dlmcol.WVCP_TENURE, phi, seed, gen, 0, tr)
+    ctx.sync()
+    return col.cpu().numpy(), bg.cpu().numpy(), fc.cpu().numpy(), mv.cpu().numpy(), (tr.cpu().numpy() if trace else None)
+
+
+@pytest.mark.parametrize("n,p,seed,iters,legal_start", [(40, 0.5, 1, 400, True), (90, 0.3, 2, 600, False),
+                                                         (150, 0.6, 3, 500, True), (63, 0.9, 4, 300, False)])
+def test_wvcp_tabu_bitexact(ctx, n, p, seed, iters, legal_start):
+    e, adj, w = _case(n, p, seed)
+    g = device_graph(ctx, n, e, w)
+    greedy = [_oracle_greedy(adj, w, seed, i) for i in range(4)]
+    k = max(u for _, u in greedy)
+    starts = np.stack([c for c, _ in greedy]) if legal_start else inputs.random_colorings(4, n, k, seed=seed)
+    phi = 2 * int(w.max())
+    col, bg, fc, mv, tr = _run_gpu(ctx, g, k, starts, iters, phi, seed, 3, trace=True)
+    for i in range(4):
+        r = _oracle_tabu((adj, w, k, starts[i], iters, phi, seed, i, 3, True))
+        assert np.array_equal(tr[i], r["trace"]), f"first divergence at {int(np.argmax(np.any(tr[i] != r['trace'], 1)))}"
+        assert (bg[i], fc[i, 0], fc[i, 1], mv[i]) == (r["best_g"], r["f"], r["c"], r["moves"])
+        assert np.array_equal(col[i], r["best_col"])
+
+
+def test_wvcp_unit_weights_and_small_phi(ctx):
+    n = 80
+    e = inputs.gnp(n, 0.4, 7)
+    adj = inputs.edges_to_adj(n, e)
+    w = np.ones(n, np.int32)
+    g = device_graph(ctx, n, e, w)
+    k = 12
+    starts = inputs.random_colorings(3, n, k, seed=5)
+    col, bg, fc, mv, _ = _run_gpu(ctx, g, k, starts, 500, 1, 9, 0)
+    for i in range(3):
+        r = _oracle_tabu((adj, w, k, starts[i], 500, 1, 9, i, 0, False))
+        assert (bg[i], fc[i, 0], fc[i, 1], mv[i]) == (r["best_g"], r["f"], r["c"], r["moves"])
+        assert np.array_equal(col[i], r["best_col"])
+
+
+def test_wvcp_rejects_bad_input(ctx):
+    n = 30
+    e = inputs.gnp(n, 0.3, 1)
+    g_now = device_graph(ctx, n, e)  # no weights
+    col = torch.zeros((1, n), dtype=torch.int16, device="cuda")
+    bg = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_wvcp_tabu_batch(ctx, g_now, 4, 1, col, bg, None, None, 10, dlmcol.WVCP_TENURE, 2)
+    g = device_graph(ctx, n, e, inputs.weights(n, 1))
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_wvcp_tabu_batch(ctx, g, 300, 1, col, bg, None, None, 10, dlmcol.WVCP_TENURE, 2)
+    col[0, 3] = 9
+    dlmcol.dlm_wvcp_tabu_batch(ctx, g, 5, 1, col, bg, None, None, 10, dlmcol.WVCP_TENURE, 2)
+    with pytest.raises(dlmcol.DlmError):
+        ctx.sync()
+
+
+def test_wvcp_full_size_sampled(ctx):
+    """The weighted workload: G(1000, 0.5), weights 1..100, k from the greedy initialisation,
+    phi = 2 max w; the conflict table spills from shared memory into the CTA's global slab.
+    Two individuals are replayed by the oracle over 1500 iterations."""
+    n, pop, iters = 1000, 160, 1500
+    e, adj, w = _case(n, 0.5, 0)
+    g = device_graph(ctx, n, e, w)
+    col = torch.zeros((pop, n), dtype=torch.int16, device="cuda")
+    used = torch.zeros(pop, dtype=torch.int32, device="cuda")
+    dlmcol.dlm_wvcp_greedy(ctx, g, pop, 0, 0, col, used)
+    ctx.sync()
+    k = int(used.max().item())
+    starts = col.cpu().numpy()
+    phi = 2 * int(w.max())
+    gcol, bg, fc, mv, _ = _run_gpu(ctx, g, k, starts, iters, phi, 0, 0)
+    # every individual: the reported f and c recount from the returned colouring
+    for i in range(0, pop, 17):
+        c_i = gcol[i]
+        conf = int(np.sum(c_i[e[:, 0]] == c_i[e[:, 1]]))
+        f = sum(int(w[c_i == q].max()) for q in range(k) if np.any(c_i == q))
+        assert (fc[i, 0], fc[i, 1], bg[i]) == (f, conf, f + phi * conf)
+    refs = oracle_pool().map(_oracle_tabu, [(adj, w, k, starts[i], iters, phi, 0, i, 0, False) for i in (0, pop - 1)])
+    for i, r in zip((0, pop - 1), refs):
+        assert (bg[i], fc[i, 0], fc[i, 1], mv[i]) == (r["best_g"], r["f"], r["c"], r["moves"])
+        assert np.array_equal(gcol[i], r["best_col"])
