@@ -107,9 +107,11 @@ typedef struct {
  *   best_f  device [pop] int64 out: conflicts of that colouring.
  *   moves   device [pop] int64 out (or NULL): iterations that made a move.
  *   iters   iteration budget per individual (paper: 128 |V|).
- * Limits: k <= 128 (DLM_EUNSUPPORTED above); the per-individual state must fit the GPU's shared
- * memory: 4 * n * k bytes plus small arrays, about 227 KB (n = 1000 with k <= 52, n = 500 with
- * k <= 108). Tenures above 32766 iterations stop the search with DLM_EUNSUPPORTED at dlm_sync. */
+ * State: one CTA per individual holds gamma and the tabu list (about 4 n k bytes) in shared memory;
+ * when they do not fit (e.g. n = 1000, k = 100), the rows that do not fit live in a per-CTA slab of
+ * global memory owned by the context (L2 resident) and resident CTAs loop over the individuals.
+ * Limits: k <= 128 (DLM_EUNSUPPORTED above). Tenures above 32766 iterations stop the search with
+ * DLM_EUNSUPPORTED at dlm_sync. */
 dlm_status dlm_tabucol_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                              int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                              uint32_t generation, uint32_t ind_base);

@@ -47,6 +47,9 @@ struct TabuRule {
   uint64_t seed;
   uint32_t gen;
   int32_t* status;
+  size_t budget;         // shared-memory bytes of the launch
+  uint16_t* slab;        // spilled rows, slab_stride u16 per CTA (null when nothing spills)
+  size_t slab_stride;
 };
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
@@ -62,14 +65,15 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 
 struct TabuSmem {
   size_t gam, tab, col, best, rowres, deg, cvl, cv, red, total;
+  int rs;  // rows of gamma and tab held in shared memory; rows rs..n-1 live in the CTA's slab
 };
 
-__host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps) {
+// Shared-memory layout of one individual within `budget` bytes: the small arrays first, then as
+// many rows of gamma and tab as fit (all n when the state fits, as for n = 500, k = 48).
+__host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps, size_t budget) {
   TabuSmem s;
   const int ks = tabu_row_stride(k);
   size_t o = 0;
-  s.gam = o; o += align16((size_t)n * ks * 2);
-  s.tab = o; o += align16((size_t)n * ks * 2);
   s.col = o; o += align16(n);
   s.best = o; o += align16(n);
   s.rowres = o; o += align16((size_t)(n > 256 ? n : 256) * 4);
@@ -77,8 +81,19 @@ __host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps) {
   s.cvl = o; o += align16((size_t)warps * n * 2);
   s.cv = o; o += 64 * 4;
   s.red = o; o += align16((size_t)warps * 8 + 64);
+  const size_t row = (size_t)ks * 2;
+  size_t rs = budget > o + 32 ? (budget - o - 32) / (2 * row) : 0;
+  if (rs > (size_t)n) rs = n;
+  s.rs = (int)rs;
+  s.gam = o; o += align16(rs * row);
+  s.tab = o; o += align16(rs * row);
   s.total = o;
   return s;
+}
+
+// gamma and tab rows that do not fit in shared memory: per CTA, (n - rs) rows of each
+__host__ __device__ inline size_t tabu_slab_elems(int n, int k, int rs) {
+  return (size_t)2 * (size_t)(n - rs) * tabu_row_stride(k);
 }
 
 // position of the r-th (0-based) set bit of x (x has more than r set bits)
@@ -180,9 +195,15 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   constexpr int NT = 32 * W;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = J.n, k = J.k, ks = J.ks, kw = ks / 2, nwords = J.words;
-  const TabuSmem L = tabu_smem_layout(n, k, W);
+  const TabuSmem L = tabu_smem_layout(n, k, W, R.budget);
+  const int rs = L.rs;
   uint16_t* gam = (uint16_t*)(smem + L.gam);
   uint16_t* tab = (uint16_t*)(smem + L.tab);
+  uint16_t* gslab = R.slab ? R.slab + (size_t)blockIdx.x * R.slab_stride : nullptr;
+  uint16_t* tslab = gslab ? gslab + (size_t)(n - rs) * ks : nullptr;
+  // row v of gamma / tab: shared memory for v < rs, the CTA's global slab beyond
+  auto grow_of = [&](int v) -> uint16_t* { return v < rs ? gam + (size_t)v * ks : gslab + (size_t)(v - rs) * ks; };
+  auto trow_of = [&](int v) -> uint16_t* { return v < rs ? tab + (size_t)v * ks : tslab + (size_t)(v - rs) * ks; };
   uint8_t* colS = smem + L.col;
   uint8_t* bestS = smem + L.best;
   uint32_t* rowres = (uint32_t*)(smem + L.rowres);
@@ -196,13 +217,12 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
 
   // ---- set-up: zero the tables (padding colours of gamma = 0xFFFF), load the start colouring --
   {
-    uint32_t* g32 = (uint32_t*)gam;
-    uint32_t* t32 = (uint32_t*)tab;
     const int nw32 = n * kw;
     for (int i = tid; i < nw32; i += NT) {
-      const int c0 = 2 * (i % kw);
-      g32[i] = (c0 >= k ? 0xFFFFu : 0u) | (c0 + 1 >= k ? 0xFFFF0000u : 0u);
-      t32[i] = 0u;
+      const int v = i / kw, w = i - v * kw;
+      const int c0 = 2 * w;
+      ((uint32_t*)grow_of(v))[w] = (c0 >= k ? 0xFFFFu : 0u) | (c0 + 1 >= k ? 0xFFFF0000u : 0u);
+      ((uint32_t*)trow_of(v))[w] = 0u;
     }
     if (tid < 16) sc[tid] = 0;
     for (int i = tid; i < 64; i += NT) cv[i] = 0u;
@@ -223,7 +243,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   // gamma rows: one thread per row, neighbours from the bit rows
   for (int v = tid; v < n; v += NT) {
     const uint32_t* brow = J.bits + (size_t)v * nwords;
-    uint16_t* grow = gam + (size_t)v * ks;
+    uint16_t* grow = grow_of(v);
     int dv = 0;
     for (int w = 0; w < nwords; ++w) {
       uint32_t m = __ldg(brow + w);
@@ -243,7 +263,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     for (int v0 = warp * 32; v0 < n; v0 += NT) {
       const int v = v0 + lane;
       int g = 0;
-      if (v < n) g = gam[(size_t)v * ks + colS[v]];
+      if (v < n) g = grow_of(v)[colS[v]];
       part += g;
       const unsigned b = __ballot_sync(FULL, g > 0);
       if (lane == 0) cv[v0 >> 5] = b;
@@ -303,12 +323,12 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       const int r = i / S, sg = i - r * S;
       const int v = cvl[r];
       const int colv = colS[v];
-      const uint16_t* grow = gam + (size_t)v * ks;
+      const uint16_t* grow = grow_of(v);
       const int g0 = grow[colv];
       const int w0 = sg * Lw, w1 = min(w0 + Lw, kw);
       unsigned km;
       int kc;
-      scan_seg((const uint32_t*)grow, (const uint32_t*)(tab + (size_t)v * ks), w0, w1, colv >> 1,
+      scan_seg((const uint32_t*)grow, (const uint32_t*)trow_of(v), w0, w1, colv >> 1,
                0xFFFFu << (16 * (colv & 1)), itrel, best_f - f + g0, km, kc);
       const int rc = km == 0xFFFFu ? 0 : kc;
       const int dm = km == 0xFFFFu ? kNone16 : (int)km - g0;
@@ -356,11 +376,11 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           const int r = i / S, sg = i - r * S;
           const int v = cvl[r];
           const int colv = colS[v];
-          const uint16_t* grow = gam + (size_t)v * ks;
+          const uint16_t* grow = grow_of(v);
           const int g0 = grow[colv];
           const int w0 = sg * Lw, w1 = min(w0 + Lw, kw);
           mv = v;
-          mc = seg_find((const uint32_t*)grow, (const uint32_t*)(tab + (size_t)v * ks), w0, w1, colv >> 1,
+          mc = seg_find((const uint32_t*)grow, (const uint32_t*)trow_of(v), w0, w1, colv >> 1,
                         0xFFFFu << (16 * (colv & 1)), itrel, best_f - f + g0, (unsigned)(dstar + g0), jj);
           break;
         }
@@ -370,9 +390,9 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           const int fn = f + dstar;
           const int64_t tt = (int64_t)below((uint32_t)sc[8], R.L1) + ((int64_t)R.an * fn) / R.ad;
           if (tt > 32766) sc[5] = 1;
-          tab[(size_t)mv * ks + old] = (uint16_t)(itrel + 1 + tt);
+          trow_of(mv)[old] = (uint16_t)(itrel + 1 + tt);
           const uint32_t bit = 1u << (mv & 31);
-          if (gam[(size_t)mv * ks + mc] > 0) atomicOr(cv + (mv >> 5), bit);
+          if (grow_of(mv)[mc] > 0) atomicOr(cv + (mv >> 5), bit);
           else atomicAnd(cv + (mv >> 5), ~bit);
           sc[0] = mv; sc[1] = old; sc[2] = mc; sc[3] = fn; sc[4] = fn < best_f;
           if (J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(mv, mc, dstar, T);
@@ -397,7 +417,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
         while (m) {
           const int u = b0 + __ffs(m) - 1;
           m &= m - 1;
-          uint16_t* grow = gam + (size_t)u * ks;
+          uint16_t* grow = grow_of(u);
           const int go = grow[old] - 1;
           grow[old] = (uint16_t)go;
           const int gn = grow[nw] + 1;
@@ -416,11 +436,12 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     }
     if (((it + 1) & 0x3FFF) == 0) {
       // the base advances by 2^14: relative expiries drop by 2^14, expired ones become 0
-      uint32_t* t32 = (uint32_t*)tab;
       for (int i = tid; i < n * kw; i += NT) {
-        const uint32_t w = t32[i];
+        const int v = i / kw;
+        uint32_t* t32 = (uint32_t*)trow_of(v) + (i - v * kw);
+        const uint32_t w = *t32;
         const uint32_t lo = w & 0xFFFF, hi = w >> 16;
-        t32[i] = (lo > 0x4000u ? lo - 0x4000u : 0u) | ((hi > 0x4000u ? hi - 0x4000u : 0u) << 16);
+        *t32 = (lo > 0x4000u ? lo - 0x4000u : 0u) | ((hi > 0x4000u ? hi - 0x4000u : 0u) << 16);
       }
     }
     __syncthreads();
@@ -454,18 +475,21 @@ struct TabuBatchArgs {
 template <int W>
 __global__ void __launch_bounds__(W * 32) tabucol_batch_kernel(TabuBatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const int i = blockIdx.x;
-  TabuJob J;
-  J.n = a.n; J.k = a.k; J.ks = a.ks; J.words = a.words; J.bits = a.bits;
-  J.col = a.col + (size_t)i * a.n;
-  J.best_f = a.best_f + i;
-  J.moves = a.moves ? a.moves + i : nullptr;
-  J.trace = a.trace ? a.trace + (size_t)i * a.iters * 4 : nullptr;
-  J.work = a.work ? a.work + 2 * (size_t)i : nullptr;
-  J.off = a.off;
-  J.iters = a.iters;
-  J.ind = a.ind_base + (uint32_t)i;
-  tabucol_individual<W>(J, a.rule, smem);
+  // one individual per CTA, or (when rows spill to a per-CTA slab) resident CTAs loop over them
+  for (int i = blockIdx.x; i < a.pop; i += gridDim.x) {
+    TabuJob J;
+    J.n = a.n; J.k = a.k; J.ks = a.ks; J.words = a.words; J.bits = a.bits;
+    J.col = a.col + (size_t)i * a.n;
+    J.best_f = a.best_f + i;
+    J.moves = a.moves ? a.moves + i : nullptr;
+    J.trace = a.trace ? a.trace + (size_t)i * a.iters * 4 : nullptr;
+    J.work = a.work ? a.work + 2 * (size_t)i : nullptr;
+    J.off = a.off;
+    J.iters = a.iters;
+    J.ind = a.ind_base + (uint32_t)i;
+    tabucol_individual<W>(J, a.rule, smem);
+    __syncthreads();
+  }
 }
 
 // ---- uneven batch: persistent CTAs pull individuals from a device queue ----------------------
@@ -504,11 +528,21 @@ __global__ void __launch_bounds__(W * 32) tabucol_multi_kernel(const MultiJob* j
 // host side
 // ------------------------------------------------------------------------------------------------
 template <int W>
-static dlm_status launch_batch(dlm_ctx* ctx, const TabuBatchArgs& a, size_t smem) {
+static dlm_status launch_batch(dlm_ctx* ctx, TabuBatchArgs a, size_t smem, size_t slab_stride) {
   auto kfn = tabucol_batch_kernel<W>;
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  kfn<<<a.pop, W * 32, smem, ctx->stream>>>(a);
+  int grid = a.pop;
+  if (slab_stride > 0) {  // rows spill: resident CTAs only, each with its own slab
+    int per_sm = 0;
+    DLM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, W * 32, smem));
+    grid = std::min(a.pop, std::max(1, per_sm) * ctx->num_sms);
+    uint16_t* slab = nullptr;
+    DLM_TRY(ctx_workspace(ctx, (size_t)grid * slab_stride * 2, (void**)&slab));
+    a.rule.slab = slab;
+    a.rule.slab_stride = slab_stride;
+  }
+  kfn<<<grid, W * 32, smem, ctx->stream>>>(a);
   return launch_check(ctx, "tabucol_batch_kernel");
 }
 
@@ -547,21 +581,22 @@ static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32
   if (warps == 0) warps = default_warps(g->n, k);
   if (warps != 1 && warps != 2 && warps != 4 && warps != 8)
     return fail(ctx, DLM_EINVAL, "tabucol: warps per individual must be 1, 2, 4 or 8");
-  const TabuSmem L = tabu_smem_layout(g->n, k, warps);
-  if (L.total > ctx->smem_optin)
-    return fail(ctx, DLM_EUNSUPPORTED, "tabucol: per-individual state (" + std::to_string(L.total) +
-                                           " B) exceeds shared memory per block");
+  const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
+  if (L.rs < 1 || L.total > ctx->smem_optin)
+    return fail(ctx, DLM_EUNSUPPORTED, "tabucol: the per-individual arrays exceed shared memory per block");
+  const size_t slab_stride = L.rs < g->n ? tabu_slab_elems(g->n, k, L.rs) : 0;
   TabuBatchArgs a;
   a.n = g->n; a.k = k; a.ks = tabu_row_stride(k); a.words = g->words; a.pop = pop;
   a.bits = g->d_bits; a.off = g->d_off; a.col = col; a.best_f = best_f; a.moves = moves; a.trace = trace;
   a.work = work; a.iters = iters;
   a.ind_base = ind_base;
-  a.rule = TabuRule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status};
+  a.rule = TabuRule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
+                    ctx->smem_optin, nullptr, 0};
   switch (warps) {
-    case 1: return launch_batch<1>(ctx, a, L.total);
-    case 2: return launch_batch<2>(ctx, a, L.total);
-    case 4: return launch_batch<4>(ctx, a, L.total);
-    default: return launch_batch<8>(ctx, a, L.total);
+    case 1: return launch_batch<1>(ctx, a, L.total, slab_stride);
+    case 2: return launch_batch<2>(ctx, a, L.total, slab_stride);
+    case 4: return launch_batch<4>(ctx, a, L.total, slab_stride);
+    default: return launch_batch<8>(ctx, a, L.total, slab_stride);
   }
 }
 
@@ -600,7 +635,7 @@ extern "C" dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int
   const int cand[4] = {1, 2, 4, 8};
   dlm_status st = DLM_OK;
   for (int c = 0; c < 4 && st == DLM_OK; ++c) {
-    const TabuSmem L = tabu_smem_layout(g->n, k, cand[c]);
+    const TabuSmem L = tabu_smem_layout(g->n, k, cand[c], ctx->smem_optin);
     if (L.total > ctx->smem_optin) continue;
     float ms_sum = 0.f;
     for (int rep = 0; rep < 2 && st == DLM_OK; ++rep) {
@@ -648,11 +683,14 @@ extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dl
     warps = w > warps ? w : warps;
     njobs += (size_t)pop[gi];
   }
+  size_t slab_stride = 0;  // graphs whose state exceeds shared memory keep their last rows in a slab
   for (int gi = 0; gi < n_graphs; ++gi) {
-    const TabuSmem L = tabu_smem_layout(graphs[gi]->n, k[gi], warps);
+    const TabuSmem L = tabu_smem_layout(graphs[gi]->n, k[gi], warps, ctx->smem_optin);
+    if (L.rs < 1 || L.total > ctx->smem_optin)
+      return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi: a graph's arrays exceed shared memory");
     smem = L.total > smem ? L.total : smem;
+    if (L.rs < graphs[gi]->n) slab_stride = std::max(slab_stride, tabu_slab_elems(graphs[gi]->n, k[gi], L.rs));
   }
-  if (smem > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi: a graph's state exceeds shared memory");
   if (njobs == 0) return DLM_OK;
   std::vector<MultiJob> jobs;
   jobs.reserve(njobs);
@@ -671,13 +709,8 @@ extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dl
     return (double)a.n * a.k * a.iters > (double)b.n * b.k * b.iters;
   });
   const size_t job_bytes = align16(jobs.size() * sizeof(MultiJob));
-  uint8_t* ws = nullptr;
-  DLM_TRY(ctx_workspace(ctx, job_bytes + 16, (void**)&ws));
-  MultiJob* d_jobs = (MultiJob*)ws;
-  int32_t* d_queue = (int32_t*)(ws + job_bytes);
-  DLM_CUDA(ctx, cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(MultiJob), cudaMemcpyHostToDevice, ctx->stream));
-  DLM_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int32_t), ctx->stream));
-  const TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status};
+  TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
+                ctx->smem_optin, nullptr, slab_stride};
   int per_sm = 0;
   dlm_status st = DLM_OK;
   auto go = [&](auto kfn) -> dlm_status {
@@ -686,6 +719,14 @@ extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dl
     DLM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem));
     if (per_sm < 1) per_sm = 1;
     const int grid = (int)std::min<size_t>((size_t)per_sm * ctx->num_sms, jobs.size());
+    uint8_t* ws = nullptr;
+    DLM_TRY(ctx_workspace(ctx, job_bytes + 16 + (size_t)grid * slab_stride * 2, (void**)&ws));
+    MultiJob* d_jobs = (MultiJob*)ws;
+    int32_t* d_queue = (int32_t*)(ws + job_bytes);
+    if (slab_stride) rule.slab = (uint16_t*)(ws + job_bytes + 16);
+    DLM_CUDA(ctx, cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(MultiJob), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    DLM_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int32_t), ctx->stream));
     kfn<<<grid, warps * 32, smem, ctx->stream>>>(d_jobs, (int32_t)jobs.size(), d_queue, rule);
     return launch_check(ctx, "tabucol_multi_kernel");
   };
@@ -758,11 +799,11 @@ extern "C" dlm_status dlm_tabucol_multi_noalloc(dlm_ctx* ctx, int32_t n_graphs, 
     return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi_noalloc: at most " + std::to_string(kNoAllocMaxJobs) +
                                            " individuals per call (the static scratch array holds that many jobs)");
   for (int gi = 0; gi < n_graphs; ++gi) {
-    const TabuSmem L = tabu_smem_layout(graphs[gi]->n, k[gi], warps);
+    const TabuSmem L = tabu_smem_layout(graphs[gi]->n, k[gi], warps, ctx->smem_optin);
     smem = L.total > smem ? L.total : smem;
+    if (L.rs < graphs[gi]->n)  // a slab for the spilled rows would have to be allocated
+      return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi_noalloc: a graph's state exceeds shared memory");
   }
-  if (smem > ctx->smem_optin)
-    return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi_noalloc: a graph's state exceeds shared memory");
   if (njobs == 0) return DLM_OK;
   std::vector<MultiJob> jobs;
   jobs.reserve(njobs);
@@ -786,7 +827,8 @@ extern "C" dlm_status dlm_tabucol_multi_noalloc(dlm_ctx* ctx, int32_t n_graphs, 
   int32_t* d_queue = (int32_t*)(scratch + kNoAllocJobBytes);
   DLM_CUDA(ctx, cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(MultiJob), cudaMemcpyHostToDevice, ctx->stream));
   DLM_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int32_t), ctx->stream));  // the queue starts at zero
-  const TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status};
+  const TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
+                      ctx->smem_optin, nullptr, 0};
   auto go = [&](auto kfn) -> dlm_status {
     int per_sm = 0;
     DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -109,6 +109,8 @@ def test_tabucol_small_random_graph_trace_bitexact(ctx, warps):
     (260, 100, 0.9, 1500, 3, 3),   # k > 64: several words per lane
     (700, 30, 0.5, 1000, 2, 4),    # n > 512: two bitmap words per lane
     (2, 2, 1.0, 50, 3, 5),         # a single edge
+    (1000, 100, 0.5, 800, 3, 6),   # state above shared memory: the last rows live in a slab
+    (1500, 128, 0.9, 400, 2, 7),   # larger spill, maximum k
 ])
 def test_tabucol_shapes_bitexact(ctx, n, k, p, iters, pop, seed):
     e, adj = gnp_case(n, p, seed)
