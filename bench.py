@@ -39,12 +39,17 @@ def parse():
     ap.add_argument("--pop", type=int, default=POP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic"],
-                    help="tabu: the headline moves/s step; memetic: learned vs random GPX time-to-target")
+    ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp"],
+                    help="tabu: the headline moves/s step; memetic: learned vs random GPX time-to-target; "
+                         "multi: the uneven 64-graph batch in one captured persistent launch")
+    ap.add_argument("--multi-pop", type=int, default=256)
+    ap.add_argument("--multi-depth", type=int, default=128, help="tabu iterations per individual = depth * n")
     ap.add_argument("--mem-n", type=int, default=1000)
     ap.add_argument("--mem-k", type=int, default=48)
     ap.add_argument("--mem-pop", type=int, default=8192)
-    ap.add_argument("--mem-iters", type=int, default=10_000, help="tabu iterations per generation (10 |V|)")
+    ap.add_argument("--mem-iters", type=int, default=2000,
+                    help="tabu iterations per generation; 2 |V|: at 10 |V| tabu alone solves the graph in the "
+                         "first generation and the crossover never matters")
     ap.add_argument("--mem-target", type=int, default=0, help="conflict level to reach")
     ap.add_argument("--mem-seeds", type=int, default=5)
     ap.add_argument("--mem-max-gens", type=int, default=40)
@@ -264,6 +269,137 @@ def run_memetic(args):
     print(json.dumps(out), flush=True)
 
 
+def run_multi(args):
+    """Uneven batch: 64 graphs (n uniform in [100, 1000], p in {0.1, 0.5, 0.9}, odd graphs planted,
+    k = n/10), `multi_pop` individuals each, depth * n iterations, one persistent launch replayed
+    from a CUDA graph; warps per individual autotuned per graph. value = moves/s."""
+    import torch
+
+    from paper_2109_05948_gb300 import build as libbuild
+    from paper_2109_05948_gb300 import dlmcol, inputs
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    ctx = dlmcol.Context(0)
+    specs = inputs.uneven_batch(64, seed=0)
+    graphs = [dlmcol.Graph(ctx, s["n"], torch.from_numpy(s["edges"]).cuda()) for s in specs]
+    ks = [s["k"] for s in specs]
+    pops = [args.multi_pop] * len(specs)
+    iters = [args.multi_depth * s["n"] for s in specs]
+    tuned = {}
+    for g, s in zip(graphs, specs):
+        key = (s["n"], s["k"])
+        if key not in tuned:
+            tuned[key] = dlmcol.dlm_tabucol_autotune(ctx, g, s["k"], 2 * 152, 2000)
+    starts, cols, bfs, mvs = [], [], [], []
+    base = 0
+    for g, s, k, p in zip(graphs, specs, ks, pops):
+        c = torch.empty((p, s["n"]), dtype=torch.int16, device="cuda")
+        dlmcol.dlm_init_colors(ctx, s["n"], k, p, SEED, base, c)
+        starts.append(c.clone())
+        cols.append(c)
+        bfs.append(torch.zeros(p, dtype=torch.int64, device="cuda"))
+        mvs.append(torch.zeros(p, dtype=torch.int64, device="cuda"))
+        base += p
+    plan = dlmcol.MultiPlan(ctx, graphs, ks, pops, cols, bfs, mvs, iters, dlmcol.COL_TENURE, SEED, 0, 0)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for c, st in zip(cols, starts):
+            c.copy_(st)
+        dlmcol.dlm_tabucol_multi_plan_launch(ctx, plan)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    moves = 0
+    for _ in range(args.steps):
+        step()
+        moves += sum(int(m.sum()) for m in mvs)  # reads after the step (stream-ordered)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    solved = sum(int((b == 0).sum()) for b in bfs)
+    out = {"metric": "tabu moves/s, uneven 64-graph batch", "workload": "multi", "value": moves / (ms / 1e3),
+           "unit": "moves/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "gpu_launches": args.steps, "clocks": ck, "data": "synthetic",
+           "config": {"workload": f"64 graphs, n uniform in [100, 1000], p in {{0.1, 0.5, 0.9}}, odd graphs planted, "
+                                  f"k = n/10, population {args.multi_pop} per graph, {args.multi_depth} n iterations, "
+                                  "one persistent launch replayed from a CUDA graph",
+                      "individuals": sum(pops), "warps_per_individual": sorted(set(tuned.values())),
+                      "solved_individuals": solved}}
+    print(json.dumps(out), flush=True)
+    plan.close()
+
+
+def run_wvcp(args):
+    """Weighted colouring: G(1000, 0.5), weights uniform in 1..100, population 8192, k = colours of
+    the GPU randomised greedy initialisation, 10 |V| iterations of the feasible/infeasible tabu
+    search with phi = 2 max w. value = moves/s."""
+    import torch
+
+    from paper_2109_05948_gb300 import build as libbuild
+    from paper_2109_05948_gb300 import dlmcol, inputs
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    ctx = dlmcol.Context(0)
+    n, pop, iters = 1000, 8192, 10 * 1000
+    e = inputs.gnp(n, 0.5, 0)
+    w = inputs.weights(n, 0)
+    g = dlmcol.Graph(ctx, n, torch.from_numpy(e).cuda(), torch.from_numpy(w).cuda())
+    col0 = torch.empty((pop, n), dtype=torch.int16, device="cuda")
+    used = torch.empty(pop, dtype=torch.int32, device="cuda")
+    dlmcol.dlm_wvcp_greedy(ctx, g, pop, SEED, 0, col0, used)
+    ctx.sync()
+    k = int(used.max())
+    phi = 2 * int(w.max())
+    col = torch.empty_like(col0)
+    bg = torch.empty(pop, dtype=torch.int64, device="cuda")
+    fc = torch.empty((pop, 2), dtype=torch.int64, device="cuda")
+    mv = torch.empty(pop, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        col.copy_(col0)
+        dlmcol.dlm_wvcp_tabu_batch(ctx, g, k, pop, col, bg, fc, mv, iters, dlmcol.WVCP_TENURE, phi, SEED, 0, 0)
+    ctx.sync()
+    f0 = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    moves = 0
+    for _ in range(args.steps):
+        col.copy_(col0)
+        dlmcol.dlm_wvcp_tabu_batch(ctx, g, k, pop, col, bg, fc, mv, iters, dlmcol.WVCP_TENURE, phi, SEED, 0, 0)
+        moves += int(mv.sum())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    legal = fc[:, 1] == 0
+    best_legal = int(fc[legal, 0].min()) if bool(legal.any()) else None
+    # algorithmic work per iteration: every (v, c) pair reads one gamma entry (2 B)
+    pairs = n * (k - 1)
+    out = {"metric": "weighted tabu moves/s, G(1000, 0.5), weights 1..100", "workload": "wvcp",
+           "value": moves / (ms / 1e3), "unit": "moves/s", "higher_is_better": True, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "gpu_launches": args.steps, "clocks": ck,
+           "pair_evaluations_per_s": moves / (ms / 1e3) * pairs, "data": "synthetic",
+           "config": {"workload": f"G(1000, 0.5), weights 1..100, population {pop}, k = {k} (greedy), "
+                                  f"{iters} iterations, phi = {phi}", "k": k, "phi": phi,
+                      "best_legal_f": best_legal, "legal_individuals": int(legal.sum())}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -271,6 +407,12 @@ def main():
         return
     if args.workload == "memetic":
         run_memetic(args)
+        return
+    if args.workload == "multi":
+        run_multi(args)
+        return
+    if args.workload == "wvcp":
+        run_wvcp(args)
         return
     import torch
     import torch.distributed as dist

@@ -154,6 +154,21 @@ dlm_status dlm_tabucol_multi_noalloc(dlm_ctx* ctx, int32_t n_graphs, const dlm_g
                                      int64_t* const* moves, const int64_t* iters, dlm_tenure tenure, uint64_t seed,
                                      uint32_t generation, uint32_t ind_base);
 
+/* The uneven batch of dlm_tabucol_multi as a reusable plan: the job list (individuals by decreasing
+ * work), the work queue and the slab of spilled rows are built once in plan-owned device memory,
+ * and the launch (queue reset + persistent kernel) is captured into a CUDA graph; each
+ * dlm_tabucol_multi_plan_launch replays it on the context's stream with the arguments given at
+ * creation (the colourings are searched in place: col holds the best colourings afterwards).
+ * The warps per individual come from the autotuner's cache (dlm_tabucol_autotune) when present. */
+typedef struct dlm_multi_plan dlm_multi_plan;
+dlm_status dlm_tabucol_multi_plan_create(dlm_ctx* ctx, int32_t n_graphs, const dlm_graph* const* graphs,
+                                         const int32_t* k, const int32_t* pop, int16_t* const* col,
+                                         int64_t* const* best_f, int64_t* const* moves, const int64_t* iters,
+                                         dlm_tenure tenure, uint64_t seed, uint32_t generation, uint32_t ind_base,
+                                         dlm_multi_plan** out);
+dlm_status dlm_tabucol_multi_plan_launch(dlm_ctx* ctx, dlm_multi_plan* plan);
+void dlm_tabucol_multi_plan_destroy(dlm_multi_plan* plan);
+
 /* Autotuner for the tabu kernel: times warps_per_individual in {1, 2, 4, 8} on a short run of
  * the given problem and caches the fastest for (n, k) in the context; returns it in *best. */
 dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,

@@ -846,3 +846,118 @@ extern "C" dlm_status dlm_tabucol_multi_noalloc(dlm_ctx* ctx, int32_t n_graphs, 
     default: return go(tabucol_multi_kernel<8>);
   }
 }
+
+// ------------------------------------------------------------------------------------------------
+// Uneven batch as a reusable plan: the job list, the queue and the slab are uploaded once into
+// plan-owned memory, and the launch (queue reset + persistent kernel) is captured once into a CUDA
+// graph; every dlm_tabucol_multi_plan_launch replays that graph on the context's stream.
+// ------------------------------------------------------------------------------------------------
+struct dlm_multi_plan {
+  uint8_t* mem = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int warps = 0, grid = 0;
+  size_t njobs = 0;
+};
+
+extern "C" void dlm_tabucol_multi_plan_destroy(dlm_multi_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  cudaFree(p->mem);
+  delete p;
+}
+
+extern "C" dlm_status dlm_tabucol_multi_plan_create(dlm_ctx* ctx, int32_t n_graphs, const dlm_graph* const* graphs,
+                                                    const int32_t* k, const int32_t* pop, int16_t* const* col,
+                                                    int64_t* const* best_f, int64_t* const* moves,
+                                                    const int64_t* iters, dlm_tenure tenure, uint64_t seed,
+                                                    uint32_t generation, uint32_t ind_base, dlm_multi_plan** out) {
+  if (!ctx || !out || n_graphs <= 0 || !graphs || !k || !pop || !col || !best_f || !iters)
+    return fail(ctx, DLM_EINVAL, "tabucol_multi_plan: bad arguments");
+  *out = nullptr;
+  int warps = 1;
+  size_t smem = 0, slab_stride = 0, njobs = 0;
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    DLM_TRY(tabucol_check(ctx, graphs[gi], k[gi], pop[gi], iters[gi], tenure));
+    if (pop[gi] > 0 && (!col[gi] || !best_f[gi])) return fail(ctx, DLM_EINVAL, "tabucol_multi_plan: null output");
+    int w = lookup_tune(ctx, graphs[gi]->n, k[gi]);
+    if (w == 0) w = default_warps(graphs[gi]->n, k[gi]);
+    warps = std::max(warps, w);
+    njobs += (size_t)pop[gi];
+  }
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    const TabuSmem L = tabu_smem_layout(graphs[gi]->n, k[gi], warps, ctx->smem_optin);
+    if (L.rs < 1 || L.total > ctx->smem_optin)
+      return fail(ctx, DLM_EUNSUPPORTED, "tabucol_multi_plan: a graph's arrays exceed shared memory");
+    smem = std::max(smem, L.total);
+    if (L.rs < graphs[gi]->n) slab_stride = std::max(slab_stride, tabu_slab_elems(graphs[gi]->n, k[gi], L.rs));
+  }
+  if (njobs == 0) return fail(ctx, DLM_EINVAL, "tabucol_multi_plan: empty batch");
+  std::vector<MultiJob> jobs;
+  jobs.reserve(njobs);
+  uint32_t id = ind_base;
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    const dlm_graph* g = graphs[gi];
+    for (int j = 0; j < pop[gi]; ++j) {
+      MultiJob M;
+      M.n = g->n; M.k = k[gi]; M.ks = tabu_row_stride(k[gi]); M.words = g->words; M.bits = g->d_bits;
+      M.col = col[gi] + (size_t)j * g->n; M.best_f = best_f[gi] + j; M.moves = moves && moves[gi] ? moves[gi] + j : nullptr;
+      M.iters = iters[gi]; M.ind = id++;
+      jobs.push_back(M);
+    }
+  }
+  std::stable_sort(jobs.begin(), jobs.end(), [](const MultiJob& a, const MultiJob& b) {
+    return (double)a.n * a.k * a.iters > (double)b.n * b.k * b.iters;
+  });
+  dlm_multi_plan* p = new dlm_multi_plan();
+  p->warps = warps;
+  p->njobs = jobs.size();
+  auto cleanup = [&](dlm_status s, const std::string& m) { dlm_tabucol_multi_plan_destroy(p); return fail(ctx, s, m); };
+  void* kfn = nullptr;
+  switch (warps) {
+    case 1: kfn = (void*)tabucol_multi_kernel<1>; break;
+    case 2: kfn = (void*)tabucol_multi_kernel<2>; break;
+    case 4: kfn = (void*)tabucol_multi_kernel<4>; break;
+    default: kfn = (void*)tabucol_multi_kernel<8>; break;
+  }
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem) != cudaSuccess)
+    return cleanup(DLM_ECUDA, "tabucol_multi_plan: kernel attributes");
+  p->grid = (int)std::min<size_t>((size_t)std::max(1, per_sm) * ctx->num_sms, jobs.size());
+  const size_t job_bytes = align16(jobs.size() * sizeof(MultiJob));
+  if (cudaMalloc(&p->mem, job_bytes + 16 + (size_t)p->grid * slab_stride * 2) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(DLM_ENOMEM, "tabucol_multi_plan: allocation failed");
+  }
+  MultiJob* d_jobs = (MultiJob*)p->mem;
+  int32_t* d_queue = (int32_t*)(p->mem + job_bytes);
+  if (cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(MultiJob), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cleanup(DLM_ECUDA, "tabucol_multi_plan: upload");
+  TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
+                ctx->smem_optin, slab_stride ? (uint16_t*)(p->mem + job_bytes + 16) : nullptr, slab_stride};
+  int32_t njobs32 = (int32_t)jobs.size();
+  void* params[] = {&d_jobs, &njobs32, &d_queue, &rule};
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cleanup(DLM_ECUDA, "stream");
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_queue, 0, sizeof(int32_t), cs);
+  if (e == cudaSuccess) e = cudaLaunchKernel(kfn, dim3(p->grid), dim3(warps * 32), params, smem, cs);
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || e2 != cudaSuccess) { cudaGetLastError(); return cleanup(DLM_ECUDA, "tabucol_multi_plan: capture"); }
+  if (cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(DLM_ECUDA, "tabucol_multi_plan: instantiate");
+  }
+  *out = p;
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_tabucol_multi_plan_launch(dlm_ctx* ctx, dlm_multi_plan* p) {
+  if (!ctx || !p) return fail(ctx, DLM_EINVAL, "tabucol_multi_plan_launch: null argument");
+  DLM_CUDA(ctx, cudaGraphLaunch(p->exec, ctx->stream));
+  return DLM_OK;
+}

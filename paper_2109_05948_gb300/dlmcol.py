@@ -60,6 +60,9 @@ _SIGS = {
     "dlm_tabucol_multi": (_i32, [_P, _i32, _P, _P, _P, _P, _P, _P, _P, Tenure, _u64, _u32, _u32]),
     "dlm_tabucol_multi_noalloc": (_i32, [_P, _i32, _P, _P, _P, _P, _P, _P, _P, Tenure, _u64, _u32, _u32]),
     "dlm_tabucol_autotune": (_i32, [_P, _P, _i32, _i32, _i64, _P]),
+    "dlm_tabucol_multi_plan_create": (_i32, [_P, _i32, _P, _P, _P, _P, _P, _P, _P, Tenure, _u64, _u32, _u32, _PP]),
+    "dlm_tabucol_multi_plan_launch": (_i32, [_P, _P]),
+    "dlm_tabucol_multi_plan_destroy": (None, [_P]),
     "dlm_gpx_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _P, _i32, _P, _u64, _u32]),
     "dlm_distance_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32]),
     "dlm_pool_update": (_i32, [_P, _i32, _i32, _P, _P, _P]),
@@ -366,3 +369,31 @@ def dlm_wvcp_tabu_batch_ex(ctx, g, k, pop, col, best_g, best_fc, moves, iters, t
 
 def dlm_wvcp_greedy(ctx, g, pop, seed, ind_base, col, used):
     ctx.check(lib().dlm_wvcp_greedy(ctx.h, g.h, pop, seed, ind_base, _ptr(col), _ptr(used)), "dlm_wvcp_greedy")
+
+
+class MultiPlan:
+    """dlm_multi_plan: an uneven batch captured once into a CUDA graph (see include/dlmcol.h)."""
+
+    def __init__(self, ctx, graphs, ks, pops, cols, best_fs, moves, iters, tenure=COL_TENURE, seed=0, generation=0,
+                 ind_base=0):
+        a = _multi_args(graphs, ks, pops, cols, best_fs, moves, iters)
+        h = ctypes.c_void_p()
+        ctx.check(lib().dlm_tabucol_multi_plan_create(ctx.h, *a, tenure, seed, generation, ind_base, ctypes.byref(h)),
+                  "dlm_tabucol_multi_plan_create")
+        self.h = h
+        self._keep = a
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dlm_tabucol_multi_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dlm_tabucol_multi_plan_launch(ctx, plan):
+    ctx.check(lib().dlm_tabucol_multi_plan_launch(ctx.h, plan.h), "dlm_tabucol_multi_plan_launch")
