@@ -622,11 +622,16 @@ extern "C" dlm_status dlm_tabucol_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int
 extern "C" dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,
                                            int32_t* best) {
   if (!ctx || !g || pop <= 0 || iters <= 0) return fail(ctx, DLM_EINVAL, "autotune: bad arguments");
+  // the trial colourings get their own allocation: the launches below take the context workspace
+  // for their spilled rows, so colourings kept there would be overwritten (or freed on growth)
   const size_t col_bytes = align16((size_t)pop * g->n * sizeof(int16_t));
-  uint8_t* ws = nullptr;
-  DLM_TRY(ctx_workspace(ctx, col_bytes + (size_t)pop * sizeof(int64_t), (void**)&ws));
-  int16_t* col = (int16_t*)ws;
-  int64_t* bf = (int64_t*)(ws + col_bytes);
+  uint8_t* buf = nullptr;
+  if (cudaMalloc(&buf, col_bytes + (size_t)pop * sizeof(int64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DLM_ENOMEM, "autotune: trial buffer allocation failed");
+  }
+  int16_t* col = (int16_t*)buf;
+  int64_t* bf = (int64_t*)(buf + col_bytes);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -654,6 +659,8 @@ extern "C" dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(buf);
   if (st != DLM_OK) return st;
   int slot = -1;
   for (int i = 0; i < ctx->n_tune; ++i)

@@ -95,3 +95,25 @@ def test_multi_plan_graph_replay_matches_direct_launch(ctx):
         for a, b in zip(bfs, ref_b):
             assert torch.equal(a, b)
     plan.close()
+
+
+@pytest.mark.parametrize("n,p,k", [(120, 0.5, 14), (1000, 0.5, 100)])
+def test_autotune_then_launches_stay_exact(ctx, n, p, k):
+    """The autotuner times every warp count that fits (the second shape spills rows to the CTA
+    slabs, which share the context workspace); afterwards a batch and a multi-graph launch with
+    the tuned warp count still replay the oracle exactly."""
+    e = inputs.gnp(n, p, 11)
+    g = device_graph(ctx, n, e)
+    w = dlmcol.dlm_tabucol_autotune(ctx, g, k, 40, 300)
+    assert w in (1, 2, 4, 8)
+    pop, iters = 2, 2 * n
+    start = oracle.init_colors(n, k, pop, 6)
+    col = torch.from_numpy(start.copy()).cuda()
+    bf = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    mv = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    dlmcol.dlm_tabucol_multi(ctx, [g], [k], [pop], [col], [bf], [mv], [iters], dlmcol.COL_TENURE, 6, 0, 0)
+    ctx.sync()
+    adj = inputs.edges_to_adj(n, e)
+    ref = oracle_tabu_many([(adj, k, start[0], iters, 6, 0, 0, False)])[0]
+    assert bf[0].item() == ref["best_f"] and mv[0].item() == ref["moves"]
+    assert np.array_equal(col[0].cpu().numpy(), ref["best_col"])
