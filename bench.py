@@ -29,6 +29,24 @@ METRIC = "tabu moves/s at n=500,k=48"
 UNIT = "moves/s"
 
 
+def shard(rank: int, pop: int) -> tuple[int, int]:
+    """Weak scaling: rank r owns the individuals [r * pop, (r + 1) * pop) of the global population.
+    Individual ids key the Philox streams, so the union over ranks computes exactly what one GPU
+    would compute on world * pop individuals; no data crosses ranks."""
+    return rank * pop, pop
+
+
+def reduce_over_ranks(dist, ms: float, units: int, device) -> tuple[float, int]:
+    """The job's time is the slowest rank's, its work the sum over ranks."""
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    m = torch.tensor([units], dtype=torch.int64, device=device)
+    dist.all_reduce(m)
+    return float(t.item()), int(m.item())
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,8 +452,8 @@ def main():
     dev = torch.device("cuda", local)
     e = inputs.gnp(N, P_EDGE, SEED)
     g = dlmcol.Graph(ctx, N, torch.from_numpy(e).to(dev))
-    pop, iters = args.pop, args.iters
-    base = rank * pop
+    base, pop = shard(rank, args.pop)
+    iters = args.iters
     col0 = torch.empty((pop, N), dtype=torch.int16, device=dev)
     dlmcol.dlm_init_colors(ctx, N, K, pop, SEED, base, col0)
     if args.warm_start > 0:
@@ -485,12 +503,7 @@ def main():
     tot_moves = int(moves[: args.steps].sum().item())
     wk = work[: args.steps].sum(dim=(0, 1)).tolist()
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        m = torch.tensor([tot_moves], dtype=torch.int64, device=dev)
-        dist.all_reduce(m)
-        tot_moves = int(m.item())
+        ms, tot_moves = reduce_over_ranks(dist, ms, tot_moves, dev)
     value = tot_moves / (ms / 1e3)
 
     # algorithmic shared-memory bytes of the tabu kernel (per launch): every conflicting row
@@ -532,12 +545,7 @@ def main():
         el = time.perf_counter() - e0
         ctx.sync()
         if world > 1:
-            t = torch.tensor([el], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-            m = torch.tensor([emoves], dtype=torch.int64, device=dev)
-            dist.all_reduce(m)
-            emoves = int(m.item())
+            el, emoves = reduce_over_ranks(dist, el, emoves, dev)
         e2e = {"value": emoves / el, "unit": UNIT, "h2d_bytes_per_step": pop * N * 2,
                "d2h_bytes_per_step": pop * N * 2 + 2 * pop * 8}
 

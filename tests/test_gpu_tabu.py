@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2109_05948_gb300 import dlmcol, inputs
 
-from gpu_util import device_graph, gnp_case, oracle_tabu_many
+from gpu_util import _oracle_tabu_job, oracle_pool, device_graph, gnp_case, oracle_tabu_many
 
 pytestmark = pytest.mark.gpu
 
@@ -170,10 +170,12 @@ def test_tabucol_rejects_bad_input(ctx):
     ctx.sync()
 
 
-def test_tabucol_full_size_sampled(ctx):
+def test_tabucol_full_size_all_individuals(ctx):
     """The benchmarked launch: G(500, 0.5), k = 48, population 4096, 10^5 iterations, random
-    starts from seed 0. 12 sampled individuals are replayed by the oracle; for all 4096 the best
-    conflicts equal the recount of the returned colouring."""
+    starts from seed 0. All 4096 individuals are replayed by the oracle (best conflicts, moves and
+    best colouring equal), the best conflicts equal the recount of the returned colouring, and 32
+    individuals (ids 0..15 and 4080..4095, launched again with a trace) match the oracle move by
+    move over the whole budget."""
     n, k, pop, iters = 500, 48, 4096, 100_000
     e, adj = gnp_case(n, 0.5, 0)
     g = device_graph(ctx, n, e)
@@ -187,9 +189,18 @@ def test_tabucol_full_size_sampled(ctx):
     dlmcol.dlm_gamma(ctx, g, k, pop, col, None, f2)
     ctx.sync()
     assert torch.equal(bf, f2)
-    sample = [0, 1, 2, 511, 1024, 2047, 2048, 3000, 3333, 4000, 4094, 4095]
-    refs = oracle_tabu_many([(adj, k, start[i], iters, 0, i, 0, False) for i in sample])
+    traced = list(range(16)) + list(range(pop - 16, pop))
+    gtr = {}
+    for base in (0, pop - 16):
+        out = _run_gpu(ctx, g, k, start[base:base + 16], iters, seed=0, ind_base=base, trace=True)
+        for j in range(16):
+            gtr[base + j] = out["trace"][j]
+    jobs = [(adj, k, start[i], iters, 0, i, 0, i in gtr) for i in range(pop)]
+    refs = oracle_pool().map(_oracle_tabu_job, jobs, chunksize=8)
     colh, bfh, mvh = col.cpu().numpy(), bf.cpu().numpy(), mv.cpu().numpy()
-    for i, r in zip(sample, refs):
-        assert bfh[i] == r["best_f"] and mvh[i] == r["moves"], i
-        assert np.array_equal(colh[i], r["best_col"]), i
+    bad = [i for i, r in enumerate(refs)
+           if bfh[i] != r["best_f"] or mvh[i] != r["moves"] or not np.array_equal(colh[i], r["best_col"])]
+    assert not bad, f"{len(bad)} individuals differ from the oracle, first {bad[:8]}"
+    for i in traced:
+        T = refs[i]["iters"]
+        assert np.array_equal(gtr[i][:T], refs[i]["trace"]), i
