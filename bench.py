@@ -57,9 +57,11 @@ def parse():
     ap.add_argument("--pop", type=int, default=POP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp"],
+    ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp", "scorer"],
                     help="tabu: the headline moves/s step; memetic: learned vs random GPX time-to-target; "
-                         "multi: the uneven 64-graph batch in one captured persistent launch")
+                         "multi: the uneven 64-graph batch in one captured persistent launch; wvcp: the "
+                         "weighted tabu search; scorer: one generation's scoring and training on the "
+                         "tensor cores")
     ap.add_argument("--multi-pop", type=int, default=256)
     ap.add_argument("--multi-depth", type=int, default=128, help="tabu iterations per individual = depth * n")
     ap.add_argument("--mem-n", type=int, default=1000)
@@ -418,6 +420,97 @@ def run_wvcp(args):
     print(json.dumps(out), flush=True)
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def run_scorer(args):
+    """The scorer's share of one learned generation at the planted n = 1000, k = 48 size: score
+    p K = 8192 x 32 GPX-sized candidates, then train on p = 8192 samples (N = 5 epochs, b = 100,
+    Adam lr 1e-3). value = candidates scored per second; the roofline is the tensor-core GEMM
+    kernel's, every launch timed with CUDA events on the context's stream."""
+    import torch
+
+    from paper_2109_05948_gb300 import build as libbuild
+    from paper_2109_05948_gb300 import dlmcol, inputs
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    ctx = dlmcol.Context(0)
+    n, k, p, Kc, epochs, b = 1000, 48, 8192, 32, 5, 100
+    C = p * Kc
+    e, _ = inputs.planted(n, k, 0.5, seed=0)
+    g = dlmcol.Graph(ctx, n, torch.from_numpy(e).cuda())
+    cand = torch.empty((C, n), dtype=torch.int16, device="cuda")
+    dlmcol.dlm_init_colors(ctx, n, k, C, SEED, 0, cand)
+    samples = cand[:p]
+    fvals = torch.empty(p, dtype=torch.int64, device="cuda")
+    dlmcol.dlm_gamma(ctx, g, k, p, samples, None, fvals)
+    out = torch.empty(C, dtype=torch.float32, device="cuda")
+    sc = dlmcol.Scorer(ctx, n, k, SEED)
+    stream = torch.cuda.current_stream()
+
+    def step(s):
+        dlmcol.dlm_score_offspring(ctx, sc, cand, C, out)
+        evs[s][1].record(stream)
+        dlmcol.dlm_scorer_train(ctx, sc, samples, fvals, p, epochs, b, 1e-3, SEED, s)
+
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(max(args.steps, args.warmup))]
+    for w in range(args.warmup):
+        step(w)
+    ctx.sync()
+    dlmcol.dlm_gemm_profile_read(ctx)  # clear
+    dlmcol.dlm_gemm_profile(ctx, True)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        evs[s][0].record(stream)
+        step(s)
+        evs[s][2].record(stream)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ck = clocks.stop()
+    gms, gflops, glaunch = dlmcol.dlm_gemm_profile_read(ctx)
+    dlmcol.dlm_gemm_profile(ctx, False)
+    fwd_ms = sum(a.elapsed_time(m) for a, m, _ in evs[: args.steps])
+    trn_ms = sum(m.elapsed_time(z) for _, m, z in evs[: args.steps])
+    # algorithmic tensor work (class rows only; the head and the class pooling run on CUDA cores):
+    # a forward pass is 2 k (64 x 256 + 2 x 256 x 256) FLOP per colouring; a training sample costs
+    # a forward pass and a backward pass of twice that (input and weight gradients)
+    fwd_flop = 2.0 * k * (64 * 256 + 2 * 256 * 256)
+    alg = args.steps * (C * fwd_flop + p * epochs * 3 * fwd_flop)
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained")
+    src = "of measured (MEASURED_PEAKS.json bf16_tflops_sustained: the GEMMs run inside a long step)"
+    if peak is None:
+        peak, src = 1700.0, "of fallback (sustained bf16)"
+    achieved = alg / (gms / 1e3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "gemm_kernel (tcgen05, TMA, TMEM)", "peak_source": src,
+            "kernel_ms_per_launch": gms / max(1, glaunch), "launches": glaunch,
+            "executed_tflops": gflops / (gms / 1e3) / 1e12,
+            "executed_over_algorithmic": gflops / alg,
+            "gemm_share_of_step": gms / (fwd_ms + trn_ms)}
+    res = {"metric": "scorer candidates/s, n=1000, k=48", "workload": "scorer", "value": C * args.steps / (fwd_ms / 1e3),
+           "unit": "candidates/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": (fwd_ms + trn_ms) / args.steps, "forward_ms_per_step": fwd_ms / args.steps,
+           "train_ms_per_step": trn_ms / args.steps,
+           "train_samples_per_s": p * epochs * args.steps / (trn_ms / 1e3), "dtype": "bf16 (fp32 accumulate)",
+           "gpu_launches": None, "clocks": ck, "roofline": roof, "data": "synthetic",
+           "config": {"workload": f"planted 48-colourable n={n}, {C} candidates ({p} x {Kc}) scored, training on "
+                                  f"{p} samples, {epochs} epochs, batch {b}, scorer 64-d embedding + 3 x 256 "
+                                  f"invariant layers (weights split hi/lo; training activations split)"}}
+    print(json.dumps(res), flush=True)
+    sc.close()
+    g.close()
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -431,6 +524,9 @@ def main():
         return
     if args.workload == "wvcp":
         run_wvcp(args)
+        return
+    if args.workload == "scorer":
+        run_scorer(args)
         return
     import torch
     import torch.distributed as dist

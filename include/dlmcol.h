@@ -318,6 +318,17 @@ dlm_status dlm_gemm_bf16(dlm_ctx* ctx, const void* A, const void* B, float* C, i
  * ------------------------------------------------------------------------------------------- */
 dlm_status dlm_probe_smem_bandwidth(dlm_ctx* ctx, double* gbps);
 
+/* ---------------------------------------------------------------------------------------------
+ * Measurement utility (no counterpart in the paper): while enabled (enable != 0), every launch of
+ * the tensor-core GEMM kernel made through ctx (scorer forward, scorer backward, dlm_gemm_bf16)
+ * is bracketed by two CUDA events recorded on the context's stream. dlm_gemm_profile_read waits
+ * for the stream, returns in host memory the summed launch time (ms), the executed tensor-core
+ * FLOPs (2 M N K per MMA pass: 1 pass, 2 with one split operand, 3 with both) and the number of
+ * launches recorded, then clears the record. Recording adds two event records per launch.
+ * ------------------------------------------------------------------------------------------- */
+dlm_status dlm_gemm_profile(dlm_ctx* ctx, int32_t enable);
+dlm_status dlm_gemm_profile_read(dlm_ctx* ctx, double* ms, double* flops, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

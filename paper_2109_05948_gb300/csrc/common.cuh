@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/dlmcol.h"
 
@@ -80,6 +81,10 @@ struct dlm_ctx {
   // grow-only device workspace for calls that need scratch (job lists, queues, tuning buffers)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // optional CUDA-event timing of every tensor-core GEMM launch (dlm_gemm_profile)
+  struct GemmRec { cudaEvent_t a, b; double flops; };
+  bool gemm_prof = false;
+  std::vector<GemmRec> gemm_recs;
 };
 
 struct dlm_graph {

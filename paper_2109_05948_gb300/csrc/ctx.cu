@@ -157,6 +157,7 @@ dlm_status dlm_create(dlm_ctx** out, int32_t device, void* stream) {
 void dlm_destroy(dlm_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  for (auto& r : ctx->gemm_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   cudaFree(ctx->d_status);
   if (ctx->ws) cudaFree(ctx->ws);
   delete ctx;

@@ -632,7 +632,17 @@ static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K
       DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr = true;
     }
+    dlm_ctx::GemmRec rec{nullptr, nullptr, 0.0};
+    if (ctx->gemm_prof && cudaEventCreate(&rec.a) == cudaSuccess && cudaEventCreate(&rec.b) == cudaSuccess) {
+      // executed tensor-core work: one pass of 2 M N K per MMA (hi.hi, plus hi.lo / lo.hi for split operands)
+      rec.flops = 2.0 * M * N * K * (1 + (A2 ? 1 : 0) + (B2 ? 1 : 0));
+      cudaEventRecord(rec.a, ctx->stream);
+    }
     kfn<<<grid, tc::kThreads, smem, ctx->stream>>>(ma, ma2, mb, mb2, sh, epi, ctx->d_status);
+    if (rec.b) {
+      cudaEventRecord(rec.b, ctx->stream);
+      ctx->gemm_recs.push_back(rec);
+    }
     return launch_check(ctx, "gemm_kernel");
   };
   if (A2 && B2) {
@@ -969,4 +979,28 @@ extern "C" dlm_status dlm_gemm_bf16(dlm_ctx* ctx, const void* A, const void* B, 
   if (N % 256 == 0)
     return gemm<256>(ctx, (const bf16*)A, nullptr, M, K, K, (const bf16*)B, nullptr, N, K, 0, EpiPlain{C, N, M, 1.f, nullptr});
   return gemm<64>(ctx, (const bf16*)A, nullptr, M, K, K, (const bf16*)B, nullptr, N, K, 0, EpiPlain{C, N, M, 1.f, nullptr});
+}
+
+extern "C" dlm_status dlm_gemm_profile(dlm_ctx* ctx, int32_t enable) {
+  if (!ctx) return DLM_EINVAL;
+  ctx->gemm_prof = enable != 0;
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_gemm_profile_read(dlm_ctx* ctx, double* ms, double* flops, int64_t* launches) {
+  if (!ctx || !ms || !flops || !launches) return fail(ctx, DLM_EINVAL, "gemm_profile_read: null argument");
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double t = 0.0, f = 0.0;
+  for (auto& r : ctx->gemm_recs) {
+    float e = 0.f;
+    if (cudaEventElapsedTime(&e, r.a, r.b) == cudaSuccess) t += e;
+    f += r.flops;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  *ms = t;
+  *flops = f;
+  *launches = (int64_t)ctx->gemm_recs.size();
+  ctx->gemm_recs.clear();
+  return DLM_OK;
 }

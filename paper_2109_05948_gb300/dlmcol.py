@@ -82,6 +82,8 @@ _SIGS = {
     "dlm_memetic_set": (_i32, [_P, _P, _i32, _P]),
     "dlm_probe_smem_bandwidth": (_i32, [_P, _P]),
     "dlm_gemm_bf16": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32]),
+    "dlm_gemm_profile": (_i32, [_P, _i32]),
+    "dlm_gemm_profile_read": (_i32, [_P, _P, _P, _P]),
     "dlm_wvcp_tabu_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32]),
     "dlm_wvcp_tabu_batch_ex": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32, _P]),
     "dlm_wvcp_greedy": (_i32, [_P, _P, _i32, _u64, _u32, _P, _P]),
@@ -346,6 +348,18 @@ def dlm_memetic_set(ctx, mm, which, src):
 
 def dlm_gemm_bf16(ctx, A, B, C, M, N, K):
     ctx.check(lib().dlm_gemm_bf16(ctx.h, _ptr(A), _ptr(B), _ptr(C), M, N, K), "dlm_gemm_bf16")
+
+
+def dlm_gemm_profile(ctx, enable):
+    ctx.check(lib().dlm_gemm_profile(ctx.h, 1 if enable else 0), "dlm_gemm_profile")
+
+
+def dlm_gemm_profile_read(ctx):
+    """(summed GEMM launch ms, executed tensor-core FLOPs, launches) since the last read."""
+    ms, fl, n = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int64(0)
+    ctx.check(lib().dlm_gemm_profile_read(ctx.h, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)),
+              "dlm_gemm_profile_read")
+    return ms.value, fl.value, n.value
 
 
 def dlm_probe_smem_bandwidth(ctx):
