@@ -46,6 +46,14 @@ typedef struct dlm_memetic dlm_memetic;
 dlm_status dlm_create(dlm_ctx** out, int32_t device, void* stream);
 void dlm_destroy(dlm_ctx* ctx);
 dlm_status dlm_set_stream(dlm_ctx* ctx, void* stream);
+/* Cancellation (no counterpart in the paper): flag is a device-readable int32 (device or managed
+ * memory, or pinned host memory, which is polled through its device mapping) or NULL to disable;
+ * pageable host memory returns DLM_EINVAL. The TabuCol kernels launched
+ * afterwards through ctx (batch, uneven batch, plans created afterwards) read it every 1024
+ * iterations of each individual; once it is nonzero each search stops after the current
+ * iteration's selection, writes its best colouring and conflicts so far, and dlm_sync returns
+ * DLM_ECANCELLED. The caller owns the flag and keeps it valid while such launches run. */
+dlm_status dlm_set_cancel_flag(dlm_ctx* ctx, const int32_t* flag);
 /* Text of the last error on this context (valid until the next call on it). */
 const char* dlm_last_error(const dlm_ctx* ctx);
 /* Waits for the context's stream and returns (then clears) the device-side status. */
@@ -116,7 +124,7 @@ dlm_status dlm_tabucol_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_
                              int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                              uint32_t generation, uint32_t ind_base);
 
-/* As dlm_tabucol_batch, with warps_per_individual forced (1, 2, 4 or 8; 0 = autotuned), an
+/* As dlm_tabucol_batch, with warps_per_individual forced (1, 2, 4, 8 or 16; 0 = autotuned), an
  * optional per-iteration trace -- device [pop][iters][4] int32 of (v, c, delta, #tied moves),
  * (-1, -1, 0, 0) for an iteration without a move, entries after an early stop untouched -- and an
  * optional work count -- device [pop][2] int64: the number of conflicting rows scanned and the sum
@@ -169,7 +177,7 @@ dlm_status dlm_tabucol_multi_plan_create(dlm_ctx* ctx, int32_t n_graphs, const d
 dlm_status dlm_tabucol_multi_plan_launch(dlm_ctx* ctx, dlm_multi_plan* plan);
 void dlm_tabucol_multi_plan_destroy(dlm_multi_plan* plan);
 
-/* Autotuner for the tabu kernel: times warps_per_individual in {1, 2, 4, 8} on a short run of
+/* Autotuner for the tabu kernel: times warps_per_individual in {1, 2, 4, 8, 16} on a short run of
  * the given problem and caches the fastest for (n, k) in the context; returns it in *best. */
 dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,
                                 int32_t* best);
@@ -236,6 +244,12 @@ dlm_status dlm_scorer_loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* col,
  * tag = BATCH).r0 (ties by i). */
 dlm_status dlm_scorer_train(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const int64_t* fvals, int32_t p,
                             int32_t epochs, int32_t b, float lr, uint64_t seed, uint32_t generation);
+/* Scorer state to or from caller-owned host memory of dlm_scorer_state_bytes bytes: parameters,
+ * Adam first and second moments (nparams float32 each) and the Adam step counter (int64). Both
+ * wait for the copies; load also refreshes the bf16 weight copies the forward pass reads. */
+int64_t dlm_scorer_state_bytes(const dlm_scorer* s);
+dlm_status dlm_scorer_save(dlm_ctx* ctx, dlm_scorer* s, void* host);
+dlm_status dlm_scorer_load(dlm_ctx* ctx, dlm_scorer* s, const void* host);
 
 /* ---------------------------------------------------------------------------------------------
  * Memetic loop (Algorithm 1). dlm_memetic_step runs one generation: TabuCol on every offspring,
@@ -267,6 +281,18 @@ dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* best_f_host)
 dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, void* dst);
 /* Overwrites the population state (which = 0..3 as above) from device memory src. */
 dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const void* src);
+
+/* Checkpoint and resume (the paper runs last up to 138 h and describes no checkpoint; this is
+ * the state Algorithm 1 carries from one generation to the next). dlm_memetic_state_bytes gives
+ * the size of the blob; dlm_memetic_save writes it to caller-owned host memory (a 64-byte header
+ * with the configuration and the generation counter, then P, f(P), D(P,P), the offspring S^O,
+ * f(S*) and S*, and, with the scorer, its parameters, Adam moments and step counter) and waits;
+ * dlm_memetic_load restores it into an object created with the same n, k, p, K and use_scorer
+ * (DLM_EINVAL otherwise) and waits. Every random draw is keyed by (seed, individual, generation,
+ * iteration), so a resumed run continues bit-identically to an uninterrupted one. */
+int64_t dlm_memetic_state_bytes(const dlm_memetic* mm);
+dlm_status dlm_memetic_save(dlm_ctx* ctx, dlm_memetic* mm, void* host);
+dlm_status dlm_memetic_load(dlm_ctx* ctx, dlm_memetic* mm, const void* host);
 
 /* ---------------------------------------------------------------------------------------------
  * Weighted vertex colouring (WVCP; Eq. score_WVCP: f(S) = sum over classes of the largest vertex

@@ -85,6 +85,8 @@ struct dlm_ctx {
   struct GemmRec { cudaEvent_t a, b; double flops; };
   bool gemm_prof = false;
   std::vector<GemmRec> gemm_recs;
+  // cancellation flag polled by the long-running search kernels (dlm_set_cancel_flag)
+  const int32_t* cancel = nullptr;
 };
 
 struct dlm_graph {

@@ -169,6 +169,35 @@ dlm_status dlm_set_stream(dlm_ctx* ctx, void* stream) {
   return DLM_OK;
 }
 
+dlm_status dlm_set_cancel_flag(dlm_ctx* ctx, const int32_t* flag) {
+  if (!ctx) return DLM_EINVAL;
+  if (!flag) {
+    ctx->cancel = nullptr;
+    return DLM_OK;
+  }
+  // only memory the device can address: device or managed memory as is, pinned host memory
+  // through its device alias; pageable host memory is refused
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, flag) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DLM_EINVAL, "set_cancel_flag: pointer unknown to CUDA");
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    ctx->cancel = flag;
+    return DLM_OK;
+  }
+  if (at.type == cudaMemoryTypeHost) {
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, (void*)flag, 0) != cudaSuccess || !d) {
+      cudaGetLastError();
+      return fail(ctx, DLM_EINVAL, "set_cancel_flag: pinned host memory without a device mapping");
+    }
+    ctx->cancel = (const int32_t*)d;
+    return DLM_OK;
+  }
+  return fail(ctx, DLM_EINVAL, "set_cancel_flag: pageable host memory cannot be polled by the device");
+}
+
 const char* dlm_last_error(const dlm_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
 
 dlm_status dlm_sync(dlm_ctx* ctx) {

@@ -4,6 +4,7 @@
 // matrix -> K nearest neighbours -> GPX offspring (best-scored of K, or one random neighbour).
 #include <algorithm>
 #include <climits>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -287,5 +288,93 @@ extern "C" dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t whi
     default: return fail(ctx, DLM_EINVAL, "memetic_set: unknown array");
   }
   DLM_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return DLM_OK;
+}
+
+// ---- checkpoint: the state carried from one generation to the next ------------------------------
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t n, k, p, K, use_scorer, reserved;
+  uint32_t gen, reserved2;
+  int64_t scorer_bytes;
+  int64_t total;
+  uint8_t pad[8];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+constexpr char kMagic[8] = {'D', 'L', 'M', 'M', 'E', 'M', '0', '1'};
+
+inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct CkptLayout {
+  size_t P, fP, DP, SO, best_f, best_col, scorer, total;
+};
+
+CkptLayout ckpt_layout(const dlm_memetic* mm) {
+  const size_t p = (size_t)mm->prm.p, n = (size_t)mm->n;
+  CkptLayout L;
+  size_t o = sizeof(CkptHeader);
+  L.P = o; o += a16(p * n * 2);
+  L.fP = o; o += a16(p * 8);
+  L.DP = o; o += a16(p * p * 2);
+  L.SO = o; o += a16(p * n * 2);
+  L.best_f = o; o += 16;
+  L.best_col = o; o += a16(n * 2);
+  L.scorer = o; o += a16(mm->scorer ? (size_t)dlm_scorer_state_bytes(mm->scorer) : 0);
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+extern "C" int64_t dlm_memetic_state_bytes(const dlm_memetic* mm) {
+  return mm ? (int64_t)ckpt_layout(mm).total : 0;
+}
+
+extern "C" dlm_status dlm_memetic_save(dlm_ctx* ctx, dlm_memetic* mm, void* host) {
+  if (!ctx || !mm || !host) return fail(ctx, DLM_EINVAL, "memetic_save: null argument");
+  const CkptLayout L = ckpt_layout(mm);
+  uint8_t* h = (uint8_t*)host;
+  const size_t p = (size_t)mm->prm.p, n = (size_t)mm->n;
+  CkptHeader H{};
+  memcpy(H.magic, kMagic, 8);
+  H.n = mm->n; H.k = mm->prm.k; H.p = mm->prm.p; H.K = mm->prm.K; H.use_scorer = mm->prm.use_scorer;
+  H.gen = mm->gen;
+  H.scorer_bytes = mm->scorer ? dlm_scorer_state_bytes(mm->scorer) : 0;
+  H.total = (int64_t)L.total;
+  cudaStream_t s = ctx->stream;
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + L.P, mm->P, p * n * 2, cudaMemcpyDeviceToHost, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + L.fP, mm->fP, p * 8, cudaMemcpyDeviceToHost, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + L.DP, mm->DP, p * p * 2, cudaMemcpyDeviceToHost, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + L.SO, mm->SO, p * n * 2, cudaMemcpyDeviceToHost, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + L.best_f, mm->best_f, 8, cudaMemcpyDeviceToHost, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + L.best_col, mm->best_col, n * 2, cudaMemcpyDeviceToHost, s));
+  DLM_CUDA(ctx, cudaStreamSynchronize(s));
+  if (mm->scorer) DLM_TRY(dlm_scorer_save(ctx, mm->scorer, h + L.scorer));
+  memcpy(h, &H, sizeof(H));
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_memetic_load(dlm_ctx* ctx, dlm_memetic* mm, const void* host) {
+  if (!ctx || !mm || !host) return fail(ctx, DLM_EINVAL, "memetic_load: null argument");
+  const CkptLayout L = ckpt_layout(mm);
+  const uint8_t* h = (const uint8_t*)host;
+  CkptHeader H;
+  memcpy(&H, h, sizeof(H));
+  if (memcmp(H.magic, kMagic, 8) != 0) return fail(ctx, DLM_EINVAL, "memetic_load: not a memetic checkpoint");
+  if (H.n != mm->n || H.k != mm->prm.k || H.p != mm->prm.p || H.K != mm->prm.K ||
+      H.use_scorer != mm->prm.use_scorer || H.total != (int64_t)L.total ||
+      H.scorer_bytes != (mm->scorer ? dlm_scorer_state_bytes(mm->scorer) : 0))
+    return fail(ctx, DLM_EINVAL, "memetic_load: checkpoint of another configuration");
+  const size_t p = (size_t)mm->prm.p, n = (size_t)mm->n;
+  cudaStream_t s = ctx->stream;
+  DLM_CUDA(ctx, cudaMemcpyAsync(mm->P, h + L.P, p * n * 2, cudaMemcpyHostToDevice, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(mm->fP, h + L.fP, p * 8, cudaMemcpyHostToDevice, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(mm->DP, h + L.DP, p * p * 2, cudaMemcpyHostToDevice, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(mm->SO, h + L.SO, p * n * 2, cudaMemcpyHostToDevice, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(mm->best_f, h + L.best_f, 8, cudaMemcpyHostToDevice, s));
+  DLM_CUDA(ctx, cudaMemcpyAsync(mm->best_col, h + L.best_col, n * 2, cudaMemcpyHostToDevice, s));
+  DLM_CUDA(ctx, cudaStreamSynchronize(s));
+  if (mm->scorer) DLM_TRY(dlm_scorer_load(ctx, mm->scorer, h + L.scorer));
+  mm->gen = H.gen;
   return DLM_OK;
 }

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -1002,5 +1003,36 @@ extern "C" dlm_status dlm_gemm_profile_read(dlm_ctx* ctx, double* ms, double* fl
   *flops = f;
   *launches = (int64_t)ctx->gemm_recs.size();
   ctx->gemm_recs.clear();
+  return DLM_OK;
+}
+
+extern "C" int64_t dlm_scorer_state_bytes(const dlm_scorer* s) { return s ? 3 * s->np * 4 + 8 : 0; }
+
+// theta, Adam m, Adam v (np float32 each) and the Adam step counter, to or from host memory
+extern "C" dlm_status dlm_scorer_save(dlm_ctx* ctx, dlm_scorer* s, void* host) {
+  if (!ctx || !s || !host) return fail(ctx, DLM_EINVAL, "scorer_save: null argument");
+  uint8_t* h = (uint8_t*)host;
+  const size_t b = (size_t)s->np * 4;
+  DLM_CUDA(ctx, cudaMemcpyAsync(h, s->theta, b, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + b, s->am, b, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + 2 * b, s->av, b, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  memcpy(h + 3 * b, &s->t, 8);
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_scorer_load(dlm_ctx* ctx, dlm_scorer* s, const void* host) {
+  if (!ctx || !s || !host) return fail(ctx, DLM_EINVAL, "scorer_load: null argument");
+  const uint8_t* h = (const uint8_t*)host;
+  const size_t b = (size_t)s->np * 4;
+  int64_t t = 0;
+  memcpy(&t, h + 3 * b, 8);
+  if (t < 0) return fail(ctx, DLM_EINVAL, "scorer_load: negative Adam step counter");
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->theta, h, b, cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->am, h + b, b, cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->av, h + 2 * b, b, cudaMemcpyHostToDevice, ctx->stream));
+  s->t = t;
+  DLM_TRY(convert_params(ctx, s));
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return DLM_OK;
 }

@@ -50,6 +50,7 @@ struct TabuRule {
   size_t budget;         // shared-memory bytes of the launch
   uint16_t* slab;        // spilled rows, slab_stride u16 per CTA (null when nothing spills)
   size_t slab_stride;
+  const int32_t* cancel; // device-readable flag, nonzero = stop (null: never)
 };
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
@@ -63,8 +64,15 @@ __host__ __device__ inline int tabu_row_stride(int k) {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Rows a warp's threads scan in one iteration: items [32 w C, 32 (w + 1) C) of the (row, segment)
+// list, C = ceil(items / threads) <= ceil(n / threads), hence at most 32 C + 1 rows.
+__host__ __device__ inline int tabu_list_cap(int n, int warps) {
+  const int nt = 32 * warps;
+  return 32 * ((n + nt - 1) / nt) + 1;
+}
+
 struct TabuSmem {
-  size_t gam, tab, col, best, rowres, deg, cvl, cv, red, total;
+  size_t gam, tab, col, best, rowres, deg, cvl, cv, red, rnd, total;
   int rs;  // rows of gamma and tab held in shared memory; rows rs..n-1 live in the CTA's slab
 };
 
@@ -76,11 +84,12 @@ __host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps, si
   size_t o = 0;
   s.col = o; o += align16(n);
   s.best = o; o += align16(n);
-  s.rowres = o; o += align16((size_t)(n > 256 ? n : 256) * 4);
+  s.rowres = o; o += align16((size_t)(n > 32 * warps ? n : 32 * warps) * 4);  // items <= max(n, threads)
   s.deg = o; o += align16((size_t)n * 2);
-  s.cvl = o; o += align16((size_t)warps * n * 2);
+  s.cvl = o; o += align16((size_t)warps * tabu_list_cap(n, warps) * 2);
   s.cv = o; o += 64 * 4;
   s.red = o; o += align16((size_t)warps * 8 + 64);
+  s.rnd = o; o += 32 * 8;
   const size_t row = (size_t)ks * 2;
   size_t rs = budget > o + 32 ? (budget - o - 32) / (2 * row) : 0;
   if (rs > (size_t)n) rs = n;
@@ -113,18 +122,23 @@ __device__ __forceinline__ int nth_set_bit64(uint64_t x, int r) {
   return r < pl ? nth_set_bit(lo, r) : 32 + nth_set_bit((uint32_t)(x >> 32), r - pl);
 }
 
-// Warp view of the conflicting-vertex bitmap: lane l owns bitmap words 2l and 2l+1 (vertices
-// 64l .. 64l+63), its popcount and the exclusive prefix over lanes (= rank of its first vertex).
+// Warp view of the conflicting-vertex bitmap: lane l owns the B = 2^lb bits of vertices
+// lB .. lB + B - 1 (B the smallest power of two with 32 B >= n, so the work spreads over all
+// lanes), its popcount and the exclusive prefix over lanes (= rank of its first vertex).
 struct CvView {
   uint64_t w;
   int cnt, excl, total;
 };
 
-__device__ __forceinline__ CvView cv_view(const uint32_t* cv, int nwords, int lane) {
+__device__ __forceinline__ CvView cv_view(const uint32_t* cv, int lb, int lane) {
   CvView c;
-  const uint32_t lo = (2 * lane < nwords) ? cv[2 * lane] : 0u;
-  const uint32_t hi = (2 * lane + 1 < nwords) ? cv[2 * lane + 1] : 0u;
-  c.w = ((uint64_t)hi << 32) | lo;
+  const int o = lane << lb;
+  if (lb == 6) {
+    c.w = ((uint64_t)cv[2 * lane + 1] << 32) | cv[2 * lane];
+  } else {
+    const uint32_t word = cv[o >> 5];
+    c.w = lb == 5 ? word : (word >> (o & 31)) & ((1u << (1 << lb)) - 1u);
+  }
   c.cnt = __popcll(c.w);
   int incl = c.cnt;
 #pragma unroll
@@ -179,41 +193,56 @@ __device__ __forceinline__ int seg_find(const uint32_t* g32, const uint32_t* t32
   return -1;
 }
 
-// One individual, one CTA of W warps.
+// One individual, one CTA of W warps (SPILL: rows beyond the shared-memory budget live in the
+// CTA's global slab).
 // Per iteration: (1) every warp compacts the conflicting-vertex bitmap into its own list; the rows
 // are cut into S contiguous segments (S = threads / |CV| when there are fewer rows than threads)
 // and thread t scans items [tC, tC + C) of the (row, segment) list, keeping per-item (min delta,
 // #ties) and its own aggregate; (2) one barrier publishes the per-warp minima and tie counts:
 // every thread derives the minimum delta, the total T and its own rank range, and the thread that
 // holds the j-th tie (j drawn from the iteration's Philox block) applies the move; (3) all
-// threads update gamma on the neighbours. Three barriers per iteration.
+// threads update gamma on the neighbours. Three barriers per iteration. The Philox blocks of 32
+// iterations are drawn at once, one per lane, by one warp every 32 iterations.
 //
 // Tabu list: u16 expiries relative to a base that advances by 2^14 every 2^14 iterations
 // (t' = expiry - base, 0 = free); a pair is tabu when t' > it - base.
-template <int W>
+template <int W, bool SPILL>
 __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t* smem) {
   constexpr int NT = 32 * W;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = J.n, k = J.k, ks = J.ks, kw = ks / 2, nwords = J.words;
   const TabuSmem L = tabu_smem_layout(n, k, W, R.budget);
-  const int rs = L.rs;
+  const int rs = SPILL ? L.rs : n;
   uint16_t* gam = (uint16_t*)(smem + L.gam);
   uint16_t* tab = (uint16_t*)(smem + L.tab);
-  uint16_t* gslab = R.slab ? R.slab + (size_t)blockIdx.x * R.slab_stride : nullptr;
-  uint16_t* tslab = gslab ? gslab + (size_t)(n - rs) * ks : nullptr;
+  uint16_t* gslab = SPILL ? R.slab + (size_t)blockIdx.x * R.slab_stride : nullptr;
+  uint16_t* tslab = SPILL ? gslab + (size_t)(n - rs) * ks : nullptr;
   // row v of gamma / tab: shared memory for v < rs, the CTA's global slab beyond
-  auto grow_of = [&](int v) -> uint16_t* { return v < rs ? gam + (size_t)v * ks : gslab + (size_t)(v - rs) * ks; };
-  auto trow_of = [&](int v) -> uint16_t* { return v < rs ? tab + (size_t)v * ks : tslab + (size_t)(v - rs) * ks; };
+  auto grow_of = [&](int v) -> uint16_t* {
+    if (!SPILL) return gam + v * ks;
+    return v < rs ? gam + (size_t)v * ks : gslab + (size_t)(v - rs) * ks;
+  };
+  auto trow_of = [&](int v) -> uint16_t* {
+    if (!SPILL) return tab + v * ks;
+    return v < rs ? tab + (size_t)v * ks : tslab + (size_t)(v - rs) * ks;
+  };
   uint8_t* colS = smem + L.col;
   uint8_t* bestS = smem + L.best;
   uint32_t* rowres = (uint32_t*)(smem + L.rowres);
   uint16_t* degS = (uint16_t*)(smem + L.deg);
-  uint16_t* cvl = (uint16_t*)(smem + L.cvl) + (size_t)warp * n;
+  uint16_t* cvl = (uint16_t*)(smem + L.cvl) + (size_t)warp * tabu_list_cap(n, W);
   uint32_t* cv = (uint32_t*)(smem + L.cv);
   int32_t* red = (int32_t*)(smem + L.red);   // [W] warp minima, [W] warp tie totals
   int32_t* sc = red + 2 * W;                 // scalars
+  uint32_t* rnd = (uint32_t*)(smem + L.rnd); // Philox words (r0, r1) of the next 32 iterations
   // sc[0] moved vertex (-1 none), sc[1] old colour, sc[2] new colour, sc[3] f after,
-  // sc[4] improved, sc[5] error, sc[6] bad input, sc[7] r0, sc[8] r1
+  // sc[4] improved, sc[5] error, sc[6] bad input
+  const int iters = (int)J.iters;  // at most 2^31 - 1 (checked by the host)
+  auto draw32 = [&](int it0) {     // one warp: lane l draws the block of iteration it0 + l
+    const U4 r = rng(R.seed, (uint32_t)(it0 + lane), R.gen, J.ind, kTagTabu);
+    rnd[2 * lane] = r.x;
+    rnd[2 * lane + 1] = r.y;
+  };
 
   // ---- set-up: zero the tables (padding colours of gamma = 0xFFFF), load the start colouring --
   {
@@ -226,6 +255,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     }
     if (tid < 16) sc[tid] = 0;
     for (int i = tid; i < 64; i += NT) cv[i] = 0u;
+    if (warp == W - 1) draw32(0);
   }
   __syncthreads();
   for (int v = tid; v < n; v += NT) {
@@ -277,8 +307,8 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     __syncthreads();
   }
   int best_f = f;
-  int64_t moves = 0;
-  int64_t it = 0;
+  int moves = 0;
+  int it = 0;
   int64_t work_rows = 0, work_deg = 0;  // kept by thread 0 only
 
   // per-thread slice of a bit row for the gamma update
@@ -289,39 +319,53 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     per = p2 > 32 ? 32 : p2;
   }
   const uint32_t slice_mask = per == 32 ? 0xFFFFFFFFu : ((1u << per) - 1u);
+  const float fNT = (float)NT + 0.5f;
+  int lb = 0;  // bitmap bits per lane = 2^lb, 32 * 2^lb >= n (n <= 2048)
+  while ((32 << lb) < n) ++lb;
 
-  for (it = 0; it < J.iters; ++it) {
+  for (it = 0; it < iters; ++it) {
     if (f == 0) break;
     const unsigned itrel = (unsigned)(it & 0x3FFF);
     // ---- phase 1: conflicting-vertex list of this warp, scan of this thread's items ----------
-    const CvView view = cv_view(cv, nwords, lane);
-    {
-      uint64_t wb = view.w;
-      int pos = view.excl;
-      while (wb) {
-        cvl[pos++] = (uint16_t)(64 * lane + __ffsll(wb) - 1);
-        wb &= wb - 1;
-      }
-    }
-    __syncwarp();
+    const CvView view = cv_view(cv, lb, lane);
     const int ncv = view.total;
     if (tid == 0) {
       work_rows += ncv;
-      const U4 r = rng(R.seed, (uint32_t)it, R.gen, J.ind, kTagTabu);
-      sc[7] = (int32_t)r.x;
-      sc[8] = (int32_t)r.y;
       sc[0] = -1;
+      // cancellation, polled every 1024 iterations: the search stops after this iteration's
+      // selection and reports its best colouring so far
+      if ((it & 1023) == 0 && R.cancel && *(volatile const int32_t*)R.cancel != 0) sc[5] = 3;
     }
-    const int S = (ncv >= NT || ncv == 0) ? 1 : min(kw, NT / ncv);
-    const int Lw = (kw + S - 1) / S;
+    // S = min(kw, floor(NT / ncv)) and Lw = ceil(kw / S) in float arithmetic: both quotients are
+    // of integers below 2^16 shifted by one half, far from the next integer compared with the
+    // rounding error, so the truncations are exact
+    int S = 1;
+    if (ncv > 0 && ncv < NT) S = min(kw, (int)(fNT / (float)ncv));
+    const float rS = 1.0f / (float)S;
+    const int Lw = (int)(((float)(kw + S - 1) + 0.5f) * rS);
     const int items = ncv * S;
     const int C = (items + NT - 1) / NT;
     const int i0 = tid * C;
     const int i1 = min(i0 + C, items);
+    // this warp's rows [rlo, rhi] of the conflicting-vertex list, compacted from the bitmap in
+    // ascending vertex order (rank = position among the conflicting vertices)
+    const int wi0 = 32 * warp * C, wi1 = min(wi0 + 32 * C, items);
+    const int rlo = S == 1 ? wi0 : (int)(((float)wi0 + 0.5f) * rS);
+    const int rhi = wi1 <= wi0 ? rlo - 1 : (S == 1 ? wi1 - 1 : (int)(((float)(wi1 - 1) + 0.5f) * rS));
+    if (view.excl <= rhi && view.excl + view.cnt > rlo) {
+      uint64_t wb = view.w;
+      int rank = view.excl;
+      while (wb && rank <= rhi) {
+        if (rank >= rlo) cvl[rank - rlo] = (uint16_t)((lane << lb) + __ffsll(wb) - 1);
+        wb &= wb - 1;
+        ++rank;
+      }
+    }
+    __syncwarp();
     int tmin = INT_MAX, tcnt = 0;
     for (int i = i0; i < i1; ++i) {
-      const int r = i / S, sg = i - r * S;
-      const int v = cvl[r];
+      const int r = S == 1 ? i : (int)(((float)i + 0.5f) * rS), sg = i - r * S;
+      const int v = cvl[r - rlo];
       const int colv = colS[v];
       const uint16_t* grow = grow_of(v);
       const int g0 = grow[colv];
@@ -345,27 +389,42 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     }
     __syncthreads();
     // ---- phase 2: minimum delta, tie ranks, move ---------------------------------------------
+    int wmin[W], wcnt[W];
+    if constexpr (W % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        const int4 a = reinterpret_cast<const int4*>(red)[q];
+        const int4 b = reinterpret_cast<const int4*>(red + W)[q];
+        wmin[4 * q] = a.x; wmin[4 * q + 1] = a.y; wmin[4 * q + 2] = a.z; wmin[4 * q + 3] = a.w;
+        wcnt[4 * q] = b.x; wcnt[4 * q + 1] = b.y; wcnt[4 * q + 2] = b.z; wcnt[4 * q + 3] = b.w;
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < W; ++w) { wmin[w] = red[w]; wcnt[w] = red[W + w]; }
+    }
     int dstar = INT_MAX;
 #pragma unroll
-    for (int w = 0; w < W; ++w) dstar = min(dstar, red[w]);
-    int T = 0, pre = 0;
+    for (int w = 0; w < W; ++w) dstar = min(dstar, wmin[w]);
+    int T = 0, pre = 0, wtot = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      const int x = (dstar != INT_MAX && red[w] == dstar) ? red[W + w] : 0;
+      const int x = (dstar != INT_MAX && wmin[w] == dstar) ? wcnt[w] : 0;
       T += x;
       pre += w < warp ? x : 0;
+      wtot += w == warp ? x : 0;
     }
-    const int ct = (dstar != INT_MAX && tmin == dstar) ? tcnt : 0;
-    int incl = ct;
+    const uint32_t r0 = rnd[2 * (it & 31)];
+    const uint32_t j = T > 0 ? below(r0, (uint32_t)T) : 0u;
+    if (T > 0 && (int)j >= pre && (int)j < pre + wtot) {  // the j-th tie is in this warp
+      const int ct = (dstar != INT_MAX && tmin == dstar) ? tcnt : 0;
+      int incl = ct;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int t = __shfl_up_sync(FULL, incl, d);
-      if (lane >= d) incl += t;
-    }
-    if (T > 0 && ct > 0) {
-      const uint32_t j = below((uint32_t)sc[7], (uint32_t)T);
+      for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += t;
+      }
       const int lo = pre + incl - ct;
-      if ((int)j >= lo && (int)j < lo + ct) {  // this thread holds the j-th tied move
+      if (ct > 0 && (int)j >= lo && (int)j < lo + ct) {  // this thread holds the j-th tied move
         int jj = (int)j - lo;
         int mv = -1, mc = -1;
         for (int i = i0; i < i1; ++i) {
@@ -373,8 +432,8 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           const int rm = (int16_t)(rr >> 16), rcn = (int)(rr & 0xFFFF);
           if (rm != dstar || rcn == 0) continue;
           if (jj >= rcn) { jj -= rcn; continue; }
-          const int r = i / S, sg = i - r * S;
-          const int v = cvl[r];
+          const int r = S == 1 ? i : (int)(((float)i + 0.5f) * rS), sg = i - r * S;
+          const int v = cvl[r - rlo];
           const int colv = colS[v];
           const uint16_t* grow = grow_of(v);
           const int g0 = grow[colv];
@@ -388,9 +447,10 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           const int old = colS[mv];
           colS[mv] = (uint8_t)mc;
           const int fn = f + dstar;
-          const int64_t tt = (int64_t)below((uint32_t)sc[8], R.L1) + ((int64_t)R.an * fn) / R.ad;
-          if (tt > 32766) sc[5] = 1;
-          trow_of(mv)[old] = (uint16_t)(itrel + 1 + tt);
+          // alpha f in 32-bit unsigned arithmetic: the host bounds alpha_num * |E| below 2^32
+          const uint32_t tt = below(rnd[2 * (it & 31) + 1], R.L1) + ((uint32_t)R.an * (uint32_t)fn) / (uint32_t)R.ad;
+          if (tt > 32766u) sc[5] = 1;
+          trow_of(mv)[old] = (uint16_t)(itrel + 1u + tt);
           const uint32_t bit = 1u << (mv & 31);
           if (grow_of(mv)[mc] > 0) atomicOr(cv + (mv >> 5), bit);
           else atomicAnd(cv + (mv >> 5), ~bit);
@@ -434,6 +494,9 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
         for (int i = tid; i < (n + 3) / 4; i += NT) d32[i] = s32[i];
       }
     }
+    // the Philox block of the next 32 iterations (every reader of the current one has passed
+    // the barrier above)
+    if (((it + 1) & 31) == 0 && warp == W - 1) draw32(it + 1);
     if (((it + 1) & 0x3FFF) == 0) {
       // the base advances by 2^14: relative expiries drop by 2^14, expired ones become 0
       for (int i = tid; i < n * kw; i += NT) {
@@ -447,7 +510,8 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     __syncthreads();
   }
   if (sc[5]) {
-    if (tid == 0) raise_status(R.status, sc[5] == 1 ? DLM_EUNSUPPORTED : DLM_ECUDA);
+    if (tid == 0)
+      raise_status(R.status, sc[5] == 1 ? DLM_EUNSUPPORTED : (sc[5] == 3 ? DLM_ECANCELLED : DLM_ECUDA));
   }
   __syncthreads();
   for (int v = tid; v < n; v += NT) J.col[v] = (int16_t)bestS[v];
@@ -487,7 +551,8 @@ __global__ void __launch_bounds__(W * 32) tabucol_batch_kernel(TabuBatchArgs a) 
     J.off = a.off;
     J.iters = a.iters;
     J.ind = a.ind_base + (uint32_t)i;
-    tabucol_individual<W>(J, a.rule, smem);
+    if (a.rule.slab) tabucol_individual<W, true>(J, a.rule, smem);
+    else tabucol_individual<W, false>(J, a.rule, smem);
     __syncthreads();
   }
 }
@@ -519,7 +584,8 @@ __global__ void __launch_bounds__(W * 32) tabucol_multi_kernel(const MultiJob* j
     J.n = M.n; J.k = M.k; J.ks = M.ks; J.words = M.words; J.bits = M.bits; J.col = M.col;
     J.best_f = M.best_f; J.moves = M.moves; J.trace = nullptr; J.work = nullptr; J.off = nullptr;
     J.iters = M.iters; J.ind = M.ind;
-    tabucol_individual<W>(J, rule, smem);
+    if (rule.slab) tabucol_individual<W, true>(J, rule, smem);
+    else tabucol_individual<W, false>(J, rule, smem);
     __syncthreads();
   }
 }
@@ -567,6 +633,9 @@ static dlm_status tabucol_check(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
   if (pop < 0 || iters < 0) return fail(ctx, DLM_EINVAL, "tabucol: negative population or budget");
   if (iters > INT32_MAX) return fail(ctx, DLM_EINVAL, "tabucol: budget above 2^31");
   if (t.L_max < 0 || t.alpha_num < 0 || t.alpha_den <= 0) return fail(ctx, DLM_EINVAL, "tabucol: bad tenure");
+  // the kernel forms alpha_num * f in 32-bit unsigned arithmetic (f <= |E|)
+  if ((uint64_t)t.alpha_num * (uint64_t)g->m >= (1ull << 32))
+    return fail(ctx, DLM_EUNSUPPORTED, "tabucol: alpha_num * |E| must be below 2^32");
   return DLM_OK;
 }
 
@@ -579,8 +648,8 @@ static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32
   if (!col || !best_f) return fail(ctx, DLM_EINVAL, "tabucol: null col or best_f");
   if (warps == 0) warps = lookup_tune(ctx, g->n, k);
   if (warps == 0) warps = default_warps(g->n, k);
-  if (warps != 1 && warps != 2 && warps != 4 && warps != 8)
-    return fail(ctx, DLM_EINVAL, "tabucol: warps per individual must be 1, 2, 4 or 8");
+  if (warps != 1 && warps != 2 && warps != 4 && warps != 8 && warps != 16)
+    return fail(ctx, DLM_EINVAL, "tabucol: warps per individual must be 1, 2, 4, 8 or 16");
   const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
   if (L.rs < 1 || L.total > ctx->smem_optin)
     return fail(ctx, DLM_EUNSUPPORTED, "tabucol: the per-individual arrays exceed shared memory per block");
@@ -591,12 +660,13 @@ static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32
   a.work = work; a.iters = iters;
   a.ind_base = ind_base;
   a.rule = TabuRule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
-                    ctx->smem_optin, nullptr, 0};
+                    ctx->smem_optin, nullptr, 0, ctx->cancel};
   switch (warps) {
     case 1: return launch_batch<1>(ctx, a, L.total, slab_stride);
     case 2: return launch_batch<2>(ctx, a, L.total, slab_stride);
     case 4: return launch_batch<4>(ctx, a, L.total, slab_stride);
-    default: return launch_batch<8>(ctx, a, L.total, slab_stride);
+    case 8: return launch_batch<8>(ctx, a, L.total, slab_stride);
+    default: return launch_batch<16>(ctx, a, L.total, slab_stride);
   }
 }
 
@@ -637,9 +707,9 @@ extern "C" dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int
   cudaEventCreate(&e1);
   float best_ms = 1e30f;
   int best_w = default_warps(g->n, k);
-  const int cand[4] = {1, 2, 4, 8};
+  const int cand[5] = {1, 2, 4, 8, 16};
   dlm_status st = DLM_OK;
-  for (int c = 0; c < 4 && st == DLM_OK; ++c) {
+  for (int c = 0; c < 5 && st == DLM_OK; ++c) {
     const TabuSmem L = tabu_smem_layout(g->n, k, cand[c], ctx->smem_optin);
     if (L.total > ctx->smem_optin) continue;
     float ms_sum = 0.f;
@@ -717,7 +787,7 @@ extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dl
   });
   const size_t job_bytes = align16(jobs.size() * sizeof(MultiJob));
   TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
-                ctx->smem_optin, nullptr, slab_stride};
+                ctx->smem_optin, nullptr, slab_stride, ctx->cancel};
   int per_sm = 0;
   dlm_status st = DLM_OK;
   auto go = [&](auto kfn) -> dlm_status {
@@ -741,7 +811,8 @@ extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dl
     case 1: st = go(tabucol_multi_kernel<1>); break;
     case 2: st = go(tabucol_multi_kernel<2>); break;
     case 4: st = go(tabucol_multi_kernel<4>); break;
-    default: st = go(tabucol_multi_kernel<8>); break;
+    case 8: st = go(tabucol_multi_kernel<8>); break;
+    default: st = go(tabucol_multi_kernel<16>); break;
   }
   return st;
 }
@@ -835,7 +906,7 @@ extern "C" dlm_status dlm_tabucol_multi_noalloc(dlm_ctx* ctx, int32_t n_graphs, 
   DLM_CUDA(ctx, cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(MultiJob), cudaMemcpyHostToDevice, ctx->stream));
   DLM_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int32_t), ctx->stream));  // the queue starts at zero
   const TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
-                      ctx->smem_optin, nullptr, 0};
+                      ctx->smem_optin, nullptr, 0, ctx->cancel};
   auto go = [&](auto kfn) -> dlm_status {
     int per_sm = 0;
     DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -850,7 +921,8 @@ extern "C" dlm_status dlm_tabucol_multi_noalloc(dlm_ctx* ctx, int32_t n_graphs, 
     case 1: return go(tabucol_multi_kernel<1>);
     case 2: return go(tabucol_multi_kernel<2>);
     case 4: return go(tabucol_multi_kernel<4>);
-    default: return go(tabucol_multi_kernel<8>);
+    case 8: return go(tabucol_multi_kernel<8>);
+    default: return go(tabucol_multi_kernel<16>);
   }
 }
 
@@ -926,7 +998,8 @@ extern "C" dlm_status dlm_tabucol_multi_plan_create(dlm_ctx* ctx, int32_t n_grap
     case 1: kfn = (void*)tabucol_multi_kernel<1>; break;
     case 2: kfn = (void*)tabucol_multi_kernel<2>; break;
     case 4: kfn = (void*)tabucol_multi_kernel<4>; break;
-    default: kfn = (void*)tabucol_multi_kernel<8>; break;
+    case 8: kfn = (void*)tabucol_multi_kernel<8>; break;
+    default: kfn = (void*)tabucol_multi_kernel<16>; break;
   }
   int per_sm = 0;
   if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
@@ -944,7 +1017,8 @@ extern "C" dlm_status dlm_tabucol_multi_plan_create(dlm_ctx* ctx, int32_t n_grap
   if (cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(MultiJob), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(DLM_ECUDA, "tabucol_multi_plan: upload");
   TabuRule rule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
-                ctx->smem_optin, slab_stride ? (uint16_t*)(p->mem + job_bytes + 16) : nullptr, slab_stride};
+                ctx->smem_optin, slab_stride ? (uint16_t*)(p->mem + job_bytes + 16) : nullptr, slab_stride,
+                ctx->cancel};
   int32_t njobs32 = (int32_t)jobs.size();
   void* params[] = {&d_jobs, &njobs32, &d_queue, &rule};
   cudaStream_t cs = nullptr;

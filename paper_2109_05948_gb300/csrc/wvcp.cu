@@ -252,7 +252,16 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
 #pragma unroll 4
         for (int c = 0; c < cs; ++c)
           wvcp_scan_key(c, o, wv, max1s[c], base, phi, gS[(size_t)c * npad + v], frozen, thr, km, kc);
-        for (int c = cs; c < k; ++c)
+        // the slab colours come from L2: 16 independent loads in flight before they are used
+        int c = cs;
+        for (; c + 16 <= k; c += 16) {
+          int gq[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) gq[q] = gG[(size_t)(c + q - cs) * npad + v];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) wvcp_scan_key(c + q, o, wv, max1s[c + q], base, phi, gq[q], frozen, thr, km, kc);
+        }
+        for (; c < k; ++c)
           wvcp_scan_key(c, o, wv, max1s[c], base, phi, gG[(size_t)(c - cs) * npad + v], frozen, thr, km, kc);
         rmin[v] = km;
         rcnt[v] = (uint16_t)(km == INT_MAX ? 0 : kc);

@@ -46,6 +46,7 @@ _SIGS = {
     "dlm_create": (_i32, [_PP, _i32, _P]),
     "dlm_destroy": (None, [_P]),
     "dlm_set_stream": (_i32, [_P, _P]),
+    "dlm_set_cancel_flag": (_i32, [_P, _P]),
     "dlm_last_error": (ctypes.c_char_p, [_P]),
     "dlm_sync": (_i32, [_P]),
     "dlm_graph_create": (_i32, [_P, _i32, _i64, _P, _P, _PP]),
@@ -80,6 +81,12 @@ _SIGS = {
     "dlm_memetic_step": (_i32, [_P, _P, _P]),
     "dlm_memetic_get": (_i32, [_P, _P, _i32, _P]),
     "dlm_memetic_set": (_i32, [_P, _P, _i32, _P]),
+    "dlm_memetic_state_bytes": (_i64, [_P]),
+    "dlm_memetic_save": (_i32, [_P, _P, _P]),
+    "dlm_memetic_load": (_i32, [_P, _P, _P]),
+    "dlm_scorer_state_bytes": (_i64, [_P]),
+    "dlm_scorer_save": (_i32, [_P, _P, _P]),
+    "dlm_scorer_load": (_i32, [_P, _P, _P]),
     "dlm_probe_smem_bandwidth": (_i32, [_P, _P]),
     "dlm_gemm_bf16": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32]),
     "dlm_gemm_profile": (_i32, [_P, _i32]),
@@ -119,6 +126,8 @@ def _ptr(t):
         return None
     if isinstance(t, int):
         return t
+    if hasattr(t, "__array_interface__"):  # numpy array in host memory
+        return ctypes.c_void_p(t.__array_interface__["data"][0])
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -344,6 +353,42 @@ def dlm_memetic_get(ctx, mm, which, dst):
 
 def dlm_memetic_set(ctx, mm, which, src):
     ctx.check(lib().dlm_memetic_set(ctx.h, mm.h, which, _ptr(src)), "dlm_memetic_set")
+
+
+def dlm_set_cancel_flag(ctx, flag):
+    """flag: an int32 tensor the device can read (CUDA or pinned host memory), or None."""
+    ctx.check(lib().dlm_set_cancel_flag(ctx.h, _ptr(flag)), "dlm_set_cancel_flag")
+
+
+def dlm_memetic_save(ctx, mm):
+    """The checkpoint blob of the memetic state as a host numpy uint8 array."""
+    import numpy as np
+
+    buf = np.empty(int(lib().dlm_memetic_state_bytes(mm.h)), np.uint8)
+    ctx.check(lib().dlm_memetic_save(ctx.h, mm.h, _ptr(buf)), "dlm_memetic_save")
+    return buf
+
+
+def dlm_memetic_load(ctx, mm, buf):
+    import numpy as np
+
+    buf = np.ascontiguousarray(buf, np.uint8)
+    ctx.check(lib().dlm_memetic_load(ctx.h, mm.h, _ptr(buf)), "dlm_memetic_load")
+
+
+def dlm_scorer_save(ctx, s):
+    import numpy as np
+
+    buf = np.empty(int(lib().dlm_scorer_state_bytes(s.h)), np.uint8)
+    ctx.check(lib().dlm_scorer_save(ctx.h, s.h, _ptr(buf)), "dlm_scorer_save")
+    return buf
+
+
+def dlm_scorer_load(ctx, s, buf):
+    import numpy as np
+
+    buf = np.ascontiguousarray(buf, np.uint8)
+    ctx.check(lib().dlm_scorer_load(ctx.h, s.h, _ptr(buf)), "dlm_scorer_load")
 
 
 def dlm_gemm_bf16(ctx, A, B, C, M, N, K):

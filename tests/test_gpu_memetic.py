@@ -102,3 +102,50 @@ def test_memetic_scorer_scores_match_oracle_after_training(ctx):
     rel = np.linalg.norm(scores - ref) / np.linalg.norm(ref)
     assert rel <= 1e-2
     mm.close()
+
+
+def _state(ctx, mm, p, n, K, learned):
+    out = [_get(ctx, mm, w, s, d) for w, s, d in [(0, (p, n), torch.int16), (1, (p,), torch.int64),
+                                                   (2, (p, p), torch.int16), (3, (p, n), torch.int16),
+                                                   (4, (n,), torch.int16), (5, (p,), torch.int64),
+                                                   (6, (p,), torch.int32)]]
+    if learned:
+        out.append(_get(ctx, mm, 7, (p, K), torch.float32))
+    return out
+
+
+@pytest.mark.parametrize("learned", [0, 1])
+def test_memetic_checkpoint_resume_and_determinism(ctx, learned):
+    """Two objects with the same seed run identical generations; a third object loaded from the
+    first one's checkpoint after two generations continues bit-identically (population, distances,
+    offspring, best colouring, picks and, in the learned mode, candidate scores)."""
+    n, k, p, K, iters, seed = 70, 5, 24, 4, 150, 8
+    e, _ = inputs.planted(n, k, 0.4, seed=seed)
+    g = device_graph(ctx, n, e)
+    prm = dlmcol.MemeticParams(k=k, p=p, K=K, iters=iters, tenure=dlmcol.COL_TENURE, use_scorer=learned, epochs=1,
+                               batch=8, lr=1e-3, seed=seed)
+    a, b = dlmcol.Memetic(ctx, g, prm), dlmcol.Memetic(ctx, g, prm)
+    for _ in range(2):
+        fa, fb = dlmcol.dlm_memetic_step(ctx, a), dlmcol.dlm_memetic_step(ctx, b)
+        assert fa == fb
+        for x, y in zip(_state(ctx, a, p, n, K, learned), _state(ctx, b, p, n, K, learned)):
+            assert np.array_equal(x, y)
+    blob = dlmcol.dlm_memetic_save(ctx, a)
+    c = dlmcol.Memetic(ctx, g, prm)
+    dlmcol.dlm_memetic_load(ctx, c, blob)
+    for _ in range(2):
+        fa, fc = dlmcol.dlm_memetic_step(ctx, a), dlmcol.dlm_memetic_step(ctx, c)
+        assert fa == fc
+        for x, y in zip(_state(ctx, a, p, n, K, learned), _state(ctx, c, p, n, K, learned)):
+            assert np.array_equal(x, y)
+    # a checkpoint of another configuration is refused
+    other = dlmcol.Memetic(ctx, g, dlmcol.MemeticParams(k=k, p=p + 2, K=K, iters=iters, tenure=dlmcol.COL_TENURE,
+                                                        use_scorer=learned, epochs=1, batch=8, lr=1e-3, seed=seed))
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_memetic_load(ctx, other, blob)
+    bad = blob.copy()
+    bad[:8] = 0
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_memetic_load(ctx, c, bad)
+    for m in (a, b, c, other):
+        m.close()

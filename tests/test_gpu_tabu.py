@@ -85,7 +85,7 @@ def test_gamma_matches_oracle(ctx):
         assert np.array_equal(gam[i].cpu().numpy(), g_ref) and f[i].item() == f_ref
 
 
-@pytest.mark.parametrize("warps", [1, 2, 4, 8])
+@pytest.mark.parametrize("warps", [1, 2, 4, 8, 16])
 def test_tabucol_small_random_graph_trace_bitexact(ctx, warps):
     """8 individuals on G(125, 0.5), k = 17, 10^4 iterations, seed 0 (gamma is exact in u16 for n < 65536): every
     iteration's move, the best colouring, best f and moves equal the oracle's."""
@@ -204,3 +204,48 @@ def test_tabucol_full_size_all_individuals(ctx):
     for i in traced:
         T = refs[i]["iters"]
         assert np.array_equal(gtr[i][:T], refs[i]["trace"]), i
+
+
+def test_tabucol_cancel_flag(ctx):
+    """A set flag stops every search at its first poll (iteration 0: no move, the start colouring
+    is returned); a pinned host flag raised while the launch runs stops it early. In both cases
+    dlm_sync reports DLM_ECANCELLED and the returned best conflicts recount from the returned
+    colouring."""
+    n, k, pop = 200, 10, 4
+    e, adj = gnp_case(n, 0.5, 3)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, pop, 3)
+    col = torch.from_numpy(start.copy()).cuda()
+    bf = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    mv = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    flag = torch.ones(1, dtype=torch.int32, device="cuda")
+    try:
+        dlmcol.dlm_set_cancel_flag(ctx, flag)
+        dlmcol.dlm_tabucol_batch(ctx, g, k, pop, col, bf, mv, 10_000)
+        with pytest.raises(dlmcol.DlmError, match="ECANCELLED"):
+            ctx.sync()
+        assert torch.equal(col.cpu(), torch.from_numpy(start)) and int(mv.sum()) == 0
+        f0 = torch.zeros(pop, dtype=torch.int64, device="cuda")
+        dlmcol.dlm_gamma(ctx, g, k, pop, col, None, f0)
+        ctx.sync()
+        assert torch.equal(bf, f0)
+        # a pinned host flag raised by the host while the kernels run
+        hflag = torch.zeros(1, dtype=torch.int32).pin_memory()
+        dlmcol.dlm_set_cancel_flag(ctx, hflag)
+        iters = 2_000_000
+        col.copy_(torch.from_numpy(start))
+        dlmcol.dlm_tabucol_batch(ctx, g, k, pop, col, bf, mv, iters)
+        import time
+        time.sleep(0.2)
+        hflag[0] = 1
+        with pytest.raises(dlmcol.DlmError, match="ECANCELLED"):
+            ctx.sync()
+        assert 0 < int(mv.max()) < iters
+        dlmcol.dlm_gamma(ctx, g, k, pop, col, None, f0)
+        ctx.sync()
+        assert torch.equal(bf, f0)
+    finally:
+        dlmcol.dlm_set_cancel_flag(ctx, None)
+    # without the flag the context runs normally again
+    dlmcol.dlm_tabucol_batch(ctx, g, k, pop, col, bf, mv, 100)
+    ctx.sync()
