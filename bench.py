@@ -9,6 +9,12 @@ dlm_tabucol_batch. value = tabu moves (iterations that moved) of all GPUs / devi
 
 Under torchrun each rank runs its own 4096 individuals (weak scaling, no data-path collective).
 --impl reference times the CPU oracle (the plain C++ statement of the method) on the host cores.
+
+Other workloads (one JSON line each, single GPU):
+  --workload memetic  learned vs random GPX time to a legal colouring, planted n = 1000, k = 48
+  --workload multi    the uneven 64-graph batch in one persistent launch replayed from a CUDA graph
+  --workload wvcp     the weighted feasible/infeasible tabu search, G(1000, 0.5), weights 1..100
+  --workload scorer   one learned generation's scoring and training with the tensor-core roofline
 """
 from __future__ import annotations
 
