@@ -210,30 +210,41 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
 }
 
 // per-candidate term G[cand][o] = beta[o] + sum_f M[cand][f] Gamma[f][o] in FP32; a block of
-// 256 threads (thread = o) handles 16 candidates, reading each Gamma row once for all 16
-constexpr int kGTile = 16;
+// 256 threads (thread = o) handles TILE candidates, reading each Gamma row once for all of them.
+// TILE shrinks for small batches so that the grid still covers the SMs.
+template <int TILE>
 __global__ void __launch_bounds__(256) k_gterm(int c, int din, const float* M, const float* theta, size_t ogam,
                                                size_t ob, float* G) {
-  __shared__ float ms[kGTile][256];
-  const int c0 = blockIdx.x * kGTile, o = threadIdx.x;
-  for (int i = threadIdx.x; i < kGTile * din; i += 256) {
+  __shared__ float ms[TILE][256];
+  const int c0 = blockIdx.x * TILE, o = threadIdx.x;
+  for (int i = threadIdx.x; i < TILE * din; i += 256) {
     const int cc = i / din, f = i % din;
     ms[cc][f] = (c0 + cc < c) ? M[(size_t)(c0 + cc) * din + f] : 0.f;
   }
   __syncthreads();
-  float acc[kGTile];
+  float acc[TILE];
 #pragma unroll
-  for (int q = 0; q < kGTile; ++q) acc[q] = 0.f;
+  for (int q = 0; q < TILE; ++q) acc[q] = 0.f;
   const float* gam = theta + ogam;
+#pragma unroll 4
   for (int f = 0; f < din; ++f) {
     const float g = gam[(size_t)f * kD + o];
 #pragma unroll
-    for (int q = 0; q < kGTile; ++q) acc[q] += ms[q][f] * g;
+    for (int q = 0; q < TILE; ++q) acc[q] += ms[q][f] * g;
   }
   const float b = theta[ob + o];
 #pragma unroll
-  for (int q = 0; q < kGTile; ++q)
+  for (int q = 0; q < TILE; ++q)
     if (c0 + q < c) G[(size_t)(c0 + q) * kD + o] = acc[q] + b;
+}
+
+static dlm_status launch_gterm(dlm_ctx* ctx, int c, int din, const float* M, const float* theta, size_t ogam, size_t ob,
+                               float* G) {
+  const int want = 2 * ctx->num_sms;
+  if (c >= 16 * want) k_gterm<16><<<(c + 15) / 16, 256, 0, ctx->stream>>>(c, din, M, theta, ogam, ob, G);
+  else if (c >= 4 * want) k_gterm<4><<<(c + 3) / 4, 256, 0, ctx->stream>>>(c, din, M, theta, ogam, ob, G);
+  else k_gterm<1><<<c, 256, 0, ctx->stream>>>(c, din, M, theta, ogam, ob, G);
+  return launch_check(ctx, "k_gterm");
 }
 
 // per-candidate mean (or sum) over the k valid rows of a bf16 [c*R][w] matrix; block = w threads
@@ -242,6 +253,7 @@ __global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, f
   const bf16* x = X + (size_t)cand * kR * w + col;
   const bf16* xl = Xlo ? Xlo + (size_t)cand * kR * w + col : nullptr;
   float s = 0.f;
+#pragma unroll 8
   for (int r = 0; r < k; ++r) s += __bfloat162float(x[(size_t)r * w]) + (xl ? __bfloat162float(xl[(size_t)r * w]) : 0.f);
   s *= scale;
   outf[(size_t)cand * w + col] = s;
@@ -446,15 +458,25 @@ __global__ void k_dgamma(int B, int din, const float* Mprev, const float* S, flo
   }
 }
 
-// Gb[cand][f] = (1/k) sum_o S[cand][o] * Gamma[f][o]
-__global__ void k_gb(int B, int din, int k, const float* S, const float* theta, size_t ogam, float* Gb) {
-  const int cand = blockIdx.x, f = threadIdx.x;
-  if (f >= din) return;
-  const float* g = theta + ogam + (size_t)f * kD;
-  const float* s = S + (size_t)cand * kD;
-  float acc = 0.f;
-  for (int o = 0; o < kD; ++o) acc += s[o] * g[o];
-  Gb[(size_t)cand * din + f] = acc / (float)k;
+// Gb[cand][f] = (1/k) sum_o S[cand][o] * Gamma[f][o]; one block of kD threads per candidate,
+// warp w takes rows f = w, w + 8, ...: its lanes read a Gamma row contiguously and reduce by a
+// fixed butterfly
+__global__ void __launch_bounds__(kD) k_gb(int B, int din, int k, const float* S, const float* theta, size_t ogam,
+                                           float* Gb) {
+  __shared__ float ss[kD];
+  const int cand = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ss[threadIdx.x] = S[(size_t)cand * kD + threadIdx.x];
+  __syncthreads();
+  const float* gam = theta + ogam;
+  for (int f = warp; f < din; f += kD / 32) {
+    const float* g = gam + (size_t)f * kD;
+    float acc = 0.f;
+#pragma unroll
+    for (int o = lane; o < kD; o += 32) acc += ss[o] * g[o];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, d);
+    if (lane == 0) Gb[(size_t)cand * din + f] = acc / (float)k;
+  }
 }
 
 // grad[dst + i] = sum_z part[z][i]
@@ -705,8 +727,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
   for (int l = 1; l <= kNL; ++l) {
     const int din = din_of(l);
     // per-candidate term rho(H_{l-1}) Gamma_l + beta_l (FP32, CUDA cores)
-    k_gterm<<<(c + kGTile - 1) / kGTile, 256, 0, ctx->stream>>>(c, din, Mf[l - 1], s->theta, s->ogam[l], s->ob[l], G[l]);
-    DLM_TRY(launch_check(ctx, "k_gterm"));
+    DLM_TRY(launch_gterm(ctx, c, din, Mf[l - 1], s->theta, s->ogam[l], s->ob[l], G[l]));
     const bool last = l == kNL;
     EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, G[l],
                last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f};
@@ -749,7 +770,7 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
     DLM_TRY(launch_check(ctx, "k_reduce_splits"));
     // dGamma_l, dbeta_l and the per-candidate term of dH_{l-1}
     k_dgamma<<<din, kD, 0, ctx->stream>>>(B, din, s->Mfb[l - 1], s->S[l], s->grad, s->ogam[l], s->ob[l]);
-    k_gb<<<B, din, 0, ctx->stream>>>(B, din, s->k, s->S[l], s->theta, s->ogam[l], s->Gb);
+    k_gb<<<B, kD, 0, ctx->stream>>>(B, din, s->k, s->S[l], s->theta, s->ogam[l], s->Gb);
     DLM_TRY(launch_check(ctx, "k_gb"));
     // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
     EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->Gb, s->Hb[l - 1]};

@@ -14,8 +14,9 @@
 //    into segments so that every thread scans (two colours per 32-bit word, no warp collectives
 //    inside a segment); the order of (row, segment) items follows the thread order.
 //  * selection: per-warp minima and tie counts go through one barrier; every thread derives the
-//    block minimum, the tie total and its rank range, and the thread holding the j-th tied move
-//    (j drawn from the iteration's Philox block) finds its colour and applies the move.
+//    block minimum, the tie total and its rank range, and the warp holding the j-th tied move
+//    (j drawn from the iteration's Philox block) finds its colour with ballots over the segment
+//    and applies the move.
 //  * update: the adjacency bit row of the moved vertex (L2 resident) is split across all threads; each neighbour costs two u16 read-modify-writes of its gamma row
 //    and, when its conflict status flips, one shared atomic on the bitmap.
 //  Three CTA barriers per iteration.
@@ -177,31 +178,15 @@ __device__ __forceinline__ void scan_seg(const uint32_t* g32, const uint32_t* t3
   cnt = c;
 }
 
-// The jj-th (0-based) colour of words [w0, w1) whose key equals kmin, in increasing colour order.
-__device__ __forceinline__ int seg_find(const uint32_t* g32, const uint32_t* t32, int w0, int w1, int killw,
-                                        uint32_t killm, unsigned itrel, int thr, unsigned kmin, int jj) {
-  for (int w = w0; w < w1; ++w) {
-    uint32_t gw = g32[w];
-    const uint32_t tw = t32[w];
-    if (w == killw) gw |= killm;
-    const unsigned ga = gw & 0xFFFFu, gb = gw >> 16;
-    const unsigned k0 = ((tw & 0xFFFFu) <= itrel || (int)ga < thr) ? ga : 0xFFFFu;
-    const unsigned k1 = ((tw >> 16) <= itrel || (int)gb < thr) ? gb : 0xFFFFu;
-    if (k0 == kmin) { if (jj == 0) return 2 * w; --jj; }
-    if (k1 == kmin) { if (jj == 0) return 2 * w + 1; --jj; }
-  }
-  return -1;
-}
-
 // One individual, one CTA of W warps (SPILL: rows beyond the shared-memory budget live in the
 // CTA's global slab).
 // Per iteration: (1) every warp compacts the conflicting-vertex bitmap into its own list; the rows
 // are cut into S contiguous segments (S = threads / |CV| when there are fewer rows than threads)
 // and thread t scans items [tC, tC + C) of the (row, segment) list, keeping per-item (min delta,
 // #ties) and its own aggregate; (2) one barrier publishes the per-warp minima and tie counts:
-// every thread derives the minimum delta, the total T and its own rank range, and the thread that
-// holds the j-th tie (j drawn from the iteration's Philox block) applies the move; (3) all
-// threads update gamma on the neighbours. Three barriers per iteration. The Philox blocks of 32
+// every thread derives the minimum delta, the total T and its own rank range; the warp holding
+// the j-th tie (j drawn from the iteration's Philox block) finds its colour with ballots over the
+// tied segment and applies the move; (3) all threads update gamma on the neighbours. Three barriers per iteration. The Philox blocks of 32
 // iterations are drawn at once, one per lane, by one warp every 32 iterations.
 //
 // Tabu list: u16 expiries relative to a base that advances by 2^14 every 2^14 iterations
@@ -415,7 +400,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     }
     const uint32_t r0 = rnd[2 * (it & 31)];
     const uint32_t j = T > 0 ? below(r0, (uint32_t)T) : 0u;
-    if (T > 0 && (int)j >= pre && (int)j < pre + wtot) {  // the j-th tie is in this warp
+    if (T > 0 && (int)j >= pre && (int)j < pre + wtot) {  // the j-th tie is in this warp (warp-uniform)
       const int ct = (dstar != INT_MAX && tmin == dstar) ? tcnt : 0;
       int incl = ct;
 #pragma unroll
@@ -424,25 +409,64 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
         if (lane >= d) incl += t;
       }
       const int lo = pre + incl - ct;
-      if (ct > 0 && (int)j >= lo && (int)j < lo + ct) {  // this thread holds the j-th tied move
+      const bool hit = ct > 0 && (int)j >= lo && (int)j < lo + ct;  // this thread holds the j-th tie
+      int hit_item = -1, hit_rank = 0;
+      if (hit) {
         int jj = (int)j - lo;
-        int mv = -1, mc = -1;
         for (int i = i0; i < i1; ++i) {
           const uint32_t rr = rowres[i];
           const int rm = (int16_t)(rr >> 16), rcn = (int)(rr & 0xFFFF);
           if (rm != dstar || rcn == 0) continue;
           if (jj >= rcn) { jj -= rcn; continue; }
-          const int r = S == 1 ? i : (int)(((float)i + 0.5f) * rS), sg = i - r * S;
-          const int v = cvl[r - rlo];
-          const int colv = colS[v];
-          const uint16_t* grow = grow_of(v);
-          const int g0 = grow[colv];
-          const int w0 = sg * Lw, w1 = min(w0 + Lw, kw);
-          mv = v;
-          mc = seg_find((const uint32_t*)grow, (const uint32_t*)trow_of(v), w0, w1, colv >> 1,
-                        0xFFFFu << (16 * (colv & 1)), itrel, best_f - f + g0, (unsigned)(dstar + g0), jj);
+          hit_item = i;
+          hit_rank = jj;
           break;
         }
+      }
+      // the whole warp searches the winning item's segment: lane l takes words w0 + l, w0 + 32 + l,
+      // ...; ballots order the tied colours (word by word, low half first) and find the rank
+      const unsigned hb = __ballot_sync(FULL, hit);
+      const int hl = hb ? __ffs(hb) - 1 : 0;
+      const int item = hb ? __shfl_sync(FULL, hit_item, hl) : -1;
+      int jj = __shfl_sync(FULL, hit_rank, hl);
+      int mv = -1, mc = -1;
+      if (item >= 0) {
+        const int r = S == 1 ? item : (int)(((float)item + 0.5f) * rS), sg = item - r * S;
+        const int v = cvl[r - rlo];
+        const int colv = colS[v];
+        const uint16_t* grow = grow_of(v);
+        const uint32_t* g32 = (const uint32_t*)grow;
+        const uint32_t* t32 = (const uint32_t*)trow_of(v);
+        const int g0 = grow[colv];
+        const int w0 = sg * Lw, w1 = min(w0 + Lw, kw);
+        const unsigned kmin = (unsigned)(dstar + g0);
+        const int thr = best_f - f + g0;
+        const int killw = colv >> 1;
+        const uint32_t killm = 0xFFFFu << (16 * (colv & 1));
+        const unsigned lt = (1u << lane) - 1u;
+        for (int wb = w0; wb < w1 && mc < 0; wb += 32) {
+          const int w = wb + lane;
+          bool m0 = false, m1 = false;
+          if (w < w1) {
+            uint32_t gw = g32[w];
+            const uint32_t tw = t32[w];
+            if (w == killw) gw |= killm;
+            const unsigned ga = gw & 0xFFFFu, gb = gw >> 16;
+            const unsigned k0 = ((tw & 0xFFFFu) <= itrel || (int)ga < thr) ? ga : 0xFFFFu;
+            const unsigned k1 = ((tw >> 16) <= itrel || (int)gb < thr) ? gb : 0xFFFFu;
+            m0 = k0 == kmin;
+            m1 = k1 == kmin;
+          }
+          const unsigned b0 = __ballot_sync(FULL, m0), b1 = __ballot_sync(FULL, m1);
+          const int before = __popc(b0 & lt) + __popc(b1 & lt);
+          const bool found = jj >= before && jj < before + (int)m0 + (int)m1;
+          const unsigned fb = __ballot_sync(FULL, found);
+          if (fb) mc = __shfl_sync(FULL, 2 * w + ((jj == before && m0) ? 0 : 1), __ffs(fb) - 1);
+          else jj -= __popc(b0) + __popc(b1);
+        }
+        mv = v;
+      }
+      if (lane == 0) {
         if (mv >= 0 && mc >= 0 && mc < k) {
           const int old = colS[mv];
           colS[mv] = (uint8_t)mc;
@@ -537,7 +561,7 @@ struct TabuBatchArgs {
 };
 
 template <int W>
-__global__ void __launch_bounds__(W * 32) tabucol_batch_kernel(TabuBatchArgs a) {
+__global__ void __launch_bounds__(W * 32, W >= 16 ? 1 : 2) tabucol_batch_kernel(TabuBatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   // one individual per CTA, or (when rows spill to a per-CTA slab) resident CTAs loop over them
   for (int i = blockIdx.x; i < a.pop; i += gridDim.x) {
@@ -569,7 +593,7 @@ struct MultiJob {
 };
 
 template <int W>
-__global__ void __launch_bounds__(W * 32) tabucol_multi_kernel(const MultiJob* jobs, int32_t njobs,
+__global__ void __launch_bounds__(W * 32, W >= 16 ? 1 : 2) tabucol_multi_kernel(const MultiJob* jobs, int32_t njobs,
                                                                int32_t* queue, TabuRule rule) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int32_t next;

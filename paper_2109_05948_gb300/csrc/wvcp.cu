@@ -7,7 +7,7 @@
 //  * every one-move (v, c) of every vertex is evaluated each iteration (n * k pairs, ~115 000 at
 //    n = 1000): delta = rem(v) + max(0, w_v - max1[c]) + phi (gamma[v][c] - gamma[v][col v]),
 //    rem(v) the drop of v's class maximum when v leaves it;
-//  * gamma is stored transposed, gT[c][v] (u16), so that thread t scanning vertices t, t + 256, ...
+//  * gamma is stored transposed, gT[c][v] (u16), so that thread t scanning vertices t, t + 512, ...
 //    reads consecutive addresses across the warp; the first Cs colours live in shared memory, the
 //    rest in an L2-resident slab of global memory owned by the CTA (n * k * 2 bytes exceeds one
 //    SM's shared memory for the benchmarked graphs);
@@ -23,7 +23,7 @@
 
 namespace dlm {
 
-constexpr int kWThreads = 256;
+constexpr int kWThreads = 512;
 constexpr int kWWarps = kWThreads / 32;
 
 struct WvcpLayout {
@@ -49,7 +49,7 @@ __host__ __device__ inline WvcpLayout wvcp_layout(int n, int k, int wmax, size_t
   L.max1 = o; o += wal16((size_t)k);
   L.rmin = o; o += wal16((size_t)n * 4);
   L.rcnt = o; o += wal16((size_t)n * 2);
-  L.red = o; o += 512;  // 24 ints, then 24 long longs
+  L.red = o; o += 1024;  // 2 kWWarps + 8 ints, then 8 + 2 kWWarps long longs
   L.gT = o;
   const size_t per_col = (size_t)L.npad * 2;
   size_t cs = budget > o ? (budget - o) / per_col : 0;
@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   uint8_t* max1s = smem + L.max1;
   int32_t* rmin = (int32_t*)(smem + L.rmin);
   uint16_t* rcnt = (uint16_t*)(smem + L.rcnt);
-  int32_t* red = (int32_t*)(smem + L.red);  // [8] warp minima, [8] warp tie totals
-  int32_t* sc = red + 16;                   // mv, old, new, improved, error, bad input, r0, r1
-  long long* sc64 = (long long*)(red + 24); // g, conf, best g, best f, best conf, f, conf partial sums
+  int32_t* red = (int32_t*)(smem + L.red);  // [kWWarps] warp minima, [kWWarps] warp tie totals
+  int32_t* sc = red + 2 * kWWarps;          // mv, old, new, improved, error, bad input, r0, r1
+  // g, conf, best g, best f, best conf; from 8: per-warp conflict and score partial sums
+  long long* sc64 = (long long*)(red + 2 * kWWarps + 8);
   uint16_t* gS = (uint16_t*)(smem + L.gT);
   uint16_t* gG = a.slab + (size_t)blockIdx.x * (size_t)(k - cs) * npad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -212,11 +213,11 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
       cpart += __shfl_down_sync(0xFFFFFFFFu, cpart, d);
       fpart += __shfl_down_sync(0xFFFFFFFFu, fpart, d);
     }
-    if (lane == 0) { sc64[8 + warp] = cpart; sc64[16 + warp] = fpart; }
+    if (lane == 0) { sc64[8 + warp] = cpart; sc64[8 + kWWarps + warp] = fpart; }
     __syncthreads();
     if (tid == 0) {
       long long ct = 0, ft = 0;
-      for (int w = 0; w < kWWarps; ++w) { ct += sc64[8 + w]; ft += sc64[16 + w]; }
+      for (int w = 0; w < kWWarps; ++w) { ct += sc64[8 + w]; ft += sc64[8 + kWWarps + w]; }
       const long long conf = ct / 2;
       sc64[0] = ft + phi * conf;
       sc64[1] = conf;
@@ -287,13 +288,13 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
         if (lane >= d) incl += t;
       }
-      if (lane == 31) red[8 + warp] = incl;
+      if (lane == 31) red[kWWarps + warp] = incl;
       __syncthreads();
       int T = 0, pre = 0;
 #pragma unroll
       for (int w = 0; w < kWWarps; ++w) {
-        T += red[8 + w];
-        pre += w < warp ? red[8 + w] : 0;
+        T += red[kWWarps + w];
+        pre += w < warp ? red[kWWarps + w] : 0;
       }
       if (T > 0 && ct > 0) {
         const uint32_t j = below((uint32_t)sc[6], (uint32_t)T);
