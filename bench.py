@@ -565,7 +565,7 @@ def main():
     col = torch.empty_like(col0)
     best_f = torch.empty(pop, dtype=torch.int64, device=dev)
     moves = torch.zeros((max(1, args.steps), pop), dtype=torch.int64, device=dev)
-    work = torch.zeros((max(1, args.steps), pop, 2), dtype=torch.int64, device=dev)
+    work = torch.zeros((max(1, args.steps), pop, 3), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     smem_gbps = dlmcol.dlm_probe_smem_bandwidth(ctx)
     stream = torch.cuda.current_stream(dev)
@@ -603,23 +603,28 @@ def main():
     ms = t0.elapsed_time(t1)
     kms = [a.elapsed_time(b) for a, b in kev]
     tot_moves = int(moves[: args.steps].sum().item())
+    local_moves = tot_moves
     wk = work[: args.steps].sum(dim=(0, 1)).tolist()
     if world > 1:
         ms, tot_moves = reduce_over_ranks(dist, ms, tot_moves, dev)
     value = tot_moves / (ms / 1e3)
 
     # algorithmic shared-memory bytes of the tabu kernel (per launch): every conflicting row
-    # scanned reads k gamma + k tabu entries (4k B); every neighbour of a moved vertex costs two
-    # u16 read-modify-writes of its gamma row (8 B) plus its colour byte (1 B)
-    alg_bytes = (4 * K * wk[0] + 9 * wk[1]) / args.steps
+    # evaluated reads its colour (1 B), gamma[v][col v] (2 B) and its summary (8 B) and writes its
+    # selection result (4 B); every neighbour of a moved vertex costs its colour (1 B), two u16
+    # gamma read-modify-writes (8 B), two u16 tabu reads (4 B) and its summary read and write
+    # (16 B); every re-summarised row reads its k gamma and k tabu entries (4k B) and its colour
+    # and writes its summary (9 B); every iteration reads the n summaries' expiry (2 B each)
+    alg_bytes = (15 * wk[0] + 29 * wk[1] + (4 * K + 9) * wk[2] + 2 * N * local_moves) / args.steps
     kmean = sum(kms) / len(kms)
     achieved = alg_bytes / (kmean / 1e3) / 1e9
     roofline = {"bound": "smem", "achieved": achieved, "peak": smem_gbps, "unit": "GB/s",
                 "frac": achieved / smem_gbps, "traffic": None,
                 "kernel": "tabucol_batch_kernel", "kernel_ms": kmean,
                 "peak_source": "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads)",
-                "work": {"rows_scanned_per_launch": wk[0] / args.steps,
-                         "neighbour_updates_per_launch": wk[1] / args.steps}}
+                "work": {"rows_evaluated_per_launch": wk[0] / args.steps,
+                         "neighbour_updates_per_launch": wk[1] / args.steps,
+                         "rows_resummarised_per_launch": wk[2] / args.steps}}
     roofline["traffic"] = recorded_traffic()
 
     e2e = None

@@ -127,8 +127,9 @@ dlm_status dlm_tabucol_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_
 /* As dlm_tabucol_batch, with warps_per_individual forced (1, 2, 4, 8 or 16; 0 = autotuned), an
  * optional per-iteration trace -- device [pop][iters][4] int32 of (v, c, delta, #tied moves),
  * (-1, -1, 0, 0) for an iteration without a move, entries after an early stop untouched -- and an
- * optional work count -- device [pop][2] int64: the number of conflicting rows scanned and the sum
- * of the degrees of the moved vertices (the algorithmic work of the scan and of the update). */
+ * optional work count -- device [pop][3] int64: the number of conflicting rows evaluated, the sum
+ * of the degrees of the moved vertices and the number of rows whose summary was recomputed (the
+ * algorithmic work of the selection, of the update and of the re-summaries). */
 dlm_status dlm_tabucol_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                 int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                                 uint32_t generation, uint32_t ind_base, int32_t warps_per_individual,

@@ -8,18 +8,19 @@
 //                      scattered row updates of a warp spread over the banks)
 //      tab[n][ks] u16  tabu expiry relative to a base that advances by 2^14 every 2^14
 //                      iterations (one sweep), so a tabu test is a single unsigned compare
-//      col[n], best[n] u8 current and best colouring; cv[] u32 bitmap of conflicting vertices;
-//      rowres[n] u32   (row minimum delta, tie count) of each conflicting row of the scan.
-//  * scan: each warp compacts the bitmap into its own list of conflicting vertices; rows are cut
-//    into segments so that every thread scans (two colours per 32-bit word, no warp collectives
-//    inside a segment); the order of (row, segment) items follows the thread order.
-//  * selection: per-warp minima and tie counts go through one barrier; every thread derives the
-//    block minimum, the tie total and its rank range, and the warp holding the j-th tied move
-//    (j drawn from the iteration's Philox block) finds its colour with ballots over the segment
-//    and applies the move.
-//  * update: the adjacency bit row of the moved vertex (L2 resident) is split across all threads; each neighbour costs two u16 read-modify-writes of its gamma row
-//    and, when its conflict status flips, one shared atomic on the bitmap.
-//  Three CTA barriers per iteration.
+//      col[n], best[n] u8 current and best colouring
+//      summ[n]         per row: the smallest gamma among its non-tabu colours and among its tabu
+//                      colours with their multiplicities, and its earliest tabu expiry
+//  * selection reads one summary per conflicting vertex (thread t owns vertices t per ..
+//    t per + per - 1, so thread order is vertex order) instead of scanning k colours per row;
+//    aspiration (f + delta < best f) is decided from the tabu minimum;
+//  * the warp holding the j-th tied move (j drawn from the iteration's Philox block) finds its
+//    colour with ballots over that one row and applies the move;
+//  * update: each thread changes gamma on its vertices adjacent to the moved vertex (bit row of
+//    the graph, L1/L2 resident) and adjusts their summaries in O(1); rows whose class minimum may
+//    have risen, the moved vertex and rows with an expiring tabu colour are summarised again by
+//    whole warps (lanes over colours).
+//  Four CTA barriers per iteration.
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -36,7 +37,7 @@ struct TabuJob {
   int64_t* best_f;       // -> one int64
   int64_t* moves;        // -> one int64 or null
   int32_t* trace;        // [iters][4] or null
-  int64_t* work;         // [2] or null: sum of conflicting rows scanned, sum of degrees of moved vertices
+  int64_t* work;         // [3] or null: sums of conflicting rows evaluated, of degrees of moved vertices, of rows summarised again
   const int32_t* off;    // CSR offsets (degrees for the work counter)
   int64_t iters;
   uint32_t ind;          // Philox stream id of this individual
@@ -55,7 +56,6 @@ struct TabuRule {
 };
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int kNone16 = 0x7FFF;
 
 __host__ __device__ inline int tabu_row_stride(int k) {
   int kw = (k + 1) / 2;
@@ -65,15 +65,21 @@ __host__ __device__ inline int tabu_row_stride(int k) {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Rows a warp's threads scan in one iteration: items [32 w C, 32 (w + 1) C) of the (row, segment)
-// list, C = ceil(items / threads) <= ceil(n / threads), hence at most 32 C + 1 rows.
-__host__ __device__ inline int tabu_list_cap(int n, int warps) {
-  const int nt = 32 * warps;
-  return 32 * ((n + nt - 1) / nt) + 1;
-}
+// Per-row summary of the admissible-move structure of a row v (colours c != col v, c < k), valid
+// for one iteration's selection: the smallest gamma over the colours whose move is not tabu and
+// how many reach it, the same over the tabu colours, and the earliest relative expiry among the
+// tabu colours (0xFFFF: none). Keys are raw gamma values, so a change of gamma[v][col v] leaves
+// the summary valid.
+struct Summ {
+  uint16_t ntmin, tmin;
+  uint8_t ntcnt, tcnt;
+  uint16_t nexp;
+};
+static_assert(sizeof(Summ) == 8, "a row summary is 8 bytes");
+constexpr unsigned kNoKey = 0xFFFFu;
 
 struct TabuSmem {
-  size_t gam, tab, col, best, rowres, deg, cvl, cv, red, rnd, total;
+  size_t gam, tab, col, best, summ, vres, deg, queue, red, rnd, total;
   int rs;  // rows of gamma and tab held in shared memory; rows rs..n-1 live in the CTA's slab
 };
 
@@ -85,11 +91,11 @@ __host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps, si
   size_t o = 0;
   s.col = o; o += align16(n);
   s.best = o; o += align16(n);
-  s.rowres = o; o += align16((size_t)(n > 32 * warps ? n : 32 * warps) * 4);  // items <= max(n, threads)
+  s.summ = o; o += align16((size_t)n * sizeof(Summ));
+  s.vres = o; o += align16((size_t)n * 4);
   s.deg = o; o += align16((size_t)n * 2);
-  s.cvl = o; o += align16((size_t)warps * tabu_list_cap(n, warps) * 2);
-  s.cv = o; o += 64 * 4;
-  s.red = o; o += align16((size_t)warps * 8 + 64);
+  s.queue = o; o += align16((size_t)n * 2 + 16);
+  s.red = o; o += align16((size_t)warps * 12 + 64);
   s.rnd = o; o += 32 * 8;
   const size_t row = (size_t)ks * 2;
   size_t rs = budget > o + 32 ? (budget - o - 32) / (2 * row) : 0;
@@ -106,88 +112,76 @@ __host__ __device__ inline size_t tabu_slab_elems(int n, int k, int rs) {
   return (size_t)2 * (size_t)(n - rs) * tabu_row_stride(k);
 }
 
-// position of the r-th (0-based) set bit of x (x has more than r set bits)
-__device__ __forceinline__ int nth_set_bit(uint32_t x, int r) {
-  int pos = 0;
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const int c = __popc(x & ((1u << s) - 1u));
-    if (r >= c) { r -= c; x >>= s; pos += s; }
-  }
-  return pos;
-}
-
-__device__ __forceinline__ int nth_set_bit64(uint64_t x, int r) {
-  const uint32_t lo = (uint32_t)x;
-  const int pl = __popc(lo);
-  return r < pl ? nth_set_bit(lo, r) : 32 + nth_set_bit((uint32_t)(x >> 32), r - pl);
-}
-
-// Warp view of the conflicting-vertex bitmap: lane l owns the B = 2^lb bits of vertices
-// lB .. lB + B - 1 (B the smallest power of two with 32 B >= n, so the work spreads over all
-// lanes), its popcount and the exclusive prefix over lanes (= rank of its first vertex).
-struct CvView {
-  uint64_t w;
-  int cnt, excl, total;
-};
-
-__device__ __forceinline__ CvView cv_view(const uint32_t* cv, int lb, int lane) {
-  CvView c;
-  const int o = lane << lb;
-  if (lb == 6) {
-    c.w = ((uint64_t)cv[2 * lane + 1] << 32) | cv[2 * lane];
-  } else {
-    const uint32_t word = cv[o >> 5];
-    c.w = lb == 5 ? word : (word >> (o & 31)) & ((1u << (1 << lb)) - 1u);
-  }
-  c.cnt = __popcll(c.w);
-  int incl = c.cnt;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int t = __shfl_up_sync(FULL, incl, d);
-    if (lane >= d) incl += t;
-  }
-  c.excl = incl - c.cnt;
-  c.total = __shfl_sync(FULL, incl, 31);
-  return c;
-}
-
-// Scan of words [w0, w1) of a conflicting row by one thread. The key of colour c is gamma[v][c]
-// when the move (v, c) is admissible -- not tabu (relative expiry <= itrel), or tabu but
-// f + delta < best_f, i.e. gamma < thr with thr = best_f - f + gamma[v][col v] -- and 0xFFFF
-// otherwise; the current colour (killed here) and the padding columns carry 0xFFFF. Returns the
-// segment's minimum key and how many colours reach it.
-__device__ __forceinline__ void scan_seg(const uint32_t* g32, const uint32_t* t32, int w0, int w1, int killw,
-                                         uint32_t killm, unsigned itrel, int thr, unsigned& kmin, int& cnt) {
-  unsigned km = 0xFFFFu;
-  int c = 0;
-#pragma unroll 4
-  for (int w = w0; w < w1; ++w) {
+// Summary of row u by one warp (lanes over the 32-bit words, two colours each): classes at
+// relative iteration itn (tabu when the expiry exceeds itn); the current colour and the padding
+// columns (gamma 0xFFFF) are skipped.
+__device__ __forceinline__ Summ summarise_row(const uint32_t* g32, const uint32_t* t32, int kw, int colu,
+                                              unsigned itn, int lane) {
+  unsigned ntm = kNoKey, tm = kNoKey, nex = kNoKey;
+  unsigned ntc = 0, tc = 0;
+  const int killw = colu >> 1;
+  const uint32_t killm = 0xFFFFu << (16 * (colu & 1));
+  for (int w = lane; w < kw; w += 32) {
     uint32_t gw = g32[w];
     const uint32_t tw = t32[w];
     if (w == killw) gw |= killm;
-    const unsigned ga = gw & 0xFFFFu, gb = gw >> 16;
-    const unsigned k0 = ((tw & 0xFFFFu) <= itrel || (int)ga < thr) ? ga : 0xFFFFu;
-    const unsigned k1 = ((tw >> 16) <= itrel || (int)gb < thr) ? gb : 0xFFFFu;
-    const unsigned m = min(k0, k1);
-    const int cc = (int)(k0 == m) + (int)(k1 == m);
-    if (m < km) { km = m; c = cc; }
-    else if (m == km) c += cc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned g = (gw >> (16 * h)) & 0xFFFFu, t = (tw >> (16 * h)) & 0xFFFFu;
+      if (g == kNoKey) continue;
+      if (t > itn) {
+        if (g < tm) { tm = g; tc = 1; } else if (g == tm) ++tc;
+        nex = min(nex, t);
+      } else {
+        if (g < ntm) { ntm = g; ntc = 1; } else if (g == ntm) ++ntc;
+      }
+    }
   }
-  kmin = km;
-  cnt = c;
+  Summ s;
+  const unsigned NTM = __reduce_min_sync(0xFFFFFFFFu, ntm), TM = __reduce_min_sync(0xFFFFFFFFu, tm);
+  s.ntmin = (uint16_t)NTM;
+  s.tmin = (uint16_t)TM;
+  s.ntcnt = (uint8_t)__reduce_add_sync(0xFFFFFFFFu, ntm == NTM ? ntc : 0u);
+  s.tcnt = (uint8_t)__reduce_add_sync(0xFFFFFFFFu, tm == TM ? tc : 0u);
+  s.nexp = (uint16_t)__reduce_min_sync(0xFFFFFFFFu, nex);
+  return s;
+}
+
+// The key of one colour dropped to g: it may become its class minimum.
+__device__ __forceinline__ void summ_lower(Summ& s, bool tabu, unsigned g) {
+  if (tabu) {
+    if (g < s.tmin) { s.tmin = (uint16_t)g; s.tcnt = 1; } else if (g == s.tmin) ++s.tcnt;
+  } else {
+    if (g < s.ntmin) { s.ntmin = (uint16_t)g; s.ntcnt = 1; } else if (g == s.ntmin) ++s.ntcnt;
+  }
+}
+
+// The key of one colour rose from g: false when it was its class's only minimum (the row must be
+// summarised again).
+__device__ __forceinline__ bool summ_raise(Summ& s, bool tabu, unsigned g) {
+  if (tabu) {
+    if (g == s.tmin) { if (s.tcnt > 1) --s.tcnt; else return false; }
+  } else {
+    if (g == s.ntmin) { if (s.ntcnt > 1) --s.ntcnt; else return false; }
+  }
+  return true;
 }
 
 // One individual, one CTA of W warps (SPILL: rows beyond the shared-memory budget live in the
-// CTA's global slab).
-// Per iteration: (1) every warp compacts the conflicting-vertex bitmap into its own list; the rows
-// are cut into S contiguous segments (S = threads / |CV| when there are fewer rows than threads)
-// and thread t scans items [tC, tC + C) of the (row, segment) list, keeping per-item (min delta,
-// #ties) and its own aggregate; (2) one barrier publishes the per-warp minima and tie counts:
-// every thread derives the minimum delta, the total T and its own rank range; the warp holding
-// the j-th tie (j drawn from the iteration's Philox block) finds its colour with ballots over the
-// tied segment and applies the move; (3) all threads update gamma on the neighbours. Three barriers per iteration. The Philox blocks of 32
-// iterations are drawn at once, one per lane, by one warp every 32 iterations.
+// CTA's global slab). Thread t owns the vertices [t per, (t + 1) per), per = ceil(n / threads), so
+// thread order is vertex order. Every row carries a summary of its admissible-move structure
+// (Summ); a row's neighbourhood is evaluated from its summary in O(1) instead of a scan of its k
+// colours. Per iteration:
+//  (A) selection: each thread evaluates its conflicting vertices from their summaries (minimum
+//      delta and number of admissible colours reaching it), warps reduce, one barrier;
+//  (B) every thread derives the minimum delta, the tie total T and its warp's rank range; the warp
+//      holding the j-th tie (j drawn from the iteration's Philox block) finds the vertex and,
+//      with ballots over that row, the colour, and applies the move; one barrier;
+//  (C) each thread updates gamma on its vertices adjacent to the moved vertex and adjusts their
+//      summaries in O(1); a row whose class minimum may have risen, the moved vertex's row and
+//      rows whose earliest tabu expiry falls at the next iteration are queued; one barrier;
+//  (D) warps summarise the queued rows again (lanes over colours); one barrier.
+// The Philox blocks of 32 iterations are drawn at once, one per lane, every 32 iterations.
 //
 // Tabu list: u16 expiries relative to a base that advances by 2^14 every 2^14 iterations
 // (t' = expiry - base, 0 = free); a pair is tabu when t' > it - base.
@@ -213,20 +207,32 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   };
   uint8_t* colS = smem + L.col;
   uint8_t* bestS = smem + L.best;
-  uint32_t* rowres = (uint32_t*)(smem + L.rowres);
+  Summ* summ = (Summ*)(smem + L.summ);
+  uint32_t* vres = (uint32_t*)(smem + L.vres);  // per vertex of the selection: (delta + 2^15) << 16 | count
   uint16_t* degS = (uint16_t*)(smem + L.deg);
-  uint16_t* cvl = (uint16_t*)(smem + L.cvl) + (size_t)warp * tabu_list_cap(n, W);
-  uint32_t* cv = (uint32_t*)(smem + L.cv);
-  int32_t* red = (int32_t*)(smem + L.red);   // [W] warp minima, [W] warp tie totals
-  int32_t* sc = red + 2 * W;                 // scalars
+  uint16_t* queue = (uint16_t*)(smem + L.queue);
+  int32_t* qcount = (int32_t*)(queue + ((n + 7) & ~7));
+  int32_t* red = (int32_t*)(smem + L.red);   // [W] warp minima, [W] tie totals, [W] conflicting rows
+  int32_t* sc = red + 3 * W;                 // scalars
   uint32_t* rnd = (uint32_t*)(smem + L.rnd); // Philox words (r0, r1) of the next 32 iterations
   // sc[0] moved vertex (-1 none), sc[1] old colour, sc[2] new colour, sc[3] f after,
-  // sc[4] improved, sc[5] error, sc[6] bad input
+  // sc[4] improved, sc[5] error, sc[6] bad input, sc[7] summarise every row
   const int iters = (int)J.iters;  // at most 2^31 - 1 (checked by the host)
+  const int per = (n + NT - 1) / NT;
+  const int v0 = tid * per, v1 = min(v0 + per, n);
   auto draw32 = [&](int it0) {     // one warp: lane l draws the block of iteration it0 + l
     const U4 r = rng(R.seed, (uint32_t)(it0 + lane), R.gen, J.ind, kTagTabu);
     rnd[2 * lane] = r.x;
     rnd[2 * lane + 1] = r.y;
+  };
+  // every row, or the queued ones, summarised at relative iteration itn (one row per warp)
+  auto resummarise = [&](bool all, unsigned itn) {
+    const int cnt = all ? n : *qcount;
+    for (int q = warp; q < cnt; q += W) {
+      const int u = all ? q : queue[q];
+      const Summ s = summarise_row((const uint32_t*)grow_of(u), (const uint32_t*)trow_of(u), kw, colS[u], itn, lane);
+      if (lane == 0) summ[u] = s;
+    }
   };
 
   // ---- set-up: zero the tables (padding colours of gamma = 0xFFFF), load the start colouring --
@@ -239,7 +245,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       ((uint32_t*)trow_of(v))[w] = 0u;
     }
     if (tid < 16) sc[tid] = 0;
-    for (int i = tid; i < 64; i += NT) cv[i] = 0u;
+    if (tid == 0) *qcount = 0;
     if (warp == W - 1) draw32(0);
   }
   __syncthreads();
@@ -272,17 +278,11 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     degS[v] = (uint16_t)dv;
   }
   __syncthreads();
+  resummarise(true, 0u);
   int f;
   {
     int part = 0;
-    for (int v0 = warp * 32; v0 < n; v0 += NT) {
-      const int v = v0 + lane;
-      int g = 0;
-      if (v < n) g = grow_of(v)[colS[v]];
-      part += g;
-      const unsigned b = __ballot_sync(FULL, g > 0);
-      if (lane == 0) cv[v0 >> 5] = b;
-    }
+    for (int v = tid; v < n; v += NT) part += grow_of(v)[colS[v]];
     part = __reduce_add_sync(FULL, part);
     if (lane == 0) red[warp] = part;
     __syncthreads();
@@ -294,86 +294,55 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   int best_f = f;
   int moves = 0;
   int it = 0;
-  int64_t work_rows = 0, work_deg = 0;  // kept by thread 0 only
-
-  // per-thread slice of a bit row for the gamma update
-  int per = (n + NT - 1) / NT;
-  {
-    int p2 = 1;
-    while (p2 < per) p2 <<= 1;
-    per = p2 > 32 ? 32 : p2;
-  }
-  const uint32_t slice_mask = per == 32 ? 0xFFFFFFFFu : ((1u << per) - 1u);
-  const float fNT = (float)NT + 0.5f;
-  int lb = 0;  // bitmap bits per lane = 2^lb, 32 * 2^lb >= n (n <= 2048)
-  while ((32 << lb) < n) ++lb;
+  int64_t work_rows = 0, work_deg = 0, work_resum = 0;  // kept by thread 0 only
 
   for (it = 0; it < iters; ++it) {
     if (f == 0) break;
     const unsigned itrel = (unsigned)(it & 0x3FFF);
-    // ---- phase 1: conflicting-vertex list of this warp, scan of this thread's items ----------
-    const CvView view = cv_view(cv, lb, lane);
-    const int ncv = view.total;
+    // ---- (A) selection from the summaries of this thread's conflicting vertices --------------
+    int tmin = INT_MAX, tcnt = 0, nconf = 0;
+    {
+      const int thrb = best_f - f;  // a tabu move is aspirated when gamma < thrb + gamma[v][col v]
+      for (int v = v0; v < v1; ++v) {
+        const int g0 = grow_of(v)[colS[v]];
+        uint32_t res = 0u;
+        if (g0 > 0) {
+          ++nconf;
+          const Summ s = summ[v];
+          const unsigned nt = s.ntcnt ? s.ntmin : kNoKey;
+          const unsigned ta = (s.tcnt && (int)s.tmin < thrb + g0) ? s.tmin : kNoKey;
+          const unsigned adm = min(nt, ta);
+          if (adm != kNoKey) {
+            const int c = (nt == adm ? s.ntcnt : 0) + (ta == adm ? s.tcnt : 0);
+            const int d = (int)adm - g0;
+            res = ((uint32_t)(d + 32768) << 16) | (uint32_t)c;
+            if (d < tmin) { tmin = d; tcnt = c; }
+            else if (d == tmin) tcnt += c;
+          }
+        }
+        vres[v] = res;
+      }
+    }
     if (tid == 0) {
-      work_rows += ncv;
       sc[0] = -1;
       // cancellation, polled every 1024 iterations: the search stops after this iteration's
       // selection and reports its best colouring so far
       if ((it & 1023) == 0 && R.cancel && *(volatile const int32_t*)R.cancel != 0) sc[5] = 3;
     }
-    // S = min(kw, floor(NT / ncv)) and Lw = ceil(kw / S) in float arithmetic: both quotients are
-    // of integers below 2^16 shifted by one half, far from the next integer compared with the
-    // rounding error, so the truncations are exact
-    int S = 1;
-    if (ncv > 0 && ncv < NT) S = min(kw, (int)(fNT / (float)ncv));
-    const float rS = 1.0f / (float)S;
-    const int Lw = (int)(((float)(kw + S - 1) + 0.5f) * rS);
-    const int items = ncv * S;
-    const int C = (items + NT - 1) / NT;
-    const int i0 = tid * C;
-    const int i1 = min(i0 + C, items);
-    // this warp's rows [rlo, rhi] of the conflicting-vertex list, compacted from the bitmap in
-    // ascending vertex order (rank = position among the conflicting vertices)
-    const int wi0 = 32 * warp * C, wi1 = min(wi0 + 32 * C, items);
-    const int rlo = S == 1 ? wi0 : (int)(((float)wi0 + 0.5f) * rS);
-    const int rhi = wi1 <= wi0 ? rlo - 1 : (S == 1 ? wi1 - 1 : (int)(((float)(wi1 - 1) + 0.5f) * rS));
-    if (view.excl <= rhi && view.excl + view.cnt > rlo) {
-      uint64_t wb = view.w;
-      int rank = view.excl;
-      while (wb && rank <= rhi) {
-        if (rank >= rlo) cvl[rank - rlo] = (uint16_t)((lane << lb) + __ffsll(wb) - 1);
-        wb &= wb - 1;
-        ++rank;
-      }
-    }
-    __syncwarp();
-    int tmin = INT_MAX, tcnt = 0;
-    for (int i = i0; i < i1; ++i) {
-      const int r = S == 1 ? i : (int)(((float)i + 0.5f) * rS), sg = i - r * S;
-      const int v = cvl[r - rlo];
-      const int colv = colS[v];
-      const uint16_t* grow = grow_of(v);
-      const int g0 = grow[colv];
-      const int w0 = sg * Lw, w1 = min(w0 + Lw, kw);
-      unsigned km;
-      int kc;
-      scan_seg((const uint32_t*)grow, (const uint32_t*)trow_of(v), w0, w1, colv >> 1,
-               0xFFFFu << (16 * (colv & 1)), itrel, best_f - f + g0, km, kc);
-      const int rc = km == 0xFFFFu ? 0 : kc;
-      const int dm = km == 0xFFFFu ? kNone16 : (int)km - g0;
-      rowres[i] = ((uint32_t)(uint16_t)dm << 16) | (uint32_t)rc;
-      if (rc > 0) {
-        if (dm < tmin) { tmin = dm; tcnt = rc; }
-        else if (dm == tmin) tcnt += rc;
-      }
-    }
     {
       const int wm = __reduce_min_sync(FULL, tmin);
       const int wc = (int)__reduce_add_sync(FULL, (wm != INT_MAX && tmin == wm) ? (unsigned)tcnt : 0u);
-      if (lane == 0) { red[warp] = wm; red[W + warp] = wc; }
+      const int wn = (int)__reduce_add_sync(FULL, (unsigned)nconf);
+      if (lane == 0) { red[warp] = wm; red[W + warp] = wc; red[2 * W + warp] = wn; }
     }
     __syncthreads();
-    // ---- phase 2: minimum delta, tie ranks, move ---------------------------------------------
+    // ---- (B) minimum delta, tie ranks, move -------------------------------------------------
+    if (tid == 0) {
+      *qcount = 0;
+      int nc = 0;
+      for (int w = 0; w < W; ++w) nc += red[2 * W + w];
+      work_rows += nc;
+    }
     int wmin[W], wcnt[W];
     if constexpr (W % 4 == 0) {
 #pragma unroll
@@ -398,10 +367,9 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       pre += w < warp ? x : 0;
       wtot += w == warp ? x : 0;
     }
-    const uint32_t r0 = rnd[2 * (it & 31)];
-    const uint32_t j = T > 0 ? below(r0, (uint32_t)T) : 0u;
+    const uint32_t j = T > 0 ? below(rnd[2 * (it & 31)], (uint32_t)T) : 0u;
     if (T > 0 && (int)j >= pre && (int)j < pre + wtot) {  // the j-th tie is in this warp (warp-uniform)
-      const int ct = (dstar != INT_MAX && tmin == dstar) ? tcnt : 0;
+      const int ct = tmin == dstar ? tcnt : 0;
       int incl = ct;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -410,50 +378,47 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       }
       const int lo = pre + incl - ct;
       const bool hit = ct > 0 && (int)j >= lo && (int)j < lo + ct;  // this thread holds the j-th tie
-      int hit_item = -1, hit_rank = 0;
+      int hit_v = -1, hit_rank = 0;
       if (hit) {
         int jj = (int)j - lo;
-        for (int i = i0; i < i1; ++i) {
-          const uint32_t rr = rowres[i];
-          const int rm = (int16_t)(rr >> 16), rcn = (int)(rr & 0xFFFF);
-          if (rm != dstar || rcn == 0) continue;
+        for (int v = v0; v < v1; ++v) {
+          const uint32_t rr = vres[v];
+          const int rcn = (int)(rr & 0xFFFFu);
+          if (rcn == 0 || (int)(rr >> 16) - 32768 != dstar) continue;
           if (jj >= rcn) { jj -= rcn; continue; }
-          hit_item = i;
+          hit_v = v;
           hit_rank = jj;
           break;
         }
       }
-      // the whole warp searches the winning item's segment: lane l takes words w0 + l, w0 + 32 + l,
-      // ...; ballots order the tied colours (word by word, low half first) and find the rank
+      // the whole warp searches the winning row: lane l takes words l, l + 32, ...; ballots order
+      // the tied colours (word by word, low half first) and find the rank
       const unsigned hb = __ballot_sync(FULL, hit);
       const int hl = hb ? __ffs(hb) - 1 : 0;
-      const int item = hb ? __shfl_sync(FULL, hit_item, hl) : -1;
+      const int v = hb ? __shfl_sync(FULL, hit_v, hl) : -1;
       int jj = __shfl_sync(FULL, hit_rank, hl);
-      int mv = -1, mc = -1;
-      if (item >= 0) {
-        const int r = S == 1 ? item : (int)(((float)item + 0.5f) * rS), sg = item - r * S;
-        const int v = cvl[r - rlo];
-        const int colv = colS[v];
+      int mc = -1, colv = 0;
+      if (v >= 0) {
+        colv = colS[v];
         const uint16_t* grow = grow_of(v);
         const uint32_t* g32 = (const uint32_t*)grow;
         const uint32_t* t32 = (const uint32_t*)trow_of(v);
         const int g0 = grow[colv];
-        const int w0 = sg * Lw, w1 = min(w0 + Lw, kw);
         const unsigned kmin = (unsigned)(dstar + g0);
         const int thr = best_f - f + g0;
         const int killw = colv >> 1;
         const uint32_t killm = 0xFFFFu << (16 * (colv & 1));
         const unsigned lt = (1u << lane) - 1u;
-        for (int wb = w0; wb < w1 && mc < 0; wb += 32) {
+        for (int wb = 0; wb < kw && mc < 0; wb += 32) {
           const int w = wb + lane;
           bool m0 = false, m1 = false;
-          if (w < w1) {
+          if (w < kw) {
             uint32_t gw = g32[w];
             const uint32_t tw = t32[w];
             if (w == killw) gw |= killm;
             const unsigned ga = gw & 0xFFFFu, gb = gw >> 16;
-            const unsigned k0 = ((tw & 0xFFFFu) <= itrel || (int)ga < thr) ? ga : 0xFFFFu;
-            const unsigned k1 = ((tw >> 16) <= itrel || (int)gb < thr) ? gb : 0xFFFFu;
+            const unsigned k0 = ((tw & 0xFFFFu) <= itrel || (int)ga < thr) ? ga : kNoKey;
+            const unsigned k1 = ((tw >> 16) <= itrel || (int)gb < thr) ? gb : kNoKey;
             m0 = k0 == kmin;
             m1 = k1 == kmin;
           }
@@ -464,52 +429,51 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           if (fb) mc = __shfl_sync(FULL, 2 * w + ((jj == before && m0) ? 0 : 1), __ffs(fb) - 1);
           else jj -= __popc(b0) + __popc(b1);
         }
-        mv = v;
       }
       if (lane == 0) {
-        if (mv >= 0 && mc >= 0 && mc < k) {
-          const int old = colS[mv];
-          colS[mv] = (uint8_t)mc;
+        if (v >= 0 && mc >= 0 && mc < k) {
+          colS[v] = (uint8_t)mc;
           const int fn = f + dstar;
           // alpha f in 32-bit unsigned arithmetic: the host bounds alpha_num * |E| below 2^32
           const uint32_t tt = below(rnd[2 * (it & 31) + 1], R.L1) + ((uint32_t)R.an * (uint32_t)fn) / (uint32_t)R.ad;
           if (tt > 32766u) sc[5] = 1;
-          trow_of(mv)[old] = (uint16_t)(itrel + 1u + tt);
-          const uint32_t bit = 1u << (mv & 31);
-          if (grow_of(mv)[mc] > 0) atomicOr(cv + (mv >> 5), bit);
-          else atomicAnd(cv + (mv >> 5), ~bit);
-          sc[0] = mv; sc[1] = old; sc[2] = mc; sc[3] = fn; sc[4] = fn < best_f;
-          if (J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(mv, mc, dstar, T);
+          trow_of(v)[colv] = (uint16_t)(itrel + 1u + tt);
+          sc[0] = v; sc[1] = colv; sc[2] = mc; sc[3] = fn; sc[4] = fn < best_f;
+          if (J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(v, mc, dstar, T);
         } else {
-          sc[5] = 2;  // tie counts inconsistent with the scan: refuse to move
+          sc[5] = 2;  // tie counts inconsistent with the row: refuse to move
         }
       }
     }
     if (T == 0 && tid == 0 && J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(-1, -1, 0, 0);
     __syncthreads();
     if (sc[5]) break;
-    // ---- phase 3: gamma update over the neighbours of the moved vertex ------------------------
+    // ---- (C) gamma and summaries of the moved vertex's neighbours --------------------------
     const int mv = sc[0];
+    const bool sweep = ((it + 1) & 0x3FFF) == 0;
+    const unsigned itn = sweep ? 0u : itrel + 1u;  // relative iteration of the next selection
     if (mv >= 0) {
       const int old = sc[1], nw = sc[2];
       f = sc[3];
       ++moves;
       if (tid == 0) work_deg += degS[mv];
       const uint32_t* brow = J.bits + (size_t)mv * nwords;
-      for (int b0 = tid * per; b0 < n; b0 += NT * per) {
-        uint32_t m = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
-        while (m) {
-          const int u = b0 + __ffs(m) - 1;
-          m &= m - 1;
+      for (int u = v0; u < v1; ++u) {
+        bool queue_it = u == mv;  // its colour changed and its old colour became tabu
+        if ((__ldg(brow + (u >> 5)) >> (u & 31)) & 1u) {
           uint16_t* grow = grow_of(u);
-          const int go = grow[old] - 1;
-          grow[old] = (uint16_t)go;
-          const int gn = grow[nw] + 1;
-          grow[nw] = (uint16_t)gn;
+          const uint16_t* trow = trow_of(u);
+          const unsigned go = grow[old], gn = grow[nw];
+          grow[old] = (uint16_t)(go - 1u);
+          grow[nw] = (uint16_t)(gn + 1u);
           const int cu = colS[u];
-          if (cu == old && go == 0) atomicAnd(cv + (u >> 5), ~(1u << (u & 31)));
-          else if (cu == nw && gn == 1) atomicOr(cv + (u >> 5), 1u << (u & 31));
+          Summ s = summ[u];
+          if (old != cu) summ_lower(s, trow[old] > itrel, go - 1u);
+          if (nw != cu && !summ_raise(s, trow[nw] > itrel, gn)) queue_it = true;
+          summ[u] = s;
         }
+        if (!queue_it && summ[u].nexp <= itn) queue_it = true;  // a tabu colour expires
+        if (queue_it && !sweep) queue[atomicAdd(qcount, 1)] = (uint16_t)u;
       }
       if (sc[4]) {
         best_f = f;
@@ -517,11 +481,14 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
         uint32_t* d32 = (uint32_t*)bestS;
         for (int i = tid; i < (n + 3) / 4; i += NT) d32[i] = s32[i];
       }
+    } else {
+      for (int u = v0; u < v1; ++u)
+        if (!sweep && summ[u].nexp <= itn) queue[atomicAdd(qcount, 1)] = (uint16_t)u;
     }
     // the Philox block of the next 32 iterations (every reader of the current one has passed
     // the barrier above)
     if (((it + 1) & 31) == 0 && warp == W - 1) draw32(it + 1);
-    if (((it + 1) & 0x3FFF) == 0) {
+    if (sweep) {
       // the base advances by 2^14: relative expiries drop by 2^14, expired ones become 0
       for (int i = tid; i < n * kw; i += NT) {
         const int v = i / kw;
@@ -531,6 +498,10 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
         *t32 = (lo > 0x4000u ? lo - 0x4000u : 0u) | ((hi > 0x4000u ? hi - 0x4000u : 0u) << 16);
       }
     }
+    __syncthreads();
+    // ---- (D) summaries of the queued rows (every row after a sweep) -------------------------
+    if (tid == 0) work_resum += sweep ? n : *qcount;
+    resummarise(sweep, itn);
     __syncthreads();
   }
   if (sc[5]) {
@@ -542,7 +513,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   if (tid == 0) {
     *J.best_f = best_f;
     if (J.moves) *J.moves = moves;
-    if (J.work) { J.work[0] = work_rows; J.work[1] = work_deg; }
+    if (J.work) { J.work[0] = work_rows; J.work[1] = work_deg; J.work[2] = work_resum; }
   }
 }
 
@@ -571,7 +542,7 @@ __global__ void __launch_bounds__(W * 32, W >= 16 ? 1 : 2) tabucol_batch_kernel(
     J.best_f = a.best_f + i;
     J.moves = a.moves ? a.moves + i : nullptr;
     J.trace = a.trace ? a.trace + (size_t)i * a.iters * 4 : nullptr;
-    J.work = a.work ? a.work + 2 * (size_t)i : nullptr;
+    J.work = a.work ? a.work + 3 * (size_t)i : nullptr;
     J.off = a.off;
     J.iters = a.iters;
     J.ind = a.ind_base + (uint32_t)i;
