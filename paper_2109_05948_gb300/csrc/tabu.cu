@@ -79,7 +79,7 @@ static_assert(sizeof(Summ) == 8, "a row summary is 8 bytes");
 constexpr unsigned kNoKey = 0xFFFFu;
 
 struct TabuSmem {
-  size_t gam, tab, col, best, summ, vres, deg, queue, red, rnd, total;
+  size_t gam, tab, col, best, summ, vres, deg, queue, red, rnd, brow, total;
   int rs;  // rows of gamma and tab held in shared memory; rows rs..n-1 live in the CTA's slab
 };
 
@@ -97,6 +97,7 @@ __host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps, si
   s.queue = o; o += align16((size_t)n * 2 + 16);
   s.red = o; o += align16((size_t)warps * 12 + 64);
   s.rnd = o; o += 32 * 8;
+  s.brow = o; o += 64 * 4;  // the moved vertex's adjacency bit row (n <= 2048)
   const size_t row = (size_t)ks * 2;
   size_t rs = budget > o + 32 ? (budget - o - 32) / (2 * row) : 0;
   if (rs > (size_t)n) rs = n;
@@ -215,6 +216,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   int32_t* red = (int32_t*)(smem + L.red);   // [W] warp minima, [W] tie totals, [W] conflicting rows
   int32_t* sc = red + 3 * W;                 // scalars
   uint32_t* rnd = (uint32_t*)(smem + L.rnd); // Philox words (r0, r1) of the next 32 iterations
+  uint32_t* browS = (uint32_t*)(smem + L.brow);  // adjacency bit row of this iteration's moved vertex
   // sc[0] moved vertex (-1 none), sc[1] old colour, sc[2] new colour, sc[3] f after,
   // sc[4] improved, sc[5] error, sc[6] bad input, sc[7] summarise every row
   const int iters = (int)J.iters;  // at most 2^31 - 1 (checked by the host)
@@ -398,7 +400,13 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       const int v = hb ? __shfl_sync(FULL, hit_v, hl) : -1;
       int jj = __shfl_sync(FULL, hit_rank, hl);
       int mc = -1, colv = 0;
+      // the moved vertex's bit row, loaded now and stored to shared memory after the colour search
+      // so that the load latency overlaps it
+      uint32_t bw0 = 0u, bw1 = 0u;
       if (v >= 0) {
+        const uint32_t* bsrc = J.bits + (size_t)v * nwords;
+        if (lane < nwords) bw0 = __ldg(bsrc + lane);
+        if (lane + 32 < nwords) bw1 = __ldg(bsrc + lane + 32);
         colv = colS[v];
         const uint16_t* grow = grow_of(v);
         const uint32_t* g32 = (const uint32_t*)grow;
@@ -430,6 +438,8 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           else jj -= __popc(b0) + __popc(b1);
         }
       }
+      if (lane < nwords) browS[lane] = bw0;
+      if (lane + 32 < nwords) browS[lane + 32] = bw1;
       if (lane == 0) {
         if (v >= 0 && mc >= 0 && mc < k) {
           colS[v] = (uint8_t)mc;
@@ -457,10 +467,9 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       f = sc[3];
       ++moves;
       if (tid == 0) work_deg += degS[mv];
-      const uint32_t* brow = J.bits + (size_t)mv * nwords;
       for (int u = v0; u < v1; ++u) {
         bool queue_it = u == mv;  // its colour changed and its old colour became tabu
-        if ((__ldg(brow + (u >> 5)) >> (u & 31)) & 1u) {
+        if ((browS[u >> 5] >> (u & 31)) & 1u) {
           uint16_t* grow = grow_of(u);
           const uint16_t* trow = trow_of(u);
           const unsigned go = grow[old], gn = grow[nw];
