@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--mem-seeds", type=int, default=5)
     ap.add_argument("--mem-max-gens", type=int, default=40)
     ap.add_argument("--mem-time-limit", type=float, default=120.0, help="seconds per run")
+    ap.add_argument("--warps", type=int, default=0, help="warps per individual (0: the library's default)")
     ap.add_argument("--warm-start", type=int, default=0,
                     help="run this many iterations first (untimed) and start every step from their best "
                          "colourings (profiling the late phase of the search)")
@@ -576,7 +577,7 @@ def main():
         if timed:
             kev[s][0].record(stream)
         dlmcol.dlm_tabucol_batch_ex(ctx, g, K, pop, col, best_f, moves[s if timed else 0], iters, dlmcol.COL_TENURE,
-                                    SEED, 0, base, 0, None, work[s if timed else 0])
+                                    SEED, 0, base, args.warps, None, work[s if timed else 0])
         if timed:
             kev[s][1].record(stream)
 

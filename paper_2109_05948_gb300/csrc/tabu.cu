@@ -468,20 +468,21 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       ++moves;
       if (tid == 0) work_deg += degS[mv];
       for (int u = v0; u < v1; ++u) {
-        bool queue_it = u == mv;  // its colour changed and its old colour became tabu
+        Summ s = summ[u];
+        // its colour changed and its old colour became tabu, or one of its tabu colours expires
+        bool queue_it = u == mv || s.nexp <= itn;
         if ((browS[u >> 5] >> (u & 31)) & 1u) {
           uint16_t* grow = grow_of(u);
           const uint16_t* trow = trow_of(u);
           const unsigned go = grow[old], gn = grow[nw];
+          const unsigned to = trow[old], tn = trow[nw];
+          const int cu = colS[u];
           grow[old] = (uint16_t)(go - 1u);
           grow[nw] = (uint16_t)(gn + 1u);
-          const int cu = colS[u];
-          Summ s = summ[u];
-          if (old != cu) summ_lower(s, trow[old] > itrel, go - 1u);
-          if (nw != cu && !summ_raise(s, trow[nw] > itrel, gn)) queue_it = true;
+          if (old != cu) summ_lower(s, to > itrel, go - 1u);
+          if (nw != cu && !summ_raise(s, tn > itrel, gn)) queue_it = true;
           summ[u] = s;
         }
-        if (!queue_it && summ[u].nexp <= itn) queue_it = true;  // a tabu colour expires
         if (queue_it && !sweep) queue[atomicAdd(qcount, 1)] = (uint16_t)u;
       }
       if (sc[4]) {
@@ -541,7 +542,7 @@ struct TabuBatchArgs {
 };
 
 template <int W>
-__global__ void __launch_bounds__(W * 32, W >= 16 ? 1 : 2) tabucol_batch_kernel(TabuBatchArgs a) {
+__global__ void __launch_bounds__(W * 32, 2) tabucol_batch_kernel(TabuBatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   // one individual per CTA, or (when rows spill to a per-CTA slab) resident CTAs loop over them
   for (int i = blockIdx.x; i < a.pop; i += gridDim.x) {
@@ -573,7 +574,7 @@ struct MultiJob {
 };
 
 template <int W>
-__global__ void __launch_bounds__(W * 32, W >= 16 ? 1 : 2) tabucol_multi_kernel(const MultiJob* jobs, int32_t njobs,
+__global__ void __launch_bounds__(W * 32, 2) tabucol_multi_kernel(const MultiJob* jobs, int32_t njobs,
                                                                int32_t* queue, TabuRule rule) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int32_t next;
