@@ -19,8 +19,8 @@
 //  * update: each thread changes gamma on its vertices adjacent to the moved vertex (bit row of
 //    the graph, L1/L2 resident) and adjusts their summaries in O(1); rows whose class minimum may
 //    have risen, the moved vertex and rows with an expiring tabu colour are summarised again by
-//    whole warps (lanes over colours).
-//  Four CTA barriers per iteration.
+//    the owner's warp (lanes over colours).
+//  Three CTA barriers per iteration.
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -79,7 +79,7 @@ static_assert(sizeof(Summ) == 8, "a row summary is 8 bytes");
 constexpr unsigned kNoKey = 0xFFFFu;
 
 struct TabuSmem {
-  size_t gam, tab, col, best, summ, vres, deg, queue, red, rnd, brow, total;
+  size_t gam, tab, col, best, summ, vres, deg, red, rnd, brow, total;
   int rs;  // rows of gamma and tab held in shared memory; rows rs..n-1 live in the CTA's slab
 };
 
@@ -94,7 +94,6 @@ __host__ __device__ inline TabuSmem tabu_smem_layout(int n, int k, int warps, si
   s.summ = o; o += align16((size_t)n * sizeof(Summ));
   s.vres = o; o += align16((size_t)n * 4);
   s.deg = o; o += align16((size_t)n * 2);
-  s.queue = o; o += align16((size_t)n * 2 + 16);
   s.red = o; o += align16((size_t)warps * 12 + 64);
   s.rnd = o; o += 32 * 8;
   s.brow = o; o += 64 * 4;  // the moved vertex's adjacency bit row (n <= 2048)
@@ -175,13 +174,13 @@ __device__ __forceinline__ bool summ_raise(Summ& s, bool tabu, unsigned g) {
 // colours. Per iteration:
 //  (A) selection: each thread evaluates its conflicting vertices from their summaries (minimum
 //      delta and number of admissible colours reaching it), warps reduce, one barrier;
-//  (B) every thread derives the minimum delta, the tie total T and its warp's rank range; the warp
+//  (B) every warp derives (warp collectives) the minimum delta, the tie total T and its rank range; the warp
 //      holding the j-th tie (j drawn from the iteration's Philox block) finds the vertex and,
 //      with ballots over that row, the colour, and applies the move; one barrier;
 //  (C) each thread updates gamma on its vertices adjacent to the moved vertex and adjusts their
 //      summaries in O(1); a row whose class minimum may have risen, the moved vertex's row and
-//      rows whose earliest tabu expiry falls at the next iteration are queued; one barrier;
-//  (D) warps summarise the queued rows again (lanes over colours); one barrier.
+//      rows whose earliest tabu expiry falls at the next iteration are flagged by their owner
+//      thread, and the owner's warp summarises them again (lanes over colours); one barrier.
 // The Philox blocks of 32 iterations are drawn at once, one per lane, every 32 iterations.
 //
 // Tabu list: u16 expiries relative to a base that advances by 2^14 every 2^14 iterations
@@ -211,8 +210,6 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   Summ* summ = (Summ*)(smem + L.summ);
   uint32_t* vres = (uint32_t*)(smem + L.vres);  // per vertex of the selection: (delta + 2^15) << 16 | count
   uint16_t* degS = (uint16_t*)(smem + L.deg);
-  uint16_t* queue = (uint16_t*)(smem + L.queue);
-  int32_t* qcount = (int32_t*)(queue + ((n + 7) & ~7));
   int32_t* red = (int32_t*)(smem + L.red);   // [W] warp minima, [W] tie totals, [W] conflicting rows
   int32_t* sc = red + 3 * W;                 // scalars
   uint32_t* rnd = (uint32_t*)(smem + L.rnd); // Philox words (r0, r1) of the next 32 iterations
@@ -227,15 +224,6 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     rnd[2 * lane] = r.x;
     rnd[2 * lane + 1] = r.y;
   };
-  // every row, or the queued ones, summarised at relative iteration itn (one row per warp)
-  auto resummarise = [&](bool all, unsigned itn) {
-    const int cnt = all ? n : *qcount;
-    for (int q = warp; q < cnt; q += W) {
-      const int u = all ? q : queue[q];
-      const Summ s = summarise_row((const uint32_t*)grow_of(u), (const uint32_t*)trow_of(u), kw, colS[u], itn, lane);
-      if (lane == 0) summ[u] = s;
-    }
-  };
 
   // ---- set-up: zero the tables (padding colours of gamma = 0xFFFF), load the start colouring --
   {
@@ -247,7 +235,6 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       ((uint32_t*)trow_of(v))[w] = 0u;
     }
     if (tid < 16) sc[tid] = 0;
-    if (tid == 0) *qcount = 0;
     if (warp == W - 1) draw32(0);
   }
   __syncthreads();
@@ -280,7 +267,10 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     degS[v] = (uint16_t)dv;
   }
   __syncthreads();
-  resummarise(true, 0u);
+  for (int u = warp; u < n; u += W) {  // every row's summary at iteration 0, one row per warp
+    const Summ su = summarise_row((const uint32_t*)grow_of(u), (const uint32_t*)trow_of(u), kw, colS[u], 0u, lane);
+    if (lane == 0) summ[u] = su;
+  }
   int f;
   {
     int part = 0;
@@ -340,35 +330,18 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     __syncthreads();
     // ---- (B) minimum delta, tie ranks, move -------------------------------------------------
     if (tid == 0) {
-      *qcount = 0;
       int nc = 0;
       for (int w = 0; w < W; ++w) nc += red[2 * W + w];
       work_rows += nc;
     }
-    int wmin[W], wcnt[W];
-    if constexpr (W % 4 == 0) {
-#pragma unroll
-      for (int q = 0; q < W / 4; ++q) {
-        const int4 a = reinterpret_cast<const int4*>(red)[q];
-        const int4 b = reinterpret_cast<const int4*>(red + W)[q];
-        wmin[4 * q] = a.x; wmin[4 * q + 1] = a.y; wmin[4 * q + 2] = a.z; wmin[4 * q + 3] = a.w;
-        wcnt[4 * q] = b.x; wcnt[4 * q + 1] = b.y; wcnt[4 * q + 2] = b.z; wcnt[4 * q + 3] = b.w;
-      }
-    } else {
-#pragma unroll
-      for (int w = 0; w < W; ++w) { wmin[w] = red[w]; wcnt[w] = red[W + w]; }
-    }
-    int dstar = INT_MAX;
-#pragma unroll
-    for (int w = 0; w < W; ++w) dstar = min(dstar, wmin[w]);
-    int T = 0, pre = 0, wtot = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-      const int x = (dstar != INT_MAX && wmin[w] == dstar) ? wcnt[w] : 0;
-      T += x;
-      pre += w < warp ? x : 0;
-      wtot += w == warp ? x : 0;
-    }
+    // lanes 0..W-1 hold the warps' minima and tie totals
+    const int lw = lane < W ? red[lane] : INT_MAX;
+    const int lc = lane < W ? red[W + lane] : 0;
+    const int dstar = __reduce_min_sync(FULL, lw);
+    const int xl = (dstar != INT_MAX && lw == dstar) ? lc : 0;
+    const int T = (int)__reduce_add_sync(FULL, (unsigned)xl);
+    const int pre = (int)__reduce_add_sync(FULL, lane < warp ? (unsigned)xl : 0u);
+    const int wtot = __shfl_sync(FULL, xl, warp);
     const uint32_t j = T > 0 ? below(rnd[2 * (it & 31)], (uint32_t)T) : 0u;
     if (T > 0 && (int)j >= pre && (int)j < pre + wtot) {  // the j-th tie is in this warp (warp-uniform)
       const int ct = tmin == dstar ? tcnt : 0;
@@ -458,10 +431,11 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
     if (T == 0 && tid == 0 && J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(-1, -1, 0, 0);
     __syncthreads();
     if (sc[5]) break;
-    // ---- (C) gamma and summaries of the moved vertex's neighbours --------------------------
+    // ---- (C) gamma and summaries of the moved vertex's neighbours ------------------------------
     const int mv = sc[0];
     const bool sweep = ((it + 1) & 0x3FFF) == 0;
     const unsigned itn = sweep ? 0u : itrel + 1u;  // relative iteration of the next selection
+    uint64_t flags = 0;  // owned rows to summarise again: bit q = vertex v0 + q
     if (mv >= 0) {
       const int old = sc[1], nw = sc[2];
       f = sc[3];
@@ -470,7 +444,7 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       for (int u = v0; u < v1; ++u) {
         Summ s = summ[u];
         // its colour changed and its old colour became tabu, or one of its tabu colours expires
-        bool queue_it = u == mv || s.nexp <= itn;
+        bool again = u == mv || s.nexp <= itn;
         if ((browS[u >> 5] >> (u & 31)) & 1u) {
           uint16_t* grow = grow_of(u);
           const uint16_t* trow = trow_of(u);
@@ -480,10 +454,10 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
           grow[old] = (uint16_t)(go - 1u);
           grow[nw] = (uint16_t)(gn + 1u);
           if (old != cu) summ_lower(s, to > itrel, go - 1u);
-          if (nw != cu && !summ_raise(s, tn > itrel, gn)) queue_it = true;
+          if (nw != cu && !summ_raise(s, tn > itrel, gn)) again = true;
           summ[u] = s;
         }
-        if (queue_it && !sweep) queue[atomicAdd(qcount, 1)] = (uint16_t)u;
+        if (again) flags |= 1ull << (u - v0);
       }
       if (sc[4]) {
         best_f = f;
@@ -493,26 +467,49 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
       }
     } else {
       for (int u = v0; u < v1; ++u)
-        if (!sweep && summ[u].nexp <= itn) queue[atomicAdd(qcount, 1)] = (uint16_t)u;
+        if (summ[u].nexp <= itn) flags |= 1ull << (u - v0);
     }
     // the Philox block of the next 32 iterations (every reader of the current one has passed
     // the barrier above)
     if (((it + 1) & 31) == 0 && warp == W - 1) draw32(it + 1);
     if (sweep) {
-      // the base advances by 2^14: relative expiries drop by 2^14, expired ones become 0
-      for (int i = tid; i < n * kw; i += NT) {
-        const int v = i / kw;
-        uint32_t* t32 = (uint32_t*)trow_of(v) + (i - v * kw);
-        const uint32_t w = *t32;
-        const uint32_t lo = w & 0xFFFF, hi = w >> 16;
-        *t32 = (lo > 0x4000u ? lo - 0x4000u : 0u) | ((hi > 0x4000u ? hi - 0x4000u : 0u) << 16);
+      // the base advances by 2^14: relative expiries drop by 2^14, expired ones become 0; each
+      // thread rebases its own rows, and every row is summarised again
+      for (int u = v0; u < v1; ++u) {
+        uint32_t* t32 = (uint32_t*)trow_of(u);
+        for (int w = 0; w < kw; ++w) {
+          const uint32_t x = t32[w];
+          const uint32_t lo = x & 0xFFFF, hi = x >> 16;
+          t32[w] = (lo > 0x4000u ? lo - 0x4000u : 0u) | ((hi > 0x4000u ? hi - 0x4000u : 0u) << 16);
+        }
+      }
+      flags = v1 > v0 ? (~0ull >> (64 - (v1 - v0))) : 0ull;
+    }
+    // the warp summarises its lanes' flagged rows (lanes over colours); a row is written only by
+    // its owner thread, so no other warp touches it
+    __syncwarp();
+    for (unsigned pend = __ballot_sync(FULL, flags != 0); pend; pend &= pend - 1) {
+      const int l = __ffs(pend) - 1;
+      uint64_t fl = __shfl_sync(FULL, flags, l);
+      const int base = __shfl_sync(FULL, v0, l);
+      for (; fl; fl &= fl - 1) {
+        const int u = base + __ffsll(fl) - 1;
+        const Summ su = summarise_row((const uint32_t*)grow_of(u), (const uint32_t*)trow_of(u), kw, colS[u], itn, lane);
+        if (lane == 0) {
+          summ[u] = su;
+          ++work_resum;
+        }
       }
     }
     __syncthreads();
-    // ---- (D) summaries of the queued rows (every row after a sweep) -------------------------
-    if (tid == 0) work_resum += sweep ? n : *qcount;
-    resummarise(sweep, itn);
+  }
+  {  // rows summarised again, summed over the warps
+    if (lane == 0) red[warp] = (int32_t)work_resum;
     __syncthreads();
+    if (tid == 0) {
+      work_resum = 0;
+      for (int w = 0; w < W; ++w) work_resum += red[w];
+    }
   }
   if (sc[5]) {
     if (tid == 0)
