@@ -649,7 +649,9 @@ static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K
   const int nchunks = K / tc::BK;
   if (kc <= 0) kc = nchunks;
   tc::GemmShape sh{M, N, K, kc};
-  dim3 grid((M + tc::BM - 1) / tc::BM, N / BN, (nchunks + kc - 1) / kc);
+  // persistent: one CTA per SM (TMEM holds two BN-column accumulators), looping over the tiles
+  const int tiles = ((M + tc::BM - 1) / tc::BM) * (N / BN) * ((nchunks + kc - 1) / kc);
+  dim3 grid(std::min(tiles, ctx->num_sms));
   auto launch = [&](auto kfn, size_t smem, bool& attr) -> dlm_status {
     if (!attr) {
       DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1,7 +1,7 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) for the offspring scorer.
 //
 // C[M][N] = A[M][K] . B[N][K]^T with A and B bf16, both K-major (row-major with K contiguous),
-// FP32 accumulation in tensor memory (TMEM). One CTA computes one 128 x BN tile:
+// FP32 accumulation in tensor memory (TMEM). Persistent CTAs loop over 128 x BN tiles:
 //   warp 0      TMA producer: 128 x 64 and BN x 64 tiles (128-byte swizzle) into an S-stage ring
 //   warp 1      allocates TMEM; one lane issues tcgen05.mma (M = 128, N = BN, K = 16 per
 //               instruction, 4 per 64-wide stage) and commits each stage back to the producer
@@ -110,10 +110,15 @@ struct GemmShape {
   int k_chunks_per_cta; // split-K: number of 64-wide chunks per CTA along blockIdx.z
 };
 
-// Epilogue functors receive (row, col0, v[16]) for 16 consecutive output columns of one row.
+// Epilogue functors receive (row, col0, v[16]) for 16 consecutive output columns of one row,
+// then finish(row); the kernel copies the functor for every tile, so per-row state starts fresh.
 // NA / NB = 2: the operand is given as two bf16 matrices, the hi and lo parts of an fp32 matrix
 // (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); every K step then issues hi.hi, and hi.lo /
 // lo.hi, into the same accumulator, so the split operand keeps about 16 mantissa bits.
+//
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... of the (M tile, N tile, K split) grid. TMEM
+// holds two accumulators, so the epilogue of one tile overlaps the loads and MMAs of the next;
+// the shared-memory ring of K chunks runs across tiles without draining.
 template <int BN, int STAGES, int NA, int NB, class Epi>
 __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapA2,
@@ -129,26 +134,35 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   uint8_t* sB = smem + STAGES * NA * A_BYTES;  // [STAGES][NB][B_BYTES]
   uint64_t* full = (uint64_t*)(sB + STAGES * NB * B_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* accf = empty + STAGES;  // [2] accumulator b complete
+  uint64_t* acce = accf + 2;        // [2] accumulator b drained by the epilogue
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
   int* abort_flag = (int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int kc0 = blockIdx.z * sh.k_chunks_per_cta;
-  const int kc1 = min(kc0 + sh.k_chunks_per_cta, sh.K / BK);
-  const int nk = kc1 - kc0;
+  const int mt = (sh.M + BM - 1) / BM, nt = sh.N / BN;
+  const int nchunks = sh.K / BK, kpc = sh.k_chunks_per_cta;
+  const int zt = (nchunks + kpc - 1) / kpc;
+  const int tiles = mt * nt * zt;
+  auto tile_of = [&](int t, int& m0, int& n0, int& kc0, int& nk) {
+    const int z = t / (mt * nt), r = t - z * mt * nt;
+    const int ny = r / mt, mx = r - ny * mt;
+    m0 = mx * BM;
+    n0 = ny * BN;
+    kc0 = z * kpc;
+    nk = min(kc0 + kpc, nchunks) - kc0;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) { mbar_init(accf + b, 1); mbar_init(acce + b, 4); }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)BN));
+                 "r"((uint32_t)(2 * BN)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     fence_before_sync();
   }
@@ -156,76 +170,102 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  if (nk > 0) {
-    if (warp == 0 && lane == 0) {
-      // ---- producer ----
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % STAGES;
-        if (i >= STAGES && !mbar_wait(empty + s, ((i / STAGES) - 1) & 1)) { *abort_flag = 1; break; }
+  if (warp == 0 && lane == 0) {
+    // ---- producer: the K chunks of every tile, through the ring ----
+    int g = 0;
+    for (int t = blockIdx.x; t < tiles && !*(volatile int*)abort_flag; t += gridDim.x) {
+      int m0, n0, kc0, nk;
+      tile_of(t, m0, n0, kc0, nk);
+      for (int i = 0; i < nk; ++i, ++g) {
+        const int s = g % STAGES;
+        if (g >= STAGES && !mbar_wait(empty + s, ((g / STAGES) - 1) & 1)) { *(volatile int*)abort_flag = 1; break; }
         mbar_expect_tx(full + s, NA * A_BYTES + NB * B_BYTES);
         tma_load_2d(sA + (s * NA) * A_BYTES, &mapA, (kc0 + i) * BK, m0, full + s);
         if (NA == 2) tma_load_2d(sA + (s * NA + 1) * A_BYTES, &mapA2, (kc0 + i) * BK, m0, full + s);
         tma_load_2d(sB + (s * NB) * B_BYTES, &mapB, (kc0 + i) * BK, n0, full + s);
         if (NB == 2) tma_load_2d(sB + (s * NB + 1) * B_BYTES, &mapB2, (kc0 + i) * BK, n0, full + s);
       }
-    } else if (warp == 1 && lane == 0) {
-      // ---- MMA issuer ----
-      constexpr uint32_t idesc = idesc_bf16(BN);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: accumulator (local tile index & 1) ----
+    constexpr uint32_t idesc = idesc_bf16(BN);
+    int g = 0, lt = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+      int m0, n0, kc0, nk;
+      tile_of(t, m0, n0, kc0, nk);
+      if (nk <= 0) { --lt; continue; }  // no accumulator used (the epilogue writes zeros)
+      if (*(volatile int*)abort_flag) break;
+      const int b = lt & 1;
+      if (lt >= 2 && !mbar_wait(acce + b, ((lt >> 1) - 1) & 1)) { *(volatile int*)abort_flag = 1; break; }
+      fence_after_sync();
+      const uint32_t acc = tmem + (uint32_t)(b * BN);
       bool ok = true;
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % STAGES;
-        if (!mbar_wait(full + s, (i / STAGES) & 1)) { ok = false; break; }
+      for (int i = 0; i < nk; ++i, ++g) {
+        const int s = g % STAGES;
+        if (!mbar_wait(full + s, (g / STAGES) & 1)) { ok = false; break; }
         fence_after_sync();
         const uint32_t a0 = smem_u32(sA + (s * NA) * A_BYTES), b0 = smem_u32(sB + (s * NB) * B_BYTES);
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
-          mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
-          if (NB == 2) mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + B_BYTES + kk * 32), idesc, 1u);
-          if (NA == 2) mma_bf16(tmem, sw128_desc(a0 + A_BYTES + kk * 32), sw128_desc(b0 + kk * 32), idesc, 1u);
+          mma_bf16(acc, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          if (NB == 2) mma_bf16(acc, sw128_desc(a0 + kk * 32), sw128_desc(b0 + B_BYTES + kk * 32), idesc, 1u);
+          if (NA == 2) mma_bf16(acc, sw128_desc(a0 + A_BYTES + kk * 32), sw128_desc(b0 + kk * 32), idesc, 1u);
         }
         mma_commit(empty + s);
       }
-      if (!ok) *abort_flag = 1;
-      mma_commit(done);  // arrives once every issued MMA has completed
-    } else if (warp >= 2) {
-      // ---- epilogue ----
-      const bool ok = mbar_wait(done, 0);
-      fence_after_sync();
-      if (ok && !*(volatile int*)abort_flag) {
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
-        const int row = m0 + q * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
-          float v[16];
-          tmem_ld16(tbase + (uint32_t)c, v);
-          epi(row, n0 + c, v);
-        }
-        epi.finish(row);
-      } else if (lane == 0) {
-        raise_status(status, DLM_ETIMEOUT);
-      }
+      if (!ok) { *(volatile int*)abort_flag = 1; mma_commit(accf + b); break; }
+      mma_commit(accf + b);  // arrives once every MMA of this tile has completed
     }
   } else if (warp >= 2) {
-    const int q = warp & 3;
-    const int row = m0 + q * 32 + lane;
-    float v[16];
+    // ---- epilogue: drains accumulator (local tile index & 1) ----
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    int lt = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+      int m0, n0, kc0, nk;
+      tile_of(t, m0, n0, kc0, nk);
+      const int row = m0 + q * 32 + lane;
+      Epi e = epi;
+      if (nk <= 0) {  // empty K range: the tile's contribution is zero
+        float v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = 0.f;
-    for (int c = 0; c < BN; c += 16) epi(row, n0 + c, v);
-    epi.finish(row);
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        for (int c = 0; c < BN; c += 16) e(row, n0 + c, v);
+        e.finish(row);
+        --lt;  // no accumulator used
+        continue;
+      }
+      const int b = lt & 1;
+      const bool ok = mbar_wait(accf + b, (lt >> 1) & 1);
+      fence_after_sync();
+      if (!ok || *(volatile int*)abort_flag) {
+        if (lane == 0) raise_status(status, DLM_ETIMEOUT);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      const uint32_t tbase = tmem + (uint32_t)(b * BN) + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(tbase + (uint32_t)c, v);
+        e(row, n0 + c, v);
+      }
+      e.finish(row);
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acce + b)) : "memory");
+    }
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)));
   }
 }
 
 template <int BN, int STAGES, int NA, int NB>
 constexpr size_t gemm_smem_bytes() {
-  return 1024 + (size_t)STAGES * (NA * BM * BK * 2 + NB * BN * BK * 2) + (2 * STAGES + 1) * 8 + 16;
+  return 1024 + (size_t)STAGES * (NA * BM * BK * 2 + NB * BN * BK * 2) + (2 * STAGES + 4) * 8 + 16;
 }
 
 // host: 2-D bf16 tensor map over a row-major [rows][cols] matrix with leading dimension ld
