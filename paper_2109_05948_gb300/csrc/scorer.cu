@@ -287,6 +287,7 @@ __global__ void k_transpose(const bf16* X, int rows, int cols, bf16* Y) {
 // GEMM epilogues
 // ------------------------------------------------------------------------------------------------
 struct EpiPlain {  // out[row][col] = alpha * acc + bias[col]
+  __device__ void tile(int) {}
   float* out;
   int ld, M;
   float alpha;
@@ -304,9 +305,11 @@ struct EpiPartial {  // split-K slice z: part[z][row][col] = acc
   float* part;
   int ld, M;
   size_t zstride;
+  int z = 0;
+  __device__ void tile(int zz) { z = zz; }
   __device__ void operator()(int row, int col0, const float (&v)[16]) const {
     if (row >= M) return;
-    float* o = part + blockIdx.z * zstride + (size_t)row * ld + col0;
+    float* o = part + (size_t)z * zstride + (size_t)row * ld + col0;
 #pragma unroll
     for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
   }
@@ -314,6 +317,7 @@ struct EpiPartial {  // split-K slice z: part[z][row][col] = acc
 };
 
 struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optional head dot
+  __device__ void tile(int) {}
   bf16* H;    // may be null (scoring the last layer)
   bf16* Hlo;  // lo part (training) or null
   int M, kv;
@@ -369,6 +373,7 @@ struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optiona
 };
 
 struct EpiBwd {  // dZprev[row][col] = mask((acc + Gb[cand][col]) * LeakyReLU'(Hprev[row][col]))
+  __device__ void tile(int) {}
   bf16* dZ;
   int ld, M, kv;
   const float* Gb;
