@@ -43,10 +43,12 @@ struct dlm_scorer {
   float *theta = nullptr, *am = nullptr, *av = nullptr, *grad = nullptr;
   bf16* E16 = nullptr;
   bf16 *LamT[4] = {}, *Lam[4] = {}, *LamTlo[4] = {}, *Lamlo[4] = {};
+  bf16 *GamT[4] = {}, *GamTlo[4] = {};  // Gamma^T [kD][din], bf16 hi and lo
   // forward work buffers for up to `cap` candidates
   int cap = 0;
   bf16* H[4] = {};
   bf16* Mb[4] = {};
+  bf16* Mblo[4] = {};
   float* Mf[4] = {};
   float* G[4] = {};
   float* rowdot = nullptr;
@@ -57,6 +59,7 @@ struct dlm_scorer {
   bf16* HT[4] = {};
   bf16* HTlo[4] = {};
   bf16* Mbb[4] = {};
+  bf16* Mbblo[4] = {};
   float* Mfb[4] = {};
   float* Gbf[4] = {};
   bf16* dZ[4] = {};
@@ -89,6 +92,7 @@ struct ConvArgs {
   size_t oE, olam[4], ogam[4];
   bf16* E16;
   bf16 *LamT[4], *Lam[4], *LamTlo[4], *Lamlo[4];
+  bf16 *GamT[4], *GamTlo[4];
 };
 
 __global__ void k_convert(ConvArgs a) {
@@ -111,6 +115,15 @@ __global__ void k_convert(ConvArgs a) {
       return;
     }
     r -= sz;
+    if (r < sz) {
+      const int f = (int)(r / kD), o = (int)(r % kD);
+      const float gam = a.theta[a.ogam[l] + r];
+      const bf16 hi = __float2bfloat16_rn(gam);
+      a.GamT[l][(size_t)o * din + f] = hi;
+      a.GamTlo[l][(size_t)o * din + f] = __float2bfloat16_rn(gam - __bfloat162float(hi));
+      return;
+    }
+    r -= sz;
   }
 }
 
@@ -120,7 +133,8 @@ __global__ void k_convert(ConvArgs a) {
 // w, w+8, ... with lane = feature pair (fixed summation order; E is read through L1/L2).
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols, int c, const float* E, const float* b0,
-                                              bf16* H0, bf16* H0lo, float* Mf0, bf16* Mb0, int32_t* status) {
+                                              bf16* H0, bf16* H0lo, float* Mf0, bf16* Mb0, bf16* Mb0lo,
+                                              int32_t* status) {
   extern __shared__ __align__(16) uint8_t sm[];
   uint8_t* col = sm;                                        // [n]
   uint16_t* mem = (uint16_t*)(sm + ((n + 15) & ~15));       // [n]
@@ -203,52 +217,17 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
       for (int w = 0; w < 8; ++w) s += part[w * 64 + tid];
       s /= (float)k;
       Mf0[(size_t)cand * kD0 + tid] = s;
-      Mb0[(size_t)cand * kD0 + tid] = __float2bfloat16_rn(s);
+      const bf16 hi = __float2bfloat16_rn(s);
+      Mb0[(size_t)cand * kD0 + tid] = hi;
+      Mb0lo[(size_t)cand * kD0 + tid] = __float2bfloat16_rn(s - __bfloat162float(hi));
     }
     __syncthreads();
   }
 }
 
-// per-candidate term G[cand][o] = beta[o] + sum_f M[cand][f] Gamma[f][o] in FP32; a block of
-// 256 threads (thread = o) handles TILE candidates, reading each Gamma row once for all of them.
-// TILE shrinks for small batches so that the grid still covers the SMs.
-template <int TILE>
-__global__ void __launch_bounds__(256) k_gterm(int c, int din, const float* M, const float* theta, size_t ogam,
-                                               size_t ob, float* G) {
-  __shared__ float ms[TILE][256];
-  const int c0 = blockIdx.x * TILE, o = threadIdx.x;
-  for (int i = threadIdx.x; i < TILE * din; i += 256) {
-    const int cc = i / din, f = i % din;
-    ms[cc][f] = (c0 + cc < c) ? M[(size_t)(c0 + cc) * din + f] : 0.f;
-  }
-  __syncthreads();
-  float acc[TILE];
-#pragma unroll
-  for (int q = 0; q < TILE; ++q) acc[q] = 0.f;
-  const float* gam = theta + ogam;
-#pragma unroll 4
-  for (int f = 0; f < din; ++f) {
-    const float g = gam[(size_t)f * kD + o];
-#pragma unroll
-    for (int q = 0; q < TILE; ++q) acc[q] += ms[q][f] * g;
-  }
-  const float b = theta[ob + o];
-#pragma unroll
-  for (int q = 0; q < TILE; ++q)
-    if (c0 + q < c) G[(size_t)(c0 + q) * kD + o] = acc[q] + b;
-}
-
-static dlm_status launch_gterm(dlm_ctx* ctx, int c, int din, const float* M, const float* theta, size_t ogam, size_t ob,
-                               float* G) {
-  const int want = 2 * ctx->num_sms;
-  if (c >= 16 * want) k_gterm<16><<<(c + 15) / 16, 256, 0, ctx->stream>>>(c, din, M, theta, ogam, ob, G);
-  else if (c >= 4 * want) k_gterm<4><<<(c + 3) / 4, 256, 0, ctx->stream>>>(c, din, M, theta, ogam, ob, G);
-  else k_gterm<1><<<c, 256, 0, ctx->stream>>>(c, din, M, theta, ogam, ob, G);
-  return launch_check(ctx, "k_gterm");
-}
-
 // per-candidate mean (or sum) over the k valid rows of a bf16 [c*R][w] matrix; block = w threads
-__global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf, bf16* outb) {
+__global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf, bf16* outb,
+                                 bf16* outblo) {
   const int cand = blockIdx.x, col = threadIdx.x;
   const bf16* x = X + (size_t)cand * kR * w + col;
   const bf16* xl = Xlo ? Xlo + (size_t)cand * kR * w + col : nullptr;
@@ -257,7 +236,11 @@ __global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, f
   for (int r = 0; r < k; ++r) s += __bfloat162float(x[(size_t)r * w]) + (xl ? __bfloat162float(xl[(size_t)r * w]) : 0.f);
   s *= scale;
   outf[(size_t)cand * w + col] = s;
-  if (outb) outb[(size_t)cand * w + col] = __float2bfloat16_rn(s);
+  if (outb) {
+    const bf16 hi = __float2bfloat16_rn(s);
+    outb[(size_t)cand * w + col] = hi;
+    outblo[(size_t)cand * w + col] = __float2bfloat16_rn(s - __bfloat162float(hi));
+  }
 }
 
 __global__ void k_head_out(int c, int k, const float* rowdot, const float* theta, size_t obh, float* out) {
@@ -297,6 +280,23 @@ struct EpiPlain {  // out[row][col] = alpha * acc + bias[col]
     float* o = out + (size_t)row * ld + col0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) o[i] = alpha * v[i] + (bias ? bias[col0 + i] : 0.f);
+  }
+  __device__ void finish(int) const {}
+};
+
+struct EpiBias {  // G[row][col] = acc + beta[col] (the per-candidate Gamma term of a layer)
+  __device__ void tile(int) {}
+  float* G;
+  int M;
+  const float* beta;
+  __device__ void operator()(int row, int col0, const float (&v)[16]) const {
+    if (row >= M) return;
+    float* o = G + (size_t)row * kD + col0;
+#pragma unroll
+    for (int i = 0; i < 16; i += 4)
+      *reinterpret_cast<float4*>(o + i) =
+          make_float4(v[i] + beta[col0 + i], v[i + 1] + beta[col0 + i + 1], v[i + 2] + beta[col0 + i + 2],
+                      v[i + 3] + beta[col0 + i + 3]);
   }
   __device__ void finish(int) const {}
 };
@@ -714,7 +714,9 @@ static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
     a.Lam[l] = s->Lam[l];
     a.LamTlo[l] = s->LamTlo[l];
     a.Lamlo[l] = s->Lamlo[l];
-    tot += (int64_t)din_of(l) * kD;
+    a.GamT[l] = s->GamT[l];
+    a.GamTlo[l] = s->GamTlo[l];
+    tot += 2 * (int64_t)din_of(l) * kD;
   }
   k_convert<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(a);
   return launch_check(ctx, "k_convert");
@@ -724,23 +726,26 @@ static size_t pool_smem(int n) { return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + 
 
 // forward over c candidates with the given buffers; train = keep every activation (and H3)
 static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int c, float* out, bf16** H, bf16** Hlo,
-                          bf16** Mb, float** Mf, float** G, float* rowdot, bool train) {
+                          bf16** Mb, bf16** Mblo, float** Mf, float** G, float* rowdot, bool train) {
   const int rows = c * kR;
   const size_t psm = pool_smem(s->n);  // < 10 KB for n <= 2048
   const int pgrid = std::min(c, ctx->num_sms * 4);
   k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, cols, c, s->theta + s->oE, s->theta + s->ob0, H[0],
-                                           Hlo ? Hlo[0] : nullptr, Mf[0], Mb[0], ctx->d_status);
+                                           Hlo ? Hlo[0] : nullptr, Mf[0], Mb[0], Mblo[0], ctx->d_status);
   DLM_TRY(launch_check(ctx, "k_pool"));
   for (int l = 1; l <= kNL; ++l) {
     const int din = din_of(l);
-    // per-candidate term rho(H_{l-1}) Gamma_l + beta_l (FP32, CUDA cores)
-    DLM_TRY(launch_gterm(ctx, c, din, Mf[l - 1], s->theta, s->ogam[l], s->ob[l], G[l]));
+    // per-candidate term rho(H_{l-1}) Gamma_l + beta_l on the tensor cores, both operands split
+    // into bf16 hi + lo (three MMA passes, about 16 mantissa bits each)
+    DLM_TRY(gemm<256>(ctx, Mb[l - 1], Mblo[l - 1], c, din, din, s->GamT[l], s->GamTlo[l], kD, din, 0,
+                      EpiBias{G[l], c, s->theta + s->ob[l]}));
     const bool last = l == kNL;
     EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, G[l],
                last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f};
     DLM_TRY(gemm<256>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din, 0, e));
     if (!last || train) {
-      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, 1.f / s->k, Mf[l], Mb[l]);
+      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, 1.f / s->k, Mf[l], Mb[l],
+                                                  Mblo[l]);
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
@@ -750,7 +755,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
 
 // forward + backward of one batch; gradient into s->grad (overwritten), predictions into outb
 static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const float* y, int B) {
-  DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mfb, s->Gbf, s->rowdotb, true));
+  DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mbblo, s->Mfb, s->Gbf, s->rowdotb, true));
   const int rows = B * kR;
   k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, s->dout, s->lossd);
   DLM_TRY(launch_check(ctx, "k_loss"));
@@ -760,7 +765,7 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
   for (int l = kNL; l >= 1; --l) {
     const int din = din_of(l);
     // column sums of dZ_l per candidate (valid rows are the only nonzero ones)
-    k_segment_reduce<<<B, kD, 0, ctx->stream>>>(s->dZ[l], nullptr, kD, s->k, 1.f, s->S[l], nullptr);
+    k_segment_reduce<<<B, kD, 0, ctx->stream>>>(s->dZ[l], nullptr, kD, s->k, 1.f, s->S[l], nullptr, nullptr);
     DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     // transposes for the weight-gradient GEMM
     dim3 tb(32, 8);
@@ -784,7 +789,7 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
     if (din == kD) DLM_TRY(gemm<256>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e));
     else DLM_TRY(gemm<64>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e));
   }
-  k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, 1.f, s->S[0], nullptr);
+  k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, 1.f, s->S[0], nullptr, nullptr);
   k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, cols, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
   return launch_check(ctx, "k_demb");
 }
@@ -800,6 +805,7 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
     DLM_TRY(dalloc(ctx, &s->HT[l], (size_t)rows * w));
     DLM_TRY(dalloc(ctx, &s->HTlo[l], (size_t)rows * w));
     DLM_TRY(dalloc(ctx, &s->Mbb[l], (size_t)cpad * w));
+    DLM_TRY(dalloc(ctx, &s->Mbblo[l], (size_t)cpad * w));
     DLM_TRY(dalloc(ctx, &s->Mfb[l], (size_t)cb * w));
     DLM_TRY(dalloc(ctx, &s->Gbf[l], (size_t)cb * kD));
     DLM_TRY(dalloc(ctx, &s->dZ[l], (size_t)rows * w));
@@ -825,6 +831,7 @@ static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
     const int w = l == 0 ? kD0 : kD;
     if (l < kNL) DLM_TRY(dalloc(ctx, &s->H[l], (size_t)rows * w));
     DLM_TRY(dalloc(ctx, &s->Mb[l], (size_t)cap * w));
+    DLM_TRY(dalloc(ctx, &s->Mblo[l], (size_t)cap * w));
     DLM_TRY(dalloc(ctx, &s->Mf[l], (size_t)cap * w));
     DLM_TRY(dalloc(ctx, &s->G[l], (size_t)cap * kD));
   }
@@ -851,6 +858,7 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
   cudaFree(s->theta); cudaFree(s->am); cudaFree(s->av); cudaFree(s->grad); cudaFree(s->E16);
   for (int l = 0; l <= kNL; ++l) {
     cudaFree(s->LamT[l]); cudaFree(s->Lam[l]); cudaFree(s->LamTlo[l]); cudaFree(s->Lamlo[l]);
+    cudaFree(s->GamT[l]); cudaFree(s->GamTlo[l]); cudaFree(s->Mblo[l]); cudaFree(s->Mbblo[l]);
     cudaFree(s->H[l]); cudaFree(s->Mb[l]); cudaFree(s->Mf[l]); cudaFree(s->G[l]);
     cudaFree(s->Hb[l]); cudaFree(s->Hblo[l]); cudaFree(s->HT[l]); cudaFree(s->HTlo[l]); cudaFree(s->Mbb[l]); cudaFree(s->Mfb[l]); cudaFree(s->Gbf[l]);
     cudaFree(s->dZ[l]); cudaFree(s->dZT[l]); cudaFree(s->S[l]);
@@ -885,6 +893,7 @@ extern "C" dlm_status dlm_scorer_create(dlm_ctx* ctx, int32_t n, int32_t k, uint
   for (int l = 1; l <= kNL; ++l) {
     A(&s->LamT[l], (size_t)din_of(l) * kD); A(&s->Lam[l], (size_t)din_of(l) * kD);
     A(&s->LamTlo[l], (size_t)din_of(l) * kD); A(&s->Lamlo[l], (size_t)din_of(l) * kD);
+    A(&s->GamT[l], (size_t)din_of(l) * kD); A(&s->GamTlo[l], (size_t)din_of(l) * kD);
   }
   if (st != DLM_OK) { dlm_scorer_destroy(s); return st; }
   // uniform +-1/sqrt(fan_in) per parameter block (fan_in of E and b0: n)
@@ -947,7 +956,8 @@ extern "C" dlm_status dlm_score_offspring(dlm_ctx* ctx, dlm_scorer* s, const int
   DLM_TRY(ensure_fwd_buffers(ctx, s));
   for (int c0 = 0; c0 < c; c0 += s->cap) {
     const int cc = std::min(s->cap, c - c0);
-    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, out + c0, s->H, nullptr, s->Mb, s->Mf, s->G, s->rowdot, false));
+    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, out + c0, s->H, nullptr, s->Mb, s->Mblo, s->Mf, s->G, s->rowdot,
+                    false));
   }
   return DLM_OK;
 }
