@@ -225,6 +225,22 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
   }
 }
 
+// per-candidate term G[cand][o] = beta[o] + sum_f M[cand][f] Gamma[f][o] in FP32 on CUDA cores,
+// for small batches (a training step's 100 candidates), where a tensor-core GEMM of one tile is
+// latency bound; a block of 256 threads (thread = o) handles one candidate.
+__global__ void __launch_bounds__(256) k_gterm(int c, int din, const float* M, const float* theta, size_t ogam,
+                                               size_t ob, float* G) {
+  __shared__ float ms[256];
+  const int cand = blockIdx.x, o = threadIdx.x;
+  if (o < din) ms[o] = M[(size_t)cand * din + o];
+  __syncthreads();
+  const float* gam = theta + ogam;
+  float acc = 0.f;
+#pragma unroll 4
+  for (int f = 0; f < din; ++f) acc += ms[f] * gam[(size_t)f * kD + o];
+  G[(size_t)cand * kD + o] = acc + theta[ob + o];
+}
+
 // per-candidate mean (or sum) over the k valid rows of a bf16 [c*R][w] matrix; block = w threads
 __global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf, bf16* outb,
                                  bf16* outblo) {
@@ -735,10 +751,16 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
   DLM_TRY(launch_check(ctx, "k_pool"));
   for (int l = 1; l <= kNL; ++l) {
     const int din = din_of(l);
-    // per-candidate term rho(H_{l-1}) Gamma_l + beta_l on the tensor cores, both operands split
-    // into bf16 hi + lo (three MMA passes, about 16 mantissa bits each)
-    DLM_TRY(gemm<256>(ctx, Mb[l - 1], Mblo[l - 1], c, din, din, s->GamT[l], s->GamTlo[l], kD, din, 0,
-                      EpiBias{G[l], c, s->theta + s->ob[l]}));
+    // per-candidate term rho(H_{l-1}) Gamma_l + beta_l: on the tensor cores for a scoring chunk,
+    // both operands split into bf16 hi + lo (three MMA passes, about 16 mantissa bits each); in
+    // FP32 on CUDA cores for a training batch
+    if (c >= 1024) {
+      DLM_TRY(gemm<256>(ctx, Mb[l - 1], Mblo[l - 1], c, din, din, s->GamT[l], s->GamTlo[l], kD, din, 0,
+                        EpiBias{G[l], c, s->theta + s->ob[l]}));
+    } else {
+      k_gterm<<<c, 256, 0, ctx->stream>>>(c, din, Mf[l - 1], s->theta, s->ogam[l], s->ob[l], G[l]);
+      DLM_TRY(launch_check(ctx, "k_gterm"));
+    }
     const bool last = l == kNL;
     EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, G[l],
                last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f};

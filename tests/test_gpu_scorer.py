@@ -59,7 +59,8 @@ def _gpu_scorer(ctx, n, k, th):
     return s
 
 
-@pytest.mark.parametrize("n,k,c,scale", [(200, 48, 37, 3.0), (97, 17, 130, 2.0), (64, 64, 9, 4.0), (30, 2, 5, 3.0)])
+@pytest.mark.parametrize("n,k,c,scale", [(200, 48, 37, 3.0), (97, 17, 130, 2.0), (64, 64, 9, 4.0), (30, 2, 5, 3.0),
+                                         (60, 9, 2048, 3.0)])  # the last: Gamma terms on the tensor cores
 def test_scorer_forward_matches_oracle(ctx, n, k, c, scale):
     dims = oracle.ScorerDims(n)
     th = _params(dims, seed=n, scale=scale)
