@@ -241,32 +241,54 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
       const long long thr64 = best_g - g;
       const int thr = thr64 < (long long)INT_MIN + 1 ? INT_MIN + 1 : (int)thr64;
       int tmin = INT_MAX;
-      for (int v = tid; v < n; v += kWThreads) {
-        const int o = colS[v], wv = wS[v];
-        const uint32_t io = info[o];
-        const int m1o = io & 0xFF, m2o = (io >> 8) & 0xFF, c1o = io >> 16;
-        const int rem = (wv == m1o && c1o == 1) ? m2o - m1o : 0;
-        const int g0 = o < cs ? gS[(size_t)o * npad + v] : gG[(size_t)(o - cs) * npad + v];
-        const bool frozen = fz[v] > itrel;
-        const int base = rem - (int)phi * g0;
-        int km = INT_MAX, kc = 0;
+      // two vertices per pass (v and v + kWThreads): two independent min/count chains share the
+      // class-maximum loads
+      for (int v = tid; v < n; v += 2 * kWThreads) {
+        const int vb = v + kWThreads < n ? v + kWThreads : v;  // second vertex (a duplicate when none)
+        const int oa = colS[v], wa = wS[v], ob = colS[vb], wb = wS[vb];
+        const uint32_t ia = info[oa], ib = info[ob];
+        const int rema = (wa == (int)(ia & 0xFF) && (ia >> 16) == 1) ? (int)((ia >> 8) & 0xFF) - (int)(ia & 0xFF) : 0;
+        const int remb = (wb == (int)(ib & 0xFF) && (ib >> 16) == 1) ? (int)((ib >> 8) & 0xFF) - (int)(ib & 0xFF) : 0;
+        const int g0a = oa < cs ? gS[(size_t)oa * npad + v] : gG[(size_t)(oa - cs) * npad + v];
+        const int g0b = ob < cs ? gS[(size_t)ob * npad + vb] : gG[(size_t)(ob - cs) * npad + vb];
+        const bool fra = fz[v] > itrel, frb = fz[vb] > itrel;
+        const int basea = rema - (int)phi * g0a, baseb = remb - (int)phi * g0b;
+        int kma = INT_MAX, kca = 0, kmb = INT_MAX, kcb = 0;
 #pragma unroll 4
-        for (int c = 0; c < cs; ++c)
-          wvcp_scan_key(c, o, wv, max1s[c], base, phi, gS[(size_t)c * npad + v], frozen, thr, km, kc);
-        // the slab colours come from L2: 16 independent loads in flight before they are used
+        for (int c = 0; c < cs; ++c) {
+          const int m1 = max1s[c];
+          wvcp_scan_key(c, oa, wa, m1, basea, phi, gS[(size_t)c * npad + v], fra, thr, kma, kca);
+          wvcp_scan_key(c, ob, wb, m1, baseb, phi, gS[(size_t)c * npad + vb], frb, thr, kmb, kcb);
+        }
+        // the slab colours come from L2: 16 independent loads per vertex in flight before use
         int c = cs;
         for (; c + 16 <= k; c += 16) {
-          int gq[16];
+          int qa[16], qb[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) gq[q] = gG[(size_t)(c + q - cs) * npad + v];
+          for (int q = 0; q < 16; ++q) {
+            qa[q] = gG[(size_t)(c + q - cs) * npad + v];
+            qb[q] = gG[(size_t)(c + q - cs) * npad + vb];
+          }
 #pragma unroll
-          for (int q = 0; q < 16; ++q) wvcp_scan_key(c + q, o, wv, max1s[c + q], base, phi, gq[q], frozen, thr, km, kc);
+          for (int q = 0; q < 16; ++q) {
+            const int m1 = max1s[c + q];
+            wvcp_scan_key(c + q, oa, wa, m1, basea, phi, qa[q], fra, thr, kma, kca);
+            wvcp_scan_key(c + q, ob, wb, m1, baseb, phi, qb[q], frb, thr, kmb, kcb);
+          }
         }
-        for (; c < k; ++c)
-          wvcp_scan_key(c, o, wv, max1s[c], base, phi, gG[(size_t)(c - cs) * npad + v], frozen, thr, km, kc);
-        rmin[v] = km;
-        rcnt[v] = (uint16_t)(km == INT_MAX ? 0 : kc);
-        tmin = min(tmin, km);
+        for (; c < k; ++c) {
+          const int m1 = max1s[c];
+          wvcp_scan_key(c, oa, wa, m1, basea, phi, gG[(size_t)(c - cs) * npad + v], fra, thr, kma, kca);
+          wvcp_scan_key(c, ob, wb, m1, baseb, phi, gG[(size_t)(c - cs) * npad + vb], frb, thr, kmb, kcb);
+        }
+        rmin[v] = kma;
+        rcnt[v] = (uint16_t)(kma == INT_MAX ? 0 : kca);
+        tmin = min(tmin, kma);
+        if (vb != v) {
+          rmin[vb] = kmb;
+          rcnt[vb] = (uint16_t)(kmb == INT_MAX ? 0 : kcb);
+          tmin = min(tmin, kmb);
+        }
       }
       {
         const int wm = __reduce_min_sync(0xFFFFFFFFu, tmin);
