@@ -77,6 +77,19 @@ struct dlm_scorer {
   float* by = nullptr;
   int32_t* perm = nullptr;
   int capp = 0;
+  // training step replayed from a CUDA graph: the batch offset within the epoch's permutation and
+  // the Adam step counter live on the device ([0] offset, [1] t), with Adam's bias corrections
+  int32_t* d_step = nullptr;
+  float* d_bc = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    int B = 0, b = 0;
+    float lr = 0.f;
+    const int16_t* cols = nullptr;
+  } sg[2];
+  int sg_next = 0;
+  bool stepped = false;  // one eager step has run (first-use attributes are set outside capture)
 };
 
 namespace dlm {
@@ -527,9 +540,10 @@ __global__ void k_demb(int n, int B, const int16_t* cols, const bf16* dZ0, const
   }
 }
 
-__global__ void k_adam(int64_t np, float* th, float* m, float* v, const float* g, float lr, float bc1, float sbc2) {
+__global__ void k_adam(int64_t np, float* th, float* m, float* v, const float* g, float lr, const float* bc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
+  const float bc1 = bc[0], sbc2 = bc[1];
   const float gi = g[i];
   const float mi = 0.9f * m[i] + 0.1f * gi;
   const float vi = 0.999f * v[i] + 0.001f * gi * gi;
@@ -537,6 +551,19 @@ __global__ void k_adam(int64_t np, float* th, float* m, float* v, const float* g
   v[i] = vi;
   const float denom = sqrtf(vi) / sbc2 + 1e-8f;
   th[i] -= (lr / bc1) * mi / denom;
+}
+
+// Adam step t + 1 (t = step[1]): bias corrections 1 - 0.9^t and sqrt(1 - 0.999^t) in double
+__global__ void k_step_prep(const int32_t* step, float* bc) {
+  const double t = (double)(step[1] + 1);
+  bc[0] = (float)(1.0 - pow(0.9, t));
+  bc[1] = (float)sqrt(1.0 - pow(0.999, t));
+}
+
+// after a step: the next batch starts b samples later, Adam's counter advances
+__global__ void k_step_end(int32_t* step, int b) {
+  step[0] += b;
+  step[1] += 1;
 }
 
 __global__ void k_init_params(int64_t np, uint64_t seed, float* th, const float* bound_of, const int64_t* seg_end, int nseg) {
@@ -608,10 +635,10 @@ __global__ void k_epoch_perm(int p, uint64_t seed, uint32_t epoch, uint32_t gen,
   for (int i = threadIdx.x; i < p; i += blockDim.x) perm[i] = (int32_t)(keys[i] & 0xFFFFFFFFu);
 }
 
-__global__ void k_gather_batch(int n, int B, const int32_t* perm, int s0, const int16_t* cols, const float* y,
-                               int16_t* bcols, float* by) {
+__global__ void k_gather_batch(int n, int B, const int32_t* perm, const int32_t* step, const int16_t* cols,
+                               const float* y, int16_t* bcols, float* by) {
   const int b = blockIdx.x;
-  const int i = perm[s0 + b];
+  const int i = perm[step[0] + b];
   for (int v = threadIdx.x; v < n; v += blockDim.x) bcols[(size_t)b * n + v] = cols[(size_t)i * n + v];
   if (threadIdx.x == 0) by[b] = y[i];
 }
@@ -862,13 +889,54 @@ static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
   return DLM_OK;
 }
 
-static dlm_status adam_step(dlm_ctx* ctx, dlm_scorer* s, float lr) {
-  s->t += 1;
-  const double bc1 = 1.0 - std::pow(0.9, (double)s->t), bc2 = 1.0 - std::pow(0.999, (double)s->t);
-  k_adam<<<(unsigned)((s->np + 255) / 256), 256, 0, ctx->stream>>>(s->np, s->theta, s->am, s->av, s->grad, lr, (float)bc1,
-                                                                   (float)std::sqrt(bc2));
+// one Adam step of batch size B (batch offset and step counter on the device)
+static dlm_status train_step(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int B, int b, float lr) {
+  k_gather_batch<<<B, 128, 0, ctx->stream>>>(s->n, B, s->perm, s->d_step, cols, s->y, s->bcols, s->by);
+  DLM_TRY(launch_check(ctx, "k_gather_batch"));
+  DLM_TRY(loss_grad(ctx, s, s->bcols, s->by, B));
+  k_step_prep<<<1, 1, 0, ctx->stream>>>(s->d_step, s->d_bc);
+  DLM_TRY(launch_check(ctx, "k_step_prep"));
+  k_adam<<<(unsigned)((s->np + 255) / 256), 256, 0, ctx->stream>>>(s->np, s->theta, s->am, s->av, s->grad, lr, s->d_bc);
   DLM_TRY(launch_check(ctx, "k_adam"));
-  return convert_params(ctx, s);
+  DLM_TRY(convert_params(ctx, s));
+  k_step_end<<<1, 1, 0, ctx->stream>>>(s->d_step, b);
+  return launch_check(ctx, "k_step_end");
+}
+
+// the training step of batch size B as an instantiated CUDA graph (captured on a private stream,
+// replayed on the context's stream); cached for the last two (B, b, lr, cols) keys
+static dlm_status step_graph(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int B, int b, float lr,
+                             cudaGraphExec_t* exec) {
+  for (auto& g : s->sg)
+    if (g.exec && g.B == B && g.b == b && g.lr == lr && g.cols == cols) { *exec = g.exec; return DLM_OK; }
+  if (!s->cap_stream) DLM_CUDA(ctx, cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = ctx->stream;
+  const bool prof = ctx->gemm_prof;
+  ctx->gemm_prof = false;  // no event records inside the graph
+  ctx->stream = s->cap_stream;
+  cudaGraph_t graph = nullptr;
+  dlm_status st = cuda_check(ctx, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+  if (st == DLM_OK) {
+    st = train_step(ctx, s, cols, B, b, lr);
+    const cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
+    if (st == DLM_OK) st = cuda_check(ctx, e, "end capture");
+  }
+  ctx->stream = user;
+  ctx->gemm_prof = prof;
+  cudaGraphExec_t ge = nullptr;
+  if (st == DLM_OK) st = cuda_check(ctx, cudaGraphInstantiate(&ge, graph, 0), "graph instantiate");
+  if (graph) cudaGraphDestroy(graph);
+  if (st != DLM_OK) return st;
+  auto& slot = s->sg[s->sg_next];
+  s->sg_next ^= 1;
+  if (slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot.exec = ge;
+  slot.B = B;
+  slot.b = b;
+  slot.lr = lr;
+  slot.cols = cols;
+  *exec = ge;
+  return DLM_OK;
 }
 
 }  // namespace dlm
@@ -877,6 +945,11 @@ using namespace dlm;
 
 extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
   if (!s) return;
+  for (auto& g : s->sg)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  cudaFree(s->d_step);
+  cudaFree(s->d_bc);
   cudaFree(s->theta); cudaFree(s->am); cudaFree(s->av); cudaFree(s->grad); cudaFree(s->E16);
   for (int l = 0; l <= kNL; ++l) {
     cudaFree(s->LamT[l]); cudaFree(s->Lam[l]); cudaFree(s->LamTlo[l]); cudaFree(s->Lamlo[l]);
@@ -1020,15 +1093,29 @@ extern "C" dlm_status dlm_scorer_train(dlm_ctx* ctx, dlm_scorer* s, const int16_
     DLM_CUDA(ctx, cudaFuncSetAttribute(k_epoch_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
     attr = true;
   }
+  if (!s->d_step) {
+    DLM_TRY(dalloc(ctx, &s->d_step, 2));
+    DLM_TRY(dalloc(ctx, &s->d_bc, 2));
+  }
+  // the device counters start from the host mirror of Adam's step counter
+  int32_t init[2] = {0, (int32_t)s->t};
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->d_step, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // init lives on the host stack
   for (int ep = 0; ep < epochs; ++ep) {
     k_epoch_perm<<<1, 1024, (size_t)mp * 8, ctx->stream>>>(p, seed, (uint32_t)ep, generation, s->perm);
     DLM_TRY(launch_check(ctx, "k_epoch_perm"));
+    DLM_CUDA(ctx, cudaMemsetAsync(s->d_step, 0, sizeof(int32_t), ctx->stream));  // batch offset 0
     for (int s0 = 0; s0 < p; s0 += b) {
       const int B = std::min(b, p - s0);
-      k_gather_batch<<<B, 128, 0, ctx->stream>>>(s->n, B, s->perm, s0, cols, s->y, s->bcols, s->by);
-      DLM_TRY(launch_check(ctx, "k_gather_batch"));
-      DLM_TRY(loss_grad(ctx, s, s->bcols, s->by, B));
-      DLM_TRY(adam_step(ctx, s, lr));
+      if (!s->stepped) {  // the first step ever runs eagerly (it sets the kernels' attributes)
+        DLM_TRY(train_step(ctx, s, cols, B, b, lr));
+        s->stepped = true;
+      } else {
+        cudaGraphExec_t ge = nullptr;
+        DLM_TRY(step_graph(ctx, s, cols, B, b, lr, &ge));
+        DLM_CUDA(ctx, cudaGraphLaunch(ge, ctx->stream));
+      }
+      s->t += 1;
     }
   }
   return DLM_OK;
