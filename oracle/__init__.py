@@ -78,6 +78,10 @@ def _declare(L):
         "oracle_wvcp_greedy": (_i32, [_i32, _P, _P, _u64, _u32, _P]),
         "oracle_wvcp_tabu": (_i32, [_i32, _P, _P, _i32, _P, _i64, _i32, _i32, _i32, _i64, _u64, _u32,
                                     _u32, _P, _P, _P, _P, _P, _i32]),
+        "oracle_wvcp_tabu_scaled": (_i32, [_i32, _P, _P, _i32, _P, _i64, _i32, _i32, _i32, _i64, _i64, _u64,
+                                           _u32, _u32, _P, _P, _P, _P, _P, _i32]),
+        "oracle_wvcp_iterated": (_i32, [_i32, _P, _P, _i32, _P, _i64, _i32, _i32, _i32, _i32, _i64, _i64, _i64,
+                                        _u64, _u32, _u32, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):
@@ -307,3 +311,39 @@ class MemeticState:
             raise RuntimeError(f"oracle_memetic_generation failed with {rc}")
         self.gen += 1
         return fprime, pick
+
+
+def wvcp_tabu(adj, w, k, col, iters, phi, seed, ind, gen=0, fscale=1, L_max=9, alpha=(2, 10), trace=False,
+              check=False):
+    """Feasible/infeasible tabu search on g = fscale f + phi c; dict(best_col, best_g, f, c, moves, trace)."""
+    adj = _c(adj, np.uint8)
+    w = _c(w, np.int32)
+    col = _c(col, np.int16)
+    n = adj.shape[0]
+    best = np.zeros(n, np.int16)
+    bg, fc, mv = np.zeros(1, np.int64), np.zeros(2, np.int64), np.zeros(1, np.int64)
+    tr = np.full((iters, 4), -7, np.int32) if trace else None
+    rc = lib().oracle_wvcp_tabu_scaled(n, _ptr(adj), _ptr(w), k, _ptr(col), iters, L_max, alpha[0], alpha[1], fscale,
+                                       phi, seed, ind, gen, _ptr(best), _ptr(bg), _ptr(fc), _ptr(mv),
+                                       _ptr(tr) if trace else None, 1 if check else 0)
+    if rc != 0:
+        raise RuntimeError(f"oracle_wvcp_tabu_scaled failed ({rc})")
+    return dict(best_col=best, best_g=int(bg[0]), f=int(fc[0]), c=int(fc[1]), moves=int(mv[0]), trace=tr)
+
+
+def wvcp_iterated(adj, w, k, col, iters, max_ls, fscale, phi0, phi_last, seed, ind, gen=0, L_max=9, alpha=(2, 10)):
+    """Iterated feasible/infeasible tabu search (Algorithm 2) of one individual:
+    dict(best_col, best_f (-1: never legal), phi (per search), fc (per search))."""
+    adj = _c(adj, np.uint8)
+    w = _c(w, np.int32)
+    col = _c(col, np.int16)
+    n = adj.shape[0]
+    best = np.zeros(n, np.int16)
+    bf = np.zeros(1, np.int64)
+    phis = np.zeros(max_ls, np.int64)
+    fcs = np.zeros((max_ls, 2), np.int64)
+    rc = lib().oracle_wvcp_iterated(n, _ptr(adj), _ptr(w), k, _ptr(col), iters, max_ls, L_max, alpha[0], alpha[1],
+                                    fscale, phi0, phi_last, seed, ind, gen, _ptr(best), _ptr(bf), _ptr(phis), _ptr(fcs))
+    if rc != 0:
+        raise RuntimeError(f"oracle_wvcp_iterated failed ({rc})")
+    return dict(best_col=best, best_f=int(bf[0]), phi=phis, fc=fcs)

@@ -727,10 +727,12 @@ int32_t oracle_wvcp_greedy(int32_t n, const uint8_t* adj, const int32_t* w, uint
 // frozen vertex is admissible only when it leads below the best g of the run (aspiration).
 // Ties: the j-th admissible minimum in (v asc, c asc) order, j uniform from the iteration's
 // Philox block. The run keeps the best g visited; best_fc receives (f, c) of that colouring.
-int32_t oracle_wvcp_tabu(int32_t n, const uint8_t* adj, const int32_t* w, int32_t k, const int16_t* col_in,
-                         int64_t iters, int32_t L_max, int32_t alpha_num, int32_t alpha_den, int64_t phi,
-                         uint64_t seed, uint32_t ind, uint32_t gen, int16_t* best_col, int64_t* best_g_out,
-                         int64_t* best_fc, int64_t* moves_out, int32_t* trace, int32_t check) {
+// Generalised objective g = fscale f + phi c (fscale = 1 is Eq. AFISA_score with an integer
+// phi; fscale > 1 holds phi in fixed point with resolution 1 / fscale).
+int32_t oracle_wvcp_tabu_scaled(int32_t n, const uint8_t* adj, const int32_t* w, int32_t k, const int16_t* col_in,
+                                int64_t iters, int32_t L_max, int32_t alpha_num, int32_t alpha_den, int64_t fscale,
+                                int64_t phi, uint64_t seed, uint32_t ind, uint32_t gen, int16_t* best_col,
+                                int64_t* best_g_out, int64_t* best_fc, int64_t* moves_out, int32_t* trace, int32_t check) {
   auto nb = neighbour_lists(n, adj);
   std::vector<int16_t> col(col_in, col_in + n);
   for (int v = 0; v < n; ++v)
@@ -738,7 +740,7 @@ int32_t oracle_wvcp_tabu(int32_t n, const uint8_t* adj, const int32_t* w, int32_
   std::vector<int32_t> gamma;
   int64_t conf = build_gamma(n, k, nb, col.data(), gamma);
   int64_t f = oracle_wvcp_score(n, adj, w, k, col.data(), nullptr);
-  int64_t g = f + phi * conf;
+  int64_t g = fscale * f + phi * conf;
   std::vector<int64_t> frozen(n, 0);
   int64_t best_g = g, best_f = f, best_c = conf, moves = 0;
   std::copy(col.begin(), col.end(), best_col);
@@ -758,11 +760,15 @@ int32_t oracle_wvcp_tabu(int32_t n, const uint8_t* adj, const int32_t* w, int32_
     uint32_t r[4];
     draw(seed, (uint32_t)it, gen, ind, TAG_TABU, r);
     int64_t dmin = INT64_MAX, ties = 0;
-    auto delta_of = [&](int v, int c) -> int64_t {
+    // change of f when v moves to c: its old class may lose its maximum, the new one may gain
+    auto df_of = [&](int v, int c) -> int64_t {
       const int o = col[v];
       const int64_t old_after = (w[v] == max1[o] && cnt1[o] == 1) ? max2[o] : max1[o];
-      const int64_t df = (old_after - max1[o]) + (std::max<int64_t>(max1[c], w[v]) - max1[c]);
-      return df + phi * (int64_t)(gamma[(size_t)v * k + c] - gamma[(size_t)v * k + o]);
+      return (old_after - max1[o]) + (std::max<int64_t>(max1[c], w[v]) - max1[c]);
+    };
+    auto delta_of = [&](int v, int c) -> int64_t {
+      const int o = col[v];
+      return fscale * df_of(v, c) + phi * (int64_t)(gamma[(size_t)v * k + c] - gamma[(size_t)v * k + o]);
     };
     for (int v = 0; v < n; ++v)
       for (int c = 0; c < k; ++c) {
@@ -788,6 +794,7 @@ int32_t oracle_wvcp_tabu(int32_t n, const uint8_t* adj, const int32_t* w, int32_
         ++seen;
       }
     const int old = col[mv];
+    const int64_t dfm = df_of(mv, mc);
     conf += gamma[(size_t)mv * k + mc] - gamma[(size_t)mv * k + old];
     col[mv] = (int16_t)mc;
     for (int u : nb[mv]) {
@@ -796,7 +803,7 @@ int32_t oracle_wvcp_tabu(int32_t n, const uint8_t* adj, const int32_t* w, int32_
     }
     const int64_t g_before = g;
     g += dmin;
-    f = g - phi * conf;
+    f += dfm;
     frozen[mv] = it + 1 + (int64_t)below(r[1], (uint32_t)(L_max + 1)) + tt_base;
     ++moves;
     if (g < best_g) { best_g = g; best_f = f; best_c = conf; std::copy(col.begin(), col.end(), best_col); }
@@ -805,13 +812,57 @@ int32_t oracle_wvcp_tabu(int32_t n, const uint8_t* adj, const int32_t* w, int32_
       std::vector<int32_t> g2;
       const int64_t c2 = build_gamma(n, k, nb, col.data(), g2);
       const int64_t f2 = oracle_wvcp_score(n, adj, w, k, col.data(), nullptr);
-      if (g2 != gamma || c2 != conf || f2 != f || f2 + phi * c2 != g || g - g_before != dmin) return -2;
+      if (g2 != gamma || c2 != conf || f2 != f || fscale * f2 + phi * c2 != g || g - g_before != dmin) return -2;
     }
   }
   *best_g_out = best_g;
   best_fc[0] = best_f;
   best_fc[1] = best_c;
   if (moves_out) *moves_out = moves;
+  return 0;
+}
+
+int32_t oracle_wvcp_tabu(int32_t n, const uint8_t* adj, const int32_t* w, int32_t k, const int16_t* col_in,
+                         int64_t iters, int32_t L_max, int32_t alpha_num, int32_t alpha_den, int64_t phi,
+                         uint64_t seed, uint32_t ind, uint32_t gen, int16_t* best_col, int64_t* best_g_out,
+                         int64_t* best_fc, int64_t* moves_out, int32_t* trace, int32_t check) {
+  return oracle_wvcp_tabu_scaled(n, adj, w, k, col_in, iters, L_max, alpha_num, alpha_den, 1, phi, seed, ind, gen,
+                                 best_col, best_g_out, best_fc, moves_out, trace, check);
+}
+
+// Parallel iterated feasible and infeasible tabu search (Algorithm 2), one individual. max_ls
+// successive searches of `iters` iterations each, from the previous search's best colouring
+// (by g). phi is held in fixed point with resolution 1 / fscale and starts at phi0. After search
+// t, when t + 1 < max_ls - 1, phi is halved (floor, at least 1) if that search's best colouring
+// is legal and doubled otherwise; the last search (t = max_ls - 1) uses phi_last (the paper's
+// 2 max w, times fscale). Search t draws from generation gen * 16 + t (max_ls <= 16). The best
+// legal colouring over the searches (smallest f) is S'; best_f = -1 when no search ended legal
+// (best_col then receives the last search's best colouring). phi_trace (max_ls, or null)
+// receives the phi each search used; fc_trace (2 max_ls, or null) each search's (f, c).
+int32_t oracle_wvcp_iterated(int32_t n, const uint8_t* adj, const int32_t* w, int32_t k, const int16_t* col_in,
+                             int64_t iters, int32_t max_ls, int32_t L_max, int32_t alpha_num, int32_t alpha_den,
+                             int64_t fscale, int64_t phi0, int64_t phi_last, uint64_t seed, uint32_t ind, uint32_t gen,
+                             int16_t* best_col, int64_t* best_f, int64_t* phi_trace, int64_t* fc_trace) {
+  if (max_ls < 1 || max_ls > 16 || fscale < 1 || phi0 < 1 || phi_last < 1) return -1;
+  std::vector<int16_t> s(col_in, col_in + n), sb(n);
+  int64_t phi = phi0, bf = -1;
+  for (int t = 0; t < max_ls; ++t) {
+    if (t == max_ls - 1) phi = phi_last;
+    if (phi_trace) phi_trace[t] = phi;
+    int64_t bg, fc[2], mv;
+    const int32_t rc = oracle_wvcp_tabu_scaled(n, adj, w, k, s.data(), iters, L_max, alpha_num, alpha_den, fscale, phi,
+                                               seed, ind, gen * 16u + (uint32_t)t, sb.data(), &bg, fc, &mv, nullptr, 0);
+    if (rc != 0) return rc;
+    s = sb;
+    if (fc_trace) { fc_trace[2 * t] = fc[0]; fc_trace[2 * t + 1] = fc[1]; }
+    if (fc[1] == 0 && (bf < 0 || fc[0] < bf)) {
+      bf = fc[0];
+      std::copy(s.begin(), s.end(), best_col);
+    }
+    if (t + 1 < max_ls - 1) phi = fc[1] == 0 ? std::max<int64_t>(1, phi / 2) : phi * 2;
+  }
+  if (bf < 0) std::copy(s.begin(), s.end(), best_col);
+  *best_f = bf;
   return 0;
 }
 

@@ -346,6 +346,81 @@ def test_wvcp_tabu_check_mode_and_recount():
     assert mv > 0
 
 
+def _wvcp_case(n, p, seed):
+    e = inputs.gnp(n, p, seed=seed)
+    return e, inputs.edges_to_adj(n, e), inputs.weights(n, seed=seed)
+
+
+@pytest.mark.parametrize("scale", [2, 256])
+def test_wvcp_scaled_objective_moves_like_the_unscaled_one(scale):
+    """g = s f + (s phi) c is s times f + phi c, so every delta scales by s and the search takes the
+    same moves (check mode recounts f, c and g after each of them)."""
+    n = 45
+    e, adj, w = _wvcp_case(n, 0.4, 6)
+    col, used = _wvcp_greedy(adj, w, seed=6)
+    start = inputs.random_colorings(1, n, used, seed=8)[0]
+    phi = 37
+    a = oracle.wvcp_tabu(adj, w, used, start, 400, phi, seed=3, ind=1, trace=True, check=True)
+    b = oracle.wvcp_tabu(adj, w, used, start, 400, scale * phi, seed=3, ind=1, fscale=scale, trace=True, check=True)
+    assert np.array_equal(a["trace"][:, :2], b["trace"][:, :2]) and np.array_equal(a["trace"][:, 3], b["trace"][:, 3])
+    assert np.array_equal(a["trace"][:, 2] * scale, b["trace"][:, 2])
+    assert (a["f"], a["c"], a["moves"]) == (b["f"], b["c"], b["moves"]) and b["best_g"] == scale * a["best_g"]
+    assert np.array_equal(a["best_col"], b["best_col"])
+
+
+def test_wvcp_iterated_single_search_is_the_last_run_setting():
+    """With one search, Algorithm 2 is one tabu search at phi = phi_last (generation 16 gen)."""
+    n = 40
+    e, adj, w = _wvcp_case(n, 0.5, 2)
+    col, used = _wvcp_greedy(adj, w, seed=2)
+    start = inputs.random_colorings(1, n, used, seed=4)[0]
+    phi_last = 2 * int(w.max())
+    it = oracle.wvcp_iterated(adj, w, used, start, 300, 1, 1, 5, phi_last, seed=7, ind=3, gen=2)
+    ref = oracle.wvcp_tabu(adj, w, used, start, 300, phi_last, seed=7, ind=3, gen=32)
+    assert list(it["phi"]) == [phi_last] and (it["fc"][0, 0], it["fc"][0, 1]) == (ref["f"], ref["c"])
+    if ref["c"] == 0:
+        assert it["best_f"] == ref["f"] and np.array_equal(it["best_col"], ref["best_col"])
+    else:
+        assert it["best_f"] == -1
+
+
+@pytest.mark.parametrize("gseed", [1, 3])
+def test_wvcp_iterated_schedule_and_best_legal(gseed):
+    """phi halves after a search whose best colouring is legal and doubles otherwise (floor, at least
+    1), the last search uses phi_last, and S' is the legal search result with the smallest f."""
+    n = 60
+    e, adj, w = _wvcp_case(n, 0.5, gseed)
+    col, used = _wvcp_greedy(adj, w, seed=gseed)
+    start = inputs.random_colorings(1, n, used, seed=gseed + 10)[0]
+    fscale, max_ls = 256, 10
+    phi0 = (fscale * used * int(w.max()) + n) // (2 * n)
+    phi_last = fscale * 2 * int(w.max())
+    r = oracle.wvcp_iterated(adj, w, used, start, 150, max_ls, fscale, phi0, phi_last, seed=gseed, ind=0, gen=1)
+    phis, fcs = r["phi"], r["fc"]
+    assert phis[0] == phi0 and phis[-1] == phi_last
+    for t in range(max_ls - 2):
+        legal = fcs[t, 1] == 0
+        assert phis[t + 1] == (max(1, phis[t] // 2) if legal else 2 * phis[t])
+    legal_f = [int(f) for f, c in fcs if c == 0]
+    assert r["best_f"] == (min(legal_f) if legal_f else -1)
+    if legal_f:
+        b = r["best_col"]
+        assert int(np.sum(b[e[:, 0]] == b[e[:, 1]])) == 0
+        assert sum(int(w[b == q].max()) for q in range(used) if np.any(b == q)) == r["best_f"]
+
+
+@pytest.mark.parametrize("gseed", [1, 2])
+def test_wvcp_iterated_reaches_brute_force_optimum(gseed):
+    n = 7
+    e = inputs.gnp(n, 0.5, seed=gseed)
+    adj = inputs.edges_to_adj(n, e)
+    w = inputs.weights(n, seed=gseed)
+    col, used = _wvcp_greedy(adj, w, seed=gseed)
+    r = oracle.wvcp_iterated(adj, w, used, col, 300, 10, 256, (256 * used * int(w.max()) + n) // (2 * n),
+                             256 * 2 * int(w.max()), seed=gseed, ind=0)
+    assert r["best_f"] == _wvcp_brute(n, e, w, used)
+
+
 # ------------------------------------------------------------------------------------------------
 # memetic generation (Algorithm 1)
 # ------------------------------------------------------------------------------------------------
