@@ -318,7 +318,7 @@ dlm_status dlm_memetic_load(dlm_ctx* ctx, dlm_memetic* mm, const void* host);
  *   col      device [pop][n] int16: in start colourings (0..k-1), out the best-g colouring visited
  *   best_g   device [pop] int64 out;  best_fc  device [pop][2] int64 out (f, c of it) or NULL
  *   moves    device [pop] int64 out or NULL;  iters  iterations per individual (paper: 10 |V|)
- * Limits: k <= 255; phi * (max degree + 1) < 2^30; tenure < 2^14. */
+ * Limits: k <= 255; max w + phi * (max degree + 1) < 2^30; tenure < 2^14. */
 dlm_status dlm_wvcp_greedy(dlm_ctx* ctx, const dlm_graph* g, int32_t pop, uint64_t seed, uint32_t ind_base,
                            int16_t* col, int32_t* used);
 dlm_status dlm_wvcp_tabu_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
@@ -330,6 +330,24 @@ dlm_status dlm_wvcp_tabu_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int32_t k, i
                                   int64_t* best_g, int64_t* best_fc, int64_t* moves, int64_t iters,
                                   dlm_tenure tenure, int64_t phi, uint64_t seed, uint32_t generation,
                                   uint32_t ind_base, int32_t* trace);
+
+/* Parallel iterated feasible and infeasible tabu search (Algorithm 2): max_ls (paper: 10, at most
+ * 16) successive searches of iters iterations (paper: 10 |V|) per individual, each from the
+ * previous one's best colouring (by g), on g = fscale f + phi c, phi held in fixed point with
+ * resolution 1 / fscale (a reading: the paper's phi is real). phi starts at phi0 (paper:
+ * k max w / (2 |V|), times fscale); after search t, while t + 1 < max_ls - 1, it is halved (floor,
+ * at least 1) when that search's best colouring is legal and doubled otherwise; the last search
+ * uses phi_last (paper: 2 max w, times fscale). Search t draws Philox blocks of generation
+ * generation * 16 + t. col (device [pop][n] int16, in: start, out: the last search's best);
+ * best_col (device [pop][n] int16 out): the legal colouring with the smallest f over the
+ * searches, or the last search's best when none was legal; best_f (device [pop] int64 out): its
+ * f, or -1. Move keys are 32-bit: fscale max w + phi (max degree + 1) must stay below 2^30 for
+ * the largest phi of the schedule (DLM_EUNSUPPORTED otherwise). Allocates and frees a pop * 32
+ * byte scratch and waits for the searches. */
+dlm_status dlm_wvcp_iterated(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                             int16_t* best_col, int64_t* best_f, int64_t iters, int32_t max_ls, dlm_tenure tenure,
+                             int32_t fscale, int64_t phi0, int64_t phi_last, uint64_t seed, uint32_t generation,
+                             uint32_t ind_base);
 
 /* ---------------------------------------------------------------------------------------------
  * Building block of the scorer, exported for testing: C = A . B^T on the tcgen05 tensor cores.

@@ -71,7 +71,9 @@ struct WvcpArgs {
   int32_t* trace;
   uint16_t* slab;  // per CTA: (k - cs) * npad u16
   int64_t iters;
-  int64_t phi;
+  int64_t phi;             // penalty (g = fscale f + phi c), or per individual from phi_arr
+  const int64_t* phi_arr;  // [pop] or null
+  int32_t fscale;
   uint32_t L1, ttbase;
   uint64_t seed;
   uint32_t gen, ind_base;
@@ -107,8 +109,8 @@ __device__ __forceinline__ void class_add(uint16_t* lvl, uint32_t* lmask, int lw
 }
 
 __device__ __forceinline__ void wvcp_scan_key(int c, int o, int wv, int m1c, int base, int64_t phi, int gc, bool frozen,
-                                              int thr, int& km, int& kc) {
-  const int d = base + (wv > m1c ? wv - m1c : 0) + (int)phi * gc;
+                                              int thr, int& km, int& kc, int fs) {
+  const int d = base + fs * (wv > m1c ? wv - m1c : 0) + (int)phi * gc;
   const int key = (c != o && (!frozen || d < thr)) ? d : INT_MAX;
   if (key < km) { km = key; kc = 1; }
   else if (key == km && key != INT_MAX) ++kc;
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   uint16_t* gS = (uint16_t*)(smem + L.gT);
   uint16_t* gG = a.slab + (size_t)blockIdx.x * (size_t)(k - cs) * npad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t phi = a.phi;
+  const int fs = a.fscale;
   int per = (n + kWThreads - 1) / kWThreads;
   {
     int p2 = 1;
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
 
   for (int ind = blockIdx.x; ind < a.pop; ind += gridDim.x) {
     int16_t* gcol = a.col + (size_t)ind * n;
+    const int64_t phi = a.phi_arr ? a.phi_arr[ind] : a.phi;
     // ---- set-up ---------------------------------------------------------------------------
     {
       uint32_t* l32 = (uint32_t*)lvl;
@@ -219,9 +222,9 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
       long long ct = 0, ft = 0;
       for (int w = 0; w < kWWarps; ++w) { ct += sc64[8 + w]; ft += sc64[8 + kWWarps + w]; }
       const long long conf = ct / 2;
-      sc64[0] = ft + phi * conf;
+      sc64[0] = fs * ft + phi * conf;
       sc64[1] = conf;
-      sc64[2] = ft + phi * conf;
+      sc64[2] = fs * ft + phi * conf;
       sc64[3] = ft;
       sc64[4] = conf;
     }
@@ -252,13 +255,13 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         const int g0a = oa < cs ? gS[(size_t)oa * npad + v] : gG[(size_t)(oa - cs) * npad + v];
         const int g0b = ob < cs ? gS[(size_t)ob * npad + vb] : gG[(size_t)(ob - cs) * npad + vb];
         const bool fra = fz[v] > itrel, frb = fz[vb] > itrel;
-        const int basea = rema - (int)phi * g0a, baseb = remb - (int)phi * g0b;
+        const int basea = fs * rema - (int)phi * g0a, baseb = fs * remb - (int)phi * g0b;
         int kma = INT_MAX, kca = 0, kmb = INT_MAX, kcb = 0;
 #pragma unroll 4
         for (int c = 0; c < cs; ++c) {
           const int m1 = max1s[c];
-          wvcp_scan_key(c, oa, wa, m1, basea, phi, gS[(size_t)c * npad + v], fra, thr, kma, kca);
-          wvcp_scan_key(c, ob, wb, m1, baseb, phi, gS[(size_t)c * npad + vb], frb, thr, kmb, kcb);
+          wvcp_scan_key(c, oa, wa, m1, basea, phi, gS[(size_t)c * npad + v], fra, thr, kma, kca, fs);
+          wvcp_scan_key(c, ob, wb, m1, baseb, phi, gS[(size_t)c * npad + vb], frb, thr, kmb, kcb, fs);
         }
         // the slab colours come from L2: 16 independent loads per vertex in flight before use
         int c = cs;
@@ -272,14 +275,14 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int m1 = max1s[c + q];
-            wvcp_scan_key(c + q, oa, wa, m1, basea, phi, qa[q], fra, thr, kma, kca);
-            wvcp_scan_key(c + q, ob, wb, m1, baseb, phi, qb[q], frb, thr, kmb, kcb);
+            wvcp_scan_key(c + q, oa, wa, m1, basea, phi, qa[q], fra, thr, kma, kca, fs);
+            wvcp_scan_key(c + q, ob, wb, m1, baseb, phi, qb[q], frb, thr, kmb, kcb, fs);
           }
         }
         for (; c < k; ++c) {
           const int m1 = max1s[c];
-          wvcp_scan_key(c, oa, wa, m1, basea, phi, gG[(size_t)(c - cs) * npad + v], fra, thr, kma, kca);
-          wvcp_scan_key(c, ob, wb, m1, baseb, phi, gG[(size_t)(c - cs) * npad + vb], frb, thr, kmb, kcb);
+          wvcp_scan_key(c, oa, wa, m1, basea, phi, gG[(size_t)(c - cs) * npad + v], fra, thr, kma, kca, fs);
+          wvcp_scan_key(c, ob, wb, m1, baseb, phi, gG[(size_t)(c - cs) * npad + vb], frb, thr, kmb, kcb, fs);
         }
         rmin[v] = kma;
         rcnt[v] = (uint16_t)(kma == INT_MAX ? 0 : kca);
@@ -333,11 +336,11 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
             const int rem = (wv == m1o && c1o == 1) ? m2o - m1o : 0;
             const int g0 = o < cs ? gS[(size_t)o * npad + v] : gG[(size_t)(o - cs) * npad + v];
             const bool frozen = fz[v] > itrel;
-            const int base = rem - (int)phi * g0;
+            const int base = fs * rem - (int)phi * g0;
             for (int c = 0; c < k; ++c) {
               int km = INT_MAX, kc = 0;
               const int gc = c < cs ? gS[(size_t)c * npad + v] : gG[(size_t)(c - cs) * npad + v];
-              wvcp_scan_key(c, o, wv, max1s[c], base, phi, gc, frozen, thr, km, kc);
+              wvcp_scan_key(c, o, wv, max1s[c], base, phi, gc, frozen, thr, km, kc, fs);
               if (km == dstar) {
                 if (jj == 0) { mc = c; break; }
                 --jj;
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
             sc[0] = mv; sc[1] = o; sc[2] = mc; sc[3] = gn64 < best_g;
             sc64[0] = gn64;
             sc64[1] = cn64;
-            if (gn64 < best_g) { sc64[2] = gn64; sc64[3] = gn64 - phi * cn64; sc64[4] = cn64; }
+            if (gn64 < best_g) { sc64[2] = gn64; sc64[3] = (gn64 - phi * cn64) / fs; sc64[4] = cn64; }
             if (trace) reinterpret_cast<int4*>(trace)[it] = make_int4(mv, mc, dstar, T);
           } else {
             sc[4] = 2;
@@ -518,14 +521,18 @@ extern "C" dlm_status dlm_wvcp_greedy(dlm_ctx* ctx, const dlm_graph* g, int32_t 
 
 static dlm_status wvcp_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col, int64_t* best_g,
                            int64_t* best_fc, int64_t* moves, int64_t iters, dlm_tenure tenure, int64_t phi, uint64_t seed,
-                           uint32_t generation, uint32_t ind_base, int32_t* trace) {
+                           uint32_t generation, uint32_t ind_base, int32_t* trace, const int64_t* phi_arr = nullptr,
+                           int32_t fscale = 1) {
   if (!ctx || !g) return fail(ctx, DLM_EINVAL, "wvcp_tabu: null argument");
   if (!g->d_weight) return fail(ctx, DLM_EINVAL, "wvcp_tabu: the graph has no vertex weights");
   if (k < 2 || k > 255) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: k must be in 2..255");
   if (g->max_weight > 255) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: vertex weights must be <= 255");
   if (pop < 0 || iters < 0 || iters > INT32_MAX) return fail(ctx, DLM_EINVAL, "wvcp_tabu: bad population or budget");
-  if (phi < 0 || phi * (int64_t)(g->max_degree + 1) >= ((int64_t)1 << 30))
-    return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: phi * (max degree + 1) must stay below 2^30");
+  // keys are 32-bit: fscale (max w) + phi (max degree + 1) must stay below 2^30 (phi: the largest
+  // per-individual value the caller can pass, checked by the caller for phi_arr)
+  if (phi < 0 || fscale < 1 ||
+      (int64_t)fscale * g->max_weight + phi * (int64_t)(g->max_degree + 1) >= ((int64_t)1 << 30))
+    return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: fscale * max w + phi * (max degree + 1) must stay below 2^30");
   if (tenure.L_max < 0 || tenure.alpha_num < 0 || tenure.alpha_den <= 0) return fail(ctx, DLM_EINVAL, "wvcp_tabu: bad tenure");
   const int64_t ttbase = ((int64_t)tenure.alpha_num * g->n) / tenure.alpha_den;
   if (ttbase + tenure.L_max + 1 >= 0x4000) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: tenure must stay below 2^14");
@@ -540,7 +547,8 @@ static dlm_status wvcp_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t 
   WvcpArgs a;
   a.n = g->n; a.k = k; a.words = g->words; a.pop = pop; a.wmax = g->max_weight;
   a.bits = g->d_bits; a.weight = g->d_weight; a.col = col; a.best_g = best_g; a.best_fc = best_fc; a.moves = moves;
-  a.trace = trace; a.slab = slab; a.iters = iters; a.phi = phi; a.L1 = (uint32_t)tenure.L_max + 1u;
+  a.trace = trace; a.slab = slab; a.iters = iters; a.phi = phi; a.phi_arr = phi_arr; a.fscale = fscale;
+  a.L1 = (uint32_t)tenure.L_max + 1u;
   a.ttbase = (uint32_t)ttbase; a.seed = seed; a.gen = generation; a.ind_base = ind_base; a.status = ctx->d_status;
   a.smem_budget = ctx->smem_optin;
   DLM_CUDA(ctx, cudaFuncSetAttribute(k_wvcp_tabu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
@@ -560,4 +568,88 @@ extern "C" dlm_status dlm_wvcp_tabu_batch_ex(dlm_ctx* ctx, const dlm_graph* g, i
                                              dlm_tenure tenure, int64_t phi, uint64_t seed, uint32_t generation,
                                              uint32_t ind_base, int32_t* trace) {
   return wvcp_run(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure, phi, seed, generation, ind_base, trace);
+}
+
+// ---- Algorithm 2: iterated feasible/infeasible tabu search with the adaptive penalty -----------
+namespace dlm {
+
+__global__ void k_ls_init(int pop, int64_t phi0, int64_t* phi, int64_t* best_f) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < pop) { phi[i] = phi0; best_f[i] = -1; }
+}
+
+// after search t: keep the best legal colouring, then adapt phi (halve after a legal result,
+// double otherwise; the last search uses phi_last); one block per individual
+__global__ void k_ls_update(int pop, int n, const int16_t* col, const int64_t* fc, int64_t* phi, int64_t* best_f,
+                            int16_t* best_col, int t, int max_ls, int64_t phi_last) {
+  const int i = blockIdx.x;
+  if (i >= pop) return;
+  const int64_t f = fc[2 * i], c = fc[2 * i + 1];
+  const bool take = c == 0 && (best_f[i] < 0 || f < best_f[i]);
+  if (take)
+    for (int v = threadIdx.x; v < n; v += blockDim.x) best_col[(size_t)i * n + v] = col[(size_t)i * n + v];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (take) best_f[i] = f;
+    if (t + 1 < max_ls - 1) phi[i] = c == 0 ? (phi[i] / 2 > 1 ? phi[i] / 2 : 1) : 2 * phi[i];
+    else phi[i] = phi_last;
+  }
+}
+
+// individuals that never reached a legal colouring report the last search's best
+__global__ void k_ls_finish(int pop, int n, const int16_t* col, const int64_t* best_f, int16_t* best_col) {
+  const int i = blockIdx.x;
+  if (i >= pop || best_f[i] >= 0) return;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) best_col[(size_t)i * n + v] = col[(size_t)i * n + v];
+}
+
+}  // namespace dlm
+
+extern "C" dlm_status dlm_wvcp_iterated(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                        int16_t* best_col, int64_t* best_f, int64_t iters, int32_t max_ls,
+                                        dlm_tenure tenure, int32_t fscale, int64_t phi0, int64_t phi_last,
+                                        uint64_t seed, uint32_t generation, uint32_t ind_base) {
+  if (!ctx || !g) return fail(ctx, DLM_EINVAL, "wvcp_iterated: null argument");
+  if (max_ls < 1 || max_ls > 16 || fscale < 1 || phi0 < 1 || phi_last < 1)
+    return fail(ctx, DLM_EINVAL, "wvcp_iterated: need 1 <= max_ls <= 16, fscale >= 1, phi0 >= 1, phi_last >= 1");
+  if (pop == 0) return DLM_OK;
+  if (!col || !best_col || !best_f || pop < 0) return fail(ctx, DLM_EINVAL, "wvcp_iterated: null output");
+  // the largest penalty any search can use: phi0 doubled before every search but the last, or phi_last
+  int64_t phi_max = phi0;
+  for (int t = 0; t + 2 < max_ls && phi_max < ((int64_t)1 << 40); ++t) phi_max *= 2;
+  phi_max = phi_max > phi_last ? phi_max : phi_last;
+  if ((int64_t)fscale * g->max_weight + phi_max * (int64_t)(g->max_degree + 1) >= ((int64_t)1 << 30))
+    return fail(ctx, DLM_EUNSUPPORTED, "wvcp_iterated: the penalty schedule would overflow 32-bit move keys");
+  // per-individual phi, (f, c) and best g of each search: their own allocation (the searches use the
+  // context workspace for their slabs)
+  uint8_t* buf = nullptr;
+  if (cudaMalloc(&buf, (size_t)pop * 32) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DLM_ENOMEM, "wvcp_iterated: scratch allocation failed");
+  }
+  int64_t* phi = (int64_t*)buf;
+  int64_t* fc = phi + pop;
+  int64_t* bg = fc + 2 * (size_t)pop;
+  dlm_status st = DLM_OK;
+  k_ls_init<<<(pop + 255) / 256, 256, 0, ctx->stream>>>(pop, phi0, phi, best_f);
+  st = launch_check(ctx, "k_ls_init");
+  for (int t = 0; t < max_ls && st == DLM_OK; ++t) {
+    if (t == max_ls - 1 && max_ls == 1) {
+      k_ls_init<<<(pop + 255) / 256, 256, 0, ctx->stream>>>(pop, phi_last, phi, best_f);
+      st = launch_check(ctx, "k_ls_init");
+      if (st != DLM_OK) break;
+    }
+    st = wvcp_run(ctx, g, k, pop, col, bg, fc, nullptr, iters, tenure, phi_max, seed, generation * 16u + (uint32_t)t,
+                  ind_base, nullptr, phi, fscale);
+    if (st != DLM_OK) break;
+    k_ls_update<<<pop, 128, 0, ctx->stream>>>(pop, g->n, col, fc, phi, best_f, best_col, t, max_ls, phi_last);
+    st = launch_check(ctx, "k_ls_update");
+  }
+  if (st == DLM_OK) {
+    k_ls_finish<<<pop, 128, 0, ctx->stream>>>(pop, g->n, col, best_f, best_col);
+    st = launch_check(ctx, "k_ls_finish");
+  }
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(buf);
+  return st;
 }

@@ -94,6 +94,8 @@ _SIGS = {
     "dlm_wvcp_tabu_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32]),
     "dlm_wvcp_tabu_batch_ex": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32, _P]),
     "dlm_wvcp_greedy": (_i32, [_P, _P, _i32, _u64, _u32, _P, _P]),
+    "dlm_wvcp_iterated": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, _i32, Tenure, _i32, _i64, _i64, _u64, _u32,
+                                 _u32]),
 }
 
 _lib = None
@@ -456,3 +458,9 @@ class MultiPlan:
 
 def dlm_tabucol_multi_plan_launch(ctx, plan):
     ctx.check(lib().dlm_tabucol_multi_plan_launch(ctx.h, plan.h), "dlm_tabucol_multi_plan_launch")
+
+
+def dlm_wvcp_iterated(ctx, g, k, pop, col, best_col, best_f, iters, max_ls=10, tenure=WVCP_TENURE, fscale=256,
+                      phi0=1, phi_last=1, seed=0, generation=0, ind_base=0):
+    ctx.check(lib().dlm_wvcp_iterated(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_col), _ptr(best_f), iters, max_ls,
+                                      tenure, fscale, phi0, phi_last, seed, generation, ind_base), "dlm_wvcp_iterated")

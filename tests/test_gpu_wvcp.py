@@ -152,3 +152,48 @@ def test_wvcp_full_size_sampled(ctx):
     for i, r in zip((0, pop - 1), refs):
         assert (bg[i], fc[i, 0], fc[i, 1], mv[i]) == (r["best_g"], r["f"], r["c"], r["moves"])
         assert np.array_equal(gcol[i], r["best_col"])
+
+
+def _oracle_iterated(args):
+    import oracle as o
+
+    adj, w, k, col, iters, max_ls, fscale, phi0, phi_last, seed, ind, gen = args
+    return o.wvcp_iterated(adj, w, k, col, iters, max_ls, fscale, phi0, phi_last, seed, ind, gen)
+
+
+@pytest.mark.parametrize("n,p,seed,iters,max_ls,legal_start", [(50, 0.5, 1, 200, 10, True), (90, 0.4, 2, 150, 4, False),
+                                                                (40, 0.6, 3, 100, 1, False), (120, 0.5, 4, 120, 2, True)])
+def test_wvcp_iterated_matches_oracle(ctx, n, p, seed, iters, max_ls, legal_start):
+    """Algorithm 2 on the GPU: the best legal colouring and its f (or -1) and the last search's best
+    colouring equal the oracle's for every individual (fixed-point phi, resolution 1/256)."""
+    e, adj, w = _case(n, p, seed)
+    g = device_graph(ctx, n, e, w)
+    pop = 5
+    greedy = [_oracle_greedy(adj, w, seed, i) for i in range(pop)]
+    k = max(u for _, u in greedy)
+    starts = np.stack([c for c, _ in greedy]) if legal_start else inputs.random_colorings(pop, n, k, seed=seed)
+    fscale = 256
+    phi0 = (fscale * k * int(w.max()) + n) // (2 * n)
+    phi_last = fscale * 2 * int(w.max())
+    col = torch.from_numpy(starts.copy()).cuda()
+    best_col = torch.zeros_like(col)
+    best_f = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    dlmcol.dlm_wvcp_iterated(ctx, g, k, pop, col, best_col, best_f, iters, max_ls, dlmcol.WVCP_TENURE, fscale, phi0,
+                             phi_last, seed, 2, 0)
+    ctx.sync()
+    refs = oracle_pool().map(_oracle_iterated, [(adj, w, k, starts[i], iters, max_ls, fscale, phi0, phi_last, seed, i, 2)
+                                                for i in range(pop)])
+    bf, bc = best_f.cpu().numpy(), best_col.cpu().numpy()
+    for i, r in enumerate(refs):
+        assert bf[i] == r["best_f"], i
+        assert np.array_equal(bc[i], r["best_col"]), i
+
+
+def test_wvcp_iterated_rejects_overflowing_schedule(ctx):
+    n = 30
+    e = inputs.gnp(n, 0.5, 1)
+    g = device_graph(ctx, n, e, inputs.weights(n, 1))
+    col = torch.zeros((1, n), dtype=torch.int16, device="cuda")
+    bf = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(dlmcol.DlmError):  # phi0 doubled eight times overflows the 32-bit keys
+        dlmcol.dlm_wvcp_iterated(ctx, g, 5, 1, col, col.clone(), bf, 10, 10, dlmcol.WVCP_TENURE, 256, 1 << 20, 1)
