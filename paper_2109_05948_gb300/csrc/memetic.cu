@@ -22,6 +22,9 @@ struct dlm_memetic {
   float* scores = nullptr;
   int64_t* h_best = nullptr;  // pinned
   dlm_scorer* scorer = nullptr;
+  // the scorer trains on a side stream while the distances and the pool update run
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_trained = nullptr;
 };
 
 namespace dlm {
@@ -150,6 +153,9 @@ extern "C" void dlm_memetic_destroy(dlm_memetic* mm) {
   cudaFree(mm->cid); cudaFree(mm->scores);
   if (mm->h_best) cudaFreeHost(mm->h_best);
   if (mm->scorer) dlm_scorer_destroy(mm->scorer);
+  if (mm->ev_ready) cudaEventDestroy(mm->ev_ready);
+  if (mm->ev_trained) cudaEventDestroy(mm->ev_trained);
+  if (mm->side) cudaStreamDestroy(mm->side);
   delete mm;
 }
 
@@ -179,6 +185,13 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
   A(&mm->cid, (size_t)p * nk); A(&mm->scores, (size_t)p * K);
   if (st == DLM_OK && cudaMallocHost(&mm->h_best, sizeof(int64_t)) != cudaSuccess) st = fail(ctx, DLM_ENOMEM, "pinned");
   if (st == DLM_OK && prm->use_scorer) st = dlm_scorer_create(ctx, n, k, prm->seed, &mm->scorer);
+  if (st == DLM_OK && prm->use_scorer &&
+      (cudaStreamCreateWithFlags(&mm->side, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaEventCreateWithFlags(&mm->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&mm->ev_trained, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    st = fail(ctx, DLM_ECUDA, "memetic_create: side stream");
+  }
   if (st != DLM_OK) { dlm_memetic_destroy(mm); return st; }
   // initial population: random colourings, their conflicts and their distance matrix
   const int64_t big = INT64_MAX;
@@ -207,9 +220,17 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
   // 2. best so far
   k_best_of<<<1, 1024, 0, s>>>(p, n, mm->fSp, mm->Sp, mm->best_f, mm->best_col);
   DLM_TRY(launch_check(ctx, "k_best_of"));
-  // 3. training on {(S^O_i, f(S'_i))}
-  if (q.use_scorer)
-    DLM_TRY(dlm_scorer_train(ctx, mm->scorer, mm->SO, mm->fSp, p, q.epochs, q.batch, q.lr, q.seed, mm->gen));
+  // 3. training on {(S^O_i, f(S'_i))}, on the side stream: it only reads S^O and f(S'), which
+  //    nothing below writes before the scoring, and the scoring waits for it
+  if (q.use_scorer) {
+    DLM_CUDA(ctx, cudaEventRecord(mm->ev_ready, s));
+    DLM_CUDA(ctx, cudaStreamWaitEvent(mm->side, mm->ev_ready, 0));
+    ctx->stream = mm->side;
+    const dlm_status ts = dlm_scorer_train(ctx, mm->scorer, mm->SO, mm->fSp, p, q.epochs, q.batch, q.lr, q.seed, mm->gen);
+    ctx->stream = s;
+    DLM_TRY(ts);
+    DLM_CUDA(ctx, cudaEventRecord(mm->ev_trained, mm->side));
+  }
   // 4. distances: P x P' (rows < p, columns >= p) and P' x P' (upper triangle), then assemble
   DLM_TRY(dlm_distance_batch(ctx, n, k, mm->P, p, mm->Sp, p, mm->Dall + p, m, 0));
   DLM_TRY(dlm_distance_batch(ctx, n, k, mm->Sp, p, mm->Sp, p, mm->Dall + (size_t)p * m + p, m, 1));
@@ -235,6 +256,7 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     k_pairs_all<<<(p * K + 255) / 256, 256, 0, s>>>(p, K, mm->nbr, mm->pairs, mm->cid);
     DLM_TRY(launch_check(ctx, "k_pairs_all"));
     DLM_TRY(dlm_gpx_batch(ctx, n, k, mm->P, p, mm->pairs, mm->cid, p * K, mm->kids, q.seed, mm->gen));
+    DLM_CUDA(ctx, cudaStreamWaitEvent(s, mm->ev_trained, 0));
     DLM_TRY(dlm_score_offspring(ctx, mm->scorer, mm->kids, p * K, mm->scores));
     k_select_best<<<p, 128, 0, s>>>(p, K, n, mm->scores, mm->kids, mm->SO, mm->pick);
     DLM_TRY(launch_check(ctx, "k_select_best"));
