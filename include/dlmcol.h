@@ -283,6 +283,16 @@ dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, void* d
 /* Overwrites the population state (which = 0..3 as above) from device memory src. */
 dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const void* src);
 
+/* The vertex colouring problem (section "Adaptations of the algorithm for the vertex coloring
+ * problem"): k-COL with decreasing k. Starting at k = prm->k, a memetic search (fresh random
+ * population, parameters prm with that k) runs up to max_gens generations; when it reaches a
+ * legal k-colouring, its colouring goes to best_col (device [n] int16) and k is decreased by one;
+ * the first k without a legal colouring within max_gens generations ends the descent. k_best
+ * (host) receives the last k with a legal colouring (-1: none); gens_per_k (host [prm->k + 1],
+ * or NULL) the generations run at each k. Waits for every generation. */
+dlm_status dlm_col_descend(dlm_ctx* ctx, const dlm_graph* g, const dlm_memetic_params* prm, int32_t max_gens,
+                           int32_t* k_best, int16_t* best_col, int32_t* gens_per_k);
+
 /* Checkpoint and resume (the paper runs last up to 138 h and describes no checkpoint; this is
  * the state Algorithm 1 carries from one generation to the next). dlm_memetic_state_bytes gives
  * the size of the blob; dlm_memetic_save writes it to caller-owned host memory (a 64-byte header

@@ -185,8 +185,10 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
   A(&mm->cid, (size_t)p * nk); A(&mm->scores, (size_t)p * K);
   if (st == DLM_OK && cudaMallocHost(&mm->h_best, sizeof(int64_t)) != cudaSuccess) st = fail(ctx, DLM_ENOMEM, "pinned");
   if (st == DLM_OK && prm->use_scorer) st = dlm_scorer_create(ctx, n, k, prm->seed, &mm->scorer);
+  int prio_least = 0, prio_greatest = 0;  // the training's short kernels take SMs as the distance blocks drain
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   if (st == DLM_OK && prm->use_scorer &&
-      (cudaStreamCreateWithFlags(&mm->side, cudaStreamNonBlocking) != cudaSuccess ||
+      (cudaStreamCreateWithPriority(&mm->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
        cudaEventCreateWithFlags(&mm->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
        cudaEventCreateWithFlags(&mm->ev_trained, cudaEventDisableTiming) != cudaSuccess)) {
     cudaGetLastError();
@@ -398,5 +400,38 @@ extern "C" dlm_status dlm_memetic_load(dlm_ctx* ctx, dlm_memetic* mm, const void
   DLM_CUDA(ctx, cudaStreamSynchronize(s));
   if (mm->scorer) DLM_TRY(dlm_scorer_load(ctx, mm->scorer, h + L.scorer));
   mm->gen = H.gen;
+  return DLM_OK;
+}
+
+// ---- COL: k-COL with decreasing k ----------------------------------------------------------------
+extern "C" dlm_status dlm_col_descend(dlm_ctx* ctx, const dlm_graph* g, const dlm_memetic_params* prm, int32_t max_gens,
+                                      int32_t* k_best, int16_t* best_col, int32_t* gens_per_k) {
+  if (!ctx || !g || !prm || !k_best || !best_col) return fail(ctx, DLM_EINVAL, "col_descend: null argument");
+  if (max_gens < 1) return fail(ctx, DLM_EINVAL, "col_descend: max_gens must be positive");
+  *k_best = -1;
+  for (int k = prm->k; k >= 2; --k) {
+    dlm_memetic_params q = *prm;
+    q.k = k;
+    dlm_memetic* mm = nullptr;
+    DLM_TRY(dlm_memetic_create(ctx, g, &q, &mm));
+    bool solved = false;
+    int gens = 0;
+    dlm_status st = DLM_OK;
+    for (; gens < max_gens && st == DLM_OK && !solved; ++gens) {
+      int64_t best = 0;
+      st = dlm_memetic_step(ctx, mm, &best);
+      solved = st == DLM_OK && best == 0;
+    }
+    if (gens_per_k) gens_per_k[k] = gens;
+    if (st == DLM_OK && solved) {
+      st = cuda_check(ctx, cudaMemcpyAsync(best_col, mm->best_col, (size_t)g->n * 2, cudaMemcpyDeviceToDevice, ctx->stream),
+                      "copy");
+      if (st == DLM_OK) st = dlm_sync(ctx);
+    }
+    dlm_memetic_destroy(mm);
+    if (st != DLM_OK) return st;
+    if (!solved) break;
+    *k_best = k;
+  }
   return DLM_OK;
 }

@@ -81,6 +81,7 @@ _SIGS = {
     "dlm_memetic_step": (_i32, [_P, _P, _P]),
     "dlm_memetic_get": (_i32, [_P, _P, _i32, _P]),
     "dlm_memetic_set": (_i32, [_P, _P, _i32, _P]),
+    "dlm_col_descend": (_i32, [_P, _P, _P, _i32, _P, _P, _P]),
     "dlm_memetic_state_bytes": (_i64, [_P]),
     "dlm_memetic_save": (_i32, [_P, _P, _P]),
     "dlm_memetic_load": (_i32, [_P, _P, _P]),
@@ -464,3 +465,14 @@ def dlm_wvcp_iterated(ctx, g, k, pop, col, best_col, best_f, iters, max_ls=10, t
                       phi0=1, phi_last=1, seed=0, generation=0, ind_base=0):
     ctx.check(lib().dlm_wvcp_iterated(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_col), _ptr(best_f), iters, max_ls,
                                       tenure, fscale, phi0, phi_last, seed, generation, ind_base), "dlm_wvcp_iterated")
+
+
+def dlm_col_descend(ctx, g, params, max_gens, best_col):
+    """k-COL with decreasing k from params.k: returns (k_best, generations run per k)."""
+    import numpy as np
+
+    kb = ctypes.c_int32(0)
+    gens = np.zeros(params.k + 1, np.int32)
+    ctx.check(lib().dlm_col_descend(ctx.h, g.h, ctypes.byref(params), max_gens, ctypes.byref(kb), _ptr(best_col),
+                                    _ptr(gens)), "dlm_col_descend")
+    return kb.value, gens

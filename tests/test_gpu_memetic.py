@@ -149,3 +149,35 @@ def test_memetic_checkpoint_resume_and_determinism(ctx, learned):
         dlmcol.dlm_memetic_load(ctx, c, bad)
     for m in (a, b, c, other):
         m.close()
+
+
+def test_col_descend_matches_oracle_descent(ctx):
+    """k-COL with decreasing k: the GPU descent stops at the same k, after the same numbers of
+    generations, with the same legal colouring as a descent driven by the oracle generation by
+    generation (random GPX, integer work throughout)."""
+    n, k0, p, K, iters, seed, max_gens = 40, 6, 16, 4, 200, 5, 6
+    e, _ = inputs.planted(n, 4, 0.5, seed=seed)
+    adj = inputs.edges_to_adj(n, e)
+    g = device_graph(ctx, n, e)
+    prm = dlmcol.MemeticParams(k=k0, p=p, K=K, iters=iters, tenure=dlmcol.COL_TENURE, use_scorer=0, epochs=0,
+                               batch=100, lr=1e-3, seed=seed)
+    best = torch.zeros(n, dtype=torch.int16, device="cuda")
+    kb, gens = dlmcol.dlm_col_descend(ctx, g, prm, max_gens, best)
+    ref_k, ref_col = -1, None
+    for k in range(k0, 1, -1):
+        st = oracle.MemeticState(adj, k, p, K, seed=seed, iters=iters, use_scorer=0)
+        solved, ran = False, 0
+        for _ in range(max_gens):
+            st.generation()
+            ran += 1
+            if st.best_f[0] == 0:
+                solved = True
+                break
+        assert gens[k] == ran, k
+        if not solved:
+            break
+        ref_k, ref_col = k, st.best_col.copy()
+    assert kb == ref_k and kb >= 2
+    b = best.cpu().numpy()
+    assert np.array_equal(b, ref_col)
+    assert int(np.sum(b[e[:, 0]] == b[e[:, 1]])) == 0 and int(b.max()) < kb
