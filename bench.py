@@ -261,6 +261,7 @@ def run_memetic(args):
                                        use_scorer=1 if mode == "learned" else 0, epochs=5, batch=100, lr=1e-3,
                                        seed=1000 + seed)
             mm = dlmcol.Memetic(ctx, g, prm)
+            dlmcol.dlm_memetic_profile(ctx, mm, True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             traj, hit = [], None
@@ -273,8 +274,11 @@ def run_memetic(args):
                     break
                 if el > args.mem_time_limit:
                     break
+            stages = dlmcol.dlm_memetic_profile(ctx, mm, False)
             runs[mode].append({"seed": 1000 + seed, "time_to_target_s": hit, "generations": len(traj),
-                               "best": traj[-1][1], "trajectory": traj})
+                               "best": traj[-1][1], "trajectory": traj,
+                               "stage_ms_per_generation": {key: round(v, 2) for key, v in stages.items()
+                                                           if key != "generations"}})
             print(json.dumps({"progress": mode, **runs[mode][-1]}), file=sys.stderr, flush=True)
             mm.close()
 

@@ -283,6 +283,15 @@ dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, void* d
 /* Overwrites the population state (which = 0..3 as above) from device memory src. */
 dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const void* src);
 
+/* Measurement utility (no counterpart in the paper): while enabled, dlm_memetic_step records CUDA
+ * events at its stage boundaries (and waits for its last one). dlm_memetic_profile returns in
+ * stage_ms (host [8] double, or NULL) the mean ms per generation since the previous call of:
+ * 0 tabu search, 1 best so far, 2 distances, 3 pool update and gathers, 4 matching, 5 offspring
+ * (GPX, and scoring and selection with the scorer), 6 scorer training (on its side stream,
+ * overlapping 2-4), and 7 the number of generations averaged; then clears them and sets the
+ * recording state to enable. */
+dlm_status dlm_memetic_profile(dlm_ctx* ctx, dlm_memetic* mm, int32_t enable, double* stage_ms);
+
 /* The vertex colouring problem (section "Adaptations of the algorithm for the vertex coloring
  * problem"): k-COL with decreasing k. Starting at k = prm->k, a memetic search (fresh random
  * population, parameters prm with that k) runs up to max_gens generations; when it reaches a

@@ -25,6 +25,12 @@ struct dlm_memetic {
   // the scorer trains on a side stream while the distances and the pool update run
   cudaStream_t side = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_trained = nullptr;
+  // optional stage timing (dlm_memetic_profile): events at the stage boundaries of the main
+  // stream (tabu, best-so-far, distances, pool update, matching, offspring) and around training
+  bool prof = false;
+  cudaEvent_t pev[8] = {}, tev[2] = {};
+  double stage_ms[7] = {};
+  int64_t prof_gens = 0;
 };
 
 namespace dlm {
@@ -153,6 +159,8 @@ extern "C" void dlm_memetic_destroy(dlm_memetic* mm) {
   cudaFree(mm->cid); cudaFree(mm->scores);
   if (mm->h_best) cudaFreeHost(mm->h_best);
   if (mm->scorer) dlm_scorer_destroy(mm->scorer);
+  for (auto e : mm->pev) if (e) cudaEventDestroy(e);
+  for (auto e : mm->tev) if (e) cudaEventDestroy(e);
   if (mm->ev_ready) cudaEventDestroy(mm->ev_ready);
   if (mm->ev_trained) cudaEventDestroy(mm->ev_trained);
   if (mm->side) cudaStreamDestroy(mm->side);
@@ -216,19 +224,25 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
   const int p = q.p, K = q.K, n = mm->n, k = q.k, m = 2 * p;
   const size_t pn = (size_t)p * n;
   cudaStream_t s = ctx->stream;
+  auto mark = [&](int i) { if (mm->prof) cudaEventRecord(mm->pev[i], s); };
+  mark(0);
   // 1. local search of every offspring: S'_i <- TabuCol(S^O_i)
   DLM_CUDA(ctx, cudaMemcpyAsync(mm->Sp, mm->SO, pn * 2, cudaMemcpyDeviceToDevice, s));
   DLM_TRY(dlm_tabucol_batch(ctx, mm->g, k, p, mm->Sp, mm->fSp, mm->moves, q.iters, q.tenure, q.seed, mm->gen, 0u));
+  mark(1);
   // 2. best so far
   k_best_of<<<1, 1024, 0, s>>>(p, n, mm->fSp, mm->Sp, mm->best_f, mm->best_col);
   DLM_TRY(launch_check(ctx, "k_best_of"));
+  mark(2);
   // 3. training on {(S^O_i, f(S'_i))}, on the side stream: it only reads S^O and f(S'), which
   //    nothing below writes before the scoring, and the scoring waits for it
   if (q.use_scorer) {
     DLM_CUDA(ctx, cudaEventRecord(mm->ev_ready, s));
     DLM_CUDA(ctx, cudaStreamWaitEvent(mm->side, mm->ev_ready, 0));
     ctx->stream = mm->side;
+    if (mm->prof) cudaEventRecord(mm->tev[0], mm->side);
     const dlm_status ts = dlm_scorer_train(ctx, mm->scorer, mm->SO, mm->fSp, p, q.epochs, q.batch, q.lr, q.seed, mm->gen);
+    if (mm->prof) cudaEventRecord(mm->tev[1], mm->side);
     ctx->stream = s;
     DLM_TRY(ts);
     DLM_CUDA(ctx, cudaEventRecord(mm->ev_trained, mm->side));
@@ -241,6 +255,7 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     k_dall_assemble<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p, mm->DP, mm->Dall);
     DLM_TRY(launch_check(ctx, "k_dall_assemble"));
   }
+  mark(3);
   // 5. pool update over P u P'
   k_fit_all<<<(p + 255) / 256, 256, 0, s>>>(p, mm->fP, mm->fSp, mm->fall);
   DLM_TRY(launch_check(ctx, "k_fit_all"));
@@ -251,8 +266,10 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
   DLM_TRY(launch_check(ctx, "k_gather_dist"));
   std::swap(mm->P, mm->Pn);
   std::swap(mm->fP, mm->fPn);
+  mark(4);
   // 6. parent matching
   DLM_TRY(dlm_knn(ctx, p, mm->DP, K, mm->nbr));
+  mark(5);
   // 7. offspring
   if (q.use_scorer) {
     k_pairs_all<<<(p * K + 255) / 256, 256, 0, s>>>(p, K, mm->nbr, mm->pairs, mm->cid);
@@ -266,6 +283,17 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     k_pairs_random<<<(p + 255) / 256, 256, 0, s>>>(p, K, mm->nbr, q.seed, mm->gen, mm->pairs, mm->cid, mm->pick);
     DLM_TRY(launch_check(ctx, "k_pairs_random"));
     DLM_TRY(dlm_gpx_batch(ctx, n, k, mm->P, p, mm->pairs, mm->cid, p, mm->SO, q.seed, mm->gen));
+  }
+  mark(6);
+  if (mm->prof) {
+    DLM_CUDA(ctx, cudaEventSynchronize(mm->pev[6]));
+    for (int i = 0; i < 6; ++i) {
+      float e = 0.f;
+      if (cudaEventElapsedTime(&e, mm->pev[i], mm->pev[i + 1]) == cudaSuccess) mm->stage_ms[i] += e;
+    }
+    float e = 0.f;
+    if (q.use_scorer && cudaEventElapsedTime(&e, mm->tev[0], mm->tev[1]) == cudaSuccess) mm->stage_ms[6] += e;
+    ++mm->prof_gens;
   }
   mm->gen++;
   if (best_f_host) {
@@ -433,5 +461,21 @@ extern "C" dlm_status dlm_col_descend(dlm_ctx* ctx, const dlm_graph* g, const dl
     if (!solved) break;
     *k_best = k;
   }
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_memetic_profile(dlm_ctx* ctx, dlm_memetic* mm, int32_t enable, double* stage_ms) {
+  if (!ctx || !mm) return fail(ctx, DLM_EINVAL, "memetic_profile: null argument");
+  if (stage_ms) {
+    for (int i = 0; i < 7; ++i) stage_ms[i] = mm->prof_gens ? mm->stage_ms[i] / (double)mm->prof_gens : 0.0;
+    stage_ms[7] = (double)mm->prof_gens;
+  }
+  for (auto& x : mm->stage_ms) x = 0.0;
+  mm->prof_gens = 0;
+  if (enable && !mm->pev[0]) {
+    for (auto& e : mm->pev) DLM_CUDA(ctx, cudaEventCreate(&e));
+    for (auto& e : mm->tev) DLM_CUDA(ctx, cudaEventCreate(&e));
+  }
+  mm->prof = enable != 0;
   return DLM_OK;
 }

@@ -82,6 +82,7 @@ _SIGS = {
     "dlm_memetic_get": (_i32, [_P, _P, _i32, _P]),
     "dlm_memetic_set": (_i32, [_P, _P, _i32, _P]),
     "dlm_col_descend": (_i32, [_P, _P, _P, _i32, _P, _P, _P]),
+    "dlm_memetic_profile": (_i32, [_P, _P, _i32, _P]),
     "dlm_memetic_state_bytes": (_i64, [_P]),
     "dlm_memetic_save": (_i32, [_P, _P, _P]),
     "dlm_memetic_load": (_i32, [_P, _P, _P]),
@@ -476,3 +477,15 @@ def dlm_col_descend(ctx, g, params, max_gens, best_col):
     ctx.check(lib().dlm_col_descend(ctx.h, g.h, ctypes.byref(params), max_gens, ctypes.byref(kb), _ptr(best_col),
                                     _ptr(gens)), "dlm_col_descend")
     return kb.value, gens
+
+
+MEMETIC_STAGES = ("tabu", "best_of", "distances", "pool_update", "matching", "offspring", "training")
+
+
+def dlm_memetic_profile(ctx, mm, enable):
+    """Mean ms per generation of each stage since the last call (dict), then (re)sets recording."""
+    import numpy as np
+
+    out = np.zeros(8, np.float64)
+    ctx.check(lib().dlm_memetic_profile(ctx.h, mm.h, 1 if enable else 0, _ptr(out)), "dlm_memetic_profile")
+    return dict(zip(MEMETIC_STAGES, out[:7].tolist()), generations=int(out[7]))
