@@ -9,11 +9,19 @@ namespace dlm {
 
 // ------------------------------------------------------------------------------------------------
 // Distances. One CTA holds one row X_i in shared memory; each warp owns a k x k overlap table and
-// handles pairs (i, j). Per pair: count M[a][b] over the vertices (shared atomics), then row and
-// column maxima of the touched entries, then reset only the touched entries -- O(n) per pair.
+// handles pairs (i, j). Per pair: count M[a][b] over the vertices (shared atomics), then the row
+// and column maxima by scanning the table (lanes over rows and over columns, no atomics), then
+// clear it -- O(n + k^2) per pair.
 // ------------------------------------------------------------------------------------------------
 constexpr int kDistWarpsMax = 8;
 constexpr int kDistCols = 64;  // Y rows handled by one CTA
+
+// overlap-table row stride in 32-bit words: ceil(k / 2) rounded up to an odd number, so that the
+// lanes scanning different rows hit different banks
+__host__ __device__ inline int dist_row_words(int k) {
+  int r = (k + 1) / 2;
+  return (r & 1) ? r : r + 1;
+}
 
 __global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, const int16_t* X, int a, const int16_t* Y,
                                                               int b, int16_t* D, int64_t ldD, int upper,
@@ -22,56 +30,52 @@ __global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, c
   const int i = blockIdx.y;
   const int j0 = blockIdx.x * kDistCols;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* xi = smem;                                    // [n]
+  uint8_t* xi = smem;  // [n]
   const size_t xoff = (n + 15) & ~15;
-  // per warp: k*k u16 counters (padded to a word boundary), then k + k u32 maxima
-  const size_t kk2 = (size_t)((k * k + 1) & ~1);
-  uint16_t* M = (uint16_t*)((uint8_t*)smem + xoff + (size_t)warp * (kk2 * 2 + (size_t)k * 8));
-  uint32_t* rmax = (uint32_t*)(M + kk2);
-  uint32_t* cmax = rmax + k;
+  // per warp: the k x k overlap table, u16 counters, rows rw words apart
+  const int rw = dist_row_words(k);
+  uint32_t* M32 = (uint32_t*)((uint8_t*)smem + xoff + (size_t)warp * k * rw * 4);
+  const uint16_t* M16 = (const uint16_t*)M32;
   for (int v = threadIdx.x; v < n; v += blockDim.x) {
     int c = X[(size_t)i * n + v];
     if (c < 0 || c >= k) { raise_status(status, DLM_EINVAL); c = 0; }
     xi[v] = (uint8_t)c;
   }
-  for (int q = lane; q < (int)kk2; q += 32) M[q] = 0;
-  for (int q = lane; q < 2 * k; q += 32) rmax[q] = 0u;
+  for (int q = lane; q < k * rw; q += 32) M32[q] = 0u;
   __syncthreads();
-  uint32_t* M32 = (uint32_t*)M;  // 16-bit counters updated through their 32-bit word
   const int nwarps = blockDim.x >> 5;
   for (int jj = warp; jj < kDistCols; jj += nwarps) {
     const int j = j0 + jj;
     if (j >= b) break;
     if (upper && j <= i) continue;
     const int16_t* y = Y + (size_t)j * n;
+    // counts of every (class of x_i, class of y_j) pair
     for (int v = lane; v < n; v += 32) {
       int c2 = y[v];
       if (c2 < 0 || c2 >= k) { raise_status(status, DLM_EINVAL); c2 = 0; }
-      const int q = xi[v] * k + c2;
+      const int q = xi[v] * 2 * rw + c2;  // u16 index
       atomicAdd(M32 + (q >> 1), 1u << (16 * (q & 1)));
     }
     __syncwarp();
-    for (int v = lane; v < n; v += 32) {
-      int c2 = y[v];
-      c2 = (c2 < 0 || c2 >= k) ? 0 : c2;
-      const int c1 = xi[v];
-      const unsigned cnt = M[c1 * k + c2];
-      atomicMax(rmax + c1, cnt);
-      atomicMax(cmax + c2, cnt);
-    }
-    __syncwarp();
+    // row maxima (lanes over rows, words along the row) and column maxima (lanes over columns)
     int sr = 0, scl = 0;
-    for (int c = lane; c < k; c += 32) { sr += (int)rmax[c]; scl += (int)cmax[c]; }
+    for (int c = lane; c < k; c += 32) {
+      const uint32_t* row = M32 + (size_t)c * rw;
+      unsigned m = 0;
+      for (int w = 0; w < rw; ++w) {
+        const uint32_t x = row[w];
+        m = max(m, max(x & 0xFFFFu, x >> 16));
+      }
+      sr += (int)m;
+      unsigned mc = 0;
+      for (int r = 0; r < k; ++r) mc = max(mc, (unsigned)M16[(size_t)r * 2 * rw + c]);
+      scl += (int)mc;
+    }
     sr = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)sr);
     scl = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)scl);
     if (lane == 0) D[(size_t)i * ldD + j] = (int16_t)(n - (sr < scl ? sr : scl));
     __syncwarp();
-    for (int v = lane; v < n; v += 32) {
-      int c2 = y[v];
-      c2 = (c2 < 0 || c2 >= k) ? 0 : c2;
-      M[xi[v] * k + c2] = 0;
-    }
-    for (int c = lane; c < k; c += 32) { rmax[c] = 0u; cmax[c] = 0u; }
+    for (int q = lane; q < k * rw; q += 32) M32[q] = 0u;
     __syncwarp();
   }
 }
@@ -191,7 +195,7 @@ extern "C" dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, con
   if (!X || !Y || !D) return fail(ctx, DLM_EINVAL, "distance: null pointer");
   if (a > 65535) return fail(ctx, DLM_EUNSUPPORTED, "distance: at most 65535 rows");
   // as many warps (overlap tables) as shared memory allows, up to 8
-  const size_t per_warp = (size_t)((k * k + 1) & ~1) * 2 + (size_t)k * 8;
+  const size_t per_warp = (size_t)k * dist_row_words(k) * 4;
   const size_t head = ((n + 15) & ~15) + 16;
   int warps = kDistWarpsMax;
   while (warps > 1 && head + warps * per_warp > ctx->smem_optin) --warps;
