@@ -288,51 +288,53 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
   int it = 0;
   int64_t work_rows = 0, work_deg = 0, work_resum = 0;  // kept by thread 0 only
 
+  // ---- (A) selection from the summaries of this thread's conflicting vertices: per-vertex
+  // (delta, count) in vres, the thread's minimum and tie count, the warp's in red. Every input was
+  // written by this thread's own warp or before the last barrier, so the next iteration's
+  // selection runs straight after the update, without a barrier of its own.
+  int tmin = INT_MAX, tcnt = 0;
+  auto select = [&]() {
+    int nconf = 0;
+    tmin = INT_MAX;
+    tcnt = 0;
+    const int thrb = best_f - f;  // a tabu move is aspirated when gamma < thrb + gamma[v][col v]
+    for (int v = v0; v < v1; ++v) {
+      const int g0 = grow_of(v)[colS[v]];
+      uint32_t res = 0u;
+      if (g0 > 0) {
+        ++nconf;
+        const Summ s = summ[v];
+        const unsigned nt = s.ntcnt ? s.ntmin : kNoKey;
+        const unsigned ta = (s.tcnt && (int)s.tmin < thrb + g0) ? s.tmin : kNoKey;
+        const unsigned adm = min(nt, ta);
+        if (adm != kNoKey) {
+          const int c = (nt == adm ? s.ntcnt : 0) + (ta == adm ? s.tcnt : 0);
+          const int d = (int)adm - g0;
+          res = ((uint32_t)(d + 32768) << 16) | (uint32_t)c;
+          if (d < tmin) { tmin = d; tcnt = c; }
+          else if (d == tmin) tcnt += c;
+        }
+      }
+      vres[v] = res;
+    }
+    const int wm = __reduce_min_sync(FULL, tmin);
+    const int wc = (int)__reduce_add_sync(FULL, (wm != INT_MAX && tmin == wm) ? (unsigned)tcnt : 0u);
+    const int wn = (int)__reduce_add_sync(FULL, (unsigned)nconf);
+    if (lane == 0) { red[warp] = wm; red[W + warp] = wc; red[2 * W + warp] = wn; }
+  };
+  select();
   for (it = 0; it < iters; ++it) {
     if (f == 0) break;
     const unsigned itrel = (unsigned)(it & 0x3FFF);
-    // ---- (A) selection from the summaries of this thread's conflicting vertices --------------
-    int tmin = INT_MAX, tcnt = 0, nconf = 0;
-    {
-      const int thrb = best_f - f;  // a tabu move is aspirated when gamma < thrb + gamma[v][col v]
-      for (int v = v0; v < v1; ++v) {
-        const int g0 = grow_of(v)[colS[v]];
-        uint32_t res = 0u;
-        if (g0 > 0) {
-          ++nconf;
-          const Summ s = summ[v];
-          const unsigned nt = s.ntcnt ? s.ntmin : kNoKey;
-          const unsigned ta = (s.tcnt && (int)s.tmin < thrb + g0) ? s.tmin : kNoKey;
-          const unsigned adm = min(nt, ta);
-          if (adm != kNoKey) {
-            const int c = (nt == adm ? s.ntcnt : 0) + (ta == adm ? s.tcnt : 0);
-            const int d = (int)adm - g0;
-            res = ((uint32_t)(d + 32768) << 16) | (uint32_t)c;
-            if (d < tmin) { tmin = d; tcnt = c; }
-            else if (d == tmin) tcnt += c;
-          }
-        }
-        vres[v] = res;
-      }
-    }
-    if (tid == 0) {
-      sc[0] = -1;
-      // cancellation, polled every 1024 iterations: the search stops after this iteration's
-      // selection and reports its best colouring so far
-      if ((it & 1023) == 0 && R.cancel && *(volatile const int32_t*)R.cancel != 0) sc[5] = 3;
-    }
-    {
-      const int wm = __reduce_min_sync(FULL, tmin);
-      const int wc = (int)__reduce_add_sync(FULL, (wm != INT_MAX && tmin == wm) ? (unsigned)tcnt : 0u);
-      const int wn = (int)__reduce_add_sync(FULL, (unsigned)nconf);
-      if (lane == 0) { red[warp] = wm; red[W + warp] = wc; red[2 * W + warp] = wn; }
-    }
     __syncthreads();
     // ---- (B) minimum delta, tie ranks, move -------------------------------------------------
     if (tid == 0) {
       int nc = 0;
       for (int w = 0; w < W; ++w) nc += red[2 * W + w];
       work_rows += nc;
+      // cancellation, polled every 1024 iterations: the search stops after this iteration's
+      // selection and reports its best colouring so far
+      if ((it & 1023) == 0 && R.cancel && *(volatile const int32_t*)R.cancel != 0) sc[5] = 3;
     }
     // lanes 0..W-1 hold the warps' minima and tie totals
     const int lw = lane < W ? red[lane] : INT_MAX;
@@ -428,7 +430,10 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
         }
       }
     }
-    if (T == 0 && tid == 0 && J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(-1, -1, 0, 0);
+    if (T == 0 && tid == 0) {
+      sc[0] = -1;  // no admissible move: the iteration counts, nothing changes
+      if (J.trace) reinterpret_cast<int4*>(J.trace)[it] = make_int4(-1, -1, 0, 0);
+    }
     __syncthreads();
     if (sc[5]) break;
     // ---- (C) gamma and summaries of the moved vertex's neighbours ------------------------------
@@ -501,7 +506,8 @@ __device__ void tabucol_individual(const TabuJob& J, const TabuRule& R, uint8_t*
         }
       }
     }
-    __syncthreads();
+    __syncwarp();
+    select();  // the next iteration's selection
   }
   {  // rows summarised again, summed over the warps
     if (lane == 0) red[warp] = (int32_t)work_resum;
