@@ -63,11 +63,12 @@ def parse():
     ap.add_argument("--pop", type=int, default=POP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp", "wvcp_iterated", "scorer"],
+    ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp", "wvcp_iterated", "scorer", "popsweep"],
                     help="tabu: the headline moves/s step; memetic: learned vs random GPX time-to-target; "
                          "multi: the uneven 64-graph batch in one captured persistent launch; wvcp: the "
                          "weighted tabu search; wvcp_iterated: its iterated form with the adaptive penalty "
-                         "(Algorithm 2); scorer: one generation's scoring and training on the tensor cores")
+                         "(Algorithm 2); scorer: one generation's scoring and training on the tensor cores; "
+                         "popsweep: best conflicts against population size at a fixed tabu budget")
     ap.add_argument("--multi-pop", type=int, default=256)
     ap.add_argument("--multi-depth", type=int, default=128, help="tabu iterations per individual = depth * n")
     ap.add_argument("--mem-n", type=int, default=1000)
@@ -493,6 +494,48 @@ def run_wvcp_iterated(args):
     print(json.dumps(out), flush=True)
 
 
+def run_popsweep(args):
+    """Sensitivity to the population size (section "Sensitivity to the population size", on k-COL
+    here): G(500, 0.5), k = 47, random-GPX memetic search, the same total tabu budget (8192 x 4
+    generations x 5000 iterations) for every population size; the line reports the best conflicts
+    reached and the wall time per size."""
+    import torch
+
+    from paper_2109_05948_gb300 import build as libbuild
+    from paper_2109_05948_gb300 import dlmcol, inputs
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    ctx = dlmcol.Context(0)
+    n, k, iters = 500, 47, 5000
+    budget = 8192 * 4 * iters
+    e = inputs.gnp(n, 0.5, SEED)
+    g = dlmcol.Graph(ctx, n, torch.from_numpy(e).cuda())
+    res = []
+    for p in (128, 512, 2048, 8192):
+        gens = max(1, budget // (p * iters))
+        prm = dlmcol.MemeticParams(k=k, p=p, K=min(16, p - 1), iters=iters, tenure=dlmcol.COL_TENURE, use_scorer=0,
+                                   epochs=0, batch=100, lr=1e-3, seed=2000 + p)
+        mm = dlmcol.Memetic(ctx, g, prm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best = None
+        for _ in range(gens):
+            best = dlmcol.dlm_memetic_step(ctx, mm)
+            if best == 0:
+                break
+        res.append({"population": p, "generations": gens, "best_conflicts": int(best),
+                    "seconds": round(time.perf_counter() - t0, 3)})
+        print(json.dumps({"progress": res[-1]}), file=sys.stderr, flush=True)
+        mm.close()
+    out = {"metric": "best conflicts at a fixed tabu budget vs population size, G(500, 0.5), k = 47",
+           "workload": "popsweep", "value": min(r["best_conflicts"] for r in res), "unit": "conflicts",
+           "higher_is_better": False, "data": "synthetic", "runs": res,
+           "config": {"workload": f"G(500, 0.5), k = {k}, random GPX, K = 16, {iters} tabu iterations per generation, "
+                                  f"total tabu budget {budget} iterations per population size"}}
+    print(json.dumps(out), flush=True)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -617,6 +660,9 @@ def main():
         return
     if args.workload == "wvcp_iterated":
         run_wvcp_iterated(args)
+        return
+    if args.workload == "popsweep":
+        run_popsweep(args)
         return
     import torch
     import torch.distributed as dist
