@@ -631,8 +631,7 @@ static int default_warps(int n, int k) {
   (void)k;
   if (n <= 128) return 2;
   if (n <= 300) return 4;
-  if (n <= 600) return 8;
-  return 16;  // one CTA per SM for these states: more warps shorten each phase
+  return 16;  // each thread owns at most ceil(n / 512) vertices: short phases between the barriers
 }
 
 static dlm_status tabucol_check(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,
