@@ -23,9 +23,12 @@ __host__ __device__ inline int dist_row_words(int k) {
   return (r & 1) ? r : r + 1;
 }
 
+// one warp's table in words, rounded up to 16 bytes
+__host__ __device__ inline int dist_table_words(int k) { return (k * dist_row_words(k) + 3) & ~3; }
+
 __global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, const int16_t* X, int a, const int16_t* Y,
                                                               int b, int16_t* D, int64_t ldD, int upper,
-                                                              int32_t* status) {
+                                                              int vec4, int32_t* status) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int i = blockIdx.y;
   const int j0 = blockIdx.x * kDistCols;
@@ -34,14 +37,13 @@ __global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, c
   const size_t xoff = (n + 15) & ~15;
   // per warp: the k x k overlap table, u16 counters, rows rw words apart
   const int rw = dist_row_words(k);
-  uint32_t* M32 = (uint32_t*)((uint8_t*)smem + xoff + (size_t)warp * k * rw * 4);
-  const uint16_t* M16 = (const uint16_t*)M32;
+  uint32_t* M32 = (uint32_t*)((uint8_t*)smem + xoff + (size_t)warp * dist_table_words(k) * 4);
   for (int v = threadIdx.x; v < n; v += blockDim.x) {
     int c = X[(size_t)i * n + v];
     if (c < 0 || c >= k) { raise_status(status, DLM_EINVAL); c = 0; }
     xi[v] = (uint8_t)c;
   }
-  for (int q = lane; q < k * rw; q += 32) M32[q] = 0u;
+  for (int q = lane; q < dist_table_words(k); q += 32) M32[q] = 0u;
   __syncthreads();
   const int nwarps = blockDim.x >> 5;
   for (int jj = warp; jj < kDistCols; jj += nwarps) {
@@ -49,15 +51,30 @@ __global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, c
     if (j >= b) break;
     if (upper && j <= i) continue;
     const int16_t* y = Y + (size_t)j * n;
-    // counts of every (class of x_i, class of y_j) pair
-    for (int v = lane; v < n; v += 32) {
-      int c2 = y[v];
-      if (c2 < 0 || c2 >= k) { raise_status(status, DLM_EINVAL); c2 = 0; }
+    // counts of every (class of x_i, class of y_j) pair; the partner's colours are checked by the
+    // CTAs of row 0 (which see every partner) and clamped everywhere
+    const bool check = blockIdx.y == 0;
+    auto count1 = [&](int v, int c2) {
+      if (check && (c2 < 0 || c2 >= k)) raise_status(status, DLM_EINVAL);
+      c2 = (int)min((unsigned)c2, (unsigned)(k - 1));
       const int q = xi[v] * 2 * rw + c2;  // u16 index
       atomicAdd(M32 + (q >> 1), 1u << (16 * (q & 1)));
+    };
+    if (vec4) {  // four vertices per lane step: 8-byte colour loads (n % 4 == 0, Y 8-byte aligned)
+      const uint2* y4 = reinterpret_cast<const uint2*>(y);
+      for (int t = lane; t < (n >> 2); t += 32) {
+        const uint2 yy = y4[t];
+        const int v = 4 * t;
+        count1(v, (int16_t)(yy.x & 0xFFFFu));
+        count1(v + 1, (int16_t)(yy.x >> 16));
+        count1(v + 2, (int16_t)(yy.y & 0xFFFFu));
+        count1(v + 3, (int16_t)(yy.y >> 16));
+      }
+    } else {
+      for (int v = lane; v < n; v += 32) count1(v, y[v]);
     }
     __syncwarp();
-    // row maxima (lanes over rows, words along the row) and column maxima (lanes over columns)
+    // row maxima (lanes over rows, words along the row) and column maxima (lanes over column pairs)
     int sr = 0, scl = 0;
     for (int c = lane; c < k; c += 32) {
       const uint32_t* row = M32 + (size_t)c * rw;
@@ -67,15 +84,24 @@ __global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, c
         m = max(m, max(x & 0xFFFFu, x >> 16));
       }
       sr += (int)m;
-      unsigned mc = 0;
-      for (int r = 0; r < k; ++r) mc = max(mc, (unsigned)M16[(size_t)r * 2 * rw + c]);
-      scl += (int)mc;
+    }
+    for (int cw = lane; cw < (k + 1) / 2; cw += 32) {
+      unsigned m0 = 0, m1 = 0;
+      for (int r = 0; r < k; ++r) {
+        const uint32_t x = M32[(size_t)r * rw + cw];
+        m0 = max(m0, x & 0xFFFFu);
+        m1 = max(m1, x >> 16);
+      }
+      scl += (int)(m0 + m1);  // the padding column of an odd k is all zero
     }
     sr = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)sr);
     scl = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)scl);
     if (lane == 0) D[(size_t)i * ldD + j] = (int16_t)(n - (sr < scl ? sr : scl));
     __syncwarp();
-    for (int q = lane; q < k * rw; q += 32) M32[q] = 0u;
+    {  // clear the table, 16 bytes per store (its size is rounded up to 16 bytes)
+      uint4* M4 = reinterpret_cast<uint4*>(M32);
+      for (int q = lane; q < dist_table_words(k) >> 2; q += 32) M4[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
     __syncwarp();
   }
 }
@@ -195,7 +221,7 @@ extern "C" dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, con
   if (!X || !Y || !D) return fail(ctx, DLM_EINVAL, "distance: null pointer");
   if (a > 65535) return fail(ctx, DLM_EUNSUPPORTED, "distance: at most 65535 rows");
   // as many warps (overlap tables) as shared memory allows, up to 8
-  const size_t per_warp = (size_t)k * dist_row_words(k) * 4;
+  const size_t per_warp = (size_t)dist_table_words(k) * 4;
   const size_t head = ((n + 15) & ~15) + 16;
   int warps = kDistWarpsMax;
   while (warps > 1 && head + warps * per_warp > ctx->smem_optin) --warps;
@@ -203,7 +229,8 @@ extern "C" dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, con
   if (smem > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "distance: shared memory");
   DLM_CUDA(ctx, cudaFuncSetAttribute(k_distance, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((b + kDistCols - 1) / kDistCols, a);
-  k_distance<<<grid, 32 * warps, smem, ctx->stream>>>(n, k, X, a, Y, b, D, ldD, upper, ctx->d_status);
+  const int vec4 = (n % 4 == 0) && (((uintptr_t)Y & 7) == 0);
+  k_distance<<<grid, 32 * warps, smem, ctx->stream>>>(n, k, X, a, Y, b, D, ldD, upper, vec4, ctx->d_status);
   return launch_check(ctx, "k_distance");
 }
 
