@@ -15,6 +15,10 @@ Other workloads (one JSON line each, single GPU):
   --workload multi    the uneven 64-graph batch in one persistent launch replayed from a CUDA graph
   --workload wvcp     the weighted feasible/infeasible tabu search, G(1000, 0.5), weights 1..100
   --workload scorer   one learned generation's scoring and training with the tensor-core roofline
+  --workload wvcp_iterated  Algorithm 2 (iterated weighted search with the adaptive penalty)
+  --workload popsweep best conflicts against population size at a fixed tabu budget
+  --workload population  distances, pool update, K nearest neighbours and GPX of one generation,
+                         each kernel against its roofline
 """
 from __future__ import annotations
 
@@ -63,12 +67,14 @@ def parse():
     ap.add_argument("--pop", type=int, default=POP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp", "wvcp_iterated", "scorer", "popsweep"],
+    ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp", "wvcp_iterated", "scorer", "popsweep",
+                                                   "population"],
                     help="tabu: the headline moves/s step; memetic: learned vs random GPX time-to-target; "
                          "multi: the uneven 64-graph batch in one captured persistent launch; wvcp: the "
                          "weighted tabu search; wvcp_iterated: its iterated form with the adaptive penalty "
                          "(Algorithm 2); scorer: one generation's scoring and training on the tensor cores; "
-                         "popsweep: best conflicts against population size at a fixed tabu budget")
+                         "popsweep: best conflicts against population size at a fixed tabu budget; population: "
+                         "distances, pool update, K nearest neighbours and GPX of one generation")
     ap.add_argument("--multi-pop", type=int, default=256)
     ap.add_argument("--multi-depth", type=int, default=128, help="tabu iterations per individual = depth * n")
     ap.add_argument("--mem-n", type=int, default=1000)
@@ -420,12 +426,20 @@ def run_wvcp(args):
     ms = e0.elapsed_time(e1)
     legal = fc[:, 1] == 0
     best_legal = int(fc[legal, 0].min()) if bool(legal.any()) else None
-    # algorithmic work per iteration: every (v, c) pair reads one gamma entry (2 B)
+    # algorithmic work per iteration: every (v, c) pair reads one gamma entry (2 B); iterations
+    # are counted by their moves (an iteration without an admissible move is not counted)
     pairs = n * (k - 1)
+    smem_gbps = dlmcol.dlm_probe_smem_bandwidth(ctx)
+    ach = 2.0 * pairs * moves / (ms / 1e3) / 1e9
+    roof = {"bound": "smem", "achieved": ach, "peak": smem_gbps, "unit": "GB/s", "frac": ach / smem_gbps,
+            "traffic": None, "kernel": "k_wvcp_tabu", "kernel_ms": ms / args.steps,
+            "algorithmic_bytes_per_launch": 2.0 * pairs * moves / args.steps,
+            "peak_source": "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads); the "
+                           "conflict table's last colours live in an L2-resident slab"}
     out = {"metric": "weighted tabu moves/s, G(1000, 0.5), weights 1..100", "workload": "wvcp",
            "value": moves / (ms / 1e3), "unit": "moves/s", "higher_is_better": True, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "gpu_launches": args.steps, "clocks": ck,
-           "pair_evaluations_per_s": moves / (ms / 1e3) * pairs, "data": "synthetic",
+           "pair_evaluations_per_s": moves / (ms / 1e3) * pairs, "data": "synthetic", "roofline": roof,
            "config": {"workload": f"G(1000, 0.5), weights 1..100, population {pop}, k = {k} (greedy), "
                                   f"{iters} iterations, phi = {phi}", "k": k, "phi": phi,
                       "best_legal_f": best_legal, "legal_individuals": int(legal.sum())}}
@@ -542,6 +556,149 @@ def measured_peaks():
             return json.load(fh)
     except (OSError, ValueError):
         return {}
+
+
+def run_population(args):
+    """Population management and crossover of one generation at the planted n = 1000, k = 48,
+    p = 8192, K = 32 size (sections "Distance computation", "Population update", "Parent matching
+    and selection of crossovers"): distances P x P' and P' x P' (upper triangle), the pool update
+    over the 2p candidates, the K nearest neighbours of the new population and GPX for its p K
+    pairs. The colourings are TabuCol results (2 |V| iterations from random starts), so the
+    overlap tables look like those of a running search. Each kernel is timed with CUDA events on
+    the context's stream; value = distance pairs per second (the dominant kernel)."""
+    import numpy as np
+    import torch
+
+    from paper_2109_05948_gb300 import build as libbuild
+    from paper_2109_05948_gb300 import dlmcol, inputs
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    ctx = dlmcol.Context(0)
+    n, k, p, Kn, iters = 1000, 48, 8192, 32, 2000
+    m = 2 * p
+    dev = torch.device("cuda", 0)
+    e, _ = inputs.planted(n, k, 0.5, seed=0)
+    g = dlmcol.Graph(ctx, n, torch.from_numpy(e).to(dev))
+    allc = torch.empty((m, n), dtype=torch.int16, device=dev)  # P (rows < p) then P'
+    fit = torch.empty(m, dtype=torch.int64, device=dev)
+    dlmcol.dlm_init_colors(ctx, n, k, m, SEED, 0, allc)
+    dlmcol.dlm_tabucol_batch(ctx, g, k, m, allc, fit, None, iters, dlmcol.COL_TENURE, SEED, 0, 0)
+    P, Sp = allc[:p], allc[p:]
+    D = torch.zeros((m, m), dtype=torch.int16, device=dev)  # 512 MiB: larger than L2
+    dlmcol.dlm_distance_batch(ctx, n, k, P, p, P, p, D, m, 0)
+    sel = torch.empty(p, dtype=torch.int32, device=dev)
+    nbr = torch.empty((p, Kn), dtype=torch.int32, device=dev)
+    kids = torch.empty((p * Kn, n), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    names = ("distance_PxPp", "distance_PpxPp", "pool_update", "knn", "gpx")
+    tms = {nm: [] for nm in names}
+
+    def timed(name, fn, rec):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        if rec:
+            tms[name].append((a, b))
+
+    def step(rec):
+        timed("distance_PxPp", lambda: dlmcol.dlm_distance_batch(ctx, n, k, P, p, Sp, p, D[:, p:], m, 0), rec)
+        timed("distance_PpxPp", lambda: dlmcol.dlm_distance_batch(ctx, n, k, Sp, p, Sp, p, D[p:, p:], m, 1), rec)
+        # symmetric completion of the matrix (plumbing between the timed kernels)
+        D[p:, :p] = D[:p, p:].t()
+        lower = torch.tril(torch.ones((p, p), dtype=torch.bool, device=dev), -1)
+        blk = D[p:, p:]
+        blk[lower] = blk.t()[lower]
+        del lower
+        timed("pool_update", lambda: dlmcol.dlm_pool_update(ctx, p, n, fit, D, sel), rec)
+        idx = sel.long()
+        DP = D[idx][:, idx].contiguous()
+        Pn = allc[idx].contiguous()
+        timed("knn", lambda: dlmcol.dlm_knn(ctx, p, DP, Kn, nbr), rec)
+        pairs = torch.stack([torch.arange(p, device=dev, dtype=torch.int32).repeat_interleave(Kn),
+                             nbr.reshape(-1)], dim=1).contiguous()
+        timed("gpx", lambda: dlmcol.dlm_gpx_batch(ctx, n, k, Pn, p, pairs, None, p * Kn, kids, SEED, 1), rec)
+        return DP
+
+    for _ in range(args.warmup):
+        step(False)
+    ctx.sync()
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        DP = step(True)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ck = clocks.stop()
+    ms = {nm: sum(a.elapsed_time(b) for a, b in tms[nm]) / len(tms[nm]) for nm in names}
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    if hbm is None:
+        hbm, hbm_src = 6800.0, "of fallback"
+    smem = dlmcol.dlm_probe_smem_bandwidth(ctx)
+    smem_src = "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads)"
+    # examined candidates of the pool update and the admitted-list length each one is checked
+    # against (the entries of D it reads), reconstructed on the host from its inputs and output.
+    # sel lists the greedily admitted members in increasing (f, index) rank, then any fill; a fill
+    # member is within n / 10 of an earlier admitted one, so the greedy prefix ends at the first
+    # member that breaks the rank order or is close to an earlier member. The greedy pass examines
+    # candidates until p are admitted (all 2p when it falls short).
+    f_np, s_np = fit.cpu().numpy(), sel.cpu().numpy()
+    order = np.lexsort((np.arange(m), f_np))
+    rank = np.empty(m, np.int64)
+    rank[order] = np.arange(m)
+    r = rank[s_np]
+    close = (10 * DP.int() <= n) & torch.tril(torch.ones((p, p), dtype=torch.bool, device=dev), -1)
+    brk = close.any(dim=1).cpu().numpy()
+    brk[1:] |= np.diff(r) <= 0
+    g_len = int(np.argmax(brk)) if brk.any() else p
+    del close
+    admitted = np.zeros(m, bool)
+    admitted[s_np[:g_len]] = True
+    before = np.concatenate([[0], np.cumsum(admitted[order])[:-1]])
+    stop = int(np.searchsorted(before, p)) if g_len >= p else m
+    pool_entries = int(before[:stop].sum())
+
+    def roof(bound, alg_bytes, t_ms, peak, src):
+        a = alg_bytes / (t_ms / 1e3) / 1e9
+        return {"bound": bound, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "peak_source": src,
+                "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": t_ms}
+
+    pairs1, pairs2 = p * p, p * (p - 1) // 2
+    # distance: per pair, n overlap-counter increments (u16 read-modify-write, 4 B each) and two
+    # passes over the k x k u16 table (row maxima and column maxima, 4 k^2 B)
+    dist_b = 4 * n + 4 * k * k
+    kern = {
+        "distance_PxPp": {"units": pairs1, "unit": "pairs", **roof("smem", dist_b * pairs1, ms["distance_PxPp"], smem, smem_src)},
+        "distance_PpxPp": {"units": pairs2, "unit": "pairs", **roof("smem", dist_b * pairs2, ms["distance_PpxPp"], smem, smem_src)},
+        # pool update: 2 B of D per (examined candidate, admitted member) check, from HBM
+        "pool_update": {"units": stop, "unit": "candidates examined",
+                        **roof("hbm", 2 * pool_entries, ms["pool_update"], hbm, hbm_src)},
+        # KNN: every row of D (2 p B) read once, K int32 written
+        "knn": {"units": p, "unit": "rows", **roof("hbm", p * (2 * p + 4 * Kn), ms["knn"], hbm, hbm_src)},
+        # GPX: two parents (2 n B each) read and one child (2 n B) written
+        "gpx": {"units": p * Kn, "unit": "children", **roof("hbm", p * Kn * 6 * n, ms["gpx"], hbm, hbm_src)},
+    }
+    dist_ms = ms["distance_PxPp"] + ms["distance_PpxPp"]
+    top = dict(kern["distance_PxPp"])
+    top.update({"kernel": "k_distance (P x P' launch)", "traffic": None})
+    for v in kern.values():
+        v["units_per_s"] = v["units"] / (v["kernel_ms"] / 1e3)
+    out = {"metric": "population stage: distance pairs/s, n=1000, k=48, p=8192", "workload": "population",
+           "value": (pairs1 + pairs2) / (dist_ms / 1e3), "unit": "pairs/s", "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms.values()),
+           "dtype": "int16/int32", "data": "synthetic", "gpu_launches": 5 * args.steps, "clocks": ck,
+           "roofline": top, "kernels": kern,
+           "config": {"workload": f"planted 48-colourable n={n}, p={p} TabuCol results ({iters} iterations) as P and "
+                                  f"P', K={Kn}: distances P x P' and P' x P' (upper), pool update over {m} "
+                                  f"candidates, K nearest neighbours, GPX for {p * Kn} pairs",
+                      "l2": "the 512 MiB distance matrix exceeds L2", "smem_probe_gbps": smem}}
+    print(json.dumps(out), flush=True)
+    g.close()
+    ctx.close()
 
 
 def run_scorer(args):
@@ -664,6 +821,9 @@ def main():
     if args.workload == "popsweep":
         run_popsweep(args)
         return
+    if args.workload == "population":
+        run_population(args)
+        return
     import torch
     import torch.distributed as dist
 
@@ -739,19 +899,30 @@ def main():
         ms, tot_moves = reduce_over_ranks(dist, ms, tot_moves, dev)
     value = tot_moves / (ms / 1e3)
 
-    # algorithmic shared-memory bytes of the tabu kernel (per launch): every conflicting row
-    # evaluated reads its colour (1 B), gamma[v][col v] (2 B) and its summary (8 B) and writes its
-    # selection result (4 B); every neighbour of a moved vertex costs its colour (1 B), two u16
-    # gamma read-modify-writes (8 B), two u16 tabu reads (4 B) and its summary read and write
-    # (16 B); every re-summarised row reads its k gamma and k tabu entries (4k B) and its colour
-    # and writes its summary (9 B); every iteration reads the n summaries' expiry (2 B each)
-    alg_bytes = (15 * wk[0] + 29 * wk[1] + (4 * K + 9) * wk[2] + 2 * N * local_moves) / args.steps
+    # algorithmic bytes of one TabuCol iteration (the method's neighbourhood evaluation, whatever
+    # the kernel does to avoid it): each conflicting vertex's k - 1 moves read a gamma and a tabu
+    # entry (2 B + 2 B), each neighbour of the moved vertex has two u16 gamma read-modify-writes
+    # (8 B), and each move reads the moved vertex's adjacency bit row (ceil(n / 8) B). The
+    # conflicting rows and the degrees are counted by the kernel itself over the timed launches.
+    alg_bytes = (4 * (K - 1) * wk[0] + 8 * wk[1] + ((N + 7) // 8) * local_moves) / args.steps
+    # bytes the kernel itself moves in shared memory (it evaluates a conflicting row from an
+    # 8-byte summary instead of its k - 1 entries): every conflicting row evaluated reads its colour
+    # (1 B), gamma[v][col v] (2 B) and its summary (8 B) and writes its selection result (4 B);
+    # every neighbour of a moved vertex costs its colour (1 B), two u16 gamma read-modify-writes
+    # (8 B), two u16 tabu reads (4 B) and its summary read and write (16 B); every re-summarised
+    # row reads its k gamma and k tabu entries (4k B) and its colour and writes its summary (9 B);
+    # every iteration reads the n summaries' expiry (2 B each)
+    kern_bytes = (15 * wk[0] + 29 * wk[1] + (4 * K + 9) * wk[2] + 2 * N * local_moves) / args.steps
     kmean = sum(kms) / len(kms)
     achieved = alg_bytes / (kmean / 1e3) / 1e9
+    kern_gbps = kern_bytes / (kmean / 1e3) / 1e9
     roofline = {"bound": "smem", "achieved": achieved, "peak": smem_gbps, "unit": "GB/s",
                 "frac": achieved / smem_gbps, "traffic": None,
                 "kernel": "tabucol_batch_kernel", "kernel_ms": kmean,
+                "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads)",
+                "kernel_smem_bytes_per_launch": kern_bytes, "kernel_smem_gbps": kern_gbps,
+                "kernel_smem_frac": kern_gbps / smem_gbps,
                 "work": {"rows_evaluated_per_launch": wk[0] / args.steps,
                          "neighbour_updates_per_launch": wk[1] / args.steps,
                          "rows_resummarised_per_launch": wk[2] / args.steps}}
