@@ -672,15 +672,15 @@ def run_population(args):
     # passes over the k x k u16 table (row maxima and column maxima, 4 k^2 B)
     dist_b = 4 * n + 4 * k * k
     kern = {
-        "distance_PxPp": {"units": pairs1, "unit": "pairs", **roof("smem", dist_b * pairs1, ms["distance_PxPp"], smem, smem_src)},
-        "distance_PpxPp": {"units": pairs2, "unit": "pairs", **roof("smem", dist_b * pairs2, ms["distance_PpxPp"], smem, smem_src)},
+        "distance_PxPp": {"units": pairs1, "work_unit": "pairs", **roof("smem", dist_b * pairs1, ms["distance_PxPp"], smem, smem_src)},
+        "distance_PpxPp": {"units": pairs2, "work_unit": "pairs", **roof("smem", dist_b * pairs2, ms["distance_PpxPp"], smem, smem_src)},
         # pool update: 2 B of D per (examined candidate, admitted member) check, from HBM
-        "pool_update": {"units": stop, "unit": "candidates examined",
+        "pool_update": {"units": stop, "work_unit": "candidates examined",
                         **roof("hbm", 2 * pool_entries, ms["pool_update"], hbm, hbm_src)},
         # KNN: every row of D (2 p B) read once, K int32 written
-        "knn": {"units": p, "unit": "rows", **roof("hbm", p * (2 * p + 4 * Kn), ms["knn"], hbm, hbm_src)},
+        "knn": {"units": p, "work_unit": "rows", **roof("hbm", p * (2 * p + 4 * Kn), ms["knn"], hbm, hbm_src)},
         # GPX: two parents (2 n B each) read and one child (2 n B) written
-        "gpx": {"units": p * Kn, "unit": "children", **roof("hbm", p * Kn * 6 * n, ms["gpx"], hbm, hbm_src)},
+        "gpx": {"units": p * Kn, "work_unit": "children", **roof("hbm", p * Kn * 6 * n, ms["gpx"], hbm, hbm_src)},
     }
     dist_ms = ms["distance_PxPp"] + ms["distance_PpxPp"]
     top = dict(kern["distance_PxPp"])

@@ -124,7 +124,8 @@ dlm_status dlm_tabucol_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_
                              int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                              uint32_t generation, uint32_t ind_base);
 
-/* As dlm_tabucol_batch, with warps_per_individual forced (1, 2, 4, 8 or 16; 0 = autotuned), an
+/* As dlm_tabucol_batch, with warps_per_individual forced (1, 2, 4, 8, 16 or 32; 0 = autotuned or
+ * the library's default; a 32-warp CTA holds all of an SM's registers, so one runs per SM), an
  * optional per-iteration trace -- device [pop][iters][4] int32 of (v, c, delta, #tied moves),
  * (-1, -1, 0, 0) for an iteration without a move, entries after an early stop untouched -- and an
  * optional work count -- device [pop][3] int64: the number of conflicting rows evaluated, the sum
@@ -210,7 +211,13 @@ dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t*
  * the population, >= p: the improved individuals) are visited by increasing fit, ties by lower
  * index; a candidate is kept when its distance to every candidate kept so far is > n / 10; if
  * fewer than p are kept the best remaining ones (same order) fill the population.
- *   fit device [2p] int64;  D device [2p][2p] int16;  sel device [p] int32 out (in keep order). */
+ *   fit device [2p] int64 in 0..2^43 - 1 (else DLM_EINVAL at dlm_sync);
+ *   D   device [2p][2p] int16, 4-byte aligned (DLM_EINVAL otherwise), row x read in full;
+ *   sel device [p] int32 out (in keep order).
+ * The visit runs in blocks of 1024 candidates: every SM scans the block's rows of D against the
+ * members kept in earlier blocks, then one warp settles the block in order; the result is that of
+ * the one-at-a-time visit. Scratch (about 9 m + 130 KB bytes, m = 2p) comes from the context's
+ * workspace. Limits: p <= 8192 (the sort runs in one CTA's shared memory; DLM_EUNSUPPORTED). */
 dlm_status dlm_pool_update(dlm_ctx* ctx, int32_t p, int32_t n, const int64_t* fit, const int16_t* D, int32_t* sel);
 
 /* Parent matching (section "Parent matching ..."): the K nearest j != i of every i by D (device

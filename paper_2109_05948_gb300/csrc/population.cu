@@ -107,22 +107,57 @@ __global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, c
 }
 
 // ------------------------------------------------------------------------------------------------
-// Pool update: one CTA. Candidates are sorted by (f, index) with a shared-memory bitonic sort of
-// 64-bit keys; then the greedy pass admits a candidate when no admitted member is within n/10
-// (the check of the admitted list is split across the threads, one barrier per candidate).
+// Pool update. The greedy pass over the 2p candidates in (f, index) order admits a candidate when
+// no member admitted before it is within n/10. A candidate's fate depends only on the candidates
+// before it, so the pass runs in blocks of kPoolBlk candidates (in sorted order):
+//  (1) k_pool_sort (one CTA): shared-memory bitonic sort of the 64-bit keys (f << 20 | index),
+//      giving order[] and rank[] (the sorted position of every candidate);
+//  (2) k_pool_scan (all SMs, one warp per candidate row of the block): one coalesced pass over
+//      the candidate's row of D finds whether a member admitted in an earlier block is within
+//      n/10 (pre) and which earlier candidates of the same block are within n/10 (a kPoolBlk-bit
+//      row);
+//  (3) k_pool_resolve (one CTA): one warp walks the block in order with those bit rows in shared
+//      memory, admitting a candidate when pre is clear and no candidate admitted earlier in the
+//      block is marked; it stops once p members are admitted;
+//  (4) k_pool_fill (one CTA): when fewer than p were admitted, the best remaining candidates in
+//      sorted order fill the population.
+// The admitted members and their order are exactly those of the one-candidate-at-a-time pass.
 // ------------------------------------------------------------------------------------------------
 constexpr int kPoolThreads = 1024;
+constexpr int kPoolBlk = 1024;            // candidates resolved per block
+constexpr int kPoolWords = kPoolBlk / 32; // words of one in-block bit row
+constexpr int kPoolScanWarps = 8;
 
-__global__ void __launch_bounds__(kPoolThreads) k_pool_update(int p, int n, const int64_t* fit, const int16_t* D,
-                                                              int32_t* sel, int32_t* status) {
+struct PoolWs {
+  int32_t* cnt;        // [1] members admitted so far
+  int32_t* order;      // [m] candidate at each sorted position
+  int32_t* rank;       // [m] sorted position of each candidate
+  uint32_t* adm;       // [ceil(m / 32)] admitted-candidate bitmask
+  uint8_t* pre;        // [kPoolBlk] within n/10 of a member admitted in an earlier block
+  uint32_t* inblk;     // [kPoolBlk][kPoolWords] earlier candidates of the block within n/10
+};
+
+__host__ inline size_t pool_ws_layout(int m, PoolWs* w, uint8_t* base) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) { uint8_t* q = base ? base + o : nullptr; o += (bytes + 255) & ~(size_t)255; return q; };
+  uint8_t* c = take(16);
+  uint8_t* ord = take((size_t)m * 4);
+  uint8_t* rk = take((size_t)m * 4);
+  uint8_t* ad = take((size_t)((m + 31) / 32) * 4);
+  uint8_t* pr = take(kPoolBlk);
+  uint8_t* ib = take((size_t)kPoolBlk * kPoolWords * 4);
+  if (w) {
+    w->cnt = (int32_t*)c; w->order = (int32_t*)ord; w->rank = (int32_t*)rk; w->adm = (uint32_t*)ad;
+    w->pre = pr; w->inblk = (uint32_t*)ib;
+  }
+  return o;
+}
+
+__global__ void __launch_bounds__(kPoolThreads) k_pool_sort(int m, const int64_t* fit, PoolWs w, int32_t* status) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const int m = 2 * p;
   int mp = 1;
   while (mp < m) mp <<= 1;
-  uint64_t* key = (uint64_t*)smem;             // [mp]
-  int32_t* adm = (int32_t*)(key + mp);          // [p] admitted, in order
-  uint8_t* chosen = (uint8_t*)(adm + p);        // [m]
-  __shared__ int cnt;
+  uint64_t* key = (uint64_t*)smem;  // [mp]
   const int t = threadIdx.x;
   for (int q = t; q < mp; q += blockDim.x) {
     if (q < m) {
@@ -133,8 +168,8 @@ __global__ void __launch_bounds__(kPoolThreads) k_pool_update(int p, int n, cons
       key[q] = ~0ull;
     }
   }
-  for (int q = t; q < m; q += blockDim.x) chosen[q] = 0;
-  if (t == 0) cnt = 0;
+  for (int q = t; q < (m + 31) / 32; q += blockDim.x) w.adm[q] = 0u;
+  if (t == 0) *w.cnt = 0;
   __syncthreads();
   for (int size = 2; size <= mp; size <<= 1)
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -148,31 +183,121 @@ __global__ void __launch_bounds__(kPoolThreads) k_pool_update(int p, int n, cons
       }
       __syncthreads();
     }
-  const int64_t lim = n;  // admitted when 10 * D > n
-  for (int s = 0; s < m; ++s) {
-    const int c = cnt;  // uniform (written before the last barrier)
-    if (c >= p) break;
-    const int x = (int)(key[s] & 0xFFFFF);
-    __syncthreads();
-    int bad = 0;
-    const int16_t* row = D + (size_t)x * m;
-    for (int q = t; q < c; q += blockDim.x)
-      if (10 * (int64_t)row[adm[q]] <= lim) bad = 1;
-    bad = __syncthreads_or(bad);
-    if (t == 0 && !bad) { adm[c] = x; chosen[x] = 1; cnt = c + 1; }
-    __syncthreads();
+  for (int q = t; q < m; q += blockDim.x) {
+    const int x = (int)(key[q] & 0xFFFFF);
+    w.order[q] = x;
+    w.rank[x] = q;
   }
-  // fill with the best remaining candidates when fewer than p were spaced
-  if (t == 0) {
-    int c = cnt;
-    for (int s = 0; s < m && c < p; ++s) {
-      const int x = (int)(key[s] & 0xFFFFF);
-      if (!chosen[x]) { adm[c++] = x; chosen[x] = 1; }
+}
+
+// one warp per candidate at sorted positions b0 .. b0 + kPoolBlk - 1 (D rows read 2 entries per lane step)
+__global__ void __launch_bounds__(32 * kPoolScanWarps) k_pool_scan(int m, int n, int p, int b0, const int16_t* D,
+                                                                   PoolWs w) {
+  __shared__ uint32_t mask[kPoolScanWarps][kPoolWords];
+  if (*(volatile int32_t*)w.cnt >= p) return;  // the pass has already admitted p members
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kPoolScanWarps + warp;  // position within the block
+  const int s = b0 + t;
+  if (s >= m) return;
+  uint32_t* mk = mask[warp];
+  mk[lane] = 0u;
+  __syncwarp();
+  const int x = w.order[s];
+  const uint32_t* row = reinterpret_cast<const uint32_t*>(D + (size_t)x * m);  // m is even: 4-byte aligned
+  bool pre = false;
+  for (int q = lane; q < (m >> 1); q += 32) {
+    const uint32_t dd = __ldg(row + q);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int d = (int)(int16_t)(h ? (dd >> 16) : (dd & 0xFFFFu));
+      if (10 * d <= n) {  // candidate y = 2q + h is within n/10 of x
+        const int y = 2 * q + h;
+        if ((__ldg(w.adm + (y >> 5)) >> (y & 31)) & 1u) pre = true;
+        const int r = w.rank[y];
+        if (r >= b0 && r < s) atomicOr(mk + ((r - b0) >> 5), 1u << ((r - b0) & 31));
+      }
     }
-    cnt = c;
+  }
+  pre = __any_sync(0xFFFFFFFFu, pre);
+  __syncwarp();
+  w.inblk[(size_t)t * kPoolWords + lane] = mk[lane];
+  if (lane == 0) w.pre[t] = pre ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kPoolThreads) k_pool_resolve(int m, int p, int b0, PoolWs w, int32_t* sel) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int c0 = *(volatile int32_t*)w.cnt;
+  if (c0 >= p) return;
+  const int nb = min(kPoolBlk, m - b0);
+  uint32_t* rows = (uint32_t*)smem;                 // [kPoolBlk][kPoolWords]
+  uint8_t* pre = smem + (size_t)kPoolBlk * kPoolWords * 4;  // [kPoolBlk]
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(w.inblk);
+    uint4* dst = reinterpret_cast<uint4*>(rows);
+    for (int q = threadIdx.x; q < nb * kPoolWords / 4; q += blockDim.x) dst[q] = src[q];
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) pre[q] = w.pre[q];
   }
   __syncthreads();
-  for (int q = t; q < p; q += blockDim.x) sel[q] = adm[q];
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  uint32_t M = 0u;  // lane l: admitted positions 32 l .. 32 l + 31 of this block
+  int c = c0;
+  for (int t0 = 0; t0 < nb && c < p; t0 += 4) {
+    uint32_t r4[4];
+    bool p4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {  // loads of the next four rows do not depend on M
+      const int t = min(t0 + u, nb - 1);
+      r4[u] = rows[t * kPoolWords + lane];
+      p4[u] = pre[t] != 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u;
+      if (t >= nb || c >= p) break;
+      const bool rej = p4[u] || __any_sync(0xFFFFFFFFu, (r4[u] & M) != 0u);
+      if (!rej) {
+        if (lane == (t >> 5)) M |= 1u << (t & 31);
+        if (lane == 0) {
+          const int x = w.order[b0 + t];
+          sel[c] = x;
+          atomicOr(w.adm + (x >> 5), 1u << (x & 31));
+        }
+        ++c;
+      }
+    }
+  }
+  if (lane == 0) *w.cnt = c;
+}
+
+// fewer than p admitted: the best remaining candidates (sorted order) fill sel[cnt .. p)
+__global__ void __launch_bounds__(kPoolThreads) k_pool_fill(int m, int p, PoolWs w, int32_t* sel) {
+  __shared__ int wsum[kPoolThreads / 32];
+  const int c0 = *(volatile int32_t*)w.cnt;
+  if (c0 >= p) return;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int per = (m + kPoolThreads - 1) / kPoolThreads;
+  const int s0 = t * per, s1 = min(s0 + per, m);
+  int mine = 0;
+  for (int s = s0; s < s1; ++s) {
+    const int x = w.order[s];
+    mine += ((w.adm[x >> 5] >> (x & 31)) & 1u) ? 0 : 1;
+  }
+  int incl = mine;  // inclusive scan over the warp, then over the warps
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  int before = 0;
+  for (int q = 0; q < warp; ++q) before += wsum[q];
+  int pos = c0 + before + incl - mine;
+  for (int s = s0; s < s1 && pos < p; ++s) {
+    const int x = w.order[s];
+    if (!((w.adm[x >> 5] >> (x & 31)) & 1u)) sel[pos++] = x;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -242,11 +367,27 @@ extern "C" dlm_status dlm_pool_update(dlm_ctx* ctx, int32_t p, int32_t n, const 
   const int m = 2 * p;
   int mp = 1;
   while (mp < m) mp <<= 1;
-  const size_t smem = (size_t)mp * 8 + (size_t)p * 4 + m + 16;
-  if (smem > ctx->smem_optin || m > (1 << 20)) return fail(ctx, DLM_EUNSUPPORTED, "pool_update: p too large");
-  DLM_CUDA(ctx, cudaFuncSetAttribute(k_pool_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_pool_update<<<1, kPoolThreads, smem, ctx->stream>>>(p, n, fit, D, sel, ctx->d_status);
-  return launch_check(ctx, "k_pool_update");
+  const size_t sort_smem = (size_t)mp * 8;
+  if (sort_smem > ctx->smem_optin || m > (1 << 20)) return fail(ctx, DLM_EUNSUPPORTED, "pool_update: p too large");
+  if (((uintptr_t)D & 3) != 0) return fail(ctx, DLM_EINVAL, "pool_update: D must be 4-byte aligned");
+  uint8_t* base = nullptr;
+  DLM_TRY(ctx_workspace(ctx, pool_ws_layout(m, nullptr, nullptr), (void**)&base));
+  PoolWs w;
+  pool_ws_layout(m, &w, base);
+  DLM_CUDA(ctx, cudaFuncSetAttribute(k_pool_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem));
+  k_pool_sort<<<1, kPoolThreads, sort_smem, ctx->stream>>>(m, fit, w, ctx->d_status);
+  DLM_TRY(launch_check(ctx, "k_pool_sort"));
+  const size_t res_smem = (size_t)kPoolBlk * kPoolWords * 4 + kPoolBlk;
+  DLM_CUDA(ctx, cudaFuncSetAttribute(k_pool_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem));
+  for (int b0 = 0; b0 < m; b0 += kPoolBlk) {
+    const int nb = std::min(kPoolBlk, m - b0);
+    k_pool_scan<<<(nb + kPoolScanWarps - 1) / kPoolScanWarps, 32 * kPoolScanWarps, 0, ctx->stream>>>(m, n, p, b0, D, w);
+    DLM_TRY(launch_check(ctx, "k_pool_scan"));
+    k_pool_resolve<<<1, kPoolThreads, res_smem, ctx->stream>>>(m, p, b0, w, sel);
+    DLM_TRY(launch_check(ctx, "k_pool_resolve"));
+  }
+  k_pool_fill<<<1, kPoolThreads, 0, ctx->stream>>>(m, p, w, sel);
+  return launch_check(ctx, "k_pool_fill");
 }
 
 extern "C" dlm_status dlm_knn(dlm_ctx* ctx, int32_t p, const int16_t* D, int32_t K, int32_t* nbr) {

@@ -544,8 +544,9 @@ struct TabuBatchArgs {
   TabuRule rule;
 };
 
+// Two CTAs per SM up to 16 warps (64 registers a thread); a 32-warp CTA takes the SM's registers alone.
 template <int W>
-__global__ void __launch_bounds__(W * 32, 2) tabucol_batch_kernel(TabuBatchArgs a) {
+__global__ void __launch_bounds__(W * 32, W >= 32 ? 1 : 2) tabucol_batch_kernel(TabuBatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   // one individual per CTA, or (when rows spill to a per-CTA slab) resident CTAs loop over them
   for (int i = blockIdx.x; i < a.pop; i += gridDim.x) {
@@ -577,7 +578,7 @@ struct MultiJob {
 };
 
 template <int W>
-__global__ void __launch_bounds__(W * 32, 2) tabucol_multi_kernel(const MultiJob* jobs, int32_t njobs,
+__global__ void __launch_bounds__(W * 32, W >= 32 ? 1 : 2) tabucol_multi_kernel(const MultiJob* jobs, int32_t njobs,
                                                                int32_t* queue, TabuRule rule) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int32_t next;
@@ -634,6 +635,24 @@ static int default_warps(int n, int k) {
   return 16;  // each thread owns at most ceil(n / 512) vertices: short phases between the barriers
 }
 
+// default of the one-graph launch: a state that leaves room for only one 16-warp CTA per SM
+// (n = 1000, k = 48 takes 217 KB) gets 32 warps, all of the SM's registers, so each thread owns
+// at most ceil(n / 1024) vertices (about 10 % faster at n = 700..1000 than 16 warps, same result)
+static int default_warps_batch(dlm_ctx* ctx, int n, int k) {
+  const int w = default_warps(n, k);
+  if (w != 16) return w;
+  const TabuSmem L = tabu_smem_layout(n, k, 16, ctx->smem_optin);
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(tabucol_batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<16>, 16 * 32, L.total) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 16;
+  }
+  return per_sm == 1 ? 32 : 16;
+}
+
 static dlm_status tabucol_check(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,
                                 dlm_tenure t) {
   if (!ctx || !g) return fail(ctx, DLM_EINVAL, "null context or graph");
@@ -655,9 +674,9 @@ static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32
   if (pop == 0) return DLM_OK;
   if (!col || !best_f) return fail(ctx, DLM_EINVAL, "tabucol: null col or best_f");
   if (warps == 0) warps = lookup_tune(ctx, g->n, k);
-  if (warps == 0) warps = default_warps(g->n, k);
-  if (warps != 1 && warps != 2 && warps != 4 && warps != 8 && warps != 16)
-    return fail(ctx, DLM_EINVAL, "tabucol: warps per individual must be 1, 2, 4, 8 or 16");
+  if (warps == 0) warps = default_warps_batch(ctx, g->n, k);
+  if (warps != 1 && warps != 2 && warps != 4 && warps != 8 && warps != 16 && warps != 32)
+    return fail(ctx, DLM_EINVAL, "tabucol: warps per individual must be 1, 2, 4, 8, 16 or 32");
   const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
   if (L.rs < 1 || L.total > ctx->smem_optin)
     return fail(ctx, DLM_EUNSUPPORTED, "tabucol: the per-individual arrays exceed shared memory per block");
@@ -674,7 +693,8 @@ static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32
     case 2: return launch_batch<2>(ctx, a, L.total, slab_stride);
     case 4: return launch_batch<4>(ctx, a, L.total, slab_stride);
     case 8: return launch_batch<8>(ctx, a, L.total, slab_stride);
-    default: return launch_batch<16>(ctx, a, L.total, slab_stride);
+    case 16: return launch_batch<16>(ctx, a, L.total, slab_stride);
+    default: return launch_batch<32>(ctx, a, L.total, slab_stride);
   }
 }
 

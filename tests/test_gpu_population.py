@@ -97,8 +97,13 @@ def _random_pool_case(p, n, seed, spread):
 
 
 @pytest.mark.parametrize("p,n,seed,spread", [(64, 100, 0, 25), (300, 500, 1, 120), (33, 50, 2, 6), (1, 10, 3, 5),
-                                             (8192, 1000, 4, 300)])
+                                             (8192, 1000, 4, 300),
+                                             (700, 100, 5, 120),       # two blocks of 1024, the last ragged
+                                             (2048, 1000, 6, 2000),    # few close pairs, four blocks
+                                             (4100, 10, 7, 32000)])    # p kept in the middle of block 4
 def test_pool_update_matches_oracle(ctx, p, n, seed, spread):
+    """The kept candidates and their order equal the oracle's one-at-a-time greedy visit, with and
+    without a fill, within one block of 1024 candidates and across several."""
     fit, D = _random_pool_case(p, n, seed, spread)
     sel = torch.zeros(p, dtype=torch.int32, device="cuda")
     dlmcol.dlm_pool_update(ctx, p, n, _cuda(fit), _cuda(D), sel)

@@ -85,7 +85,7 @@ def test_gamma_matches_oracle(ctx):
         assert np.array_equal(gam[i].cpu().numpy(), g_ref) and f[i].item() == f_ref
 
 
-@pytest.mark.parametrize("warps", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("warps", [1, 2, 4, 8, 16, 32])
 def test_tabucol_small_random_graph_trace_bitexact(ctx, warps):
     """8 individuals on G(125, 0.5), k = 17, 10^4 iterations, seed 0 (gamma is exact in u16 for n < 65536): every
     iteration's move, the best colouring, best f and moves equal the oracle's."""
@@ -124,6 +124,23 @@ def test_tabucol_shapes_bitexact(ctx, n, k, p, iters, pop, seed):
         assert np.array_equal(gpu["col"][i], r["best_col"])
 
 
+@pytest.mark.parametrize("warps", [16, 32])
+def test_tabucol_planted_1000_k48_trace_bitexact(ctx, warps):
+    """The memetic workload's graph (planted 48-colourable, n = 1000, p = 0.5 across parts): one
+    vertex (32 warps) or two vertices (16 warps) per thread, every move equal to the oracle's."""
+    n, k, pop, iters = 1000, 48, 3, 2000
+    e, _ = inputs.planted(n, k, 0.5, seed=0)
+    adj = inputs.edges_to_adj(n, e)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, pop, 5, 40)
+    gpu = _run_gpu(ctx, g, k, start, iters, seed=5, gen=1, ind_base=40, warps=warps, trace=True)
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 5, 40 + i, 1, True) for i in range(pop)])
+    for i, r in enumerate(refs):
+        assert np.array_equal(gpu["trace"][i, :r["iters"]], r["trace"])
+        assert gpu["best_f"][i] == r["best_f"] and gpu["moves"][i] == r["moves"]
+        assert np.array_equal(gpu["col"][i], r["best_col"])
+
+
 def test_tabucol_planted_early_stop_and_legal_start(ctx):
     n, k = 200, 8
     e, part = inputs.planted(n, k, 0.5, seed=2)
@@ -137,6 +154,29 @@ def test_tabucol_planted_early_stop_and_legal_start(ctx):
         assert gpu["best_f"][i] == r["best_f"] == 0 and gpu["moves"][i] == r["moves"]
         assert np.array_equal(gpu["col"][i], r["best_col"])
     assert gpu["moves"][3] == 0
+
+
+@pytest.mark.parametrize("case", ["no_budget", "edgeless", "max_n", "k_above_n"])
+def test_tabucol_degenerate_cases_match_oracle(ctx, case):
+    """Degenerate inputs: a zero budget (the start colouring and its conflicts come back, no
+    move), an edgeless graph (f = 0 at the start: nothing runs), the largest n the kernel takes
+    (2048, sparse) and more colours than vertices (K_10 with k = 20 reaches 0)."""
+    n, k, p, iters, pop = {"no_budget": (300, 20, 0.5, 0, 3), "edgeless": (64, 3, 0.0, 100, 2),
+                           "max_n": (2048, 8, 0.004, 300, 2), "k_above_n": (10, 20, 1.0, 200, 3)}[case]
+    e, adj = gnp_case(n, p, 9)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, pop, 9)
+    gpu = _run_gpu(ctx, g, k, start, iters, seed=9, trace=iters > 0)
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 9, i, 0, iters > 0) for i in range(pop)])
+    for i, r in enumerate(refs):
+        if iters > 0:
+            assert np.array_equal(gpu["trace"][i, :r["iters"]], r["trace"])
+        assert gpu["best_f"][i] == r["best_f"] and gpu["moves"][i] == r["moves"]
+        assert np.array_equal(gpu["col"][i], r["best_col"])
+    if case in ("no_budget", "edgeless"):
+        assert np.array_equal(gpu["col"], start) and not gpu["moves"].any()
+    if case == "k_above_n":
+        assert not gpu["best_f"].any()
 
 
 def test_tabucol_long_run_crosses_tabu_sweeps(ctx):
@@ -168,6 +208,9 @@ def test_tabucol_rejects_bad_input(ctx):
         dlmcol.dlm_tabucol_batch_ex(ctx, g, k, 2, col, bf, None, 10, warps=3)
     dlmcol.dlm_tabucol_batch(ctx, g, k, 0, col, bf, None, 10)  # empty population is a no-op
     ctx.sync()
+    for bad_n in (1, 2049):  # graphs take 2..2048 vertices
+        with pytest.raises(dlmcol.DlmError):
+            device_graph(ctx, bad_n, np.zeros((0, 2), np.int32))
 
 
 def test_tabucol_full_size_all_individuals(ctx):
