@@ -202,9 +202,22 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
     for (int q = warp; q < kR; q += 8) {
       float2 acc = make_float2(0.f, 0.f);
       if (q < k) {
-        for (int j = off[q]; j < off[q + 1]; ++j) {
-          const int v = mem[j];
-          const float2 ef = *reinterpret_cast<const float2*>(E + (size_t)v * kD0 + 2 * lane);
+        // members in ascending order; eight embedding rows are loaded before they are added (the
+        // rows come from L2, so the loads of a class overlap), the sum keeps the member order
+        int j = off[q];
+        const int je = off[q + 1];
+        for (; j + 8 <= je; j += 8) {
+          float2 ef[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) ef[u] = *reinterpret_cast<const float2*>(E + (size_t)mem[j + u] * kD0 + 2 * lane);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            acc.x += ef[u].x;
+            acc.y += ef[u].y;
+          }
+        }
+        for (; j < je; ++j) {
+          const float2 ef = *reinterpret_cast<const float2*>(E + (size_t)mem[j] * kD0 + 2 * lane);
           acc.x += ef.x;
           acc.y += ef.y;
         }
@@ -249,8 +262,13 @@ __global__ void __launch_bounds__(256) k_gterm(int c, int din, const float* M, c
   __syncthreads();
   const float* gam = theta + ogam;
   float acc = 0.f;
-#pragma unroll 4
-  for (int f = 0; f < din; ++f) acc += ms[f] * gam[(size_t)f * kD + o];
+  for (int f = 0; f < din; f += 16) {  // din is 64 or 256: sixteen Gamma loads in flight, sum in f order
+    float g[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) g[u] = gam[(size_t)(f + u) * kD + o];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc += ms[f + u] * g[u];
+  }
   G[(size_t)cand * kD + o] = acc + theta[ob + o];
 }
 
@@ -261,8 +279,16 @@ __global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, f
   const bf16* x = X + (size_t)cand * kR * w + col;
   const bf16* xl = Xlo ? Xlo + (size_t)cand * kR * w + col : nullptr;
   float s = 0.f;
-#pragma unroll 8
-  for (int r = 0; r < k; ++r) s += __bfloat162float(x[(size_t)r * w]) + (xl ? __bfloat162float(xl[(size_t)r * w]) : 0.f);
+  int r = 0;
+  for (; r + 16 <= k; r += 16) {  // sixteen rows loaded before they are added, sum in row order
+    float t[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      t[u] = __bfloat162float(x[(size_t)(r + u) * w]) + (xl ? __bfloat162float(xl[(size_t)(r + u) * w]) : 0.f);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) s += t[u];
+  }
+  for (; r < k; ++r) s += __bfloat162float(x[(size_t)r * w]) + (xl ? __bfloat162float(xl[(size_t)r * w]) : 0.f);
   s *= scale;
   outf[(size_t)cand * w + col] = s;
   if (outb) {
@@ -272,11 +298,18 @@ __global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, f
   }
 }
 
-__global__ void k_head_out(int c, int k, const float* rowdot, const float* theta, size_t obh, float* out) {
+// output = head bias + mean over the k class rows of the head dot, whose row values come in
+// `parts` column slices of M = c * R rows each (summed in slice order)
+__global__ void k_head_out(int c, int k, const float* rowdot, int parts, const float* theta, size_t obh, float* out) {
   const int cand = blockIdx.x * blockDim.x + threadIdx.x;
   if (cand >= c) return;
+  const size_t M = (size_t)c * kR;
   float s = 0.f;
-  for (int r = 0; r < k; ++r) s += rowdot[(size_t)cand * kR + r];
+  for (int r = 0; r < k; ++r) {
+    float t = rowdot[(size_t)cand * kR + r];
+    for (int q = 1; q < parts; ++q) t += rowdot[q * M + (size_t)cand * kR + r];
+    s += t;
+  }
   out[cand] = theta[obh] + s / (float)k;
 }
 
@@ -299,7 +332,7 @@ __global__ void k_transpose(const bf16* X, int rows, int cols, bf16* Y) {
 // GEMM epilogues
 // ------------------------------------------------------------------------------------------------
 struct EpiPlain {  // out[row][col] = alpha * acc + bias[col]
-  __device__ void tile(int) {}
+  __device__ void tile(int, int) {}
   float* out;
   int ld, M;
   float alpha;
@@ -314,7 +347,7 @@ struct EpiPlain {  // out[row][col] = alpha * acc + bias[col]
 };
 
 struct EpiBias {  // G[row][col] = acc + beta[col] (the per-candidate Gamma term of a layer)
-  __device__ void tile(int) {}
+  __device__ void tile(int, int) {}
   float* G;
   int M;
   const float* beta;
@@ -335,7 +368,7 @@ struct EpiPartial {  // split-K slice z: part[z][row][col] = acc
   int ld, M;
   size_t zstride;
   int z = 0;
-  __device__ void tile(int zz) { z = zz; }
+  __device__ void tile(int zz, int) { z = zz; }
   __device__ void operator()(int row, int col0, const float (&v)[16]) const {
     if (row >= M) return;
     float* o = part + (size_t)z * zstride + (size_t)row * ld + col0;
@@ -346,14 +379,16 @@ struct EpiPartial {  // split-K slice z: part[z][row][col] = acc
 };
 
 struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optional head dot
-  __device__ void tile(int) {}
   bf16* H;    // may be null (scoring the last layer)
   bf16* Hlo;  // lo part (training) or null
   int M, kv;
   const float* G;
   const float* wh;
-  float* rowdot;
+  float* rowdot;  // [256 / pbn][M]: the head dot of each row over the pbn columns of one N tile
   float dot;
+  int pbn;        // the GEMM's N tile width
+  int part;
+  __device__ void tile(int, int n0) { part = n0 / pbn; }
   __device__ void operator()(int row, int col0, const float (&v)[16]) {
     if (row >= M) return;
     const int cand = row / kR;
@@ -397,12 +432,12 @@ struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optiona
     }
   }
   __device__ void finish(int row) const {
-    if (rowdot && row < M) rowdot[row] = dot;
+    if (rowdot && row < M) rowdot[(size_t)part * M + row] = dot;
   }
 };
 
 struct EpiBwd {  // dZprev[row][col] = mask((acc + Gb[cand][col]) * LeakyReLU'(Hprev[row][col]))
-  __device__ void tile(int) {}
+  __device__ void tile(int, int) {}
   bf16* dZ;
   int ld, M, kv;
   const float* Gb;
@@ -470,7 +505,15 @@ __global__ void k_head_back(int B, int k, const float* dout, const float* theta,
 __global__ void k_head_grad(int B, const float* dout, const float* Mf3, float* grad, size_t owh, size_t obh) {
   const int o = threadIdx.x;
   float s = 0.f;
-  for (int c = 0; c < B; ++c) s += dout[c] * Mf3[(size_t)c * kD + o];
+  int c = 0;
+  for (; c + 8 <= B; c += 8) {
+    float m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = Mf3[(size_t)(c + u) * kD + o];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += dout[c + u] * m[u];
+  }
+  for (; c < B; ++c) s += dout[c] * Mf3[(size_t)c * kD + o];
   grad[owh + o] = s;
   if (o == 0) {
     float b = 0.f;
@@ -483,7 +526,18 @@ __global__ void k_head_grad(int B, const float* dout, const float* Mf3, float* g
 __global__ void k_dgamma(int B, int din, const float* Mprev, const float* S, float* grad, size_t ogam, size_t ob) {
   const int f = blockIdx.x, o = threadIdx.x;
   float s = 0.f;
-  for (int c = 0; c < B; ++c) s += Mprev[(size_t)c * din + f] * S[(size_t)c * kD + o];
+  int c = 0;
+  for (; c + 8 <= B; c += 8) {  // eight candidates' loads in flight, sum in candidate order
+    float a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a[u] = Mprev[(size_t)(c + u) * din + f];
+      b[u] = S[(size_t)(c + u) * kD + o];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += a[u] * b[u];
+  }
+  for (; c < B; ++c) s += Mprev[(size_t)c * din + f] * S[(size_t)c * kD + o];
   grad[ogam + (size_t)f * kD + o] = s;
   if (f == 0) {
     float b = 0.f;
@@ -502,14 +556,22 @@ __global__ void __launch_bounds__(kD) k_gb(int B, int din, int k, const float* S
   ss[threadIdx.x] = S[(size_t)cand * kD + threadIdx.x];
   __syncthreads();
   const float* gam = theta + ogam;
-  for (int f = warp; f < din; f += kD / 32) {
-    const float* g = gam + (size_t)f * kD;
-    float acc = 0.f;
+  constexpr int kStep = kD / 32;  // rows f = warp, warp + 8, ...; four of them in flight (din % 32 == 0)
+  for (int f0 = warp; f0 < din; f0 += 4 * kStep) {
+    float gv[4][kD / 32];
 #pragma unroll
-    for (int o = lane; o < kD; o += 32) acc += ss[o] * g[o];
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, d);
-    if (lane == 0) Gb[(size_t)cand * din + f] = acc / (float)k;
+      for (int i = 0; i < kD / 32; ++i) gv[q][i] = gam[(size_t)(f0 + q * kStep) * kD + lane + 32 * i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int i = 0; i < kD / 32; ++i) acc += ss[lane + 32 * i] * gv[q][i];
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, d);
+      if (lane == 0) Gb[(size_t)cand * din + f0 + q * kStep] = acc / (float)k;
+    }
   }
 }
 
@@ -528,7 +590,18 @@ __global__ void k_demb(int n, int B, const int16_t* cols, const bf16* dZ0, const
   const int v = blockIdx.x, f = threadIdx.x;  // 64 threads
   if (v < n) {
     float s = 0.f;
-    for (int c = 0; c < B; ++c) {
+    int c = 0;
+    for (; c + 8 <= B; c += 8) {  // eight candidates' colour and gradient loads in flight
+      int q[8];
+      float z[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) q[u] = cols[(size_t)(c + u) * n + v];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) z[u] = __bfloat162float(dZ0[((size_t)(c + u) * kR + q[u]) * kD0 + f]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += z[u];
+    }
+    for (; c < B; ++c) {
       const int q = cols[(size_t)c * n + v];
       s += __bfloat162float(dZ0[((size_t)c * kR + q) * kD0 + f]);
     }
@@ -682,9 +755,12 @@ dlm_status make_map_bf16(dlm_ctx* ctx, CUtensorMap* map, const void* base, uint6
 
 // C[M][N] = (A + A2)[M][K] . (B + B2)[N][K]^T through the tcgen05 kernel, A2 / B2 the lo parts
 // of split operands (or null); kc = 64-wide K chunks per CTA (split-K along grid z)
-template <int BN, class Epi>
+// ST = 0: two pipeline stages (split operands) or four; ST > 0: that many (one keeps the shared
+// memory of a 128 x 64 tile at about 50 KB)
+template <int BN, int ST = 0, class Epi>
 static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K, int lda, const bf16* B, const bf16* B2,
                        int N, int ldb, int kc, Epi epi) {
+  constexpr int S2 = ST ? ST : 2, S4 = ST ? ST : 4;
   if (M <= 0) return DLM_OK;
   if (K % tc::BK || N % BN) return fail(ctx, DLM_EINVAL, "gemm: K must be a multiple of 64 and N of the tile");
   CUtensorMap ma, ma2, mb, mb2;
@@ -720,18 +796,18 @@ static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K
   };
   if (A2 && B2) {
     static bool attr = false;
-    return launch(tc::gemm_kernel<BN, 2, 2, 2, Epi>, tc::gemm_smem_bytes<BN, 2, 2, 2>(), attr);
+    return launch(tc::gemm_kernel<BN, S2, 2, 2, Epi>, tc::gemm_smem_bytes<BN, S2, 2, 2>(), attr);
   }
   if (A2) {
     static bool attr = false;
-    return launch(tc::gemm_kernel<BN, 2, 2, 1, Epi>, tc::gemm_smem_bytes<BN, 2, 2, 1>(), attr);
+    return launch(tc::gemm_kernel<BN, S2, 2, 1, Epi>, tc::gemm_smem_bytes<BN, S2, 2, 1>(), attr);
   }
   if (B2) {
     static bool attr = false;
-    return launch(tc::gemm_kernel<BN, 2, 1, 2, Epi>, tc::gemm_smem_bytes<BN, 2, 1, 2>(), attr);
+    return launch(tc::gemm_kernel<BN, S2, 1, 2, Epi>, tc::gemm_smem_bytes<BN, S2, 1, 2>(), attr);
   }
   static bool attr = false;
-  return launch(tc::gemm_kernel<BN, 4, 1, 1, Epi>, tc::gemm_smem_bytes<BN, 4, 1, 1>(), attr);
+  return launch(tc::gemm_kernel<BN, S4, 1, 1, Epi>, tc::gemm_smem_bytes<BN, S4, 1, 1>(), attr);
 }
 
 template <typename T>
@@ -789,16 +865,24 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       DLM_TRY(launch_check(ctx, "k_gterm"));
     }
     const bool last = l == kNL;
+    // a training batch (train) runs its layer GEMMs as 128 x 64 tiles with one pipeline stage:
+    // four times the CTAs of a 128 x 256 tile for a few thousand rows, and about 50 KB of shared
+    // memory each instead of 193 KB
     EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, G[l],
-               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f};
-    DLM_TRY(gemm<256>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din, 0, e));
+               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, train ? 64 : 256, 0};
+    if (train)
+      DLM_TRY((gemm<64, 1>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din,
+                          0, e)));
+    else
+      DLM_TRY(gemm<256>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din, 0,
+                        e));
     if (!last || train) {
       k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, 1.f / s->k, Mf[l], Mb[l],
                                                   Mblo[l]);
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
-  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, rowdot, s->theta, s->obh, out);
+  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, rowdot, train ? kD / 64 : 1, s->theta, s->obh, out);
   return launch_check(ctx, "k_head_out");
 }
 
@@ -824,8 +908,8 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
     DLM_TRY(launch_check(ctx, "k_transpose"));
     // dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction)
     const int nchunks = rows / tc::BK, kc = 4, splits = (nchunks + kc - 1) / kc;
-    DLM_TRY(gemm<256>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc,
-                      EpiPartial{s->part, kD, din, (size_t)din * kD}));
+    DLM_TRY((gemm<64, 1>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc,
+                        EpiPartial{s->part, kD, din, (size_t)din * kD})));
     const int64_t cnt = (int64_t)din * kD;
     k_reduce_splits<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, splits, s->part, s->grad + s->olam[l]);
     DLM_TRY(launch_check(ctx, "k_reduce_splits"));
@@ -835,8 +919,7 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
     DLM_TRY(launch_check(ctx, "k_gb"));
     // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
     EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->Gb, s->Hb[l - 1]};
-    if (din == kD) DLM_TRY(gemm<256>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e));
-    else DLM_TRY(gemm<64>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e));
+    DLM_TRY((gemm<64, 1>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
   }
   k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, 1.f, s->S[0], nullptr, nullptr);
   k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, cols, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
@@ -863,7 +946,7 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
   }
   DLM_TRY(dalloc(ctx, &s->Gb, (size_t)cb * kD));
   DLM_TRY(dalloc(ctx, &s->part, (size_t)(rows / tc::BK / 4 + 1) * kD * kD));
-  DLM_TRY(dalloc(ctx, &s->rowdotb, (size_t)rows));
+  DLM_TRY(dalloc(ctx, &s->rowdotb, (size_t)rows * (kD / 64)));
   DLM_TRY(dalloc(ctx, &s->outb, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->dout, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->lossd, 1));

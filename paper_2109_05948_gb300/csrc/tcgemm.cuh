@@ -110,7 +110,7 @@ struct GemmShape {
   int k_chunks_per_cta; // split-K: number of 64-wide chunks per CTA along blockIdx.z
 };
 
-// Epilogue functors receive tile(z) with the tile's K split, then (row, col0, v[16]) for 16
+// Epilogue functors receive tile(z, n0) with the tile's K split and first column, then (row, col0, v[16]) for 16
 // consecutive output columns of one row, then finish(row); the kernel copies the functor for
 // every tile, so per-row state starts fresh.
 // NA / NB = 2: the operand is given as two bf16 matrices, the hi and lo parts of an fp32 matrix
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       tile_of(t, m0, n0, kc0, nk);
       const int row = m0 + q * 32 + lane;
       Epi e = epi;
-      e.tile(kc0 / kpc);  // the tile's K split
+      e.tile(kc0 / kpc, n0);  // the tile's K split and first column
       if (nk <= 0) {  // empty K range: the tile's contribution is zero
         float v[16];
 #pragma unroll
