@@ -72,15 +72,12 @@ struct dlm_scorer {
   float* dout = nullptr;
   float* lossd = nullptr;
   // training
-  int16_t* bcols = nullptr;   // gathered batch colourings
   float* y = nullptr;         // standardised targets
-  float* by = nullptr;
   int32_t* perm = nullptr;
   int capp = 0;
   // training step replayed from a CUDA graph: the batch offset within the epoch's permutation and
-  // the Adam step counter live on the device ([0] offset, [1] t), with Adam's bias corrections
+  // the Adam step counter live on the device ([0] offset, [1] t)
   int32_t* d_step = nullptr;
-  float* d_bc = nullptr;
   cudaStream_t cap_stream = nullptr;
   struct StepGraph {
     cudaGraphExec_t exec = nullptr;
@@ -140,14 +137,32 @@ __global__ void k_convert(ConvArgs a) {
   }
 }
 
+// G[o] = beta[o] + sum_f m[f] Gamma[f][o] for the 256 threads o of a block (m in shared memory,
+// f ascending; sixteen Gamma loads in flight; din a multiple of 16)
+__device__ __forceinline__ float gterm_col(const float* m, int din, const float* gam, const float* beta, int o) {
+  float acc = 0.f;
+  for (int f = 0; f < din; f += 16) {
+    float g[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) g[u] = gam[(size_t)(f + u) * kD + o];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc += m[f + u] * g[u];
+  }
+  return acc + beta[o];
+}
+
 // ------------------------------------------------------------------------------------------------
 // layer 0: class pooling. One CTA per candidate (grid-stride): a stable counting sort puts the
 // vertices of each class in ascending order, then warp w sums the FP32 embedding rows of classes
 // w, w+8, ... with lane = feature pair (fixed summation order; E is read through L1/L2).
+// A training batch reads its candidates through the epoch permutation (candidate b = sample
+// perm[step[0] + b]) and, with G1 set, ends with layer 1's per-candidate term
+// G1 = beta_1 + mean_c(H0) Gamma_1.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols, int c, const float* E, const float* b0,
-                                              bf16* H0, bf16* H0lo, float* Mf0, bf16* Mb0, bf16* Mb0lo,
-                                              int32_t* status) {
+__global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols, int c, const int32_t* perm,
+                                              const int32_t* step, const float* E, const float* b0, bf16* H0,
+                                              bf16* H0lo, float* Mf0, bf16* Mb0, bf16* Mb0lo, const float* gam1,
+                                              const float* beta1, float* G1, int32_t* status) {
   extern __shared__ __align__(16) uint8_t sm[];
   uint8_t* col = sm;                                        // [n]
   uint16_t* mem = (uint16_t*)(sm + ((n + 15) & ~15));       // [n]
@@ -155,9 +170,11 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
   int* off = cnt + 64;                                      // [65]
   int* cur = off + 65;                                      // [64]
   float* part = (float*)(cur + 64);                         // [8][64]
+  float* mvec = part + 8 * 64;                              // [64]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int cand = blockIdx.x; cand < c; cand += gridDim.x) {
-    const int16_t* cc = cols + (size_t)cand * n;
+    const int srow = perm ? perm[step[0] + cand] : cand;
+    const int16_t* cc = cols + (size_t)srow * n;
     if (tid < 64) cnt[tid] = 0;
     __syncthreads();
     for (int v = tid; v < n; v += 256) {
@@ -243,11 +260,13 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
       for (int w = 0; w < 8; ++w) s += part[w * 64 + tid];
       s /= (float)k;
       Mf0[(size_t)cand * kD0 + tid] = s;
+      mvec[tid] = s;
       const bf16 hi = __float2bfloat16_rn(s);
       Mb0[(size_t)cand * kD0 + tid] = hi;
       Mb0lo[(size_t)cand * kD0 + tid] = __float2bfloat16_rn(s - __bfloat162float(hi));
     }
     __syncthreads();
+    if (G1) G1[(size_t)cand * kD + tid] = gterm_col(mvec, kD0, gam1, beta1, tid);
   }
 }
 
@@ -260,22 +279,13 @@ __global__ void __launch_bounds__(256) k_gterm(int c, int din, const float* M, c
   const int cand = blockIdx.x, o = threadIdx.x;
   if (o < din) ms[o] = M[(size_t)cand * din + o];
   __syncthreads();
-  const float* gam = theta + ogam;
-  float acc = 0.f;
-  for (int f = 0; f < din; f += 16) {  // din is 64 or 256: sixteen Gamma loads in flight, sum in f order
-    float g[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) g[u] = gam[(size_t)(f + u) * kD + o];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) acc += ms[f + u] * g[u];
-  }
-  G[(size_t)cand * kD + o] = acc + theta[ob + o];
+  G[(size_t)cand * kD + o] = gterm_col(ms, din, theta + ogam, theta + ob, o);
 }
 
-// per-candidate mean (or sum) over the k valid rows of a bf16 [c*R][w] matrix; block = w threads
-__global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf, bf16* outb,
-                                 bf16* outblo) {
-  const int cand = blockIdx.x, col = threadIdx.x;
+// per-candidate mean (or sum) over the k valid rows of a bf16 [c*R][w] matrix, column col of
+// candidate cand; returns the value written to outf
+__device__ __forceinline__ float segment_col(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf,
+                                             bf16* outb, bf16* outblo, int cand, int col) {
   const bf16* x = X + (size_t)cand * kR * w + col;
   const bf16* xl = Xlo ? Xlo + (size_t)cand * kR * w + col : nullptr;
   float s = 0.f;
@@ -296,6 +306,24 @@ __global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, f
     outb[(size_t)cand * w + col] = hi;
     outblo[(size_t)cand * w + col] = __float2bfloat16_rn(s - __bfloat162float(hi));
   }
+  return s;
+}
+
+// block = w threads, one candidate per block
+__global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf, bf16* outb,
+                                 bf16* outblo) {
+  segment_col(X, Xlo, w, k, scale, outf, outb, outblo, blockIdx.x, threadIdx.x);
+}
+
+// a training batch between layers l and l + 1: the class mean of H_l (written as above), then
+// the next layer's per-candidate term G = beta + mean Gamma (block = 256 threads, one candidate)
+__global__ void __launch_bounds__(kD) k_mean_gterm(const bf16* X, const bf16* Xlo, int k, float* outf, bf16* outb,
+                                                   bf16* outblo, const float* gam, const float* beta, float* G) {
+  __shared__ float ms[kD];
+  const int cand = blockIdx.x, o = threadIdx.x;
+  ms[o] = segment_col(X, Xlo, kD, k, 1.f / k, outf, outb, outblo, cand, o);
+  __syncthreads();
+  G[(size_t)cand * kD + o] = gterm_col(ms, kD, gam, beta, o);
 }
 
 // output = head bias + mean over the k class rows of the head dot, whose row values come in
@@ -313,19 +341,47 @@ __global__ void k_head_out(int c, int k, const float* rowdot, int parts, const f
   out[cand] = theta[obh] + s / (float)k;
 }
 
-// 32x32 tiled transpose of a bf16 [rows][cols] matrix into [cols][rows]
-__global__ void k_transpose(const bf16* X, int rows, int cols, bf16* Y) {
-  __shared__ bf16 tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int r = by + i, c = bx + threadIdx.x;
-    if (r < rows && c < cols) tile[i][threadIdx.x] = X[(size_t)r * cols + c];
+// 32x32 tile (bx, by) of the transpose of a bf16 [rows][cols] matrix into [cols][rows]; 256
+// threads as 32 x 8
+__device__ __forceinline__ void transpose_tile(const bf16* X, int rows, int cols, bf16* Y, int bx, int by,
+                                               bf16 (&tile)[32][33]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = by + i, c = bx + tx;
+    if (r < rows && c < cols) tile[i][tx] = X[(size_t)r * cols + c];
   }
   __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int c = bx + i, r = by + threadIdx.x;
-    if (r < rows && c < cols) Y[(size_t)c * rows + r] = tile[threadIdx.x][i];
+  for (int i = ty; i < 32; i += 8) {
+    const int c = bx + i, r = by + tx;
+    if (r < rows && c < cols) Y[(size_t)c * rows + r] = tile[tx][i];
   }
+}
+
+// backward layer l, before its weight-gradient GEMM (256 threads a block):
+//   blocks [0, B)            column sums S = sum over the k valid rows of dZ_l, per candidate
+//   next ceil(rows/32) * 8   tiles of dZ_l^T
+//   next 2 ceil(rows/32) (din/32)  tiles of H_{l-1}^T and of its lo part
+__global__ void __launch_bounds__(256) k_bwd_prep(int B, int k, int rows, int din, const bf16* dZ, float* S,
+                                                  bf16* dZT, const bf16* H, const bf16* Hlo, bf16* HT, bf16* HTlo) {
+  __shared__ bf16 tile[32][33];
+  int t = blockIdx.x;
+  if (t < B) {
+    segment_col(dZ, nullptr, kD, k, 1.f, S, nullptr, nullptr, t, threadIdx.x);
+    return;
+  }
+  t -= B;
+  const int ty = (rows + 31) / 32;
+  const int tz = ty * (kD / 32);
+  if (t < tz) {
+    transpose_tile(dZ, rows, kD, dZT, (t % (kD / 32)) * 32, (t / (kD / 32)) * 32, tile);
+    return;
+  }
+  t -= tz;
+  const int xh = din / 32, th = ty * xh;
+  const bf16* src = t < th ? H : Hlo;
+  bf16* dst = t < th ? HT : HTlo;
+  if (t >= th) t -= th;
+  transpose_tile(src, rows, din, dst, (t % xh) * 32, (t / xh) * 32, tile);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -471,11 +527,13 @@ struct EpiBwd {  // dZprev[row][col] = mask((acc + Gb[cand][col]) * LeakyReLU'(H
 // ------------------------------------------------------------------------------------------------
 // backward helpers (batch of B candidates)
 // ------------------------------------------------------------------------------------------------
-__global__ void k_loss(int B, const float* out, const float* y, float* dout, float* loss) {
+// MSE loss of the batch; with perm, candidate i is sample perm[step[0] + i] (target y of that sample)
+__global__ void k_loss(int B, const float* out, const float* y, const int32_t* perm, const int32_t* step, float* dout,
+                       float* loss) {
   __shared__ float s[256];
   float l = 0.f;
   for (int i = threadIdx.x; i < B; i += blockDim.x) {
-    const float e = out[i] - y[i];
+    const float e = out[i] - y[perm ? perm[step[0] + i] : i];
     dout[i] = 2.f * e / (float)B;
     l += e * e;
   }
@@ -489,8 +547,8 @@ __global__ void k_loss(int B, const float* out, const float* y, float* dout, flo
 }
 
 // dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows; block = one candidate row chunk
-__global__ void k_head_back(int B, int k, const float* dout, const float* theta, size_t owh, const bf16* H3, bf16* dZ3) {
-  const int row = blockIdx.x, o = threadIdx.x;
+__device__ __forceinline__ void head_back_row(int k, const float* dout, const float* theta, size_t owh, const bf16* H3,
+                                              bf16* dZ3, int row, int o) {
   const int cand = row / kR;
   const bool valid = (row % kR) < k;
   float d = 0.f;
@@ -502,8 +560,8 @@ __global__ void k_head_back(int B, int k, const float* dout, const float* theta,
 }
 
 // grad of the head: wh[o] = sum_cand dout * mean(H3)[cand][o]; bh = sum dout
-__global__ void k_head_grad(int B, const float* dout, const float* Mf3, float* grad, size_t owh, size_t obh) {
-  const int o = threadIdx.x;
+__device__ __forceinline__ void head_grad_col(int B, const float* dout, const float* Mf3, float* grad, size_t owh,
+                                              size_t obh, int o) {
   float s = 0.f;
   int c = 0;
   for (; c + 8 <= B; c += 8) {
@@ -522,9 +580,18 @@ __global__ void k_head_grad(int B, const float* dout, const float* Mf3, float* g
   }
 }
 
+// blocks 0 .. rows - 1: dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows (thread = column);
+// block rows: the head's gradient (wh[o] = sum_cand dout * mean(H3)[cand][o], bh = sum dout)
+__global__ void __launch_bounds__(kD) k_head_bwd(int B, int k, int rows, const float* dout, const float* theta,
+                                                 size_t owh, size_t obh, const bf16* H3, const float* Mf3, bf16* dZ3,
+                                                 float* grad) {
+  if ((int)blockIdx.x < rows) head_back_row(k, dout, theta, owh, H3, dZ3, blockIdx.x, threadIdx.x);
+  else head_grad_col(B, dout, Mf3, grad, owh, obh, threadIdx.x);
+}
+
 // dGamma[f][o] = sum_cand Mprev[cand][f] * S[cand][o]; dbeta[o] = sum_cand S[cand][o]
-__global__ void k_dgamma(int B, int din, const float* Mprev, const float* S, float* grad, size_t ogam, size_t ob) {
-  const int f = blockIdx.x, o = threadIdx.x;
+__device__ __forceinline__ void dgamma_col(int B, int din, const float* Mprev, const float* S, float* grad,
+                                           size_t ogam, size_t ob, int f, int o) {
   float s = 0.f;
   int c = 0;
   for (; c + 8 <= B; c += 8) {  // eight candidates' loads in flight, sum in candidate order
@@ -549,10 +616,9 @@ __global__ void k_dgamma(int B, int din, const float* Mprev, const float* S, flo
 // Gb[cand][f] = (1/k) sum_o S[cand][o] * Gamma[f][o]; one block of kD threads per candidate,
 // warp w takes rows f = w, w + 8, ...: its lanes read a Gamma row contiguously and reduce by a
 // fixed butterfly
-__global__ void __launch_bounds__(kD) k_gb(int B, int din, int k, const float* S, const float* theta, size_t ogam,
-                                           float* Gb) {
-  __shared__ float ss[kD];
-  const int cand = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void gb_cand(int din, int k, const float* S, const float* theta, size_t ogam, float* Gb,
+                                        int cand, float (&ss)[kD]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ss[threadIdx.x] = S[(size_t)cand * kD + threadIdx.x];
   __syncthreads();
   const float* gam = theta + ogam;
@@ -576,18 +642,38 @@ __global__ void __launch_bounds__(kD) k_gb(int B, int din, int k, const float* S
 }
 
 // grad[dst + i] = sum_z part[z][i]
-__global__ void k_reduce_splits(int64_t cnt, int splits, const float* part, float* dst) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cnt) return;
-  float s = 0.f;
-  for (int z = 0; z < splits; ++z) s += part[(size_t)z * cnt + i];
-  dst[i] = s;
+// backward layer l, after its weight-gradient GEMM (256 threads a block):
+//   blocks [0, cnt / 256)   dLambda = sum of the split-K slices (fixed slice order)
+//   next din blocks         dGamma row f and (f = 0) dbeta
+//   next B blocks           the per-candidate term Gb of dH_{l-1}
+__global__ void __launch_bounds__(kD) k_bwd_grads(int B, int din, int k, int64_t cnt, int splits, const float* part,
+                                                  float* dlam, const float* Mprev, const float* S, float* grad,
+                                                  const float* theta, size_t ogam, size_t ob, float* Gb) {
+  __shared__ float ss[kD];
+  const int64_t nr = (cnt + 255) / 256;
+  int64_t t = blockIdx.x;
+  if (t < nr) {
+    const int64_t i = t * 256 + threadIdx.x;
+    if (i >= cnt) return;
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * cnt + i];
+    dlam[i] = s;
+    return;
+  }
+  t -= nr;
+  if (t < din) {
+    dgamma_col(B, din, Mprev, S, grad, ogam, ob, (int)t, threadIdx.x);
+    return;
+  }
+  gb_cand(din, k, S, theta, ogam, Gb, (int)(t - din), ss);
 }
 
 // embedding gradient: dE[v][f] = sum_cand dZ0[cand*R + col_cand[v]][f]; db0[f] = sum_cand S0[cand][f]
-__global__ void k_demb(int n, int B, const int16_t* cols, const bf16* dZ0, const float* S0, float* grad, size_t oE,
-                       size_t ob0) {
+// (with perm, candidate c of the batch is sample perm[step[0] + c] of cols)
+__global__ void k_demb(int n, int B, const int16_t* cols, const int32_t* perm, const int32_t* step, const bf16* dZ0,
+                       const float* S0, float* grad, size_t oE, size_t ob0) {
   const int v = blockIdx.x, f = threadIdx.x;  // 64 threads
+  auto row = [&](int c) -> size_t { return (size_t)(perm ? perm[step[0] + c] : c) * n; };
   if (v < n) {
     float s = 0.f;
     int c = 0;
@@ -595,14 +681,14 @@ __global__ void k_demb(int n, int B, const int16_t* cols, const bf16* dZ0, const
       int q[8];
       float z[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) q[u] = cols[(size_t)(c + u) * n + v];
+      for (int u = 0; u < 8; ++u) q[u] = cols[row(c + u) + v];
 #pragma unroll
       for (int u = 0; u < 8; ++u) z[u] = __bfloat162float(dZ0[((size_t)(c + u) * kR + q[u]) * kD0 + f]);
 #pragma unroll
       for (int u = 0; u < 8; ++u) s += z[u];
     }
     for (; c < B; ++c) {
-      const int q = cols[(size_t)c * n + v];
+      const int q = cols[row(c) + v];
       s += __bfloat162float(dZ0[((size_t)c * kR + q) * kD0 + f]);
     }
     grad[oE + (size_t)v * kD0 + f] = s;
@@ -613,7 +699,17 @@ __global__ void k_demb(int n, int B, const int16_t* cols, const bf16* dZ0, const
   }
 }
 
-__global__ void k_adam(int64_t np, float* th, float* m, float* v, const float* g, float lr, const float* bc) {
+// Adam step t + 1 (t = step[1]) of every parameter, then the parameter's bf16 operand copies
+// (those k_convert writes). Bias corrections 1 - 0.9^t and sqrt(1 - 0.999^t) in double.
+__global__ void __launch_bounds__(256) k_adam_convert(int64_t np, float* th, float* m, float* v, const float* g,
+                                                      float lr, const int32_t* step, ConvArgs a) {
+  __shared__ float bc[2];
+  if (threadIdx.x == 0) {
+    const double t = (double)(step[1] + 1);
+    bc[0] = (float)(1.0 - pow(0.9, t));
+    bc[1] = (float)sqrt(1.0 - pow(0.999, t));
+  }
+  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   const float bc1 = bc[0], sbc2 = bc[1];
@@ -623,14 +719,36 @@ __global__ void k_adam(int64_t np, float* th, float* m, float* v, const float* g
   m[i] = mi;
   v[i] = vi;
   const float denom = sqrtf(vi) / sbc2 + 1e-8f;
-  th[i] -= (lr / bc1) * mi / denom;
-}
-
-// Adam step t + 1 (t = step[1]): bias corrections 1 - 0.9^t and sqrt(1 - 0.999^t) in double
-__global__ void k_step_prep(const int32_t* step, float* bc) {
-  const double t = (double)(step[1] + 1);
-  bc[0] = (float)(1.0 - pow(0.9, t));
-  bc[1] = (float)sqrt(1.0 - pow(0.999, t));
+  const float tn = th[i] - (lr / bc1) * mi / denom;
+  th[i] = tn;
+  const int64_t nE = (int64_t)a.n * kD0;
+  if (i >= (int64_t)a.oE && i < (int64_t)a.oE + nE) {
+    a.E16[i - a.oE] = __float2bfloat16_rn(tn);
+    return;
+  }
+  for (int l = 1; l <= kNL; ++l) {
+    const int din = l == 1 ? kD0 : kD;
+    const int64_t sz = (int64_t)din * kD;
+    int64_t r = i - (int64_t)a.olam[l];
+    if (r >= 0 && r < sz) {
+      const int f = (int)(r / kD), o = (int)(r % kD);
+      const bf16 hi = __float2bfloat16_rn(tn);
+      const bf16 lo = __float2bfloat16_rn(tn - __bfloat162float(hi));
+      a.Lam[l][r] = hi;
+      a.Lamlo[l][r] = lo;
+      a.LamT[l][(size_t)o * din + f] = hi;
+      a.LamTlo[l][(size_t)o * din + f] = lo;
+      return;
+    }
+    r = i - (int64_t)a.ogam[l];
+    if (r >= 0 && r < sz) {
+      const int f = (int)(r / kD), o = (int)(r % kD);
+      const bf16 hi = __float2bfloat16_rn(tn);
+      a.GamT[l][(size_t)o * din + f] = hi;
+      a.GamTlo[l][(size_t)o * din + f] = __float2bfloat16_rn(tn - __bfloat162float(hi));
+      return;
+    }
+  }
 }
 
 // after a step: the next batch starts b samples later, Adam's counter advances
@@ -708,13 +826,6 @@ __global__ void k_epoch_perm(int p, uint64_t seed, uint32_t epoch, uint32_t gen,
   for (int i = threadIdx.x; i < p; i += blockDim.x) perm[i] = (int32_t)(keys[i] & 0xFFFFFFFFu);
 }
 
-__global__ void k_gather_batch(int n, int B, const int32_t* perm, const int32_t* step, const int16_t* cols,
-                               const float* y, int16_t* bcols, float* by) {
-  const int b = blockIdx.x;
-  const int i = perm[step[0] + b];
-  for (int v = threadIdx.x; v < n; v += blockDim.x) bcols[(size_t)b * n + v] = cols[(size_t)i * n + v];
-  if (threadIdx.x == 0) by[b] = y[i];
-}
 
 // ------------------------------------------------------------------------------------------------
 // host plumbing
@@ -819,7 +930,7 @@ static dlm_status dalloc(dlm_ctx* ctx, T** p, size_t count) {
   return DLM_OK;
 }
 
-static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
+static ConvArgs conv_args(const dlm_scorer* s, int64_t* tot_out) {
   ConvArgs a;
   a.theta = s->theta;
   a.n = s->n;
@@ -837,36 +948,50 @@ static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
     a.GamTlo[l] = s->GamTlo[l];
     tot += 2 * (int64_t)din_of(l) * kD;
   }
+  if (tot_out) *tot_out = tot;
+  return a;
+}
+
+static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
+  int64_t tot = 0;
+  const ConvArgs a = conv_args(s, &tot);
   k_convert<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(a);
   return launch_check(ctx, "k_convert");
 }
 
-static size_t pool_smem(int n) { return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + (64 + 65 + 64) * 4 + 8 * 64 * 4 + 64; }
+static size_t pool_smem(int n) { return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + (64 + 65 + 64) * 4 + 9 * 64 * 4 + 64; }
 
-// forward over c candidates with the given buffers; train = keep every activation (and H3)
+// forward over c candidates with the given buffers; train = a training batch: keep every
+// activation (and H3), candidate b being sample perm[step[0] + b] of cols when perm is given
 static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int c, float* out, bf16** H, bf16** Hlo,
-                          bf16** Mb, bf16** Mblo, float** Mf, float** G, float* rowdot, bool train) {
+                          bf16** Mb, bf16** Mblo, float** Mf, float** G, float* rowdot, bool train,
+                          const int32_t* perm = nullptr, const int32_t* step = nullptr) {
   const int rows = c * kR;
   const size_t psm = pool_smem(s->n);  // < 10 KB for n <= 2048
   const int pgrid = std::min(c, ctx->num_sms * 4);
-  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, cols, c, s->theta + s->oE, s->theta + s->ob0, H[0],
-                                           Hlo ? Hlo[0] : nullptr, Mf[0], Mb[0], Mblo[0], ctx->d_status);
+  // per-candidate term rho(H_{l-1}) Gamma_l + beta_l: on the tensor cores for a scoring chunk,
+  // both operands split into bf16 hi + lo (three MMA passes, about 16 mantissa bits each); in
+  // FP32 on CUDA cores for a small batch, for a training batch fused into the kernel that forms
+  // the class means (k_pool for layer 1, k_mean_gterm for layers 2 and 3)
+  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, cols, c, perm, step, s->theta + s->oE, s->theta + s->ob0, H[0],
+                                           Hlo ? Hlo[0] : nullptr, Mf[0], Mb[0], Mblo[0],
+                                           s->theta + s->ogam[1], s->theta + s->ob[1], train ? G[1] : nullptr,
+                                           ctx->d_status);
   DLM_TRY(launch_check(ctx, "k_pool"));
   for (int l = 1; l <= kNL; ++l) {
     const int din = din_of(l);
-    // per-candidate term rho(H_{l-1}) Gamma_l + beta_l: on the tensor cores for a scoring chunk,
-    // both operands split into bf16 hi + lo (three MMA passes, about 16 mantissa bits each); in
-    // FP32 on CUDA cores for a training batch
-    if (c >= 1024) {
-      DLM_TRY(gemm<256>(ctx, Mb[l - 1], Mblo[l - 1], c, din, din, s->GamT[l], s->GamTlo[l], kD, din, 0,
-                        EpiBias{G[l], c, s->theta + s->ob[l]}));
-    } else {
-      k_gterm<<<c, 256, 0, ctx->stream>>>(c, din, Mf[l - 1], s->theta, s->ogam[l], s->ob[l], G[l]);
-      DLM_TRY(launch_check(ctx, "k_gterm"));
+    if (!train) {
+      if (c >= 1024) {
+        DLM_TRY(gemm<256>(ctx, Mb[l - 1], Mblo[l - 1], c, din, din, s->GamT[l], s->GamTlo[l], kD, din, 0,
+                          EpiBias{G[l], c, s->theta + s->ob[l]}));
+      } else {
+        k_gterm<<<c, 256, 0, ctx->stream>>>(c, din, Mf[l - 1], s->theta, s->ogam[l], s->ob[l], G[l]);
+        DLM_TRY(launch_check(ctx, "k_gterm"));
+      }
     }
     const bool last = l == kNL;
-    // a training batch (train) runs its layer GEMMs as 128 x 64 tiles with one pipeline stage:
-    // four times the CTAs of a 128 x 256 tile for a few thousand rows, and about 50 KB of shared
+    // a training batch runs its layer GEMMs as 128 x 64 tiles with one pipeline stage: four
+    // times the CTAs of a 128 x 256 tile for a few thousand rows, and about 50 KB of shared
     // memory each instead of 193 KB
     EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, G[l],
                last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, train ? 64 : 256, 0};
@@ -876,7 +1001,11 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
     else
       DLM_TRY(gemm<256>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din, 0,
                         e));
-    if (!last || train) {
+    if (train && !last) {
+      k_mean_gterm<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, s->k, Mf[l], Mb[l], Mblo[l],
+                                              s->theta + s->ogam[l + 1], s->theta + s->ob[l + 1], G[l + 1]);
+      DLM_TRY(launch_check(ctx, "k_mean_gterm"));
+    } else if (!last || train) {
       k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, 1.f / s->k, Mf[l], Mb[l],
                                                   Mblo[l]);
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
@@ -886,43 +1015,43 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
   return launch_check(ctx, "k_head_out");
 }
 
-// forward + backward of one batch; gradient into s->grad (overwritten), predictions into outb
-static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const float* y, int B) {
-  DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mbblo, s->Mfb, s->Gbf, s->rowdotb, true));
+// forward + backward of one batch; gradient into s->grad (overwritten), predictions into outb.
+// With perm, candidate b of the batch is sample perm[step[0] + b] of cols (target y of that
+// sample); otherwise cols and y hold the batch itself.
+static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const float* y, int B,
+                            const int32_t* perm = nullptr, const int32_t* step = nullptr) {
+  DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mbblo, s->Mfb, s->Gbf, s->rowdotb, true, perm,
+                  step));
   const int rows = B * kR;
-  k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, s->dout, s->lossd);
+  k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, perm, step, s->dout, s->lossd);
   DLM_TRY(launch_check(ctx, "k_loss"));
-  k_head_grad<<<1, kD, 0, ctx->stream>>>(B, s->dout, s->Mfb[kNL], s->grad, s->owh, s->obh);
-  k_head_back<<<rows, kD, 0, ctx->stream>>>(B, s->k, s->dout, s->theta, s->owh, s->Hb[kNL], s->dZ[kNL]);
-  DLM_TRY(launch_check(ctx, "k_head_back"));
+  k_head_bwd<<<rows + 1, kD, 0, ctx->stream>>>(B, s->k, rows, s->dout, s->theta, s->owh, s->obh, s->Hb[kNL],
+                                               s->Mfb[kNL], s->dZ[kNL], s->grad);
+  DLM_TRY(launch_check(ctx, "k_head_bwd"));
   for (int l = kNL; l >= 1; --l) {
     const int din = din_of(l);
-    // column sums of dZ_l per candidate (valid rows are the only nonzero ones)
-    k_segment_reduce<<<B, kD, 0, ctx->stream>>>(s->dZ[l], nullptr, kD, s->k, 1.f, s->S[l], nullptr, nullptr);
-    DLM_TRY(launch_check(ctx, "k_segment_reduce"));
-    // transposes for the weight-gradient GEMM
-    dim3 tb(32, 8);
-    k_transpose<<<dim3(kD / 32, (rows + 31) / 32), tb, 0, ctx->stream>>>(s->dZ[l], rows, kD, s->dZT[l]);
-    k_transpose<<<dim3(din / 32, (rows + 31) / 32), tb, 0, ctx->stream>>>(s->Hb[l - 1], rows, din, s->HT[l - 1]);
-    k_transpose<<<dim3(din / 32, (rows + 31) / 32), tb, 0, ctx->stream>>>(s->Hblo[l - 1], rows, din, s->HTlo[l - 1]);
-    DLM_TRY(launch_check(ctx, "k_transpose"));
+    // column sums of dZ_l per candidate (valid rows are the only nonzero ones) and the
+    // transposes of dZ_l and H_{l-1} (hi and lo) for the weight-gradient GEMM, in one launch
+    const int ty = (rows + 31) / 32;
+    k_bwd_prep<<<B + ty * (kD / 32) + 2 * ty * (din / 32), 256, 0, ctx->stream>>>(
+        B, s->k, rows, din, s->dZ[l], s->S[l], s->dZT[l], s->Hb[l - 1], s->Hblo[l - 1], s->HT[l - 1], s->HTlo[l - 1]);
+    DLM_TRY(launch_check(ctx, "k_bwd_prep"));
     // dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction)
     const int nchunks = rows / tc::BK, kc = 4, splits = (nchunks + kc - 1) / kc;
     DLM_TRY((gemm<64, 1>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc,
                         EpiPartial{s->part, kD, din, (size_t)din * kD})));
+    // the split sums into dLambda_l, dGamma_l and dbeta_l, and the per-candidate term of dH_{l-1}
     const int64_t cnt = (int64_t)din * kD;
-    k_reduce_splits<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, splits, s->part, s->grad + s->olam[l]);
-    DLM_TRY(launch_check(ctx, "k_reduce_splits"));
-    // dGamma_l, dbeta_l and the per-candidate term of dH_{l-1}
-    k_dgamma<<<din, kD, 0, ctx->stream>>>(B, din, s->Mfb[l - 1], s->S[l], s->grad, s->ogam[l], s->ob[l]);
-    k_gb<<<B, kD, 0, ctx->stream>>>(B, din, s->k, s->S[l], s->theta, s->ogam[l], s->Gb);
-    DLM_TRY(launch_check(ctx, "k_gb"));
+    k_bwd_grads<<<(unsigned)((cnt + 255) / 256 + din + B), kD, 0, ctx->stream>>>(
+        B, din, s->k, cnt, splits, s->part, s->grad + s->olam[l], s->Mfb[l - 1], s->S[l], s->grad, s->theta,
+        s->ogam[l], s->ob[l], s->Gb);
+    DLM_TRY(launch_check(ctx, "k_bwd_grads"));
     // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
     EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->Gb, s->Hb[l - 1]};
     DLM_TRY((gemm<64, 1>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
   }
   k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, 1.f, s->S[0], nullptr, nullptr);
-  k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, cols, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
+  k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
   return launch_check(ctx, "k_demb");
 }
 
@@ -950,8 +1079,6 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
   DLM_TRY(dalloc(ctx, &s->outb, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->dout, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->lossd, 1));
-  DLM_TRY(dalloc(ctx, &s->bcols, (size_t)cb * s->n));
-  DLM_TRY(dalloc(ctx, &s->by, (size_t)cb));
   s->capb = cb;
   return DLM_OK;
 }
@@ -972,16 +1099,13 @@ static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
   return DLM_OK;
 }
 
-// one Adam step of batch size B (batch offset and step counter on the device)
+// one Adam step of batch size B (batch offset and step counter on the device): the batch is read
+// through the epoch permutation, the Adam update writes the bf16 operand copies too
 static dlm_status train_step(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int B, int b, float lr) {
-  k_gather_batch<<<B, 128, 0, ctx->stream>>>(s->n, B, s->perm, s->d_step, cols, s->y, s->bcols, s->by);
-  DLM_TRY(launch_check(ctx, "k_gather_batch"));
-  DLM_TRY(loss_grad(ctx, s, s->bcols, s->by, B));
-  k_step_prep<<<1, 1, 0, ctx->stream>>>(s->d_step, s->d_bc);
-  DLM_TRY(launch_check(ctx, "k_step_prep"));
-  k_adam<<<(unsigned)((s->np + 255) / 256), 256, 0, ctx->stream>>>(s->np, s->theta, s->am, s->av, s->grad, lr, s->d_bc);
-  DLM_TRY(launch_check(ctx, "k_adam"));
-  DLM_TRY(convert_params(ctx, s));
+  DLM_TRY(loss_grad(ctx, s, cols, s->y, B, s->perm, s->d_step));
+  k_adam_convert<<<(unsigned)((s->np + 255) / 256), 256, 0, ctx->stream>>>(s->np, s->theta, s->am, s->av, s->grad, lr,
+                                                                          s->d_step, conv_args(s, nullptr));
+  DLM_TRY(launch_check(ctx, "k_adam_convert"));
   k_step_end<<<1, 1, 0, ctx->stream>>>(s->d_step, b);
   return launch_check(ctx, "k_step_end");
 }
@@ -1032,7 +1156,6 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   cudaFree(s->d_step);
-  cudaFree(s->d_bc);
   cudaFree(s->theta); cudaFree(s->am); cudaFree(s->av); cudaFree(s->grad); cudaFree(s->E16);
   for (int l = 0; l <= kNL; ++l) {
     cudaFree(s->LamT[l]); cudaFree(s->Lam[l]); cudaFree(s->LamTlo[l]); cudaFree(s->Lamlo[l]);
@@ -1042,7 +1165,7 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
     cudaFree(s->dZ[l]); cudaFree(s->dZT[l]); cudaFree(s->S[l]);
   }
   cudaFree(s->rowdot); cudaFree(s->Gb); cudaFree(s->part); cudaFree(s->rowdotb); cudaFree(s->outb); cudaFree(s->dout);
-  cudaFree(s->lossd); cudaFree(s->bcols); cudaFree(s->y); cudaFree(s->by); cudaFree(s->perm);
+  cudaFree(s->lossd); cudaFree(s->y); cudaFree(s->perm);
   delete s;
 }
 
@@ -1178,7 +1301,6 @@ extern "C" dlm_status dlm_scorer_train(dlm_ctx* ctx, dlm_scorer* s, const int16_
   }
   if (!s->d_step) {
     DLM_TRY(dalloc(ctx, &s->d_step, 2));
-    DLM_TRY(dalloc(ctx, &s->d_bc, 2));
   }
   // the device counters start from the host mirror of Adam's step counter
   int32_t init[2] = {0, (int32_t)s->t};
