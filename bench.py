@@ -262,6 +262,8 @@ def run_memetic(args):
     e, _ = inputs.planted(n, k, 0.5, seed=0)
     g = dlmcol.Graph(ctx, n, torch.from_numpy(e).cuda())
     runs = {"learned": [], "random": []}
+    clocks = Clocks(0)
+    clocks.start()
     for seed in range(args.mem_seeds):
         for mode in ("learned", "random"):
             prm = dlmcol.MemeticParams(k=k, p=args.mem_pop, K=32, iters=args.mem_iters, tenure=dlmcol.COL_TENURE,
@@ -289,6 +291,8 @@ def run_memetic(args):
             print(json.dumps({"progress": mode, **runs[mode][-1]}), file=sys.stderr, flush=True)
             mm.close()
 
+    ck = clocks.stop()
+
     def med(mode):
         ts = [r["time_to_target_s"] for r in runs[mode]]
         if any(t is None for t in ts):
@@ -303,7 +307,7 @@ def run_memetic(args):
                                   f"scorer 64-d embedding + 3 x 256 invariant layers, N=5 epochs, b=100, lr=1e-3",
                       "target_conflicts": args.mem_target, "seeds": args.mem_seeds,
                       "time_limit_s": args.mem_time_limit, "max_generations": args.mem_max_gens},
-           "runs": runs, "data": "synthetic"}
+           "clocks": ck, "runs": runs, "data": "synthetic"}
     print(json.dumps(out), flush=True)
 
 
