@@ -440,9 +440,9 @@ struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optiona
   int M, kv;
   const float* G;
   const float* wh;
-  float* rowdot;  // [256 / pbn][M]: the head dot of each row over the pbn columns of one N tile
+  float* rowdot;  // [256 / pbn][M]: the head dot of each row over the pbn columns one epilogue warp drains
   float dot;
-  int pbn;        // the GEMM's N tile width
+  int pbn;        // half the GEMM's N tile width
   int part;
   __device__ void tile(int, int n0) { part = n0 / pbn; }
   __device__ void operator()(int row, int col0, const float (&v)[16]) {
@@ -994,7 +994,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
     // times the CTAs of a 128 x 256 tile for a few thousand rows, and about 50 KB of shared
     // memory each instead of 193 KB
     EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, G[l],
-               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, train ? 64 : 256, 0};
+               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, train ? 32 : 128, 0};
     if (train)
       DLM_TRY((gemm<64, 1>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din,
                           0, e)));
@@ -1011,7 +1011,8 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
-  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, rowdot, train ? kD / 64 : 1, s->theta, s->obh, out);
+  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, rowdot, train ? kD / 32 : kD / 128, s->theta, s->obh,
+                                                       out);
   return launch_check(ctx, "k_head_out");
 }
 
@@ -1075,7 +1076,7 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
   }
   DLM_TRY(dalloc(ctx, &s->Gb, (size_t)cb * kD));
   DLM_TRY(dalloc(ctx, &s->part, (size_t)(rows / tc::BK / 4 + 1) * kD * kD));
-  DLM_TRY(dalloc(ctx, &s->rowdotb, (size_t)rows * (kD / 64)));
+  DLM_TRY(dalloc(ctx, &s->rowdotb, (size_t)rows * (kD / 32)));
   DLM_TRY(dalloc(ctx, &s->outb, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->dout, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->lossd, 1));
@@ -1094,7 +1095,7 @@ static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
     DLM_TRY(dalloc(ctx, &s->Mf[l], (size_t)cap * w));
     DLM_TRY(dalloc(ctx, &s->G[l], (size_t)cap * kD));
   }
-  DLM_TRY(dalloc(ctx, &s->rowdot, (size_t)rows));
+  DLM_TRY(dalloc(ctx, &s->rowdot, (size_t)rows * (kD / 128)));
   s->cap = cap;
   return DLM_OK;
 }

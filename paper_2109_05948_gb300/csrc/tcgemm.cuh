@@ -5,8 +5,9 @@
 //   warp 0      TMA producer: 128 x 64 and BN x 64 tiles (128-byte swizzle) into an S-stage ring
 //   warp 1      allocates TMEM; one lane issues tcgen05.mma (M = 128, N = BN, K = 16 per
 //               instruction, 4 per 64-wide stage) and commits each stage back to the producer
-//   warps 2..5  epilogue: tcgen05.ld of their TMEM lane quarter (one output row per thread),
-//               then a fused epilogue functor
+//   warps 2..9  epilogue: tcgen05.ld of their TMEM lane quarter (one output row per thread), two
+//               warps per quarter, each taking half of the tile's columns, then a fused
+//               epilogue functor
 // Every mbarrier wait is bounded; on timeout the CTA records DLM_ETIMEOUT, stops issuing work,
 // drains what it issued (again bounded), frees its TMEM and returns.
 #pragma once
@@ -21,7 +22,8 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;            // one 128-byte swizzle atom of bf16
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -110,7 +112,8 @@ struct GemmShape {
   int k_chunks_per_cta; // split-K: number of 64-wide chunks per CTA along blockIdx.z
 };
 
-// Epilogue functors receive tile(z, n0) with the tile's K split and first column, then (row, col0, v[16]) for 16
+// Epilogue functors receive tile(z, n0) with the tile's K split and the first column of the
+// half tile they drain (BN / 2 columns), then (row, col0, v[16]) for 16
 // consecutive output columns of one row, then finish(row); the kernel copies the functor for
 // every tile, so per-row state starts fresh.
 // NA / NB = 2: the operand is given as two bf16 matrices, the hi and lo parts of an fp32 matrix
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(accf + b, 1); mbar_init(acce + b, 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(accf + b, 1); mbar_init(acce + b, kEpiWarps); }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -219,19 +222,21 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     }
   } else if (warp >= 2) {
     // ---- epilogue: drains accumulator (local tile index & 1) ----
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int q = warp & 3;                               // TMEM lane quarter this warp may access
+    constexpr int HALF = BN / 2;
+    const int c0 = ((warp - 2) / 4) * HALF;               // this warp's half of the columns
     int lt = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
       int m0, n0, kc0, nk;
       tile_of(t, m0, n0, kc0, nk);
       const int row = m0 + q * 32 + lane;
       Epi e = epi;
-      e.tile(kc0 / kpc, n0);  // the tile's K split and first column
+      e.tile(kc0 / kpc, n0 + c0);  // the tile's K split and the first column of this half
       if (nk <= 0) {  // empty K range: the tile's contribution is zero
         float v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = 0.f;
-        for (int c = 0; c < BN; c += 16) e(row, n0 + c, v);
+        for (int c = c0; c < c0 + HALF; c += 16) e(row, n0 + c, v);
         e.finish(row);
         --lt;  // no accumulator used
         continue;
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       }
       const uint32_t tbase = tmem + (uint32_t)(b * BN) + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 16) {
+      for (int c = c0; c < c0 + HALF; c += 16) {
         float v[16];
         tmem_ld16(tbase + (uint32_t)c, v);
         e(row, n0 + c, v);
