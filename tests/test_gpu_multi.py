@@ -117,3 +117,45 @@ def test_autotune_then_launches_stay_exact(ctx, n, p, k):
     ref = oracle_tabu_many([(adj, k, start[0], iters, 6, 0, 0, False)])[0]
     assert bf[0].item() == ref["best_f"] and mv[0].item() == ref["moves"]
     assert np.array_equal(col[0].cpu().numpy(), ref["best_col"])
+
+
+def test_multi_full_workload_sampled(ctx):
+    """The uneven workload as the bench runs it: 64 graphs (n in [100, 1000], k = n/10), 256
+    individuals each, 128 n iterations, one persistent launch replayed from a captured plan.
+    Every returned conflict count recounts from its colouring, and two individuals of each of
+    the four smallest graphs equal the oracle over the whole budget."""
+    specs = inputs.uneven_batch(64, seed=0)
+    graphs = [device_graph(ctx, s["n"], s["edges"]) for s in specs]
+    ks = [s["k"] for s in specs]
+    pops = [256] * len(specs)
+    iters = [128 * s["n"] for s in specs]
+    starts, cols, bfs, mvs = [], [], [], []
+    base = 0
+    for g, (s, k, p) in enumerate(zip(specs, ks, pops)):
+        c = torch.empty((p, s["n"]), dtype=torch.int16, device="cuda")
+        dlmcol.dlm_init_colors(ctx, s["n"], k, p, 0, base, c)
+        starts.append(c.cpu().numpy())
+        cols.append(c)
+        bfs.append(torch.zeros(p, dtype=torch.int64, device="cuda"))
+        mvs.append(torch.zeros(p, dtype=torch.int64, device="cuda"))
+        base += p
+    plan = dlmcol.MultiPlan(ctx, graphs, ks, pops, cols, bfs, mvs, iters, dlmcol.COL_TENURE, 0, 0, 0)
+    dlmcol.dlm_tabucol_multi_plan_launch(ctx, plan)
+    ctx.sync()
+    for g, (s, k, p) in enumerate(zip(specs, ks, pops)):
+        f = torch.zeros(p, dtype=torch.int64, device="cuda")
+        dlmcol.dlm_gamma(ctx, graphs[g], k, p, cols[g], None, f)
+        ctx.sync()
+        assert torch.equal(f, bfs[g]), g
+    small = sorted(range(len(specs)), key=lambda g: specs[g]["n"])[:4]
+    jobs = []
+    for g in small:
+        adj = inputs.edges_to_adj(specs[g]["n"], specs[g]["edges"])
+        gbase = 256 * g
+        for i in (0, 255):
+            jobs.append((g, i, (adj, ks[g], starts[g][i], iters[g], 0, gbase + i, 0, False)))
+    refs = oracle_tabu_many([j for _, _, j in jobs])
+    for (g, i, _), r in zip(jobs, refs):
+        assert bfs[g][i].item() == r["best_f"] and mvs[g][i].item() == r["moves"], (g, i)
+        assert np.array_equal(cols[g][i].cpu().numpy(), r["best_col"]), (g, i)
+    plan.close()

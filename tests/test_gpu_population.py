@@ -134,3 +134,38 @@ def test_knn_rejects_bad_k(ctx):
     nbr = torch.zeros((4, 4), dtype=torch.int32, device="cuda")
     with pytest.raises(dlmcol.DlmError):
         dlmcol.dlm_knn(ctx, 4, D, 4, nbr)
+
+
+def test_distance_and_gpx_full_size_sampled(ctx):
+    """The learned workload's sizes, in the launches the population bench times: P x P' and the
+    upper triangle of P' x P' over 8192 colourings each (n = 1000, k = 48), and GPX for
+    8192 x 32 parent pairs. Sampled rows of D and sampled children equal the oracle's."""
+    n, k, p, K = 1000, 48, 8192, 32
+    P = inputs.random_colorings(p, n, k, seed=21)
+    Sp = inputs.random_colorings(p, n, k, seed=22)
+    Sp[5] = P[7]  # a zero distance inside the sampled rows
+    m = 2 * p
+    dP, dSp = _cuda(P), _cuda(Sp)
+    D = torch.full((m, m), -1, dtype=torch.int16, device="cuda")
+    dlmcol.dlm_distance_batch(ctx, n, k, dP, p, dSp, p, D[:, p:], m, 0)
+    dlmcol.dlm_distance_batch(ctx, n, k, dSp, p, dSp, p, D[p:, p:], m, 1)
+    ctx.sync()
+    rows = [0, 7, 4095, p - 1]
+    for i in rows:
+        got = D[i, p:].cpu().numpy()
+        assert np.array_equal(got, oracle.distance_matrix(k, P[i:i + 1], Sp)[0]), i
+        assert got[5] == 0 or i != 7
+        up = D[p + i, p:].cpu().numpy()
+        ref = oracle.distance_matrix(k, Sp[i:i + 1], Sp)[0]
+        assert np.array_equal(up[i + 1:], ref[i + 1:]), i
+        assert np.all(up[: i + 1] == -1), i
+    # GPX: child t = i K + j of parents (i, nbr[i][j]) with random neighbours
+    rng = np.random.default_rng(23)
+    nbr = rng.integers(0, p, size=(p, K)).astype(np.int32)
+    pairs = np.stack([np.repeat(np.arange(p, dtype=np.int32), K), nbr.reshape(-1)], 1)
+    kids = torch.zeros((p * K, n), dtype=torch.int16, device="cuda")
+    dlmcol.dlm_gpx_batch(ctx, n, k, dP, p, _cuda(pairs), None, p * K, kids, 31, 2)
+    ctx.sync()
+    for t in [0, 1, 31, 32, 131071, 200003, p * K - 1]:
+        ref = oracle.gpx(k, P[pairs[t, 0]], P[pairs[t, 1]], seed=31, child_id=t, gen=2)
+        assert np.array_equal(kids[t].cpu().numpy(), ref), t
