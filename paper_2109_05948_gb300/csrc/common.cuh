@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -145,5 +146,15 @@ inline dlm_status ctx_workspace(dlm_ctx* ctx, size_t bytes, void** out) {
 inline dlm_status launch_check(dlm_ctx* ctx, const char* what) {
   return cuda_check(ctx, cudaGetLastError(), what);
 }
+
+// A kernel attribute (such as its dynamic shared-memory limit) belongs to one device: the devices
+// (0..63) on which a call site has set it; devices beyond 63 set it on every call.
+struct PerDeviceOnce {
+  std::atomic<uint64_t> done{0};
+  bool need(int device) const { return device < 0 || device >= 64 || !((done.load() >> device) & 1u); }
+  void mark(int device) {
+    if (device >= 0 && device < 64) done.fetch_or(1ull << device);
+  }
+};
 
 }  // namespace dlm

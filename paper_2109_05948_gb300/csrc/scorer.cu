@@ -887,10 +887,10 @@ static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K
   // persistent: one CTA per SM (TMEM holds two BN-column accumulators), looping over the tiles
   const int tiles = ((M + tc::BM - 1) / tc::BM) * (N / BN) * ((nchunks + kc - 1) / kc);
   dim3 grid(std::min(tiles, ctx->num_sms));
-  auto launch = [&](auto kfn, size_t smem, bool& attr) -> dlm_status {
-    if (!attr) {
+  auto launch = [&](auto kfn, size_t smem, PerDeviceOnce& attr) -> dlm_status {
+    if (attr.need(ctx->device)) {
       DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr = true;
+      attr.mark(ctx->device);
     }
     dlm_ctx::GemmRec rec{nullptr, nullptr, 0.0};
     if (ctx->gemm_prof && cudaEventCreate(&rec.a) == cudaSuccess && cudaEventCreate(&rec.b) == cudaSuccess) {
@@ -906,18 +906,18 @@ static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K
     return launch_check(ctx, "gemm_kernel");
   };
   if (A2 && B2) {
-    static bool attr = false;
+    static PerDeviceOnce attr;
     return launch(tc::gemm_kernel<BN, S2, 2, 2, Epi>, tc::gemm_smem_bytes<BN, S2, 2, 2>(), attr);
   }
   if (A2) {
-    static bool attr = false;
+    static PerDeviceOnce attr;
     return launch(tc::gemm_kernel<BN, S2, 2, 1, Epi>, tc::gemm_smem_bytes<BN, S2, 2, 1>(), attr);
   }
   if (B2) {
-    static bool attr = false;
+    static PerDeviceOnce attr;
     return launch(tc::gemm_kernel<BN, S2, 1, 2, Epi>, tc::gemm_smem_bytes<BN, S2, 1, 2>(), attr);
   }
-  static bool attr = false;
+  static PerDeviceOnce attr;
   return launch(tc::gemm_kernel<BN, S4, 1, 1, Epi>, tc::gemm_smem_bytes<BN, S4, 1, 1>(), attr);
 }
 
@@ -1295,10 +1295,10 @@ extern "C" dlm_status dlm_scorer_train(dlm_ctx* ctx, dlm_scorer* s, const int16_
   DLM_TRY(launch_check(ctx, "k_standardise"));
   int mp = 1;
   while (mp < p) mp <<= 1;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.need(ctx->device)) {
     DLM_CUDA(ctx, cudaFuncSetAttribute(k_epoch_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8));
-    attr = true;
+    attr.mark(ctx->device);
   }
   if (!s->d_step) {
     DLM_TRY(dalloc(ctx, &s->d_step, 2));
