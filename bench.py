@@ -138,11 +138,12 @@ def oracle_sample(n_ind: int, iters: int):
 
 
 def cpu_baseline(args):
-    n_ind = min(16, os.cpu_count() or 1)
+    # two individuals per host core (at most 32): about 10-15 s of CPU work at the full budget
+    n_ind = 2 * min(16, os.cpu_count() or 1)
     moves, wall, procs, cpu_s = oracle_sample(n_ind, args.iters)
     return {"value": moves / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"{n_ind} individuals x {args.iters} iterations of the same workload, one spawned "
-                      f"process per individual on {procs} host cores ({cpu_s:.1f} s of CPU work)"}
+            "sample": f"{n_ind} individuals x {args.iters} iterations of the same workload on {procs} spawned "
+                      f"worker processes, one per host core ({cpu_s:.1f} s of CPU work)"}
 
 
 def run_reference(args):
