@@ -4,9 +4,14 @@
 // AFISA_score, Eq. score_WVCP), run on every individual of a population.
 //
 // GB300 design of the tabu search (one CTA per individual, persistent over the population):
-//  * every one-move (v, c) of every vertex is evaluated each iteration (n * k pairs, ~115 000 at
-//    n = 1000): delta = rem(v) + max(0, w_v - max1[c]) + phi (gamma[v][c] - gamma[v][col v]),
-//    rem(v) the drop of v's class maximum when v leaves it;
+//  * every one-move (v, c) of every vertex is a candidate each iteration (n * k pairs, ~145 000
+//    at n = 1000): delta = rem(v) + max(0, w_v - max1[c]) + phi (gamma[v][c] - gamma[v][col v]),
+//    rem(v) the drop of v's class maximum when v leaves it. Each row v keeps a summary of its
+//    colour keys max(0, w_v - max1[c]) + phi gamma[v][c] over c != col v (their minimum and how
+//    many reach it); the selection reads one summary per row. A move from colour a to b changes
+//    only the keys of colours a and b (gamma of the neighbours, the two class maxima), which
+//    update the summaries in O(1) per row; a row whose only minimum key rose, and the moved
+//    vertex's row, are scanned again;
 //  * gamma is stored transposed, gT[c][v] (u16), so that thread t scanning vertices t, t + 512, ...
 //    reads consecutive addresses across the warp; the first Cs colours live in shared memory, the
 //    rest in an L2-resident slab of global memory owned by the CTA (n * k * 2 bytes exceeds one
@@ -27,7 +32,7 @@ constexpr int kWThreads = 512;
 constexpr int kWWarps = kWThreads / 32;
 
 struct WvcpLayout {
-  size_t col, best, w, fz, lvl, lmask, info, max1, rmin, rcnt, red, gT, total;
+  size_t col, best, w, fz, lvl, lmask, info, max1, rmin, rcnt, skey, scnt, red, gT, total;
   int npad, lw, cs;  // vertices padded to 8, mask words per class, colours held in shared memory
 };
 
@@ -49,7 +54,9 @@ __host__ __device__ inline WvcpLayout wvcp_layout(int n, int k, int wmax, size_t
   L.max1 = o; o += wal16((size_t)k);
   L.rmin = o; o += wal16((size_t)n * 4);
   L.rcnt = o; o += wal16((size_t)n * 2);
-  L.red = o; o += 1024;  // 2 kWWarps + 8 ints, then 8 + 2 kWWarps long longs
+  L.skey = o; o += wal16((size_t)n * 4);
+  L.scnt = o; o += wal16((size_t)n * 2);
+  L.red = o; o += 1024;  // 2 kWWarps + 8 ints, then 8 + 2 kWWarps long longs; 2 ints at byte 896
   L.gT = o;
   const size_t per_col = (size_t)L.npad * 2;
   size_t cs = budget > o ? (budget - o) / per_col : 0;
@@ -116,6 +123,52 @@ __device__ __forceinline__ void wvcp_scan_key(int c, int o, int wv, int m1c, int
   else if (key == km && key != INT_MAX) ++kc;
 }
 
+// key of colour c for row v: the weight term of joining class c plus phi times gamma[v][c]
+__device__ __forceinline__ int wvcp_key(int fs, int wv, int m1c, int phi, int gc) {
+  return fs * (wv > m1c ? wv - m1c : 0) + phi * gc;
+}
+
+// a key of a row changed from kold to knew: update the row's (minimum, count); false when the
+// key was the row's only minimum and rose (the row must be scanned again)
+__device__ __forceinline__ bool wvcp_summ_apply(int& km, int& kc, int kold, int knew) {
+  if (knew == kold) return true;
+  if (knew < kold) {
+    if (knew < km) { km = knew; kc = 1; }
+    else if (knew == km) ++kc;
+    return true;
+  }
+  if (kold == km) {
+    if (kc > 1) { --kc; return true; }
+    return false;
+  }
+  return true;
+}
+
+// minimum key of row v over the colours c != o and how many colours reach it (in colour order:
+// the shared-memory colours, then the slab colours sixteen loads at a time)
+__device__ __forceinline__ void wvcp_row_summary(int v, int o, int wv, const uint8_t* max1s, const uint16_t* gS,
+                                                 const uint16_t* gG, int npad, int cs, int k, int fs, int phi,
+                                                 int& km, int& kc) {
+  km = INT_MAX;
+  kc = 0;
+  auto take = [&](int c, int gc) {
+    if (c == o) return;
+    const int key = wvcp_key(fs, wv, max1s[c], phi, gc);
+    if (key < km) { km = key; kc = 1; }
+    else if (key == km) ++kc;
+  };
+  for (int c = 0; c < cs; ++c) take(c, gS[(size_t)c * npad + v]);
+  int c = cs;
+  for (; c + 16 <= k; c += 16) {
+    int q16[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) q16[q] = gG[(size_t)(c + q - cs) * npad + v];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) take(c + q, q16[q]);
+  }
+  for (; c < k; ++c) take(c, gG[(size_t)(c - cs) * npad + v]);
+}
+
 __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int n = a.n, k = a.k, wmax = a.wmax, nwords = a.words;
@@ -131,6 +184,9 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   uint8_t* max1s = smem + L.max1;
   int32_t* rmin = (int32_t*)(smem + L.rmin);
   uint16_t* rcnt = (uint16_t*)(smem + L.rcnt);
+  int32_t* skey = (int32_t*)(smem + L.skey);   // per row: minimum key over the colours c != col v
+  uint16_t* scnt = (uint16_t*)(smem + L.scnt); // per row: colours reaching it
+  int32_t* sx = (int32_t*)(smem + L.red + 896); // class maxima of the move's two colours before it
   int32_t* red = (int32_t*)(smem + L.red);  // [kWWarps] warp minima, [kWWarps] warp tie totals
   int32_t* sc = red + 2 * kWWarps;          // mv, old, new, improved, error, bad input, r0, r1
   // g, conf, best g, best f, best conf; from 8: per-warp conflict and score partial sums
@@ -230,6 +286,13 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
     }
     __syncthreads();
     long long g = sc64[0], conf = sc64[1], best_g = sc64[2];
+    for (int v = tid; v < n; v += kWThreads) {  // every row's key summary at the start colouring
+      int km, kc;
+      wvcp_row_summary(v, colS[v], wS[v], max1s, gS, gG, npad, cs, k, fs, (int)phi, km, kc);
+      skey[v] = km;
+      scnt[v] = (uint16_t)kc;
+    }
+    __syncthreads();
     int64_t moves = 0;
     int32_t* trace = a.trace ? a.trace + (size_t)ind * a.iters * 4 : nullptr;
     for (int64_t it = 0; it < a.iters; ++it) {
@@ -240,58 +303,22 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         sc[7] = (int32_t)r.y;
         sc[0] = -1;
       }
-      // ---- phase 1: every one-move of the thread's vertices -----------------------------------
+      // ---- phase 1: the best one-move of every row from its key summary ------------------------
+      // d = rem(v) fs - phi gamma[v][col v] + key; a frozen vertex's moves count only when they
+      // reach below the aspiration threshold (all its tied moves have the same d)
       const long long thr64 = best_g - g;
       const int thr = thr64 < (long long)INT_MIN + 1 ? INT_MIN + 1 : (int)thr64;
       int tmin = INT_MAX;
-      // two vertices per pass (v and v + kWThreads): two independent min/count chains share the
-      // class-maximum loads
-      for (int v = tid; v < n; v += 2 * kWThreads) {
-        const int vb = v + kWThreads < n ? v + kWThreads : v;  // second vertex (a duplicate when none)
-        const int oa = colS[v], wa = wS[v], ob = colS[vb], wb = wS[vb];
-        const uint32_t ia = info[oa], ib = info[ob];
-        const int rema = (wa == (int)(ia & 0xFF) && (ia >> 16) == 1) ? (int)((ia >> 8) & 0xFF) - (int)(ia & 0xFF) : 0;
-        const int remb = (wb == (int)(ib & 0xFF) && (ib >> 16) == 1) ? (int)((ib >> 8) & 0xFF) - (int)(ib & 0xFF) : 0;
-        const int g0a = oa < cs ? gS[(size_t)oa * npad + v] : gG[(size_t)(oa - cs) * npad + v];
-        const int g0b = ob < cs ? gS[(size_t)ob * npad + vb] : gG[(size_t)(ob - cs) * npad + vb];
-        const bool fra = fz[v] > itrel, frb = fz[vb] > itrel;
-        const int basea = fs * rema - (int)phi * g0a, baseb = fs * remb - (int)phi * g0b;
-        int kma = INT_MAX, kca = 0, kmb = INT_MAX, kcb = 0;
-#pragma unroll 4
-        for (int c = 0; c < cs; ++c) {
-          const int m1 = max1s[c];
-          wvcp_scan_key(c, oa, wa, m1, basea, phi, gS[(size_t)c * npad + v], fra, thr, kma, kca, fs);
-          wvcp_scan_key(c, ob, wb, m1, baseb, phi, gS[(size_t)c * npad + vb], frb, thr, kmb, kcb, fs);
-        }
-        // the slab colours come from L2: 16 independent loads per vertex in flight before use
-        int c = cs;
-        for (; c + 16 <= k; c += 16) {
-          int qa[16], qb[16];
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            qa[q] = gG[(size_t)(c + q - cs) * npad + v];
-            qb[q] = gG[(size_t)(c + q - cs) * npad + vb];
-          }
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int m1 = max1s[c + q];
-            wvcp_scan_key(c + q, oa, wa, m1, basea, phi, qa[q], fra, thr, kma, kca, fs);
-            wvcp_scan_key(c + q, ob, wb, m1, baseb, phi, qb[q], frb, thr, kmb, kcb, fs);
-          }
-        }
-        for (; c < k; ++c) {
-          const int m1 = max1s[c];
-          wvcp_scan_key(c, oa, wa, m1, basea, phi, gG[(size_t)(c - cs) * npad + v], fra, thr, kma, kca, fs);
-          wvcp_scan_key(c, ob, wb, m1, baseb, phi, gG[(size_t)(c - cs) * npad + vb], frb, thr, kmb, kcb, fs);
-        }
-        rmin[v] = kma;
-        rcnt[v] = (uint16_t)(kma == INT_MAX ? 0 : kca);
-        tmin = min(tmin, kma);
-        if (vb != v) {
-          rmin[vb] = kmb;
-          rcnt[vb] = (uint16_t)(kmb == INT_MAX ? 0 : kcb);
-          tmin = min(tmin, kmb);
-        }
+      for (int v = tid; v < n; v += kWThreads) {
+        const int o = colS[v], wv = wS[v];
+        const uint32_t io = info[o];
+        const int rem = (wv == (int)(io & 0xFF) && (io >> 16) == 1) ? (int)((io >> 8) & 0xFF) - (int)(io & 0xFF) : 0;
+        const int g0 = o < cs ? gS[(size_t)o * npad + v] : gG[(size_t)(o - cs) * npad + v];
+        const int d = fs * rem - (int)phi * g0 + skey[v];
+        const bool ok = !(fz[v] > itrel) || d < thr;
+        rmin[v] = ok ? d : INT_MAX;
+        rcnt[v] = ok ? scnt[v] : (uint16_t)0;
+        tmin = min(tmin, ok ? d : INT_MAX);
       }
       {
         const int wm = __reduce_min_sync(0xFFFFFFFFu, tmin);
@@ -351,6 +378,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
             const int o = colS[mv], wv = wS[mv];
             const int go = o < cs ? gS[(size_t)o * npad + mv] : gG[(size_t)(o - cs) * npad + mv];
             const int gn = mc < cs ? gS[(size_t)mc * npad + mv] : gG[(size_t)(mc - cs) * npad + mv];
+            sx[0] = max1s[o];
+            sx[1] = max1s[mc];
             class_add(lvl, lmask, lw, wmax, o, wv, -1);
             class_add(lvl, lmask, lw, wmax, mc, wv, +1);
             info[o] = class_info(lvl, lmask, lw, wmax, o);
@@ -385,13 +414,35 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         uint16_t* po = old < cs ? gS + (size_t)old * npad : gG + (size_t)(old - cs) * npad;
         uint16_t* pn = nw < cs ? gS + (size_t)nw * npad : gG + (size_t)(nw - cs) * npad;
         const uint32_t* brow = a.bits + (size_t)mv * nwords;
+        const int m1a_old = sx[0], m1b_old = sx[1], m1a = max1s[old], m1b = max1s[nw], ph = (int)phi;
         for (int b0 = tid * per; b0 < n; b0 += kWThreads * per) {
-          uint32_t m = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
+          const uint32_t nb = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
+          uint32_t m = nb;
           while (m) {
             const int u = b0 + __ffs(m) - 1;
             m &= m - 1;
             po[u]--;
             pn[u]++;
+          }
+          // the key summaries of this thread's rows: colours old and nw changed (gamma of the
+          // neighbours, both class maxima); the moved vertex's row is scanned again
+          const int e = min(b0 + per, n);
+          for (int u = b0; u < e; ++u) {
+            const int cu = colS[u], wu = wS[u];
+            int km = skey[u], kc = scnt[u];
+            bool ok = u != mv;
+            const int adj = (int)((nb >> (u - b0)) & 1u);
+            if (ok && old != cu) {
+              const int gnew = po[u];
+              ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1a_old, ph, gnew + adj), wvcp_key(fs, wu, m1a, ph, gnew));
+            }
+            if (ok && nw != cu) {
+              const int gnew = pn[u];
+              ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1b_old, ph, gnew - adj), wvcp_key(fs, wu, m1b, ph, gnew));
+            }
+            if (!ok) wvcp_row_summary(u, cu, wu, max1s, gS, gG, npad, cs, k, fs, ph, km, kc);
+            skey[u] = km;
+            scnt[u] = (uint16_t)kc;
           }
         }
         if (improved) {
