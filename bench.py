@@ -563,6 +563,31 @@ def measured_peaks():
         return {}
 
 
+def pool_work(p: int, fit, sel, close_to_earlier):
+    """Work of the pool update's greedy visit, reconstructed from its inputs and output: the number
+    of candidates it examined and the number of (examined candidate, member kept before it) checks,
+    each one entry of D. sel lists the greedily kept members in increasing (f, index) rank, then
+    any fill; close_to_earlier[j] says whether sel[j] is within n/10 of some sel[i], i < j. A fill
+    member is within n/10 of an earlier kept one, so the greedy prefix of sel ends at the first
+    member that breaks the rank order or is close to an earlier member. The visit examines
+    candidates until p are kept (all 2p when it falls short)."""
+    import numpy as np
+
+    m = 2 * p
+    order = np.lexsort((np.arange(m), fit))
+    rank = np.empty(m, np.int64)
+    rank[order] = np.arange(m)
+    r = rank[np.asarray(sel)]
+    brk = np.array(close_to_earlier, dtype=bool, copy=True)
+    brk[1:] |= np.diff(r) <= 0
+    g_len = int(np.argmax(brk)) if brk.any() else p
+    kept = np.zeros(m, bool)
+    kept[np.asarray(sel)[:g_len]] = True
+    before = np.concatenate([[0], np.cumsum(kept[order])[:-1]])
+    stop = int(np.searchsorted(before, p)) if g_len >= p else m
+    return stop, int(before[:stop].sum())
+
+
 def run_population(args):
     """Population management and crossover of one generation at the planted n = 1000, k = 48,
     p = 8192, K = 32 size (sections "Distance computation", "Population update", "Parent matching
@@ -571,7 +596,6 @@ def run_population(args):
     pairs. The colourings are TabuCol results (2 |V| iterations from random starts), so the
     overlap tables look like those of a running search. Each kernel is timed with CUDA events on
     the context's stream; value = distance pairs per second (the dominant kernel)."""
-    import numpy as np
     import torch
 
     from paper_2109_05948_gb300 import build as libbuild
@@ -645,27 +669,10 @@ def run_population(args):
         hbm, hbm_src = 6800.0, "of fallback"
     smem = dlmcol.dlm_probe_smem_bandwidth(ctx)
     smem_src = "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads)"
-    # examined candidates of the pool update and the admitted-list length each one is checked
-    # against (the entries of D it reads), reconstructed on the host from its inputs and output.
-    # sel lists the greedily admitted members in increasing (f, index) rank, then any fill; a fill
-    # member is within n / 10 of an earlier admitted one, so the greedy prefix ends at the first
-    # member that breaks the rank order or is close to an earlier member. The greedy pass examines
-    # candidates until p are admitted (all 2p when it falls short).
     f_np, s_np = fit.cpu().numpy(), sel.cpu().numpy()
-    order = np.lexsort((np.arange(m), f_np))
-    rank = np.empty(m, np.int64)
-    rank[order] = np.arange(m)
-    r = rank[s_np]
     close = (10 * DP.int() <= n) & torch.tril(torch.ones((p, p), dtype=torch.bool, device=dev), -1)
-    brk = close.any(dim=1).cpu().numpy()
-    brk[1:] |= np.diff(r) <= 0
-    g_len = int(np.argmax(brk)) if brk.any() else p
+    stop, pool_entries = pool_work(p, f_np, s_np, close.any(dim=1).cpu().numpy())
     del close
-    admitted = np.zeros(m, bool)
-    admitted[s_np[:g_len]] = True
-    before = np.concatenate([[0], np.cumsum(admitted[order])[:-1]])
-    stop = int(np.searchsorted(before, p)) if g_len >= p else m
-    pool_entries = int(before[:stop].sum())
 
     def roof(bound, alg_bytes, t_ms, peak, src):
         a = alg_bytes / (t_ms / 1e3) / 1e9
