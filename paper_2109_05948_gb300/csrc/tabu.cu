@@ -19,8 +19,8 @@
 //  * update: each thread changes gamma on its vertices adjacent to the moved vertex (bit row of
 //    the graph, L1/L2 resident) and adjusts their summaries in O(1); rows whose class minimum may
 //    have risen, the moved vertex and rows with an expiring tabu colour are summarised again by
-//    the owner's warp (lanes over colours).
-//  Three CTA barriers per iteration.
+//    the owner's warp (lanes over colours); the next iteration's selection follows in the same
+//    phase. Two CTA barriers per iteration.
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -173,14 +173,17 @@ __device__ __forceinline__ bool summ_raise(Summ& s, bool tabu, unsigned g) {
 // (Summ); a row's neighbourhood is evaluated from its summary in O(1) instead of a scan of its k
 // colours. Per iteration:
 //  (A) selection: each thread evaluates its conflicting vertices from their summaries (minimum
-//      delta and number of admissible colours reaching it), warps reduce, one barrier;
+//      delta and number of admissible colours reaching it), warps reduce; it runs at the end of
+//      phase (C) of the previous iteration (its inputs come from the thread's own warp), and one
+//      barrier follows;
 //  (B) every warp derives (warp collectives) the minimum delta, the tie total T and its rank range; the warp
 //      holding the j-th tie (j drawn from the iteration's Philox block) finds the vertex and,
 //      with ballots over that row, the colour, and applies the move; one barrier;
 //  (C) each thread updates gamma on its vertices adjacent to the moved vertex and adjusts their
 //      summaries in O(1); a row whose class minimum may have risen, the moved vertex's row and
 //      rows whose earliest tabu expiry falls at the next iteration are flagged by their owner
-//      thread, and the owner's warp summarises them again (lanes over colours); one barrier.
+//      thread, and the owner's warp summarises them again (lanes over colours), then (A) of the
+//      next iteration.
 // The Philox blocks of 32 iterations are drawn at once, one per lane, every 32 iterations.
 //
 // Tabu list: u16 expiries relative to a base that advances by 2^14 every 2^14 iterations
