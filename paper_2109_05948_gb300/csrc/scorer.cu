@@ -12,13 +12,16 @@
 // Where the work runs:
 //   tcgen05 BF16 GEMMs (FP32 accumulate in TMEM): H Lambda for layers 1..3 (fused epilogue:
 //     + per-candidate (rho Gamma + beta), LeakyReLU, row mask, bf16 store, head dot product),
-//     the backward dH = dZ Lambda^T (fused: + per-candidate term, LeakyReLU derivative, row mask)
-//     and the weight gradients dLambda = H^T dZ (split-K). Lambda enters as two bf16 matrices
-//     (hi + lo): two MMAs per K step keep the weights at ~16 mantissa bits, since rounding the
-//     weights to bf16 shifts every row of a layer the same way and dominates the error.
+//     the backward dH = dZ Lambda^T (fused: + per-candidate term, LeakyReLU derivative, row mask),
+//     the weight gradients dLambda = H^T dZ (split-K) and, for scoring chunks, the per-candidate
+//     rho(H) Gamma terms (both operands split). Lambda enters as two bf16 matrices (hi + lo):
+//     two MMAs per K step keep the weights at ~16 mantissa bits, since rounding the weights to
+//     bf16 shifts every row of a layer the same way and dominates the error.
 //   CUDA cores (FP32): the class pooling of layer 0 (a gather, not a contraction), per-candidate
-//     means and column sums, the per-candidate rho(H) Gamma terms (one row per candidate, 1/64 of
-//     the layer's work), the embedding gradient (scatter by colour), Adam.
+//     means and column sums, the rho(H) Gamma terms of small and training batches (fused into
+//     the pooling and the class-mean kernels), the embedding gradient (scatter by colour), Adam
+//     (which also writes the bf16 operand copies). A training step is 26 launches replayed from
+//     a CUDA graph.
 // All reductions run in a fixed order: results are deterministic run to run.
 #include <cuda_bf16.h>
 
