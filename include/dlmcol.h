@@ -115,11 +115,15 @@ typedef struct {
  *   best_f  device [pop] int64 out: conflicts of that colouring.
  *   moves   device [pop] int64 out (or NULL): iterations that made a move.
  *   iters   iteration budget per individual (paper: 128 |V|).
- * State: one CTA per individual holds gamma and the tabu list (about 4 n k bytes) in shared memory;
- * when they do not fit (e.g. n = 1000, k = 100), the rows that do not fit live in a per-CTA slab of
- * global memory owned by the context (L2 resident) and resident CTAs loop over the individuals.
- * Limits: k <= 128 (DLM_EUNSUPPORTED above). Tenures above 32766 iterations stop the search with
- * DLM_EUNSUPPORTED at dlm_sync. */
+ * State: each individual's conflict table gamma (2 n k bytes, the tabu flag of every (v, c) in its
+ * top bit), row summaries and a ring of tabu entries live in shared memory, several individuals
+ * per CTA sharing the graph's bit rows; tabu entries whose tenure does not fit the ring go to a
+ * per-individual list in the context's workspace. When one individual's gamma does not fit in
+ * shared memory (n k above about 110 000), the search runs one individual per CTA with a separate
+ * expiry table, its last rows in a per-CTA slab of global memory (L2 resident).
+ * Limits: k <= 128 (DLM_EUNSUPPORTED above); iters + L_max + alpha_num |E| / alpha_den below 2^32
+ * (DLM_EUNSUPPORTED); on the one-individual-per-CTA path, tenures above 32766 iterations stop the
+ * search with DLM_EUNSUPPORTED at dlm_sync. */
 dlm_status dlm_tabucol_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                              int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                              uint32_t generation, uint32_t ind_base);
@@ -135,6 +139,21 @@ dlm_status dlm_tabucol_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
                                 int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                                 uint32_t generation, uint32_t ind_base, int32_t warps_per_individual,
                                 int32_t* trace, int64_t* work);
+
+/* Launch options of dlm_tabucol_batch_opts (all zero = the library's choice). */
+typedef struct {
+  int32_t warps_per_individual; /* 1, 2, 4, 8, 16 or 32; 0 = autotuned or default */
+  int32_t ring;                 /* tabu ring entries per individual: a power of two in 64..8192, or 0 =
+                                   the largest that fits beside the most individuals per CTA; entries
+                                   with longer tenures go to the global list (tests use small rings) */
+  int32_t legacy;               /* 1 = one individual per CTA with an expiry table (the spill path) */
+} dlm_tabu_opts;
+
+/* dlm_tabucol_batch_ex with launch options (opts may be NULL); same results for every option. */
+dlm_status dlm_tabucol_batch_opts(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                  int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
+                                  uint32_t generation, uint32_t ind_base, const dlm_tabu_opts* opts,
+                                  int32_t* trace, int64_t* work);
 
 /* Uneven batch: several graphs, each with its own k, population and budget, in one persistent
  * launch (individuals ordered by decreasing work and handed to resident blocks from a device

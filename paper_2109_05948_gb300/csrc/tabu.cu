@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tabu_group.cuh"
 
 namespace dlm {
 
@@ -669,17 +670,41 @@ static dlm_status tabucol_check(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
   return DLM_OK;
 }
 
+// default warps per individual of the grouped kernel: the fewest (at least 2) that give each
+// thread at most 4 vertices
+static int default_group_warps(int n) {
+  int w = 2;
+  while (w < 16 && 32 * w * 4 < n) w *= 2;
+  return w;
+}
+
 static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                               int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                               uint32_t generation, uint32_t ind_base, int warps, int32_t* trace,
-                              int64_t* work) {
+                              int64_t* work, int ring = 0, int legacy = 0) {
   DLM_TRY(tabucol_check(ctx, g, k, pop, iters, tenure));
   if (pop == 0) return DLM_OK;
   if (!col || !best_f) return fail(ctx, DLM_EINVAL, "tabucol: null col or best_f");
   if (warps == 0) warps = lookup_tune(ctx, g->n, k);
-  if (warps == 0) warps = default_warps_batch(ctx, g->n, k);
-  if (warps != 1 && warps != 2 && warps != 4 && warps != 8 && warps != 16 && warps != 32)
+  if (warps != 0 && warps != 1 && warps != 2 && warps != 4 && warps != 8 && warps != 16 && warps != 32)
     return fail(ctx, DLM_EINVAL, "tabucol: warps per individual must be 1, 2, 4, 8, 16 or 32");
+  if (ring != 0 && (ring < 64 || ring > 8192 || (ring & (ring - 1)) != 0))
+    return fail(ctx, DLM_EINVAL, "tabucol: the tabu ring size must be a power of two in 64..8192");
+  if (!legacy) {
+    // several individuals per CTA, tabu flags inside gamma: whenever one individual's state fits
+    const int wg = warps ? warps : default_group_warps(g->n);
+    GroupPlan P;
+    if (group_plan(g->n, k, g->words, wg, ctx->smem_optin, pop, ctx->num_sms, ring, &P)) {
+      const uint64_t tt_max =
+          (uint64_t)tenure.L_max + ((uint64_t)tenure.alpha_num * (uint64_t)g->m) / (uint64_t)tenure.alpha_den;
+      if ((uint64_t)iters + tt_max + 2 >= (1ull << 32))
+        return fail(ctx, DLM_EUNSUPPORTED, "tabucol: budget plus the longest tenure must stay below 2^32");
+      return tabucol_group_launch(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base, P,
+                                  trace, work);
+    }
+    if (ring) return fail(ctx, DLM_EINVAL, "tabucol: the requested tabu ring does not fit in shared memory");
+  }
+  if (warps == 0) warps = default_warps_batch(ctx, g->n, k);
   const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
   if (L.rs < 1 || L.total > ctx->smem_optin)
     return fail(ctx, DLM_EUNSUPPORTED, "tabucol: the per-individual arrays exceed shared memory per block");
@@ -718,6 +743,15 @@ extern "C" dlm_status dlm_tabucol_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int
                                            int32_t warps_per_individual, int32_t* trace, int64_t* work) {
   return tabucol_run(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base,
                      warps_per_individual, trace, work);
+}
+
+extern "C" dlm_status dlm_tabucol_batch_opts(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                             int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure,
+                                             uint64_t seed, uint32_t generation, uint32_t ind_base,
+                                             const dlm_tabu_opts* opts, int32_t* trace, int64_t* work) {
+  const dlm_tabu_opts o = opts ? *opts : dlm_tabu_opts{0, 0, 0};
+  return tabucol_run(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base,
+                     o.warps_per_individual, trace, work, o.ring, o.legacy);
 }
 
 extern "C" dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,

@@ -1,0 +1,60 @@
+// TabuCol with several individuals per CTA (tabu_group.cu): launch arguments, shared-memory plan.
+#pragma once
+
+#include "common.cuh"
+
+namespace dlm {
+
+// gamma row stride in u16 entries: ks / 2 odd, so that rows of different vertices start in
+// different shared-memory banks
+__host__ __device__ inline int group_row_stride(int k) {
+  int kw = (k + 1) / 2;
+  if ((kw & 1) == 0) kw += 1;
+  return 2 * kw;
+}
+
+// byte offsets of one individual's arrays within its group's shared memory
+struct GroupLayout {
+  size_t gam, rec, g0, col, best, dirty, nb, ring, due, red, sc, total;
+};
+
+struct GroupArgs {
+  int32_t n, k, ks, words, pop, G, R, per;
+  const uint32_t* bits;  // device [n][words] adjacency bit rows
+  int16_t* col;          // [pop][n] in: start colourings, out: best colourings
+  int64_t* best_f;       // [pop]
+  int64_t* moves;        // [pop] or null
+  int32_t* trace;        // [pop][iters][4] or null
+  int64_t* work;         // [pop][3] or null
+  int64_t iters;
+  uint32_t ind_base;
+  uint32_t L1;           // L_max + 1
+  int32_t an, ad;        // alpha = an / ad
+  uint64_t seed;
+  uint32_t gen;
+  int32_t* status;
+  const int32_t* cancel;
+  uint2* far;            // per slot far_cap entries, or null
+  int32_t far_cap;
+  size_t group_bytes, bits_bytes;
+};
+
+// W warps per individual, G individuals per CTA, ring of R tabu entries, per vertices a thread,
+// the graph's bit rows in shared memory (bsm) or read from global memory
+struct GroupPlan {
+  int W, G, R, per;
+  bool bsm;
+  size_t group_bytes, bits_bytes, smem;
+};
+
+// Shared-memory plan for n vertices, k colours, W warps per individual within `optin` bytes
+// (ring_force > 0 forces the ring size); false when one individual's state does not fit.
+bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_sms, int ring_force,
+                GroupPlan* out);
+
+dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
+                                uint32_t generation, uint32_t ind_base, const GroupPlan& plan, int32_t* trace,
+                                int64_t* work);
+
+}  // namespace dlm

@@ -35,6 +35,10 @@ class MemeticParams(ctypes.Structure):
                 ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
+class TabuOpts(ctypes.Structure):
+    _fields_ = [("warps_per_individual", ctypes.c_int32), ("ring", ctypes.c_int32), ("legacy", ctypes.c_int32)]
+
+
 COL_TENURE = Tenure(9, 6, 10)    # Table params-COL: alpha = 0.6, L in 0..9
 WVCP_TENURE = Tenure(9, 2, 10)   # Table params-WVCP: alpha = 0.2 (times |V|), L in 0..9
 
@@ -58,6 +62,7 @@ _SIGS = {
     "dlm_gamma": (_i32, [_P, _P, _i32, _i32, _P, _P, _P]),
     "dlm_tabucol_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, Tenure, _u64, _u32, _u32]),
     "dlm_tabucol_batch_ex": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, Tenure, _u64, _u32, _u32, _i32, _P, _P]),
+    "dlm_tabucol_batch_opts": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, Tenure, _u64, _u32, _u32, _P, _P, _P]),
     "dlm_tabucol_multi": (_i32, [_P, _i32, _P, _P, _P, _P, _P, _P, _P, Tenure, _u64, _u32, _u32]),
     "dlm_tabucol_multi_noalloc": (_i32, [_P, _i32, _P, _P, _P, _P, _P, _P, _P, Tenure, _u64, _u32, _u32]),
     "dlm_tabucol_autotune": (_i32, [_P, _P, _i32, _i32, _i64, _P]),
@@ -226,6 +231,14 @@ def dlm_tabucol_batch_ex(ctx, g, k, pop, col, best_f, moves, iters, tenure=COL_T
     ctx.check(lib().dlm_tabucol_batch_ex(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_f), _ptr(moves), iters, tenure,
                                          seed, generation, ind_base, warps, _ptr(trace), _ptr(work)),
               "dlm_tabucol_batch_ex")
+
+
+def dlm_tabucol_batch_opts(ctx, g, k, pop, col, best_f, moves, iters, tenure=COL_TENURE, seed=0, generation=0,
+                           ind_base=0, warps=0, ring=0, legacy=0, trace=None, work=None):
+    o = TabuOpts(warps, ring, legacy)
+    ctx.check(lib().dlm_tabucol_batch_opts(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_f), _ptr(moves), iters, tenure,
+                                           seed, generation, ind_base, ctypes.byref(o), _ptr(trace), _ptr(work)),
+              "dlm_tabucol_batch_opts")
 
 
 def _multi_args(graphs, ks, pops, cols, best_fs, moves, iters):

@@ -31,6 +31,13 @@ def _oracle_tabu_job(args):
     return oracle.tabucol(adj, k, col, iters, seed=seed, ind=ind, gen=gen, trace=trace)
 
 
+def _oracle_tabu_alpha_job(args):
+    import oracle
+
+    (adj, k, col, iters, seed, ind, gen, trace), alpha = args
+    return oracle.tabucol(adj, k, col, iters, seed=seed, ind=ind, gen=gen, alpha=alpha, trace=trace)
+
+
 def oracle_tabu_many(jobs):
     """jobs: list of (adj, k, col, iters, seed, ind, gen, trace) -> list of oracle results."""
     if len(jobs) <= 2:

@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2109_05948_gb300 import dlmcol, inputs
 
-from gpu_util import _oracle_tabu_job, oracle_pool, device_graph, gnp_case, oracle_tabu_many
+from gpu_util import _oracle_tabu_alpha_job, _oracle_tabu_job, oracle_pool, device_graph, gnp_case, oracle_tabu_many
 
 pytestmark = pytest.mark.gpu
 
@@ -292,3 +292,64 @@ def test_tabucol_cancel_flag(ctx):
     # without the flag the context runs normally again
     dlmcol.dlm_tabucol_batch(ctx, g, k, pop, col, bf, mv, 100)
     ctx.sync()
+
+
+def _run_opts(ctx, g, k, col_np, iters, seed=0, gen=0, ind_base=0, warps=0, ring=0, legacy=0, trace=False,
+              tenure=None, work=False):
+    pop, n = col_np.shape
+    col = torch.from_numpy(col_np.copy()).cuda()
+    bf = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    mv = torch.zeros(pop, dtype=torch.int64, device="cuda")
+    tr = torch.full((pop, iters, 4), -7, dtype=torch.int32, device="cuda") if trace else None
+    wk = torch.zeros((pop, 3), dtype=torch.int64, device="cuda") if work else None
+    dlmcol.dlm_tabucol_batch_opts(ctx, g, k, pop, col, bf, mv, iters, tenure or dlmcol.COL_TENURE, seed, gen,
+                                  ind_base, warps=warps, ring=ring, legacy=legacy, trace=tr, work=wk)
+    ctx.sync()
+    out = dict(col=col.cpu().numpy(), best_f=bf.cpu().numpy(), moves=mv.cpu().numpy())
+    if trace:
+        out["trace"] = tr.cpu().numpy()
+    if work:
+        out["work"] = wk.cpu().numpy()
+    return out
+
+
+@pytest.mark.parametrize("warps,ring,alpha", [(2, 64, (6, 10)), (4, 64, (30, 10)), (8, 128, (6, 10)),
+                                              (1, 64, (60, 10)), (4, 0, (6, 10))])
+def test_tabucol_grouped_rings_and_far_list_bitexact(ctx, warps, ring, alpha):
+    """The grouped kernel with small tabu rings: tenures of 64 iterations and more go to the
+    global far list (alpha = 3 and 6 make them common), and several individuals share a CTA
+    (population 400). Every move, best colouring, best f and move count equal the oracle's."""
+    n, k, pop, iters = 90, 7, 400, 1500
+    e, adj = gnp_case(n, 0.5, 17)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, pop, 17)
+    ten = dlmcol.Tenure(9, alpha[0], alpha[1])
+    gpu = _run_opts(ctx, g, k, start, iters, seed=17, gen=2, warps=warps, ring=ring, trace=True, tenure=ten)
+    sample = list(range(0, pop, 37)) + [pop - 1]
+    jobs = [(adj, k, start[i], iters, 17, i, 2, True) for i in sample]
+    refs = oracle_pool().map(_oracle_tabu_alpha_job, [(j, alpha) for j in jobs])
+    for i, r in zip(sample, refs):
+        T = r["iters"]
+        assert np.array_equal(gpu["trace"][i, :T], r["trace"]), f"individual {i}: first divergence at " \
+            f"{int(np.argmax(np.any(gpu['trace'][i, :T] != r['trace'], axis=1)))}"
+        assert gpu["best_f"][i] == r["best_f"] and gpu["moves"][i] == r["moves"]
+        assert np.array_equal(gpu["col"][i], r["best_col"])
+
+
+def test_tabucol_grouped_equals_legacy_path(ctx):
+    """The grouped kernel (tabu flags inside gamma, several individuals per CTA, bit rows in shared
+    memory) and the one-individual-per-CTA kernel (expiry table) return the same results on the
+    benchmark's graph, G(500, 0.5), k = 48."""
+    n, k, pop, iters = 500, 48, 912, 4000
+    e, adj = gnp_case(n, 0.5, 0)
+    g = device_graph(ctx, n, e)
+    start = oracle.init_colors(n, k, pop, 3)
+    a = _run_opts(ctx, g, k, start, iters, seed=3, work=True)
+    b = _run_opts(ctx, g, k, start, iters, seed=3, legacy=1, warps=16, work=True)
+    assert np.array_equal(a["best_f"], b["best_f"]) and np.array_equal(a["moves"], b["moves"])
+    assert np.array_equal(a["col"], b["col"])
+    # the selection and the update visit the same rows on both paths
+    assert np.array_equal(a["work"][:, :2], b["work"][:, :2])
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 3, i, 0, False) for i in (0, 455, 911)])
+    for i, r in zip((0, 455, 911), refs):
+        assert a["best_f"][i] == r["best_f"] and np.array_equal(a["col"][i], r["best_col"])
