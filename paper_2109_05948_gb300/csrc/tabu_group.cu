@@ -41,34 +41,26 @@ namespace tg {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr unsigned kNone = 0x7FFFu;  // key of an absent colour, minimum of an empty class
 constexpr unsigned kFlag = 0x8000u;  // tabu flag of a gamma entry
-constexpr uint8_t kUnk = 0xFF;       // count at minimum + 1 not known
 constexpr int kDueCap = 32;          // expiring ring entries listed per iteration (more: window scan)
 
-// sc[] slots of a group (shared memory)
-enum { SC_MV = 0, SC_OLD, SC_NEW, SC_F, SC_STOP, SC_ERR, SC_LO, SC_NINS, SC_DUE, SC_FARDUE, SC_FARN,
-       SC_REQV, SC_REQC, SC_REQTT, SC_REQWAS, SC_BAD, SC_N = 32 };
-
-struct Rec {
-  uint16_t nmin, tmin;   // smallest key among the non-tabu / tabu colours (kNone: class empty)
-  uint8_t ncnt, ncnt2;   // colours at nmin, at nmin + 1 (kUnk: unknown)
-  uint8_t tcnt, tcnt2;
-};
-static_assert(sizeof(Rec) == 8, "a row summary is 8 bytes");
+// sc[] slots of a group (shared memory); 0..3, 4..7 and 8..11 are each read as one int4
+enum { SC_MV = 0, SC_OLD, SC_NEW, SC_F,          // the iteration's move and f after it
+       SC_DUE, SC_LO, SC_NINS, SC_FARN,          // expiring entries (count | far flag << 30), ring window, far list size
+       SC_STOP, SC_ERR, SC_BAD, SC_FARMIN,
+       SC_REQV, SC_REQC, SC_REQTT, SC_REQWAS,    // the move's tabu entry for the ring (v < 0: none)
+       SC_N = 32 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 __host__ __device__ inline GroupLayout group_layout(int n, int k, int W, int per, int R) {
   GroupLayout L;
-  const size_t nv = (size_t)32 * W * per;
+  const size_t nv = (size_t)32 * W * per;  // rows: every thread's per slots (n rounded up)
   const int ks = group_row_stride(k);
+  (void)n;
   size_t o = 0;
-  L.gam = o; o += a16((size_t)n * ks * 2);
-  L.rec = o; o += a16(nv * 8);
-  L.g0 = o; o += a16(nv * 2);
+  L.gam = o; o += a16(nv * ks * 2);
   L.col = o; o += a16(nv);
   L.best = o; o += a16(nv);
-  L.dirty = o; o += a16(nv);
-  L.nb = o; o += a16(nv * 2);
   L.ring = o; o += a16((size_t)R * 8);
   L.due = o; o += a16((size_t)kDueCap * 4);
   L.red = o; o += a16((size_t)W * 32);  // per warp: selection (int4), at the end 3 work counters (int64)
@@ -77,48 +69,63 @@ __host__ __device__ inline GroupLayout group_layout(int n, int k, int W, int per
   return L;
 }
 
-// ---- class summaries: insert / remove / decrement / increment one colour's key ---------------
-// A class (the non-tabu or the tabu colours of a row) keeps its minimum key mn, the number of
-// colours at mn (c1) and at mn + 1 (c2, or kUnk). Each operation returns false when the new
-// minimum cannot be derived (the row is then summarised again from its gamma entries).
-__device__ __forceinline__ void cls_ins(uint16_t& mn, uint8_t& c1, uint8_t& c2, unsigned g) {
-  if (g + 1u < mn) { mn = (uint16_t)g; c1 = 1; c2 = 0; }
-  else if (g + 1u == mn) { c2 = c1; mn = (uint16_t)g; c1 = 1; }
-  else if (g == mn) { ++c1; }
-  else if (g == mn + 1u) { if (c2 != kUnk) ++c2; }
+// ---- class summaries ---------------------------------------------------------------------------
+// A row keeps one 32-bit word per class (its non-tabu colours, its tabu colours; the current colour
+// belongs to neither): bits 0-11 the smallest key (kEmpty: no colour), 12-19 how many colours reach
+// it, bit 20 set when the count at the minimum + 1 is unknown, 24-31 that count. One colour's key
+// can enter the class (ins), leave it (rem), drop by one (dec) or rise by one (inc); the common
+// cases are one addition to the word. rem and inc report false when the new minimum cannot be
+// derived (the row is then summarised again from its gamma entries). When the count at the
+// minimum + 1 is unknown its byte may wrap; the byte is the word's top, so nothing else changes.
+constexpr uint32_t kEmpty = 0xFFFu, kC1 = 1u << 12, kUnkBit = 1u << 20, kC2 = 1u << 24;
+
+__device__ __forceinline__ uint32_t cw_make(uint32_t mn, uint32_t c1, uint32_t c2, bool unk) {
+  return mn | (c1 << 12) | (unk ? kUnkBit : (c2 << 24));
 }
-__device__ __forceinline__ bool cls_rem(uint16_t& mn, uint8_t& c1, uint8_t& c2, unsigned g) {
-  if (g == mn) {
-    if (c1 > 1) { --c1; return true; }
-    if (c2 != kUnk && c2 > 0) { mn = (uint16_t)(mn + 1u); c1 = c2; c2 = kUnk; return true; }
-    return false;
+__device__ __forceinline__ uint32_t cw_mn(uint32_t w) { return w & 0xFFFu; }
+__device__ __forceinline__ uint32_t cw_c1(uint32_t w) { return (w >> 12) & 0xFFu; }
+__device__ __forceinline__ bool cw_unk(uint32_t w) { return (w & kUnkBit) != 0; }
+__device__ __forceinline__ uint32_t cw_c2(uint32_t w) { return w >> 24; }
+
+__device__ __forceinline__ uint32_t cw_ins(uint32_t w, uint32_t g) {
+  const uint32_t mn = cw_mn(w);
+  if (g + 1u < mn) return cw_make(g, 1u, 0u, false);
+  if (g + 1u == mn) return cw_make(g, 1u, cw_c1(w), false);
+  return w + (g == mn ? kC1 : (g == mn + 1u ? kC2 : 0u));
+}
+__device__ __forceinline__ uint32_t cw_rem(uint32_t w, uint32_t g, bool& ok) {
+  const uint32_t mn = cw_mn(w), c1 = cw_c1(w);
+  if (g == mn && c1 == 1u) {
+    ok = !cw_unk(w) && cw_c2(w) > 0u;
+    return cw_make(mn + 1u, cw_c2(w), 0u, true);
   }
-  if (g == mn + 1u && c2 != kUnk) --c2;
-  return true;
+  ok = true;
+  return w - (g == mn ? kC1 : (g == mn + 1u ? kC2 : 0u));
 }
-__device__ __forceinline__ void cls_dec(uint16_t& mn, uint8_t& c1, uint8_t& c2, unsigned g) {  // g -> g - 1
-  if (g == mn) { c2 = (uint8_t)(c1 - 1); mn = (uint16_t)(g - 1u); c1 = 1; }
-  else if (g == mn + 1u) { ++c1; if (c2 != kUnk) --c2; }
-  else if (g == mn + 2u) { if (c2 != kUnk) ++c2; }
+__device__ __forceinline__ uint32_t cw_dec(uint32_t w, uint32_t g) {  // g -> g - 1, g >= minimum
+  const uint32_t mn = cw_mn(w);
+  if (g == mn) return cw_make(g - 1u, 1u, cw_c1(w) - 1u, false);
+  return w + (g == mn + 1u ? kC1 - kC2 : (g == mn + 2u ? kC2 : 0u));
 }
-__device__ __forceinline__ bool cls_inc(uint16_t& mn, uint8_t& c1, uint8_t& c2, unsigned g) {  // g -> g + 1
-  if (g == mn) {
-    if (c1 > 1) { --c1; if (c2 != kUnk) ++c2; return true; }
-    if (c2 == kUnk) return false;
-    mn = (uint16_t)(mn + 1u); c1 = (uint8_t)(c2 + 1); c2 = kUnk;
-    return true;
+__device__ __forceinline__ uint32_t cw_inc(uint32_t w, uint32_t g, bool& ok) {  // g -> g + 1
+  const uint32_t mn = cw_mn(w), c1 = cw_c1(w);
+  ok = true;
+  if (g == mn && c1 == 1u) {
+    ok = !cw_unk(w);
+    return cw_make(mn + 1u, cw_c2(w) + 1u, 0u, true);
   }
-  if (g == mn + 1u && c2 != kUnk) --c2;
-  return true;
+  return w + (g == mn ? kC2 - kC1 : (g == mn + 1u ? 0u - kC2 : 0u));
 }
 
 // Summary of row u by one warp (lanes over its 32-bit words, two colours each, at most 3 words a
 // lane for k <= 128): the current colour cu and the padding colours (key kNone) are skipped.
-__device__ __forceinline__ Rec summarise(const uint32_t* row32, int kw, int cu, int lane) {
-  uint32_t x[3];
+// Returns (non-tabu class word, tabu class word), the same in every lane.
+template <int NWL>
+__device__ __forceinline__ uint2 summarise_n(const uint32_t* row32, int kw, int cu, int lane) {
+  uint32_t x[NWL];
   unsigned nm = kNone, tm = kNone;
 #pragma unroll
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < NWL; ++t) {
     const int w = lane + 32 * t;
     uint32_t v = 0xFFFFFFFFu;
     if (w < kw) {
@@ -128,43 +135,46 @@ __device__ __forceinline__ Rec summarise(const uint32_t* row32, int kw, int cu, 
     x[t] = v;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const unsigned key = (v >> (16 * h)) & kNone, fl = (v >> (16 * h + 15)) & 1u;
-      if (key != kNone) {
-        if (fl) tm = min(tm, key); else nm = min(nm, key);
-      }
+      const unsigned key = (v >> (16 * h)) & kNone;
+      const bool fl = (v >> (16 * h + 15)) & 1u;
+      tm = fl ? min(tm, key) : tm;
+      nm = fl ? nm : min(nm, key);
     }
   }
   const unsigned NM = __reduce_min_sync(FULL, nm), TM = __reduce_min_sync(FULL, tm);
   unsigned cn = 0, ct = 0;  // count at the minimum | count at the minimum + 1 << 16
 #pragma unroll
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < NWL; ++t) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const unsigned key = (x[t] >> (16 * h)) & kNone, fl = (x[t] >> (16 * h + 15)) & 1u;
-      if (key != kNone) {
-        if (fl) ct += (key == TM ? 1u : 0u) + (key == TM + 1u ? 0x10000u : 0u);
-        else cn += (key == NM ? 1u : 0u) + (key == NM + 1u ? 0x10000u : 0u);
-      }
+      const unsigned key = (x[t] >> (16 * h)) & kNone;
+      const bool fl = (x[t] >> (16 * h + 15)) & 1u;
+      const unsigned ref = fl ? TM : NM;
+      const unsigned add = key == kNone ? 0u : ((key == ref ? 1u : 0u) + (key == ref + 1u ? 0x10000u : 0u));
+      ct += fl ? add : 0u;
+      cn += fl ? 0u : add;
     }
   }
   const unsigned CN = __reduce_add_sync(FULL, cn), CT = __reduce_add_sync(FULL, ct);
-  Rec r;
-  r.nmin = (uint16_t)NM; r.tmin = (uint16_t)TM;
-  r.ncnt = (uint8_t)(CN & 0xFFFFu); r.ncnt2 = (uint8_t)(CN >> 16);
-  r.tcnt = (uint8_t)(CT & 0xFFFFu); r.tcnt2 = (uint8_t)(CT >> 16);
-  return r;
+  return make_uint2(cw_make(NM == kNone ? kEmpty : NM, CN & 0xFFFFu, CN >> 16, false),
+                    cw_make(TM == kNone ? kEmpty : TM, CT & 0xFFFFu, CT >> 16, false));
+}
+__device__ __forceinline__ uint2 summarise(const uint32_t* row32, int kw, int cu, int lane) {
+  if (kw <= 32) return summarise_n<1>(row32, kw, cu, lane);
+  if (kw <= 64) return summarise_n<2>(row32, kw, cu, lane);
+  return summarise_n<3>(row32, kw, cu, lane);
 }
 
-// Best admissible move of a conflicting row from its summary: (delta, number of colours reaching
-// it); count 0 when every colour is tabu and none is aspirated. A tabu colour is aspirated when
-// f + gamma - g0 < best f, i.e. gamma < thrb + g0 with thrb = best f - f.
-__device__ __forceinline__ void eval_row(const Rec r, int gv, int thrb, int& d, int& c) {
-  const unsigned nt = r.ncnt ? (unsigned)r.nmin : kNone;
-  const unsigned ta = (r.tcnt && (int)r.tmin < thrb + gv) ? (unsigned)r.tmin : kNone;
+// Best admissible move of a conflicting row from its class words (N, T): (delta, number of
+// colours reaching it); count 0 when every colour is tabu and none is aspirated. A tabu colour is
+// aspirated when f + gamma - g0 < best f, i.e. gamma < thrb + g0 with thrb = best f - f.
+__device__ __forceinline__ void eval_row(const uint2 r, int gv, int thrb, int& d, int& c) {
+  const unsigned nt = cw_mn(r.x);
+  const unsigned tmn = cw_mn(r.y);
+  const unsigned ta = (int)tmn < thrb + gv ? tmn : kEmpty;
   const unsigned adm = min(nt, ta);
-  if (adm == kNone) { c = 0; d = INT_MAX; return; }
-  c = (nt == adm ? r.ncnt : 0) + (ta == adm ? r.tcnt : 0);
-  d = (int)adm - gv;
+  c = adm == kEmpty ? 0 : (int)((nt == adm ? cw_c1(r.x) : 0u) + (ta == adm ? cw_c1(r.y) : 0u));
+  d = adm == kEmpty ? INT_MAX : (int)adm - gv;
 }
 
 __device__ __forceinline__ int incl_scan(int x, int lane) {
@@ -186,93 +196,102 @@ __device__ __forceinline__ unsigned ent_v(uint32_t x) { return x & 0xFFFFu; }
 __device__ __forceinline__ unsigned ent_c(uint32_t x) { return (x >> 16) & 0xFFu; }
 __device__ __forceinline__ unsigned ent_st(uint32_t x) { return x >> 24; }
 
-template <int W>
-struct GroupMax { static constexpr int value = W >= 16 ? 1 : (W == 8 ? 2 : (W == 4 ? 4 : 8)); };
+// threads of a CTA (all its groups): 768 (85 registers a thread) with 2 vertices a thread, 512
+// (128 registers) with more
+__host__ __device__ constexpr int max_threads_for(int per) { return per <= 2 ? 768 : 512; }
 
-template <int W, bool BSM>
-__device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const uint32_t* bits, int bar_id,
-                               uint2* far) {
-  constexpr int NT = 32 * W;
+// One individual by the W warps of one group (W at run time, PER vertices a thread at compile
+// time). Thread t owns the vertices v0 = t PER .. v0 + PER - 1 and keeps their colours, their
+// gamma[v][col v] and their two class words in registers; the gamma row of vertex v is q NT + t
+// (slot q of its owner thread t), so that the threads of a warp touching their slot q address
+// consecutive rows (distinct banks).
+template <int PER, bool BSM>
+__device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t* gs, const uint32_t* bits,
+                               int bar_id, uint2* far) {
+  const int NT = 32 * W;
   const int tid = threadIdx.x % NT, lane = tid & 31, warp = tid >> 5;
-  const int n = a.n, k = a.k, ks = a.ks, kw = ks >> 1, words = a.words, per = a.per, R = a.R;
-  const GroupLayout L = group_layout(n, k, W, per, R);
+  const int n = a.n, k = a.k, ks = a.ks, kw = ks >> 1, words = a.words, R = a.R;
+  const GroupLayout L = group_layout(n, k, W, PER, R);
   uint16_t* gam = (uint16_t*)(gs + L.gam);
-  Rec* rec = (Rec*)(gs + L.rec);
-  uint16_t* g0 = (uint16_t*)(gs + L.g0);
   uint8_t* colS = gs + L.col;
   uint8_t* bestS = gs + L.best;
-  uint8_t* dirty = gs + L.dirty;
-  uint16_t* nbw = (uint16_t*)(gs + L.nb) + (size_t)warp * 32 * per;  // this warp's neighbour list
   uint2* ring = (uint2*)(gs + L.ring);
   uint32_t* due = (uint32_t*)(gs + L.due);
   int4* red = (int4*)(gs + L.red);
   int32_t* sc = (int32_t*)(gs + L.sc);
-  const int v0 = tid * per;                           // this thread's vertices [v0, v0 + per)
-  const int wv0 = warp * 32 * per, wv1 = wv0 + 32 * per;  // this warp's
+  const int v0 = tid * PER;
   const uint32_t ind_id = a.ind_base + (uint32_t)ind;
   int16_t* gcol = a.col + (size_t)ind * n;
   const unsigned lt = (1u << lane) - 1u;
   auto bar = [&]() { group_bar(bar_id, NT); };
+  auto rowof = [&](int v) -> uint16_t* { return gam + ((v % PER) * NT + v / PER) * ks; };
+  auto myrow = [&](int q) -> uint16_t* { return gam + (q * NT + tid) * ks; };
+
+  int colq[PER], g0q[PER];
+  uint2 recq[PER];
 
   // ---- set-up: tables, start colouring, gamma, summaries, f ------------------------------------
-  for (int i = tid; i < n * kw; i += NT) {
-    const int v = i / kw, w = i - v * kw, c0 = 2 * w;
-    ((uint32_t*)gam)[i] = (c0 >= k ? kNone : 0u) | (c0 + 1 >= k ? (kNone << 16) : 0u);
-  }
-  if (tid < SC_N) sc[tid] = 0;
   int bad = 0;
-  for (int q = 0; q < per; ++q) {
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    uint32_t* r32 = (uint32_t*)myrow(q);
+    for (int w = 0; w < kw; ++w) r32[w] = (2 * w >= k ? kNone : 0u) | (2 * w + 1 >= k ? (kNone << 16) : 0u);
     const int v = v0 + q;
-    uint8_t c = 0;
+    int c = 0;
     if (v < n) {
       const int cc = gcol[v];
       if (cc < 0 || cc >= k) bad = 1;
-      else c = (uint8_t)cc;
+      else c = cc;
     }
-    colS[v] = c;
-    bestS[v] = c;
-    dirty[v] = 0;
-    g0[v] = 0;
+    colq[q] = c;
+    colS[v] = (uint8_t)c;
+    bestS[v] = (uint8_t)c;
   }
+  if (tid < SC_N) sc[tid] = 0;
   bar();
   if (bad) sc[SC_BAD] = 1;
-  if (tid == 0) sc[SC_REQV] = -1;
+  if (tid == 0) {
+    sc[SC_REQV] = -1;
+    sc[SC_FARMIN] = -1;
+  }
   bar();
   if (sc[SC_BAD]) {
     if (tid == 0) raise_status(a.status, DLM_EINVAL);
     bar();  // every thread has read the flag before the next individual clears it
     return;
   }
-  for (int v = tid; v < n; v += NT) {
-    const uint32_t* br = bits + (size_t)v * words;
-    uint16_t* gr = gam + (size_t)v * ks;
-    for (int w = 0; w < words; ++w) {
-      uint32_t m = br[w];
-      while (m) {
-        const int u = 32 * w + __ffs(m) - 1;
-        m &= m - 1;
-        gr[colS[u]]++;
+  int part = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int v = v0 + q;
+    g0q[q] = 0;
+    if (v < n) {
+      const uint32_t* br = bits + v * words;
+      uint16_t* gr = myrow(q);
+      for (int w = 0; w < words; ++w) {
+        uint32_t m = br[w];
+        while (m) {
+          const int u = 32 * w + __ffs(m) - 1;
+          m &= m - 1;
+          gr[colS[u]]++;
+        }
       }
+      g0q[q] = gr[colq[q]];
+      part += g0q[q];
     }
   }
-  bar();
-  {
-    int part = 0;
-    for (int q = 0; q < per; ++q) {
-      const int v = v0 + q;
-      if (v < n) {
-        const int g = gam[(size_t)v * ks + colS[v]];
-        g0[v] = (uint16_t)g;
-        part += g;
-      }
+  __syncwarp();
+  // every row's summary, the warp's lanes in turn (the result of the reductions is in every lane)
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    for (int l = 0; l < 32; ++l) {
+      const int cu = __shfl_sync(FULL, colq[q], l);
+      const uint2 r = summarise((const uint32_t*)(gam + (q * NT + warp * 32 + l) * ks), kw, cu, lane);
+      if (lane == l) recq[q] = r;
     }
-    part = __reduce_add_sync(FULL, part);
-    if (lane == 0) red[warp].x = part;
   }
-  for (int u = warp; u < n; u += W) {
-    const Rec r = summarise((const uint32_t*)(gam + (size_t)u * ks), kw, colS[u], lane);
-    if (lane == 0) rec[u] = r;
-  }
+  part = __reduce_add_sync(FULL, part);
+  if (lane == 0) red[warp].x = part;
   bar();
   int f = 0;
   for (int w = 0; w < W; ++w) f += red[w].x;
@@ -281,58 +300,35 @@ __device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const u
 
   int best_f = f, moves = 0;
   int64_t w_rows = 0, w_deg = 0, w_resum = 0;
-  // ring maintenance state (used by warp W - 1 only; identical in its lanes)
-  int lo = 0, nins = 0, far_n = 0;
-  uint32_t far_min = 0xFFFFFFFFu;
   // Philox blocks: lane l holds (r0, r1) of iteration (it & ~31) + l
   U4 rr = rng(a.seed, (uint32_t)lane, a.gen, ind_id, kTagTabu);
   uint32_t r0l = rr.x, r1l = rr.y;
+  // the warp's vertex range, for the scanner's expiry lists (bit w: warp w has an expiring entry)
+  const int wpv = 32 * PER;
 
-  // selection from the summaries of this thread's conflicting vertices; the thread's minimum and
-  // tie count stay in registers (the deciding warp needs them), the warp's go to red[warp]
+  // selection from the class words in registers: per slot (delta, number of tied colours), the
+  // thread's minimum and tie count (kept for the deciding warp), the warp's in red[warp]
+  int dq[PER], cq[PER];
   int tmin = INT_MAX, tcnt = 0;
   auto select = [&]() {
     int nconf = 0;
+    const int thrb = best_f - f;
     tmin = INT_MAX;
     tcnt = 0;
-    const int thrb = best_f - f;
-    for (int q = 0; q < per; q += 2) {
-      const uint32_t gg = *(const uint32_t*)(g0 + v0 + q);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int gv = (int)((gg >> (16 * h)) & 0xFFFFu);
-        if (gv > 0) {
-          ++nconf;
-          int d, c;
-          eval_row(rec[v0 + q + h], gv, thrb, d, c);
-          if (c) {
-            if (d < tmin) { tmin = d; tcnt = c; }
-            else if (d == tmin) tcnt += c;
-          }
-        }
-      }
+    for (int q = 0; q < PER; ++q) {
+      eval_row(recq[q], g0q[q], thrb, dq[q], cq[q]);
+      cq[q] = g0q[q] > 0 ? cq[q] : 0;
+      dq[q] = cq[q] > 0 ? dq[q] : INT_MAX;
+      nconf += g0q[q] > 0 ? 1 : 0;
+      const bool lo2 = dq[q] < tmin;
+      tcnt = lo2 ? cq[q] : (dq[q] == tmin ? tcnt + cq[q] : tcnt);
+      tmin = lo2 ? dq[q] : tmin;
     }
     const int wm = __reduce_min_sync(FULL, tmin);
     const int wc = (int)__reduce_add_sync(FULL, (wm != INT_MAX && tmin == wm) ? (unsigned)tcnt : 0u);
     const int wn = (int)__reduce_add_sync(FULL, (unsigned)nconf);
     if (lane == 0) red[warp] = make_int4(wm, wc, wn, 0);
-  };
-
-  // expiry of the tabu entry (v, c) before the next selection, unless this iteration's move has
-  // just made the same pair tabu again; called by one lane at a time of the warp owning v
-  auto expire = [&](int v, int c, int mv, int old) {
-    if (v == mv && c == old) return;
-    uint16_t* ge = gam + (size_t)v * ks + c;
-    const unsigned g = *ge;
-    if (!(g & kFlag)) return;
-    *ge = (uint16_t)(g & kNone);
-    if (c != colS[v]) {
-      Rec r = rec[v];
-      const bool ok = cls_rem(r.tmin, r.tcnt, r.tcnt2, g & kNone);
-      cls_ins(r.nmin, r.ncnt, r.ncnt2, g & kNone);
-      rec[v] = r;
-      if (!ok) dirty[v] = 1;
-    }
   };
 
   select();
@@ -348,50 +344,66 @@ __device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const u
       r1l = rr.y;
     }
     const uint32_t r0 = __shfl_sync(FULL, r0l, it & 31), r1 = __shfl_sync(FULL, r1l, it & 31);
+    // lanes 0..W-1 hold the warps' results: the minimum, the tie total, the warp holding the j-th
+    // tie and the ties before it
     const int4 rw = lane < W ? red[lane] : make_int4(INT_MAX, 0, 0, 0);
     const int dstar = __reduce_min_sync(FULL, rw.x);
-    const int xl = (lane < W && dstar != INT_MAX && rw.x == dstar) ? rw.y : 0;
-    const int T = (int)__reduce_add_sync(FULL, (unsigned)xl);
-    const int pre = (int)__reduce_add_sync(FULL, lane < warp ? (unsigned)xl : 0u);
-    const int wtot = __shfl_sync(FULL, xl, warp);
+    const int xl = (dstar != INT_MAX && rw.x == dstar) ? rw.y : 0;
+    int xincl = xl;
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {  // W <= 16
+      const int t = __shfl_up_sync(FULL, xincl, d);
+      if (lane >= d) xincl += t;
+    }
+    const int T = __shfl_sync(FULL, xincl, 15);
+    const uint32_t j = T > 0 ? below(r0, (uint32_t)T) : 0u;
+    const unsigned dball = __ballot_sync(FULL, lane < W && xincl > (int)j);
+    const int wdec = T > 0 ? __ffs(dball) - 1 : -1;
+    const int wscan = wdec < 0 ? 0 : (wdec + 1 == W ? 0 : wdec + 1);
     if (warp == 0) {
-      const int nc = (int)__reduce_add_sync(FULL, lane < W ? (unsigned)rw.z : 0u);
+      const int nc = (int)__reduce_add_sync(FULL, (unsigned)(lane < W ? rw.z : 0));
       if (lane == 0) w_rows += nc;
     }
-    const uint32_t j = T > 0 ? below(r0, (uint32_t)T) : 0u;
-    if (T > 0 && (int)j >= pre && (int)j < pre + wtot) {  // this warp holds the j-th tie
+    if (warp == wdec) {
+      const int pre = __shfl_sync(FULL, xincl - xl, wdec);
       const int ct = tmin == dstar ? tcnt : 0;
-      const int incl = incl_scan(ct, lane);
-      const int lo_l = pre + incl - ct;
-      const bool hit = ct > 0 && (int)j >= lo_l && (int)j < lo_l + ct;
-      int hit_v = -1, hit_rank = 0;
-      if (hit) {
-        int jj = (int)j - lo_l;
-        const int thrb = best_f - f;
-        for (int q = 0; q < per; ++q) {
-          const int v = v0 + q;
-          const int gv = g0[v];
-          if (v >= n || gv == 0) continue;
-          int d, c;
-          eval_row(rec[v], gv, thrb, d, c);
-          if (c == 0 || d != dstar) continue;
-          if (jj >= c) { jj -= c; continue; }
-          hit_v = v;
-          hit_rank = jj;
-          break;
+      const unsigned hbal = __ballot_sync(FULL, ct > 0);
+      int hl, lo_h;
+      if ((hbal & (hbal - 1)) == 0) {  // one lane holds every tie of this warp
+        hl = hbal ? __ffs(hbal) - 1 : 0;
+        lo_h = pre;
+      } else {
+        const int incl = incl_scan(ct, lane);
+        const int lo_l = pre + incl - ct;
+        const unsigned hb = __ballot_sync(FULL, ct > 0 && (int)j >= lo_l && (int)j < lo_l + ct);
+        hl = __ffs(hb) - 1;
+        lo_h = __shfl_sync(FULL, lo_l, hl);
+      }
+      // the tied slot of lane hl, its rank among the row's tied colours, its colour and g0
+      int hv = -1, hr = 0, hc = 0, hg = 0;
+      {
+        int jj = (int)j - lo_h;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const bool tie = hv < 0 && dq[q] == dstar && cq[q] > 0;
+          const bool take = tie && jj < cq[q];
+          hv = take ? v0 + q : hv;
+          hr = take ? jj : hr;
+          hc = take ? colq[q] : hc;
+          hg = take ? g0q[q] : hg;
+          jj = (tie && !take) ? jj - cq[q] : jj;
         }
       }
-      const unsigned hb = __ballot_sync(FULL, hit);
-      const int hl = hb ? __ffs(hb) - 1 : 0;
-      const int v = hb ? __shfl_sync(FULL, hit_v, hl) : -1;
-      int jj = __shfl_sync(FULL, hit_rank, hl);
-      int mc = -1, colv = 0;
+      const int v = __shfl_sync(FULL, hv, hl);
+      const int jj = __shfl_sync(FULL, hr, hl);
+      const int colv = __shfl_sync(FULL, hc, hl);
+      const int gv = __shfl_sync(FULL, hg, hl);
+      int mc = -1;
       if (v >= 0) {
-        colv = colS[v];
-        const int gv = g0[v];
         const unsigned kmin = (unsigned)(dstar + gv);
         const int thr = best_f - f + gv;
-        const uint32_t* row32 = (const uint32_t*)(gam + (size_t)v * ks);
+        const uint32_t* row32 = (const uint32_t*)rowof(v);
+        int rem = jj;
         for (int wb = 0; wb < kw && mc < 0; wb += 32) {
           const int w = wb + lane;
           bool m0 = false, m1 = false;
@@ -402,20 +414,23 @@ __device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const u
             m0 = ka == kmin && (!(x & kFlag) || (int)ka < thr);
             m1 = kb == kmin && (!((x >> 16) & kFlag) || (int)kb < thr);
           }
+          // colours 2w (m0) and 2w + 1 (m1) in colour order: the lane whose pair holds the rem-th
           const unsigned b0 = __ballot_sync(FULL, m0), b1 = __ballot_sync(FULL, m1);
           const int before = __popc(b0 & lt) + __popc(b1 & lt);
-          const bool found = jj >= before && jj < before + (int)m0 + (int)m1;
-          const unsigned fb = __ballot_sync(FULL, found);
-          if (fb) mc = __shfl_sync(FULL, 2 * w + ((jj == before && m0) ? 0 : 1), __ffs(fb) - 1);
-          else jj -= __popc(b0) + __popc(b1);
+          const unsigned fb = __ballot_sync(FULL, rem >= before && rem < before + (int)m0 + (int)m1);
+          if (fb) {
+            const int wl = __ffs(fb) - 1;
+            const unsigned lw = (1u << wl) - 1u;
+            const int bw = __popc(b0 & lw) + __popc(b1 & lw);
+            mc = 2 * (wb + wl) + ((rem == bw && ((b0 >> wl) & 1u)) ? 0 : 1);
+          } else {
+            rem -= __popc(b0) + __popc(b1);
+          }
         }
       }
       if (lane == 0) {
         if (v >= 0 && mc >= 0 && mc < k) {
-          sc[SC_MV] = v;
-          sc[SC_OLD] = colv;
-          sc[SC_NEW] = mc;
-          sc[SC_F] = f + dstar;
+          *(int4*)(sc + SC_MV) = make_int4(v, colv, mc, f + dstar);
           if (a.trace) reinterpret_cast<int4*>(a.trace)[(size_t)ind * iters + it] = make_int4(v, mc, dstar, T);
         } else {
           sc[SC_ERR] = 2;  // tie counts inconsistent with the row: refuse to move
@@ -427,7 +442,9 @@ __device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const u
       // cancellation, polled every 1024 iterations: the search stops before this iteration's move
       if ((it & 1023) == 0 && a.cancel && *(volatile const int32_t*)a.cancel != 0) sc[SC_STOP] = 1;
     }
-    if (warp == W - 1) {
+    if (warp == wscan) {
+      int lo = sc[SC_LO], nins = sc[SC_NINS], far_n = sc[SC_FARN];
+      uint32_t far_min = (uint32_t)sc[SC_FARMIN];
       // (a) retired entries at the front of the ring; far entries that expired at iteration it
       while (lo < nins) {
         const int s = lo + lane;
@@ -504,8 +521,10 @@ __device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const u
         __syncwarp();
         if (lane == 0) sc[SC_REQV] = -1;
       }
-      // (c) entries that expire before the next selection (no longer tabu at it + 1)
+      // (c) entries that expire before the next selection (no longer tabu at it + 1), and which
+      // warps own their rows
       int dcnt = 0;
+      unsigned dwarps = 0;
       for (int b = lo; b < nins; b += 32) {
         const int s = b + lane;
         bool d = false;
@@ -521,188 +540,179 @@ __device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const u
           if (pos < kDueCap) due[pos] = (uint32_t)(s & (R - 1));
           ring[s & (R - 1)].x = (x & 0xFFFFFFu) | (2u << 24);
         }
+        dwarps |= __reduce_or_sync(FULL, d ? 1u << (ent_v(x) / wpv) : 0u);
         dcnt += __popc(db);
       }
+      const bool fdue = far_n > 0 && far_min == (uint32_t)(it + 1);
+      __syncwarp();
       if (lane == 0) {
-        sc[SC_LO] = lo;
-        sc[SC_NINS] = nins;
-        sc[SC_DUE] = dcnt;
-        sc[SC_FARDUE] = far_n > 0 && far_min == (uint32_t)(it + 1);
-        sc[SC_FARN] = far_n;
+        *(int4*)(sc + SC_DUE) = make_int4(min(dcnt, 0x3FFF) | (fdue ? 1 << 14 : 0) | (int)(dwarps << 16), lo, nins, far_n);
+        sc[SC_FARMIN] = (int32_t)far_min;
       }
     }
     bar();
-    if (sc[SC_STOP] | sc[SC_ERR]) break;
     // ---- (U) the move, expiries, neighbours, summaries, next selection ------------------------
-    const int mv = T > 0 ? sc[SC_MV] : -1;
-    int old = -1, nw = -1;
+    const int4 A = *(const int4*)(sc + SC_MV);
+    const int4 B = *(const int4*)(sc + SC_DUE);
+    const int4 C = *(const int4*)(sc + SC_STOP);
+    if (C.x | C.y) break;
+    int mv = -1, old = -1, nw = -1;
     bool improved = false;
-    if (mv >= 0) {
-      old = sc[SC_OLD];
-      nw = sc[SC_NEW];
-      f = sc[SC_F];
+    uint32_t dmask = 0;  // own rows to summarise again
+    if (T > 0) {
+      mv = A.x;
+      old = A.y;
+      nw = A.z;
+      f = A.w;
       ++moves;
       improved = f < best_f;
-      if (improved) best_f = f;
-      if (mv >= v0 && mv < v0 + per) {  // the owner of the moved vertex updates its row
-        uint16_t* gr = gam + (size_t)mv * ks;
+      best_f = improved ? f : best_f;
+      if (mv >= v0 && mv < v0 + PER) {  // the owner of the moved vertex updates its row
+        const int qs = mv - v0;
+        uint2 rc = recq[0];
+#pragma unroll
+        for (int q = 1; q < PER; ++q) rc = q == qs ? recq[q] : rc;
+        uint16_t* gr = rowof(mv);
         const unsigned go = gr[old], gn = gr[nw];
         const bool was = (go & kFlag) != 0;
-        // alpha f in 32-bit unsigned arithmetic: the host bounds alpha_num * |E| below 2^32
-        const uint32_t tt = below(r1, a.L1) + ((uint32_t)a.an * (uint32_t)f) / (uint32_t)a.ad;
+        // alpha f: 32-bit unsigned (the host bounds alpha_num * |E| below 2^32), divided by
+        // alpha_den through its precomputed 64-bit reciprocal
+        const uint32_t af = (uint32_t)a.an * (uint32_t)f;
+        const uint32_t tt = below(r1, a.L1) + (a.ad == 1 ? af : (uint32_t)__umul64hi((uint64_t)af, a.ad_recip));
         const bool tabu = tt > 0;
         gr[old] = (uint16_t)((go & kNone) | (tabu ? kFlag : 0u));
-        colS[mv] = (uint8_t)nw;
-        g0[mv] = (uint16_t)(gn & kNone);
-        Rec r = rec[mv];
-        bool ok;  // the new colour leaves its class, the old one joins the tabu (or free) class
-        if (gn & kFlag) ok = cls_rem(r.tmin, r.tcnt, r.tcnt2, gn & kNone);
-        else ok = cls_rem(r.nmin, r.ncnt, r.ncnt2, gn & kNone);
-        if (tabu) cls_ins(r.tmin, r.tcnt, r.tcnt2, go & kNone);
-        else cls_ins(r.nmin, r.ncnt, r.ncnt2, go & kNone);
-        rec[mv] = r;
-        if (!ok) dirty[mv] = 1;
-        if (tabu || was) {
-          sc[SC_REQC] = old;
-          sc[SC_REQTT] = (int32_t)tt;
-          sc[SC_REQWAS] = was ? 1 : 0;
-          sc[SC_REQV] = mv;
+        // the new colour leaves its class, the old one joins the tabu (or the free) class
+        bool ok;
+        if (gn & kFlag) rc.y = cw_rem(rc.y, gn & kNone, ok);
+        else rc.x = cw_rem(rc.x, gn & kNone, ok);
+        if (tabu) rc.y = cw_ins(rc.y, go & kNone);
+        else rc.x = cw_ins(rc.x, go & kNone);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          if (q == qs) {
+            recq[q] = rc;
+            colq[q] = nw;
+            g0q[q] = (int)(gn & kNone);
+          }
         }
+        dmask |= ok ? 0u : (1u << qs);
+        if (tabu || was) *(int4*)(sc + SC_REQV) = make_int4(mv, old, (int32_t)tt, was ? 1 : 0);
       }
     }
-    __syncwarp();
-    // expiring entries of this warp's rows, one at a time (several may touch one row)
-    {
-      const int dcnt = sc[SC_DUE];
-      if (dcnt > 0 && dcnt <= kDueCap) {
-        int s = -1, ev = 0, ec = 0;
-        if (lane < dcnt) {
-          s = (int)due[lane];
+    // expiring entries of this thread's rows, in list order (several may touch one row)
+    auto expire = [&](int v, int c) {
+      if (v == mv && c == old) return;
+      const int qs = v - v0;
+      uint16_t* ge = myrow(qs) + c;
+      const unsigned g = *ge;
+      if (!(g & kFlag)) return;
+      *ge = (uint16_t)(g & kNone);
+      int cu = colq[0];
+      uint2 rc = recq[0];
+#pragma unroll
+      for (int q = 1; q < PER; ++q) {
+        cu = q == qs ? colq[q] : cu;
+        rc = q == qs ? recq[q] : rc;
+      }
+      if (c == cu) return;
+      bool ok;
+      rc.y = cw_rem(rc.y, g & kNone, ok);
+      rc.x = cw_ins(rc.x, g & kNone);
+#pragma unroll
+      for (int q = 0; q < PER; ++q) recq[q] = q == qs ? rc : recq[q];
+      dmask |= ok ? 0u : (1u << qs);
+    };
+    if ((B.x >> (16 + warp)) & 1) {
+      const int dcnt = B.x & 0x3FFF;
+      if (dcnt < kDueCap) {
+        for (int i = 0; i < dcnt; ++i) {
+          const int s = (int)due[i];
           const uint32_t x = ring[s].x;
-          ev = (int)ent_v(x);
-          ec = (int)ent_c(x);
-        }
-        const bool mine = s >= 0 && ev >= wv0 && ev < wv1;
-        for (unsigned b = __ballot_sync(FULL, mine); b; b &= b - 1) {
-          if (lane == __ffs(b) - 1) {
-            expire(ev, ec, mv, old);
-            ring[s].x &= 0xFFFFFFu;
-          }
-          __syncwarp();
-        }
-      } else if (dcnt > kDueCap) {
-        const int slo = sc[SC_LO], snins = sc[SC_NINS];
-        for (int bb = slo; bb < snins; bb += 32) {
-          const int s = bb + lane;
-          bool mine = false;
-          int ev = 0, ec = 0;
-          if (s < snins) {
-            const uint32_t x = ring[s & (R - 1)].x;
-            ev = (int)ent_v(x);
-            ec = (int)ent_c(x);
-            mine = ent_st(x) == 2 && ev >= wv0 && ev < wv1;
-          }
-          for (unsigned b = __ballot_sync(FULL, mine); b; b &= b - 1) {
-            if (lane == __ffs(b) - 1) {
-              expire(ev, ec, mv, old);
-              ring[s & (R - 1)].x &= 0xFFFFFFu;
-            }
-            __syncwarp();
+          const int ev = (int)ent_v(x);
+          if (ev >= v0 && ev < v0 + PER) {
+            expire(ev, (int)ent_c(x));
+            ring[s].x = x & 0xFFFFFFu;
           }
         }
-      }
-      if (sc[SC_FARDUE]) {
-        const int fn = sc[SC_FARN];
-        for (int bb = 0; bb < fn; bb += 32) {
-          const int s = bb + lane;
-          bool mine = false;
-          int ev = 0, ec = 0;
-          if (s < fn) {
-            const uint2 e = far[s];
-            ev = (int)ent_v(e.x);
-            ec = (int)ent_c(e.x);
-            mine = e.y == (uint32_t)(it + 1) && ev >= wv0 && ev < wv1;
-          }
-          for (unsigned b = __ballot_sync(FULL, mine); b; b &= b - 1) {
-            if (lane == __ffs(b) - 1) expire(ev, ec, mv, old);
-            __syncwarp();
+      } else {
+        for (int s = B.y; s < B.z; ++s) {
+          const uint32_t x = ring[s & (R - 1)].x;
+          const int ev = (int)ent_v(x);
+          if (ent_st(x) == 2 && ev >= v0 && ev < v0 + PER) {
+            expire(ev, (int)ent_c(x));
+            ring[s & (R - 1)].x = x & 0xFFFFFFu;
           }
         }
       }
     }
-    __syncwarp();
-    // gamma of this warp's neighbours of the moved vertex, listed across the lanes
+    if ((B.x >> 14) & 1) {  // far entries expire too
+      for (int s = 0; s < B.w; ++s) {
+        const uint2 e = far[s];
+        const int ev = (int)ent_v(e.x);
+        if (e.y == (uint32_t)(it + 1) && ev >= v0 && ev < v0 + PER) expire(ev, (int)ent_c(e.x));
+      }
+    }
+    // gamma of this thread's neighbours of the moved vertex: every load first, then the updates
     if (mv >= 0) {
       uint32_t m = 0;
       if (v0 < n) {
-        const uint32_t* br = bits + (size_t)mv * words;
+        const uint32_t* br = bits + mv * words;
         const int w0 = v0 >> 5, sh = v0 & 31;
         const uint32_t lw = br[w0];
-        const uint32_t hw = (sh + per > 32 && w0 + 1 < words) ? br[w0 + 1] : 0u;
-        m = __funnelshift_r(lw, hw, sh);
-        if (per < 32) m &= (1u << per) - 1u;
+        const uint32_t hw = (sh + PER > 32 && w0 + 1 < words) ? br[w0 + 1] : 0u;
+        constexpr uint32_t kPerMask = PER >= 32 ? 0xFFFFFFFFu : ((1u << (PER & 31)) - 1u);
+        m = __funnelshift_r(lw, hw, sh) & kPerMask;
       }
-      const int cnt = __popc(m);
-      const int incl = incl_scan(cnt, lane);
-      const int total = __shfl_sync(FULL, incl, 31);
-      int o = incl - cnt;
-      while (m) {
-        nbw[o++] = (uint16_t)(v0 + __ffs(m) - 1);
-        m &= m - 1;
-      }
-      __syncwarp();
-      if (lane == 0) w_deg += total;
-      for (int r = lane; r < total; r += 32) {
-        const int u = nbw[r];
-        const int cu = colS[u];
-        uint16_t* gr = gam + (size_t)u * ks;
-        const unsigned go = gr[old], gn = gr[nw];
-        gr[old] = (uint16_t)(go - 1u);
-        gr[nw] = (uint16_t)(gn + 1u);
-        Rec rc = rec[u];
-        bool ok = true;
-        if (old != cu) {
-          if (go & kFlag) cls_dec(rc.tmin, rc.tcnt, rc.tcnt2, go & kNone);
-          else cls_dec(rc.nmin, rc.ncnt, rc.ncnt2, go & kNone);
-        } else {
-          g0[u] = (uint16_t)((go & kNone) - 1u);
+      w_deg += __popc(m);
+      unsigned go[PER], gn[PER];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        go[q] = 0; gn[q] = 0;
+        if ((m >> q) & 1u) {
+          const uint16_t* gr = myrow(q);
+          go[q] = gr[old];
+          gn[q] = gr[nw];
         }
-        if (nw != cu) {
-          if (gn & kFlag) ok = cls_inc(rc.tmin, rc.tcnt, rc.tcnt2, gn & kNone);
-          else ok = cls_inc(rc.nmin, rc.ncnt, rc.ncnt2, gn & kNone);
-        } else {
-          g0[u] = (uint16_t)((gn & kNone) + 1u);
-        }
-        rec[u] = rc;
-        if (!ok) dirty[u] = 1;
       }
-      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        if ((m >> q) & 1u) {
+          uint16_t* gr = myrow(q);
+          gr[old] = (uint16_t)(go[q] - 1u);
+          gr[nw] = (uint16_t)(gn[q] + 1u);
+          const bool fo = (go[q] & kFlag) != 0, fn = (gn[q] & kFlag) != 0;
+          const bool is_old = colq[q] == old, is_new = colq[q] == nw;
+          // the old colour's key drops by one, the new colour's rises by one (when neither is
+          // the vertex's own colour, whose gamma is g0)
+          uint32_t wo = fo ? recq[q].y : recq[q].x;
+          wo = cw_dec(wo, go[q] & kNone);
+          if (!is_old) { if (fo) recq[q].y = wo; else recq[q].x = wo; }
+          bool ok = true;
+          uint32_t wn = fn ? recq[q].y : recq[q].x;
+          wn = cw_inc(wn, gn[q] & kNone, ok);
+          if (!is_new) { if (fn) recq[q].y = wn; else recq[q].x = wn; }
+          g0q[q] = is_old ? (int)(go[q] & kNone) - 1 : (is_new ? (int)(gn[q] & kNone) + 1 : g0q[q]);
+          dmask |= (ok || is_new) ? 0u : (1u << q);
+        }
+      }
     }
     // rows whose summary could not be adjusted, summarised again by the warp (lanes over colours)
-    {
-      uint32_t dm = 0;
-      for (int q = 0; q < per; q += 2) {
-        const uint32_t x = *(const uint16_t*)(dirty + v0 + q);
-        if (x & 0xFFu) dm |= 1u << q;
-        if (x >> 8) dm |= 2u << q;
-      }
-      for (unsigned pend = __ballot_sync(FULL, dm != 0); pend; pend &= pend - 1) {
-        const int l = __ffs(pend) - 1;
-        uint32_t fl = __shfl_sync(FULL, dm, l);
-        const int base = (warp * 32 + l) * per;
-        for (; fl; fl &= fl - 1) {
-          const int u = base + __ffs(fl) - 1;
-          const Rec r = summarise((const uint32_t*)(gam + (size_t)u * ks), kw, colS[u], lane);
-          if (lane == 0) {
-            rec[u] = r;
-            dirty[u] = 0;
-            ++w_resum;
-          }
+    if (__any_sync(FULL, dmask != 0)) {
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        for (unsigned pend = __ballot_sync(FULL, (dmask >> q) & 1u); pend; pend &= pend - 1) {
+          const int l = __ffs(pend) - 1;
+          const int cu = __shfl_sync(FULL, colq[q], l);
+          const uint2 r = summarise((const uint32_t*)(gam + (q * NT + warp * 32 + l) * ks), kw, cu, lane);
+          if (lane == l) recq[q] = r;
+          if (lane == 0) ++w_resum;
         }
       }
-      if (improved)
-        for (int q = 0; q < per; q += 2) *(uint16_t*)(bestS + v0 + q) = *(const uint16_t*)(colS + v0 + q);
-      __syncwarp();
+    }
+    if (improved) {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) bestS[v0 + q] = (uint8_t)colq[q];
     }
     select();  // the next iteration's selection
   }
@@ -710,12 +720,18 @@ __device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const u
   const int err = sc[SC_ERR], stop = sc[SC_STOP];
   long long* wk = (long long*)(gs + L.red);
   bar();  // every warp has left the loop: red[] is free
-  if (lane == 0) {
-    wk[4 * warp + 0] = w_rows;
-    wk[4 * warp + 1] = w_deg;
-    wk[4 * warp + 2] = w_resum;
+  {
+    long long d = w_deg;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULL, d, o);
+    if (lane == 0) {
+      wk[4 * warp + 0] = w_rows;
+      wk[4 * warp + 1] = d;
+      wk[4 * warp + 2] = w_resum;
+    }
   }
-  for (int q = 0; q < per; ++q) {
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
     const int v = v0 + q;
     if (v < n) gcol[v] = (int16_t)bestS[v];
   }
@@ -736,10 +752,10 @@ __device__ void run_individual(const GroupArgs& a, int ind, uint8_t* gs, const u
   bar();  // shared memory is reused by the next individual
 }
 
-template <int W, bool BSM>
-__global__ void __launch_bounds__(32 * W * GroupMax<W>::value) tabucol_group_kernel(GroupArgs a) {
+template <int PER, bool BSM>
+__global__ void __launch_bounds__(max_threads_for(PER)) tabucol_group_kernel(GroupArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const int G = a.G;
+  const int G = a.G, W = a.W;
   const int grp = threadIdx.x / (32 * W);
   const uint32_t* bits = a.bits;
   if (BSM) {  // the graph's bit rows, shared by the CTA's individuals
@@ -757,31 +773,25 @@ __global__ void __launch_bounds__(32 * W * GroupMax<W>::value) tabucol_group_ker
   uint8_t* gs = smem + a.bits_bytes + (size_t)grp * a.group_bytes;
   const int slot = blockIdx.x * G + grp;
   uint2* far = a.far ? a.far + (size_t)slot * (size_t)a.far_cap : nullptr;
-  for (int i = slot; i < a.pop; i += gridDim.x * G) run_individual<W, BSM>(a, i, gs, bits, 1 + grp, far);
+  for (int i = slot; i < a.pop; i += gridDim.x * G) run_individual<PER, BSM>(a, W, i, gs, bits, 1 + grp, far);
 }
 
-template <int W, bool BSM>
+template <int PER, bool BSM>
 static dlm_status launch_one(dlm_ctx* ctx, GroupArgs a, int grid, size_t smem) {
-  auto kfn = tabucol_group_kernel<W, BSM>;
+  auto kfn = tabucol_group_kernel<PER, BSM>;
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  kfn<<<grid, 32 * W * a.G, smem, ctx->stream>>>(a);
+  kfn<<<grid, 32 * a.W * a.G, smem, ctx->stream>>>(a);
   return launch_check(ctx, "tabucol_group_kernel");
 }
 
-template <int W>
-static int occupancy(int G, size_t smem, bool bsm) {
+template <int PER, bool BSM>
+static int occupancy_one(int threads, size_t smem) {
   int per_sm = 0;
-  cudaError_t e;
-  if (bsm) {
-    e = cudaFuncSetAttribute(tabucol_group_kernel<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_group_kernel<W, true>, 32 * W * G, smem);
-  } else {
-    e = cudaFuncSetAttribute(tabucol_group_kernel<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_group_kernel<W, false>, 32 * W * G, smem);
-  }
+  cudaError_t e = cudaFuncSetAttribute(tabucol_group_kernel<PER, BSM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_group_kernel<PER, BSM>, threads, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -793,28 +803,16 @@ static int occupancy(int G, size_t smem, bool bsm) {
 
 using namespace tg;
 
-static int group_max_for(int W) {
-  switch (W) {
-    case 1: return GroupMax<1>::value;
-    case 2: return GroupMax<2>::value;
-    case 4: return GroupMax<4>::value;
-    case 8: return GroupMax<8>::value;
-    case 16: return GroupMax<16>::value;
-    default: return GroupMax<32>::value;
-  }
-}
-
 bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_sms, int ring_force,
                 GroupPlan* out) {
-  if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16 && W != 32) return false;
+  if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16) return false;
   const int NT = 32 * W;
-  int per = (n + NT - 1) / NT;
-  per = (per + 1) & ~1;  // even: vertices are read in pairs
-  if (per < 2) per = 2;
-  if (per > 32) return false;
+  int per = 2;
+  while (per < 8 && per * NT < n) per *= 2;  // a power of two up to 8: each value is its own kernel
+  if (per * NT < n) return false;
   const size_t bits_bytes = a16(((size_t)n * words + 1) * 4);
   const int gmax_pop = std::max(1, (pop + num_sms - 1) / std::max(1, num_sms));
-  const int gmax = std::min(group_max_for(W), gmax_pop);
+  const int gmax = std::min(std::min(max_threads_for(per) / NT, 8), gmax_pop);
   auto ring_for = [&](int G, bool bsm, int* R) -> bool {
     for (int r = ring_force > 0 ? ring_force : 8192; r >= 64; r >>= 1) {
       const size_t tot = (size_t)G * group_layout(n, k, W, per, r).total + (bsm ? bits_bytes : 0);
@@ -839,6 +837,25 @@ bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_s
   return false;
 }
 
+template <int PER>
+static dlm_status launch_per(dlm_ctx* ctx, const GroupArgs& a, const GroupPlan& P) {
+  const int threads = 32 * P.W * P.G;
+  const int per_sm = P.bsm ? occupancy_one<PER, true>(threads, P.smem) : occupancy_one<PER, false>(threads, P.smem);
+  const int blocks = (a.pop + P.G - 1) / P.G;
+  const int grid = std::max(1, std::min(blocks, per_sm * ctx->num_sms));
+  GroupArgs b = a;
+  // far list: tabu entries whose tenure does not fit the ring. A pair holds at most one live
+  // entry, at most one entry is made per iteration and a tenure never exceeds L_max + alpha |E|,
+  // so n (k - 1) + 1 entries, the budget + 1 and L_max + alpha |E| + 1 each bound what one search
+  // keeps there at once.
+  if (b.far_cap > 0) {
+    void* ws = nullptr;
+    DLM_TRY(ctx_workspace(ctx, (size_t)grid * P.G * (size_t)b.far_cap * sizeof(uint2), &ws));
+    b.far = (uint2*)ws;
+  }
+  return P.bsm ? launch_one<PER, true>(ctx, b, grid, P.smem) : launch_one<PER, false>(ctx, b, grid, P.smem);
+}
+
 dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                 int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                                 uint32_t generation, uint32_t ind_base, const GroupPlan& P, int32_t* trace,
@@ -846,27 +863,15 @@ dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
   GroupArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = g->n; a.k = k; a.ks = group_row_stride(k); a.words = g->words; a.pop = pop; a.G = P.G; a.R = P.R;
-  a.per = P.per;
+  a.W = P.W; a.per = P.per;
   a.bits = g->d_bits; a.col = col; a.best_f = best_f; a.moves = moves; a.trace = trace; a.work = work;
   a.iters = iters; a.ind_base = ind_base;
   a.L1 = (uint32_t)tenure.L_max + 1u; a.an = tenure.alpha_num; a.ad = tenure.alpha_den;
   a.seed = seed; a.gen = generation; a.status = ctx->d_status; a.cancel = ctx->cancel;
   a.group_bytes = P.group_bytes; a.bits_bytes = P.bits_bytes;
-  int per_sm = 1;
-  switch (P.W) {
-    case 1: per_sm = occupancy<1>(P.G, P.smem, P.bsm); break;
-    case 2: per_sm = occupancy<2>(P.G, P.smem, P.bsm); break;
-    case 4: per_sm = occupancy<4>(P.G, P.smem, P.bsm); break;
-    case 8: per_sm = occupancy<8>(P.G, P.smem, P.bsm); break;
-    case 16: per_sm = occupancy<16>(P.G, P.smem, P.bsm); break;
-    default: per_sm = occupancy<32>(P.G, P.smem, P.bsm); break;
-  }
-  const int blocks = (pop + P.G - 1) / P.G;
-  const int grid = std::max(1, std::min(blocks, per_sm * ctx->num_sms));
-  // far list: tabu entries whose tenure does not fit the ring. A pair holds at most one live
-  // entry, at most one entry is made per iteration and a tenure never exceeds L_max + alpha |E|,
-  // so n (k - 1) + 1 entries, the budget + 1 and L_max + alpha |E| + 1 each bound what one search
-  // keeps there at once.
+  // floor(x / alpha_den) for x < 2^32 as the high word of x * ceil(2^64 / alpha_den) (division by
+  // an invariant integer through a multiplication, Granlund and Montgomery 1994)
+  a.ad_recip = tenure.alpha_den >= 2 ? ~0ull / (uint64_t)tenure.alpha_den + 1ull : 0ull;
   const uint64_t tt_max = (uint64_t)tenure.L_max + ((uint64_t)tenure.alpha_num * (uint64_t)g->m) / tenure.alpha_den;
   int64_t far_cap = 0;
   if (tt_max >= (uint64_t)P.R) {
@@ -874,18 +879,10 @@ dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
     far_cap = std::min<int64_t>(far_cap, (int64_t)tt_max + 1);
   }
   a.far_cap = (int32_t)far_cap;
-  if (far_cap > 0) {
-    void* ws = nullptr;
-    DLM_TRY(ctx_workspace(ctx, (size_t)grid * P.G * (size_t)far_cap * sizeof(uint2), &ws));
-    a.far = (uint2*)ws;
-  }
-  switch (P.W) {
-    case 1: return P.bsm ? launch_one<1, true>(ctx, a, grid, P.smem) : launch_one<1, false>(ctx, a, grid, P.smem);
-    case 2: return P.bsm ? launch_one<2, true>(ctx, a, grid, P.smem) : launch_one<2, false>(ctx, a, grid, P.smem);
-    case 4: return P.bsm ? launch_one<4, true>(ctx, a, grid, P.smem) : launch_one<4, false>(ctx, a, grid, P.smem);
-    case 8: return P.bsm ? launch_one<8, true>(ctx, a, grid, P.smem) : launch_one<8, false>(ctx, a, grid, P.smem);
-    case 16: return P.bsm ? launch_one<16, true>(ctx, a, grid, P.smem) : launch_one<16, false>(ctx, a, grid, P.smem);
-    default: return P.bsm ? launch_one<32, true>(ctx, a, grid, P.smem) : launch_one<32, false>(ctx, a, grid, P.smem);
+  switch (P.per) {
+    case 2: return launch_per<2>(ctx, a, P);
+    case 4: return launch_per<4>(ctx, a, P);
+    default: return launch_per<8>(ctx, a, P);
   }
 }
 

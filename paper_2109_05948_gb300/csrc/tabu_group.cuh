@@ -15,11 +15,11 @@ __host__ __device__ inline int group_row_stride(int k) {
 
 // byte offsets of one individual's arrays within its group's shared memory
 struct GroupLayout {
-  size_t gam, rec, g0, col, best, dirty, nb, ring, due, red, sc, total;
+  size_t gam, col, best, ring, due, red, sc, total;
 };
 
 struct GroupArgs {
-  int32_t n, k, ks, words, pop, G, R, per;
+  int32_t n, k, ks, words, pop, W, G, R, per;
   const uint32_t* bits;  // device [n][words] adjacency bit rows
   int16_t* col;          // [pop][n] in: start colourings, out: best colourings
   int64_t* best_f;       // [pop]
@@ -30,6 +30,7 @@ struct GroupArgs {
   uint32_t ind_base;
   uint32_t L1;           // L_max + 1
   int32_t an, ad;        // alpha = an / ad
+  uint64_t ad_recip;     // ceil(2^64 / ad) for ad >= 2
   uint64_t seed;
   uint32_t gen;
   int32_t* status;
