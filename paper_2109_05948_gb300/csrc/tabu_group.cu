@@ -47,7 +47,8 @@ constexpr int kDueCap = 32;          // expiring ring entries listed per iterati
 enum { SC_MV = 0, SC_OLD, SC_NEW, SC_F,          // the iteration's move and f after it
        SC_DUE, SC_LO, SC_NINS, SC_FARN,          // expiring entries (count | far flag << 30), ring window, far list size
        SC_STOP, SC_ERR, SC_BAD, SC_FARMIN,
-       SC_REQV, SC_REQC, SC_REQTT, SC_REQWAS,    // the move's tabu entry for the ring (v < 0: none)
+       SC_REQ = 12,                              // two int4 (by iteration parity): the move's tabu entry
+                                                 // (v, c, tenure, was tabu) for the ring, v < 0: none
        SC_N = 32 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -251,7 +252,8 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
   bar();
   if (bad) sc[SC_BAD] = 1;
   if (tid == 0) {
-    sc[SC_REQV] = -1;
+    sc[SC_REQ] = -1;
+    sc[SC_REQ + 4] = -1;
     sc[SC_FARMIN] = -1;
   }
   bar();
@@ -337,6 +339,7 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
   for (it = 0; it < iters; ++it) {
     if (f == 0) break;
     bar();
+    uint32_t dmask = 0;  // own rows to summarise again
     // ---- (D) minimum delta, tie rank, move; ring maintenance ----------------------------------
     if ((it & 31) == 0 && it > 0) {
       rr = rng(a.seed, (uint32_t)(it + lane), a.gen, ind_id, kTagTabu);
@@ -428,13 +431,46 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
           }
         }
       }
+      const bool good = v >= 0 && mc >= 0 && mc < k;
       if (lane == 0) {
-        if (v >= 0 && mc >= 0 && mc < k) {
+        if (good) {
           *(int4*)(sc + SC_MV) = make_int4(v, colv, mc, f + dstar);
           if (a.trace) reinterpret_cast<int4*>(a.trace)[(size_t)ind * iters + it] = make_int4(v, mc, dstar, T);
         } else {
           sc[SC_ERR] = 2;  // tie counts inconsistent with the row: refuse to move
         }
+      }
+      if (good && lane == hl) {  // the deciding lane owns the moved vertex: it updates the row now
+        const int qs = v - v0;
+        uint2 rc = recq[0];
+#pragma unroll
+        for (int q = 1; q < PER; ++q) rc = q == qs ? recq[q] : rc;
+        uint16_t* gr = rowof(v);
+        const unsigned go = gr[colv], gn = gr[mc];
+        const bool was = (go & kFlag) != 0;
+        // alpha f (f after the move): 32-bit unsigned (the host bounds alpha_num * |E| below
+        // 2^32), divided by alpha_den through its precomputed 64-bit reciprocal
+        const uint32_t af = (uint32_t)a.an * (uint32_t)(f + dstar);
+        const uint32_t tt = below(r1, a.L1) + (a.ad == 1 ? af : (uint32_t)__umul64hi((uint64_t)af, a.ad_recip));
+        const bool tabu = tt > 0;
+        gr[colv] = (uint16_t)((go & kNone) | (tabu ? kFlag : 0u));
+        // the new colour leaves its class, the old one joins the tabu (or the free) class
+        bool ok;
+        if (gn & kFlag) rc.y = cw_rem(rc.y, gn & kNone, ok);
+        else rc.x = cw_rem(rc.x, gn & kNone, ok);
+        if (tabu) rc.y = cw_ins(rc.y, go & kNone);
+        else rc.x = cw_ins(rc.x, go & kNone);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          if (q == qs) {
+            recq[q] = rc;
+            colq[q] = mc;
+            g0q[q] = (int)(gn & kNone);
+          }
+        }
+        dmask |= ok ? 0u : (1u << qs);
+        *(int4*)(sc + SC_REQ + 4 * (it & 1)) =
+            (tabu || was) ? make_int4(v, colv, (int32_t)tt, was ? 1 : 0) : make_int4(-1, 0, 0, 0);
       }
     }
     if (tid == 0) {
@@ -472,12 +508,13 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
       }
       // (b) the previous iteration's move: drop the pair's older entry when it was still tabu,
       // then insert the new one (tabu until it + tt)
-      const int rv = sc[SC_REQV];
+      int32_t* req = sc + SC_REQ + 4 * ((it + 1) & 1);  // written by the previous iteration's decider
+      const int rv = req[0];
       if (rv >= 0) {
-        const int rc = sc[SC_REQC];
-        const uint32_t rtt = (uint32_t)sc[SC_REQTT];
+        const int rc = req[1];
+        const uint32_t rtt = (uint32_t)req[2];
         const uint32_t key = (uint32_t)rv | ((uint32_t)rc << 16);
-        if (sc[SC_REQWAS]) {
+        if (req[3]) {
           bool done = false;
           for (int b = lo; b < nins && !done; b += 32) {
             const int s = b + lane;
@@ -519,7 +556,7 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
           }
         }
         __syncwarp();
-        if (lane == 0) sc[SC_REQV] = -1;
+        if (lane == 0) req[0] = -1;
       }
       // (c) entries that expire before the next selection (no longer tabu at it + 1), and which
       // warps own their rows
@@ -558,7 +595,6 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
     if (C.x | C.y) break;
     int mv = -1, old = -1, nw = -1;
     bool improved = false;
-    uint32_t dmask = 0;  // own rows to summarise again
     if (T > 0) {
       mv = A.x;
       old = A.y;
@@ -567,37 +603,6 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
       ++moves;
       improved = f < best_f;
       best_f = improved ? f : best_f;
-      if (mv >= v0 && mv < v0 + PER) {  // the owner of the moved vertex updates its row
-        const int qs = mv - v0;
-        uint2 rc = recq[0];
-#pragma unroll
-        for (int q = 1; q < PER; ++q) rc = q == qs ? recq[q] : rc;
-        uint16_t* gr = rowof(mv);
-        const unsigned go = gr[old], gn = gr[nw];
-        const bool was = (go & kFlag) != 0;
-        // alpha f: 32-bit unsigned (the host bounds alpha_num * |E| below 2^32), divided by
-        // alpha_den through its precomputed 64-bit reciprocal
-        const uint32_t af = (uint32_t)a.an * (uint32_t)f;
-        const uint32_t tt = below(r1, a.L1) + (a.ad == 1 ? af : (uint32_t)__umul64hi((uint64_t)af, a.ad_recip));
-        const bool tabu = tt > 0;
-        gr[old] = (uint16_t)((go & kNone) | (tabu ? kFlag : 0u));
-        // the new colour leaves its class, the old one joins the tabu (or the free) class
-        bool ok;
-        if (gn & kFlag) rc.y = cw_rem(rc.y, gn & kNone, ok);
-        else rc.x = cw_rem(rc.x, gn & kNone, ok);
-        if (tabu) rc.y = cw_ins(rc.y, go & kNone);
-        else rc.x = cw_ins(rc.x, go & kNone);
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          if (q == qs) {
-            recq[q] = rc;
-            colq[q] = nw;
-            g0q[q] = (int)(gn & kNone);
-          }
-        }
-        dmask |= ok ? 0u : (1u << qs);
-        if (tabu || was) *(int4*)(sc + SC_REQV) = make_int4(mv, old, (int32_t)tt, was ? 1 : 0);
-      }
     }
     // expiring entries of this thread's rows, in list order (several may touch one row)
     auto expire = [&](int v, int c) {
