@@ -88,6 +88,9 @@ def parse():
     ap.add_argument("--mem-max-gens", type=int, default=40)
     ap.add_argument("--mem-time-limit", type=float, default=120.0, help="seconds per run")
     ap.add_argument("--warps", type=int, default=0, help="warps per individual (0: the library's default)")
+    ap.add_argument("--traffic-from", default=None,
+                    help="write profiles/tabucol_C2_dram.json from this ncu CSV of one tabu launch and exit")
+    ap.add_argument("--traffic-command", default="", help="the ncu command that wrote --traffic-from")
     ap.add_argument("--warm-start", type=int, default=0,
                     help="run this many iterations first (untimed) and start every step from their best "
                          "colourings (profiling the late phase of the search)")
@@ -150,8 +153,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    # one individual per host core over the workload's full budget: the same per-individual work as
+    # the GPU arm, on a sample of the population
     n_ind = min(16, os.cpu_count() or 1)
-    iters = max(1000, min(args.iters, 20_000))
+    iters = args.iters
     for _ in range(args.warmup):
         oracle_sample(n_ind, iters)
     moves = 0
@@ -173,22 +178,57 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the tabu kernel from the committed ncu summary, or None when the
-    kernel source has changed since the counters were taken."""
-    import hashlib
-    import re
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "tabucol_C2_dram.json")
+TABU_SOURCES = [os.path.join(ROOT, "paper_2109_05948_gb300", "csrc", f) for f in ("tabu_group.cu", "tabu_group.cuh")]
 
-    path = os.path.join(ROOT, "profiles", "tabucol_C2_launches.md")
-    src = os.path.join(ROOT, "paper_2109_05948_gb300", "csrc", "tabu.cu")
+
+def tabu_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TABU_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM (and L2) bytes per launch of the tabu kernel, written by --traffic-from from an ncu
+    capture, or None when the kernel's source has changed since the counters were taken."""
     try:
-        txt = open(path).read()
-        h = re.search(r"kernel_source_sha256_16 = ([0-9a-f]{16})", txt).group(1)
-        b = int(re.search(r"dram_bytes_per_launch = (\d+)", txt).group(1))
+        rec = json.load(open(TRAFFIC_JSON))
     except Exception:
         return None
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return b if cur == h else None
+    return rec if rec.get("kernel_source_sha256_16") == tabu_source_hash() else None
+
+
+def write_traffic(csv_path, command):
+    """Reads the ncu CSV of one tabu launch (dram__bytes_read.sum, dram__bytes_write.sum,
+    lts__t_bytes.sum, gpu__time_duration.sum; --print-units base) and writes the per-launch
+    counters with the hash of the kernel's source to profiles/tabucol_C2_dram.json."""
+    import csv
+
+    vals = {}
+    with open(csv_path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    for row in csv.DictReader(lines):
+        if "tabucol_group" not in row.get("Kernel Name", ""):
+            continue
+        name = row.get("Metric Name")
+        try:
+            vals[name] = float(row.get("Metric Value", "").replace(",", ""))
+        except ValueError:
+            pass
+    need = ("dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum")
+    if not all(k in vals for k in need):
+        raise SystemExit(f"{csv_path}: no tabucol_group launch with {need}")
+    rec = {"dram_bytes_per_launch": vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"],
+           "dram_read_bytes": vals["dram__bytes_read.sum"], "dram_write_bytes": vals["dram__bytes_write.sum"],
+           "l2_bytes_per_launch": vals.get("lts__t_bytes.sum"), "duration_ns": vals["gpu__time_duration.sum"],
+           "kernel_source_sha256_16": tabu_source_hash(), "command": command}
+    with open(TRAFFIC_JSON, "w") as fh:
+        json.dump(rec, fh, indent=1)
+        fh.write("\n")
+    print(json.dumps(rec))
 
 
 # ------------------------------------------------------------------------------------------------
@@ -812,6 +852,9 @@ def run_scorer(args):
 
 def main():
     args = parse()
+    if args.traffic_from:
+        write_traffic(args.traffic_from, args.traffic_command)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -870,6 +913,8 @@ def main():
     work = torch.zeros((max(1, args.steps), pop, 3), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     smem_gbps = dlmcol.dlm_probe_smem_bandwidth(ctx)
+    l2_gbps = dlmcol.dlm_probe_l2_bandwidth(ctx)
+    launch = dlmcol.dlm_tabucol_launch_info(ctx, g, K, pop, args.warps)
     stream = torch.cuda.current_stream(dev)
 
     def step(s, timed):
@@ -917,28 +962,47 @@ def main():
     # (8 B), and each move reads the moved vertex's adjacency bit row (ceil(n / 8) B). The
     # conflicting rows and the degrees are counted by the kernel itself over the timed launches.
     alg_bytes = (4 * (K - 1) * wk[0] + 8 * wk[1] + ((N + 7) // 8) * local_moves) / args.steps
-    # bytes the kernel itself moves in shared memory (it evaluates a conflicting row from an
-    # 8-byte summary instead of its k - 1 entries): every conflicting row evaluated reads its colour
-    # (1 B), gamma[v][col v] (2 B) and its summary (8 B) and writes its selection result (4 B);
-    # every neighbour of a moved vertex costs its colour (1 B), two u16 gamma read-modify-writes
-    # (8 B), two u16 tabu reads (4 B) and its summary read and write (16 B); every re-summarised
-    # row reads its k gamma and k tabu entries (4k B) and its colour and writes its summary (9 B);
-    # every iteration reads the n summaries' expiry (2 B each)
-    kern_bytes = (15 * wk[0] + 29 * wk[1] + (4 * K + 9) * wk[2] + 2 * N * local_moves) / args.steps
+    # bytes the kernel itself moves in shared memory: the grouped kernel keeps every row's colour,
+    # gamma[v][col v] and class summaries in its owner thread's registers, so it evaluates a
+    # conflicting row without touching shared memory; each neighbour of a moved vertex costs two
+    # u16 gamma read-modify-writes (8 B), and each move (the colour search of the moved vertex)
+    # and each row summarised again reads the row's gamma entries with their tabu flags (2 ks B,
+    # ks the row stride)
+    ks = 2 * ((K + 1) // 2 + (1 - ((K + 1) // 2) % 2))
+    kern_bytes = (8 * wk[1] + 2 * ks * (local_moves + wk[2])) / args.steps
+    # L2: the moved vertex's adjacency bit row (ceil(n / 8) B per move) when the bit rows are not
+    # held in shared memory
+    l2_bytes = 0 if launch["bits_in_smem"] else ((N + 7) // 8) * local_moves / args.steps
     kmean = sum(kms) / len(kms)
     achieved = alg_bytes / (kmean / 1e3) / 1e9
     kern_gbps = kern_bytes / (kmean / 1e3) / 1e9
+    l2_achieved = l2_bytes / (kmean / 1e3) / 1e9
+    # cycles of one iteration of one individual: the launch's time at the sampled SM clock over the
+    # iterations each individual slot runs
+    sm_mhz = (ck or {}).get("sm_mhz") or 0.0
+    slot_iters = pop * iters / max(1, launch["slots"])
+    cyc_it = kmean * 1e-3 * sm_mhz * 1e6 / slot_iters if sm_mhz else None
+    per_sm = launch["slots"] / max(1, min(launch["grid"], torch.cuda.get_device_properties(dev).multi_processor_count))
     roofline = {"bound": "smem", "achieved": achieved, "peak": smem_gbps, "unit": "GB/s",
                 "frac": achieved / smem_gbps, "traffic": None,
-                "kernel": "tabucol_batch_kernel", "kernel_ms": kmean,
+                "kernel": "tabucol_group_kernel" if launch["grouped"] else "tabucol_batch_kernel", "kernel_ms": kmean,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads)",
                 "kernel_smem_bytes_per_launch": kern_bytes, "kernel_smem_gbps": kern_gbps,
                 "kernel_smem_frac": kern_gbps / smem_gbps,
+                "l2": {"achieved": l2_achieved, "peak": l2_gbps, "unit": "GB/s", "frac": l2_achieved / l2_gbps,
+                       "bytes_per_launch": l2_bytes,
+                       "peak_source": "measured by dlm_probe_l2_bandwidth on this GPU (L1-bypassing 16 B loads)"},
+                "launch": launch,
+                "cycles_per_iteration_per_individual": cyc_it,
+                "cycles_per_iteration_per_sm": cyc_it / per_sm if cyc_it else None,
                 "work": {"rows_evaluated_per_launch": wk[0] / args.steps,
                          "neighbour_updates_per_launch": wk[1] / args.steps,
                          "rows_resummarised_per_launch": wk[2] / args.steps}}
-    roofline["traffic"] = recorded_traffic()
+    rec = recorded_traffic()  # counters of one launch of this default workload, same kernel source
+    if rec and pop == POP and iters == ITERS:
+        roofline["traffic"] = rec["dram_bytes_per_launch"]
+        roofline["traffic_source"] = os.path.relpath(TRAFFIC_JSON, ROOT)
 
     e2e = None
     if not args.no_e2e:

@@ -408,6 +408,19 @@ dlm_status dlm_gemm_bf16(dlm_ctx* ctx, const void* A, const void* B, float* C, i
  * ------------------------------------------------------------------------------------------- */
 dlm_status dlm_probe_smem_bandwidth(dlm_ctx* ctx, double* gbps);
 
+/* L2 read bandwidth of this GPU in GB/s (the paper has no counterpart: measurement support): every
+ * SM streams 16-byte loads that bypass L1 over a 32 MB buffer held in L2, 16 passes after a warm-up
+ * pass; uses the context's workspace and synchronises its stream. */
+dlm_status dlm_probe_l2_bandwidth(dlm_ctx* ctx, double* gbps);
+
+/* How dlm_tabucol_batch would run a problem (the paper has no counterpart: measurement support).
+ * info (host, 8 int32): [0] 1 = several individuals per CTA (tabu flags inside gamma), 0 = one
+ * individual per CTA; [1] warps per individual; [2] individuals per CTA; [3] tabu ring entries;
+ * [4] vertices per thread; [5] 1 = the graph's bit rows in shared memory; [6] CTAs launched;
+ * [7] individual slots (CTAs x individuals per CTA). warps = 0: the library's choice. */
+dlm_status dlm_tabucol_launch_info(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int32_t warps,
+                                   int32_t* info);
+
 /* ---------------------------------------------------------------------------------------------
  * Measurement utility (no counterpart in the paper): while enabled (enable != 0), every launch of
  * the tensor-core GEMM kernel made through ctx (scorer forward, scorer backward, dlm_gemm_bf16)

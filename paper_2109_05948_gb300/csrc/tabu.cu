@@ -745,6 +745,39 @@ extern "C" dlm_status dlm_tabucol_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int
                      warps_per_individual, trace, work);
 }
 
+extern "C" dlm_status dlm_tabucol_launch_info(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop,
+                                              int32_t warps, int32_t* info) {
+  if (!ctx || !g || !info || pop <= 0 || k < 2 || k > 128) return fail(ctx, DLM_EINVAL, "launch_info: bad arguments");
+  if (warps == 0) warps = lookup_tune(ctx, g->n, k);
+  GroupPlan P;
+  if (group_plan(g->n, k, g->words, warps ? warps : default_group_warps(g->n), ctx->smem_optin, pop, ctx->num_sms, 0,
+                 &P)) {
+    const int grid = group_grid(ctx, P, pop);
+    const int32_t v[8] = {1, P.W, P.G, P.R, P.per, P.bsm ? 1 : 0, grid, grid * P.G};
+    for (int i = 0; i < 8; ++i) info[i] = v[i];
+    return DLM_OK;
+  }
+  if (warps == 0) warps = default_warps_batch(ctx, g->n, k);
+  const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
+  int grid = pop;
+  if (L.rs < g->n) {
+    int per_sm = 1;
+    switch (warps) {
+      case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<1>, 32, L.total); break;
+      case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<2>, 64, L.total); break;
+      case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<4>, 128, L.total); break;
+      case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<8>, 256, L.total); break;
+      case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<16>, 512, L.total); break;
+      default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<32>, 1024, L.total); break;
+    }
+    cudaGetLastError();
+    grid = std::min(pop, std::max(1, per_sm) * ctx->num_sms);
+  }
+  const int32_t v[8] = {0, warps, 1, 0, (g->n + 32 * warps - 1) / (32 * warps), 0, grid, grid};
+  for (int i = 0; i < 8; ++i) info[i] = v[i];
+  return DLM_OK;
+}
+
 extern "C" dlm_status dlm_tabucol_batch_opts(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                              int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure,
                                              uint64_t seed, uint32_t generation, uint32_t ind_base,

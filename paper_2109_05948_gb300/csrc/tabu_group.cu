@@ -842,12 +842,21 @@ bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_s
   return false;
 }
 
+int group_grid(dlm_ctx* ctx, const GroupPlan& P, int pop) {
+  const int threads = 32 * P.W * P.G;
+  int per_sm = 1;
+  switch (P.per) {
+    case 2: per_sm = P.bsm ? occupancy_one<2, true>(threads, P.smem) : occupancy_one<2, false>(threads, P.smem); break;
+    case 4: per_sm = P.bsm ? occupancy_one<4, true>(threads, P.smem) : occupancy_one<4, false>(threads, P.smem); break;
+    default: per_sm = P.bsm ? occupancy_one<8, true>(threads, P.smem) : occupancy_one<8, false>(threads, P.smem); break;
+  }
+  const int blocks = (pop + P.G - 1) / P.G;
+  return std::max(1, std::min(blocks, per_sm * ctx->num_sms));
+}
+
 template <int PER>
 static dlm_status launch_per(dlm_ctx* ctx, const GroupArgs& a, const GroupPlan& P) {
-  const int threads = 32 * P.W * P.G;
-  const int per_sm = P.bsm ? occupancy_one<PER, true>(threads, P.smem) : occupancy_one<PER, false>(threads, P.smem);
-  const int blocks = (a.pop + P.G - 1) / P.G;
-  const int grid = std::max(1, std::min(blocks, per_sm * ctx->num_sms));
+  const int grid = group_grid(ctx, P, a.pop);
   GroupArgs b = a;
   // far list: tabu entries whose tenure does not fit the ring. A pair holds at most one live
   // entry, at most one entry is made per iteration and a tenure never exceeds L_max + alpha |E|,

@@ -53,6 +53,10 @@ struct GroupPlan {
 bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_sms, int ring_force,
                 GroupPlan* out);
 
+// CTAs the grouped launch of `pop` individuals uses (resident CTAs at most; each loops over its
+// individuals)
+int group_grid(dlm_ctx* ctx, const GroupPlan& plan, int pop);
+
 dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                 int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                                 uint32_t generation, uint32_t ind_base, const GroupPlan& plan, int32_t* trace,

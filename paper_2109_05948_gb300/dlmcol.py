@@ -95,6 +95,8 @@ _SIGS = {
     "dlm_scorer_save": (_i32, [_P, _P, _P]),
     "dlm_scorer_load": (_i32, [_P, _P, _P]),
     "dlm_probe_smem_bandwidth": (_i32, [_P, _P]),
+    "dlm_probe_l2_bandwidth": (_i32, [_P, _P]),
+    "dlm_tabucol_launch_info": (_i32, [_P, _P, _i32, _i32, _i32, _P]),
     "dlm_gemm_bf16": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32]),
     "dlm_gemm_profile": (_i32, [_P, _i32]),
     "dlm_gemm_profile_read": (_i32, [_P, _P, _P, _P]),
@@ -428,6 +430,21 @@ def dlm_probe_smem_bandwidth(ctx):
     g = ctypes.c_double(0.0)
     ctx.check(lib().dlm_probe_smem_bandwidth(ctx.h, ctypes.byref(g)), "dlm_probe_smem_bandwidth")
     return g.value
+
+
+def dlm_probe_l2_bandwidth(ctx):
+    g = ctypes.c_double(0)
+    ctx.check(lib().dlm_probe_l2_bandwidth(ctx.h, ctypes.byref(g)), "dlm_probe_l2_bandwidth")
+    return g.value
+
+
+def dlm_tabucol_launch_info(ctx, g, k, pop, warps=0):
+    """dict(grouped, warps, groups, ring, per, bits_in_smem, grid, slots) of the launch the library
+    would make for this problem."""
+    info = (ctypes.c_int32 * 8)()
+    ctx.check(lib().dlm_tabucol_launch_info(ctx.h, g.h, k, pop, warps, info), "dlm_tabucol_launch_info")
+    keys = ("grouped", "warps", "groups", "ring", "per", "bits_in_smem", "grid", "slots")
+    return dict(zip(keys, [int(x) for x in info]))
 
 
 def dlm_wvcp_tabu_batch(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure=WVCP_TENURE, phi=0, seed=0,
