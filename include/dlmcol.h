@@ -259,8 +259,16 @@ int64_t dlm_scorer_nparams(const dlm_scorer* s);
 /* params: device [nparams] float32 (copy out / copy in; set also resets the Adam state). */
 dlm_status dlm_scorer_get_params(dlm_ctx* ctx, dlm_scorer* s, float* params);
 dlm_status dlm_scorer_set_params(dlm_ctx* ctx, dlm_scorer* s, const float* params);
-/* Scores c colourings: col device [c][n] int16, out device [c] float32. */
+/* Scores c colourings: col device [c][n] int16, out device [c] float32. By default the
+ * activations between layers are kept as bf16 hi + lo pairs (about 16 mantissa bits, three MMA
+ * passes per layer product), which holds every score's colour-dependent part (score minus the
+ * head bias) within 1e-2 of FP64. */
 dlm_status dlm_score_offspring(dlm_ctx* ctx, dlm_scorer* s, const int16_t* col, int32_t c, float* out);
+/* split = 1 (default): scoring activations as bf16 hi + lo; split = 0: bf16 activations alone
+ * (two MMA passes, half the activation traffic; the colour-dependent part of a score then carries
+ * about 3e-2 relative error). The paper has no counterpart: a precision/speed choice of this
+ * implementation. Waits for the context's stream and frees the scoring buffers. */
+dlm_status dlm_scorer_set_scoring_precision(dlm_ctx* ctx, dlm_scorer* s, int32_t split);
 /* Mean squared error of B samples (col device [B][n], y device [B]) and its gradient
  * (grad device [nparams] float32, out device [B] float32 predictions, loss device [1]). */
 dlm_status dlm_scorer_loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* col, const float* y, int32_t B,

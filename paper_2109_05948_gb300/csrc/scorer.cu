@@ -50,6 +50,8 @@ struct dlm_scorer {
   // forward work buffers for up to `cap` candidates
   int cap = 0;
   bf16* H[4] = {};
+  bf16* Hlo[4] = {};  // lo parts of the scoring activations (split_act)
+  int split_act = 1;  // scoring activations as bf16 hi + lo (three MMA passes) or bf16 alone
   bf16* Mb[4] = {};
   bf16* Mblo[4] = {};
   float* Mf[4] = {};
@@ -1093,6 +1095,7 @@ static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
   for (int l = 0; l <= kNL; ++l) {
     const int w = l == 0 ? kD0 : kD;
     if (l < kNL) DLM_TRY(dalloc(ctx, &s->H[l], (size_t)rows * w));
+    if (l < kNL && s->split_act) DLM_TRY(dalloc(ctx, &s->Hlo[l], (size_t)rows * w));
     DLM_TRY(dalloc(ctx, &s->Mb[l], (size_t)cap * w));
     DLM_TRY(dalloc(ctx, &s->Mblo[l], (size_t)cap * w));
     DLM_TRY(dalloc(ctx, &s->Mf[l], (size_t)cap * w));
@@ -1164,7 +1167,7 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
   for (int l = 0; l <= kNL; ++l) {
     cudaFree(s->LamT[l]); cudaFree(s->Lam[l]); cudaFree(s->LamTlo[l]); cudaFree(s->Lamlo[l]);
     cudaFree(s->GamT[l]); cudaFree(s->GamTlo[l]); cudaFree(s->Mblo[l]); cudaFree(s->Mbblo[l]);
-    cudaFree(s->H[l]); cudaFree(s->Mb[l]); cudaFree(s->Mf[l]); cudaFree(s->G[l]);
+    cudaFree(s->H[l]); cudaFree(s->Hlo[l]); cudaFree(s->Mb[l]); cudaFree(s->Mf[l]); cudaFree(s->G[l]);
     cudaFree(s->Hb[l]); cudaFree(s->Hblo[l]); cudaFree(s->HT[l]); cudaFree(s->HTlo[l]); cudaFree(s->Mbb[l]); cudaFree(s->Mfb[l]); cudaFree(s->Gbf[l]);
     cudaFree(s->dZ[l]); cudaFree(s->dZT[l]); cudaFree(s->S[l]);
   }
@@ -1261,9 +1264,26 @@ extern "C" dlm_status dlm_score_offspring(dlm_ctx* ctx, dlm_scorer* s, const int
   DLM_TRY(ensure_fwd_buffers(ctx, s));
   for (int c0 = 0; c0 < c; c0 += s->cap) {
     const int cc = std::min(s->cap, c - c0);
-    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, out + c0, s->H, nullptr, s->Mb, s->Mblo, s->Mf, s->G, s->rowdot,
-                    false));
+    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, out + c0, s->H, s->split_act ? s->Hlo : nullptr, s->Mb,
+                    s->Mblo, s->Mf, s->G, s->rowdot, false));
   }
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_scorer_set_scoring_precision(dlm_ctx* ctx, dlm_scorer* s, int32_t split) {
+  if (!ctx || !s || (split != 0 && split != 1)) return fail(ctx, DLM_EINVAL, "scorer_set_scoring_precision: bad argument");
+  if (split == s->split_act) return DLM_OK;
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the buffers may be in use by queued work
+  for (int l = 0; l <= kNL; ++l) {
+    cudaFree(s->H[l]); cudaFree(s->Hlo[l]); cudaFree(s->Mb[l]); cudaFree(s->Mblo[l]); cudaFree(s->Mf[l]);
+    cudaFree(s->G[l]);
+    s->H[l] = s->Hlo[l] = s->Mb[l] = s->Mblo[l] = nullptr;
+    s->Mf[l] = s->G[l] = nullptr;
+  }
+  cudaFree(s->rowdot);
+  s->rowdot = nullptr;
+  s->cap = 0;  // reallocated by the next scoring call
+  s->split_act = split;
   return DLM_OK;
 }
 

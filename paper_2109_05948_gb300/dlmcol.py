@@ -79,6 +79,7 @@ _SIGS = {
     "dlm_scorer_get_params": (_i32, [_P, _P, _P]),
     "dlm_scorer_set_params": (_i32, [_P, _P, _P]),
     "dlm_score_offspring": (_i32, [_P, _P, _P, _i32, _P]),
+    "dlm_scorer_set_scoring_precision": (_i32, [_P, _P, _i32]),
     "dlm_scorer_loss_grad": (_i32, [_P, _P, _P, _P, _i32, _P, _P, _P]),
     "dlm_scorer_train": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32, _f32, _u64, _u32]),
     "dlm_memetic_create": (_i32, [_P, _P, _P, _PP]),
@@ -326,6 +327,10 @@ def dlm_scorer_get_params(ctx, s, params):
 
 def dlm_scorer_set_params(ctx, s, params):
     ctx.check(lib().dlm_scorer_set_params(ctx.h, s.h, _ptr(params)), "dlm_scorer_set_params")
+
+
+def dlm_scorer_set_scoring_precision(ctx, scorer, split):
+    ctx.check(lib().dlm_scorer_set_scoring_precision(ctx.h, scorer.h, int(split)), "dlm_scorer_set_scoring_precision")
 
 
 def dlm_score_offspring(ctx, s, col, c, out):

@@ -1,8 +1,12 @@
 """GPU parity of the tcgen05 scorer: the GEMM building block against a plain PyTorch fp32 matmul,
 and the network's forward pass, gradients and Adam training against the FP64 oracle.
 
-Tolerance: the scorer computes in BF16 with FP32 accumulation; results must be within 1e-2
-relative (norm-wise over a batch or a parameter block) of the FP64 oracle."""
+Tolerance: the scorer computes in BF16 with FP32 accumulation (weights and, for scoring and
+training, activations split into bf16 hi + lo pairs); every score's colour-dependent part (score
+minus the exact head bias) must be within 1e-2 of the FP64 oracle's, relative to the larger of its
+own magnitude and the batch's RMS (the absolute floor); gradients within 1e-2 norm-wise per
+parameter block; the best of every group of 32 candidates (one parent's K = 32 children) must be
+the oracle's best or within 2e-2 RMS of it."""
 import numpy as np
 import pytest
 
@@ -59,8 +63,32 @@ def _gpu_scorer(ctx, n, k, th):
     return s
 
 
+def _per_element(got, ref, bias):
+    """max over candidates of |got - ref| / max(|ref - bias|, rms(ref - bias)) on the
+    colour-dependent part of the score."""
+    cg = np.asarray(got, np.float64) - bias
+    cr = np.asarray(ref, np.float64) - bias
+    floor = max(float(np.sqrt(np.mean(cr * cr))), 1e-30)
+    return float(np.max(np.abs(cg - cr) / np.maximum(np.abs(cr), floor))), floor
+
+
+def _group_best_ok(got, ref, floor, G=32):
+    """In every group of G consecutive candidates the GPU's best (smallest score) is the oracle's
+    best, or the oracle's own scores of the two differ by at most 2e-2 of the RMS floor."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    bad = []
+    for g0 in range(0, len(got) - G + 1, G):
+        a = g0 + int(np.argmin(got[g0:g0 + G]))
+        b = g0 + int(np.argmin(ref[g0:g0 + G]))
+        if a != b and ref[a] - ref[b] > 2 * TOL * floor:
+            bad.append((g0, a, b, ref[a] - ref[b]))
+    return bad
+
+
 @pytest.mark.parametrize("n,k,c,scale", [(200, 48, 37, 3.0), (97, 17, 130, 2.0), (64, 64, 9, 4.0), (30, 2, 5, 3.0),
-                                         (60, 9, 2048, 3.0)])  # the last: Gamma terms on the tensor cores
+                                         (60, 9, 2048, 3.0),  # Gamma terms on the tensor cores
+                                         (1000, 48, 1024, 3.0)])  # the learned workload's shape
 def test_scorer_forward_matches_oracle(ctx, n, k, c, scale):
     dims = oracle.ScorerDims(n)
     th = _params(dims, seed=n, scale=scale)
@@ -71,13 +99,34 @@ def test_scorer_forward_matches_oracle(ctx, n, k, c, scale):
     dlmcol.dlm_score_offspring(ctx, s, torch.from_numpy(cols).cuda(), c, out)
     ctx.sync()
     got = out.cpu().numpy()
+    err, floor = _per_element(got, ref, th[-1])
+    assert err <= TOL, err
     assert _rel(got, ref) <= TOL
-    # the part of the score that depends on the colouring (the head bias is exact): BF16 rounding
-    # of the activations at each of the four layers keeps it within 3e-2, and the ranking that
-    # the offspring selection relies on is preserved
-    assert _rel(got - th[-1], ref - th[-1]) <= 3 * TOL
-    if c > 2:
-        assert np.corrcoef(got, ref)[0, 1] >= 0.999
+    if c >= 64:
+        assert not _group_best_ok(got, ref, floor)
+    s.close()
+
+
+def test_scorer_bf16_activations_precision_switch(ctx):
+    """With bf16 activations alone (the faster setting) the colour-dependent part carries a few
+    1e-2 of error; switching back restores the default's 1e-2 per candidate."""
+    n, k, c = 200, 48, 256
+    dims = oracle.ScorerDims(n)
+    th = _params(dims, seed=n, scale=3.0)
+    cols = inputs.random_colorings(c, n, k, seed=c)
+    ref = oracle.scorer_forward(dims, k, th, cols)
+    s = _gpu_scorer(ctx, n, k, th)
+    out = torch.zeros(c, dtype=torch.float32, device="cuda")
+    dc = torch.from_numpy(cols).cuda()
+    dlmcol.dlm_scorer_set_scoring_precision(ctx, s, 0)
+    dlmcol.dlm_score_offspring(ctx, s, dc, c, out)
+    ctx.sync()
+    e_fast, _ = _per_element(out.cpu().numpy(), ref, th[-1])
+    dlmcol.dlm_scorer_set_scoring_precision(ctx, s, 1)
+    dlmcol.dlm_score_offspring(ctx, s, dc, c, out)
+    ctx.sync()
+    e_split, _ = _per_element(out.cpu().numpy(), ref, th[-1])
+    assert e_split <= TOL and e_split < e_fast and e_fast <= 0.5
     s.close()
 
 
@@ -93,8 +142,9 @@ def test_scorer_permutation_invariant_on_gpu(ctx):
     dlmcol.dlm_score_offspring(ctx, s, torch.from_numpy(cols).cuda(), c, a)
     dlmcol.dlm_score_offspring(ctx, s, torch.from_numpy(sigma[cols].astype(np.int16)).cuda(), c, b)
     ctx.sync()
-    # exact up to the order of the fp32 sums over class rows (and the bf16 roundings they feed)
-    assert torch.allclose(a, b, rtol=1e-3, atol=1e-5)
+    # exact up to the order of the fp32 sums over class rows (and the roundings they feed)
+    cen = (a - th[-1]).abs().max().item()
+    assert (a - b).abs().max().item() <= 1e-4 * max(cen, 1e-6)
     s.close()
 
 
@@ -139,9 +189,16 @@ def test_scorer_training_matches_oracle(ctx):
     got = torch.zeros(s.nparams, dtype=torch.float32, device="cuda")
     dlmcol.dlm_scorer_get_params(ctx, s, got)
     ctx.sync()
-    d_gpu = got.cpu().numpy().astype(np.float64) - th0.astype(np.float32).astype(np.float64)
+    gp = got.cpu().numpy().astype(np.float64)
+    # the trained parameters, per block, within 1e-2 of the FP64 run's
+    for name, (off, shape) in dims.offsets().items():
+        sz = int(np.prod(shape))
+        assert _rel(gp[off:off + sz], th[off:off + sz]) <= TOL, name
+    # and the change itself: Adam divides by sqrt(v), so parameters whose gradients are tiny
+    # amplify the rounding of their updates; the change as a whole stays within 3e-2
+    d_gpu = gp - th0.astype(np.float32).astype(np.float64)
     d_ref = th - th0
-    assert _rel(d_gpu, d_ref) <= 5 * TOL  # Adam divides by sqrt(v): tiny gradients amplify rounding
+    assert _rel(d_gpu, d_ref) <= 3 * TOL
     s.close()
 
 
@@ -159,5 +216,7 @@ def test_scorer_full_size_sampled(ctx):
     sample = [0, 1, 127, 128, 8191, 8192, 100000, 200000, 262142, 262143, 5, 77, 4096, 65536, 131072, 250000]
     ref = oracle.scorer_forward(dims, k, th, cols[sample].cpu().numpy())
     assert _rel(out[sample].cpu().numpy(), ref) <= TOL
+    err, _ = _per_element(out[sample].cpu().numpy(), ref, th[-1])
+    assert err <= TOL, err
     assert torch.isfinite(out).all()
     s.close()
