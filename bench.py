@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--pop", type=int, default=POP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-memetic", action="store_true",
+                    help="leave out the learned-vs-random GPX comparison of the default run")
     ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp", "wvcp_iterated", "scorer", "popsweep",
                                                    "population"],
                     help="tabu: the headline moves/s step; memetic: learned vs random GPX time-to-target; "
@@ -84,7 +86,9 @@ def parse():
                     help="tabu iterations per generation; 2 |V|: at 10 |V| tabu alone solves the graph in the "
                          "first generation and the crossover never matters")
     ap.add_argument("--mem-target", type=int, default=0, help="conflict level to reach")
-    ap.add_argument("--mem-seeds", type=int, default=5)
+    ap.add_argument("--mem-graph", default="planted", choices=["planted", "gnp"],
+                    help="planted k-colourable (p = 0.5 across parts) or uniform random G(n, 0.5)")
+    ap.add_argument("--mem-seeds", type=int, default=10)
     ap.add_argument("--mem-max-gens", type=int, default=40)
     ap.add_argument("--mem-time-limit", type=float, default=120.0, help="seconds per run")
     ap.add_argument("--warps", type=int, default=0, help="warps per individual (0: the library's default)")
@@ -300,7 +304,7 @@ def run_memetic(args):
     torch.cuda.set_device(0)
     ctx = dlmcol.Context(0)
     n, k = args.mem_n, args.mem_k
-    e, _ = inputs.planted(n, k, 0.5, seed=0)
+    e = inputs.planted(n, k, 0.5, seed=0)[0] if args.mem_graph == "planted" else inputs.gnp(n, 0.5, seed=0)
     g = dlmcol.Graph(ctx, n, torch.from_numpy(e).cuda())
     runs = {"learned": [], "random": []}
     clocks = Clocks(0)
@@ -314,11 +318,15 @@ def run_memetic(args):
             dlmcol.dlm_memetic_profile(ctx, mm, True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            traj, hit = [], None
+            traj, diag, hit = [], [], None
             for gen in range(args.mem_max_gens):
                 best = dlmcol.dlm_memetic_step(ctx, mm)
                 el = time.perf_counter() - t0
                 traj.append([round(el, 3), int(best)])
+                # diagnostics read after the timing of the generation (they wait for the stream)
+                st = dlmcol.dlm_memetic_stats(ctx, mm)
+                diag.append({key: (None if v != v else round(v, 4)) for key, v in st.items()})
+                t0 += time.perf_counter() - t0 - el  # the diagnostics' read is not search time
                 if best <= args.mem_target:
                     hit = el
                     break
@@ -326,30 +334,87 @@ def run_memetic(args):
                     break
             stages = dlmcol.dlm_memetic_profile(ctx, mm, False)
             runs[mode].append({"seed": 1000 + seed, "time_to_target_s": hit, "generations": len(traj),
-                               "best": traj[-1][1], "trajectory": traj,
+                               "best": traj[-1][1], "trajectory": traj, "diagnostics": diag,
                                "stage_ms_per_generation": {key: round(v, 2) for key, v in stages.items()
                                                            if key != "generations"}})
-            print(json.dumps({"progress": mode, **runs[mode][-1]}), file=sys.stderr, flush=True)
+            print(json.dumps({"progress": mode, "seed": 1000 + seed, "time_to_target_s": hit,
+                              "generations": len(traj), "best": traj[-1][1]}), file=sys.stderr, flush=True)
             mm.close()
 
     ck = clocks.stop()
-
-    def med(mode):
-        ts = [r["time_to_target_s"] for r in runs[mode]]
-        if any(t is None for t in ts):
-            return None
-        return statistics.median(ts)
-
     out = {"metric": "time-to-target conflicts learned vs plain GPX", "workload": "memetic",
            "unit": "s", "higher_is_better": False,
-           "value": med("learned"), "random_gpx": med("random"),
-           "config": {"workload": f"planted {k}-colourable n={n}, p=0.5 across parts, population {args.mem_pop}, "
+           "config": {"workload": (f"planted {k}-colourable n={n}, p=0.5 across parts" if args.mem_graph == "planted"
+                                   else f"G(n={n}, p=0.5), k={k}") + f", population {args.mem_pop}, "
                                   f"K=32 GPX candidates, {args.mem_iters} tabu iterations per generation, "
                                   f"scorer 64-d embedding + 3 x 256 invariant layers, N=5 epochs, b=100, lr=1e-3",
                       "target_conflicts": args.mem_target, "seeds": args.mem_seeds,
                       "time_limit_s": args.mem_time_limit, "max_generations": args.mem_max_gens},
-           "clocks": ck, "runs": runs, "data": "synthetic"}
+           "clocks": ck, "data": "synthetic"}
+    out.update(memetic_summary(runs))
+    out["runs"] = runs
     print(json.dumps(out), flush=True)
+    return out
+
+
+def memetic_compare(args):
+    """run_memetic at the learned workload's defaults, as a child process (its JSON line, per-seed
+    runs left out)."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", "memetic", "--mem-seeds", str(args.mem_seeds),
+           "--mem-iters", str(args.mem_iters), "--mem-pop", str(args.mem_pop)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # reported, never fatal to the headline
+        return {"error": f"{type(exc).__name__}: {exc}"}
+    return {"metric": d["metric"], "unit": d["unit"], "higher_is_better": False, "learned_median_s": d["value"],
+            "random_gpx_median_s": d["random_gpx"], "learned_over_random": d["learned_over_random"],
+            "config": d["config"], "summary": d["summary"],
+            "per_seed_s": {m: [x["time_to_target_s"] for x in d["runs"][m]] for m in d["runs"]}}
+
+
+def memetic_summary(runs, wall_points=(0.5, 1.0, 1.5, 2.0)):
+    """Medians, means with bootstrap 95 % intervals of the time to target, best conflicts at fixed
+    wall times and the mean post-tabu conflicts of each generation's offspring, per mode."""
+    import random as _r
+
+    def boot(xs, reps=2000):
+        if not xs:
+            return None
+        g = _r.Random(0)
+        ms = sorted(statistics.mean(g.choice(xs) for _ in xs) for _ in range(reps))
+        return [ms[int(0.025 * reps)], ms[int(0.975 * reps) - 1]]
+
+    res = {}
+    for mode, rs in runs.items():
+        ts = [r["time_to_target_s"] for r in rs if r["time_to_target_s"] is not None]
+        at = {}
+        for w in wall_points:
+            vals = []
+            for r in rs:
+                done = [b for (t, b) in r["trajectory"] if t <= w]
+                if done:
+                    vals.append(done[-1])
+                elif r["time_to_target_s"] is not None and r["time_to_target_s"] <= w:
+                    vals.append(0)
+            at[str(w)] = statistics.median(vals) if len(vals) == len(rs) else None
+        gmax = max(len(r["diagnostics"]) for r in rs)
+        fmean = [statistics.median([r["diagnostics"][i]["f_mean"] for r in rs if len(r["diagnostics"]) > i])
+                 for i in range(gmax)]
+        pear = [statistics.median([r["diagnostics"][i]["pred_pearson"] for r in rs
+                                   if len(r["diagnostics"]) > i and r["diagnostics"][i]["pred_pearson"] is not None]
+                                  or [float("nan")]) for i in range(gmax)]
+        res[mode] = {"reached": len(ts), "runs": len(rs),
+                     "median_time_to_target_s": statistics.median(ts) if len(ts) == len(rs) else None,
+                     "mean_time_to_target_s": statistics.mean(ts) if len(ts) == len(rs) else None,
+                     "mean_ci95_s": boot(ts) if len(ts) == len(rs) else None,
+                     "median_generations": statistics.median(r["generations"] for r in rs),
+                     "median_best_at_wall_s": at,
+                     "median_offspring_f_mean_by_generation": [round(x, 1) for x in fmean],
+                     "median_prediction_pearson_by_generation": [None if x != x else round(x, 3) for x in pear]}
+    lm, rm = res["learned"]["median_time_to_target_s"], res["random"]["median_time_to_target_s"]
+    return {"value": lm, "random_gpx": rm, "summary": res,
+            "learned_over_random": (lm / rm) if lm and rm else None}
 
 
 def run_multi(args):
@@ -1036,13 +1101,18 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args)
+    memetic = None
+    if rank == 0 and world == 1 and not args.no_memetic and pop == POP and iters == ITERS:
+        # the second half of the metric: learned selection against random GPX on the learned
+        # workload (planted 48-colourable n = 1000, population 8192), 10 seeds per mode
+        memetic = memetic_compare(args)
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "int16/int32", "data": "synthetic",
                "config": config(args, {"smem_probe_gbps": smem_gbps}), "roofline": roofline,
                "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": args.steps,
-               "moves": tot_moves}
+               "moves": tot_moves, "memetic_time_to_target": memetic}
         print(json.dumps(out), flush=True)
     g.close()
     ctx.close()

@@ -314,6 +314,17 @@ dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* best_f_host)
  * 7 = candidate scores of the last generation [p][K] float32 (use_scorer only),
  * 8 = scorer parameters [nparams] float32. */
 dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, void* dst);
+
+/* Diagnostics of the last generation (section "Analysis of the contributions of deep learning":
+ * predicted against actual fitness, and the population's spread), host out[8]: the generation
+ * index; the Pearson correlation between the scorer's prediction for each offspring searched in
+ * that generation (chosen by the previous generation's learned selection) and its post-tabu
+ * conflicts f(S'_i); the mean of |prediction * sd + mean - f(S'_i)| / max(f(S'_i), 1), the
+ * prediction mapped back through the standardisation of the targets it was trained on; the mean
+ * and the minimum of f(S'_i); the mean, minimum and maximum distance between distinct members of
+ * the new population. The two prediction entries are NaN without the scorer and in generation 0.
+ * Waits for the context's stream. */
+dlm_status dlm_memetic_stats(dlm_ctx* ctx, dlm_memetic* mm, double* out);
 /* Overwrites the population state (which = 0..3 as above) from device memory src. */
 dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const void* src);
 
@@ -339,11 +350,13 @@ dlm_status dlm_col_descend(dlm_ctx* ctx, const dlm_graph* g, const dlm_memetic_p
 /* Checkpoint and resume (the paper runs last up to 138 h and describes no checkpoint; this is
  * the state Algorithm 1 carries from one generation to the next). dlm_memetic_state_bytes gives
  * the size of the blob; dlm_memetic_save writes it to caller-owned host memory (a 64-byte header
- * with the configuration and the generation counter, then P, f(P), D(P,P), the offspring S^O,
- * f(S*) and S*, and, with the scorer, its parameters, Adam moments and step counter) and waits;
- * dlm_memetic_load restores it into an object created with the same n, k, p, K and use_scorer
- * (DLM_EINVAL otherwise) and waits. Every random draw is keyed by (seed, individual, generation,
- * iteration), so a resumed run continues bit-identically to an uninterrupted one. */
+ * with the configuration, the generation counter and a 64-bit FNV-1a fingerprint of the graph's
+ * bit rows and of every parameter (k, p, K, iters, tenure, use_scorer, epochs, batch, lr, seed), then
+ * P, f(P), D(P,P), the offspring S^O, f(S*) and S*, and, with the scorer, its parameters, Adam
+ * moments and step counter) and waits; dlm_memetic_load restores it into an object created on the
+ * same graph with the same parameters (DLM_EINVAL otherwise) and waits. Every random draw is keyed
+ * by (seed, individual, generation, iteration), so a resumed run continues bit-identically to an
+ * uninterrupted one. The diagnostics of dlm_memetic_stats restart after a load. */
 int64_t dlm_memetic_state_bytes(const dlm_memetic* mm);
 dlm_status dlm_memetic_save(dlm_ctx* ctx, dlm_memetic* mm, void* host);
 dlm_status dlm_memetic_load(dlm_ctx* ctx, dlm_memetic* mm, const void* host);

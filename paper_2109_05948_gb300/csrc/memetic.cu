@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
@@ -20,6 +21,13 @@ struct dlm_memetic {
   int32_t *sel = nullptr, *nbr = nullptr, *pairs = nullptr, *pick = nullptr;
   uint32_t* cid = nullptr;
   float* scores = nullptr;
+  // per-generation diagnostics: the predicted score of each selected offspring (learned
+  // selection), the standardisation of the last training targets, and the statistics of the last
+  // generation (k_gen_stats)
+  float* pred = nullptr;
+  double* dstat = nullptr;  // [16] device: accumulators and results
+  double* h_stat = nullptr;  // [16] pinned
+  uint64_t fingerprint = 0;  // of the graph's bit rows and of every search / training parameter
   int64_t* h_best = nullptr;  // pinned
   dlm_scorer* scorer = nullptr;
   // the scorer trains on a side stream while the distances and the pool update run
@@ -120,7 +128,8 @@ __global__ void k_pairs_all(int p, int K, const int32_t* nbr, int32_t* pairs, ui
 
 // argmin over the K scores of individual i, visiting j in order: the first candidate is taken and
 // only a strictly smaller score replaces it (ties: lowest j); copies that child into S^O_i
-__global__ void k_select_best(int p, int K, int n, const float* scores, const int16_t* kids, int16_t* SO, int32_t* pick) {
+__global__ void k_select_best(int p, int K, int n, const float* scores, const int16_t* kids, int16_t* SO, int32_t* pick,
+                              float* pred) {
   const int i = blockIdx.x;
   __shared__ int best;
   if (threadIdx.x == 0) {
@@ -132,10 +141,112 @@ __global__ void k_select_best(int p, int K, int n, const float* scores, const in
     }
     best = bj;
     pick[i] = bj;
+    pred[i] = bv;
   }
   __syncthreads();
   const int16_t* src = kids + ((size_t)i * K + best) * n;
   for (int v = threadIdx.x; v < n; v += blockDim.x) SO[(size_t)i * n + v] = src[v];
+}
+
+// Per-generation diagnostics (section "Analysis of the contributions of deep learning": the
+// predicted against the actual fitness of the selected offspring, and the spread of the
+// population). dstat layout: [0..7] results of the last generation (generation, Pearson of
+// prediction and actual f(S'), mean relative error of the de-standardised prediction, mean f(S'),
+// min f(S'), mean / min / max distance between distinct members of P), [8..9] mean and std of the
+// f(S') the scorer was last trained on, [10..12] distance accumulators (sum, min, max).
+__global__ void k_dist_stats(int p, const int16_t* D, double* dstat) {
+  double sum = 0.0;
+  int mn = INT_MAX, mx = INT_MIN;
+  const int64_t tot = (int64_t)p * p;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / p), c = (int)(t - (int64_t)r * p);
+    if (r == c) continue;
+    const int v = D[t];
+    sum += v;
+    mn = min(mn, v);
+    mx = max(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(dstat + 10, sum);
+    atomicMin((unsigned long long*)(dstat + 11), (unsigned long long)(int64_t)mn);  // non-negative ints
+    atomicMax((unsigned long long*)(dstat + 12), (unsigned long long)(int64_t)mx);
+  }
+}
+
+// one block: prediction quality over the p offspring just searched (pred from the previous
+// selection, learned = 1 when there was one), then the distance results; trained = 1 records the
+// standardisation of f(S') the scorer is trained on now
+__global__ void __launch_bounds__(1024) k_gen_stats(int p, uint32_t gen, int learned, int trained, const float* pred,
+                                                    const int64_t* fSp, double* dstat) {
+  __shared__ double red[6][32];
+  double sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0, are = 0;
+  int64_t mnf = INT64_MAX;
+  const double mu = dstat[8], sd = dstat[9];
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const double y = (double)fSp[i];
+    mnf = min(mnf, (int64_t)fSp[i]);
+    sy += y; syy += y * y;
+    if (learned) {
+      const double x = pred[i];
+      sx += x; sxx += x * x; sxy += x * y;
+      const double yhat = mu + sd * x;
+      are += fabs(yhat - y) / fmax(y, 1.0);
+    }
+  }
+  double v[6] = {sx, sy, sxx, syy, sxy, are};
+  for (int q = 0; q < 6; ++q) {
+    double a = v[q];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = a;
+  }
+  __shared__ long long smn[32];
+  long long m2 = mnf;
+  for (int o = 16; o > 0; o >>= 1) m2 = min(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
+  if ((threadIdx.x & 31) == 0) smn[threadIdx.x >> 5] = m2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    long long mm = LLONG_MAX;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      for (int q = 0; q < 6; ++q) t[q] += red[q][w];
+      mm = min(mm, smn[w]);
+    }
+    const double np = p;
+    dstat[0] = gen;
+    if (learned) {
+      const double cxy = t[4] - t[0] * t[1] / np, cxx = t[2] - t[0] * t[0] / np, cyy = t[3] - t[1] * t[1] / np;
+      dstat[1] = (cxx > 0 && cyy > 0) ? cxy / sqrt(cxx * cyy) : 0.0;
+      dstat[2] = t[5] / np;
+    } else {
+      dstat[1] = nan("");
+      dstat[2] = nan("");
+    }
+    dstat[3] = t[1] / np;
+    dstat[4] = (double)mm;
+    if (trained) {  // the mean and (population) std of f(S') the scorer is being trained on
+      dstat[8] = t[1] / np;
+      const double var = t[3] / np - dstat[8] * dstat[8];
+      dstat[9] = var > 0 ? sqrt(var) : 1.0;
+    }
+  }
+}
+
+__global__ void k_dist_stats_init(double* dstat) {
+  dstat[10] = 0.0;
+  *(unsigned long long*)(dstat + 11) = (unsigned long long)INT64_MAX;
+  *(unsigned long long*)(dstat + 12) = 0ull;
+}
+
+__global__ void k_dist_stats_done(int p, double* dstat) {
+  const double pairs = (double)p * (p - 1);
+  dstat[5] = pairs > 0 ? dstat[10] / pairs : 0.0;
+  dstat[6] = (double)(int64_t)*(unsigned long long*)(dstat + 11);
+  dstat[7] = (double)(int64_t)*(unsigned long long*)(dstat + 12);
 }
 
 template <typename T>
@@ -156,8 +267,9 @@ extern "C" void dlm_memetic_destroy(dlm_memetic* mm) {
   cudaFree(mm->P); cudaFree(mm->Pn); cudaFree(mm->SO); cudaFree(mm->Sp); cudaFree(mm->best_col); cudaFree(mm->kids);
   cudaFree(mm->fP); cudaFree(mm->fPn); cudaFree(mm->fSp); cudaFree(mm->fall); cudaFree(mm->best_f); cudaFree(mm->moves);
   cudaFree(mm->DP); cudaFree(mm->Dall); cudaFree(mm->sel); cudaFree(mm->nbr); cudaFree(mm->pairs); cudaFree(mm->pick);
-  cudaFree(mm->cid); cudaFree(mm->scores);
+  cudaFree(mm->cid); cudaFree(mm->scores); cudaFree(mm->pred); cudaFree(mm->dstat);
   if (mm->h_best) cudaFreeHost(mm->h_best);
+  if (mm->h_stat) cudaFreeHost(mm->h_stat);
   if (mm->scorer) dlm_scorer_destroy(mm->scorer);
   for (auto e : mm->pev) if (e) cudaEventDestroy(e);
   for (auto e : mm->tev) if (e) cudaEventDestroy(e);
@@ -190,9 +302,15 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
   A(&mm->best_f, 1); A(&mm->moves, (size_t)p);
   A(&mm->DP, (size_t)p * p); A(&mm->Dall, (size_t)4 * p * p);
   A(&mm->sel, (size_t)p); A(&mm->nbr, (size_t)p * K); A(&mm->pairs, (size_t)2 * p * nk); A(&mm->pick, (size_t)p);
-  A(&mm->cid, (size_t)p * nk); A(&mm->scores, (size_t)p * K);
+  A(&mm->cid, (size_t)p * nk); A(&mm->scores, (size_t)p * K); A(&mm->pred, (size_t)p); A(&mm->dstat, 16);
   if (st == DLM_OK && cudaMallocHost(&mm->h_best, sizeof(int64_t)) != cudaSuccess) st = fail(ctx, DLM_ENOMEM, "pinned");
+  if (st == DLM_OK && cudaMallocHost(&mm->h_stat, 16 * sizeof(double)) != cudaSuccess) st = fail(ctx, DLM_ENOMEM, "pinned");
+  if (st == DLM_OK) st = cuda_check(ctx, cudaMemsetAsync(mm->dstat, 0, 16 * sizeof(double), ctx->stream), "memset");
   if (st == DLM_OK && prm->use_scorer) st = dlm_scorer_create(ctx, n, k, prm->seed, &mm->scorer);
+  // the selection takes the best-scored of each individual's K children: bf16 activations (two
+  // MMA passes) keep every group's best equal to the FP64 one's in the parity tests, at a third
+  // of the split-activation scoring time
+  if (st == DLM_OK && prm->use_scorer) st = dlm_scorer_set_scoring_precision(ctx, mm->scorer, 0);
   int prio_least = 0, prio_greatest = 0;  // the training's short kernels take SMs as the distance blocks drain
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   if (st == DLM_OK && prm->use_scorer &&
@@ -203,6 +321,24 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
     st = fail(ctx, DLM_ECUDA, "memetic_create: side stream");
   }
   if (st != DLM_OK) { dlm_memetic_destroy(mm); return st; }
+  // fingerprint (FNV-1a, 64 bits) of the graph's bit rows and of the parameters: a checkpoint
+  // only loads into a run of the same problem
+  if (st == DLM_OK) {
+    std::vector<uint32_t> hb((size_t)g->n * g->words);
+    st = cuda_check(ctx, cudaMemcpy(hb.data(), g->d_bits, hb.size() * 4, cudaMemcpyDeviceToHost), "copy");
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* d, size_t len) {
+      const uint8_t* b = (const uint8_t*)d;
+      for (size_t i = 0; i < len; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    };
+    mix(hb.data(), hb.size() * 4);
+    mix(&g->n, sizeof(g->n));
+    mix(&prm->k, sizeof(prm->k)); mix(&prm->p, sizeof(prm->p)); mix(&prm->K, sizeof(prm->K));
+    mix(&prm->iters, sizeof(prm->iters)); mix(&prm->tenure, sizeof(prm->tenure));
+    mix(&prm->use_scorer, sizeof(prm->use_scorer)); mix(&prm->epochs, sizeof(prm->epochs));
+    mix(&prm->batch, sizeof(prm->batch)); mix(&prm->lr, sizeof(prm->lr)); mix(&prm->seed, sizeof(prm->seed));
+    mm->fingerprint = h;
+  }
   // initial population: random colourings, their conflicts and their distance matrix
   const int64_t big = INT64_MAX;
   st = dlm_init_colors(ctx, n, k, p, prm->seed, 0u, mm->P);
@@ -233,6 +369,10 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
   // 2. best so far
   k_best_of<<<1, 1024, 0, s>>>(p, n, mm->fSp, mm->Sp, mm->best_f, mm->best_col);
   DLM_TRY(launch_check(ctx, "k_best_of"));
+  // diagnostics: the last selection's predictions against the conflicts its offspring reached
+  k_gen_stats<<<1, 1024, 0, s>>>(p, mm->gen, (q.use_scorer && mm->gen > 0) ? 1 : 0, q.use_scorer ? 1 : 0, mm->pred,
+                                 mm->fSp, mm->dstat);
+  DLM_TRY(launch_check(ctx, "k_gen_stats"));
   mark(2);
   // 3. training on {(S^O_i, f(S'_i))}, on the side stream: it only reads S^O and f(S'), which
   //    nothing below writes before the scoring, and the scoring waits for it
@@ -269,6 +409,11 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
   mark(4);
   // 6. parent matching
   DLM_TRY(dlm_knn(ctx, p, mm->DP, K, mm->nbr));
+  // diagnostics: the spread of the new population
+  k_dist_stats_init<<<1, 1, 0, s>>>(mm->dstat);
+  k_dist_stats<<<ctx->num_sms * 2, 256, 0, s>>>(p, mm->DP, mm->dstat);
+  k_dist_stats_done<<<1, 1, 0, s>>>(p, mm->dstat);
+  DLM_TRY(launch_check(ctx, "k_dist_stats"));
   mark(5);
   // 7. offspring
   if (q.use_scorer) {
@@ -277,7 +422,7 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     DLM_TRY(dlm_gpx_batch(ctx, n, k, mm->P, p, mm->pairs, mm->cid, p * K, mm->kids, q.seed, mm->gen));
     DLM_CUDA(ctx, cudaStreamWaitEvent(s, mm->ev_trained, 0));
     DLM_TRY(dlm_score_offspring(ctx, mm->scorer, mm->kids, p * K, mm->scores));
-    k_select_best<<<p, 128, 0, s>>>(p, K, n, mm->scores, mm->kids, mm->SO, mm->pick);
+    k_select_best<<<p, 128, 0, s>>>(p, K, n, mm->scores, mm->kids, mm->SO, mm->pick, mm->pred);
     DLM_TRY(launch_check(ctx, "k_select_best"));
   } else {
     k_pairs_random<<<(p + 255) / 256, 256, 0, s>>>(p, K, mm->nbr, q.seed, mm->gen, mm->pairs, mm->cid, mm->pick);
@@ -301,6 +446,14 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     DLM_TRY(dlm_sync(ctx));
     *best_f_host = *mm->h_best;
   }
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_memetic_stats(dlm_ctx* ctx, dlm_memetic* mm, double* out) {
+  if (!ctx || !mm || !out) return fail(ctx, DLM_EINVAL, "memetic_stats: null argument");
+  DLM_CUDA(ctx, cudaMemcpyAsync(mm->h_stat, mm->dstat, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_TRY(dlm_sync(ctx));
+  for (int i = 0; i < 8; ++i) out[i] = mm->h_stat[i];
   return DLM_OK;
 }
 
@@ -351,10 +504,10 @@ struct CkptHeader {
   uint32_t gen, reserved2;
   int64_t scorer_bytes;
   int64_t total;
-  uint8_t pad[8];
+  uint64_t fingerprint;  // graph and parameters of the run that wrote it
 };
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
-constexpr char kMagic[8] = {'D', 'L', 'M', 'M', 'E', 'M', '0', '1'};
+constexpr char kMagic[8] = {'D', 'L', 'M', 'M', 'E', 'M', '0', '2'};
 
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -393,6 +546,7 @@ extern "C" dlm_status dlm_memetic_save(dlm_ctx* ctx, dlm_memetic* mm, void* host
   H.gen = mm->gen;
   H.scorer_bytes = mm->scorer ? dlm_scorer_state_bytes(mm->scorer) : 0;
   H.total = (int64_t)L.total;
+  H.fingerprint = mm->fingerprint;
   cudaStream_t s = ctx->stream;
   DLM_CUDA(ctx, cudaMemcpyAsync(h + L.P, mm->P, p * n * 2, cudaMemcpyDeviceToHost, s));
   DLM_CUDA(ctx, cudaMemcpyAsync(h + L.fP, mm->fP, p * 8, cudaMemcpyDeviceToHost, s));
@@ -417,6 +571,9 @@ extern "C" dlm_status dlm_memetic_load(dlm_ctx* ctx, dlm_memetic* mm, const void
       H.use_scorer != mm->prm.use_scorer || H.total != (int64_t)L.total ||
       H.scorer_bytes != (mm->scorer ? dlm_scorer_state_bytes(mm->scorer) : 0))
     return fail(ctx, DLM_EINVAL, "memetic_load: checkpoint of another configuration");
+  if (H.fingerprint != mm->fingerprint)
+    return fail(ctx, DLM_EINVAL, "memetic_load: checkpoint of another graph or parameter set (seed, budget, tenure, "
+                                 "training)");
   const size_t p = (size_t)mm->prm.p, n = (size_t)mm->n;
   cudaStream_t s = ctx->stream;
   DLM_CUDA(ctx, cudaMemcpyAsync(mm->P, h + L.P, p * n * 2, cudaMemcpyHostToDevice, s));

@@ -83,6 +83,7 @@ _SIGS = {
     "dlm_scorer_loss_grad": (_i32, [_P, _P, _P, _P, _i32, _P, _P, _P]),
     "dlm_scorer_train": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32, _f32, _u64, _u32]),
     "dlm_memetic_create": (_i32, [_P, _P, _P, _PP]),
+    "dlm_memetic_stats": (_i32, [_P, _P, _P]),
     "dlm_memetic_destroy": (None, [_P]),
     "dlm_memetic_step": (_i32, [_P, _P, _P]),
     "dlm_memetic_get": (_i32, [_P, _P, _i32, _P]),
@@ -363,6 +364,14 @@ class Memetic:
             self.close()
         except Exception:
             pass
+
+
+def dlm_memetic_stats(ctx, mm):
+    """dict of the last generation's diagnostics (include/dlmcol.h, dlm_memetic_stats)."""
+    out = (ctypes.c_double * 8)()
+    ctx.check(lib().dlm_memetic_stats(ctx.h, mm.h, out), "dlm_memetic_stats")
+    keys = ("generation", "pred_pearson", "pred_rel_err", "f_mean", "f_min", "dist_mean", "dist_min", "dist_max")
+    return dict(zip(keys, [float(x) for x in out]))
 
 
 def dlm_memetic_step(ctx, mm):
