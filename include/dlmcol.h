@@ -210,7 +210,7 @@ dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
  * or B (l odd); those vertices leave both parents. Vertices left over get the label high word of
  * r0 * k, r = Philox(a = v, b = generation, c = child_id[t], tag = GPX).
  *   parents  device [pop][n] int16;  pairs device [m][2] int32;  child_id device [m] uint32 or
- *   NULL (child_id = t);  children device [m][n] int16 out.  Limits: k <= 128, n <= 2048.
+ *   NULL (child_id = t);  children device [m][n] int16 out.  Limits: k <= 255, n <= 2048.
  * ------------------------------------------------------------------------------------------- */
 dlm_status dlm_gpx_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* parents, int32_t pop,
                          const int32_t* pairs, const uint32_t* child_id, int32_t m, int16_t* children,
@@ -221,7 +221,7 @@ dlm_status dlm_gpx_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* pare
  * M[c][c'] = |A_c intersect B_c'|, D = n - min(sum_c max_c' M, sum_c' max_c M), a symmetric lower
  * bound of the exact (Hungarian) distance, exact when the best-match map is injective.
  *   X device [a][n], Y device [b][n] int16 colourings; D device out, D[i * ldD + j] = D(X_i, Y_j).
- *   upper != 0 with X == Y computes only j > i (and writes those entries). Limits: k <= 128.
+ *   upper != 0 with X == Y computes only j > i (and writes those entries). Limits: k <= 255.
  * ------------------------------------------------------------------------------------------- */
 dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a, const int16_t* Y,
                               int32_t b, int16_t* D, int64_t ldD, int32_t upper);
@@ -251,7 +251,8 @@ dlm_status dlm_knn(dlm_ctx* ctx, int32_t p, const int16_t* D, int32_t K, int32_t
  * Matrix products run on the tcgen05 tensor cores in BF16 with FP32 accumulation; parameters
  * are kept in FP32. Flat parameter order: E[n][64], b0[64], for l = 1..3 (din = 64, 256, 256):
  * Lambda_l[din][256], Gamma_l[din][256], beta_l[256]; then w_head[256], b_head[1].
- * Limits: k <= 64, n <= 2048.
+ * Each candidate occupies 64 ceil(k / 64) class rows of the tensor-core tiles (rows at and above
+ * k are empty and masked out of rho and of the head mean). Limits: k <= 256, n <= 2048.
  * ------------------------------------------------------------------------------------------- */
 dlm_status dlm_scorer_create(dlm_ctx* ctx, int32_t n, int32_t k, uint64_t seed, dlm_scorer** out);
 void dlm_scorer_destroy(dlm_scorer* s);
@@ -287,9 +288,10 @@ dlm_status dlm_scorer_save(dlm_ctx* ctx, dlm_scorer* s, void* host);
 dlm_status dlm_scorer_load(dlm_ctx* ctx, dlm_scorer* s, const void* host);
 
 /* ---------------------------------------------------------------------------------------------
- * Memetic loop (Algorithm 1). dlm_memetic_step runs one generation: TabuCol on every offspring,
- * best-so-far update, scorer training (use_scorer), distances between P and P' and within P',
- * pool update, K nearest neighbours, and offspring: with use_scorer the best-scored of the K GPX
+ * Memetic loop (Algorithm 1). dlm_memetic_step runs one generation: the local search of every
+ * offspring (TabuCol for k-COL, the iterated tabu search for the WVCP), best-so-far update,
+ * scorer training (use_scorer), distances between P and P' and within P', pool update, K nearest
+ * neighbours, and offspring: with use_scorer the best-scored of the K GPX
  * children of i (parent 2 = its j-th neighbour, child id i*K + j); without, one GPX child with a
  * neighbour drawn uniformly (Philox(a = i, b = generation, c = 0, tag = SELECT)), the ablation of
  * section "Benefits of the neural network based crossover selection".
@@ -299,9 +301,18 @@ typedef struct {
   int64_t iters;          /* tabu iterations per generation (paper: 128 |V|) */
   dlm_tenure tenure;      /* paper: {9, 6, 10} */
   int32_t use_scorer;     /* 1 = learned selection, 0 = random GPX */
-  int32_t epochs, batch;  /* paper: 5, 100 */
+  int32_t epochs, batch;  /* paper: 5, 100 (k-COL), 20, 100 (WVCP) */
   float lr;               /* paper: 1e-3 */
   uint64_t seed;
+  int32_t problem;        /* 0 = k-COL; 1 = WVCP (the graph needs vertex weights): the initial
+                             population from the randomised greedy initialisation (individual i
+                             from stream i; it must open at most k colours, k <= 255), fitness =
+                             the WVCP score f, the local search = the iterated feasible and
+                             infeasible tabu search of dlm_wvcp_iterated (max_ls searches of iters
+                             iterations, fscale 256, phi0 = round(256 k max w / (2 |V|)),
+                             phi_last = 256 * 2 max w); an offspring none of whose searches ended
+                             legal gets the fitness sum(w) + 1 */
+  int32_t max_ls;         /* WVCP: searches per generation (paper: 10); ignored for k-COL */
 } dlm_memetic_params;
 
 dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const dlm_memetic_params* prm, dlm_memetic** out);
@@ -351,7 +362,8 @@ dlm_status dlm_col_descend(dlm_ctx* ctx, const dlm_graph* g, const dlm_memetic_p
  * the state Algorithm 1 carries from one generation to the next). dlm_memetic_state_bytes gives
  * the size of the blob; dlm_memetic_save writes it to caller-owned host memory (a 64-byte header
  * with the configuration, the generation counter and a 64-bit FNV-1a fingerprint of the graph's
- * bit rows and of every parameter (k, p, K, iters, tenure, use_scorer, epochs, batch, lr, seed), then
+ * bit rows and of every parameter (k, p, K, iters, tenure, use_scorer, epochs, batch, lr, seed,
+ * problem; for the WVCP also the vertex weights and max_ls), then
  * P, f(P), D(P,P), the offspring S^O, f(S*) and S*, and, with the scorer, its parameters, Adam
  * moments and step counter) and waits; dlm_memetic_load restores it into an object created on the
  * same graph with the same parameters (DLM_EINVAL otherwise) and waits. Every random draw is keyed

@@ -75,6 +75,9 @@ def _declare(L):
                                              _i32, _i32, _i32, _i32, _i32, _i32, _P, _P, _P, _P, _i32,
                                              _i32, _f64, _P, _u64, _u32, _P, _P, _P, _P]),
         "oracle_wvcp_score": (_i64, [_i32, _P, _P, _i32, _P, _P]),
+        "oracle_wvcp_memetic_generation": (_i32, [_i32, _P, _P, _i32, _i32, _i32, _P, _P, _P, _P, _i64, _i32, _i32,
+                                                  _i32, _i32, _i64, _i64, _i64, _i32, _i32, _i32, _i32, _P, _P, _P,
+                                                  _P, _i32, _i32, _f64, _P, _u64, _u32, _P, _P, _P, _P]),
         "oracle_wvcp_greedy": (_i32, [_i32, _P, _P, _u64, _u32, _P]),
         "oracle_wvcp_tabu": (_i32, [_i32, _P, _P, _i32, _P, _i64, _i32, _i32, _i32, _i64, _u64, _u32,
                                     _u32, _P, _P, _P, _P, _P, _i32]),
@@ -347,3 +350,69 @@ def wvcp_iterated(adj, w, k, col, iters, max_ls, fscale, phi0, phi_last, seed, i
     if rc != 0:
         raise RuntimeError(f"oracle_wvcp_iterated failed ({rc})")
     return dict(best_col=best, best_f=int(bf[0]), phi=phis, fc=fcs)
+
+
+def wvcp_greedy(adj, w, seed, ind=0):
+    """Randomised greedy WVCP initialisation of one individual: (colouring, colours opened)."""
+    adj = _c(adj, np.uint8)
+    w = _c(w, np.int32)
+    n = adj.shape[0]
+    col = np.zeros(n, np.int16)
+    used = lib().oracle_wvcp_greedy(n, _ptr(adj), _ptr(w), seed, ind, _ptr(col))
+    return col, int(used)
+
+
+def wvcp_score(adj, w, k, col):
+    """(f, conflicts) of a colouring (Eq. score_WVCP)."""
+    adj = _c(adj, np.uint8)
+    w = _c(w, np.int32)
+    col = _c(col, np.int16)
+    conf = np.zeros(1, np.int64)
+    f = lib().oracle_wvcp_score(adj.shape[0], _ptr(adj), _ptr(w), k, _ptr(col), _ptr(conf))
+    return int(f), int(conf[0])
+
+
+class WvcpMemeticState(MemeticState):
+    """State of Algorithm 1 for the WVCP: the initial population from the randomised greedy
+    initialisation (individual i with stream i), fitness = WVCP score, the iterated feasible and
+    infeasible tabu search (Algorithm 2) as the local search."""
+
+    def __init__(self, adj, w, k, p, K, seed, iters, max_ls, fscale, phi0, phi_last, use_scorer, d0=64, d=256,
+                 nl=3, epochs=5, batch=100, lr=1e-3, L_max=9, alpha=(2, 10)):
+        self.adj = _c(adj, np.uint8)
+        self.w = _c(w, np.int32)
+        self.n = self.adj.shape[0]
+        self.k, self.p, self.K, self.seed, self.iters = k, p, K, seed, iters
+        self.max_ls, self.fscale, self.phi0, self.phi_last = max_ls, fscale, phi0, phi_last
+        self.use_scorer = 1 if use_scorer else 0
+        self.dims = ScorerDims(self.n, d0, d, nl)
+        self.epochs, self.batch, self.lr, self.L_max, self.alpha = epochs, batch, lr, L_max, alpha
+        cols = [wvcp_greedy(self.adj, self.w, seed, i) for i in range(p)]
+        if max(u for _, u in cols) > k:
+            raise ValueError("the greedy initialisation opens more than k colours")
+        self.P = np.stack([c for c, _ in cols]).astype(np.int16)
+        self.fP = np.array([wvcp_score(self.adj, self.w, k, c)[0] for c in self.P], np.int64)
+        self.DP = distance_matrix(k, self.P, self.P)
+        self.SO = self.P.copy()
+        self.th = scorer_init(self.dims, seed)
+        self.am = np.zeros_like(self.th)
+        self.av = np.zeros_like(self.th)
+        self.adam_t = np.zeros(1, np.int64)
+        self.best_col = np.zeros(self.n, np.int16)
+        self.best_f = np.array([np.iinfo(np.int64).max], np.int64)
+        self.gen = 0
+
+    def generation(self, ext_scores=None):
+        fprime = np.zeros(self.p, np.int64)
+        pick = np.zeros(self.p, np.int32)
+        ext = None if ext_scores is None else _c(ext_scores, np.float32)
+        rc = lib().oracle_wvcp_memetic_generation(
+            self.n, _ptr(self.adj), _ptr(self.w), self.k, self.p, self.K, _ptr(self.P), _ptr(self.fP), _ptr(self.DP),
+            _ptr(self.SO), self.iters, self.max_ls, self.L_max, self.alpha[0], self.alpha[1], self.fscale, self.phi0,
+            self.phi_last, self.use_scorer, self.dims.d0, self.dims.d, self.dims.nl, _ptr(self.th), _ptr(self.am),
+            _ptr(self.av), _ptr(self.adam_t), self.epochs, self.batch, self.lr, _ptr(ext) if ext is not None else None,
+            self.seed, self.gen, _ptr(self.best_col), _ptr(self.best_f), _ptr(fprime), _ptr(pick))
+        if rc != 0:
+            raise RuntimeError(f"oracle_wvcp_memetic_generation failed with {rc}")
+        self.gen += 1
+        return fprime, pick

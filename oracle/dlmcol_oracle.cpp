@@ -562,31 +562,19 @@ double oracle_scorer_train(int32_t n, int32_t d0, int32_t d, int32_t nl, int32_t
   return loss;
 }
 
-// One generation of the deep-learning-guided memetic framework (Algorithm 1, one pass of its
-// loop) for k-COL: tabu search of every offspring S^O_i -> S'_i; best-so-far update; training of
-// f_theta on {(S^O_i, f(S'_i))} (when use_scorer); distances between P and P' and within P';
-// pool update; K nearest neighbours; offspring selection. With use_scorer the offspring of i is
-// the argmin of the scores of its K GPX children (ext_scores, when given, replaces the oracle's
-// own scores); without it the second parent is drawn uniformly among the K nearest (the
-// ablation of section "Benefits of the neural network based crossover selection").
-// State arrays are updated in place. diag_fprime (p) receives f(S'_i); diag_pick (p) the chosen j.
-int32_t oracle_memetic_generation(int32_t n, const uint8_t* adj, int32_t k, int32_t p, int32_t K,
-                                  int16_t* P, int64_t* fP, int16_t* DP, int16_t* SO, int64_t iters,
-                                  int32_t L_max, int32_t a_num, int32_t a_den, int32_t use_scorer,
-                                  int32_t d0, int32_t d, int32_t nl, double* th, double* am, double* av,
-                                  int64_t* adam_t, int32_t epochs, int32_t batch, double lr,
-                                  const float* ext_scores, uint64_t seed, uint32_t gen, int16_t* best_col,
-                                  int64_t* best_f, int64_t* diag_fprime, int32_t* diag_pick) {
-  if (K > p - 1 || K < 1) return -1;
-  // 1. parallel local search
-  std::vector<int16_t> Sp((size_t)p * n);
-  std::vector<int64_t> fSp(p);
-  for (int i = 0; i < p; ++i) {
-    int64_t mv, itd;
-    int32_t rc = oracle_tabucol(n, adj, k, SO + (size_t)i * n, iters, L_max, a_num, a_den, seed, (uint32_t)i,
-                                gen, Sp.data() + (size_t)i * n, &fSp[i], &mv, &itd, nullptr, 0);
-    if (rc) return rc;
-  }
+}  // extern "C"
+
+namespace {
+// Algorithm 1 after the local search of the offspring (Sp, fSp): best so far, training,
+// distances over P u P', pool update, K nearest neighbours and the offspring of the next
+// generation. Shared by the k-COL and the WVCP generations; the population arrays are updated in
+// place.
+int32_t memetic_after_search(int32_t n, int32_t k, int32_t p, int32_t K, int16_t* P, int64_t* fP, int16_t* DP,
+                             int16_t* SO, std::vector<int16_t>& Sp, std::vector<int64_t>& fSp, int32_t use_scorer,
+                             int32_t d0, int32_t d, int32_t nl, double* th, double* am, double* av, int64_t* adam_t,
+                             int32_t epochs, int32_t batch, double lr, const float* ext_scores, uint64_t seed,
+                             uint32_t gen, int16_t* best_col, int64_t* best_f, int64_t* diag_fprime,
+                             int32_t* diag_pick) {
   if (diag_fprime) std::copy(fSp.begin(), fSp.end(), diag_fprime);
   // 2. best so far
   int ib = 0;
@@ -662,6 +650,38 @@ int32_t oracle_memetic_generation(int32_t n, const uint8_t* adj, int32_t k, int3
     if (diag_pick) diag_pick[i] = pick;
   }
   return 0;
+}
+}  // namespace
+
+extern "C" {
+
+// One generation of the deep-learning-guided memetic framework (Algorithm 1, one pass of its
+// loop) for k-COL: tabu search of every offspring S^O_i -> S'_i; best-so-far update; training of
+// f_theta on {(S^O_i, f(S'_i))} (when use_scorer); distances between P and P' and within P';
+// pool update; K nearest neighbours; offspring selection. With use_scorer the offspring of i is
+// the argmin of the scores of its K GPX children (ext_scores, when given, replaces the oracle's
+// own scores); without it the second parent is drawn uniformly among the K nearest (the
+// ablation of section "Benefits of the neural network based crossover selection").
+// State arrays are updated in place. diag_fprime (p) receives f(S'_i); diag_pick (p) the chosen j.
+int32_t oracle_memetic_generation(int32_t n, const uint8_t* adj, int32_t k, int32_t p, int32_t K,
+                                  int16_t* P, int64_t* fP, int16_t* DP, int16_t* SO, int64_t iters,
+                                  int32_t L_max, int32_t a_num, int32_t a_den, int32_t use_scorer,
+                                  int32_t d0, int32_t d, int32_t nl, double* th, double* am, double* av,
+                                  int64_t* adam_t, int32_t epochs, int32_t batch, double lr,
+                                  const float* ext_scores, uint64_t seed, uint32_t gen, int16_t* best_col,
+                                  int64_t* best_f, int64_t* diag_fprime, int32_t* diag_pick) {
+  if (K > p - 1 || K < 1) return -1;
+  // 1. parallel local search
+  std::vector<int16_t> Sp((size_t)p * n);
+  std::vector<int64_t> fSp(p);
+  for (int i = 0; i < p; ++i) {
+    int64_t mv, itd;
+    int32_t rc = oracle_tabucol(n, adj, k, SO + (size_t)i * n, iters, L_max, a_num, a_den, seed, (uint32_t)i,
+                                gen, Sp.data() + (size_t)i * n, &fSp[i], &mv, &itd, nullptr, 0);
+    if (rc) return rc;
+  }
+  return memetic_after_search(n, k, p, K, P, fP, DP, SO, Sp, fSp, use_scorer, d0, d, nl, th, am, av, adam_t, epochs,
+                              batch, lr, ext_scores, seed, gen, best_col, best_f, diag_fprime, diag_pick);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -866,4 +886,34 @@ int32_t oracle_wvcp_iterated(int32_t n, const uint8_t* adj, const int32_t* w, in
   return 0;
 }
 
+// One generation of Algorithm 1 for the WVCP: as oracle_memetic_generation, with the iterated
+// feasible and infeasible tabu search (Algorithm 2, oracle_wvcp_iterated) as the local search of
+// every offspring; the fitness of S'_i is the WVCP score f of its best legal colouring, or
+// sum(w) + 1 (worse than every legal colouring) when none of its searches ended legal.
+int32_t oracle_wvcp_memetic_generation(int32_t n, const uint8_t* adj, const int32_t* w, int32_t k, int32_t p,
+                                       int32_t K, int16_t* P, int64_t* fP, int16_t* DP, int16_t* SO, int64_t iters,
+                                       int32_t max_ls, int32_t L_max, int32_t a_num, int32_t a_den, int64_t fscale,
+                                       int64_t phi0, int64_t phi_last, int32_t use_scorer, int32_t d0, int32_t d,
+                                       int32_t nl, double* th, double* am, double* av, int64_t* adam_t,
+                                       int32_t epochs, int32_t batch, double lr, const float* ext_scores,
+                                       uint64_t seed, uint32_t gen, int16_t* best_col, int64_t* best_f,
+                                       int64_t* diag_fprime, int32_t* diag_pick) {
+  if (K > p - 1 || K < 1) return -1;
+  int64_t wsum = 0;
+  for (int v = 0; v < n; ++v) wsum += w[v];
+  std::vector<int16_t> Sp((size_t)p * n);
+  std::vector<int64_t> fSp(p);
+  for (int i = 0; i < p; ++i) {
+    int64_t bf = -1;
+    const int32_t rc = oracle_wvcp_iterated(n, adj, w, k, SO + (size_t)i * n, iters, max_ls, L_max, a_num, a_den,
+                                            fscale, phi0, phi_last, seed, (uint32_t)i, gen, Sp.data() + (size_t)i * n,
+                                            &bf, nullptr, nullptr);
+    if (rc) return rc;
+    fSp[i] = bf >= 0 ? bf : wsum + 1;
+  }
+  return memetic_after_search(n, k, p, K, P, fP, DP, SO, Sp, fSp, use_scorer, d0, d, nl, th, am, av, adam_t, epochs,
+                              batch, lr, ext_scores, seed, gen, best_col, best_f, diag_fprime, diag_pick);
+}
+
 }  // extern "C"
+

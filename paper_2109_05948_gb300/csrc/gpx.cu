@@ -159,7 +159,7 @@ extern "C" dlm_status dlm_gpx_batch(dlm_ctx* ctx, int32_t n, int32_t k, const in
                                     uint64_t seed, uint32_t generation) {
   if (!ctx) return DLM_EINVAL;
   if (n < 1 || n > 2048 || k < 1 || pop < 1 || m < 0) return fail(ctx, DLM_EINVAL, "gpx_batch: bad sizes");
-  if (k > 128) return fail(ctx, DLM_EUNSUPPORTED, "gpx_batch: k must be <= 128");
+  if (k > 255) return fail(ctx, DLM_EUNSUPPORTED, "gpx_batch: k must be <= 255");
   if (m == 0) return DLM_OK;
   if (!parents || !pairs || !children) return fail(ctx, DLM_EINVAL, "gpx_batch: null pointer");
   const size_t smem = gpx_layout(n, k).total * kGpxWarps;

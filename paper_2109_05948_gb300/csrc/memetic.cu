@@ -28,6 +28,9 @@ struct dlm_memetic {
   double* dstat = nullptr;  // [16] device: accumulators and results
   double* h_stat = nullptr;  // [16] pinned
   uint64_t fingerprint = 0;  // of the graph's bit rows and of every search / training parameter
+  // WVCP (problem 1): the total weight (fitness of an offspring that never became legal) and the
+  // fixed-point penalty schedule of the iterated search
+  int64_t wsum = 0, phi0 = 0, phi_last = 0;
   int64_t* h_best = nullptr;  // pinned
   dlm_scorer* scorer = nullptr;
   // the scorer trains on a side stream while the distances and the pool update run
@@ -249,6 +252,30 @@ __global__ void k_dist_stats_done(int p, double* dstat) {
   dstat[7] = (double)(int64_t)*(unsigned long long*)(dstat + 12);
 }
 
+// WVCP score f(S) = sum over colour classes of the largest weight in the class (section "Weighted
+// vertex coloring problem"), one block per colouring; k <= 256
+__global__ void __launch_bounds__(256) k_wvcp_fitness(int n, int k, const int16_t* col, const int32_t* w, int64_t* f) {
+  __shared__ int mx[256];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) mx[c] = 0;
+  __syncthreads();
+  const int16_t* s = col + (size_t)blockIdx.x * n;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) atomicMax(&mx[s[v]], w[v]);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    long long t = 0;
+    for (int c = threadIdx.x; c < k; c += 32) t += mx[c];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    if (threadIdx.x == 0) f[blockIdx.x] = t;
+  }
+}
+
+// an offspring none of whose searches ended legal (best f = -1) gets sum(w) + 1, above every legal
+// colouring's score
+__global__ void k_wvcp_fix(int p, int64_t wsum, int64_t* f) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < p && f[i] < 0) f[i] = wsum + 1;
+}
+
 template <typename T>
 static dlm_status alloc(dlm_ctx* ctx, T** p, size_t count) {
   if (cudaMalloc((void**)p, std::max<size_t>(1, count) * sizeof(T)) != cudaSuccess) {
@@ -284,9 +311,13 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
   if (!ctx || !g || !prm || !out) return fail(ctx, DLM_EINVAL, "memetic_create: null argument");
   *out = nullptr;
   const int p = prm->p, K = prm->K, n = g->n, k = prm->k;
-  if (p < 2 || K < 1 || K > p - 1 || K > 64 || k < 2 || k > 128 || prm->iters < 0)
-    return fail(ctx, DLM_EINVAL, "memetic_create: need p >= 2, 1 <= K <= min(64, p-1), 2 <= k <= 128");
+  const bool wvcp = prm->problem == 1;
+  if (prm->problem != 0 && prm->problem != 1) return fail(ctx, DLM_EINVAL, "memetic_create: problem must be 0 or 1");
+  if (p < 2 || K < 1 || K > p - 1 || K > 64 || k < 2 || k > (wvcp ? 255 : 128) || prm->iters < 0)
+    return fail(ctx, DLM_EINVAL, "memetic_create: need p >= 2, 1 <= K <= min(64, p-1), 2 <= k <= 128 (255 for WVCP)");
   if (p > 8192) return fail(ctx, DLM_EUNSUPPORTED, "memetic_create: p must be <= 8192");
+  if (wvcp && !g->d_weight) return fail(ctx, DLM_EINVAL, "memetic_create: WVCP needs a graph with vertex weights");
+  if (wvcp && (prm->max_ls < 1 || prm->max_ls > 16)) return fail(ctx, DLM_EINVAL, "memetic_create: max_ls must be in 1..16");
   if (prm->use_scorer && (prm->epochs < 0 || prm->batch < 1)) return fail(ctx, DLM_EINVAL, "memetic_create: bad training parameters");
   dlm_memetic* mm = new dlm_memetic();
   mm->g = g;
@@ -337,12 +368,40 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
     mix(&prm->iters, sizeof(prm->iters)); mix(&prm->tenure, sizeof(prm->tenure));
     mix(&prm->use_scorer, sizeof(prm->use_scorer)); mix(&prm->epochs, sizeof(prm->epochs));
     mix(&prm->batch, sizeof(prm->batch)); mix(&prm->lr, sizeof(prm->lr)); mix(&prm->seed, sizeof(prm->seed));
+    mix(&prm->problem, sizeof(prm->problem));
+    if (wvcp && st == DLM_OK) {
+      std::vector<int32_t> hw((size_t)n);
+      st = cuda_check(ctx, cudaMemcpy(hw.data(), g->d_weight, (size_t)n * 4, cudaMemcpyDeviceToHost), "copy");
+      mix(hw.data(), hw.size() * 4);
+      mix(&prm->max_ls, sizeof(prm->max_ls));
+      for (int32_t x : hw) mm->wsum += x;
+      // phi0 = k max w / (2 |V|) and phi_last = 2 max w (Algorithm 2), in fixed point of 1/256
+      const int64_t wmax = g->max_weight;
+      mm->phi0 = std::max<int64_t>(1, (256 * (int64_t)k * wmax + n) / (2 * (int64_t)n));
+      mm->phi_last = std::max<int64_t>(1, 256 * 2 * wmax);
+    }
     mm->fingerprint = h;
   }
-  // initial population: random colourings, their conflicts and their distance matrix
+  if (st != DLM_OK) { dlm_memetic_destroy(mm); return st; }
+  // initial population: random colourings (k-COL) or the randomised greedy initialisation (WVCP),
+  // their fitness and their distance matrix
   const int64_t big = INT64_MAX;
-  st = dlm_init_colors(ctx, n, k, p, prm->seed, 0u, mm->P);
-  if (st == DLM_OK) st = dlm_gamma(ctx, g, k, p, mm->P, nullptr, mm->fP);
+  if (wvcp) {
+    st = dlm_wvcp_greedy(ctx, g, p, prm->seed, 0u, mm->P, mm->sel);
+    if (st == DLM_OK) {
+      std::vector<int32_t> used((size_t)p);
+      st = cuda_check(ctx, cudaMemcpy(used.data(), mm->sel, (size_t)p * 4, cudaMemcpyDeviceToHost), "copy");
+      if (st == DLM_OK && *std::max_element(used.begin(), used.end()) > k)
+        st = fail(ctx, DLM_EINVAL, "memetic_create: the greedy initialisation opens more than k colours");
+    }
+    if (st == DLM_OK) {
+      k_wvcp_fitness<<<p, 256, 0, ctx->stream>>>(n, k, mm->P, g->d_weight, mm->fP);
+      st = launch_check(ctx, "k_wvcp_fitness");
+    }
+  } else {
+    st = dlm_init_colors(ctx, n, k, p, prm->seed, 0u, mm->P);
+    if (st == DLM_OK) st = dlm_gamma(ctx, g, k, p, mm->P, nullptr, mm->fP);
+  }
   if (st == DLM_OK) st = dlm_distance_batch(ctx, n, k, mm->P, p, mm->P, p, mm->DP, p, 0);
   if (st == DLM_OK) st = cuda_check(ctx, cudaMemcpyAsync(mm->SO, mm->P, pn * 2, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
   if (st == DLM_OK) st = cuda_check(ctx, cudaMemcpyAsync(mm->best_f, &big, 8, cudaMemcpyHostToDevice, ctx->stream), "copy");
@@ -362,9 +421,19 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
   cudaStream_t s = ctx->stream;
   auto mark = [&](int i) { if (mm->prof) cudaEventRecord(mm->pev[i], s); };
   mark(0);
-  // 1. local search of every offspring: S'_i <- TabuCol(S^O_i)
-  DLM_CUDA(ctx, cudaMemcpyAsync(mm->Sp, mm->SO, pn * 2, cudaMemcpyDeviceToDevice, s));
-  DLM_TRY(dlm_tabucol_batch(ctx, mm->g, k, p, mm->Sp, mm->fSp, mm->moves, q.iters, q.tenure, q.seed, mm->gen, 0u));
+  // 1. local search of every offspring: S'_i <- TabuCol(S^O_i) (k-COL), or the iterated feasible
+  //    and infeasible tabu search from S^O_i (WVCP; Pn, free until the gather, holds its running
+  //    colourings)
+  if (q.problem == 1) {
+    DLM_CUDA(ctx, cudaMemcpyAsync(mm->Pn, mm->SO, pn * 2, cudaMemcpyDeviceToDevice, s));
+    DLM_TRY(dlm_wvcp_iterated(ctx, mm->g, k, p, mm->Pn, mm->Sp, mm->fSp, q.iters, q.max_ls, q.tenure, 256, mm->phi0,
+                              mm->phi_last, q.seed, mm->gen, 0u));
+    k_wvcp_fix<<<(p + 255) / 256, 256, 0, s>>>(p, mm->wsum, mm->fSp);
+    DLM_TRY(launch_check(ctx, "k_wvcp_fix"));
+  } else {
+    DLM_CUDA(ctx, cudaMemcpyAsync(mm->Sp, mm->SO, pn * 2, cudaMemcpyDeviceToDevice, s));
+    DLM_TRY(dlm_tabucol_batch(ctx, mm->g, k, p, mm->Sp, mm->fSp, mm->moves, q.iters, q.tenure, q.seed, mm->gen, 0u));
+  }
   mark(1);
   // 2. best so far
   k_best_of<<<1, 1024, 0, s>>>(p, n, mm->fSp, mm->Sp, mm->best_f, mm->best_col);

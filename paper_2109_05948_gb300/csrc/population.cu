@@ -341,7 +341,7 @@ extern "C" dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, con
                                          const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper) {
   if (!ctx) return DLM_EINVAL;
   if (n < 1 || n > 2048 || k < 1 || a < 0 || b < 0 || ldD < b) return fail(ctx, DLM_EINVAL, "distance: bad sizes");
-  if (k > 128) return fail(ctx, DLM_EUNSUPPORTED, "distance: k must be <= 128");
+  if (k > 255) return fail(ctx, DLM_EUNSUPPORTED, "distance: k must be <= 255");
   if (a == 0 || b == 0) return DLM_OK;
   if (!X || !Y || !D) return fail(ctx, DLM_EINVAL, "distance: null pointer");
   if (a > 65535) return fail(ctx, DLM_EUNSUPPORTED, "distance: at most 65535 rows");

@@ -35,11 +35,12 @@
 using bf16 = __nv_bfloat16;
 
 namespace dlm {
-constexpr int kD0 = 64, kD = 256, kNL = 3, kR = 64;
+constexpr int kD0 = 64, kD = 256, kNL = 3, kRMax = 256;  // rows per candidate: 64 ceil(k / 64) <= 256
 }
 
 struct dlm_scorer {
   int n = 0, k = 0;
+  int R = 64;  // rows per candidate in the layer matrices: k rounded up to a multiple of 64
   int64_t np = 0;
   int64_t t = 0;  // Adam step counter
   size_t oE = 0, ob0 = 0, olam[4] = {}, ogam[4] = {}, ob[4] = {}, owh = 0, obh = 0;
@@ -164,23 +165,23 @@ __device__ __forceinline__ float gterm_col(const float* m, int din, const float*
 // perm[step[0] + b]) and, with G1 set, ends with layer 1's per-candidate term
 // G1 = beta_1 + mean_c(H0) Gamma_1.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols, int c, const int32_t* perm,
+__global__ void __launch_bounds__(256) k_pool(int n, int k, int R, const int16_t* cols, int c, const int32_t* perm,
                                               const int32_t* step, const float* E, const float* b0, bf16* H0,
                                               bf16* H0lo, float* Mf0, bf16* Mb0, bf16* Mb0lo, const float* gam1,
                                               const float* beta1, float* G1, int32_t* status) {
   extern __shared__ __align__(16) uint8_t sm[];
   uint8_t* col = sm;                                        // [n]
   uint16_t* mem = (uint16_t*)(sm + ((n + 15) & ~15));       // [n]
-  int* cnt = (int*)(mem + ((n + 7) & ~7));                  // [64]
-  int* off = cnt + 64;                                      // [65]
-  int* cur = off + 65;                                      // [64]
-  float* part = (float*)(cur + 64);                         // [8][64]
+  int* cnt = (int*)(mem + ((n + 7) & ~7));                  // [256]
+  int* off = cnt + kRMax;                                   // [257]
+  int* cur = off + kRMax + 1;                               // [256]
+  float* part = (float*)(cur + kRMax);                      // [8][64]
   float* mvec = part + 8 * 64;                              // [64]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int cand = blockIdx.x; cand < c; cand += gridDim.x) {
     const int srow = perm ? perm[step[0] + cand] : cand;
     const int16_t* cc = cols + (size_t)srow * n;
-    if (tid < 64) cnt[tid] = 0;
+    cnt[tid] = 0;  // 256 threads: every class counter
     __syncthreads();
     for (int v = tid; v < n; v += 256) {
       int q = cc[v];
@@ -190,22 +191,27 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
     }
     __syncthreads();
     if (warp == 0) {
-      const int x0 = cnt[lane], x1 = cnt[lane + 32];
-      int i0 = x0, i1 = x1;
+      // exclusive prefix of the class sizes: lane l holds classes 8 l .. 8 l + 7
+      int x[8], loc = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { x[u] = cnt[8 * lane + u]; loc += x[u]; }
+      int incl = loc;
       for (int d = 1; d < 32; d <<= 1) {
-        const int a = __shfl_up_sync(0xFFFFFFFFu, i0, d), b = __shfl_up_sync(0xFFFFFFFFu, i1, d);
-        if (lane >= d) { i0 += a; i1 += b; }
+        const int a = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += a;
       }
-      const int tot0 = __shfl_sync(0xFFFFFFFFu, i0, 31);
-      off[lane] = i0 - x0;
-      off[lane + 32] = tot0 + i1 - x1;
-      cur[lane] = i0 - x0;
-      cur[lane + 32] = tot0 + i1 - x1;
-      if (lane == 31) off[64] = tot0 + i1;
+      int o = incl - loc;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        off[8 * lane + u] = o;
+        cur[8 * lane + u] = o;
+        o += x[u];
+      }
+      if (lane == 31) off[kRMax] = incl;
       // stable scatter: chunks of 32 vertices in order, rank among equal colours by lane order
       for (int v0 = 0; v0 < n; v0 += 32) {
         const int v = v0 + lane;
-        const int q = v < n ? col[v] : 64 + lane;
+        const int q = v < n ? col[v] : kRMax + lane;
         const unsigned same = __match_any_sync(0xFFFFFFFFu, q);
         const int rank = __popc(same & ((1u << lane) - 1u));
         int base = 0;
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
     __syncthreads();
     float2 msum = make_float2(0.f, 0.f);
     const float2 bb = make_float2(b0[2 * lane], b0[2 * lane + 1]);
-    for (int q = warp; q < kR; q += 8) {
+    for (int q = warp; q < R; q += 8) {
       float2 acc = make_float2(0.f, 0.f);
       if (q < k) {
         // members in ascending order; eight embedding rows are loaded before they are added (the
@@ -250,10 +256,10 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, const int16_t* cols,
         msum.y += acc.y;
       }
       const __nv_bfloat162 hi = __floats2bfloat162_rn(acc.x, acc.y);
-      *reinterpret_cast<__nv_bfloat162*>(H0 + ((size_t)cand * kR + q) * kD0 + 2 * lane) = hi;
+      *reinterpret_cast<__nv_bfloat162*>(H0 + ((size_t)cand * R + q) * kD0 + 2 * lane) = hi;
       if (H0lo) {
         const float2 hf = __bfloat1622float2(hi);
-        *reinterpret_cast<__nv_bfloat162*>(H0lo + ((size_t)cand * kR + q) * kD0 + 2 * lane) =
+        *reinterpret_cast<__nv_bfloat162*>(H0lo + ((size_t)cand * R + q) * kD0 + 2 * lane) =
             __floats2bfloat162_rn(acc.x - hf.x, acc.y - hf.y);
       }
     }
@@ -289,10 +295,10 @@ __global__ void __launch_bounds__(256) k_gterm(int c, int din, const float* M, c
 
 // per-candidate mean (or sum) over the k valid rows of a bf16 [c*R][w] matrix, column col of
 // candidate cand; returns the value written to outf
-__device__ __forceinline__ float segment_col(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf,
-                                             bf16* outb, bf16* outblo, int cand, int col) {
-  const bf16* x = X + (size_t)cand * kR * w + col;
-  const bf16* xl = Xlo ? Xlo + (size_t)cand * kR * w + col : nullptr;
+__device__ __forceinline__ float segment_col(const bf16* X, const bf16* Xlo, int w, int k, int R, float scale,
+                                             float* outf, bf16* outb, bf16* outblo, int cand, int col) {
+  const bf16* x = X + (size_t)cand * R * w + col;
+  const bf16* xl = Xlo ? Xlo + (size_t)cand * R * w + col : nullptr;
   float s = 0.f;
   int r = 0;
   for (; r + 16 <= k; r += 16) {  // sixteen rows loaded before they are added, sum in row order
@@ -315,32 +321,34 @@ __device__ __forceinline__ float segment_col(const bf16* X, const bf16* Xlo, int
 }
 
 // block = w threads, one candidate per block
-__global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, float scale, float* outf, bf16* outb,
-                                 bf16* outblo) {
-  segment_col(X, Xlo, w, k, scale, outf, outb, outblo, blockIdx.x, threadIdx.x);
+__global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, int R, float scale, float* outf,
+                                 bf16* outb, bf16* outblo) {
+  segment_col(X, Xlo, w, k, R, scale, outf, outb, outblo, blockIdx.x, threadIdx.x);
 }
 
 // a training batch between layers l and l + 1: the class mean of H_l (written as above), then
 // the next layer's per-candidate term G = beta + mean Gamma (block = 256 threads, one candidate)
-__global__ void __launch_bounds__(kD) k_mean_gterm(const bf16* X, const bf16* Xlo, int k, float* outf, bf16* outb,
-                                                   bf16* outblo, const float* gam, const float* beta, float* G) {
+__global__ void __launch_bounds__(kD) k_mean_gterm(const bf16* X, const bf16* Xlo, int k, int R, float* outf,
+                                                   bf16* outb, bf16* outblo, const float* gam, const float* beta,
+                                                   float* G) {
   __shared__ float ms[kD];
   const int cand = blockIdx.x, o = threadIdx.x;
-  ms[o] = segment_col(X, Xlo, kD, k, 1.f / k, outf, outb, outblo, cand, o);
+  ms[o] = segment_col(X, Xlo, kD, k, R, 1.f / k, outf, outb, outblo, cand, o);
   __syncthreads();
   G[(size_t)cand * kD + o] = gterm_col(ms, kD, gam, beta, o);
 }
 
 // output = head bias + mean over the k class rows of the head dot, whose row values come in
 // `parts` column slices of M = c * R rows each (summed in slice order)
-__global__ void k_head_out(int c, int k, const float* rowdot, int parts, const float* theta, size_t obh, float* out) {
+__global__ void k_head_out(int c, int k, int R, const float* rowdot, int parts, const float* theta, size_t obh,
+                           float* out) {
   const int cand = blockIdx.x * blockDim.x + threadIdx.x;
   if (cand >= c) return;
-  const size_t M = (size_t)c * kR;
+  const size_t M = (size_t)c * R;
   float s = 0.f;
   for (int r = 0; r < k; ++r) {
-    float t = rowdot[(size_t)cand * kR + r];
-    for (int q = 1; q < parts; ++q) t += rowdot[q * M + (size_t)cand * kR + r];
+    float t = rowdot[(size_t)cand * R + r];
+    for (int q = 1; q < parts; ++q) t += rowdot[q * M + (size_t)cand * R + r];
     s += t;
   }
   out[cand] = theta[obh] + s / (float)k;
@@ -366,12 +374,12 @@ __device__ __forceinline__ void transpose_tile(const bf16* X, int rows, int cols
 //   blocks [0, B)            column sums S = sum over the k valid rows of dZ_l, per candidate
 //   next ceil(rows/32) * 8   tiles of dZ_l^T
 //   next 2 ceil(rows/32) (din/32)  tiles of H_{l-1}^T and of its lo part
-__global__ void __launch_bounds__(256) k_bwd_prep(int B, int k, int rows, int din, const bf16* dZ, float* S,
+__global__ void __launch_bounds__(256) k_bwd_prep(int B, int k, int R, int rows, int din, const bf16* dZ, float* S,
                                                   bf16* dZT, const bf16* H, const bf16* Hlo, bf16* HT, bf16* HTlo) {
   __shared__ bf16 tile[32][33];
   int t = blockIdx.x;
   if (t < B) {
-    segment_col(dZ, nullptr, kD, k, 1.f, S, nullptr, nullptr, t, threadIdx.x);
+    segment_col(dZ, nullptr, kD, k, R, 1.f, S, nullptr, nullptr, t, threadIdx.x);
     return;
   }
   t -= B;
@@ -442,7 +450,7 @@ struct EpiPartial {  // split-K slice z: part[z][row][col] = acc
 struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optional head dot
   bf16* H;    // may be null (scoring the last layer)
   bf16* Hlo;  // lo part (training) or null
-  int M, kv;
+  int M, kv, R;
   const float* G;
   const float* wh;
   float* rowdot;  // [256 / pbn][M]: the head dot of each row over the pbn columns one epilogue warp drains
@@ -452,8 +460,8 @@ struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optiona
   __device__ void tile(int, int n0) { part = n0 / pbn; }
   __device__ void operator()(int row, int col0, const float (&v)[16]) {
     if (row >= M) return;
-    const int cand = row / kR;
-    const bool valid = (row % kR) < kv;
+    const int cand = row / R;
+    const bool valid = row - cand * R < kv;
     const float* g = G + (size_t)cand * kD + col0;
     float h[16];
 #pragma unroll
@@ -500,13 +508,13 @@ struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optiona
 struct EpiBwd {  // dZprev[row][col] = mask((acc + Gb[cand][col]) * LeakyReLU'(Hprev[row][col]))
   __device__ void tile(int, int) {}
   bf16* dZ;
-  int ld, M, kv;
+  int ld, M, kv, R;
   const float* Gb;
   const bf16* Hp;
   __device__ void operator()(int row, int col0, const float (&v)[16]) const {
     if (row >= M) return;
-    const int cand = row / kR;
-    const bool valid = (row % kR) < kv;
+    const int cand = row / R;
+    const bool valid = row - cand * R < kv;
     const float* g = Gb + (size_t)cand * ld + col0;
     const uint4* hsrc = reinterpret_cast<const uint4*>(Hp + (size_t)row * ld + col0);
     uint4 hv[2] = {hsrc[0], hsrc[1]};
@@ -552,10 +560,10 @@ __global__ void k_loss(int B, const float* out, const float* y, const int32_t* p
 }
 
 // dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows; block = one candidate row chunk
-__device__ __forceinline__ void head_back_row(int k, const float* dout, const float* theta, size_t owh, const bf16* H3,
-                                              bf16* dZ3, int row, int o) {
-  const int cand = row / kR;
-  const bool valid = (row % kR) < k;
+__device__ __forceinline__ void head_back_row(int k, int R, const float* dout, const float* theta, size_t owh,
+                                              const bf16* H3, bf16* dZ3, int row, int o) {
+  const int cand = row / R;
+  const bool valid = row - cand * R < k;
   float d = 0.f;
   if (valid) {
     d = dout[cand] / (float)k * theta[owh + o];
@@ -587,10 +595,10 @@ __device__ __forceinline__ void head_grad_col(int B, const float* dout, const fl
 
 // blocks 0 .. rows - 1: dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows (thread = column);
 // block rows: the head's gradient (wh[o] = sum_cand dout * mean(H3)[cand][o], bh = sum dout)
-__global__ void __launch_bounds__(kD) k_head_bwd(int B, int k, int rows, const float* dout, const float* theta,
+__global__ void __launch_bounds__(kD) k_head_bwd(int B, int k, int R, int rows, const float* dout, const float* theta,
                                                  size_t owh, size_t obh, const bf16* H3, const float* Mf3, bf16* dZ3,
                                                  float* grad) {
-  if ((int)blockIdx.x < rows) head_back_row(k, dout, theta, owh, H3, dZ3, blockIdx.x, threadIdx.x);
+  if ((int)blockIdx.x < rows) head_back_row(k, R, dout, theta, owh, H3, dZ3, blockIdx.x, threadIdx.x);
   else head_grad_col(B, dout, Mf3, grad, owh, obh, threadIdx.x);
 }
 
@@ -675,8 +683,8 @@ __global__ void __launch_bounds__(kD) k_bwd_grads(int B, int din, int k, int64_t
 
 // embedding gradient: dE[v][f] = sum_cand dZ0[cand*R + col_cand[v]][f]; db0[f] = sum_cand S0[cand][f]
 // (with perm, candidate c of the batch is sample perm[step[0] + c] of cols)
-__global__ void k_demb(int n, int B, const int16_t* cols, const int32_t* perm, const int32_t* step, const bf16* dZ0,
-                       const float* S0, float* grad, size_t oE, size_t ob0) {
+__global__ void k_demb(int n, int B, int R, const int16_t* cols, const int32_t* perm, const int32_t* step,
+                       const bf16* dZ0, const float* S0, float* grad, size_t oE, size_t ob0) {
   const int v = blockIdx.x, f = threadIdx.x;  // 64 threads
   auto row = [&](int c) -> size_t { return (size_t)(perm ? perm[step[0] + c] : c) * n; };
   if (v < n) {
@@ -688,13 +696,13 @@ __global__ void k_demb(int n, int B, const int16_t* cols, const int32_t* perm, c
 #pragma unroll
       for (int u = 0; u < 8; ++u) q[u] = cols[row(c + u) + v];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) z[u] = __bfloat162float(dZ0[((size_t)(c + u) * kR + q[u]) * kD0 + f]);
+      for (int u = 0; u < 8; ++u) z[u] = __bfloat162float(dZ0[((size_t)(c + u) * R + q[u]) * kD0 + f]);
 #pragma unroll
       for (int u = 0; u < 8; ++u) s += z[u];
     }
     for (; c < B; ++c) {
       const int q = cols[row(c) + v];
-      s += __bfloat162float(dZ0[((size_t)c * kR + q) * kD0 + f]);
+      s += __bfloat162float(dZ0[((size_t)c * R + q) * kD0 + f]);
     }
     grad[oE + (size_t)v * kD0 + f] = s;
   } else {
@@ -964,21 +972,23 @@ static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
   return launch_check(ctx, "k_convert");
 }
 
-static size_t pool_smem(int n) { return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + (64 + 65 + 64) * 4 + 9 * 64 * 4 + 64; }
+static size_t pool_smem(int n) {
+  return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + (3 * kRMax + 1) * 4 + 9 * 64 * 4 + 64;
+}
 
 // forward over c candidates with the given buffers; train = a training batch: keep every
 // activation (and H3), candidate b being sample perm[step[0] + b] of cols when perm is given
 static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int c, float* out, bf16** H, bf16** Hlo,
                           bf16** Mb, bf16** Mblo, float** Mf, float** G, float* rowdot, bool train,
                           const int32_t* perm = nullptr, const int32_t* step = nullptr) {
-  const int rows = c * kR;
+  const int rows = c * s->R;
   const size_t psm = pool_smem(s->n);  // < 10 KB for n <= 2048
   const int pgrid = std::min(c, ctx->num_sms * 4);
   // per-candidate term rho(H_{l-1}) Gamma_l + beta_l: on the tensor cores for a scoring chunk,
   // both operands split into bf16 hi + lo (three MMA passes, about 16 mantissa bits each); in
   // FP32 on CUDA cores for a small batch, for a training batch fused into the kernel that forms
   // the class means (k_pool for layer 1, k_mean_gterm for layers 2 and 3)
-  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, cols, c, perm, step, s->theta + s->oE, s->theta + s->ob0, H[0],
+  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, s->R, cols, c, perm, step, s->theta + s->oE, s->theta + s->ob0, H[0],
                                            Hlo ? Hlo[0] : nullptr, Mf[0], Mb[0], Mblo[0],
                                            s->theta + s->ogam[1], s->theta + s->ob[1], train ? G[1] : nullptr,
                                            ctx->d_status);
@@ -998,7 +1008,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
     // a training batch runs its layer GEMMs as 128 x 64 tiles with one pipeline stage: four
     // times the CTAs of a 128 x 256 tile for a few thousand rows, and about 50 KB of shared
     // memory each instead of 193 KB
-    EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, G[l],
+    EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, s->R, G[l],
                last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, train ? 32 : 128, 0};
     if (train)
       DLM_TRY((gemm<64, 1>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din,
@@ -1007,16 +1017,16 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       DLM_TRY(gemm<256>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din, 0,
                         e));
     if (train && !last) {
-      k_mean_gterm<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, s->k, Mf[l], Mb[l], Mblo[l],
+      k_mean_gterm<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, s->k, s->R, Mf[l], Mb[l], Mblo[l],
                                               s->theta + s->ogam[l + 1], s->theta + s->ob[l + 1], G[l + 1]);
       DLM_TRY(launch_check(ctx, "k_mean_gterm"));
     } else if (!last || train) {
-      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, 1.f / s->k, Mf[l], Mb[l],
+      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, s->R, 1.f / s->k, Mf[l], Mb[l],
                                                   Mblo[l]);
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
-  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, rowdot, train ? kD / 32 : kD / 128, s->theta, s->obh,
+  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, s->R, rowdot, train ? kD / 32 : kD / 128, s->theta, s->obh,
                                                        out);
   return launch_check(ctx, "k_head_out");
 }
@@ -1028,10 +1038,10 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
                             const int32_t* perm = nullptr, const int32_t* step = nullptr) {
   DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mbblo, s->Mfb, s->Gbf, s->rowdotb, true, perm,
                   step));
-  const int rows = B * kR;
+  const int rows = B * s->R;
   k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, perm, step, s->dout, s->lossd);
   DLM_TRY(launch_check(ctx, "k_loss"));
-  k_head_bwd<<<rows + 1, kD, 0, ctx->stream>>>(B, s->k, rows, s->dout, s->theta, s->owh, s->obh, s->Hb[kNL],
+  k_head_bwd<<<rows + 1, kD, 0, ctx->stream>>>(B, s->k, s->R, rows, s->dout, s->theta, s->owh, s->obh, s->Hb[kNL],
                                                s->Mfb[kNL], s->dZ[kNL], s->grad);
   DLM_TRY(launch_check(ctx, "k_head_bwd"));
   for (int l = kNL; l >= 1; --l) {
@@ -1040,7 +1050,8 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
     // transposes of dZ_l and H_{l-1} (hi and lo) for the weight-gradient GEMM, in one launch
     const int ty = (rows + 31) / 32;
     k_bwd_prep<<<B + ty * (kD / 32) + 2 * ty * (din / 32), 256, 0, ctx->stream>>>(
-        B, s->k, rows, din, s->dZ[l], s->S[l], s->dZT[l], s->Hb[l - 1], s->Hblo[l - 1], s->HT[l - 1], s->HTlo[l - 1]);
+        B, s->k, s->R, rows, din, s->dZ[l], s->S[l], s->dZT[l], s->Hb[l - 1], s->Hblo[l - 1], s->HT[l - 1],
+        s->HTlo[l - 1]);
     DLM_TRY(launch_check(ctx, "k_bwd_prep"));
     // dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction)
     const int nchunks = rows / tc::BK, kc = 4, splits = (nchunks + kc - 1) / kc;
@@ -1053,18 +1064,18 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
         s->ogam[l], s->ob[l], s->Gb);
     DLM_TRY(launch_check(ctx, "k_bwd_grads"));
     // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
-    EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->Gb, s->Hb[l - 1]};
+    EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->R, s->Gb, s->Hb[l - 1]};
     DLM_TRY((gemm<64, 1>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
   }
-  k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, 1.f, s->S[0], nullptr, nullptr);
-  k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
+  k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, s->R, 1.f, s->S[0], nullptr, nullptr);
+  k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, s->R, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
   return launch_check(ctx, "k_demb");
 }
 
 static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
   if (B <= s->capb) return DLM_OK;
   if (B > 256) return fail(ctx, DLM_EUNSUPPORTED, "scorer: training batches are limited to 256 samples");
-  const int cb = 256, rows = cb * kR, cpad = cb;
+  const int cb = 256, rows = cb * s->R, cpad = cb;
   for (int l = 0; l <= kNL; ++l) {
     const int w = l == 0 ? kD0 : kD;
     DLM_TRY(dalloc(ctx, &s->Hb[l], (size_t)rows * w));
@@ -1091,7 +1102,7 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
 
 static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
   if (s->cap) return DLM_OK;
-  const int cap = 8192, rows = cap * kR;
+  const int cap = 8192 * 64 / s->R, rows = cap * s->R;  // the same bytes for every k
   for (int l = 0; l <= kNL; ++l) {
     const int w = l == 0 ? kD0 : kD;
     if (l < kNL) DLM_TRY(dalloc(ctx, &s->H[l], (size_t)rows * w));
@@ -1180,10 +1191,11 @@ extern "C" dlm_status dlm_scorer_create(dlm_ctx* ctx, int32_t n, int32_t k, uint
   if (!ctx || !out) return fail(ctx, DLM_EINVAL, "scorer_create: null argument");
   *out = nullptr;
   if (n < 1 || n > 2048 || k < 1) return fail(ctx, DLM_EINVAL, "scorer_create: bad sizes");
-  if (k > kR) return fail(ctx, DLM_EUNSUPPORTED, "scorer_create: k must be <= 64");
+  if (k > kRMax) return fail(ctx, DLM_EUNSUPPORTED, "scorer_create: k must be <= 256");
   dlm_scorer* s = new dlm_scorer();
   s->n = n;
   s->k = k;
+  s->R = 64 * ((k + 63) / 64);
   size_t o = 0;
   s->oE = o; o += (size_t)n * kD0;
   s->ob0 = o; o += kD0;

@@ -32,7 +32,8 @@ class Tenure(ctypes.Structure):
 class MemeticParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("p", ctypes.c_int32), ("K", ctypes.c_int32), ("iters", ctypes.c_int64),
                 ("tenure", Tenure), ("use_scorer", ctypes.c_int32), ("epochs", ctypes.c_int32),
-                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("problem", ctypes.c_int32), ("max_ls", ctypes.c_int32)]
 
 
 class TabuOpts(ctypes.Structure):

@@ -239,3 +239,95 @@ def test_learned_selection_gain_over_random_gpx(ctx):
             assert fl < fr, (gi, fl, fr)
     assert abs(med_at(1, "pred_pearson", 1)) < 0.3  # before the first training pays off
     assert np.median([r for _, r in res[1]]) <= np.median([r for _, r in res[0]])
+
+
+def _wvcp_case(n, dens, seed, extra):
+    e = inputs.gnp(n, dens, seed)
+    w = inputs.weights(n, seed)
+    adj = inputs.edges_to_adj(n, e)
+    used = max(oracle.wvcp_greedy(adj, w, seed, i)[1] for i in range(64))
+    return e, w, adj, used + extra
+
+
+def _wvcp_phi(n, k, w):
+    # the penalty schedule dlm_memetic_create documents: round(256 k max w / (2 |V|)), 256 * 2 max w
+    return max(1, (256 * k * int(w.max()) + n) // (2 * n)), 256 * 2 * int(w.max())
+
+
+@pytest.mark.parametrize("n,dens,p,K,iters,max_ls,gens,seed,extra",
+                         [(60, 0.3, 24, 4, 120, 3, 2, 11, 3), (90, 0.5, 16, 15, 90, 4, 2, 12, 70)])
+def test_wvcp_memetic_random_gpx_bitexact(ctx, n, dens, p, K, iters, max_ls, gens, seed, extra):
+    """WVCP generations (greedy initial population, iterated feasible / infeasible tabu search,
+    WVCP fitness) against the oracle, bit for bit; the second case has k above 64 colours."""
+    e, w, adj, k = _wvcp_case(n, dens, seed, extra)
+    g = device_graph(ctx, n, e, w)
+    prm = dlmcol.MemeticParams(k=k, p=p, K=K, iters=iters, tenure=dlmcol.WVCP_TENURE, use_scorer=0, epochs=0,
+                               batch=100, lr=1e-3, seed=seed, problem=1, max_ls=max_ls)
+    mm = dlmcol.Memetic(ctx, g, prm)
+    phi0, phi_last = _wvcp_phi(n, k, w)
+    st = oracle.WvcpMemeticState(adj, w, k, p, K, seed, iters, max_ls, 256, phi0, phi_last, use_scorer=0)
+    _compare(ctx, mm, st, p, n, K, -1)
+    for gen in range(gens):
+        best = dlmcol.dlm_memetic_step(ctx, mm)
+        fprime, pick = st.generation()
+        assert np.array_equal(_get(ctx, mm, 5, (p,), torch.int64), fprime)
+        assert np.array_equal(_get(ctx, mm, 6, (p,), torch.int32), pick)
+        assert best == st.best_f[0]
+        _compare(ctx, mm, st, p, n, K, gen)
+    mm.close()
+
+
+@pytest.mark.parametrize("extra", [2, 100])
+def test_wvcp_memetic_learned_bitexact_with_gpu_scores(ctx, extra):
+    """Learned WVCP generations: with the GPU's candidate scores the oracle picks the same
+    offspring and every array matches; extra = 100 puts k above 128 (three 64-row blocks of the
+    scorer's colour rows)."""
+    n, dens, p, K, iters, max_ls, seed = 70, 0.4, 16, 4, 80, 3, 13
+    e, w, adj, k = _wvcp_case(n, dens, seed, extra)
+    g = device_graph(ctx, n, e, w)
+    prm = dlmcol.MemeticParams(k=k, p=p, K=K, iters=iters, tenure=dlmcol.WVCP_TENURE, use_scorer=1, epochs=1,
+                               batch=8, lr=1e-3, seed=seed, problem=1, max_ls=max_ls)
+    mm = dlmcol.Memetic(ctx, g, prm)
+    phi0, phi_last = _wvcp_phi(n, k, w)
+    st = oracle.WvcpMemeticState(adj, w, k, p, K, seed, iters, max_ls, 256, phi0, phi_last, use_scorer=1, epochs=1,
+                                 batch=8)
+    for gen in range(2):
+        dlmcol.dlm_memetic_step(ctx, mm)
+        scores = _get(ctx, mm, 7, (p, K), torch.float32)
+        assert np.all(np.isfinite(scores))
+        fprime, pick = st.generation(ext_scores=scores)
+        assert np.array_equal(_get(ctx, mm, 6, (p,), torch.int32), pick)
+        assert np.array_equal(_get(ctx, mm, 5, (p,), torch.int64), fprime)
+        _compare(ctx, mm, st, p, n, K, gen)
+    # the trained network's scores of the GPU's candidates against the oracle network (FP64) with the
+    # GPU's parameters: selection-precision scores within the memetic's bf16 bound
+    dlmcol.dlm_memetic_step(ctx, mm)
+    nparams = oracle.ScorerDims(n).nparams()
+    th = _get(ctx, mm, 8, (nparams,), torch.float32).astype(np.float64)
+    scores = _get(ctx, mm, 7, (p, K), torch.float32)
+    P = _get(ctx, mm, 0, (p, n), torch.int16)
+    nbr = oracle.knn(_get(ctx, mm, 2, (p, p), torch.int16), K)
+    kids = np.stack([oracle.gpx(k, P[i], P[nbr[i, j]], seed, i * K + j, 2) for i in range(p) for j in range(K)])
+    ref = oracle.scorer_forward(oracle.ScorerDims(n), k, th, kids).reshape(p, K)
+    rel = np.linalg.norm(scores - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-2
+    mm.close()
+
+
+def test_wvcp_memetic_rejects_bad_parameters(ctx):
+    n = 40
+    e = inputs.gnp(n, 0.3, 1)
+    w = inputs.weights(n, 1)
+    g_now = device_graph(ctx, n, e)
+    g = device_graph(ctx, n, e, w)
+    base = dict(p=8, K=2, iters=10, tenure=dlmcol.WVCP_TENURE, use_scorer=0, epochs=0, batch=8, lr=1e-3, seed=1,
+                problem=1, max_ls=2)
+    with pytest.raises(RuntimeError):
+        dlmcol.Memetic(ctx, g_now, dlmcol.MemeticParams(k=20, **base))  # no weights
+    with pytest.raises(RuntimeError):
+        dlmcol.Memetic(ctx, g, dlmcol.MemeticParams(k=2, **base))  # the greedy needs more colours
+    with pytest.raises(RuntimeError):
+        dlmcol.Memetic(ctx, g, dlmcol.MemeticParams(k=256, **base))
+    bad = dict(base, max_ls=0)
+    with pytest.raises(RuntimeError):
+        dlmcol.Memetic(ctx, g, dlmcol.MemeticParams(k=20, **bad))

@@ -88,7 +88,9 @@ def _group_best_ok(got, ref, floor, G=32):
 
 @pytest.mark.parametrize("n,k,c,scale", [(200, 48, 37, 3.0), (97, 17, 130, 2.0), (64, 64, 9, 4.0), (30, 2, 5, 3.0),
                                          (60, 9, 2048, 3.0),  # Gamma terms on the tensor cores
-                                         (1000, 48, 1024, 3.0)])  # the learned workload's shape
+                                         (1000, 48, 1024, 3.0),  # the learned workload's shape
+                                         (120, 65, 70, 3.0), (300, 146, 300, 3.0),  # 2 and 3 blocks of 64 rows
+                                         (400, 256, 40, 3.0)])  # the largest k
 def test_scorer_forward_matches_oracle(ctx, n, k, c, scale):
     dims = oracle.ScorerDims(n)
     th = _params(dims, seed=n, scale=scale)
@@ -151,7 +153,7 @@ def test_scorer_permutation_invariant_on_gpu(ctx):
     s.close()
 
 
-@pytest.mark.parametrize("n,k,B", [(120, 17, 100), (300, 48, 33)])
+@pytest.mark.parametrize("n,k,B", [(120, 17, 100), (300, 48, 33), (200, 146, 40), (260, 256, 17)])
 def test_scorer_gradients_match_oracle(ctx, n, k, B):
     dims = oracle.ScorerDims(n)
     th = _params(dims, seed=k, scale=3.0)

@@ -448,3 +448,40 @@ def test_memetic_generation_invariants(use_scorer):
             j = nbr[i, pick[i]]
             child = oracle.gpx(k, st.P[i], st.P[j], seed=5, child_id=i * K + pick[i], gen=st.gen - 1)
             assert np.array_equal(child, st.SO[i])
+
+
+@pytest.mark.parametrize("use_scorer", [0, 1])
+def test_wvcp_memetic_generation_invariants(use_scorer):
+    """Algorithm 1 for the WVCP: the stored fitness is the WVCP score of the stored (legal)
+    colourings, the distances describe the population, the best-so-far is monotone and recounts,
+    every f(S') is the score of a legal colouring or sum(w) + 1, and every offspring is the GPX
+    child of i and one of its K nearest neighbours."""
+    n, p, K = 30, 10, 3
+    e = inputs.gnp(n, 0.3, seed=4)
+    adj = inputs.edges_to_adj(n, e)
+    w = inputs.weights(n, seed=4, hi=20)
+    k = max(oracle.wvcp_greedy(adj, w, 6, i)[1] for i in range(p)) + 1
+    fscale = 16
+    phi0 = (fscale * k * int(w.max()) + n) // (2 * n)
+    st = oracle.WvcpMemeticState(adj, w, k, p, K, seed=6, iters=40, max_ls=3, fscale=fscale, phi0=phi0,
+                                 phi_last=fscale * 2 * int(w.max()), use_scorer=use_scorer, d0=8, d=16, nl=3,
+                                 epochs=2, batch=4)
+    assert all(oracle.wvcp_score(adj, w, k, c)[1] == 0 for c in st.P)
+    prev = None
+    for _ in range(3):
+        fprime, pick = st.generation()
+        assert np.all((fprime > 0) & (fprime <= w.sum() + 1))
+        for i in range(p):  # a member without a legal result carries the fitness sum(w) + 1
+            f, c = oracle.wvcp_score(adj, w, k, st.P[i])
+            assert st.fP[i] == (f if c == 0 else w.sum() + 1)
+        assert np.array_equal(st.DP, oracle.distance_matrix(k, st.P, st.P))
+        bf, bc = oracle.wvcp_score(adj, w, k, st.best_col)
+        assert bc == 0 and bf == st.best_f[0] <= fprime.min()
+        if prev is not None:
+            assert st.best_f[0] <= prev
+        prev = st.best_f[0]
+        nbr = oracle.knn(st.DP, K)
+        for i in range(p):
+            j = nbr[i, pick[i]]
+            child = oracle.gpx(k, st.P[i], st.P[j], seed=6, child_id=i * K + pick[i], gen=st.gen - 1)
+            assert np.array_equal(child, st.SO[i])
