@@ -17,6 +17,7 @@ Other workloads (one JSON line each, single GPU):
   --workload scorer   one learned generation's scoring and training with the tensor-core roofline
   --workload wvcp_iterated  Algorithm 2 (iterated weighted search with the adaptive penalty)
   --workload popsweep best conflicts against population size at a fixed tabu budget
+  --workload wvcp_memetic  learned vs random GPX on the weighted problem, WVCP score at fixed wall time
   --workload population  distances, pool update, K nearest neighbours and GPX of one generation,
                          each kernel against its roofline
 """
@@ -70,7 +71,7 @@ def parse():
     ap.add_argument("--no-memetic", action="store_true",
                     help="leave out the learned-vs-random GPX comparison of the default run")
     ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp", "wvcp_iterated", "scorer", "popsweep",
-                                                   "population"],
+                                                   "population", "wvcp_memetic"],
                     help="tabu: the headline moves/s step; memetic: learned vs random GPX time-to-target; "
                          "multi: the uneven 64-graph batch in one captured persistent launch; wvcp: the "
                          "weighted tabu search; wvcp_iterated: its iterated form with the adaptive penalty "
@@ -91,6 +92,15 @@ def parse():
     ap.add_argument("--mem-seeds", type=int, default=10)
     ap.add_argument("--mem-max-gens", type=int, default=40)
     ap.add_argument("--mem-time-limit", type=float, default=120.0, help="seconds per run")
+    ap.add_argument("--wm-pop", type=int, default=8192)
+    ap.add_argument("--wm-iters", type=int, default=500, help="iterations of each search of the weighted local search")
+    ap.add_argument("--wm-ls", type=int, default=2,
+                    help="searches per generation (the paper's 10 x 10 |V| takes minutes per generation at "
+                         "population 8192)")
+    ap.add_argument("--wm-epochs", type=int, default=20)
+    ap.add_argument("--wm-seeds", type=int, default=3)
+    ap.add_argument("--wm-time", type=float, default=60.0, help="wall budget per run, seconds")
+    ap.add_argument("--wm-max-gens", type=int, default=400)
     ap.add_argument("--warps", type=int, default=0, help="warps per individual (0: the library's default)")
     ap.add_argument("--traffic-from", default=None,
                     help="write profiles/tabucol_C2_dram.json from this ncu CSV of one tabu launch and exit")
@@ -415,6 +425,103 @@ def memetic_summary(runs, wall_points=(0.5, 1.0, 1.5, 2.0)):
     lm, rm = res["learned"]["median_time_to_target_s"], res["random"]["median_time_to_target_s"]
     return {"value": lm, "random_gpx": rm, "summary": res,
             "learned_over_random": (lm / rm) if lm and rm else None}
+
+
+def run_wvcp_memetic(args):
+    """Learned-guided vs random-GPX memetic search on the weighted problem (Algorithm 1 with the
+    iterated feasible / infeasible tabu search of Algorithm 2 as the local search): G(1000, 0.5),
+    weights uniform in 1..100, population 8192, K = 32, N = 20 epochs (the WVCP parameter table),
+    k = the largest colour count of the seed's greedy initial population. Each run has a wall
+    budget; value = the learned mode's median best WVCP score at that budget, beside the random
+    mode's, their medians at intermediate wall times and the time each run needs to reach the
+    worst final best over all runs (a level every run reaches)."""
+    import torch
+
+    from paper_2109_05948_gb300 import build as libbuild
+    from paper_2109_05948_gb300 import dlmcol, inputs
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    ctx = dlmcol.Context(0)
+    n, pop = 1000, args.wm_pop
+    e = inputs.gnp(n, 0.5, 0)
+    w = inputs.weights(n, 0)
+    g = dlmcol.Graph(ctx, n, torch.from_numpy(e).cuda(), torch.from_numpy(w).cuda())
+    used = torch.empty(pop, dtype=torch.int32, device="cuda")
+    scratch = torch.empty((pop, n), dtype=torch.int16, device="cuda")
+    runs = {"learned": [], "random": []}
+    clocks = Clocks(0)
+    clocks.start()
+    for si in range(args.wm_seeds):
+        seed = 2000 + si
+        dlmcol.dlm_wvcp_greedy(ctx, g, pop, seed, 0, scratch, used)
+        ctx.sync()
+        k = int(used.max())
+        for mode in ("learned", "random"):
+            prm = dlmcol.MemeticParams(k=k, p=pop, K=32, iters=args.wm_iters, tenure=dlmcol.WVCP_TENURE,
+                                       use_scorer=1 if mode == "learned" else 0, epochs=args.wm_epochs, batch=100,
+                                       lr=1e-3, seed=seed, problem=1, max_ls=args.wm_ls)
+            mm = dlmcol.Memetic(ctx, g, prm)
+            dlmcol.dlm_memetic_profile(ctx, mm, True)
+            f0 = torch.empty(pop, dtype=torch.int64, device="cuda")
+            dlmcol.dlm_memetic_get(ctx, mm, 1, f0)
+            ctx.sync()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            traj, diag = [[0.0, int(f0.min())]], []
+            for gen in range(args.wm_max_gens):
+                best = dlmcol.dlm_memetic_step(ctx, mm)
+                el = time.perf_counter() - t0
+                traj.append([round(el, 3), int(best)])
+                st = dlmcol.dlm_memetic_stats(ctx, mm)
+                diag.append({key: (None if v != v else round(v, 4)) for key, v in st.items()})
+                t0 += time.perf_counter() - t0 - el  # the diagnostics' read is not search time
+                if el > args.wm_time:
+                    break
+            stages = dlmcol.dlm_memetic_profile(ctx, mm, False)
+            runs[mode].append({"seed": seed, "k": k, "generations": len(traj) - 1, "best": traj[-1][1],
+                               "trajectory": traj, "diagnostics": diag,
+                               "stage_ms_per_generation": {key: round(v, 2) for key, v in stages.items()
+                                                           if key != "generations"}})
+            print(json.dumps({"progress": mode, "seed": seed, "k": k, "generations": len(traj) - 1,
+                              "best": traj[-1][1], "stage_ms": runs[mode][-1]["stage_ms_per_generation"]}),
+                  file=sys.stderr, flush=True)
+            mm.close()
+    ck = clocks.stop()
+
+    def best_at(r, t):
+        return [b for (x, b) in r["trajectory"] if x <= t][-1]
+
+    level = max(r["best"] for rs in runs.values() for r in rs)
+    res = {}
+    for mode, rs in runs.items():
+        hit = [next(x for (x, b) in r["trajectory"] if b <= level) for r in rs]
+        res[mode] = {"median_best_at_budget": statistics.median(best_at(r, args.wm_time) for r in rs),
+                     "per_seed_best": [r["best"] for r in rs],
+                     "median_best_at_wall_s": {str(t): statistics.median(best_at(r, t) for r in rs)
+                                               for t in (args.wm_time / 4, args.wm_time / 2, 3 * args.wm_time / 4)},
+                     "time_to_level_s": hit, "median_time_to_level_s": statistics.median(hit),
+                     "median_generations": statistics.median(r["generations"] for r in rs),
+                     "median_offspring_f_mean_by_generation": [
+                         round(statistics.median(r["diagnostics"][i]["f_mean"] for r in rs
+                                                 if len(r["diagnostics"]) > i), 1)
+                         for i in range(max(len(r["diagnostics"]) for r in rs))],
+                     "median_prediction_pearson_by_generation": [
+                         (lambda xs: round(statistics.median(xs), 3) if xs else None)(
+                             [r["diagnostics"][i]["pred_pearson"] for r in rs if len(r["diagnostics"]) > i
+                              and r["diagnostics"][i]["pred_pearson"] is not None])
+                         for i in range(max(len(r["diagnostics"]) for r in rs))]}
+    out = {"metric": "WVCP score at fixed wall time, learned vs plain GPX", "workload": "wvcp_memetic",
+           "value": res["learned"]["median_best_at_budget"], "unit": "WVCP score", "higher_is_better": False,
+           "random_gpx": res["random"]["median_best_at_budget"], "level": level, "summary": res,
+           "config": {"workload": f"G(n={n}, p=0.5), weights 1..100, population {pop}, K=32 GPX candidates, "
+                                  f"k = greedy colours per seed, local search {args.wm_ls} x {args.wm_iters} "
+                                  f"iterations per generation (fscale 256, adaptive penalty), scorer 64-d "
+                                  f"embedding + 3 x 256 invariant layers, N={args.wm_epochs} epochs, b=100, "
+                                  f"lr=1e-3", "seeds": args.wm_seeds, "wall_budget_s": args.wm_time},
+           "clocks": ck, "data": "synthetic", "runs": runs}
+    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_multi(args):
@@ -943,6 +1050,9 @@ def main():
         return
     if args.workload == "population":
         run_population(args)
+        return
+    if args.workload == "wvcp_memetic":
+        run_wvcp_memetic(args)
         return
     import torch
     import torch.distributed as dist

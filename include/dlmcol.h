@@ -225,6 +225,14 @@ dlm_status dlm_gpx_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* pare
  * ------------------------------------------------------------------------------------------- */
 dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a, const int16_t* Y,
                               int32_t b, int16_t* D, int64_t ldD, int32_t upper);
+/* As dlm_distance_batch with the kernel chosen by the caller (same results; the paper has no
+ * counterpart: measurement and testing support). method 1: one warp per pair counts M in a k x k
+ * table and scans it for the row and column maxima, O(n + k^2) per pair; method 2: the CTA
+ * counts one pair at a time and takes the maxima with atomic maxima while counting, O(n) per
+ * pair; method 0: the library's choice (method 2 from k = 72 on). */
+dlm_status dlm_distance_batch_ex(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
+                                 const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper,
+                                 int32_t method);
 
 /* Distance-and-quality pool update (section "Population update"): the 2p candidates (index < p:
  * the population, >= p: the improved individuals) are visited by increasing fit, ties by lower

@@ -107,6 +107,116 @@ __global__ void __launch_bounds__(32 * kDistWarpsMax) k_distance(int n, int k, c
 }
 
 // ------------------------------------------------------------------------------------------------
+// Distances, O(n) per pair whatever k (large k, where the k^2 scan of k_distance dominates). One
+// CTA of kDistTeam threads holds X_i and ONE overlap table; the whole CTA handles one pair at a
+// time. Every vertex v increments M[a][b] (a = X_i(v), b = Y_j(v)); the counter's new value cnt
+// is offered to the running row maximum rmax[a] and column maximum cmax[b] with atomicMax. Counts
+// grow by one, so each successful raise lifts a maximum by cnt - (its previous value), and these
+// raises add up to the final maximum: their sum over the CTA is sum_a max_b M[a][b] (and the
+// column analogue) without a pass over the table. The vertices then clear the entries they
+// touched. Two CTA barriers per pair.
+// ------------------------------------------------------------------------------------------------
+constexpr int kDistTeam = 128;
+constexpr int kDistIncMinK = 72;  // from this k on, the automatic choice is k_distance_inc (measured crossover)
+
+template <int VPT>
+__global__ void __launch_bounds__(kDistTeam) k_distance_inc(int n, int k, const int16_t* X, int a, const int16_t* Y,
+                                                           int b, int16_t* D, int64_t ldD, int upper, int vec4,
+                                                           int32_t* status) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int i = blockIdx.y;
+  const int j0 = blockIdx.x * kDistCols;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rw = dist_row_words(k);
+  uint8_t* xi = smem;
+  const size_t xoff = (n + 15) & ~15;
+  uint32_t* M32 = (uint32_t*)(smem + xoff);
+  uint16_t* M16 = (uint16_t*)M32;
+  const int tw = dist_table_words(k);
+  uint32_t* rmax = M32 + tw;
+  uint32_t* cmax = rmax + k;
+  int* red = (int*)(cmax + k);  // [2 parities][kDistTeam / 32 warps][2]
+  for (int v = tid; v < n; v += kDistTeam) {
+    int c = X[(size_t)i * n + v];
+    if (c < 0 || c >= k) { raise_status(status, DLM_EINVAL); c = 0; }
+    xi[v] = (uint8_t)c;
+  }
+  for (int q = tid; q < tw + 2 * k; q += kDistTeam) M32[q] = 0u;
+  __syncthreads();
+  const bool check = blockIdx.y == 0;
+  int par = 0;
+  for (int jj = 0; jj < kDistCols; ++jj) {
+    const int j = j0 + jj;
+    if (j >= b) break;
+    if (upper && j <= i) continue;
+    const int16_t* y = Y + (size_t)j * n;
+    int qv[VPT];  // u16 index of the touched entry (a * 2 rw + b), or -1
+    int rs = 0, cs = 0;
+    auto touch = [&](int r, int v, int c2) {
+      if (check && (c2 < 0 || c2 >= k)) raise_status(status, DLM_EINVAL);
+      c2 = (int)min((unsigned)c2, (unsigned)(k - 1));
+      const int av = xi[v];
+      const int q = av * 2 * rw + c2;
+      qv[r] = q;
+      const int sh = 16 * (q & 1);
+      const uint32_t old = atomicAdd(M32 + (q >> 1), 1u << sh);
+      const uint32_t cnt = ((old >> sh) & 0xFFFFu) + 1u;
+      const uint32_t r0 = atomicMax(rmax + av, cnt);
+      if (r0 < cnt) rs += (int)(cnt - r0);
+      const uint32_t c0 = atomicMax(cmax + c2, cnt);
+      if (c0 < cnt) cs += (int)(cnt - c0);
+    };
+    if (vec4) {  // four consecutive vertices per thread and step: one 8-byte colour load
+      const uint2* y4 = reinterpret_cast<const uint2*>(y);
+#pragma unroll
+      for (int r4 = 0; r4 < VPT / 4; ++r4) {
+        const int t = tid + kDistTeam * r4;
+        if (t < (n >> 2)) {
+          const uint2 yy = y4[t];
+          touch(4 * r4, 4 * t, (int16_t)(yy.x & 0xFFFFu));
+          touch(4 * r4 + 1, 4 * t + 1, (int16_t)(yy.x >> 16));
+          touch(4 * r4 + 2, 4 * t + 2, (int16_t)(yy.y & 0xFFFFu));
+          touch(4 * r4 + 3, 4 * t + 3, (int16_t)(yy.y >> 16));
+        } else {
+          qv[4 * r4] = qv[4 * r4 + 1] = qv[4 * r4 + 2] = qv[4 * r4 + 3] = -1;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < VPT; ++r) {
+        const int v = tid + kDistTeam * r;
+        if (v < n) touch(r, v, y[v]);
+        else qv[r] = -1;
+      }
+    }
+    rs = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)rs);
+    cs = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)cs);
+    if (lane == 0) { red[(par * (kDistTeam / 32) + warp) * 2] = rs; red[(par * (kDistTeam / 32) + warp) * 2 + 1] = cs; }
+    __syncthreads();
+    // clear what this pair touched (duplicates store the same zero)
+#pragma unroll
+    for (int r = 0; r < VPT; ++r) {
+      const int q = qv[r];
+      if (q >= 0) {
+        M16[q] = 0;
+        rmax[q / (2 * rw)] = 0u;
+        cmax[q % (2 * rw)] = 0u;
+      }
+    }
+    if (tid == 0) {
+      int sr = 0, sc = 0;
+      for (int w = 0; w < kDistTeam / 32; ++w) {
+        sr += red[(par * (kDistTeam / 32) + w) * 2];
+        sc += red[(par * (kDistTeam / 32) + w) * 2 + 1];
+      }
+      D[(size_t)i * ldD + j] = (int16_t)(n - (sr < sc ? sr : sc));
+    }
+    par ^= 1;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Pool update. The greedy pass over the 2p candidates in (f, index) order admits a candidate when
 // no member admitted before it is within n/10. A candidate's fate depends only on the candidates
 // before it, so the pass runs in blocks of kPoolBlk candidates (in sorted order):
@@ -337,14 +447,27 @@ __global__ void __launch_bounds__(32 * kKnnWarps) k_knn(int p, const int16_t* D,
 
 using namespace dlm;
 
-extern "C" dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
-                                         const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper) {
+extern "C" dlm_status dlm_distance_batch_ex(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
+                                            const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper,
+                                            int32_t method) {
   if (!ctx) return DLM_EINVAL;
   if (n < 1 || n > 2048 || k < 1 || a < 0 || b < 0 || ldD < b) return fail(ctx, DLM_EINVAL, "distance: bad sizes");
   if (k > 255) return fail(ctx, DLM_EUNSUPPORTED, "distance: k must be <= 255");
+  if (method < 0 || method > 2) return fail(ctx, DLM_EINVAL, "distance: method must be 0, 1 or 2");
   if (a == 0 || b == 0) return DLM_OK;
   if (!X || !Y || !D) return fail(ctx, DLM_EINVAL, "distance: null pointer");
   if (a > 65535) return fail(ctx, DLM_EUNSUPPORTED, "distance: at most 65535 rows");
+  if (method == 0) method = k >= kDistIncMinK ? 2 : 1;
+  const int vec4 = (n % 4 == 0) && (((uintptr_t)Y & 7) == 0);
+  dim3 grid((b + kDistCols - 1) / kDistCols, a);
+  if (method == 2) {
+    const size_t smem = ((n + 15) & ~15) + (size_t)dist_table_words(k) * 4 + (size_t)2 * k * 4 + 2 * (kDistTeam / 32) * 8;
+    if (smem > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "distance: shared memory");
+    auto kern = n <= 4 * kDistTeam ? k_distance_inc<4> : n <= 8 * kDistTeam ? k_distance_inc<8> : k_distance_inc<16>;
+    DLM_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, kDistTeam, smem, ctx->stream>>>(n, k, X, a, Y, b, D, ldD, upper, vec4, ctx->d_status);
+    return launch_check(ctx, "k_distance_inc");
+  }
   // as many warps (overlap tables) as shared memory allows, up to 8
   const size_t per_warp = (size_t)dist_table_words(k) * 4;
   const size_t head = ((n + 15) & ~15) + 16;
@@ -353,10 +476,13 @@ extern "C" dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, con
   const size_t smem = head + warps * per_warp;
   if (smem > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "distance: shared memory");
   DLM_CUDA(ctx, cudaFuncSetAttribute(k_distance, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((b + kDistCols - 1) / kDistCols, a);
-  const int vec4 = (n % 4 == 0) && (((uintptr_t)Y & 7) == 0);
   k_distance<<<grid, 32 * warps, smem, ctx->stream>>>(n, k, X, a, Y, b, D, ldD, upper, vec4, ctx->d_status);
   return launch_check(ctx, "k_distance");
+}
+
+extern "C" dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
+                                         const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper) {
+  return dlm_distance_batch_ex(ctx, n, k, X, a, Y, b, D, ldD, upper, 0);
 }
 
 extern "C" dlm_status dlm_pool_update(dlm_ctx* ctx, int32_t p, int32_t n, const int64_t* fit, const int16_t* D,

@@ -72,6 +72,7 @@ _SIGS = {
     "dlm_tabucol_multi_plan_destroy": (None, [_P]),
     "dlm_gpx_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _P, _i32, _P, _u64, _u32]),
     "dlm_distance_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32]),
+    "dlm_distance_batch_ex": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32, _i32]),
     "dlm_pool_update": (_i32, [_P, _i32, _i32, _P, _P, _P]),
     "dlm_knn": (_i32, [_P, _i32, _P, _i32, _P]),
     "dlm_scorer_create": (_i32, [_P, _i32, _i32, _u64, _PP]),
@@ -291,9 +292,13 @@ def dlm_gpx_batch(ctx, n, k, parents, pop, pairs, child_id, m, children, seed, g
                                   seed, generation), "dlm_gpx_batch")
 
 
-def dlm_distance_batch(ctx, n, k, X, a, Y, b, D, ldD, upper=0):
-    ctx.check(lib().dlm_distance_batch(ctx.h, n, k, _ptr(X), a, _ptr(Y), b, _ptr(D), ldD, upper),
-              "dlm_distance_batch")
+def dlm_distance_batch(ctx, n, k, X, a, Y, b, D, ldD, upper=0, method=None):
+    if method is None:
+        ctx.check(lib().dlm_distance_batch(ctx.h, n, k, _ptr(X), a, _ptr(Y), b, _ptr(D), ldD, upper),
+                  "dlm_distance_batch")
+    else:
+        ctx.check(lib().dlm_distance_batch_ex(ctx.h, n, k, _ptr(X), a, _ptr(Y), b, _ptr(D), ldD, upper, method),
+                  "dlm_distance_batch_ex")
 
 
 def dlm_pool_update(ctx, p, n, fit, D, sel):

@@ -59,25 +59,32 @@ def test_gpx_default_child_ids_and_bad_pairs(ctx):
         ctx.sync()
 
 
-@pytest.mark.parametrize("n,k,a,b", [(257, 33, 40, 70), (1000, 48, 17, 130), (64, 128, 5, 9), (3, 2, 4, 4)])
-def test_distance_matches_oracle(ctx, n, k, a, b):
+@pytest.mark.parametrize("method", [None, 1, 2])
+@pytest.mark.parametrize("n,k,a,b", [(257, 33, 40, 70), (1000, 48, 17, 130), (64, 128, 5, 9), (3, 2, 4, 4),
+                                     (1000, 144, 9, 150), (2048, 255, 4, 70), (1001, 97, 6, 66)])
+def test_distance_matches_oracle(ctx, n, k, a, b, method):
     X = inputs.random_colorings(a, n, k, seed=a)
     Y = inputs.random_colorings(b, n, k, seed=b + 1)
     Y[0] = X[0]  # a zero distance
+    Y[1] = np.random.default_rng(b).permutation(k)[X[min(1, a - 1)]]  # a relabelling: zero distance
+    Y[2] = 0  # one class holding every vertex: a count of n
+    if b > 3:
+        Y[3] = X[0] % 2  # two classes
     ld = b + 3
     D = torch.full((a, ld), -1, dtype=torch.int16, device="cuda")
-    dlmcol.dlm_distance_batch(ctx, n, k, _cuda(X), a, _cuda(Y), b, D, ld, 0)
+    dlmcol.dlm_distance_batch(ctx, n, k, _cuda(X), a, _cuda(Y), b, D, ld, 0, method=method)
     ctx.sync()
     got = D.cpu().numpy()
     assert np.array_equal(got[:, :b], oracle.distance_matrix(k, X, Y))
     assert np.all(got[:, b:] == -1)
 
 
-def test_distance_upper_triangle(ctx):
-    n, k, a = 200, 12, 50
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("n,k,a", [(200, 12, 50), (300, 150, 70)])
+def test_distance_upper_triangle(ctx, n, k, a, method):
     X = inputs.random_colorings(a, n, k, seed=3)
     D = torch.full((a, a), -1, dtype=torch.int16, device="cuda")
-    dlmcol.dlm_distance_batch(ctx, n, k, _cuda(X), a, _cuda(X), a, D, a, 1)
+    dlmcol.dlm_distance_batch(ctx, n, k, _cuda(X), a, _cuda(X), a, D, a, 1, method=method)
     ctx.sync()
     got = D.cpu().numpy()
     ref = oracle.distance_matrix(k, X, X)
