@@ -353,12 +353,11 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
     const int dstar = __reduce_min_sync(FULL, rw.x);
     const int xl = (dstar != INT_MAX && rw.x == dstar) ? rw.y : 0;
     int xincl = xl;
-#pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {  // W <= 16
+    for (int d = 1; d < W; d <<= 1) {  // inclusive scan over lanes 0..W-1 (W <= 16, a power of two)
       const int t = __shfl_up_sync(FULL, xincl, d);
       if (lane >= d) xincl += t;
     }
-    const int T = __shfl_sync(FULL, xincl, 15);
+    const int T = __shfl_sync(FULL, xincl, W - 1);
     const uint32_t j = T > 0 ? below(r0, (uint32_t)T) : 0u;
     const unsigned dball = __ballot_sync(FULL, lane < W && xincl > (int)j);
     const int wdec = T > 0 ? __ffs(dball) - 1 : -1;
@@ -669,36 +668,39 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
         m = __funnelshift_r(lw, hw, sh) & kPerMask;
       }
       w_deg += __popc(m);
+      // branch-free over the thread's slots, so that their chains overlap: every slot loads and
+      // stores its two entries (a non-neighbour stores them back unchanged; rows belong to their
+      // owner thread, and old != nw) and its class words take the adjusted value only when the
+      // vertex is a neighbour
       unsigned go[PER], gn[PER];
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
-        go[q] = 0; gn[q] = 0;
-        if ((m >> q) & 1u) {
-          const uint16_t* gr = myrow(q);
-          go[q] = gr[old];
-          gn[q] = gr[nw];
-        }
+        const uint16_t* gr = myrow(q);
+        go[q] = gr[old];
+        gn[q] = gr[nw];
       }
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
-        if ((m >> q) & 1u) {
-          uint16_t* gr = myrow(q);
-          gr[old] = (uint16_t)(go[q] - 1u);
-          gr[nw] = (uint16_t)(gn[q] + 1u);
-          const bool fo = (go[q] & kFlag) != 0, fn = (gn[q] & kFlag) != 0;
-          const bool is_old = colq[q] == old, is_new = colq[q] == nw;
-          // the old colour's key drops by one, the new colour's rises by one (when neither is
-          // the vertex's own colour, whose gamma is g0)
-          uint32_t wo = fo ? recq[q].y : recq[q].x;
-          wo = cw_dec(wo, go[q] & kNone);
-          if (!is_old) { if (fo) recq[q].y = wo; else recq[q].x = wo; }
-          bool ok = true;
-          uint32_t wn = fn ? recq[q].y : recq[q].x;
-          wn = cw_inc(wn, gn[q] & kNone, ok);
-          if (!is_new) { if (fn) recq[q].y = wn; else recq[q].x = wn; }
-          g0q[q] = is_old ? (int)(go[q] & kNone) - 1 : (is_new ? (int)(gn[q] & kNone) + 1 : g0q[q]);
-          dmask |= (ok || is_new) ? 0u : (1u << q);
-        }
+        const unsigned nb = (m >> q) & 1u;
+        uint16_t* gr = myrow(q);
+        gr[old] = (uint16_t)(go[q] - nb);
+        gr[nw] = (uint16_t)(gn[q] + nb);
+        const bool fo = (go[q] & kFlag) != 0, fn = (gn[q] & kFlag) != 0;
+        const bool is_old = colq[q] == old, is_new = colq[q] == nw;
+        // the old colour's key drops by one, the new colour's rises by one (when neither is the
+        // vertex's own colour, whose gamma is g0)
+        const uint32_t wo = cw_dec(fo ? recq[q].y : recq[q].x, go[q] & kNone);
+        const bool ao = nb && !is_old;
+        recq[q].y = (ao && fo) ? wo : recq[q].y;
+        recq[q].x = (ao && !fo) ? wo : recq[q].x;
+        bool ok = true;
+        const uint32_t wn = cw_inc(fn ? recq[q].y : recq[q].x, gn[q] & kNone, ok);
+        const bool an = nb && !is_new;
+        recq[q].y = (an && fn) ? wn : recq[q].y;
+        recq[q].x = (an && !fn) ? wn : recq[q].x;
+        const int g0n = is_old ? (int)(go[q] & kNone) - 1 : (is_new ? (int)(gn[q] & kNone) + 1 : g0q[q]);
+        g0q[q] = nb ? g0n : g0q[q];
+        dmask |= (!nb || ok || is_new) ? 0u : (1u << q);
       }
     }
     // rows whose summary could not be adjusted, summarised again by the warp (lanes over colours)
