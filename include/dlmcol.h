@@ -229,10 +229,24 @@ dlm_status dlm_distance_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t*
  * counterpart: measurement and testing support). method 1: one warp per pair counts M in a k x k
  * table and scans it for the row and column maxima, O(n + k^2) per pair; method 2: the CTA
  * counts one pair at a time and takes the maxima with atomic maxima while counting, O(n) per
- * pair; method 0: the library's choice (method 2 from k = 72 on). */
+ * pair; method 3: every M as a block of one-hot matrix products on the tcgen05 tensor cores
+ * (bf16 0/1 operands, exact FP32 counts), row maxima from X . Y^T and column maxima from
+ * Y . X^T, 2 (a + b) kp n_64 + 8 a b B of context workspace (kp = 64 for k <= 64, 128 for
+ * k <= 128; n_64 = n rounded up to 64; k > 128: DLM_EUNSUPPORTED), O(n kp^2) per pair; method
+ * 0: the library's
+ * choice (method 2 from k = 72 on). */
 dlm_status dlm_distance_batch_ex(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
                                  const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper,
                                  int32_t method);
+/* Exact partition distance (section "Distance computation"): D = n - the largest total overlap
+ * sum_c M[c][pi(c)] over one-to-one matchings pi of the classes, i.e. the fewest vertices to
+ * recolour to turn one partition into the other up to colour names. One warp per pair: counting
+ * for M, then the Hungarian algorithm (shortest augmenting paths with integer potentials),
+ * O(n + k^3) per pair. Arguments as for dlm_distance_batch; k <= 128 (DLM_EUNSUPPORTED). The
+ * approximate D of dlm_distance_batch is a lower bound of this value and equal to it when the
+ * best-match map is one-to-one. */
+dlm_status dlm_distance_exact_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
+                                    const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper);
 
 /* Distance-and-quality pool update (section "Population update"): the 2p candidates (index < p:
  * the population, >= p: the improved individuals) are visited by increasing fit, ties by lower

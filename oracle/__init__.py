@@ -188,6 +188,24 @@ def distance_matrix(k, X, Y) -> np.ndarray:
     return out
 
 
+def distance_exact(k, A, B) -> int:
+    """Exact partition distance (section "Distance computation"): n minus the largest total
+    class overlap over one-to-one matchings of the k classes of A with those of B. The overlap
+    matrix is counted directly; the matching is a library assignment solver (scipy)."""
+    from scipy.optimize import linear_sum_assignment
+
+    A = np.asarray(A, np.int64)
+    B = np.asarray(B, np.int64)
+    M = np.zeros((k, k), np.int64)
+    np.add.at(M, (A, B), 1)
+    r, c = linear_sum_assignment(-M)
+    return int(len(A) - M[r, c].sum())
+
+
+def distance_exact_matrix(k, X, Y) -> np.ndarray:
+    return np.array([[distance_exact(k, x, y) for y in Y] for x in X], np.int16).reshape(len(X), len(Y))
+
+
 def pool_update(p, n, fit, D) -> np.ndarray:
     fit = _c(fit, np.int64)
     D = _c(D, np.int16)

@@ -217,6 +217,93 @@ __global__ void __launch_bounds__(kDistTeam) k_distance_inc(int n, int k, const 
 }
 
 // ------------------------------------------------------------------------------------------------
+// Exact partition distance (section "Distance computation": the distance is n minus the largest
+// total overlap over one-to-one matchings of the classes; the paper takes the approximation
+// above, this is the exact value it approximates). One warp per pair: the k x k overlap table by
+// counting, then the Hungarian algorithm (shortest augmenting paths with row and column
+// potentials) on the cost -M, the lanes sharing the column loops. Costs and potentials are
+// integers, so the result is exact.
+// ------------------------------------------------------------------------------------------------
+constexpr int kExactWarps = 4;
+
+__host__ __device__ inline size_t exact_warp_ints(int k) { return (size_t)k * k + 6 * (size_t)(k + 1); }
+
+__global__ void __launch_bounds__(32 * kExactWarps) k_distance_exact(int n, int k, const int16_t* X, int a,
+                                                                    const int16_t* Y, int b, int16_t* D, int64_t ldD,
+                                                                    int upper, int32_t* status) {
+  extern __shared__ __align__(16) int esm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* M = esm + (size_t)warp * exact_warp_ints(k);  // [k][k] overlaps
+  int* u = M + (size_t)k * k;                        // [k + 1] row potentials (1-based)
+  int* vp = u + (k + 1);                             // [k + 1] column potentials
+  int* pm = vp + (k + 1);                            // [k + 1] row matched to column j (0: none)
+  int* way = pm + (k + 1);                           // [k + 1] previous column on the path
+  int* minv = way + (k + 1);                         // [k + 1]
+  int* used = minv + (k + 1);                        // [k + 1]
+  const int64_t npairs = (int64_t)a * b;
+  const int nw = blockDim.x >> 5;
+  constexpr int INF = 0x3FFFFFFF;
+  for (int64_t pr = (int64_t)blockIdx.x * nw + warp; pr < npairs; pr += (int64_t)gridDim.x * nw) {
+    const int i = (int)(pr / b), j = (int)(pr % b);
+    if (upper && j <= i) continue;
+    for (int q = lane; q < k * k; q += 32) M[q] = 0;
+    __syncwarp();
+    const int16_t* x = X + (size_t)i * n;
+    const int16_t* y = Y + (size_t)j * n;
+    for (int v = lane; v < n; v += 32) {
+      int c1 = x[v], c2 = y[v];
+      if (c1 < 0 || c1 >= k || c2 < 0 || c2 >= k) { raise_status(status, DLM_EINVAL); c1 = 0; c2 = 0; }
+      atomicAdd(M + c1 * k + c2, 1);
+    }
+    for (int q = lane; q <= k; q += 32) { u[q] = 0; vp[q] = 0; pm[q] = 0; way[q] = 0; }
+    __syncwarp();
+    for (int r = 1; r <= k; ++r) {
+      if (lane == 0) pm[0] = r;
+      for (int q = lane; q <= k; q += 32) { minv[q] = INF; used[q] = 0; }
+      __syncwarp();
+      int j0 = 0;
+      for (int guard = 0; guard <= k + 1; ++guard) {
+        if (lane == 0) used[j0] = 1;
+        __syncwarp();
+        const int i0 = pm[j0];
+        // over the free columns: reduced cost of (i0, jj), the smallest minv and its column
+        int best = INF, bj = k + 1;
+        for (int jj = 1 + lane; jj <= k; jj += 32) {
+          if (!used[jj]) {
+            const int cur = -M[(i0 - 1) * k + (jj - 1)] - u[i0] - vp[jj];
+            if (cur < minv[jj]) { minv[jj] = cur; way[jj] = j0; }
+            if (minv[jj] < best) { best = minv[jj]; bj = jj; }
+          }
+        }
+        const int delta = (int)__reduce_min_sync(0xFFFFFFFFu, (unsigned)(best + 0x40000000)) - 0x40000000;
+        const int j1 = (int)__reduce_min_sync(0xFFFFFFFFu, best == delta ? (unsigned)bj : 0xFFFFFFFFu);
+        __syncwarp();
+        for (int jj = lane; jj <= k; jj += 32) {
+          if (used[jj]) { u[pm[jj]] += delta; vp[jj] -= delta; }
+          else minv[jj] -= delta;
+        }
+        __syncwarp();
+        j0 = j1;
+        if (j0 > k || pm[j0] == 0) break;
+      }
+      if (lane == 0 && j0 <= k) {  // augment along the path
+        for (int guard = 0; guard <= k + 1 && j0 != 0; ++guard) {
+          const int j1 = way[j0];
+          pm[j0] = pm[j1];
+          j0 = j1;
+        }
+      }
+      __syncwarp();
+    }
+    int s = 0;
+    for (int jj = 1 + lane; jj <= k; jj += 32) s += pm[jj] > 0 ? M[(pm[jj] - 1) * k + (jj - 1)] : 0;
+    s = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)s);
+    if (lane == 0) D[(size_t)i * ldD + j] = (int16_t)(n - s);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Pool update. The greedy pass over the 2p candidates in (f, index) order admits a candidate when
 // no member admitted before it is within n/10. A candidate's fate depends only on the candidates
 // before it, so the pass runs in blocks of kPoolBlk candidates (in sorted order):
@@ -445,7 +532,31 @@ __global__ void __launch_bounds__(32 * kKnnWarps) k_knn(int p, const int16_t* D,
 
 }  // namespace dlm
 
+namespace dlm {
+dlm_status distance_tc(dlm_ctx* ctx, int n, int k, const int16_t* X, int a, const int16_t* Y, int b, int16_t* D,
+                       int64_t ldD, int upper);
+}
+
 using namespace dlm;
+
+extern "C" dlm_status dlm_distance_exact_batch(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
+                                               const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper) {
+  if (!ctx) return DLM_EINVAL;
+  if (n < 1 || n > 2048 || k < 1 || a < 0 || b < 0 || ldD < b) return fail(ctx, DLM_EINVAL, "distance_exact: bad sizes");
+  if (k > 128) return fail(ctx, DLM_EUNSUPPORTED, "distance_exact: k must be <= 128");
+  if (a == 0 || b == 0) return DLM_OK;
+  if (!X || !Y || !D) return fail(ctx, DLM_EINVAL, "distance_exact: null pointer");
+  const size_t per_warp = exact_warp_ints(k) * 4;
+  int warps = kExactWarps;
+  while (warps > 1 && (size_t)warps * per_warp > ctx->smem_optin) --warps;
+  const size_t smem = (size_t)warps * per_warp;
+  if (smem > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "distance_exact: shared memory");
+  DLM_CUDA(ctx, cudaFuncSetAttribute(k_distance_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t npairs = (int64_t)a * b;
+  const int grid = (int)std::min<int64_t>((npairs + warps - 1) / warps, (int64_t)ctx->num_sms * 16);
+  k_distance_exact<<<grid, 32 * warps, smem, ctx->stream>>>(n, k, X, a, Y, b, D, ldD, upper, ctx->d_status);
+  return launch_check(ctx, "k_distance_exact");
+}
 
 extern "C" dlm_status dlm_distance_batch_ex(dlm_ctx* ctx, int32_t n, int32_t k, const int16_t* X, int32_t a,
                                             const int16_t* Y, int32_t b, int16_t* D, int64_t ldD, int32_t upper,
@@ -453,11 +564,12 @@ extern "C" dlm_status dlm_distance_batch_ex(dlm_ctx* ctx, int32_t n, int32_t k, 
   if (!ctx) return DLM_EINVAL;
   if (n < 1 || n > 2048 || k < 1 || a < 0 || b < 0 || ldD < b) return fail(ctx, DLM_EINVAL, "distance: bad sizes");
   if (k > 255) return fail(ctx, DLM_EUNSUPPORTED, "distance: k must be <= 255");
-  if (method < 0 || method > 2) return fail(ctx, DLM_EINVAL, "distance: method must be 0, 1 or 2");
+  if (method < 0 || method > 3) return fail(ctx, DLM_EINVAL, "distance: method must be 0, 1, 2 or 3");
   if (a == 0 || b == 0) return DLM_OK;
   if (!X || !Y || !D) return fail(ctx, DLM_EINVAL, "distance: null pointer");
   if (a > 65535) return fail(ctx, DLM_EUNSUPPORTED, "distance: at most 65535 rows");
   if (method == 0) method = k >= kDistIncMinK ? 2 : 1;
+  if (method == 3) return distance_tc(ctx, n, k, X, a, Y, b, D, ldD, upper);
   const int vec4 = (n % 4 == 0) && (((uintptr_t)Y & 7) == 0);
   dim3 grid((b + kDistCols - 1) / kDistCols, a);
   if (method == 2) {

@@ -73,6 +73,7 @@ _SIGS = {
     "dlm_gpx_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _P, _i32, _P, _u64, _u32]),
     "dlm_distance_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32]),
     "dlm_distance_batch_ex": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32, _i32]),
+    "dlm_distance_exact_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32]),
     "dlm_pool_update": (_i32, [_P, _i32, _i32, _P, _P, _P]),
     "dlm_knn": (_i32, [_P, _i32, _P, _i32, _P]),
     "dlm_scorer_create": (_i32, [_P, _i32, _i32, _u64, _PP]),
@@ -290,6 +291,11 @@ def dlm_tabucol_autotune(ctx, g, k, pop, iters):
 def dlm_gpx_batch(ctx, n, k, parents, pop, pairs, child_id, m, children, seed, generation):
     ctx.check(lib().dlm_gpx_batch(ctx.h, n, k, _ptr(parents), pop, _ptr(pairs), _ptr(child_id), m, _ptr(children),
                                   seed, generation), "dlm_gpx_batch")
+
+
+def dlm_distance_exact_batch(ctx, n, k, X, a, Y, b, D, ldD, upper=0):
+    ctx.check(lib().dlm_distance_exact_batch(ctx.h, n, k, _ptr(X), a, _ptr(Y), b, _ptr(D), ldD, upper),
+              "dlm_distance_exact_batch")
 
 
 def dlm_distance_batch(ctx, n, k, X, a, Y, b, D, ldD, upper=0, method=None):

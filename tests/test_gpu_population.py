@@ -59,10 +59,16 @@ def test_gpx_default_child_ids_and_bad_pairs(ctx):
         ctx.sync()
 
 
-@pytest.mark.parametrize("method", [None, 1, 2])
+@pytest.mark.parametrize("method", [None, 1, 2, 3])
 @pytest.mark.parametrize("n,k,a,b", [(257, 33, 40, 70), (1000, 48, 17, 130), (64, 128, 5, 9), (3, 2, 4, 4),
                                      (1000, 144, 9, 150), (2048, 255, 4, 70), (1001, 97, 6, 66)])
 def test_distance_matches_oracle(ctx, n, k, a, b, method):
+    if method == 3 and k > 128:  # the tensor-core path holds a pair's classes in one 128-row tile
+        D = torch.zeros((a, b), dtype=torch.int16, device="cuda")
+        X = _cuda(inputs.random_colorings(a, n, k, seed=a))
+        with pytest.raises(dlmcol.DlmError):
+            dlmcol.dlm_distance_batch(ctx, n, k, X, a, X, a, D, b, 0, method=3)
+        return
     X = inputs.random_colorings(a, n, k, seed=a)
     Y = inputs.random_colorings(b, n, k, seed=b + 1)
     Y[0] = X[0]  # a zero distance
@@ -79,8 +85,8 @@ def test_distance_matches_oracle(ctx, n, k, a, b, method):
     assert np.all(got[:, b:] == -1)
 
 
-@pytest.mark.parametrize("method", [1, 2])
-@pytest.mark.parametrize("n,k,a", [(200, 12, 50), (300, 150, 70)])
+@pytest.mark.parametrize("method", [1, 2, 3])
+@pytest.mark.parametrize("n,k,a", [(200, 12, 50), (300, 120, 70)])
 def test_distance_upper_triangle(ctx, n, k, a, method):
     X = inputs.random_colorings(a, n, k, seed=3)
     D = torch.full((a, a), -1, dtype=torch.int16, device="cuda")
@@ -91,6 +97,44 @@ def test_distance_upper_triangle(ctx, n, k, a, method):
     iu = np.triu_indices(a, 1)
     assert np.array_equal(got[iu], ref[iu])
     assert np.all(got[np.tril_indices(a)] == -1)
+
+
+@pytest.mark.parametrize("n,k,a,b", [(60, 5, 7, 9), (257, 33, 6, 11), (1000, 48, 3, 20), (300, 128, 2, 5),
+                                     (130, 70, 4, 4), (5, 2, 3, 3)])
+def test_distance_exact_matches_oracle(ctx, n, k, a, b):
+    """The exact (Hungarian) distance equals the oracle's assignment-solver value on random pairs,
+    relabellings (0), partners recoloured in a few vertices and partners far from one matching."""
+    X = inputs.random_colorings(a, n, k, seed=a + 100)
+    Y = inputs.random_colorings(b, n, k, seed=b + 200)
+    Y[0] = np.random.default_rng(1).permutation(k)[X[0]]
+    Y[1] = X[min(1, a - 1)].copy()
+    Y[1][: min(n, 7)] = (Y[1][: min(n, 7)] + 1) % k
+    Y[2] = 0
+    ld = b + 1
+    D = torch.full((a, ld), -1, dtype=torch.int16, device="cuda")
+    dlmcol.dlm_distance_exact_batch(ctx, n, k, _cuda(X), a, _cuda(Y), b, D, ld, 0)
+    ctx.sync()
+    got = D.cpu().numpy()
+    ref = oracle.distance_exact_matrix(k, X, Y)
+    assert np.array_equal(got[:, :b], ref)
+    assert np.all(got[:, b:] == -1)
+    # the approximation is a lower bound of the exact value
+    assert np.all(oracle.distance_matrix(k, X, Y) <= ref)
+
+
+def test_distance_exact_upper_and_limits(ctx):
+    n, k, a = 200, 20, 12
+    X = inputs.random_colorings(a, n, k, seed=5)
+    D = torch.full((a, a), -1, dtype=torch.int16, device="cuda")
+    dlmcol.dlm_distance_exact_batch(ctx, n, k, _cuda(X), a, _cuda(X), a, D, a, 1)
+    ctx.sync()
+    got = D.cpu().numpy()
+    ref = oracle.distance_exact_matrix(k, X, X)
+    iu = np.triu_indices(a, 1)
+    assert np.array_equal(got[iu], ref[iu])
+    assert np.all(got[np.tril_indices(a)] == -1)
+    with pytest.raises(dlmcol.DlmError):
+        dlmcol.dlm_distance_exact_batch(ctx, n, 129, _cuda(X), a, _cuda(X), a, D, a, 0)
 
 
 def _random_pool_case(p, n, seed, spread):

@@ -81,6 +81,35 @@ def _exact_distance(A, B, k):
     return len(A) - int(M[r, c].sum())
 
 
+@pytest.mark.parametrize("n,k,seed", [(12, 3, 0), (20, 4, 1), (30, 5, 2), (40, 6, 3), (9, 6, 4)])
+def test_distance_exact_against_brute_force_matchings(n, k, seed):
+    """oracle.distance_exact is n minus the best one-to-one class matching: checked against every
+    permutation of the k classes, with the overlaps counted vertex by vertex."""
+    import itertools
+
+    A, B = inputs.random_colorings(2, n, k, seed=seed)
+    best = 0
+    for perm in itertools.permutations(range(k)):
+        best = max(best, sum(1 for v in range(n) if perm[A[v]] == B[v]))
+    assert oracle.distance_exact(k, A, B) == n - best
+    assert oracle.distance_exact(k, A, B) == oracle.distance_exact(k, B, A)
+    assert oracle.distance(k, A, B) <= oracle.distance_exact(k, A, B)
+
+
+def test_distance_exact_relabel_and_recolour():
+    n, k = 150, 9
+    A = inputs.random_colorings(1, n, k, seed=7)[0]
+    sigma = np.random.default_rng(3).permutation(k)
+    B = sigma[A].astype(np.int16)
+    assert oracle.distance_exact(k, A, B) == 0
+    # recolouring m vertices of a partition with classes of at least 2 m + 1 vertices costs exactly m
+    A = np.repeat(np.arange(k), n // k + 1)[:n].astype(np.int16)
+    B = A.copy()
+    idx = np.random.default_rng(4).choice(n, 5, replace=False)
+    B[idx] = (B[idx] + 1) % k
+    assert oracle.distance_exact(k, A, B) == 5
+
+
 def test_distance_relabel_is_zero_and_symmetric():
     n, k = 100, 8
     A, B = inputs.random_colorings(2, n, k, seed=6)
