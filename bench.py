@@ -18,6 +18,7 @@ Other workloads (one JSON line each, single GPU):
   --workload wvcp_iterated  Algorithm 2 (iterated weighted search with the adaptive penalty)
   --workload popsweep best conflicts against population size at a fixed tabu budget
   --workload wvcp_memetic  learned vs random GPX on the weighted problem, WVCP score at fixed wall time
+  --workload deepnet  the paper-size invariant network (batch normalisation): scoring and training
   --workload population  distances, pool update, K nearest neighbours and GPX of one generation,
                          each kernel against its roofline
 """
@@ -71,7 +72,7 @@ def parse():
     ap.add_argument("--no-memetic", action="store_true",
                     help="leave out the learned-vs-random GPX comparison of the default run")
     ap.add_argument("--workload", default="tabu", choices=["tabu", "memetic", "multi", "wvcp", "wvcp_iterated", "scorer", "popsweep",
-                                                   "population", "wvcp_memetic"],
+                                                   "population", "wvcp_memetic", "deepnet"],
                     help="tabu: the headline moves/s step; memetic: learned vs random GPX time-to-target; "
                          "multi: the uneven 64-graph batch in one captured persistent launch; wvcp: the "
                          "weighted tabu search; wvcp_iterated: its iterated form with the adaptive penalty "
@@ -101,6 +102,10 @@ def parse():
     ap.add_argument("--wm-seeds", type=int, default=3)
     ap.add_argument("--wm-time", type=float, default=60.0, help="wall budget per run, seconds")
     ap.add_argument("--wm-max-gens", type=int, default=400)
+    ap.add_argument("--dn-problem", default="col", choices=["col", "wvcp"])
+    ap.add_argument("--dn-cands", type=int, default=1024)
+    ap.add_argument("--dn-samples", type=int, default=500)
+    ap.add_argument("--dn-bf16", action="store_true", help="bf16 operands alone (no hi + lo split)")
     ap.add_argument("--warps", type=int, default=0, help="warps per individual (0: the library's default)")
     ap.add_argument("--traffic-from", default=None,
                     help="write profiles/tabucol_C2_dram.json from this ncu CSV of one tabu launch and exit")
@@ -522,6 +527,83 @@ def run_wvcp_memetic(args):
            "clocks": ck, "data": "synthetic", "runs": runs}
     print(json.dumps(out), flush=True)
     return out
+
+
+def run_deepnet(args):
+    """The paper-size invariant network with invariant batch normalisation (section
+    "Implementation and parameter setting"): hidden widths 10|V|, 5|V|, 2|V| x 5, |V|, |V|//2 for
+    k-COL (n = 1000, k = 48) or 5|V|, 2|V|, |V|, |V|//2 for the WVCP (n = 1000, k = 145). Times
+    the scoring of a batch of candidates (evaluation mode) and online training (Adam, b = 100)
+    with CUDA events; value = candidates scored per second."""
+    import numpy as np
+    import torch
+
+    from paper_2109_05948_gb300 import build as libbuild
+    from paper_2109_05948_gb300 import dlmcol, inputs
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    ctx = dlmcol.Context(0)
+    n = 1000
+    k = 48 if args.dn_problem == "col" else 145
+    widths = ([10 * n, 5 * n, 2 * n, 2 * n, 2 * n, 2 * n, 2 * n, n, n // 2] if args.dn_problem == "col"
+              else [5 * n, 2 * n, n, n // 2])
+    net = dlmcol.DeepNet(ctx, n, k, widths, seed=SEED)
+    net.set_precision(0 if args.dn_bf16 else 1)
+    C, P, B = args.dn_cands, args.dn_samples, 100
+    cols = torch.from_numpy(inputs.random_colorings(C, n, k, seed=1)).cuda()
+    fvals = torch.from_numpy(np.random.default_rng(0).integers(0, 1000, size=P).astype(np.int64)).cuda()
+    out = torch.empty(C, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        return a, b
+
+    for _ in range(args.warmup):
+        net.forward(cols, C, 0, out)
+        net.train(cols[:P], fvals, P, 1, B, 1e-3, SEED, 0)
+    ctx.sync()
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev_s, ev_t = [], []
+    for st in range(args.steps):
+        ev_s.append(timed(lambda: net.forward(cols, C, 0, out)))
+        ev_t.append(timed(lambda: net.train(cols[:P], fvals, P, 1, B, 1e-3, SEED, st + 1)))
+    torch.cuda.synchronize()
+    ctx.sync()
+    ck = clocks.stop()
+    ms_s = sum(a.elapsed_time(b) for a, b in ev_s) / args.steps
+    ms_t = sum(a.elapsed_time(b) for a, b in ev_t) / args.steps
+    h = widths
+    pad = [64 * ((x + 63) // 64) for x in h]
+    # algorithmic tensor work per scored candidate: every layer l >= 1 multiplies the k class rows
+    # and the colour average by Lambda_l and Gamma_l (2 h_l-1 h_l flops each per row); a training
+    # sample adds the input-gradient and weight-gradient products (three times the forward)
+    fwd = sum(2.0 * (k + 1) * h[l - 1] * h[l] for l in range(1, len(h)))
+    fwd_exec = sum(2.0 * (k + 1) * pad[l - 1] * pad[l] for l in range(1, len(h))) * (1 if args.dn_bf16 else 3)
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    src = "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)" if peaks.get("bf16_tflops_sustained") else "of fallback"
+    ach_s = fwd * C / (ms_s / 1e3) / 1e12
+    ach_t = 3 * fwd * P / (ms_t / 1e3) / 1e12
+    roof = {"bound": "tensor", "achieved": ach_s, "peak": peak, "unit": "TFLOP/s", "frac": ach_s / peak,
+            "peak_source": src, "traffic": None, "kernel": "gemm_kernel (all layer products of the scoring pass)",
+            "executed_tflops": fwd_exec * C / (ms_s / 1e3) / 1e12,
+            "training_achieved_tflops": ach_t, "training_frac": ach_t / peak}
+    res = {"metric": f"paper-size invariant network: candidates scored per second ({args.dn_problem})",
+           "workload": "deepnet", "value": C / (ms_s / 1e3), "unit": "candidates/s", "higher_is_better": True,
+           "training_samples_per_s": P / (ms_t / 1e3), "ms_scoring": ms_s, "ms_training_epoch": ms_t,
+           "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 (hi + lo split)" if not args.dn_bf16 else "bf16",
+           "data": "synthetic", "clocks": ck, "roofline": roof, "nparams": net.nparams,
+           "config": {"workload": f"n={n}, k={k}, hidden widths {widths}, invariant batch normalisation, "
+                                  f"{C} random colourings scored, one epoch of Adam over {P} samples (b={B})"}}
+    print(json.dumps(res), flush=True)
+    net.close()
 
 
 def run_multi(args):
@@ -1053,6 +1135,9 @@ def main():
         return
     if args.workload == "wvcp_memetic":
         run_wvcp_memetic(args)
+        return
+    if args.workload == "deepnet":
+        run_deepnet(args)
         return
     import torch
     import torch.distributed as dist

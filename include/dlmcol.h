@@ -310,6 +310,55 @@ dlm_status dlm_scorer_save(dlm_ctx* ctx, dlm_scorer* s, void* host);
 dlm_status dlm_scorer_load(dlm_ctx* ctx, dlm_scorer* s, const void* host);
 
 /* ---------------------------------------------------------------------------------------------
+ * Paper-size offspring scorer (section "Deep neural network training" with its invariant batch
+ * normalisation; section "Implementation and parameter setting": hidden widths 10|V|, 5|V|,
+ * 2|V| x 5, |V|, |V|//2 for k-COL, 5|V|, 2|V|, |V|, |V|//2 for the WVCP), any depth and widths.
+ * Layer 0 sums the rows E[v] over each class (+ beta_0); layer l >= 1 computes
+ * Z = H Lambda_l + rho(H) Gamma_l + beta_l on the tcgen05 tensor cores; every layer normalises
+ * each feature over the batch and the k classes (training: batch mean and biased variance,
+ * running estimates updated with momentum 0.1, the variance unbiased; evaluation: the running
+ * estimates), y = x^ gamma + mu, then LeakyReLU_0.2; the output is the mean over the classes of
+ * a linear head. eps = 1e-5.
+ * Flat parameter order (float32): E[n][h0], b0[h0], g0[h0], mu0[h0]; for l = 1 .. nh-1:
+ * Lambda_l[h_l-1][h_l], Gamma_l[h_l-1][h_l], beta_l[h_l], g_l[h_l], mu_l[h_l]; then w_head[h_nh-1],
+ * b_head[1]. Statistics (float32): per layer, running mean[h_l] then running variance[h_l].
+ * Initial parameters: weights and biases uniform in +-1/sqrt(fan_in) from Philox(a = index,
+ * b = 1, c = 0, tag = NNINIT), gamma = 1, mu = 0; running mean 0, variance 1.
+ * GEMM operands are bf16 hi + lo pairs by default (dlm_deepnet_set_precision: split = 0 for
+ * bf16 alone). Limits: n <= 2048, k <= 256, 1..16 hidden layers of 1..16384 features; a
+ * training batch (or a training-mode forward) holds at most 8192 candidates. Buffers grow with
+ * the largest batch (evaluation: chunks of about 4 GB of activations).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct dlm_deepnet dlm_deepnet;
+/* widths: host [nh] int32, the hidden widths h_0 .. h_nh-1. Waits for its initialisation. */
+dlm_status dlm_deepnet_create(dlm_ctx* ctx, int32_t n, int32_t k, int32_t nh, const int32_t* widths, uint64_t seed,
+                              dlm_deepnet** out);
+void dlm_deepnet_destroy(dlm_deepnet* net);
+int64_t dlm_deepnet_nparams(const dlm_deepnet* net);
+int64_t dlm_deepnet_nstats(const dlm_deepnet* net);
+/* which = 0: parameters (set also resets the Adam state), 1: running statistics; device float32. */
+dlm_status dlm_deepnet_get(dlm_ctx* ctx, dlm_deepnet* net, int32_t which, float* dst);
+dlm_status dlm_deepnet_set(dlm_ctx* ctx, dlm_deepnet* net, int32_t which, const float* src);
+dlm_status dlm_deepnet_set_precision(dlm_ctx* ctx, dlm_deepnet* net, int32_t split);
+/* Scores of c colourings (col device [c][n] int16, colours 0..k-1; out device [c] float32).
+ * train = 0: evaluation (running statistics); train = 1: one training-mode batch (its own
+ * statistics, running estimates updated), c <= 8192. */
+dlm_status dlm_deepnet_forward(dlm_ctx* ctx, dlm_deepnet* net, const int16_t* col, int32_t c, int32_t train,
+                               float* out);
+/* Training-mode forward (running estimates updated) and backward of B samples: mean squared
+ * error against y (device [B] float32), its gradient (grad device [nparams] or NULL), the
+ * predictions (out device [B] or NULL) and the loss (loss device [1] or NULL). */
+dlm_status dlm_deepnet_loss_grad(dlm_ctx* ctx, dlm_deepnet* net, const int16_t* col, const float* y, int32_t B,
+                                 float* grad, float* out, float* loss);
+/* One Adam step (lr, betas 0.9 / 0.999, eps 1e-8) with a given gradient (device [nparams]). */
+dlm_status dlm_deepnet_adam_step(dlm_ctx* ctx, dlm_deepnet* net, const float* grad, float lr);
+/* Online training as dlm_scorer_train: targets fvals (device [p] int64) standardised by their
+ * mean and population standard deviation, N epochs of Adam over batches of b in the epoch order
+ * (samples sorted by Philox(a = i, b = epoch, c = generation, tag = BATCH).r0, ties by i). */
+dlm_status dlm_deepnet_train(dlm_ctx* ctx, dlm_deepnet* net, const int16_t* cols, const int64_t* fvals, int32_t p,
+                             int32_t epochs, int32_t b, float lr, uint64_t seed, uint32_t generation);
+
+/* ---------------------------------------------------------------------------------------------
  * Memetic loop (Algorithm 1). dlm_memetic_step runs one generation: the local search of every
  * offspring (TabuCol for k-COL, the iterated tabu search for the WVCP), best-so-far update,
  * scorer training (use_scorer), distances between P and P' and within P', pool update, K nearest

@@ -74,6 +74,17 @@ _SIGS = {
     "dlm_distance_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32]),
     "dlm_distance_batch_ex": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32, _i32]),
     "dlm_distance_exact_batch": (_i32, [_P, _i32, _i32, _P, _i32, _P, _i32, _P, _i64, _i32]),
+    "dlm_deepnet_create": (_i32, [_P, _i32, _i32, _i32, _P, _u64, _P]),
+    "dlm_deepnet_destroy": (None, [_P]),
+    "dlm_deepnet_nparams": (_i64, [_P]),
+    "dlm_deepnet_nstats": (_i64, [_P]),
+    "dlm_deepnet_get": (_i32, [_P, _P, _i32, _P]),
+    "dlm_deepnet_set": (_i32, [_P, _P, _i32, _P]),
+    "dlm_deepnet_set_precision": (_i32, [_P, _P, _i32]),
+    "dlm_deepnet_forward": (_i32, [_P, _P, _P, _i32, _i32, _P]),
+    "dlm_deepnet_loss_grad": (_i32, [_P, _P, _P, _P, _i32, _P, _P, _P]),
+    "dlm_deepnet_adam_step": (_i32, [_P, _P, _P, ctypes.c_float]),
+    "dlm_deepnet_train": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32, ctypes.c_float, _u64, _u32]),
     "dlm_pool_update": (_i32, [_P, _i32, _i32, _P, _P, _P]),
     "dlm_knn": (_i32, [_P, _i32, _P, _i32, _P]),
     "dlm_scorer_create": (_i32, [_P, _i32, _i32, _u64, _PP]),
@@ -358,6 +369,53 @@ def dlm_scorer_loss_grad(ctx, s, col, y, B, grad, out, loss):
 def dlm_scorer_train(ctx, s, cols, fvals, p, epochs, b, lr, seed, generation):
     ctx.check(lib().dlm_scorer_train(ctx.h, s.h, _ptr(cols), _ptr(fvals), p, epochs, b, lr, seed, generation),
               "dlm_scorer_train")
+
+
+class DeepNet:
+    """The paper-size invariant network with invariant batch normalisation (dlm_deepnet_*)."""
+
+    def __init__(self, ctx: Context, n, k, widths, seed=0):
+        arr = (ctypes.c_int32 * len(widths))(*[int(w) for w in widths])
+        h = ctypes.c_void_p()
+        ctx.check(lib().dlm_deepnet_create(ctx.h, n, k, len(widths), arr, seed, ctypes.byref(h)), "dlm_deepnet_create")
+        self.h, self.ctx = h, ctx
+        self.nparams = int(lib().dlm_deepnet_nparams(h))
+        self.nstats = int(lib().dlm_deepnet_nstats(h))
+
+    def get(self, which, dst):
+        self.ctx.check(lib().dlm_deepnet_get(self.ctx.h, self.h, which, _ptr(dst)), "dlm_deepnet_get")
+
+    def set(self, which, src):
+        self.ctx.check(lib().dlm_deepnet_set(self.ctx.h, self.h, which, _ptr(src)), "dlm_deepnet_set")
+
+    def set_precision(self, split):
+        self.ctx.check(lib().dlm_deepnet_set_precision(self.ctx.h, self.h, split), "dlm_deepnet_set_precision")
+
+    def forward(self, col, c, train, out):
+        self.ctx.check(lib().dlm_deepnet_forward(self.ctx.h, self.h, _ptr(col), c, train, _ptr(out)),
+                       "dlm_deepnet_forward")
+
+    def loss_grad(self, col, y, B, grad=None, out=None, loss=None):
+        self.ctx.check(lib().dlm_deepnet_loss_grad(self.ctx.h, self.h, _ptr(col), _ptr(y), B, _ptr(grad), _ptr(out),
+                                                   _ptr(loss)), "dlm_deepnet_loss_grad")
+
+    def adam_step(self, grad, lr):
+        self.ctx.check(lib().dlm_deepnet_adam_step(self.ctx.h, self.h, _ptr(grad), lr), "dlm_deepnet_adam_step")
+
+    def train(self, cols, fvals, p, epochs, b, lr, seed, generation):
+        self.ctx.check(lib().dlm_deepnet_train(self.ctx.h, self.h, _ptr(cols), _ptr(fvals), p, epochs, b, lr, seed,
+                                               generation), "dlm_deepnet_train")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dlm_deepnet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Memetic:
