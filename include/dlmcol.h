@@ -357,6 +357,11 @@ dlm_status dlm_deepnet_adam_step(dlm_ctx* ctx, dlm_deepnet* net, const float* gr
  * (samples sorted by Philox(a = i, b = epoch, c = generation, tag = BATCH).r0, ties by i). */
 dlm_status dlm_deepnet_train(dlm_ctx* ctx, dlm_deepnet* net, const int16_t* cols, const int64_t* fvals, int32_t p,
                              int32_t epochs, int32_t b, float lr, uint64_t seed, uint32_t generation);
+/* State to or from caller-owned host memory of dlm_deepnet_state_bytes bytes: parameters, Adam
+ * moments, running statistics (float32 each) and the Adam step counter (int64); both wait. */
+int64_t dlm_deepnet_state_bytes(const dlm_deepnet* net);
+dlm_status dlm_deepnet_save(dlm_ctx* ctx, dlm_deepnet* net, void* host);
+dlm_status dlm_deepnet_load(dlm_ctx* ctx, dlm_deepnet* net, const void* host);
 
 /* ---------------------------------------------------------------------------------------------
  * Memetic loop (Algorithm 1). dlm_memetic_step runs one generation: the local search of every
@@ -371,7 +376,11 @@ typedef struct {
   int32_t k, p, K;
   int64_t iters;          /* tabu iterations per generation (paper: 128 |V|) */
   dlm_tenure tenure;      /* paper: {9, 6, 10} */
-  int32_t use_scorer;     /* 1 = learned selection, 0 = random GPX */
+  int32_t use_scorer;     /* 1 = learned selection with the 64-d + 3 x 256 scorer (dlm_scorer_*),
+                             2 = learned selection with the paper-size network with invariant
+                             batch normalisation (dlm_deepnet_*; hidden widths 10|V|, 5|V|, 2|V| x 5,
+                             |V|, |V|//2 for k-COL, 5|V|, 2|V|, |V|, |V|//2 for the WVCP),
+                             0 = random GPX */
   int32_t epochs, batch;  /* paper: 5, 100 (k-COL), 20, 100 (WVCP) */
   float lr;               /* paper: 1e-3 */
   uint64_t seed;
@@ -394,7 +403,8 @@ dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* best_f_host)
  * 2 = D(P,P) [p][p] int16, 3 = offspring S^O [p][n] int16, 4 = best colouring [n] int16,
  * 5 = f(S'_i) of the last generation [p] int64, 6 = chosen candidate j [p] int32,
  * 7 = candidate scores of the last generation [p][K] float32 (use_scorer only),
- * 8 = scorer parameters [nparams] float32. */
+ * 8 = scorer parameters [nparams] float32 (of the paper-size network with use_scorer = 2),
+ * 9 = its running statistics [nstats] float32 (use_scorer = 2 only). */
 dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, void* dst);
 
 /* Diagnostics of the last generation (section "Analysis of the contributions of deep learning":

@@ -960,3 +960,36 @@ extern "C" dlm_status dlm_deepnet_adam_step(dlm_ctx* ctx, dlm_deepnet* s, const 
   DLM_CUDA(ctx, cudaMemcpyAsync(s->grad, grad, (size_t)s->np * 4, cudaMemcpyDeviceToDevice, ctx->stream));
   return adam_step(ctx, s, lr);
 }
+
+// state for checkpoints: parameters, Adam moments, running statistics (float32) and the Adam
+// step counter (int64)
+extern "C" int64_t dlm_deepnet_state_bytes(const dlm_deepnet* s) {
+  return s ? (int64_t)((3 * s->np + s->nst) * 4 + 8) : 0;
+}
+
+extern "C" dlm_status dlm_deepnet_save(dlm_ctx* ctx, dlm_deepnet* s, void* host) {
+  if (!ctx || !s || !host) return fail(ctx, DLM_EINVAL, "deepnet_save: null argument");
+  uint8_t* h = (uint8_t*)host;
+  const size_t P = (size_t)s->np * 4;
+  DLM_CUDA(ctx, cudaMemcpyAsync(h, s->theta, P, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + P, s->am, P, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + 2 * P, s->av, P, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(h + 3 * P, s->stats, (size_t)s->nst * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  memcpy(h + 3 * P + (size_t)s->nst * 4, &s->t, 8);
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_deepnet_load(dlm_ctx* ctx, dlm_deepnet* s, const void* host) {
+  if (!ctx || !s || !host) return fail(ctx, DLM_EINVAL, "deepnet_load: null argument");
+  const uint8_t* h = (const uint8_t*)host;
+  const size_t P = (size_t)s->np * 4;
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->theta, h, P, cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->am, h + P, P, cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->av, h + 2 * P, P, cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->stats, h + 3 * P, (size_t)s->nst * 4, cudaMemcpyHostToDevice, ctx->stream));
+  memcpy(&s->t, h + 3 * P + (size_t)s->nst * 4, 8);
+  DLM_TRY(convert_weights(ctx, s));
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return DLM_OK;
+}

@@ -33,6 +33,7 @@ struct dlm_memetic {
   int64_t wsum = 0, phi0 = 0, phi_last = 0;
   int64_t* h_best = nullptr;  // pinned
   dlm_scorer* scorer = nullptr;
+  dlm_deepnet* deep = nullptr;  // use_scorer = 2: the paper-size network
   // the scorer trains on a side stream while the distances and the pool update run
   cudaStream_t side = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_trained = nullptr;
@@ -298,6 +299,7 @@ extern "C" void dlm_memetic_destroy(dlm_memetic* mm) {
   if (mm->h_best) cudaFreeHost(mm->h_best);
   if (mm->h_stat) cudaFreeHost(mm->h_stat);
   if (mm->scorer) dlm_scorer_destroy(mm->scorer);
+  if (mm->deep) dlm_deepnet_destroy(mm->deep);
   for (auto e : mm->pev) if (e) cudaEventDestroy(e);
   for (auto e : mm->tev) if (e) cudaEventDestroy(e);
   if (mm->ev_ready) cudaEventDestroy(mm->ev_ready);
@@ -318,6 +320,7 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
   if (p > 8192) return fail(ctx, DLM_EUNSUPPORTED, "memetic_create: p must be <= 8192");
   if (wvcp && !g->d_weight) return fail(ctx, DLM_EINVAL, "memetic_create: WVCP needs a graph with vertex weights");
   if (wvcp && (prm->max_ls < 1 || prm->max_ls > 16)) return fail(ctx, DLM_EINVAL, "memetic_create: max_ls must be in 1..16");
+  if (prm->use_scorer < 0 || prm->use_scorer > 2) return fail(ctx, DLM_EINVAL, "memetic_create: use_scorer must be 0, 1 or 2");
   if (prm->use_scorer && (prm->epochs < 0 || prm->batch < 1)) return fail(ctx, DLM_EINVAL, "memetic_create: bad training parameters");
   dlm_memetic* mm = new dlm_memetic();
   mm->g = g;
@@ -337,11 +340,17 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
   if (st == DLM_OK && cudaMallocHost(&mm->h_best, sizeof(int64_t)) != cudaSuccess) st = fail(ctx, DLM_ENOMEM, "pinned");
   if (st == DLM_OK && cudaMallocHost(&mm->h_stat, 16 * sizeof(double)) != cudaSuccess) st = fail(ctx, DLM_ENOMEM, "pinned");
   if (st == DLM_OK) st = cuda_check(ctx, cudaMemsetAsync(mm->dstat, 0, 16 * sizeof(double), ctx->stream), "memset");
-  if (st == DLM_OK && prm->use_scorer) st = dlm_scorer_create(ctx, n, k, prm->seed, &mm->scorer);
+  if (st == DLM_OK && prm->use_scorer == 1) st = dlm_scorer_create(ctx, n, k, prm->seed, &mm->scorer);
   // the selection takes the best-scored of each individual's K children: bf16 activations (two
   // MMA passes) keep every group's best equal to the FP64 one's in the parity tests, at a third
   // of the split-activation scoring time
-  if (st == DLM_OK && prm->use_scorer) st = dlm_scorer_set_scoring_precision(ctx, mm->scorer, 0);
+  if (st == DLM_OK && prm->use_scorer == 1) st = dlm_scorer_set_scoring_precision(ctx, mm->scorer, 0);
+  if (st == DLM_OK && prm->use_scorer == 2) {  // hidden widths of section "Implementation and parameter setting"
+    std::vector<int32_t> w = wvcp ? std::vector<int32_t>{5 * n, 2 * n, n, std::max(1, n / 2)}
+                                  : std::vector<int32_t>{10 * n, 5 * n, 2 * n, 2 * n, 2 * n, 2 * n, 2 * n, n,
+                                                         std::max(1, n / 2)};
+    st = dlm_deepnet_create(ctx, n, k, (int32_t)w.size(), w.data(), prm->seed, &mm->deep);
+  }
   int prio_least = 0, prio_greatest = 0;  // the training's short kernels take SMs as the distance blocks drain
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   if (st == DLM_OK && prm->use_scorer &&
@@ -450,7 +459,10 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     DLM_CUDA(ctx, cudaStreamWaitEvent(mm->side, mm->ev_ready, 0));
     ctx->stream = mm->side;
     if (mm->prof) cudaEventRecord(mm->tev[0], mm->side);
-    const dlm_status ts = dlm_scorer_train(ctx, mm->scorer, mm->SO, mm->fSp, p, q.epochs, q.batch, q.lr, q.seed, mm->gen);
+    const dlm_status ts = mm->deep ? dlm_deepnet_train(ctx, mm->deep, mm->SO, mm->fSp, p, q.epochs, q.batch, q.lr,
+                                                       q.seed, mm->gen)
+                                   : dlm_scorer_train(ctx, mm->scorer, mm->SO, mm->fSp, p, q.epochs, q.batch, q.lr,
+                                                      q.seed, mm->gen);
     if (mm->prof) cudaEventRecord(mm->tev[1], mm->side);
     ctx->stream = s;
     DLM_TRY(ts);
@@ -490,7 +502,8 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     DLM_TRY(launch_check(ctx, "k_pairs_all"));
     DLM_TRY(dlm_gpx_batch(ctx, n, k, mm->P, p, mm->pairs, mm->cid, p * K, mm->kids, q.seed, mm->gen));
     DLM_CUDA(ctx, cudaStreamWaitEvent(s, mm->ev_trained, 0));
-    DLM_TRY(dlm_score_offspring(ctx, mm->scorer, mm->kids, p * K, mm->scores));
+    if (mm->deep) DLM_TRY(dlm_deepnet_forward(ctx, mm->deep, mm->kids, p * K, 0, mm->scores));
+    else DLM_TRY(dlm_score_offspring(ctx, mm->scorer, mm->kids, p * K, mm->scores));
     k_select_best<<<p, 128, 0, s>>>(p, K, n, mm->scores, mm->kids, mm->SO, mm->pick, mm->pred);
     DLM_TRY(launch_check(ctx, "k_select_best"));
   } else {
@@ -541,8 +554,11 @@ extern "C" dlm_status dlm_memetic_get(dlm_ctx* ctx, dlm_memetic* mm, int32_t whi
     case 6: src = mm->pick; bytes = (size_t)p * 4; break;
     case 7: if (!mm->prm.use_scorer) return fail(ctx, DLM_EINVAL, "memetic_get: no scores without the scorer");
             src = mm->scores; bytes = (size_t)p * K * 4; break;
-    case 8: if (!mm->scorer) return fail(ctx, DLM_EINVAL, "memetic_get: no scorer");
+    case 8: if (mm->deep) return dlm_deepnet_get(ctx, mm->deep, 0, (float*)dst);
+            if (!mm->scorer) return fail(ctx, DLM_EINVAL, "memetic_get: no scorer");
             return dlm_scorer_get_params(ctx, mm->scorer, (float*)dst);
+    case 9: if (!mm->deep) return fail(ctx, DLM_EINVAL, "memetic_get: no paper-size network");
+            return dlm_deepnet_get(ctx, mm->deep, 1, (float*)dst);
     default: return fail(ctx, DLM_EINVAL, "memetic_get: unknown array");
   }
   DLM_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -594,7 +610,9 @@ CkptLayout ckpt_layout(const dlm_memetic* mm) {
   L.SO = o; o += a16(p * n * 2);
   L.best_f = o; o += 16;
   L.best_col = o; o += a16(n * 2);
-  L.scorer = o; o += a16(mm->scorer ? (size_t)dlm_scorer_state_bytes(mm->scorer) : 0);
+  L.scorer = o;
+  o += a16(mm->scorer ? (size_t)dlm_scorer_state_bytes(mm->scorer)
+                      : (mm->deep ? (size_t)dlm_deepnet_state_bytes(mm->deep) : 0));
   L.total = o;
   return L;
 }
@@ -613,7 +631,7 @@ extern "C" dlm_status dlm_memetic_save(dlm_ctx* ctx, dlm_memetic* mm, void* host
   memcpy(H.magic, kMagic, 8);
   H.n = mm->n; H.k = mm->prm.k; H.p = mm->prm.p; H.K = mm->prm.K; H.use_scorer = mm->prm.use_scorer;
   H.gen = mm->gen;
-  H.scorer_bytes = mm->scorer ? dlm_scorer_state_bytes(mm->scorer) : 0;
+  H.scorer_bytes = mm->scorer ? dlm_scorer_state_bytes(mm->scorer) : (mm->deep ? dlm_deepnet_state_bytes(mm->deep) : 0);
   H.total = (int64_t)L.total;
   H.fingerprint = mm->fingerprint;
   cudaStream_t s = ctx->stream;
@@ -625,6 +643,7 @@ extern "C" dlm_status dlm_memetic_save(dlm_ctx* ctx, dlm_memetic* mm, void* host
   DLM_CUDA(ctx, cudaMemcpyAsync(h + L.best_col, mm->best_col, n * 2, cudaMemcpyDeviceToHost, s));
   DLM_CUDA(ctx, cudaStreamSynchronize(s));
   if (mm->scorer) DLM_TRY(dlm_scorer_save(ctx, mm->scorer, h + L.scorer));
+  if (mm->deep) DLM_TRY(dlm_deepnet_save(ctx, mm->deep, h + L.scorer));
   memcpy(h, &H, sizeof(H));
   return DLM_OK;
 }
@@ -638,7 +657,8 @@ extern "C" dlm_status dlm_memetic_load(dlm_ctx* ctx, dlm_memetic* mm, const void
   if (memcmp(H.magic, kMagic, 8) != 0) return fail(ctx, DLM_EINVAL, "memetic_load: not a memetic checkpoint");
   if (H.n != mm->n || H.k != mm->prm.k || H.p != mm->prm.p || H.K != mm->prm.K ||
       H.use_scorer != mm->prm.use_scorer || H.total != (int64_t)L.total ||
-      H.scorer_bytes != (mm->scorer ? dlm_scorer_state_bytes(mm->scorer) : 0))
+      H.scorer_bytes != (mm->scorer ? dlm_scorer_state_bytes(mm->scorer)
+                                    : (mm->deep ? dlm_deepnet_state_bytes(mm->deep) : 0)))
     return fail(ctx, DLM_EINVAL, "memetic_load: checkpoint of another configuration");
   if (H.fingerprint != mm->fingerprint)
     return fail(ctx, DLM_EINVAL, "memetic_load: checkpoint of another graph or parameter set (seed, budget, tenure, "
@@ -653,6 +673,7 @@ extern "C" dlm_status dlm_memetic_load(dlm_ctx* ctx, dlm_memetic* mm, const void
   DLM_CUDA(ctx, cudaMemcpyAsync(mm->best_col, h + L.best_col, n * 2, cudaMemcpyHostToDevice, s));
   DLM_CUDA(ctx, cudaStreamSynchronize(s));
   if (mm->scorer) DLM_TRY(dlm_scorer_load(ctx, mm->scorer, h + L.scorer));
+  if (mm->deep) DLM_TRY(dlm_deepnet_load(ctx, mm->deep, h + L.scorer));
   mm->gen = H.gen;
   return DLM_OK;
 }

@@ -85,6 +85,9 @@ _SIGS = {
     "dlm_deepnet_loss_grad": (_i32, [_P, _P, _P, _P, _i32, _P, _P, _P]),
     "dlm_deepnet_adam_step": (_i32, [_P, _P, _P, ctypes.c_float]),
     "dlm_deepnet_train": (_i32, [_P, _P, _P, _P, _i32, _i32, _i32, ctypes.c_float, _u64, _u32]),
+    "dlm_deepnet_state_bytes": (_i64, [_P]),
+    "dlm_deepnet_save": (_i32, [_P, _P, _P]),
+    "dlm_deepnet_load": (_i32, [_P, _P, _P]),
     "dlm_pool_update": (_i32, [_P, _i32, _i32, _P, _P, _P]),
     "dlm_knn": (_i32, [_P, _i32, _P, _i32, _P]),
     "dlm_scorer_create": (_i32, [_P, _i32, _i32, _u64, _PP]),

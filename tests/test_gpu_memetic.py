@@ -331,3 +331,49 @@ def test_wvcp_memetic_rejects_bad_parameters(ctx):
     bad = dict(base, max_ls=0)
     with pytest.raises(RuntimeError):
         dlmcol.Memetic(ctx, g, dlmcol.MemeticParams(k=20, **bad))
+
+
+def test_memetic_paper_size_network_selection(ctx):
+    """use_scorer = 2 (the paper-size network with invariant batch normalisation, widths 10|V| ...
+    |V|//2): generations bit-exact with the oracle selecting on the GPU's scores; the scores equal
+    the FP64 network with the GPU's trained parameters and running statistics; a checkpoint resumes
+    bit-identically."""
+    from oracle import deepnet as dn
+
+    n, k, p, K, iters, seed = 40, 5, 12, 3, 120, 5
+    e, _ = inputs.planted(n, k, 0.4, seed=seed)
+    adj = inputs.edges_to_adj(n, e)
+    g = device_graph(ctx, n, e)
+    prm = dlmcol.MemeticParams(k=k, p=p, K=K, iters=iters, tenure=dlmcol.COL_TENURE, use_scorer=2, epochs=2, batch=5,
+                               lr=1e-3, seed=seed)
+    mm = dlmcol.Memetic(ctx, g, prm)
+    st = oracle.MemeticState(adj, k, p, K, seed=seed, iters=iters, use_scorer=1, epochs=1, batch=5)
+    dims = dn.DeepDims(n, dn.paper_widths(n, "col"))
+    for gen in range(2):
+        dlmcol.dlm_memetic_step(ctx, mm)
+        scores = _get(ctx, mm, 7, (p, K), torch.float32)
+        assert np.all(np.isfinite(scores))
+        fprime, pick = st.generation(ext_scores=scores)
+        assert np.array_equal(_get(ctx, mm, 6, (p,), torch.int32), pick)
+        assert np.array_equal(_get(ctx, mm, 5, (p,), torch.int64), fprime)
+        _compare(ctx, mm, st, p, n, K, gen)
+    th = _get(ctx, mm, 8, (dims.nparams(),), torch.float32).astype(np.float64)
+    stats = _get(ctx, mm, 9, (dims.nstats(),), torch.float32).astype(np.float64)
+    P = _get(ctx, mm, 0, (p, n), torch.int16)
+    nbr = oracle.knn(_get(ctx, mm, 2, (p, p), torch.int16), K)
+    kids = np.stack([oracle.gpx(k, P[i], P[nbr[i, j]], seed, i * K + j, 1) for i in range(p) for j in range(K)])
+    ref = dn.forward(dims, k, th, kids, False, stats.copy()).reshape(p, K)
+    bh = dims.view(th)["bh"][0]
+    cg, cr = scores - bh, ref - bh
+    floor = np.sqrt(np.mean(cr * cr))
+    assert np.max(np.abs(cg - cr) / np.maximum(np.abs(cr), floor)) <= 1e-2
+    # checkpoint and resume
+    blob = dlmcol.dlm_memetic_save(ctx, mm)
+    other = dlmcol.Memetic(ctx, g, prm)
+    dlmcol.dlm_memetic_load(ctx, other, blob)
+    fa, fb = dlmcol.dlm_memetic_step(ctx, mm), dlmcol.dlm_memetic_step(ctx, other)
+    assert fa == fb
+    for w, shp, dt in [(0, (p, n), torch.int16), (3, (p, n), torch.int16), (7, (p, K), torch.float32)]:
+        assert np.array_equal(_get(ctx, mm, w, shp, dt), _get(ctx, other, w, shp, dt))
+    mm.close()
+    other.close()
