@@ -88,6 +88,11 @@ struct dlm_ctx {
   std::vector<GemmRec> gemm_recs;
   // cancellation flag polled by the long-running search kernels (dlm_set_cancel_flag)
   const int32_t* cancel = nullptr;
+  // streams and events for launches that run side by side (the uneven batch: one launch per
+  // graph), created on first use
+  static constexpr int kPool = 16;
+  cudaStream_t pool[kPool] = {};
+  cudaEvent_t pool_ev[kPool + 1] = {};
 };
 
 struct dlm_graph {

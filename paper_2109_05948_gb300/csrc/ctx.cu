@@ -160,6 +160,8 @@ void dlm_destroy(dlm_ctx* ctx) {
   for (auto& r : ctx->gemm_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   cudaFree(ctx->d_status);
   if (ctx->ws) cudaFree(ctx->ws);
+  for (auto s : ctx->pool) if (s) cudaStreamDestroy(s);
+  for (auto e : ctx->pool_ev) if (e) cudaEventDestroy(e);
   delete ctx;
 }
 

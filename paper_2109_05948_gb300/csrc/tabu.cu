@@ -839,6 +839,84 @@ extern "C" dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int
   return DLM_OK;
 }
 
+// ---- the uneven batch on the grouped kernel: one launch per graph, side by side on the context's
+// stream pool, the graphs with the most work per individual first; individual j of graph gi draws
+// the Philox id ind_base + (individuals of the graphs before gi) + j, as in the one-launch path ----
+struct MultiGroupPlan {
+  std::vector<int> order;       // graphs with individuals, by decreasing n k iters
+  std::vector<GroupPlan> plans;
+  std::vector<size_t> far_off;  // byte offset of each graph's far lists
+  std::vector<uint32_t> ind0;   // Philox id of each graph's first individual
+  size_t far_total = 0;
+};
+
+static bool multi_group_plan(dlm_ctx* ctx, int n_graphs, const dlm_graph* const* graphs, const int32_t* k,
+                             const int32_t* pop, const int64_t* iters, dlm_tenure tenure, uint32_t ind_base,
+                             MultiGroupPlan* out) {
+  MultiGroupPlan M;
+  M.plans.resize(n_graphs);
+  M.far_off.assign(n_graphs, 0);
+  M.ind0.resize(n_graphs);
+  uint32_t id = ind_base;
+  for (int gi = 0; gi < n_graphs; ++gi) {
+    M.ind0[gi] = id;
+    id += (uint32_t)pop[gi];
+    if (pop[gi] == 0) continue;
+    const dlm_graph* g = graphs[gi];
+    if (!group_plan(g->n, k[gi], g->words, default_group_warps(g->n), ctx->smem_optin, pop[gi], ctx->num_sms, 0,
+                    &M.plans[gi]))
+      return false;
+    const uint64_t tt_max =
+        (uint64_t)tenure.L_max + ((uint64_t)tenure.alpha_num * (uint64_t)g->m) / (uint64_t)tenure.alpha_den;
+    if ((uint64_t)iters[gi] + tt_max + 2 >= (1ull << 32)) return false;
+    M.far_off[gi] = M.far_total;
+    M.far_total += align16(group_far_bytes(ctx, g, k[gi], pop[gi], iters[gi], tenure, M.plans[gi]));
+    M.order.push_back(gi);
+  }
+  std::stable_sort(M.order.begin(), M.order.end(), [&](int a, int b) {
+    return (double)graphs[a]->n * k[a] * iters[a] > (double)graphs[b]->n * k[b] * iters[b];
+  });
+  *out = std::move(M);
+  return true;
+}
+
+static dlm_status ensure_pool(dlm_ctx* ctx) {
+  for (int i = 0; i < dlm_ctx::kPool; ++i)
+    if (!ctx->pool[i]) DLM_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->pool[i], cudaStreamNonBlocking));
+  for (int i = 0; i <= dlm_ctx::kPool; ++i)
+    if (!ctx->pool_ev[i]) DLM_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pool_ev[i], cudaEventDisableTiming));
+  return DLM_OK;
+}
+
+// forks from `base` to the pool, launches every graph, joins back into `base`; far: device memory
+// of M.far_total bytes
+static dlm_status multi_group_launch(dlm_ctx* ctx, cudaStream_t base, const MultiGroupPlan& M,
+                                     const dlm_graph* const* graphs, const int32_t* k, const int32_t* pop,
+                                     int16_t* const* col, int64_t* const* best_f, int64_t* const* moves,
+                                     const int64_t* iters, dlm_tenure tenure, uint64_t seed, uint32_t generation,
+                                     uint8_t* far) {
+  if (M.order.empty()) return DLM_OK;
+  DLM_TRY(ensure_pool(ctx));
+  const int ns = std::min<int>(dlm_ctx::kPool, (int)M.order.size());
+  DLM_CUDA(ctx, cudaEventRecord(ctx->pool_ev[dlm_ctx::kPool], base));
+  for (int i = 0; i < ns; ++i) DLM_CUDA(ctx, cudaStreamWaitEvent(ctx->pool[i], ctx->pool_ev[dlm_ctx::kPool], 0));
+  const cudaStream_t saved = ctx->stream;
+  dlm_status st = DLM_OK;
+  for (size_t t = 0; t < M.order.size() && st == DLM_OK; ++t) {
+    const int gi = M.order[t];
+    ctx->stream = ctx->pool[t % ns];
+    st = tabucol_group_launch(ctx, graphs[gi], k[gi], pop[gi], col[gi], best_f[gi], moves ? moves[gi] : nullptr,
+                              iters[gi], tenure, seed, generation, M.ind0[gi], M.plans[gi], nullptr, nullptr,
+                              far ? far + M.far_off[gi] : nullptr);
+  }
+  ctx->stream = saved;
+  for (int i = 0; i < ns; ++i) {  // join, also after an error, so that no pool stream stays forked
+    DLM_CUDA(ctx, cudaEventRecord(ctx->pool_ev[i], ctx->pool[i]));
+    DLM_CUDA(ctx, cudaStreamWaitEvent(base, ctx->pool_ev[i], 0));
+  }
+  return st;
+}
+
 extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dlm_graph* const* graphs,
                                         const int32_t* k, const int32_t* pop, int16_t* const* col,
                                         int64_t* const* best_f, int64_t* const* moves, const int64_t* iters,
@@ -857,6 +935,16 @@ extern "C" dlm_status dlm_tabucol_multi(dlm_ctx* ctx, int32_t n_graphs, const dl
     if (w == 0) w = default_warps(graphs[gi]->n, k[gi]);
     warps = w > warps ? w : warps;
     njobs += (size_t)pop[gi];
+  }
+  if (njobs == 0) return DLM_OK;
+  {  // every graph's state fits the grouped kernel: one launch per graph, side by side
+    MultiGroupPlan M;
+    if (multi_group_plan(ctx, n_graphs, graphs, k, pop, iters, tenure, ind_base, &M)) {
+      uint8_t* far = nullptr;
+      if (M.far_total) DLM_TRY(ctx_workspace(ctx, M.far_total, (void**)&far));
+      return multi_group_launch(ctx, ctx->stream, M, graphs, k, pop, col, best_f, moves, iters, tenure, seed,
+                                generation, far);
+    }
   }
   size_t slab_stride = 0;  // graphs whose state exceeds shared memory keep their last rows in a slab
   for (int gi = 0; gi < n_graphs; ++gi) {
@@ -1035,6 +1123,7 @@ struct dlm_multi_plan {
   cudaGraphExec_t exec = nullptr;
   int warps = 0, grid = 0;
   size_t njobs = 0;
+  bool grouped = false;  // one grouped launch per graph (branches of the captured graph)
 };
 
 extern "C" void dlm_tabucol_multi_plan_destroy(dlm_multi_plan* p) {
@@ -1071,6 +1160,38 @@ extern "C" dlm_status dlm_tabucol_multi_plan_create(dlm_ctx* ctx, int32_t n_grap
     if (L.rs < graphs[gi]->n) slab_stride = std::max(slab_stride, tabu_slab_elems(graphs[gi]->n, k[gi], L.rs));
   }
   if (njobs == 0) return fail(ctx, DLM_EINVAL, "tabucol_multi_plan: empty batch");
+  {  // the grouped kernel when every graph fits it: the per-graph launches captured as branches
+    MultiGroupPlan M;
+    if (multi_group_plan(ctx, n_graphs, graphs, k, pop, iters, tenure, ind_base, &M)) {
+      dlm_multi_plan* p = new dlm_multi_plan();
+      p->grouped = true;
+      p->njobs = njobs;
+      auto bail = [&](dlm_status s, const std::string& m) { dlm_tabucol_multi_plan_destroy(p); return fail(ctx, s, m); };
+      if (M.far_total && cudaMalloc(&p->mem, M.far_total) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(DLM_ENOMEM, "tabucol_multi_plan: allocation failed");
+      }
+      DLM_TRY(ensure_pool(ctx));
+      cudaStream_t cs = nullptr;
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return bail(DLM_ECUDA, "stream");
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      dlm_status ls = DLM_OK;
+      if (e == cudaSuccess)
+        ls = multi_group_launch(ctx, cs, M, graphs, k, pop, col, best_f, moves, iters, tenure, seed, generation, p->mem);
+      const cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+      cudaStreamDestroy(cs);
+      if (e != cudaSuccess || e2 != cudaSuccess || ls != DLM_OK) {
+        cudaGetLastError();
+        return bail(ls != DLM_OK ? ls : DLM_ECUDA, "tabucol_multi_plan: capture");
+      }
+      if (cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(DLM_ECUDA, "tabucol_multi_plan: instantiate");
+      }
+      *out = p;
+      return DLM_OK;
+    }
+  }
   std::vector<MultiJob> jobs;
   jobs.reserve(njobs);
   uint32_t id = ind_base;

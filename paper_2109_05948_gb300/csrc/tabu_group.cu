@@ -857,25 +857,41 @@ int group_grid(dlm_ctx* ctx, const GroupPlan& P, int pop) {
 }
 
 template <int PER>
-static dlm_status launch_per(dlm_ctx* ctx, const GroupArgs& a, const GroupPlan& P) {
+static dlm_status launch_per(dlm_ctx* ctx, const GroupArgs& a, const GroupPlan& P, uint2* far_mem) {
   const int grid = group_grid(ctx, P, a.pop);
   GroupArgs b = a;
-  // far list: tabu entries whose tenure does not fit the ring. A pair holds at most one live
-  // entry, at most one entry is made per iteration and a tenure never exceeds L_max + alpha |E|,
-  // so n (k - 1) + 1 entries, the budget + 1 and L_max + alpha |E| + 1 each bound what one search
-  // keeps there at once.
   if (b.far_cap > 0) {
-    void* ws = nullptr;
-    DLM_TRY(ctx_workspace(ctx, (size_t)grid * P.G * (size_t)b.far_cap * sizeof(uint2), &ws));
-    b.far = (uint2*)ws;
+    if (far_mem) {
+      b.far = far_mem;
+    } else {
+      void* ws = nullptr;
+      DLM_TRY(ctx_workspace(ctx, (size_t)grid * P.G * (size_t)b.far_cap * sizeof(uint2), &ws));
+      b.far = (uint2*)ws;
+    }
   }
   return P.bsm ? launch_one<PER, true>(ctx, b, grid, P.smem) : launch_one<PER, false>(ctx, b, grid, P.smem);
+}
+
+// far list: tabu entries whose tenure does not fit the ring. A pair holds at most one live entry,
+// at most one entry is made per iteration and a tenure never exceeds L_max + alpha |E|, so
+// n (k - 1) + 1 entries, the budget + 1 and L_max + alpha |E| + 1 each bound what one search
+// keeps there at once; 0 when every tenure fits the ring
+int64_t group_far_cap(const dlm_graph* g, int32_t k, int64_t iters, dlm_tenure tenure, const GroupPlan& P) {
+  const uint64_t tt_max = (uint64_t)tenure.L_max + ((uint64_t)tenure.alpha_num * (uint64_t)g->m) / tenure.alpha_den;
+  if (tt_max < (uint64_t)P.R) return 0;
+  int64_t far_cap = std::min<int64_t>((int64_t)g->n * (k - 1) + 1, iters + 1);
+  return std::min<int64_t>(far_cap, (int64_t)tt_max + 1);
+}
+
+size_t group_far_bytes(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters, dlm_tenure tenure,
+                       const GroupPlan& P) {
+  return (size_t)group_grid(ctx, P, pop) * P.G * (size_t)group_far_cap(g, k, iters, tenure, P) * sizeof(uint2);
 }
 
 dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                 int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                                 uint32_t generation, uint32_t ind_base, const GroupPlan& P, int32_t* trace,
-                                int64_t* work) {
+                                int64_t* work, void* far_mem) {
   GroupArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = g->n; a.k = k; a.ks = group_row_stride(k); a.words = g->words; a.pop = pop; a.G = P.G; a.R = P.R;
@@ -888,17 +904,11 @@ dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
   // floor(x / alpha_den) for x < 2^32 as the high word of x * ceil(2^64 / alpha_den) (division by
   // an invariant integer through a multiplication, Granlund and Montgomery 1994)
   a.ad_recip = tenure.alpha_den >= 2 ? ~0ull / (uint64_t)tenure.alpha_den + 1ull : 0ull;
-  const uint64_t tt_max = (uint64_t)tenure.L_max + ((uint64_t)tenure.alpha_num * (uint64_t)g->m) / tenure.alpha_den;
-  int64_t far_cap = 0;
-  if (tt_max >= (uint64_t)P.R) {
-    far_cap = std::min<int64_t>((int64_t)g->n * (k - 1) + 1, iters + 1);
-    far_cap = std::min<int64_t>(far_cap, (int64_t)tt_max + 1);
-  }
-  a.far_cap = (int32_t)far_cap;
+  a.far_cap = (int32_t)group_far_cap(g, k, iters, tenure, P);
   switch (P.per) {
-    case 2: return launch_per<2>(ctx, a, P);
-    case 4: return launch_per<4>(ctx, a, P);
-    default: return launch_per<8>(ctx, a, P);
+    case 2: return launch_per<2>(ctx, a, P, (uint2*)far_mem);
+    case 4: return launch_per<4>(ctx, a, P, (uint2*)far_mem);
+    default: return launch_per<8>(ctx, a, P, (uint2*)far_mem);
   }
 }
 

@@ -60,6 +60,11 @@ int group_grid(dlm_ctx* ctx, const GroupPlan& plan, int pop);
 dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                 int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                                 uint32_t generation, uint32_t ind_base, const GroupPlan& plan, int32_t* trace,
-                                int64_t* work);
+                                int64_t* work, void* far_mem = nullptr);
+// bytes of far-list memory a launch needs (0 when every tenure fits the ring); far_mem of
+// tabucol_group_launch: that much device memory, or null to take it from the context's workspace
+int64_t group_far_cap(const dlm_graph* g, int32_t k, int64_t iters, dlm_tenure tenure, const GroupPlan& plan);
+size_t group_far_bytes(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters, dlm_tenure tenure,
+                       const GroupPlan& plan);
 
 }  // namespace dlm
