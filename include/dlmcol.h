@@ -147,6 +147,11 @@ typedef struct {
                                    the largest that fits beside the most individuals per CTA; entries
                                    with longer tenures go to the global list (tests use small rings) */
   int32_t legacy;               /* 1 = one individual per CTA with an expiry table (the spill path) */
+  int32_t entry_bits;           /* conflict-table entries of the grouped kernel: 16, 8 (a 7-bit count
+                                   and the tabu flag, valid while every colour class holds at most
+                                   126 vertices; an individual whose search would exceed that is
+                                   searched again with 16-bit entries, with the same result), or 0 =
+                                   8 when it fits more individuals on an SM */
 } dlm_tabu_opts;
 
 /* dlm_tabucol_batch_ex with launch options (opts may be NULL); same results for every option. */
@@ -528,8 +533,8 @@ dlm_status dlm_probe_smem_bandwidth(dlm_ctx* ctx, double* gbps);
 dlm_status dlm_probe_l2_bandwidth(dlm_ctx* ctx, double* gbps);
 
 /* How dlm_tabucol_batch would run a problem (the paper has no counterpart: measurement support).
- * info (host, 8 int32): [0] 1 = several individuals per CTA (tabu flags inside gamma), 0 = one
- * individual per CTA; [1] warps per individual; [2] individuals per CTA; [3] tabu ring entries;
+ * info (host, 8 int32): [0] 1 = several individuals per CTA (tabu flags inside gamma), 2 = the
+ * same with 8-bit conflict-table entries, 0 = one individual per CTA; [1] warps per individual; [2] individuals per CTA; [3] tabu ring entries;
  * [4] vertices per thread; [5] 1 = the graph's bit rows in shared memory; [6] CTAs launched;
  * [7] individual slots (CTAs x individuals per CTA). warps = 0: the library's choice. */
 dlm_status dlm_tabucol_launch_info(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int32_t warps,

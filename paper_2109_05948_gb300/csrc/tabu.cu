@@ -678,10 +678,28 @@ static int default_group_warps(int n) {
   return w;
 }
 
+// the grouped kernel's plan for a problem: u16 gamma entries, or u8 entries when they fit more
+// individuals on an SM (eb = 0: that choice; 8 or 16: forced, u8 only where u16 also fits, for
+// the fallback)
+static bool choose_group_plan(dlm_ctx* ctx, const dlm_graph* g, int k, int pop, int W, int ring, int eb,
+                              GroupPlan* out) {
+  GroupPlan P16, P8;
+  if (!group_plan(g->n, k, g->words, W, ctx->smem_optin, pop, ctx->num_sms, ring, 16, &P16)) return false;
+  if (eb == 16) { *out = P16; return true; }
+  const bool ok8 = k <= 128 && group_plan(g->n, k, g->words, W, ctx->smem_optin, pop, ctx->num_sms, ring, 8, &P8);
+  if (eb == 8) {
+    if (!ok8) return false;
+    *out = P8;
+    return true;
+  }
+  *out = (ok8 && P8.G * group_ctas_per_sm(P8) > P16.G * group_ctas_per_sm(P16)) ? P8 : P16;
+  return true;
+}
+
 static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                               int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                               uint32_t generation, uint32_t ind_base, int warps, int32_t* trace,
-                              int64_t* work, int ring = 0, int legacy = 0) {
+                              int64_t* work, int ring = 0, int legacy = 0, int eb = 0) {
   DLM_TRY(tabucol_check(ctx, g, k, pop, iters, tenure));
   if (pop == 0) return DLM_OK;
   if (!col || !best_f) return fail(ctx, DLM_EINVAL, "tabucol: null col or best_f");
@@ -690,11 +708,12 @@ static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32
     return fail(ctx, DLM_EINVAL, "tabucol: warps per individual must be 1, 2, 4, 8, 16 or 32");
   if (ring != 0 && (ring < 64 || ring > 8192 || (ring & (ring - 1)) != 0))
     return fail(ctx, DLM_EINVAL, "tabucol: the tabu ring size must be a power of two in 64..8192");
+  if (eb != 0 && eb != 8 && eb != 16) return fail(ctx, DLM_EINVAL, "tabucol: entry bits must be 0, 8 or 16");
   if (!legacy) {
     // several individuals per CTA, tabu flags inside gamma: whenever one individual's state fits
     const int wg = warps ? warps : default_group_warps(g->n);
     GroupPlan P;
-    if (group_plan(g->n, k, g->words, wg, ctx->smem_optin, pop, ctx->num_sms, ring, &P)) {
+    if (choose_group_plan(ctx, g, k, pop, wg, ring, eb, &P)) {
       const uint64_t tt_max =
           (uint64_t)tenure.L_max + ((uint64_t)tenure.alpha_num * (uint64_t)g->m) / (uint64_t)tenure.alpha_den;
       if ((uint64_t)iters + tt_max + 2 >= (1ull << 32))
@@ -703,6 +722,7 @@ static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32
                                   trace, work);
     }
     if (ring) return fail(ctx, DLM_EINVAL, "tabucol: the requested tabu ring does not fit in shared memory");
+    if (eb) return fail(ctx, DLM_EINVAL, "tabucol: the requested gamma entries do not fit in shared memory");
   }
   if (warps == 0) warps = default_warps_batch(ctx, g->n, k);
   const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
@@ -750,10 +770,9 @@ extern "C" dlm_status dlm_tabucol_launch_info(dlm_ctx* ctx, const dlm_graph* g, 
   if (!ctx || !g || !info || pop <= 0 || k < 2 || k > 128) return fail(ctx, DLM_EINVAL, "launch_info: bad arguments");
   if (warps == 0) warps = lookup_tune(ctx, g->n, k);
   GroupPlan P;
-  if (group_plan(g->n, k, g->words, warps ? warps : default_group_warps(g->n), ctx->smem_optin, pop, ctx->num_sms, 0,
-                 &P)) {
+  if (choose_group_plan(ctx, g, k, pop, warps ? warps : default_group_warps(g->n), 0, 0, &P)) {
     const int grid = group_grid(ctx, P, pop);
-    const int32_t v[8] = {1, P.W, P.G, P.R, P.per, P.bsm ? 1 : 0, grid, grid * P.G};
+    const int32_t v[8] = {P.eb == 8 ? 2 : 1, P.W, P.G, P.R, P.per, P.bsm ? 1 : 0, grid, grid * P.G};
     for (int i = 0; i < 8; ++i) info[i] = v[i];
     return DLM_OK;
   }
@@ -782,9 +801,9 @@ extern "C" dlm_status dlm_tabucol_batch_opts(dlm_ctx* ctx, const dlm_graph* g, i
                                              int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure,
                                              uint64_t seed, uint32_t generation, uint32_t ind_base,
                                              const dlm_tabu_opts* opts, int32_t* trace, int64_t* work) {
-  const dlm_tabu_opts o = opts ? *opts : dlm_tabu_opts{0, 0, 0};
+  const dlm_tabu_opts o = opts ? *opts : dlm_tabu_opts{0, 0, 0, 0};
   return tabucol_run(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base,
-                     o.warps_per_individual, trace, work, o.ring, o.legacy);
+                     o.warps_per_individual, trace, work, o.ring, o.legacy, o.entry_bits);
 }
 
 extern "C" dlm_status dlm_tabucol_autotune(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters,
@@ -863,9 +882,7 @@ static bool multi_group_plan(dlm_ctx* ctx, int n_graphs, const dlm_graph* const*
     id += (uint32_t)pop[gi];
     if (pop[gi] == 0) continue;
     const dlm_graph* g = graphs[gi];
-    if (!group_plan(g->n, k[gi], g->words, default_group_warps(g->n), ctx->smem_optin, pop[gi], ctx->num_sms, 0,
-                    &M.plans[gi]))
-      return false;
+    if (!choose_group_plan(ctx, g, k[gi], pop[gi], default_group_warps(g->n), 0, 0, &M.plans[gi])) return false;
     const uint64_t tt_max =
         (uint64_t)tenure.L_max + ((uint64_t)tenure.alpha_num * (uint64_t)g->m) / (uint64_t)tenure.alpha_den;
     if ((uint64_t)iters[gi] + tt_max + 2 >= (1ull << 32)) return false;

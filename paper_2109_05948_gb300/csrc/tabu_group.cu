@@ -39,8 +39,18 @@ namespace dlm {
 namespace tg {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr unsigned kNone = 0x7FFFu;  // key of an absent colour, minimum of an empty class
-constexpr unsigned kFlag = 0x8000u;  // tabu flag of a gamma entry
+// gamma entries of EB bits: the top bit is the tabu flag, the rest the count; the largest value
+// (NONE) marks an absent colour. u8 entries hold counts up to 126, which the kernel guarantees by
+// keeping every colour class at most 126 vertices (gamma[v][c] <= |V_c|); an individual whose
+// search would grow a class beyond that gives up and is searched again with u16 entries.
+template <int EB>
+struct Ent {
+  using T = typename std::conditional<EB == 8, uint8_t, uint16_t>::type;
+  static constexpr unsigned NONE = EB == 8 ? 0x7Fu : 0x7FFFu;
+  static constexpr unsigned FLAG = EB == 8 ? 0x80u : 0x8000u;
+  static constexpr int EPW = 32 / EB;  // entries per 32-bit word
+};
+constexpr int kMaxClass8 = 126;
 constexpr int kDueCap = 32;          // expiring ring entries listed per iteration (more: window scan)
 
 // sc[] slots of a group (shared memory); 0..3, 4..7 and 8..11 are each read as one int4
@@ -49,17 +59,19 @@ enum { SC_MV = 0, SC_OLD, SC_NEW, SC_F,          // the iteration's move and f a
        SC_STOP, SC_ERR, SC_BAD, SC_FARMIN,
        SC_REQ = 12,                              // two int4 (by iteration parity): the move's tabu entry
                                                  // (v, c, tenure, was tabu) for the ring, v < 0: none
+       SC_ABORT = 20,                            // u8 entries: a class would exceed kMaxClass8
        SC_N = 32 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline GroupLayout group_layout(int n, int k, int W, int per, int R) {
+__host__ __device__ inline GroupLayout group_layout(int n, int k, int W, int per, int R, int eb) {
   GroupLayout L;
   const size_t nv = (size_t)32 * W * per;  // rows: every thread's per slots (n rounded up)
-  const int ks = group_row_stride(k);
+  const int ks = eb == 8 ? group_row_stride8(k) : group_row_stride(k);
   (void)n;
   size_t o = 0;
-  L.gam = o; o += a16(nv * ks * 2);
+  L.gam = o; o += a16(nv * ks * (eb / 8));
+  L.csz = o; o += eb == 8 ? a16((size_t)k * 4) : 0;  // class sizes (u8 entries only)
   L.col = o; o += a16(nv);
   L.best = o; o += a16(nv);
   L.ring = o; o += a16((size_t)R * 8);
@@ -119,25 +131,27 @@ __device__ __forceinline__ uint32_t cw_inc(uint32_t w, uint32_t g, bool& ok) {  
 }
 
 // Summary of row u by one warp (lanes over its 32-bit words, two colours each, at most 3 words a
-// lane for k <= 128): the current colour cu and the padding colours (key kNone) are skipped.
+// lane for k <= 128): the current colour cu and the padding colours (key NONE) are skipped.
 // Returns (non-tabu class word, tabu class word), the same in every lane.
-template <int NWL>
+template <int NWL, int EB>
 __device__ __forceinline__ uint2 summarise_n(const uint32_t* row32, int kw, int cu, int lane) {
+  constexpr unsigned NONE = Ent<EB>::NONE;
+  constexpr int EPW = Ent<EB>::EPW;
   uint32_t x[NWL];
-  unsigned nm = kNone, tm = kNone;
+  unsigned nm = NONE, tm = NONE;
 #pragma unroll
   for (int t = 0; t < NWL; ++t) {
     const int w = lane + 32 * t;
     uint32_t v = 0xFFFFFFFFu;
     if (w < kw) {
       v = row32[w];
-      if (w == (cu >> 1)) v |= (cu & 1) ? (kNone << 16) : kNone;
+      if (w == cu / EPW) v |= NONE << (EB * (cu % EPW));
     }
     x[t] = v;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const unsigned key = (v >> (16 * h)) & kNone;
-      const bool fl = (v >> (16 * h + 15)) & 1u;
+    for (int h = 0; h < EPW; ++h) {
+      const unsigned key = (v >> (EB * h)) & NONE;
+      const bool fl = (v >> (EB * h + EB - 1)) & 1u;
       tm = fl ? min(tm, key) : tm;
       nm = fl ? nm : min(nm, key);
     }
@@ -147,23 +161,24 @@ __device__ __forceinline__ uint2 summarise_n(const uint32_t* row32, int kw, int 
 #pragma unroll
   for (int t = 0; t < NWL; ++t) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const unsigned key = (x[t] >> (16 * h)) & kNone;
-      const bool fl = (x[t] >> (16 * h + 15)) & 1u;
+    for (int h = 0; h < EPW; ++h) {
+      const unsigned key = (x[t] >> (EB * h)) & NONE;
+      const bool fl = (x[t] >> (EB * h + EB - 1)) & 1u;
       const unsigned ref = fl ? TM : NM;
-      const unsigned add = key == kNone ? 0u : ((key == ref ? 1u : 0u) + (key == ref + 1u ? 0x10000u : 0u));
+      const unsigned add = key == NONE ? 0u : ((key == ref ? 1u : 0u) + (key == ref + 1u ? 0x10000u : 0u));
       ct += fl ? add : 0u;
       cn += fl ? 0u : add;
     }
   }
   const unsigned CN = __reduce_add_sync(FULL, cn), CT = __reduce_add_sync(FULL, ct);
-  return make_uint2(cw_make(NM == kNone ? kEmpty : NM, CN & 0xFFFFu, CN >> 16, false),
-                    cw_make(TM == kNone ? kEmpty : TM, CT & 0xFFFFu, CT >> 16, false));
+  return make_uint2(cw_make(NM == NONE ? kEmpty : NM, CN & 0xFFFFu, CN >> 16, false),
+                    cw_make(TM == NONE ? kEmpty : TM, CT & 0xFFFFu, CT >> 16, false));
 }
+template <int EB>
 __device__ __forceinline__ uint2 summarise(const uint32_t* row32, int kw, int cu, int lane) {
-  if (kw <= 32) return summarise_n<1>(row32, kw, cu, lane);
-  if (kw <= 64) return summarise_n<2>(row32, kw, cu, lane);
-  return summarise_n<3>(row32, kw, cu, lane);
+  if (kw <= 32) return summarise_n<1, EB>(row32, kw, cu, lane);
+  if (kw <= 64) return summarise_n<2, EB>(row32, kw, cu, lane);
+  return summarise_n<3, EB>(row32, kw, cu, lane);
 }
 
 // Best admissible move of a conflicting row from its class words (N, T): (delta, number of
@@ -197,23 +212,31 @@ __device__ __forceinline__ unsigned ent_v(uint32_t x) { return x & 0xFFFFu; }
 __device__ __forceinline__ unsigned ent_c(uint32_t x) { return (x >> 16) & 0xFFu; }
 __device__ __forceinline__ unsigned ent_st(uint32_t x) { return x >> 24; }
 
-// threads of a CTA (all its groups): 768 (85 registers a thread) with 2 vertices a thread, 512
-// (128 registers) with more
-__host__ __device__ constexpr int max_threads_for(int per) { return per <= 2 ? 768 : 512; }
+// threads of a CTA (all its groups): 768 (85 registers a thread) with 2 vertices a thread and with
+// 4 vertices and u8 entries, 512 (128 registers) otherwise
+__host__ __device__ constexpr int max_threads_for(int per, int eb) {
+  return per <= 2 ? 768 : (eb == 8 && per == 4 ? 768 : 512);
+}
 
 // One individual by the W warps of one group (W at run time, PER vertices a thread at compile
 // time). Thread t owns the vertices v0 = t PER .. v0 + PER - 1 and keeps their colours, their
 // gamma[v][col v] and their two class words in registers; the gamma row of vertex v is q NT + t
 // (slot q of its owner thread t), so that the threads of a warp touching their slot q address
 // consecutive rows (distinct banks).
-template <int PER, bool BSM>
+template <int PER, bool BSM, int EB>
 __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t* gs, const uint32_t* bits,
                                int bar_id, uint2* far) {
+  using ET = typename Ent<EB>::T;
+  constexpr unsigned NONE = Ent<EB>::NONE, FLAG = Ent<EB>::FLAG;
+  constexpr int EPW = Ent<EB>::EPW;
   const int NT = 32 * W;
   const int tid = threadIdx.x % NT, lane = tid & 31, warp = tid >> 5;
-  const int n = a.n, k = a.k, ks = a.ks, kw = ks >> 1, words = a.words, R = a.R;
-  const GroupLayout L = group_layout(n, k, W, PER, R);
-  uint16_t* gam = (uint16_t*)(gs + L.gam);
+  // u16 pass after a u8 launch: only the individuals the u8 launch gave up (a uniform branch)
+  if (a.redo_mode == 2 && a.redo[ind] == 0) return;
+  const int n = a.n, k = a.k, ks = a.ks, kw = ks / EPW, words = a.words, R = a.R;
+  const GroupLayout L = group_layout(n, k, W, PER, R, EB);
+  ET* gam = (ET*)(gs + L.gam);
+  uint32_t* csz = (uint32_t*)(gs + L.csz);
   uint8_t* colS = gs + L.col;
   uint8_t* bestS = gs + L.best;
   uint2* ring = (uint2*)(gs + L.ring);
@@ -225,8 +248,8 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
   int16_t* gcol = a.col + (size_t)ind * n;
   const unsigned lt = (1u << lane) - 1u;
   auto bar = [&]() { group_bar(bar_id, NT); };
-  auto rowof = [&](int v) -> uint16_t* { return gam + ((v % PER) * NT + v / PER) * ks; };
-  auto myrow = [&](int q) -> uint16_t* { return gam + (q * NT + tid) * ks; };
+  auto rowof = [&](int v) -> ET* { return gam + ((v % PER) * NT + v / PER) * ks; };
+  auto myrow = [&](int q) -> ET* { return gam + (q * NT + tid) * ks; };
 
   int colq[PER], g0q[PER];
   uint2 recq[PER];
@@ -236,7 +259,12 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     uint32_t* r32 = (uint32_t*)myrow(q);
-    for (int w = 0; w < kw; ++w) r32[w] = (2 * w >= k ? kNone : 0u) | (2 * w + 1 >= k ? (kNone << 16) : 0u);
+    for (int w = 0; w < kw; ++w) {
+      uint32_t x = 0u;
+#pragma unroll
+      for (int e = 0; e < EPW; ++e) x |= (EPW * w + e >= k) ? NONE << (EB * e) : 0u;
+      r32[w] = x;
+    }
     const int v = v0 + q;
     int c = 0;
     if (v < n) {
@@ -249,8 +277,15 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
     bestS[v] = (uint8_t)c;
   }
   if (tid < SC_N) sc[tid] = 0;
+  if (EB == 8)
+    for (int c = tid; c < k; c += NT) csz[c] = 0u;
   bar();
   if (bad) sc[SC_BAD] = 1;
+  if (EB == 8 && !bad) {  // class sizes of the start colouring
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if (v0 + q < n) atomicAdd(csz + colq[q], 1u);
+  }
   if (tid == 0) {
     sc[SC_REQ] = -1;
     sc[SC_REQ + 4] = -1;
@@ -262,6 +297,16 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
     bar();  // every thread has read the flag before the next individual clears it
     return;
   }
+  if (EB == 8) {  // a start class above the u8 bound: the u16 pass searches this individual
+    bool big = false;
+    for (int c = lane; c < k; c += 32) big |= csz[c] > (uint32_t)kMaxClass8;
+    if (__any_sync(FULL, big)) {
+      bar();
+      if (tid == 0 && a.redo_mode == 1) a.redo[ind] = 1;
+      bar();
+      return;
+    }
+  }
   int part = 0;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -269,7 +314,7 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
     g0q[q] = 0;
     if (v < n) {
       const uint32_t* br = bits + v * words;
-      uint16_t* gr = myrow(q);
+      ET* gr = myrow(q);
       for (int w = 0; w < words; ++w) {
         uint32_t m = br[w];
         while (m) {
@@ -288,7 +333,7 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
   for (int q = 0; q < PER; ++q) {
     for (int l = 0; l < 32; ++l) {
       const int cu = __shfl_sync(FULL, colq[q], l);
-      const uint2 r = summarise((const uint32_t*)(gam + (q * NT + warp * 32 + l) * ks), kw, cu, lane);
+      const uint2 r = summarise<EB>((const uint32_t*)(gam + (q * NT + warp * 32 + l) * ks), kw, cu, lane);
       if (lane == l) recq[q] = r;
     }
   }
@@ -408,33 +453,59 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
         int rem = jj;
         for (int wb = 0; wb < kw && mc < 0; wb += 32) {
           const int w = wb + lane;
-          bool m0 = false, m1 = false;
+          bool mh[EPW];
+          uint32_t x = 0u;
           if (w < kw) {
-            uint32_t x = row32[w];
-            if (w == (colv >> 1)) x |= (colv & 1) ? (kNone << 16) : kNone;
-            const unsigned ka = x & kNone, kb = (x >> 16) & kNone;
-            m0 = ka == kmin && (!(x & kFlag) || (int)ka < thr);
-            m1 = kb == kmin && (!((x >> 16) & kFlag) || (int)kb < thr);
+            x = row32[w];
+            if (w == colv / EPW) x |= NONE << (EB * (colv % EPW));
           }
-          // colours 2w (m0) and 2w + 1 (m1) in colour order: the lane whose pair holds the rem-th
-          const unsigned b0 = __ballot_sync(FULL, m0), b1 = __ballot_sync(FULL, m1);
-          const int before = __popc(b0 & lt) + __popc(b1 & lt);
-          const unsigned fb = __ballot_sync(FULL, rem >= before && rem < before + (int)m0 + (int)m1);
+          int mine = 0;
+#pragma unroll
+          for (int h = 0; h < EPW; ++h) {
+            const unsigned kh = (x >> (EB * h)) & NONE;
+            mh[h] = w < kw && kh == kmin && (!((x >> (EB * h + EB - 1)) & 1u) || (int)kh < thr);
+            mine += mh[h] ? 1 : 0;
+          }
+          // colours EPW w + h in colour order: the lane whose word holds the rem-th
+          unsigned bh[EPW];
+          int before = 0, total = 0;
+#pragma unroll
+          for (int h = 0; h < EPW; ++h) {
+            bh[h] = __ballot_sync(FULL, mh[h]);
+            before += __popc(bh[h] & lt);
+            total += __popc(bh[h]);
+          }
+          const unsigned fb = __ballot_sync(FULL, rem >= before && rem < before + mine);
           if (fb) {
             const int wl = __ffs(fb) - 1;
             const unsigned lw = (1u << wl) - 1u;
-            const int bw = __popc(b0 & lw) + __popc(b1 & lw);
-            mc = 2 * (wb + wl) + ((rem == bw && ((b0 >> wl) & 1u)) ? 0 : 1);
+            int r = rem;
+#pragma unroll
+            for (int h = 0; h < EPW; ++h) r -= __popc(bh[h] & lw);
+            int pick = EPW - 1;
+#pragma unroll
+            for (int h = EPW - 1; h >= 0; --h) {  // the r-th set colour of word wl, in colour order
+              int before_h = 0;
+#pragma unroll
+              for (int g = 0; g < h; ++g) before_h += (bh[g] >> wl) & 1u;
+              if (((bh[h] >> wl) & 1u) && before_h == r) pick = h;
+            }
+            mc = EPW * (wb + wl) + pick;
           } else {
-            rem -= __popc(b0) + __popc(b1);
+            rem -= total;
           }
         }
       }
-      const bool good = v >= 0 && mc >= 0 && mc < k;
+      // u8 entries: a move that would grow a class beyond kMaxClass8 ends this search (the u16
+      // pass repeats the individual from its start)
+      const bool full = EB == 8 && v >= 0 && mc >= 0 && mc < k && csz[mc] >= (uint32_t)kMaxClass8;
+      const bool good = v >= 0 && mc >= 0 && mc < k && !full;
       if (lane == 0) {
         if (good) {
           *(int4*)(sc + SC_MV) = make_int4(v, colv, mc, f + dstar);
           if (a.trace) reinterpret_cast<int4*>(a.trace)[(size_t)ind * iters + it] = make_int4(v, mc, dstar, T);
+        } else if (full) {
+          sc[SC_ABORT] = 1;
         } else {
           sc[SC_ERR] = 2;  // tie counts inconsistent with the row: refuse to move
         }
@@ -444,27 +515,31 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
         uint2 rc = recq[0];
 #pragma unroll
         for (int q = 1; q < PER; ++q) rc = q == qs ? recq[q] : rc;
-        uint16_t* gr = rowof(v);
+        ET* gr = rowof(v);
         const unsigned go = gr[colv], gn = gr[mc];
-        const bool was = (go & kFlag) != 0;
+        const bool was = (go & FLAG) != 0;
         // alpha f (f after the move): 32-bit unsigned (the host bounds alpha_num * |E| below
         // 2^32), divided by alpha_den through its precomputed 64-bit reciprocal
         const uint32_t af = (uint32_t)a.an * (uint32_t)(f + dstar);
         const uint32_t tt = below(r1, a.L1) + (a.ad == 1 ? af : (uint32_t)__umul64hi((uint64_t)af, a.ad_recip));
         const bool tabu = tt > 0;
-        gr[colv] = (uint16_t)((go & kNone) | (tabu ? kFlag : 0u));
+        gr[colv] = (ET)((go & NONE) | (tabu ? FLAG : 0u));
+        if (EB == 8) {
+          csz[colv] -= 1u;
+          csz[mc] += 1u;
+        }
         // the new colour leaves its class, the old one joins the tabu (or the free) class
         bool ok;
-        if (gn & kFlag) rc.y = cw_rem(rc.y, gn & kNone, ok);
-        else rc.x = cw_rem(rc.x, gn & kNone, ok);
-        if (tabu) rc.y = cw_ins(rc.y, go & kNone);
-        else rc.x = cw_ins(rc.x, go & kNone);
+        if (gn & FLAG) rc.y = cw_rem(rc.y, gn & NONE, ok);
+        else rc.x = cw_rem(rc.x, gn & NONE, ok);
+        if (tabu) rc.y = cw_ins(rc.y, go & NONE);
+        else rc.x = cw_ins(rc.x, go & NONE);
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
           if (q == qs) {
             recq[q] = rc;
             colq[q] = mc;
-            g0q[q] = (int)(gn & kNone);
+            g0q[q] = (int)(gn & NONE);
           }
         }
         dmask |= ok ? 0u : (1u << qs);
@@ -592,6 +667,7 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
     const int4 B = *(const int4*)(sc + SC_DUE);
     const int4 C = *(const int4*)(sc + SC_STOP);
     if (C.x | C.y) break;
+    if (EB == 8 && sc[SC_ABORT]) break;
     int mv = -1, old = -1, nw = -1;
     bool improved = false;
     if (T > 0) {
@@ -607,10 +683,10 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
     auto expire = [&](int v, int c) {
       if (v == mv && c == old) return;
       const int qs = v - v0;
-      uint16_t* ge = myrow(qs) + c;
+      ET* ge = myrow(qs) + c;
       const unsigned g = *ge;
-      if (!(g & kFlag)) return;
-      *ge = (uint16_t)(g & kNone);
+      if (!(g & FLAG)) return;
+      *ge = (ET)(g & NONE);
       int cu = colq[0];
       uint2 rc = recq[0];
 #pragma unroll
@@ -620,8 +696,8 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
       }
       if (c == cu) return;
       bool ok;
-      rc.y = cw_rem(rc.y, g & kNone, ok);
-      rc.x = cw_ins(rc.x, g & kNone);
+      rc.y = cw_rem(rc.y, g & NONE, ok);
+      rc.x = cw_ins(rc.x, g & NONE);
 #pragma unroll
       for (int q = 0; q < PER; ++q) recq[q] = q == qs ? rc : recq[q];
       dmask |= ok ? 0u : (1u << qs);
@@ -675,30 +751,30 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
       unsigned go[PER], gn[PER];
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
-        const uint16_t* gr = myrow(q);
+        const ET* gr = myrow(q);
         go[q] = gr[old];
         gn[q] = gr[nw];
       }
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
         const unsigned nb = (m >> q) & 1u;
-        uint16_t* gr = myrow(q);
-        gr[old] = (uint16_t)(go[q] - nb);
-        gr[nw] = (uint16_t)(gn[q] + nb);
-        const bool fo = (go[q] & kFlag) != 0, fn = (gn[q] & kFlag) != 0;
+        ET* gr = myrow(q);
+        gr[old] = (ET)(go[q] - nb);
+        gr[nw] = (ET)(gn[q] + nb);
+        const bool fo = (go[q] & FLAG) != 0, fn = (gn[q] & FLAG) != 0;
         const bool is_old = colq[q] == old, is_new = colq[q] == nw;
         // the old colour's key drops by one, the new colour's rises by one (when neither is the
         // vertex's own colour, whose gamma is g0)
-        const uint32_t wo = cw_dec(fo ? recq[q].y : recq[q].x, go[q] & kNone);
+        const uint32_t wo = cw_dec(fo ? recq[q].y : recq[q].x, go[q] & NONE);
         const bool ao = nb && !is_old;
         recq[q].y = (ao && fo) ? wo : recq[q].y;
         recq[q].x = (ao && !fo) ? wo : recq[q].x;
         bool ok = true;
-        const uint32_t wn = cw_inc(fn ? recq[q].y : recq[q].x, gn[q] & kNone, ok);
+        const uint32_t wn = cw_inc(fn ? recq[q].y : recq[q].x, gn[q] & NONE, ok);
         const bool an = nb && !is_new;
         recq[q].y = (an && fn) ? wn : recq[q].y;
         recq[q].x = (an && !fn) ? wn : recq[q].x;
-        const int g0n = is_old ? (int)(go[q] & kNone) - 1 : (is_new ? (int)(gn[q] & kNone) + 1 : g0q[q]);
+        const int g0n = is_old ? (int)(go[q] & NONE) - 1 : (is_new ? (int)(gn[q] & NONE) + 1 : g0q[q]);
         g0q[q] = nb ? g0n : g0q[q];
         dmask |= (!nb || ok || is_new) ? 0u : (1u << q);
       }
@@ -711,7 +787,7 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
         for (unsigned pend = __ballot_sync(FULL, (dmask >> q) & 1u); pend; pend &= pend - 1) {
           const int l = __ffs(pend) - 1;
           const int cu = __shfl_sync(FULL, colq[q], l);
-          const uint2 r = summarise((const uint32_t*)(gam + (q * NT + warp * 32 + l) * ks), kw, cu, lane);
+          const uint2 r = summarise<EB>((const uint32_t*)(gam + (q * NT + warp * 32 + l) * ks), kw, cu, lane);
           if (lane == l) recq[q] = r;
           if (lane == 0) ++w_resum;
         }
@@ -725,8 +801,14 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
   }
   // ---- results ---------------------------------------------------------------------------------
   const int err = sc[SC_ERR], stop = sc[SC_STOP];
+  const int gave_up = EB == 8 ? sc[SC_ABORT] : 0;
   long long* wk = (long long*)(gs + L.red);
   bar();  // every warp has left the loop: red[] is free
+  if (gave_up) {  // no result: the u16 pass searches this individual from its start colouring
+    if (tid == 0 && a.redo_mode == 1) a.redo[ind] = 1;
+    bar();
+    return;
+  }
   {
     long long d = w_deg;
 #pragma unroll
@@ -759,8 +841,8 @@ __device__ void run_individual(const GroupArgs& a, const int W, int ind, uint8_t
   bar();  // shared memory is reused by the next individual
 }
 
-template <int PER, bool BSM>
-__global__ void __launch_bounds__(max_threads_for(PER)) tabucol_group_kernel(GroupArgs a) {
+template <int PER, bool BSM, int EB>
+__global__ void __launch_bounds__(max_threads_for(PER, EB)) tabucol_group_kernel(GroupArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int G = a.G, W = a.W;
   const int grp = threadIdx.x / (32 * W);
@@ -778,27 +860,29 @@ __global__ void __launch_bounds__(max_threads_for(PER)) tabucol_group_kernel(Gro
     bits = bs;
   }
   uint8_t* gs = smem + a.bits_bytes + (size_t)grp * a.group_bytes;
-  const int slot = blockIdx.x * G + grp;
+  // slots group-major: a last, partial round of individuals spreads over every CTA (fewer groups
+  // per SM run each faster) instead of filling the first CTAs
+  const int slot = grp * gridDim.x + blockIdx.x;
   uint2* far = a.far ? a.far + (size_t)slot * (size_t)a.far_cap : nullptr;
-  for (int i = slot; i < a.pop; i += gridDim.x * G) run_individual<PER, BSM>(a, W, i, gs, bits, 1 + grp, far);
+  for (int i = slot; i < a.pop; i += gridDim.x * G) run_individual<PER, BSM, EB>(a, W, i, gs, bits, 1 + grp, far);
 }
 
-template <int PER, bool BSM>
+template <int PER, bool BSM, int EB>
 static dlm_status launch_one(dlm_ctx* ctx, GroupArgs a, int grid, size_t smem) {
-  auto kfn = tabucol_group_kernel<PER, BSM>;
+  auto kfn = tabucol_group_kernel<PER, BSM, EB>;
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   kfn<<<grid, 32 * a.W * a.G, smem, ctx->stream>>>(a);
   return launch_check(ctx, "tabucol_group_kernel");
 }
 
-template <int PER, bool BSM>
+template <int PER, bool BSM, int EB>
 static int occupancy_one(int threads, size_t smem) {
   int per_sm = 0;
-  cudaError_t e = cudaFuncSetAttribute(tabucol_group_kernel<PER, BSM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(tabucol_group_kernel<PER, BSM, EB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_group_kernel<PER, BSM>, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_group_kernel<PER, BSM, EB>, threads, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -810,19 +894,21 @@ static int occupancy_one(int threads, size_t smem) {
 
 using namespace tg;
 
-bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_sms, int ring_force,
+bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_sms, int ring_force, int eb,
                 GroupPlan* out) {
   if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16) return false;
+  if (eb != 8 && eb != 16) return false;
   const int NT = 32 * W;
   int per = 2;
   while (per < 8 && per * NT < n) per *= 2;  // a power of two up to 8: each value is its own kernel
   if (per * NT < n) return false;
+  if (eb == 8 && per > 4) return false;  // u8 entries: kernels for 2 and 4 vertices a thread
   const size_t bits_bytes = a16(((size_t)n * words + 1) * 4);
   const int gmax_pop = std::max(1, (pop + num_sms - 1) / std::max(1, num_sms));
-  const int gmax = std::min(std::min(max_threads_for(per) / NT, 8), gmax_pop);
+  const int gmax = std::min(std::min(max_threads_for(per, eb) / NT, 8), gmax_pop);
   auto ring_for = [&](int G, bool bsm, int* R) -> bool {
     for (int r = ring_force > 0 ? ring_force : 8192; r >= 64; r >>= 1) {
-      const size_t tot = (size_t)G * group_layout(n, k, W, per, r).total + (bsm ? bits_bytes : 0);
+      const size_t tot = (size_t)G * group_layout(n, k, W, per, r, eb).total + (bsm ? bits_bytes : 0);
       if (tot <= optin) { *R = r; return true; }
       if (ring_force > 0) return false;
     }
@@ -833,8 +919,8 @@ bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_s
       const bool bsm = b == 0;
       int R = 0;
       if (ring_for(G, bsm, &R) && (R >= 512 || ring_force > 0 || (G == 1 && !bsm))) {
-        out->W = W; out->G = G; out->R = R; out->per = per; out->bsm = bsm;
-        out->group_bytes = group_layout(n, k, W, per, R).total;
+        out->W = W; out->G = G; out->R = R; out->per = per; out->bsm = bsm; out->eb = eb;
+        out->group_bytes = group_layout(n, k, W, per, R, eb).total;
         out->bits_bytes = bsm ? bits_bytes : 0;
         out->smem = (size_t)G * out->group_bytes + out->bits_bytes;
         return true;
@@ -844,32 +930,30 @@ bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_s
   return false;
 }
 
-int group_grid(dlm_ctx* ctx, const GroupPlan& P, int pop) {
+int group_ctas_per_sm(const GroupPlan& P) {
   const int threads = 32 * P.W * P.G;
-  int per_sm = 1;
-  switch (P.per) {
-    case 2: per_sm = P.bsm ? occupancy_one<2, true>(threads, P.smem) : occupancy_one<2, false>(threads, P.smem); break;
-    case 4: per_sm = P.bsm ? occupancy_one<4, true>(threads, P.smem) : occupancy_one<4, false>(threads, P.smem); break;
-    default: per_sm = P.bsm ? occupancy_one<8, true>(threads, P.smem) : occupancy_one<8, false>(threads, P.smem); break;
+  if (P.eb == 8) {
+    if (P.per == 2) return P.bsm ? occupancy_one<2, true, 8>(threads, P.smem) : occupancy_one<2, false, 8>(threads, P.smem);
+    return P.bsm ? occupancy_one<4, true, 8>(threads, P.smem) : occupancy_one<4, false, 8>(threads, P.smem);
   }
-  const int blocks = (pop + P.G - 1) / P.G;
-  return std::max(1, std::min(blocks, per_sm * ctx->num_sms));
+  switch (P.per) {
+    case 2: return P.bsm ? occupancy_one<2, true, 16>(threads, P.smem) : occupancy_one<2, false, 16>(threads, P.smem);
+    case 4: return P.bsm ? occupancy_one<4, true, 16>(threads, P.smem) : occupancy_one<4, false, 16>(threads, P.smem);
+    default: return P.bsm ? occupancy_one<8, true, 16>(threads, P.smem) : occupancy_one<8, false, 16>(threads, P.smem);
+  }
 }
 
-template <int PER>
+int group_grid(dlm_ctx* ctx, const GroupPlan& P, int pop) {
+  const int blocks = (pop + P.G - 1) / P.G;
+  return std::max(1, std::min(blocks, group_ctas_per_sm(P) * ctx->num_sms));
+}
+
+template <int PER, int EB>
 static dlm_status launch_per(dlm_ctx* ctx, const GroupArgs& a, const GroupPlan& P, uint2* far_mem) {
   const int grid = group_grid(ctx, P, a.pop);
   GroupArgs b = a;
-  if (b.far_cap > 0) {
-    if (far_mem) {
-      b.far = far_mem;
-    } else {
-      void* ws = nullptr;
-      DLM_TRY(ctx_workspace(ctx, (size_t)grid * P.G * (size_t)b.far_cap * sizeof(uint2), &ws));
-      b.far = (uint2*)ws;
-    }
-  }
-  return P.bsm ? launch_one<PER, true>(ctx, b, grid, P.smem) : launch_one<PER, false>(ctx, b, grid, P.smem);
+  b.far = b.far_cap > 0 ? far_mem : nullptr;
+  return P.bsm ? launch_one<PER, true, EB>(ctx, b, grid, P.smem) : launch_one<PER, false, EB>(ctx, b, grid, P.smem);
 }
 
 // far list: tabu entries whose tenure does not fit the ring. A pair holds at most one live entry,
@@ -883,9 +967,25 @@ int64_t group_far_cap(const dlm_graph* g, int32_t k, int64_t iters, dlm_tenure t
   return std::min<int64_t>(far_cap, (int64_t)tt_max + 1);
 }
 
+static size_t far_bytes_of(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters, dlm_tenure tenure,
+                           const GroupPlan& P) {
+  return (size_t)group_grid(ctx, P, pop) * P.G * (size_t)group_far_cap(g, k, iters, tenure, P) * sizeof(uint2);
+}
+
+// the u16 plan that repeats the individuals a u8 launch gives up
+static bool fallback_plan(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, const GroupPlan& P, GroupPlan* F) {
+  return group_plan(g->n, k, g->words, P.W, ctx->smem_optin, pop, ctx->num_sms, 0, 16, F);
+}
+
 size_t group_far_bytes(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int64_t iters, dlm_tenure tenure,
                        const GroupPlan& P) {
-  return (size_t)group_grid(ctx, P, pop) * P.G * (size_t)group_far_cap(g, k, iters, tenure, P) * sizeof(uint2);
+  size_t far = far_bytes_of(ctx, g, k, pop, iters, tenure, P);
+  if (P.eb == 8) {
+    GroupPlan F;
+    if (fallback_plan(ctx, g, k, pop, P, &F)) far = std::max(far, far_bytes_of(ctx, g, k, pop, iters, tenure, F));
+    far = a16(far) + a16((size_t)pop * 4);  // then the flags of the individuals to search again
+  }
+  return far;
 }
 
 dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
@@ -894,7 +994,8 @@ dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
                                 int64_t* work, void* far_mem) {
   GroupArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.n = g->n; a.k = k; a.ks = group_row_stride(k); a.words = g->words; a.pop = pop; a.G = P.G; a.R = P.R;
+  a.n = g->n; a.k = k; a.ks = P.eb == 8 ? group_row_stride8(k) : group_row_stride(k); a.words = g->words; a.pop = pop;
+  a.G = P.G; a.R = P.R;
   a.W = P.W; a.per = P.per;
   a.bits = g->d_bits; a.col = col; a.best_f = best_f; a.moves = moves; a.trace = trace; a.work = work;
   a.iters = iters; a.ind_base = ind_base;
@@ -905,10 +1006,37 @@ dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
   // an invariant integer through a multiplication, Granlund and Montgomery 1994)
   a.ad_recip = tenure.alpha_den >= 2 ? ~0ull / (uint64_t)tenure.alpha_den + 1ull : 0ull;
   a.far_cap = (int32_t)group_far_cap(g, k, iters, tenure, P);
-  switch (P.per) {
-    case 2: return launch_per<2>(ctx, a, P, (uint2*)far_mem);
-    case 4: return launch_per<4>(ctx, a, P, (uint2*)far_mem);
-    default: return launch_per<8>(ctx, a, P, (uint2*)far_mem);
+  uint8_t* scratch = (uint8_t*)far_mem;
+  const size_t need = group_far_bytes(ctx, g, k, pop, iters, tenure, P);
+  if (!scratch && need) DLM_TRY(ctx_workspace(ctx, need, (void**)&scratch));
+  if (P.eb == 16) {
+    switch (P.per) {
+      case 2: return launch_per<2, 16>(ctx, a, P, (uint2*)scratch);
+      case 4: return launch_per<4, 16>(ctx, a, P, (uint2*)scratch);
+      default: return launch_per<8, 16>(ctx, a, P, (uint2*)scratch);
+    }
+  }
+  // u8 entries, then a u16 pass over the individuals the u8 launch gave up (their start colourings
+  // are untouched; the same random streams give the same searches)
+  GroupPlan F;
+  if (!fallback_plan(ctx, g, k, pop, P, &F)) return fail(ctx, DLM_EUNSUPPORTED, "tabucol: no u16 plan for the fallback");
+  const size_t far16 = std::max(far_bytes_of(ctx, g, k, pop, iters, tenure, P), far_bytes_of(ctx, g, k, pop, iters, tenure, F));
+  int32_t* redo = (int32_t*)(scratch + a16(far16));
+  DLM_CUDA(ctx, cudaMemsetAsync(redo, 0, (size_t)pop * 4, ctx->stream));
+  a.redo = redo;
+  a.redo_mode = 1;
+  if (P.per == 2) DLM_TRY((launch_per<2, 8>(ctx, a, P, (uint2*)scratch)));
+  else DLM_TRY((launch_per<4, 8>(ctx, a, P, (uint2*)scratch)));
+  GroupArgs b = a;
+  b.ks = group_row_stride(k);
+  b.G = F.G; b.R = F.R; b.W = F.W; b.per = F.per;
+  b.group_bytes = F.group_bytes; b.bits_bytes = F.bits_bytes;
+  b.far_cap = (int32_t)group_far_cap(g, k, iters, tenure, F);
+  b.redo_mode = 2;
+  switch (F.per) {
+    case 2: return launch_per<2, 16>(ctx, b, F, (uint2*)scratch);
+    case 4: return launch_per<4, 16>(ctx, b, F, (uint2*)scratch);
+    default: return launch_per<8, 16>(ctx, b, F, (uint2*)scratch);
   }
 }
 

@@ -13,9 +13,16 @@ __host__ __device__ inline int group_row_stride(int k) {
   return 2 * kw;
 }
 
+// gamma row stride in u8 entries: ks / 4 odd (the same bank rule for byte entries)
+__host__ __device__ inline int group_row_stride8(int k) {
+  int kw = (k + 3) / 4;
+  if ((kw & 1) == 0) kw += 1;
+  return 4 * kw;
+}
+
 // byte offsets of one individual's arrays within its group's shared memory
 struct GroupLayout {
-  size_t gam, col, best, ring, due, red, sc, total;
+  size_t gam, csz, col, best, ring, due, red, sc, total;
 };
 
 struct GroupArgs {
@@ -38,6 +45,8 @@ struct GroupArgs {
   uint2* far;            // per slot far_cap entries, or null
   int32_t far_cap;
   size_t group_bytes, bits_bytes;
+  int32_t* redo;         // [pop] individuals a u8 launch gave up
+  int32_t redo_mode;     // 0: none; 1 (u8 launch): flag the individuals given up; 2: only those
 };
 
 // W warps per individual, G individuals per CTA, ring of R tabu entries, per vertices a thread,
@@ -45,13 +54,16 @@ struct GroupArgs {
 struct GroupPlan {
   int W, G, R, per;
   bool bsm;
+  int eb;                // bits of a gamma entry: 16, or 8 (counts up to 126, u16 fallback)
   size_t group_bytes, bits_bytes, smem;
 };
 
 // Shared-memory plan for n vertices, k colours, W warps per individual within `optin` bytes
 // (ring_force > 0 forces the ring size); false when one individual's state does not fit.
-bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_sms, int ring_force,
+bool group_plan(int n, int k, int words, int W, size_t optin, int pop, int num_sms, int ring_force, int eb,
                 GroupPlan* out);
+// resident CTAs of the plan's kernel on one SM
+int group_ctas_per_sm(const GroupPlan& plan);
 
 // CTAs the grouped launch of `pop` individuals uses (resident CTAs at most; each loops over its
 // individuals)

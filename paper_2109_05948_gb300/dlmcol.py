@@ -37,7 +37,8 @@ class MemeticParams(ctypes.Structure):
 
 
 class TabuOpts(ctypes.Structure):
-    _fields_ = [("warps_per_individual", ctypes.c_int32), ("ring", ctypes.c_int32), ("legacy", ctypes.c_int32)]
+    _fields_ = [("warps_per_individual", ctypes.c_int32), ("ring", ctypes.c_int32), ("legacy", ctypes.c_int32),
+                ("entry_bits", ctypes.c_int32)]
 
 
 COL_TENURE = Tenure(9, 6, 10)    # Table params-COL: alpha = 0.6, L in 0..9
@@ -255,8 +256,8 @@ def dlm_tabucol_batch_ex(ctx, g, k, pop, col, best_f, moves, iters, tenure=COL_T
 
 
 def dlm_tabucol_batch_opts(ctx, g, k, pop, col, best_f, moves, iters, tenure=COL_TENURE, seed=0, generation=0,
-                           ind_base=0, warps=0, ring=0, legacy=0, trace=None, work=None):
-    o = TabuOpts(warps, ring, legacy)
+                           ind_base=0, warps=0, ring=0, legacy=0, trace=None, work=None, entry_bits=0):
+    o = TabuOpts(warps, ring, legacy, entry_bits)
     ctx.check(lib().dlm_tabucol_batch_opts(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_f), _ptr(moves), iters, tenure,
                                            seed, generation, ind_base, ctypes.byref(o), _ptr(trace), _ptr(work)),
               "dlm_tabucol_batch_opts")
@@ -530,7 +531,7 @@ def dlm_tabucol_launch_info(ctx, g, k, pop, warps=0):
     would make for this problem."""
     info = (ctypes.c_int32 * 8)()
     ctx.check(lib().dlm_tabucol_launch_info(ctx.h, g.h, k, pop, warps, info), "dlm_tabucol_launch_info")
-    keys = ("grouped", "warps", "groups", "ring", "per", "bits_in_smem", "grid", "slots")
+    keys = ("grouped", "warps", "groups", "ring", "per", "bits_in_smem", "grid", "slots")  # grouped 2: u8 entries
     return dict(zip(keys, [int(x) for x in info]))
 
 

@@ -295,7 +295,7 @@ def test_tabucol_cancel_flag(ctx):
 
 
 def _run_opts(ctx, g, k, col_np, iters, seed=0, gen=0, ind_base=0, warps=0, ring=0, legacy=0, trace=False,
-              tenure=None, work=False):
+              tenure=None, work=False, entry_bits=0):
     pop, n = col_np.shape
     col = torch.from_numpy(col_np.copy()).cuda()
     bf = torch.zeros(pop, dtype=torch.int64, device="cuda")
@@ -303,7 +303,8 @@ def _run_opts(ctx, g, k, col_np, iters, seed=0, gen=0, ind_base=0, warps=0, ring
     tr = torch.full((pop, iters, 4), -7, dtype=torch.int32, device="cuda") if trace else None
     wk = torch.zeros((pop, 3), dtype=torch.int64, device="cuda") if work else None
     dlmcol.dlm_tabucol_batch_opts(ctx, g, k, pop, col, bf, mv, iters, tenure or dlmcol.COL_TENURE, seed, gen,
-                                  ind_base, warps=warps, ring=ring, legacy=legacy, trace=tr, work=wk)
+                                  ind_base, warps=warps, ring=ring, legacy=legacy, trace=tr, work=wk,
+                                  entry_bits=entry_bits)
     ctx.sync()
     out = dict(col=col.cpu().numpy(), best_f=bf.cpu().numpy(), moves=mv.cpu().numpy())
     if trace:
@@ -313,9 +314,10 @@ def _run_opts(ctx, g, k, col_np, iters, seed=0, gen=0, ind_base=0, warps=0, ring
     return out
 
 
+@pytest.mark.parametrize("entry_bits", [16, 8])
 @pytest.mark.parametrize("warps,ring,alpha", [(2, 64, (6, 10)), (4, 64, (30, 10)), (8, 128, (6, 10)),
                                               (1, 64, (60, 10)), (4, 0, (6, 10))])
-def test_tabucol_grouped_rings_and_far_list_bitexact(ctx, warps, ring, alpha):
+def test_tabucol_grouped_rings_and_far_list_bitexact(ctx, warps, ring, alpha, entry_bits):
     """The grouped kernel with small tabu rings: tenures of 64 iterations and more go to the
     global far list (alpha = 3 and 6 make them common), and several individuals share a CTA
     (population 400). Every move, best colouring, best f and move count equal the oracle's."""
@@ -324,7 +326,10 @@ def test_tabucol_grouped_rings_and_far_list_bitexact(ctx, warps, ring, alpha):
     g = device_graph(ctx, n, e)
     start = oracle.init_colors(n, k, pop, 17)
     ten = dlmcol.Tenure(9, alpha[0], alpha[1])
-    gpu = _run_opts(ctx, g, k, start, iters, seed=17, gen=2, warps=warps, ring=ring, trace=True, tenure=ten)
+    if entry_bits == 8 and 32 * warps * 4 < n:  # u8 entries: kernels for up to 4 vertices a thread
+        return
+    gpu = _run_opts(ctx, g, k, start, iters, seed=17, gen=2, warps=warps, ring=ring, trace=True, tenure=ten,
+                    entry_bits=entry_bits)
     sample = list(range(0, pop, 37)) + [pop - 1]
     jobs = [(adj, k, start[i], iters, 17, i, 2, True) for i in sample]
     refs = oracle_pool().map(_oracle_tabu_alpha_job, [(j, alpha) for j in jobs])
@@ -334,6 +339,60 @@ def test_tabucol_grouped_rings_and_far_list_bitexact(ctx, warps, ring, alpha):
             f"{int(np.argmax(np.any(gpu['trace'][i, :T] != r['trace'], axis=1)))}"
         assert gpu["best_f"][i] == r["best_f"] and gpu["moves"][i] == r["moves"]
         assert np.array_equal(gpu["col"][i], r["best_col"])
+
+
+@pytest.mark.parametrize("case", ["start_class_too_large", "first_move_overflows", "mixed"])
+def test_tabucol_u8_entries_fall_back_to_u16(ctx, case):
+    """8-bit conflict-table entries hold counts up to 126, guaranteed by keeping every colour class
+    at most 126 vertices; an individual whose start colouring has a larger class, or whose search
+    would grow one, is searched again with 16-bit entries. Traces, results and move counts equal the
+    oracle's in every case, and individuals that never reach the bound keep their u8 results."""
+    if case == "start_class_too_large":
+        n, k, pop, iters = 300, 2, 24, 400
+        e, adj = gnp_case(n, 0.1, 5)
+        start = oracle.init_colors(n, k, pop, 5)
+    elif case == "first_move_overflows":
+        # two classes of exactly 126: the first move makes one of them 127
+        n, k, pop, iters = 252, 2, 16, 300
+        e, adj = gnp_case(n, 0.05, 6)
+        rng = np.random.default_rng(6)
+        start = np.stack([rng.permutation(np.repeat(np.arange(k), n // k)) for _ in range(pop)]).astype(np.int16)
+    else:
+        # half the population starts with a class of 127 (searched again), half balanced far below
+        n, k, pop, iters = 254, 4, 20, 500
+        e, adj = gnp_case(n, 0.2, 7)
+        start = oracle.init_colors(n, k, pop, 7)
+        for i in range(0, pop, 2):
+            start[i] = 0
+            start[i][127:] = np.random.default_rng(i).integers(1, k, size=n - 127)
+    g = device_graph(ctx, n, e)
+    gpu = _run_opts(ctx, g, k, start, iters, seed=8, gen=1, warps=4, trace=True, entry_bits=8)
+    ref16 = _run_opts(ctx, g, k, start, iters, seed=8, gen=1, warps=4, trace=True, entry_bits=16)
+    for key in ("col", "best_f", "moves", "trace"):
+        assert np.array_equal(gpu[key], ref16[key]), key
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 8, i, 1, True) for i in range(0, pop, 5)])
+    for i, r in zip(range(0, pop, 5), refs):
+        T = r["iters"]
+        assert np.array_equal(gpu["trace"][i, :T], r["trace"])
+        assert gpu["best_f"][i] == r["best_f"] and np.array_equal(gpu["col"][i], r["best_col"])
+
+
+def test_tabucol_u8_entries_on_the_benchmark_graph(ctx):
+    """The library's choice on G(500, 0.5), k = 48 is u8 entries (more individuals per SM); its
+    results equal the u16 kernel's and the oracle's."""
+    n, k, pop, iters = 500, 48, 1000, 3000
+    e, adj = gnp_case(n, 0.5, 0)
+    g = device_graph(ctx, n, e)
+    info = dlmcol.dlm_tabucol_launch_info(ctx, g, k, 4096)
+    assert info["grouped"] == 2 and info["groups"] > 4
+    start = oracle.init_colors(n, k, pop, 4)
+    a = _run_opts(ctx, g, k, start, iters, seed=4, work=True)
+    b = _run_opts(ctx, g, k, start, iters, seed=4, work=True, entry_bits=16)
+    for key in ("col", "best_f", "moves", "work"):
+        assert np.array_equal(a[key], b[key]), key
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 4, i, 0, False) for i in (0, 499, 999)])
+    for i, r in zip((0, 499, 999), refs):
+        assert a["best_f"][i] == r["best_f"] and np.array_equal(a["col"][i], r["best_col"])
 
 
 def test_tabucol_grouped_equals_legacy_path(ctx):
