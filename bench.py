@@ -1225,11 +1225,16 @@ def main():
     # bytes the kernel itself moves in shared memory: the grouped kernel keeps every row's colour,
     # gamma[v][col v] and class summaries in its owner thread's registers, so it evaluates a
     # conflicting row without touching shared memory; each neighbour of a moved vertex costs two
-    # u16 gamma read-modify-writes (8 B), and each move (the colour search of the moved vertex)
-    # and each row summarised again reads the row's gamma entries with their tabu flags (2 ks B,
-    # ks the row stride)
-    ks = 2 * ((K + 1) // 2 + (1 - ((K + 1) // 2) % 2))
-    kern_bytes = (8 * wk[1] + 2 * ks * (local_moves + wk[2])) / args.steps
+    # gamma read-modify-writes (4 e B, e the entry size: 2 B, or 1 B with u8 entries), and each
+    # move (the colour search of the moved vertex) and each row summarised again reads the row's
+    # gamma entries with their tabu flags (e ks B, ks the row stride in entries)
+    if launch["grouped"] == 2:
+        esz, epw = 1, 4
+    else:
+        esz, epw = 2, 2
+    kw = (K + epw - 1) // epw
+    ks = epw * (kw if kw % 2 else kw + 1)
+    kern_bytes = (4 * esz * wk[1] + esz * ks * (local_moves + wk[2])) / args.steps
     # L2: the moved vertex's adjacency bit row (ceil(n / 8) B per move) when the bit rows are not
     # held in shared memory
     l2_bytes = 0 if launch["bits_in_smem"] else ((N + 7) // 8) * local_moves / args.steps
