@@ -221,9 +221,11 @@ def recorded_traffic():
 
 
 def write_traffic(csv_path, command):
-    """Reads the ncu CSV of one tabu launch (dram__bytes_read.sum, dram__bytes_write.sum,
-    lts__t_bytes.sum, gpu__time_duration.sum; --print-units base) and writes the per-launch
-    counters with the hash of the kernel's source to profiles/tabucol_C2_dram.json."""
+    """Reads the ncu CSV of the tabu launches of one dlm_tabucol_batch call (dram__bytes_read.sum,
+    dram__bytes_write.sum, lts__t_bytes.sum, gpu__time_duration.sum; --print-units base; with u8
+    conflict-table entries the call is the u8 launch and the u16 pass over the individuals it gave
+    up) and writes their summed counters with the hash of the kernel's source to
+    profiles/tabucol_C2_dram.json."""
     import csv
 
     vals = {}
@@ -234,7 +236,7 @@ def write_traffic(csv_path, command):
             continue
         name = row.get("Metric Name")
         try:
-            vals[name] = float(row.get("Metric Value", "").replace(",", ""))
+            vals[name] = vals.get(name, 0.0) + float(row.get("Metric Value", "").replace(",", ""))
         except ValueError:
             pass
     need = ("dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum")
