@@ -546,6 +546,7 @@ struct TabuBatchArgs {
   int64_t iters;
   uint32_t ind_base;
   TabuRule rule;
+  const int32_t* only;  // [pop] or null: search only the individuals flagged here
 };
 
 // Two CTAs per SM up to 16 warps (64 registers a thread); a 32-warp CTA takes the SM's registers alone.
@@ -554,6 +555,7 @@ __global__ void __launch_bounds__(W * 32, W >= 32 ? 1 : 2) tabucol_batch_kernel(
   extern __shared__ __align__(16) uint8_t smem[];
   // one individual per CTA, or (when rows spill to a per-CTA slab) resident CTAs loop over them
   for (int i = blockIdx.x; i < a.pop; i += gridDim.x) {
+    if (a.only && a.only[i] == 0) continue;  // the same for every thread of the CTA
     TabuJob J;
     J.n = a.n; J.k = a.k; J.ks = a.ks; J.words = a.words; J.bits = a.bits;
     J.col = a.col + (size_t)i * a.n;
@@ -607,7 +609,8 @@ __global__ void __launch_bounds__(W * 32, W >= 32 ? 1 : 2) tabucol_multi_kernel(
 // host side
 // ------------------------------------------------------------------------------------------------
 template <int W>
-static dlm_status launch_batch(dlm_ctx* ctx, TabuBatchArgs a, size_t smem, size_t slab_stride) {
+static dlm_status launch_batch(dlm_ctx* ctx, TabuBatchArgs a, size_t smem, size_t slab_stride,
+                               uint16_t* slab_mem = nullptr) {
   auto kfn = tabucol_batch_kernel<W>;
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DLM_CUDA(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -616,8 +619,8 @@ static dlm_status launch_batch(dlm_ctx* ctx, TabuBatchArgs a, size_t smem, size_
     int per_sm = 0;
     DLM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, W * 32, smem));
     grid = std::min(a.pop, std::max(1, per_sm) * ctx->num_sms);
-    uint16_t* slab = nullptr;
-    DLM_TRY(ctx_workspace(ctx, (size_t)grid * slab_stride * 2, (void**)&slab));
+    uint16_t* slab = slab_mem;
+    if (!slab) DLM_TRY(ctx_workspace(ctx, (size_t)grid * slab_stride * 2, (void**)&slab));
     a.rule.slab = slab;
     a.rule.slab_stride = slab_stride;
   }
@@ -678,13 +681,90 @@ static int default_group_warps(int n) {
   return w;
 }
 
+// the one-individual-per-CTA launch of a batch (rows beyond shared memory in per-CTA slabs);
+// only: search just the individuals flagged there (null: all); slab_mem: the slabs, or null for the
+// context's workspace
+static dlm_status legacy_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
+                                uint32_t generation, uint32_t ind_base, int warps, int32_t* trace, int64_t* work,
+                                const int32_t* only, uint16_t* slab_mem) {
+  const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
+  if (L.rs < 1 || L.total > ctx->smem_optin)
+    return fail(ctx, DLM_EUNSUPPORTED, "tabucol: the per-individual arrays exceed shared memory per block");
+  const size_t slab_stride = L.rs < g->n ? tabu_slab_elems(g->n, k, L.rs) : 0;
+  TabuBatchArgs a;
+  a.n = g->n; a.k = k; a.ks = tabu_row_stride(k); a.words = g->words; a.pop = pop;
+  a.bits = g->d_bits; a.off = g->d_off; a.col = col; a.best_f = best_f; a.moves = moves; a.trace = trace;
+  a.work = work; a.iters = iters;
+  a.ind_base = ind_base;
+  a.only = only;
+  a.rule = TabuRule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
+                    ctx->smem_optin, nullptr, 0, ctx->cancel};
+  switch (warps) {
+    case 1: return launch_batch<1>(ctx, a, L.total, slab_stride, slab_mem);
+    case 2: return launch_batch<2>(ctx, a, L.total, slab_stride, slab_mem);
+    case 4: return launch_batch<4>(ctx, a, L.total, slab_stride, slab_mem);
+    case 8: return launch_batch<8>(ctx, a, L.total, slab_stride, slab_mem);
+    case 16: return launch_batch<16>(ctx, a, L.total, slab_stride, slab_mem);
+    default: return launch_batch<32>(ctx, a, L.total, slab_stride, slab_mem);
+  }
+}
+
+// bytes of the slabs legacy_launch uses for pop individuals (0 when every row fits)
+static size_t legacy_slab_bytes(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int warps) {
+  const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
+  if (L.rs < 1 || L.rs >= g->n) return 0;
+  int per_sm = 0;
+  switch (warps) {
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<1>, 32, L.total); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<2>, 64, L.total); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<4>, 128, L.total); break;
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<8>, 256, L.total); break;
+    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<16>, 512, L.total); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tabucol_batch_kernel<32>, 1024, L.total); break;
+  }
+  cudaGetLastError();
+  const size_t grid = (size_t)std::min(pop, std::max(1, per_sm) * ctx->num_sms);
+  return grid * tabu_slab_elems(g->n, k, L.rs) * 2;
+}
+
+// u8 entries where the u16 state exceeds one SM: the grouped u8 launch, then the one-individual-
+// per-CTA kernel over the individuals it gave up (a class grew beyond 126 vertices); both use one
+// workspace, so the flags survive between them
+static dlm_status tabucol_u8_then_legacy(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
+                                         int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure,
+                                         uint64_t seed, uint32_t generation, uint32_t ind_base, const GroupPlan& P,
+                                         int warps, int32_t* trace, int64_t* work) {
+  const int wl = warps ? warps : default_warps_batch(ctx, g->n, k);
+  const size_t gbytes = align16(group_far_bytes(ctx, g, k, pop, iters, tenure, P));
+  const size_t sbytes = legacy_slab_bytes(ctx, g, k, pop, wl);
+  uint8_t* ws = nullptr;
+  DLM_TRY(ctx_workspace(ctx, gbytes + sbytes + 16, (void**)&ws));
+  int32_t* redo = nullptr;
+  DLM_TRY(tabucol_group_launch(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base, P, trace,
+                               work, ws, &redo));
+  return legacy_launch(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base, wl, trace, work,
+                       redo, sbytes ? (uint16_t*)(ws + gbytes) : nullptr);
+}
+
 // the grouped kernel's plan for a problem: u16 gamma entries, or u8 entries when they fit more
 // individuals on an SM (eb = 0: that choice; 8 or 16: forced, u8 only where u16 also fits, for
 // the fallback)
+// legacy_fb (or null): u8 entries may also be taken where no u16 grouped plan exists; then
+// *legacy_fb is set and the caller searches the individuals the u8 launch gives up with the
+// one-individual-per-CTA kernel
 static bool choose_group_plan(dlm_ctx* ctx, const dlm_graph* g, int k, int pop, int W, int ring, int eb,
-                              GroupPlan* out) {
+                              GroupPlan* out, bool* legacy_fb = nullptr) {
   GroupPlan P16, P8;
-  if (!group_plan(g->n, k, g->words, W, ctx->smem_optin, pop, ctx->num_sms, ring, 16, &P16)) return false;
+  if (legacy_fb) *legacy_fb = false;
+  if (!group_plan(g->n, k, g->words, W, ctx->smem_optin, pop, ctx->num_sms, ring, 16, &P16)) {
+    if (!legacy_fb || eb == 16 || ring || k > 128 ||
+        !group_plan(g->n, k, g->words, W, ctx->smem_optin, pop, ctx->num_sms, 0, 8, &P8))
+      return false;
+    *legacy_fb = true;
+    *out = P8;
+    return true;
+  }
   if (eb == 16) { *out = P16; return true; }
   const bool ok8 = k <= 128 && group_plan(g->n, k, g->words, W, ctx->smem_optin, pop, ctx->num_sms, ring, 8, &P8);
   if (eb == 8) {
@@ -713,37 +793,24 @@ static dlm_status tabucol_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32
     // several individuals per CTA, tabu flags inside gamma: whenever one individual's state fits
     const int wg = warps ? warps : default_group_warps(g->n);
     GroupPlan P;
-    if (choose_group_plan(ctx, g, k, pop, wg, ring, eb, &P)) {
+    bool legacy_fb = false;
+    if (choose_group_plan(ctx, g, k, pop, wg, ring, eb, &P, &legacy_fb)) {
       const uint64_t tt_max =
           (uint64_t)tenure.L_max + ((uint64_t)tenure.alpha_num * (uint64_t)g->m) / (uint64_t)tenure.alpha_den;
       if ((uint64_t)iters + tt_max + 2 >= (1ull << 32))
         return fail(ctx, DLM_EUNSUPPORTED, "tabucol: budget plus the longest tenure must stay below 2^32");
-      return tabucol_group_launch(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base, P,
-                                  trace, work);
+      if (!legacy_fb)
+        return tabucol_group_launch(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base, P,
+                                    trace, work);
+      return tabucol_u8_then_legacy(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base, P,
+                                    warps, trace, work);
     }
     if (ring) return fail(ctx, DLM_EINVAL, "tabucol: the requested tabu ring does not fit in shared memory");
     if (eb) return fail(ctx, DLM_EINVAL, "tabucol: the requested gamma entries do not fit in shared memory");
   }
   if (warps == 0) warps = default_warps_batch(ctx, g->n, k);
-  const TabuSmem L = tabu_smem_layout(g->n, k, warps, ctx->smem_optin);
-  if (L.rs < 1 || L.total > ctx->smem_optin)
-    return fail(ctx, DLM_EUNSUPPORTED, "tabucol: the per-individual arrays exceed shared memory per block");
-  const size_t slab_stride = L.rs < g->n ? tabu_slab_elems(g->n, k, L.rs) : 0;
-  TabuBatchArgs a;
-  a.n = g->n; a.k = k; a.ks = tabu_row_stride(k); a.words = g->words; a.pop = pop;
-  a.bits = g->d_bits; a.off = g->d_off; a.col = col; a.best_f = best_f; a.moves = moves; a.trace = trace;
-  a.work = work; a.iters = iters;
-  a.ind_base = ind_base;
-  a.rule = TabuRule{(uint32_t)tenure.L_max + 1u, tenure.alpha_num, tenure.alpha_den, seed, generation, ctx->d_status,
-                    ctx->smem_optin, nullptr, 0, ctx->cancel};
-  switch (warps) {
-    case 1: return launch_batch<1>(ctx, a, L.total, slab_stride);
-    case 2: return launch_batch<2>(ctx, a, L.total, slab_stride);
-    case 4: return launch_batch<4>(ctx, a, L.total, slab_stride);
-    case 8: return launch_batch<8>(ctx, a, L.total, slab_stride);
-    case 16: return launch_batch<16>(ctx, a, L.total, slab_stride);
-    default: return launch_batch<32>(ctx, a, L.total, slab_stride);
-  }
+  return legacy_launch(ctx, g, k, pop, col, best_f, moves, iters, tenure, seed, generation, ind_base, warps, trace,
+                       work, nullptr, nullptr);
 }
 
 }  // namespace dlm
@@ -770,7 +837,8 @@ extern "C" dlm_status dlm_tabucol_launch_info(dlm_ctx* ctx, const dlm_graph* g, 
   if (!ctx || !g || !info || pop <= 0 || k < 2 || k > 128) return fail(ctx, DLM_EINVAL, "launch_info: bad arguments");
   if (warps == 0) warps = lookup_tune(ctx, g->n, k);
   GroupPlan P;
-  if (choose_group_plan(ctx, g, k, pop, warps ? warps : default_group_warps(g->n), 0, 0, &P)) {
+  bool legacy_fb = false;
+  if (choose_group_plan(ctx, g, k, pop, warps ? warps : default_group_warps(g->n), 0, 0, &P, &legacy_fb)) {
     const int grid = group_grid(ctx, P, pop);
     const int32_t v[8] = {P.eb == 8 ? 2 : 1, P.W, P.G, P.R, P.per, P.bsm ? 1 : 0, grid, grid * P.G};
     for (int i = 0; i < 8; ++i) info[i] = v[i];

@@ -991,7 +991,7 @@ size_t group_far_bytes(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop,
 dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                 int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                                 uint32_t generation, uint32_t ind_base, const GroupPlan& P, int32_t* trace,
-                                int64_t* work, void* far_mem) {
+                                int64_t* work, void* far_mem, int32_t** redo_out) {
   GroupArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = g->n; a.k = k; a.ks = P.eb == 8 ? group_row_stride8(k) : group_row_stride(k); a.words = g->words; a.pop = pop;
@@ -1019,7 +1019,9 @@ dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
   // u8 entries, then a u16 pass over the individuals the u8 launch gave up (their start colourings
   // are untouched; the same random streams give the same searches)
   GroupPlan F;
-  if (!fallback_plan(ctx, g, k, pop, P, &F)) return fail(ctx, DLM_EUNSUPPORTED, "tabucol: no u16 plan for the fallback");
+  const bool have_f = fallback_plan(ctx, g, k, pop, P, &F);
+  if (!have_f && !redo_out) return fail(ctx, DLM_EUNSUPPORTED, "tabucol: no u16 plan for the fallback");
+  if (!have_f) F = P;  // the caller searches the flagged individuals (one-individual-per-CTA kernel)
   const size_t far16 = std::max(far_bytes_of(ctx, g, k, pop, iters, tenure, P), far_bytes_of(ctx, g, k, pop, iters, tenure, F));
   int32_t* redo = (int32_t*)(scratch + a16(far16));
   DLM_CUDA(ctx, cudaMemsetAsync(redo, 0, (size_t)pop * 4, ctx->stream));
@@ -1027,6 +1029,10 @@ dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int
   a.redo_mode = 1;
   if (P.per == 2) DLM_TRY((launch_per<2, 8>(ctx, a, P, (uint2*)scratch)));
   else DLM_TRY((launch_per<4, 8>(ctx, a, P, (uint2*)scratch)));
+  if (!have_f) {
+    *redo_out = redo;
+    return DLM_OK;
+  }
   GroupArgs b = a;
   b.ks = group_row_stride(k);
   b.G = F.G; b.R = F.R; b.W = F.W; b.per = F.per;

@@ -72,7 +72,10 @@ int group_grid(dlm_ctx* ctx, const GroupPlan& plan, int pop);
 dlm_status tabucol_group_launch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                 int64_t* best_f, int64_t* moves, int64_t iters, dlm_tenure tenure, uint64_t seed,
                                 uint32_t generation, uint32_t ind_base, const GroupPlan& plan, int32_t* trace,
-                                int64_t* work, void* far_mem = nullptr);
+                                int64_t* work, void* far_mem = nullptr, int32_t** redo_out = nullptr);
+// (redo_out: with u8 entries and no u16 plan of the grouped kernel, only the u8 pass runs and
+// *redo_out receives the device flags [pop] of the individuals it gave up, for the caller to
+// search with the one-individual-per-CTA kernel)
 // bytes of far-list memory a launch needs (0 when every tenure fits the ring); far_mem of
 // tabucol_group_launch: that much device memory, or null to take it from the context's workspace
 int64_t group_far_cap(const dlm_graph* g, int32_t k, int64_t iters, dlm_tenure tenure, const GroupPlan& plan);

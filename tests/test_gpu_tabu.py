@@ -377,6 +377,33 @@ def test_tabucol_u8_entries_fall_back_to_u16(ctx, case):
         assert gpu["best_f"][i] == r["best_f"] and np.array_equal(gpu["col"][i], r["best_col"])
 
 
+@pytest.mark.parametrize("n,k,pop,iters,dens", [(1000, 128, 64, 1500, 0.5), (2048, 100, 24, 600, 0.1)])
+def test_tabucol_u8_on_chip_beyond_the_u16_state(ctx, n, k, pop, iters, dens):
+    """States whose u16 conflict table exceeds one SM (n = 1000, k = 128: 266 KB; n = 2048,
+    k = 100: 418 KB) run on chip with u8 entries; the individuals a u8 launch gives up (here every
+    other one starts with a class of 127 vertices) are searched by the one-individual-per-CTA
+    kernel with its L2 slab. Results, moves and traces equal that kernel's on every individual and
+    the oracle's on a sample."""
+    e, adj = gnp_case(n, dens, 9)
+    g = device_graph(ctx, n, e)
+    info = dlmcol.dlm_tabucol_launch_info(ctx, g, k, pop)
+    assert info["grouped"] == 2
+    start = oracle.init_colors(n, k, pop, 9)
+    for i in range(0, pop, 2):
+        start[i][:127] = 0
+        start[i][127:] = np.random.default_rng(i).integers(1, k, size=n - 127)
+    a = _run_opts(ctx, g, k, start, iters, seed=9, gen=1, trace=True)
+    b = _run_opts(ctx, g, k, start, iters, seed=9, gen=1, trace=True, legacy=1)
+    for key in ("col", "best_f", "moves", "trace"):
+        assert np.array_equal(a[key], b[key]), key
+    sample = [0, 1, pop - 1]
+    refs = oracle_tabu_many([(adj, k, start[i], iters, 9, i, 1, True) for i in sample])
+    for i, r in zip(sample, refs):
+        T = r["iters"]
+        assert np.array_equal(a["trace"][i, :T], r["trace"])
+        assert a["best_f"][i] == r["best_f"] and np.array_equal(a["col"][i], r["best_col"])
+
+
 def test_tabucol_u8_entries_on_the_benchmark_graph(ctx):
     """The library's choice on G(500, 0.5), k = 48 is u8 entries (more individuals per SM); its
     results equal the u16 kernel's and the oracle's."""
