@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--mem-graph", default="planted", choices=["planted", "gnp"],
                     help="planted k-colourable (p = 0.5 across parts) or uniform random G(n, 0.5)")
     ap.add_argument("--mem-seeds", type=int, default=10)
+    ap.add_argument("--mem-log", default=None,
+                    help="append one JSON line per generation (mode, seed, generation, elapsed s, best, the "
+                         "dlm_memetic_stats diagnostics) to this file (memetic and wvcp_memetic workloads)")
     ap.add_argument("--mem-max-gens", type=int, default=40)
     ap.add_argument("--mem-time-limit", type=float, default=120.0, help="seconds per run")
     ap.add_argument("--wm-pop", type=int, default=8192)
@@ -307,6 +310,16 @@ class Clocks:
 # ------------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------------
+def log_generation(path, workload, mode, seed, gen, elapsed, best, diag):
+    """One JSON line per memetic generation (the per-generation prediction and population
+    diagnostics of section "Analysis of the contributions of deep learning")."""
+    if not path:
+        return
+    with open(path, "a") as fh:
+        fh.write(json.dumps({"workload": workload, "mode": mode, "seed": seed, "generation": gen,
+                             "elapsed_s": round(elapsed, 4), "best": int(best), **diag}) + "\n")
+
+
 def run_memetic(args):
     """Learned-guided vs random-GPX memetic search (Algorithm 1 and the ablation of section
     "Benefits of the neural network based crossover selection") on a planted 48-colourable graph:
@@ -343,6 +356,7 @@ def run_memetic(args):
                 # diagnostics read after the timing of the generation (they wait for the stream)
                 st = dlmcol.dlm_memetic_stats(ctx, mm)
                 diag.append({key: (None if v != v else round(v, 4)) for key, v in st.items()})
+                log_generation(args.mem_log, "memetic", mode, 1000 + seed, gen, el, best, diag[-1])
                 t0 += time.perf_counter() - t0 - el  # the diagnostics' read is not search time
                 if best <= args.mem_target:
                     hit = el
@@ -482,6 +496,7 @@ def run_wvcp_memetic(args):
                 traj.append([round(el, 3), int(best)])
                 st = dlmcol.dlm_memetic_stats(ctx, mm)
                 diag.append({key: (None if v != v else round(v, 4)) for key, v in st.items()})
+                log_generation(args.mem_log, "wvcp_memetic", mode, seed, gen, el, best, diag[-1])
                 t0 += time.perf_counter() - t0 - el  # the diagnostics' read is not search time
                 if el > args.wm_time:
                     break

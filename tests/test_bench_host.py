@@ -36,3 +36,40 @@ def test_pool_work_matches_a_direct_count(seed):
     DP = D[sel][:, sel].astype(np.int64)
     close = ((10 * DP <= n) & np.tril(np.ones((p, p), bool), -1)).any(axis=1)
     assert bench.pool_work(p, fit, sel, close) == _direct(p, n, fit, D)
+
+
+def test_traffic_record_sums_the_launches_of_one_call(tmp_path, monkeypatch):
+    """--traffic-from sums the DRAM counters of every tabu launch of one call (the u8 launch and
+    the u16 pass) and keys the record by the kernel source hash; other kernels are ignored."""
+    csv = tmp_path / "dram.csv"
+    rows = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    for i, (kern, rd, wr, t) in enumerate([("void tabucol_group_kernel<4, 1, 8>(GroupArgs)", 4661760, 35840, 1770046464),
+                                           ("void tabucol_group_kernel<4, 0, 16>(GroupArgs)", 84992, 0, 7264),
+                                           ("k_smem_probe(int, uint4 *)", 999, 999, 999)]):
+        rows += [f'"{i}","{kern}","dram__bytes_read.sum","byte","{rd}"',
+                 f'"{i}","{kern}","dram__bytes_write.sum","byte","{wr}"',
+                 f'"{i}","{kern}","gpu__time_duration.sum","ns","{t}"']
+    csv.write_text("==PROF== header line\n" + "\n".join(rows) + "\n")
+    out = tmp_path / "rec.json"
+    monkeypatch.setattr(bench, "TRAFFIC_JSON", str(out))
+    bench.write_traffic(str(csv), "ncu ...")
+    import json
+
+    rec = json.loads(out.read_text())
+    assert rec["dram_read_bytes"] == 4661760 + 84992 and rec["dram_write_bytes"] == 35840
+    assert rec["dram_bytes_per_launch"] == 4661760 + 84992 + 35840
+    assert rec["duration_ns"] == 1770046464 + 7264
+    assert rec["kernel_source_sha256_16"] == bench.tabu_source_hash()
+    assert bench.recorded_traffic() == rec
+
+
+def test_generation_log_lines(tmp_path):
+    path = tmp_path / "gens.jsonl"
+    bench.log_generation(str(path), "memetic", "learned", 1000, 0, 0.51234, 17, {"pred_pearson": None, "f_mean": 3.5})
+    bench.log_generation(str(path), "memetic", "learned", 1000, 1, 1.0, 0, {"pred_pearson": 0.7, "f_mean": 1.0})
+    bench.log_generation(None, "memetic", "learned", 1000, 2, 1.5, 0, {})
+    import json
+
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert [x["generation"] for x in lines] == [0, 1]
+    assert lines[0]["elapsed_s"] == 0.5123 and lines[1]["pred_pearson"] == 0.7 and lines[0]["best"] == 17
