@@ -9,10 +9,14 @@ dlm_tabucol_batch. value = tabu moves (iterations that moved) of all GPUs / devi
 
 Under torchrun each rank runs its own 4096 individuals (weak scaling, no data-path collective).
 --impl reference times the CPU oracle (the plain C++ statement of the method) on the host cores.
+The default run also compares learned and random GPX selection (the metric's second half) in two
+child processes: time to a legal colouring on the planted k-COL workload (memetic_time_to_target)
+and the best WVCP score at a fixed wall time on the weighted one (wvcp_memetic_score_at_wall);
+--no-memetic leaves both out.
 
 Other workloads (one JSON line each, single GPU):
   --workload memetic  learned vs random GPX time to a legal colouring, planted n = 1000, k = 48
-  --workload multi    the uneven 64-graph batch in one persistent launch replayed from a CUDA graph
+  --workload multi    the uneven 64-graph batch (one grouped launch per graph) replayed from a CUDA graph
   --workload wvcp     the weighted feasible/infeasible tabu search, G(1000, 0.5), weights 1..100
   --workload scorer   one learned generation's scoring and training with the tensor-core roofline
   --workload wvcp_iterated  Algorithm 2 (iterated weighted search with the adaptive penalty)
@@ -105,6 +109,8 @@ def parse():
     ap.add_argument("--wm-seeds", type=int, default=3)
     ap.add_argument("--wm-time", type=float, default=60.0, help="wall budget per run, seconds")
     ap.add_argument("--wm-max-gens", type=int, default=400)
+    ap.add_argument("--wm-short-seeds", type=int, default=2, help="seeds of the default run's weighted comparison")
+    ap.add_argument("--wm-short-time", type=float, default=15.0, help="wall budget per run of that comparison, s")
     ap.add_argument("--dn-problem", default="col", choices=["col", "wvcp"])
     ap.add_argument("--dn-cands", type=int, default=1024)
     ap.add_argument("--dn-samples", type=int, default=500)
@@ -402,6 +408,26 @@ def memetic_compare(args):
             "random_gpx_median_s": d["random_gpx"], "learned_over_random": d["learned_over_random"],
             "config": d["config"], "summary": d["summary"],
             "per_seed_s": {m: [x["time_to_target_s"] for x in d["runs"][m]] for m in d["runs"]}}
+
+
+def wvcp_memetic_compare(args):
+    """run_wvcp_memetic on the weighted workload (G(1000, 0.5), weights 1..100, population
+    8192) with a short wall budget, as a child process: the learned and random modes' best WVCP
+    scores at fixed wall time (per-seed trajectories left out)."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", "wvcp_memetic", "--wm-seeds", str(args.wm_short_seeds),
+           "--wm-time", str(args.wm_short_time)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # reported, never fatal to the headline
+        return {"error": f"{type(exc).__name__}: {exc}"}
+    sm = d["summary"]
+    return {"metric": d["metric"], "unit": d["unit"], "higher_is_better": False,
+            "learned_median_best": d["value"], "random_gpx_median_best": d["random_gpx"],
+            "level": d["level"], "config": d["config"],
+            "per_seed_best": {m: sm[m]["per_seed_best"] for m in sm},
+            "time_to_level_s": {m: sm[m]["time_to_level_s"] for m in sm},
+            "median_generations": {m: sm[m]["median_generations"] for m in sm}}
 
 
 def memetic_summary(runs, wall_points=(0.5, 1.0, 1.5, 2.0)):
@@ -1318,18 +1344,20 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args)
-    memetic = None
+    memetic = wmem = None
     if rank == 0 and world == 1 and not args.no_memetic and pop == POP and iters == ITERS:
         # the second half of the metric: learned selection against random GPX on the learned
         # workload (planted 48-colourable n = 1000, population 8192), 10 seeds per mode
         memetic = memetic_compare(args)
+        # and on the weighted workload, where the memetic search has more to do
+        wmem = wvcp_memetic_compare(args)
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "int16/int32", "data": "synthetic",
                "config": config(args, {"smem_probe_gbps": smem_gbps}), "roofline": roofline,
                "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": args.steps,
-               "moves": tot_moves, "memetic_time_to_target": memetic}
+               "moves": tot_moves, "memetic_time_to_target": memetic, "wvcp_memetic_score_at_wall": wmem}
         print(json.dumps(out), flush=True)
     g.close()
     ctx.close()
