@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--mem-graph", default="planted", choices=["planted", "gnp"],
                     help="planted k-colourable (p = 0.5 across parts) or uniform random G(n, 0.5)")
     ap.add_argument("--mem-seeds", type=int, default=10)
+    ap.add_argument("--wvcp-entry-bits", type=int, default=0, choices=(0, 8, 16),
+                    help="--workload wvcp: conflict-table entry size (0: the library's choice)")
     ap.add_argument("--mem-log", default=None,
                     help="append one JSON line per generation (mode, seed, generation, elapsed s, best, the "
                          "dlm_memetic_stats diagnostics) to this file (memetic and wvcp_memetic workloads)")
@@ -746,9 +748,15 @@ def run_wvcp(args):
     fc = torch.empty((pop, 2), dtype=torch.int64, device="cuda")
     mv = torch.empty(pop, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
+    eb = args.wvcp_entry_bits or dlmcol.dlm_wvcp_entry_bits(ctx, g, k)
+
+    def search():
+        dlmcol.dlm_wvcp_tabu_batch_ex(ctx, g, k, pop, col, bg, fc, mv, iters, dlmcol.WVCP_TENURE, phi, SEED, 0, 0,
+                                      None, eb)
+
     for _ in range(args.warmup):
         col.copy_(col0)
-        dlmcol.dlm_wvcp_tabu_batch(ctx, g, k, pop, col, bg, fc, mv, iters, dlmcol.WVCP_TENURE, phi, SEED, 0, 0)
+        search()
     ctx.sync()
     f0 = None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -759,7 +767,7 @@ def run_wvcp(args):
     moves = 0
     for _ in range(args.steps):
         col.copy_(col0)
-        dlmcol.dlm_wvcp_tabu_batch(ctx, g, k, pop, col, bg, fc, mv, iters, dlmcol.WVCP_TENURE, phi, SEED, 0, 0)
+        search()
         moves += int(mv.sum())
     e1.record(stream)
     torch.cuda.synchronize()
@@ -768,16 +776,19 @@ def run_wvcp(args):
     ms = e0.elapsed_time(e1)
     legal = fc[:, 1] == 0
     best_legal = int(fc[legal, 0].min()) if bool(legal.any()) else None
-    # algorithmic work per iteration: every (v, c) pair reads one gamma entry (2 B); iterations
-    # are counted by their moves (an iteration without an admissible move is not counted)
+    # algorithmic work per iteration: every (v, c) pair reads one gamma entry (1 B with u8
+    # entries, 2 B with u16); iterations are counted by their moves (an iteration without an
+    # admissible move is not counted)
     pairs = n * (k - 1)
+    eb_bytes = eb // 8
     smem_gbps = dlmcol.dlm_probe_smem_bandwidth(ctx)
-    ach = 2.0 * pairs * moves / (ms / 1e3) / 1e9
+    ach = eb_bytes * pairs * moves / (ms / 1e3) / 1e9
+    where = ("the whole conflict table in shared memory (u8 entries)" if eb == 8 else
+             "u16 entries: the conflict table's last colours live in an L2-resident slab")
     roof = {"bound": "smem", "achieved": ach, "peak": smem_gbps, "unit": "GB/s", "frac": ach / smem_gbps,
             "traffic": None, "kernel": "k_wvcp_tabu", "kernel_ms": ms / args.steps,
-            "algorithmic_bytes_per_launch": 2.0 * pairs * moves / args.steps,
-            "peak_source": "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads); the "
-                           "conflict table's last colours live in an L2-resident slab"}
+            "algorithmic_bytes_per_launch": eb_bytes * pairs * moves / args.steps, "entry_bits": eb,
+            "peak_source": "measured by dlm_probe_smem_bandwidth on this GPU (conflict-free 16 B loads); " + where}
     out = {"metric": "weighted tabu moves/s, G(1000, 0.5), weights 1..100", "workload": "wvcp",
            "value": moves / (ms / 1e3), "unit": "moves/s", "higher_is_better": True, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "gpu_launches": args.steps, "clocks": ck,

@@ -489,11 +489,21 @@ dlm_status dlm_wvcp_tabu_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int3
                                int64_t* best_g, int64_t* best_fc, int64_t* moves, int64_t iters, dlm_tenure tenure,
                                int64_t phi, uint64_t seed, uint32_t generation, uint32_t ind_base);
 /* As dlm_wvcp_tabu_batch with a per-iteration trace: device [pop][iters][4] int32 of
- * (v, c', delta, #ties), (-1, -1, 0, 0) for an iteration without a move. */
+ * (v, c', delta, #ties), (-1, -1, 0, 0) for an iteration without a move, or NULL; and the entry
+ * size of the per-individual conflict table: 0 automatic (as dlm_wvcp_entry_bits reports), 8 or
+ * 16. With 8-bit entries the whole table stays in shared memory; an individual whose start
+ * colouring has a class of more than 255 vertices, or whose search would grow one past 255, is
+ * searched again from its start colouring with 16-bit entries (same draws, same result). 16 puts
+ * the colours that do not fit shared memory in an L2-resident slab per CTA. 8 returns
+ * DLM_EUNSUPPORTED when the u8 table does not fit. The result never depends on the entry size. */
 dlm_status dlm_wvcp_tabu_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                   int64_t* best_g, int64_t* best_fc, int64_t* moves, int64_t iters,
                                   dlm_tenure tenure, int64_t phi, uint64_t seed, uint32_t generation,
-                                  uint32_t ind_base, int32_t* trace);
+                                  uint32_t ind_base, int32_t* trace, int32_t entry_bits);
+/* The entry size (8 or 16; 0 when the state does not fit at all) the weighted tabu search takes
+ * on graph g with k colours: 8 when only 8-bit entries keep the whole conflict table in shared
+ * memory, else 16.   bits  host int32 out. */
+dlm_status dlm_wvcp_entry_bits(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t* bits);
 
 /* Parallel iterated feasible and infeasible tabu search (Algorithm 2): max_ls (paper: 10, at most
  * 16) successive searches of iters iterations (paper: 10 |V|) per individual, each from the

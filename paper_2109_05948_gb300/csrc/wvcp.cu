@@ -12,10 +12,14 @@
 //    only the keys of colours a and b (gamma of the neighbours, the two class maxima), which
 //    update the summaries in O(1) per row; a row whose only minimum key rose, and the moved
 //    vertex's row, are scanned again;
-//  * gamma is stored transposed, gT[c][v] (u16), so that thread t scanning vertices t, t + 512, ...
-//    reads consecutive addresses across the warp; the first Cs colours live in shared memory, the
-//    rest in an L2-resident slab of global memory owned by the CTA (n * k * 2 bytes exceeds one
-//    SM's shared memory for the benchmarked graphs);
+//  * gamma is stored transposed, gT[c][v], so that thread t scanning vertices t, t + 512, ...
+//    reads consecutive addresses across the warp. With u8 entries the whole table stays in shared
+//    memory (n * k bytes: 144 KB at n = 1000, k = 144); gamma[v][c] never exceeds the size of class
+//    c, so u8 is exact while every class holds at most 255 vertices: the u8 search of an individual
+//    gives up (at set-up, or before the move that would grow a class past 255) and a u16 pass
+//    searches the individuals it gave up from their start colourings, with the same draws, hence
+//    the same result. With u16 entries the first Cs colours live in shared memory and the rest in
+//    an L2-resident slab of global memory owned by the CTA;
 //  * class maxima are kept exactly by per-class counts per weight level plus a level bitmask, so
 //    max1, its multiplicity and the second largest weight come from two bit scans after a move;
 //  * ties: the j-th admissible minimum in (v ascending, c ascending) order, found by a block
@@ -30,16 +34,18 @@ namespace dlm {
 
 constexpr int kWThreads = 512;
 constexpr int kWWarps = kWThreads / 32;
+constexpr uint32_t kWClass8 = 255;  // largest class the u8 conflict table holds exactly
 
 struct WvcpLayout {
-  size_t col, best, w, fz, lvl, lmask, info, max1, rmin, rcnt, skey, scnt, red, gT, total;
+  size_t col, best, w, fz, lvl, lmask, info, max1, csz, rmin, rcnt, skey, scnt, red, gT, total;
   int npad, lw, cs;  // vertices padded to 8, mask words per class, colours held in shared memory
 };
 
 __host__ __device__ inline size_t wal16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// as many colours in shared memory as `budget` allows (the rest go to the CTA's global slab)
-__host__ __device__ inline WvcpLayout wvcp_layout(int n, int k, int wmax, size_t budget) {
+// as many colours in shared memory as `budget` allows (the rest go to the CTA's global slab);
+// eb = bytes per conflict-table entry (1 or 2)
+__host__ __device__ inline WvcpLayout wvcp_layout(int n, int k, int wmax, size_t budget, int eb) {
   WvcpLayout L;
   L.npad = (n + 7) & ~7;
   L.lw = (wmax + 32) / 32;  // levels 0..wmax
@@ -52,13 +58,14 @@ __host__ __device__ inline WvcpLayout wvcp_layout(int n, int k, int wmax, size_t
   L.lmask = o; o += wal16((size_t)k * L.lw * 4);
   L.info = o; o += wal16((size_t)k * 4);
   L.max1 = o; o += wal16((size_t)k);
+  L.csz = o; o += wal16((size_t)k * 4);
   L.rmin = o; o += wal16((size_t)n * 4);
   L.rcnt = o; o += wal16((size_t)n * 2);
   L.skey = o; o += wal16((size_t)n * 4);
   L.scnt = o; o += wal16((size_t)n * 2);
   L.red = o; o += 1024;  // 2 kWWarps + 8 ints, then 8 + 2 kWWarps long longs; 2 ints at byte 896
   L.gT = o;
-  const size_t per_col = (size_t)L.npad * 2;
+  const size_t per_col = (size_t)L.npad * eb;
   size_t cs = budget > o ? (budget - o) / per_col : 0;
   if (cs > (size_t)k) cs = k;
   L.cs = (int)cs;
@@ -76,7 +83,9 @@ struct WvcpArgs {
   int64_t* best_fc;
   int64_t* moves;
   int32_t* trace;
-  uint16_t* slab;  // per CTA: (k - cs) * npad u16
+  void* slab;      // per CTA: (k - cs) * npad entries
+  int32_t* redo;   // [pop]: individuals the u8 search gave up
+  int32_t redo_mode;  // 0: every individual; 1: u8 search, flags what it gives up; 2: flagged only
   int64_t iters;
   int64_t phi;             // penalty (g = fscale f + phi c), or per individual from phi_arr
   const int64_t* phi_arr;  // [pop] or null
@@ -115,14 +124,6 @@ __device__ __forceinline__ void class_add(uint16_t* lvl, uint32_t* lmask, int lw
   else *m &= ~(1u << (w & 31));
 }
 
-__device__ __forceinline__ void wvcp_scan_key(int c, int o, int wv, int m1c, int base, int64_t phi, int gc, bool frozen,
-                                              int thr, int& km, int& kc, int fs) {
-  const int d = base + fs * (wv > m1c ? wv - m1c : 0) + (int)phi * gc;
-  const int key = (c != o && (!frozen || d < thr)) ? d : INT_MAX;
-  if (key < km) { km = key; kc = 1; }
-  else if (key == km && key != INT_MAX) ++kc;
-}
-
 // key of colour c for row v: the weight term of joining class c plus phi times gamma[v][c]
 __device__ __forceinline__ int wvcp_key(int fs, int wv, int m1c, int phi, int gc) {
   return fs * (wv > m1c ? wv - m1c : 0) + phi * gc;
@@ -146,8 +147,9 @@ __device__ __forceinline__ bool wvcp_summ_apply(int& km, int& kc, int kold, int 
 
 // minimum key of row v over the colours c != o and how many colours reach it (in colour order:
 // the shared-memory colours, then the slab colours sixteen loads at a time)
-__device__ __forceinline__ void wvcp_row_summary(int v, int o, int wv, const uint8_t* max1s, const uint16_t* gS,
-                                                 const uint16_t* gG, int npad, int cs, int k, int fs, int phi,
+template <typename G>
+__device__ __forceinline__ void wvcp_row_summary(int v, int o, int wv, const uint8_t* max1s, const G* gS,
+                                                 const G* gG, int npad, int cs, int k, int fs, int phi,
                                                  int& km, int& kc) {
   km = INT_MAX;
   kc = 0;
@@ -169,10 +171,29 @@ __device__ __forceinline__ void wvcp_row_summary(int v, int o, int wv, const uin
   for (; c < k; ++c) take(c, gG[(size_t)(c - cs) * npad + v]);
 }
 
+// the same summary computed by a warp: lane l takes the colours l, l + 32, ...; the minimum and
+// its count do not depend on the order the colours are taken in
+template <typename G>
+__device__ __forceinline__ void wvcp_row_summary_warp(int v, int o, int wv, const uint8_t* max1s, const G* gS,
+                                                      const G* gG, int npad, int cs, int k, int fs, int phi, int lane,
+                                                      int& km, int& kc) {
+  int lm = INT_MAX, lc = 0;
+  for (int c = lane; c < k; c += 32) {
+    if (c == o) continue;
+    const int gc = c < cs ? gS[(size_t)c * npad + v] : gG[(size_t)(c - cs) * npad + v];
+    const int key = wvcp_key(fs, wv, max1s[c], phi, gc);
+    if (key < lm) { lm = key; lc = 1; }
+    else if (key == lm) ++lc;
+  }
+  km = __reduce_min_sync(0xFFFFFFFFu, lm);
+  kc = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)(lm == km ? lc : 0));
+}
+
+template <typename G>
 __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int n = a.n, k = a.k, wmax = a.wmax, nwords = a.words;
-  const WvcpLayout L = wvcp_layout(n, k, wmax, a.smem_budget);
+  const WvcpLayout L = wvcp_layout(n, k, wmax, a.smem_budget, (int)sizeof(G));
   const int npad = L.npad, lw = L.lw, cs = L.cs;
   uint8_t* colS = smem + L.col;
   uint8_t* bestS = smem + L.best;
@@ -182,6 +203,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   uint32_t* lmask = (uint32_t*)(smem + L.lmask);
   uint32_t* info = (uint32_t*)(smem + L.info);
   uint8_t* max1s = smem + L.max1;
+  uint32_t* csz = (uint32_t*)(smem + L.csz);  // class sizes
   int32_t* rmin = (int32_t*)(smem + L.rmin);
   uint16_t* rcnt = (uint16_t*)(smem + L.rcnt);
   int32_t* skey = (int32_t*)(smem + L.skey);   // per row: minimum key over the colours c != col v
@@ -191,8 +213,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   int32_t* sc = red + 2 * kWWarps;          // mv, old, new, improved, error, bad input, r0, r1
   // g, conf, best g, best f, best conf; from 8: per-warp conflict and score partial sums
   long long* sc64 = (long long*)(red + 2 * kWWarps + 8);
-  uint16_t* gS = (uint16_t*)(smem + L.gT);
-  uint16_t* gG = a.slab + (size_t)blockIdx.x * (size_t)(k - cs) * npad;
+  G* gS = (G*)(smem + L.gT);
+  G* gG = (G*)a.slab + (size_t)blockIdx.x * (size_t)(k - cs) * npad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int fs = a.fscale;
   int per = (n + kWThreads - 1) / kWThreads;
@@ -204,6 +226,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   const uint32_t slice_mask = per == 32 ? 0xFFFFFFFFu : ((1u << per) - 1u);
 
   for (int ind = blockIdx.x; ind < a.pop; ind += gridDim.x) {
+    if (a.redo_mode == 2 && a.redo[ind] == 0) continue;
     int16_t* gcol = a.col + (size_t)ind * n;
     const int64_t phi = a.phi_arr ? a.phi_arr[ind] : a.phi;
     // ---- set-up ---------------------------------------------------------------------------
@@ -215,6 +238,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         if (c < cs) gS[(size_t)c * npad + v] = 0;
         else gG[(size_t)(c - cs) * npad + v] = 0;
       }
+      for (int c = tid; c < k; c += kWThreads) csz[c] = 0u;
       if (tid < 8) sc[tid] = 0;
     }
     __syncthreads();
@@ -228,12 +252,21 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
       fz[v] = 0;
       const int q = c * (wmax + 1) + w;
       atomicAdd((uint32_t*)lvl + (q >> 1), 1u << (16 * (q & 1)));
+      atomicAdd(csz + c, 1u);
     }
     __syncthreads();
     if (sc[5]) {
       if (tid == 0) raise_status(a.status, DLM_EINVAL);
       __syncthreads();
       continue;
+    }
+    if (a.redo_mode == 1) {  // a start class too large for u8 entries: left to the u16 pass
+      bool big = false;
+      for (int c = tid; c < k; c += kWThreads) big |= csz[c] > kWClass8;
+      if (__syncthreads_or(big)) {
+        if (tid == 0) a.redo[ind] = 1;
+        continue;
+      }
     }
     for (int i = tid; i < k * lw; i += kWThreads) {
       const int c = i / lw, wd = i - c * lw;
@@ -348,34 +381,64 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         T += red[kWWarps + w];
         pre += w < warp ? red[kWWarps + w] : 0;
       }
+      // the thread holding tie j finds its vertex; its warp then finds the colour, 32 colours at a
+      // time in colour order (a ballot of the colours that reach dstar, the jj-th set bit)
+      bool win = false;
+      int jj = 0;
       if (T > 0 && ct > 0) {
-        const uint32_t j = below((uint32_t)sc[6], (uint32_t)T);
+        const int j = (int)below((uint32_t)sc[6], (uint32_t)T);
         const int lo = pre + incl - ct;
-        if ((int)j >= lo && (int)j < lo + ct) {
-          int jj = (int)j - lo, mv = -1, mc = -1;
-          for (int v = v0; v < v1 && mv < 0; ++v) {
+        win = j >= lo && j < lo + ct;
+        jj = j - lo;
+      }
+      const unsigned wb = __ballot_sync(0xFFFFFFFFu, win);
+      if (wb) {
+        const int src = __ffs(wb) - 1;
+        int mv = -1;
+        if (win)
+          for (int v = v0; v < v1; ++v) {
             if (rmin[v] != dstar) continue;
             if (jj >= rcnt[v]) { jj -= rcnt[v]; continue; }
             mv = v;
-            const int o = colS[v], wv = wS[v];
-            const uint32_t io = info[o];
-            const int m1o = io & 0xFF, m2o = (io >> 8) & 0xFF, c1o = io >> 16;
-            const int rem = (wv == m1o && c1o == 1) ? m2o - m1o : 0;
-            const int g0 = o < cs ? gS[(size_t)o * npad + v] : gG[(size_t)(o - cs) * npad + v];
-            const bool frozen = fz[v] > itrel;
-            const int base = fs * rem - (int)phi * g0;
-            for (int c = 0; c < k; ++c) {
-              int km = INT_MAX, kc = 0;
-              const int gc = c < cs ? gS[(size_t)c * npad + v] : gG[(size_t)(c - cs) * npad + v];
-              wvcp_scan_key(c, o, wv, max1s[c], base, phi, gc, frozen, thr, km, kc, fs);
-              if (km == dstar) {
-                if (jj == 0) { mc = c; break; }
-                --jj;
-              }
+            break;
+          }
+        mv = __shfl_sync(0xFFFFFFFFu, mv, src);
+        jj = __shfl_sync(0xFFFFFFFFu, jj, src);
+        int mc = -1;
+        if (mv >= 0) {
+          const int o = colS[mv], wv = wS[mv];
+          const uint32_t io = info[o];
+          const int m1o = io & 0xFF, m2o = (io >> 8) & 0xFF, c1o = io >> 16;
+          const int rem = (wv == m1o && c1o == 1) ? m2o - m1o : 0;
+          const int g0 = o < cs ? gS[(size_t)o * npad + mv] : gG[(size_t)(o - cs) * npad + mv];
+          const bool frozen = fz[mv] > itrel;
+          const int base = fs * rem - (int)phi * g0;
+          for (int c0 = 0; c0 < k && mc < 0; c0 += 32) {
+            const int c = c0 + lane;
+            bool hit = false;
+            if (c < k && c != o) {
+              const int gc = c < cs ? gS[(size_t)c * npad + mv] : gG[(size_t)(c - cs) * npad + mv];
+              const int d = base + wvcp_key(fs, wv, max1s[c], (int)phi, gc);
+              hit = d == dstar && (!frozen || d < thr);
+            }
+            const unsigned hb = __ballot_sync(0xFFFFFFFFu, hit);
+            const int pc = __popc(hb);
+            if (jj < pc) {
+              unsigned x = hb;
+              for (int q = 0; q < jj; ++q) x &= x - 1;
+              mc = c0 + __ffs(x) - 1;
+            } else {
+              jj -= pc;
             }
           }
-          if (mv >= 0 && mc >= 0) {
+        }
+        if (lane == src) {
+          if (mv >= 0 && mc >= 0 && a.redo_mode == 1 && csz[mc] >= kWClass8) {
+            sc[4] = 3;  // class mc would outgrow u8 entries: give the individual up
+          } else if (mv >= 0 && mc >= 0) {
             const int o = colS[mv], wv = wS[mv];
+            --csz[o];
+            ++csz[mc];
             const int go = o < cs ? gS[(size_t)o * npad + mv] : gG[(size_t)(o - cs) * npad + mv];
             const int gn = mc < cs ? gS[(size_t)mc * npad + mv] : gG[(size_t)(mc - cs) * npad + mv];
             sx[0] = max1s[o];
@@ -411,38 +474,66 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         const int old = sc[1], nw = sc[2];
         const bool improved = sc[3] != 0;
         if (improved) best_g = sc64[2];
-        uint16_t* po = old < cs ? gS + (size_t)old * npad : gG + (size_t)(old - cs) * npad;
-        uint16_t* pn = nw < cs ? gS + (size_t)nw * npad : gG + (size_t)(nw - cs) * npad;
+        G* po = old < cs ? gS + (size_t)old * npad : gG + (size_t)(old - cs) * npad;
+        G* pn = nw < cs ? gS + (size_t)nw * npad : gG + (size_t)(nw - cs) * npad;
         const uint32_t* brow = a.bits + (size_t)mv * nwords;
         const int m1a_old = sx[0], m1b_old = sx[1], m1a = max1s[old], m1b = max1s[nw], ph = (int)phi;
-        for (int b0 = tid * per; b0 < n; b0 += kWThreads * per) {
-          const uint32_t nb = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
-          uint32_t m = nb;
-          while (m) {
-            const int u = b0 + __ffs(m) - 1;
-            m &= m - 1;
-            po[u]--;
-            pn[u]++;
+        // thread t owns the rows of slice t (per rows); the rows whose only minimum rose (and the
+        // moved vertex's row) are then scanned again by the owner's whole warp
+        const int nslice = (n + per - 1) / per;
+        for (int sb = 0; sb < nslice; sb += kWThreads) {
+          const int b0 = (sb + tid) * per;
+          uint32_t need = 0;
+          if (b0 < n) {
+            const uint32_t nb = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
+            uint32_t m = nb;
+            while (m) {
+              const int u = b0 + __ffs(m) - 1;
+              m &= m - 1;
+              po[u]--;
+              pn[u]++;
+            }
+            // the key summaries of this thread's rows: colours old and nw changed (gamma of the
+            // neighbours, both class maxima)
+            const int e = min(b0 + per, n);
+            for (int u = b0; u < e; ++u) {
+              const int cu = colS[u], wu = wS[u];
+              int km = skey[u], kc = scnt[u];
+              bool ok = u != mv;
+              const int adj = (int)((nb >> (u - b0)) & 1u);
+              if (ok && old != cu) {
+                const int gnew = po[u];
+                ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1a_old, ph, gnew + adj), wvcp_key(fs, wu, m1a, ph, gnew));
+              }
+              if (ok && nw != cu) {
+                const int gnew = pn[u];
+                ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1b_old, ph, gnew - adj), wvcp_key(fs, wu, m1b, ph, gnew));
+              }
+              if (ok) {
+                skey[u] = km;
+                scnt[u] = (uint16_t)kc;
+              } else {
+                need |= 1u << (u - b0);
+              }
+            }
           }
-          // the key summaries of this thread's rows: colours old and nw changed (gamma of the
-          // neighbours, both class maxima); the moved vertex's row is scanned again
-          const int e = min(b0 + per, n);
-          for (int u = b0; u < e; ++u) {
-            const int cu = colS[u], wu = wS[u];
-            int km = skey[u], kc = scnt[u];
-            bool ok = u != mv;
-            const int adj = (int)((nb >> (u - b0)) & 1u);
-            if (ok && old != cu) {
-              const int gnew = po[u];
-              ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1a_old, ph, gnew + adj), wvcp_key(fs, wu, m1a, ph, gnew));
+          __syncwarp();
+          unsigned lanes = __ballot_sync(0xFFFFFFFFu, need != 0);
+          while (lanes) {
+            const int src = __ffs(lanes) - 1;
+            lanes &= lanes - 1;
+            uint32_t rows = __shfl_sync(0xFFFFFFFFu, need, src);
+            const int bs = __shfl_sync(0xFFFFFFFFu, b0, src);
+            while (rows) {
+              const int u = bs + __ffs(rows) - 1;
+              rows &= rows - 1;
+              int km, kc;
+              wvcp_row_summary_warp(u, colS[u], wS[u], max1s, gS, gG, npad, cs, k, fs, ph, lane, km, kc);
+              if (lane == 0) {
+                skey[u] = km;
+                scnt[u] = (uint16_t)kc;
+              }
             }
-            if (ok && nw != cu) {
-              const int gnew = pn[u];
-              ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1b_old, ph, gnew - adj), wvcp_key(fs, wu, m1b, ph, gnew));
-            }
-            if (!ok) wvcp_row_summary(u, cu, wu, max1s, gS, gG, npad, cs, k, fs, ph, km, kc);
-            skey[u] = km;
-            scnt[u] = (uint16_t)kc;
           }
         }
         if (improved) {
@@ -454,6 +545,11 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
       if (((it + 1) & 0x3FFF) == 0)
         for (int v = tid; v < n; v += kWThreads) fz[v] = fz[v] > 0x4000 ? (uint16_t)(fz[v] - 0x4000) : 0;
       __syncthreads();
+    }
+    if (sc[4] == 3) {  // given up: the u16 pass searches it from its start colouring
+      if (tid == 0) a.redo[ind] = 1;
+      __syncthreads();
+      continue;
     }
     if (sc[4] && tid == 0) raise_status(a.status, DLM_ECUDA);
     for (int v = tid; v < n; v += kWThreads) gcol[v] = (int16_t)bestS[v];
@@ -570,15 +666,35 @@ extern "C" dlm_status dlm_wvcp_greedy(dlm_ctx* ctx, const dlm_graph* g, int32_t 
   return DLM_OK;
 }
 
+// entry size of the conflict table: u8 when only u8 entries keep the whole table in shared memory
+// (entry_bits 0), or as the caller forces it (8 or 16); 0 when the state does not fit at all
+static int wvcp_entry_bits(const dlm_ctx* ctx, int n, int k, int wmax, int entry_bits) {
+  const WvcpLayout L16 = wvcp_layout(n, k, wmax, ctx->smem_optin, 2);
+  const WvcpLayout L8 = wvcp_layout(n, k, wmax, ctx->smem_optin, 1);
+  if (entry_bits == 16) return L16.gT <= ctx->smem_optin ? 16 : 0;
+  if (entry_bits == 8) return L8.cs == k ? 8 : 0;
+  if (L16.cs < k && L8.cs == k) return 8;
+  return L16.gT <= ctx->smem_optin ? 16 : 0;
+}
+
+template <typename G>
+static dlm_status wvcp_launch(dlm_ctx* ctx, const WvcpArgs& a, size_t smem, int grid) {
+  DLM_CUDA(ctx, cudaFuncSetAttribute(k_wvcp_tabu<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_wvcp_tabu<G><<<grid, kWThreads, smem, ctx->stream>>>(a);
+  return launch_check(ctx, "k_wvcp_tabu");
+}
+
 static dlm_status wvcp_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col, int64_t* best_g,
                            int64_t* best_fc, int64_t* moves, int64_t iters, dlm_tenure tenure, int64_t phi, uint64_t seed,
                            uint32_t generation, uint32_t ind_base, int32_t* trace, const int64_t* phi_arr = nullptr,
-                           int32_t fscale = 1) {
+                           int32_t fscale = 1, int32_t entry_bits = 0) {
   if (!ctx || !g) return fail(ctx, DLM_EINVAL, "wvcp_tabu: null argument");
   if (!g->d_weight) return fail(ctx, DLM_EINVAL, "wvcp_tabu: the graph has no vertex weights");
   if (k < 2 || k > 255) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: k must be in 2..255");
   if (g->max_weight > 255) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: vertex weights must be <= 255");
   if (pop < 0 || iters < 0 || iters > INT32_MAX) return fail(ctx, DLM_EINVAL, "wvcp_tabu: bad population or budget");
+  if (entry_bits != 0 && entry_bits != 8 && entry_bits != 16)
+    return fail(ctx, DLM_EINVAL, "wvcp_tabu: entry_bits must be 0, 8 or 16");
   // keys are 32-bit: fscale (max w) + phi (max degree + 1) must stay below 2^30 (phi: the largest
   // per-individual value the caller can pass, checked by the caller for phi_arr)
   if (phi < 0 || fscale < 1 ||
@@ -589,22 +705,38 @@ static dlm_status wvcp_run(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t 
   if (ttbase + tenure.L_max + 1 >= 0x4000) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: tenure must stay below 2^14");
   if (pop == 0) return DLM_OK;
   if (!col || !best_g) return fail(ctx, DLM_EINVAL, "wvcp_tabu: null col or best_g");
-  const WvcpLayout L = wvcp_layout(g->n, k, g->max_weight, ctx->smem_optin);
-  if (L.gT > ctx->smem_optin) return fail(ctx, DLM_EUNSUPPORTED, "wvcp_tabu: per-individual state exceeds shared memory");
+  const int eb = wvcp_entry_bits(ctx, g->n, k, g->max_weight, entry_bits);
+  if (eb == 0)
+    return fail(ctx, DLM_EUNSUPPORTED, entry_bits == 8 ? "wvcp_tabu: the u8 conflict table does not fit shared memory"
+                                                       : "wvcp_tabu: per-individual state exceeds shared memory");
+  const WvcpLayout L16 = wvcp_layout(g->n, k, g->max_weight, ctx->smem_optin, 2);
+  const WvcpLayout L8 = wvcp_layout(g->n, k, g->max_weight, ctx->smem_optin, 1);
   const int grid = std::min(pop, ctx->num_sms);
-  uint16_t* slab = nullptr;
-  const size_t slab_cols = (size_t)(k - L.cs);
-  DLM_TRY(ctx_workspace(ctx, std::max<size_t>(16, (size_t)grid * slab_cols * L.npad * 2), (void**)&slab));
+  // a u8 search can give an individual up only when a class can exceed 255 vertices; the u16 pass
+  // (its slab, the flags) then follows
+  const bool redo = eb == 8 && g->n > (int)kWClass8;
+  const size_t slab_bytes = eb == 16 || redo ? (size_t)grid * (size_t)(k - L16.cs) * L16.npad * 2 : 0;
+  const size_t redo_off = wal16(std::max<size_t>(16, slab_bytes));
+  uint8_t* ws = nullptr;
+  DLM_TRY(ctx_workspace(ctx, redo_off + (redo ? (size_t)pop * 4 : 0), (void**)&ws));
   WvcpArgs a;
   a.n = g->n; a.k = k; a.words = g->words; a.pop = pop; a.wmax = g->max_weight;
   a.bits = g->d_bits; a.weight = g->d_weight; a.col = col; a.best_g = best_g; a.best_fc = best_fc; a.moves = moves;
-  a.trace = trace; a.slab = slab; a.iters = iters; a.phi = phi; a.phi_arr = phi_arr; a.fscale = fscale;
+  a.trace = trace; a.slab = ws; a.iters = iters; a.phi = phi; a.phi_arr = phi_arr; a.fscale = fscale;
   a.L1 = (uint32_t)tenure.L_max + 1u;
   a.ttbase = (uint32_t)ttbase; a.seed = seed; a.gen = generation; a.ind_base = ind_base; a.status = ctx->d_status;
   a.smem_budget = ctx->smem_optin;
-  DLM_CUDA(ctx, cudaFuncSetAttribute(k_wvcp_tabu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-  k_wvcp_tabu<<<grid, kWThreads, L.total, ctx->stream>>>(a);
-  return launch_check(ctx, "k_wvcp_tabu");
+  a.redo = redo ? (int32_t*)(ws + redo_off) : nullptr;
+  a.redo_mode = 0;
+  if (eb == 16) return wvcp_launch<uint16_t>(ctx, a, L16.total, grid);
+  if (redo) {
+    DLM_CUDA(ctx, cudaMemsetAsync(a.redo, 0, (size_t)pop * 4, ctx->stream));
+    a.redo_mode = 1;
+  }
+  DLM_TRY(wvcp_launch<uint8_t>(ctx, a, L8.total, grid));
+  if (!redo) return DLM_OK;
+  a.redo_mode = 2;
+  return wvcp_launch<uint16_t>(ctx, a, L16.total, grid);
 }
 
 extern "C" dlm_status dlm_wvcp_tabu_batch(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
@@ -617,8 +749,16 @@ extern "C" dlm_status dlm_wvcp_tabu_batch(dlm_ctx* ctx, const dlm_graph* g, int3
 extern "C" dlm_status dlm_wvcp_tabu_batch_ex(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t pop, int16_t* col,
                                              int64_t* best_g, int64_t* best_fc, int64_t* moves, int64_t iters,
                                              dlm_tenure tenure, int64_t phi, uint64_t seed, uint32_t generation,
-                                             uint32_t ind_base, int32_t* trace) {
-  return wvcp_run(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure, phi, seed, generation, ind_base, trace);
+                                             uint32_t ind_base, int32_t* trace, int32_t entry_bits) {
+  return wvcp_run(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure, phi, seed, generation, ind_base, trace,
+                  nullptr, 1, entry_bits);
+}
+
+extern "C" dlm_status dlm_wvcp_entry_bits(dlm_ctx* ctx, const dlm_graph* g, int32_t k, int32_t* bits) {
+  if (!ctx || !g || !bits) return fail(ctx, DLM_EINVAL, "wvcp_entry_bits: null argument");
+  if (k < 2 || k > 255 || !g->d_weight) return fail(ctx, DLM_EINVAL, "wvcp_entry_bits: bad k or no weights");
+  *bits = wvcp_entry_bits(ctx, g->n, k, g->max_weight, 0);
+  return DLM_OK;
 }
 
 // ---- Algorithm 2: iterated feasible/infeasible tabu search with the adaptive penalty -----------

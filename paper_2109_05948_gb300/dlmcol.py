@@ -121,7 +121,9 @@ _SIGS = {
     "dlm_gemm_profile": (_i32, [_P, _i32]),
     "dlm_gemm_profile_read": (_i32, [_P, _P, _P, _P]),
     "dlm_wvcp_tabu_batch": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32]),
-    "dlm_wvcp_tabu_batch_ex": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32, _P]),
+    "dlm_wvcp_tabu_batch_ex": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _P, _i64, Tenure, _i64, _u64, _u32, _u32, _P,
+                                      _i32]),
+    "dlm_wvcp_entry_bits": (_i32, [_P, _P, _i32, _P]),
     "dlm_wvcp_greedy": (_i32, [_P, _P, _i32, _u64, _u32, _P, _P]),
     "dlm_wvcp_iterated": (_i32, [_P, _P, _i32, _i32, _P, _P, _P, _i64, _i32, Tenure, _i32, _i64, _i64, _u64, _u32,
                                  _u32]),
@@ -542,10 +544,18 @@ def dlm_wvcp_tabu_batch(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenu
 
 
 def dlm_wvcp_tabu_batch_ex(ctx, g, k, pop, col, best_g, best_fc, moves, iters, tenure=WVCP_TENURE, phi=0, seed=0,
-                           generation=0, ind_base=0, trace=None):
+                           generation=0, ind_base=0, trace=None, entry_bits=0):
     ctx.check(lib().dlm_wvcp_tabu_batch_ex(ctx.h, g.h, k, pop, _ptr(col), _ptr(best_g), _ptr(best_fc), _ptr(moves),
-                                           iters, tenure, phi, seed, generation, ind_base, _ptr(trace)),
+                                           iters, tenure, phi, seed, generation, ind_base, _ptr(trace), entry_bits),
               "dlm_wvcp_tabu_batch_ex")
+
+
+def dlm_wvcp_entry_bits(ctx, g, k):
+    """The conflict-table entry size (8 or 16, 0 if the state does not fit) of the weighted tabu
+    search on graph g with k colours."""
+    out = ctypes.c_int32(0)
+    ctx.check(lib().dlm_wvcp_entry_bits(ctx.h, g.h, k, ctypes.byref(out)), "dlm_wvcp_entry_bits")
+    return out.value
 
 
 def dlm_wvcp_greedy(ctx, g, pop, seed, ind_base, col, used):
