@@ -12,8 +12,8 @@
 //    only the keys of colours a and b (gamma of the neighbours, the two class maxima), which
 //    update the summaries in O(1) per row; a row whose only minimum key rose, and the moved
 //    vertex's row, are scanned again;
-//  * gamma is stored transposed, gT[c][v], so that thread t scanning vertices t, t + 512, ...
-//    reads consecutive addresses across the warp. With u8 entries the whole table stays in shared
+//  * gamma is stored transposed, gT[c][v], so that the lanes of a warp, each on its own rows,
+//    read neighbouring addresses of one colour. With u8 entries the whole table stays in shared
 //    memory (n * k bytes: 144 KB at n = 1000, k = 144); gamma[v][c] never exceeds the size of class
 //    c, so u8 is exact while every class holds at most 255 vertices: the u8 search of an individual
 //    gives up (at set-up, or before the move that would grow a class past 255) and a u16 pass
@@ -22,8 +22,15 @@
 //    an L2-resident slab of global memory owned by the CTA;
 //  * class maxima are kept exactly by per-class counts per weight level plus a level bitmask, so
 //    max1, its multiplicity and the second largest weight come from two bit scans after a move;
-//  * ties: the j-th admissible minimum in (v ascending, c ascending) order, found by a block
-//    prefix sum over per-vertex tie counts.
+//  * ties: the j-th admissible minimum in (v ascending, c ascending) order. Thread t owns the rows
+//    of slice t, so warps hold consecutive row ranges; each warp publishes its minimum and how many
+//    moves reach it, every warp finds the global minimum and the warp holding tie j from those 16
+//    pairs, and that warp alone ranks its lanes, finds the row and then the colour (a ballot over
+//    32 colours at a time);
+//  * an iteration has two block barriers: after the move, and after the neighbour updates, which
+//    end with the next iteration's per-row selection (the owner of a row updates and selects it);
+//    rows whose summary must be scanned again are scanned by the owner's whole warp, and the moved
+//    vertex's adjacency row is loaded during the colour search.
 #include <algorithm>
 #include <climits>
 #include <vector>
@@ -37,7 +44,7 @@ constexpr int kWWarps = kWThreads / 32;
 constexpr uint32_t kWClass8 = 255;  // largest class the u8 conflict table holds exactly
 
 struct WvcpLayout {
-  size_t col, best, w, fz, lvl, lmask, info, max1, csz, rmin, rcnt, skey, scnt, red, gT, total;
+  size_t col, best, w, fz, lvl, lmask, info, max1, csz, mvrow, rmin, rcnt, skey, scnt, red, gT, total;
   int npad, lw, cs;  // vertices padded to 8, mask words per class, colours held in shared memory
 };
 
@@ -59,6 +66,7 @@ __host__ __device__ inline WvcpLayout wvcp_layout(int n, int k, int wmax, size_t
   L.info = o; o += wal16((size_t)k * 4);
   L.max1 = o; o += wal16((size_t)k);
   L.csz = o; o += wal16((size_t)k * 4);
+  L.mvrow = o; o += wal16((size_t)((n + 31) / 32) * 4);
   L.rmin = o; o += wal16((size_t)n * 4);
   L.rcnt = o; o += wal16((size_t)n * 2);
   L.skey = o; o += wal16((size_t)n * 4);
@@ -209,8 +217,10 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
   int32_t* skey = (int32_t*)(smem + L.skey);   // per row: minimum key over the colours c != col v
   uint16_t* scnt = (uint16_t*)(smem + L.scnt); // per row: colours reaching it
   int32_t* sx = (int32_t*)(smem + L.red + 896); // class maxima of the move's two colours before it
+  int32_t* mvslot = (int32_t*)(smem + L.red + 904);  // moved vertex of even / odd iterations (-1: none)
+  uint32_t* mvrow = (uint32_t*)(smem + L.mvrow);     // its adjacency row
   int32_t* red = (int32_t*)(smem + L.red);  // [kWWarps] warp minima, [kWWarps] warp tie totals
-  int32_t* sc = red + 2 * kWWarps;          // mv, old, new, improved, error, bad input, r0, r1
+  int32_t* sc = red + 2 * kWWarps;          // -, old, new, improved, error, bad input, r0, r1
   // g, conf, best g, best f, best conf; from 8: per-warp conflict and score partial sums
   long long* sc64 = (long long*)(red + 2 * kWWarps + 8);
   G* gS = (G*)(smem + L.gT);
@@ -328,75 +338,79 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
     __syncthreads();
     int64_t moves = 0;
     int32_t* trace = a.trace ? a.trace + (size_t)ind * a.iters * 4 : nullptr;
-    for (int64_t it = 0; it < a.iters; ++it) {
-      const unsigned itrel = (unsigned)(it & 0x3FFF);
-      if (tid == 0) {
-        const U4 r = rng(a.seed, (uint32_t)it, a.gen, a.ind_base + (uint32_t)ind, kTagTabu);
-        sc[6] = (int32_t)r.x;
-        sc[7] = (int32_t)r.y;
-        sc[0] = -1;
-      }
-      // ---- phase 1: the best one-move of every row from its key summary ------------------------
-      // d = rem(v) fs - phi gamma[v][col v] + key; a frozen vertex's moves count only when they
-      // reach below the aspiration threshold (all its tied moves have the same d)
-      const long long thr64 = best_g - g;
+    // thread t owns rows [b0, b1) (slice t of per rows): warps hold consecutive row ranges, so the
+    // tie order (v ascending) is warp, lane, row
+    const int b0 = tid * per, b1 = min(b0 + per, n);
+    // the best one-move of every row of this thread from its key summary: d = rem(v) fs -
+    // phi gamma[v][col v] + key; a frozen vertex's moves count only when they reach below the
+    // aspiration threshold (all its tied moves have the same d). Per warp: the minimum and the
+    // number of moves that reach it
+    auto select_rows = [&](unsigned itn, long long g_now, long long best_now) {
+      const long long thr64 = best_now - g_now;
       const int thr = thr64 < (long long)INT_MIN + 1 ? INT_MIN + 1 : (int)thr64;
-      int tmin = INT_MAX;
-      for (int v = tid; v < n; v += kWThreads) {
+      int tmin = INT_MAX, tcnt = 0;
+      for (int v = b0; v < b1; ++v) {
         const int o = colS[v], wv = wS[v];
         const uint32_t io = info[o];
         const int rem = (wv == (int)(io & 0xFF) && (io >> 16) == 1) ? (int)((io >> 8) & 0xFF) - (int)(io & 0xFF) : 0;
         const int g0 = o < cs ? gS[(size_t)o * npad + v] : gG[(size_t)(o - cs) * npad + v];
         const int d = fs * rem - (int)phi * g0 + skey[v];
-        const bool ok = !(fz[v] > itrel) || d < thr;
-        rmin[v] = ok ? d : INT_MAX;
-        rcnt[v] = ok ? scnt[v] : (uint16_t)0;
-        tmin = min(tmin, ok ? d : INT_MAX);
+        const bool ok = !(fz[v] > itn) || d < thr;
+        const int dv = ok ? d : INT_MAX, cv = ok ? (int)scnt[v] : 0;
+        rmin[v] = dv;
+        rcnt[v] = (uint16_t)cv;
+        if (dv < tmin) { tmin = dv; tcnt = cv; }
+        else if (dv == tmin) tcnt += cv;
       }
-      {
-        const int wm = __reduce_min_sync(0xFFFFFFFFu, tmin);
-        if (lane == 0) red[warp] = wm;
-      }
-      __syncthreads();
-      // ---- phase 2: minimum, tie ranks over vertices in order, move -----------------------------
-      int dstar = INT_MAX;
+      const int wm = __reduce_min_sync(0xFFFFFFFFu, tmin);
+      const int wc = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)(tmin == wm ? tcnt : 0));
+      if (lane == 0) { red[warp] = wm; red[kWWarps + warp] = wc; }
+    };
+    select_rows(0u, g, best_g);
+    if (tid == 0) {
+      const U4 r = rng(a.seed, 0u, a.gen, a.ind_base + (uint32_t)ind, kTagTabu);
+      sc[6] = (int32_t)r.x;
+      sc[7] = (int32_t)r.y;
+      mvslot[0] = -1;
+      mvslot[1] = -1;
+    }
+    __syncthreads();
+    for (int64_t it = 0; it < a.iters; ++it) {
+      const unsigned itrel = (unsigned)(it & 0x3FFF);
+      const long long thr64 = best_g - g;
+      const int thr = thr64 < (long long)INT_MIN + 1 ? INT_MIN + 1 : (int)thr64;
+      // ---- phase 2: minimum over the warps, the tie j (Philox r0), its warp, lane and row; the
+      // warp then finds the colour, 32 colours at a time in colour order (a ballot of the colours
+      // that reach dstar, the jj-th set bit), and one lane makes the move ------------------------
+      const int wmin = lane < kWWarps ? red[lane] : INT_MAX;
+      const int dstar = __reduce_min_sync(0xFFFFFFFFu, wmin);
+      const int wcnt = (lane < kWWarps && dstar != INT_MAX && wmin == dstar) ? red[kWWarps + lane] : 0;
+      int winc = wcnt;
 #pragma unroll
-      for (int w = 0; w < kWWarps; ++w) dstar = min(dstar, red[w]);
-      const int C2 = (n + kWThreads - 1) / kWThreads;
-      const int v0 = tid * C2, v1 = min(v0 + C2, n);
-      int ct = 0;
-      if (dstar != INT_MAX)
-        for (int v = v0; v < v1; ++v) ct += rmin[v] == dstar ? rcnt[v] : 0;
-      int incl = ct;
+      for (int d = 1; d < kWWarps; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, winc, d);
+        if (lane >= d) winc += t;
+      }
+      const int T = __shfl_sync(0xFFFFFFFFu, winc, kWWarps - 1);
+      const int wpre = __shfl_sync(0xFFFFFFFFu, winc - wcnt, warp);
+      const int wown = __shfl_sync(0xFFFFFFFFu, wcnt, warp);
+      const int j = T > 0 ? (int)below((uint32_t)sc[6], (uint32_t)T) : 0;
+      if (T > 0 && j >= wpre && j < wpre + wown) {
+        int ct = 0;
+        for (int v = b0; v < b1; ++v) ct += rmin[v] == dstar ? rcnt[v] : 0;
+        int incl = ct;
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += t;
-      }
-      if (lane == 31) red[kWWarps + warp] = incl;
-      __syncthreads();
-      int T = 0, pre = 0;
-#pragma unroll
-      for (int w = 0; w < kWWarps; ++w) {
-        T += red[kWWarps + w];
-        pre += w < warp ? red[kWWarps + w] : 0;
-      }
-      // the thread holding tie j finds its vertex; its warp then finds the colour, 32 colours at a
-      // time in colour order (a ballot of the colours that reach dstar, the jj-th set bit)
-      bool win = false;
-      int jj = 0;
-      if (T > 0 && ct > 0) {
-        const int j = (int)below((uint32_t)sc[6], (uint32_t)T);
-        const int lo = pre + incl - ct;
-        win = j >= lo && j < lo + ct;
-        jj = j - lo;
-      }
-      const unsigned wb = __ballot_sync(0xFFFFFFFFu, win);
-      if (wb) {
-        const int src = __ffs(wb) - 1;
-        int mv = -1;
+        for (int d = 1; d < 32; d <<= 1) {
+          const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+          if (lane >= d) incl += t;
+        }
+        const int lo = wpre + incl - ct;
+        const bool win = ct > 0 && j >= lo && j < lo + ct;
+        const unsigned wb = __ballot_sync(0xFFFFFFFFu, win);
+        const int src = wb ? __ffs(wb) - 1 : 0;
+        int mv = -1, jj = j - lo;
         if (win)
-          for (int v = v0; v < v1; ++v) {
+          for (int v = b0; v < b1; ++v) {
             if (rmin[v] != dstar) continue;
             if (jj >= rcnt[v]) { jj -= rcnt[v]; continue; }
             mv = v;
@@ -405,7 +419,11 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         mv = __shfl_sync(0xFFFFFFFFu, mv, src);
         jj = __shfl_sync(0xFFFFFFFFu, jj, src);
         int mc = -1;
+        uint32_t rw0 = 0u, rw1 = 0u;  // the moved vertex's adjacency row, loaded during the search
         if (mv >= 0) {
+          const uint32_t* brow = a.bits + (size_t)mv * nwords;
+          if (lane < nwords) rw0 = __ldg(brow + lane);
+          if (lane + 32 < nwords) rw1 = __ldg(brow + lane + 32);
           const int o = colS[mv], wv = wS[mv];
           const uint32_t io = info[o];
           const int m1o = io & 0xFF, m2o = (io >> 8) & 0xFF, c1o = io >> 16;
@@ -452,7 +470,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
             colS[mv] = (uint8_t)mc;
             const long long gn64 = g + dstar, cn64 = conf + (gn - go);
             fz[mv] = (uint16_t)(itrel + 1 + below((uint32_t)sc[7], a.L1) + a.ttbase);
-            sc[0] = mv; sc[1] = o; sc[2] = mc; sc[3] = gn64 < best_g;
+            mvslot[it & 1] = mv;
+            sc[1] = o; sc[2] = mc; sc[3] = gn64 < best_g;
             sc64[0] = gn64;
             sc64[1] = cn64;
             if (gn64 < best_g) { sc64[2] = gn64; sc64[3] = (gn64 - phi * cn64) / fs; sc64[4] = cn64; }
@@ -461,12 +480,15 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
             sc[4] = 2;
           }
         }
+        if (lane < nwords) mvrow[lane] = rw0;
+        if (lane + 32 < nwords) mvrow[lane + 32] = rw1;
       }
       if (T == 0 && tid == 0 && trace) reinterpret_cast<int4*>(trace)[it] = make_int4(-1, -1, 0, 0);
       __syncthreads();
       if (sc[4]) break;
-      // ---- phase 3: conflict-table update on the neighbours of the moved vertex ----------------
-      const int mv = sc[0];
+      // ---- phase 3: conflict-table update on the neighbours of the moved vertex, then the next
+      // iteration's row selection ----------------------------------------------------------------
+      const int mv = mvslot[it & 1];
       if (mv >= 0) {
         g = sc64[0];
         conf = sc64[1];
@@ -476,63 +498,56 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         if (improved) best_g = sc64[2];
         G* po = old < cs ? gS + (size_t)old * npad : gG + (size_t)(old - cs) * npad;
         G* pn = nw < cs ? gS + (size_t)nw * npad : gG + (size_t)(nw - cs) * npad;
-        const uint32_t* brow = a.bits + (size_t)mv * nwords;
         const int m1a_old = sx[0], m1b_old = sx[1], m1a = max1s[old], m1b = max1s[nw], ph = (int)phi;
-        // thread t owns the rows of slice t (per rows); the rows whose only minimum rose (and the
-        // moved vertex's row) are then scanned again by the owner's whole warp
-        const int nslice = (n + per - 1) / per;
-        for (int sb = 0; sb < nslice; sb += kWThreads) {
-          const int b0 = (sb + tid) * per;
-          uint32_t need = 0;
-          if (b0 < n) {
-            const uint32_t nb = (__ldg(brow + (b0 >> 5)) >> (b0 & 31)) & slice_mask;
-            uint32_t m = nb;
-            while (m) {
-              const int u = b0 + __ffs(m) - 1;
-              m &= m - 1;
-              po[u]--;
-              pn[u]++;
+        uint32_t need = 0;  // rows of this thread whose only minimum rose (and the moved vertex's)
+        if (b0 < n) {
+          const uint32_t nb = (mvrow[b0 >> 5] >> (b0 & 31)) & slice_mask;
+          uint32_t m = nb;
+          while (m) {
+            const int u = b0 + __ffs(m) - 1;
+            m &= m - 1;
+            po[u]--;
+            pn[u]++;
+          }
+          // the key summaries of this thread's rows: colours old and nw changed (gamma of the
+          // neighbours, both class maxima)
+          for (int u = b0; u < b1; ++u) {
+            const int cu = colS[u], wu = wS[u];
+            int km = skey[u], kc = scnt[u];
+            bool ok = u != mv;
+            const int adj = (int)((nb >> (u - b0)) & 1u);
+            if (ok && old != cu) {
+              const int gnew = po[u];
+              ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1a_old, ph, gnew + adj), wvcp_key(fs, wu, m1a, ph, gnew));
             }
-            // the key summaries of this thread's rows: colours old and nw changed (gamma of the
-            // neighbours, both class maxima)
-            const int e = min(b0 + per, n);
-            for (int u = b0; u < e; ++u) {
-              const int cu = colS[u], wu = wS[u];
-              int km = skey[u], kc = scnt[u];
-              bool ok = u != mv;
-              const int adj = (int)((nb >> (u - b0)) & 1u);
-              if (ok && old != cu) {
-                const int gnew = po[u];
-                ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1a_old, ph, gnew + adj), wvcp_key(fs, wu, m1a, ph, gnew));
-              }
-              if (ok && nw != cu) {
-                const int gnew = pn[u];
-                ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1b_old, ph, gnew - adj), wvcp_key(fs, wu, m1b, ph, gnew));
-              }
-              if (ok) {
-                skey[u] = km;
-                scnt[u] = (uint16_t)kc;
-              } else {
-                need |= 1u << (u - b0);
-              }
+            if (ok && nw != cu) {
+              const int gnew = pn[u];
+              ok = wvcp_summ_apply(km, kc, wvcp_key(fs, wu, m1b_old, ph, gnew - adj), wvcp_key(fs, wu, m1b, ph, gnew));
+            }
+            if (ok) {
+              skey[u] = km;
+              scnt[u] = (uint16_t)kc;
+            } else {
+              need |= 1u << (u - b0);
             }
           }
-          __syncwarp();
-          unsigned lanes = __ballot_sync(0xFFFFFFFFu, need != 0);
-          while (lanes) {
-            const int src = __ffs(lanes) - 1;
-            lanes &= lanes - 1;
-            uint32_t rows = __shfl_sync(0xFFFFFFFFu, need, src);
-            const int bs = __shfl_sync(0xFFFFFFFFu, b0, src);
-            while (rows) {
-              const int u = bs + __ffs(rows) - 1;
-              rows &= rows - 1;
-              int km, kc;
-              wvcp_row_summary_warp(u, colS[u], wS[u], max1s, gS, gG, npad, cs, k, fs, ph, lane, km, kc);
-              if (lane == 0) {
-                skey[u] = km;
-                scnt[u] = (uint16_t)kc;
-              }
+        }
+        // the flagged rows are scanned again by the owner's whole warp
+        __syncwarp();
+        unsigned lanes = __ballot_sync(0xFFFFFFFFu, need != 0);
+        while (lanes) {
+          const int src = __ffs(lanes) - 1;
+          lanes &= lanes - 1;
+          uint32_t rows = __shfl_sync(0xFFFFFFFFu, need, src);
+          const int bs = src * per + warp * 32 * per;
+          while (rows) {
+            const int u = bs + __ffs(rows) - 1;
+            rows &= rows - 1;
+            int km, kc;
+            wvcp_row_summary_warp(u, colS[u], wS[u], max1s, gS, gG, npad, cs, k, fs, ph, lane, km, kc);
+            if (lane == 0) {
+              skey[u] = km;
+              scnt[u] = (uint16_t)kc;
             }
           }
         }
@@ -543,7 +558,15 @@ __global__ void __launch_bounds__(kWThreads, 1) k_wvcp_tabu(WvcpArgs a) {
         }
       }
       if (((it + 1) & 0x3FFF) == 0)
-        for (int v = tid; v < n; v += kWThreads) fz[v] = fz[v] > 0x4000 ? (uint16_t)(fz[v] - 0x4000) : 0;
+        for (int v = b0; v < b1; ++v) fz[v] = fz[v] > 0x4000 ? (uint16_t)(fz[v] - 0x4000) : 0;
+      __syncwarp();
+      select_rows((unsigned)((it + 1) & 0x3FFF), g, best_g);
+      if (tid == 0) {
+        const U4 r = rng(a.seed, (uint32_t)(it + 1), a.gen, a.ind_base + (uint32_t)ind, kTagTabu);
+        sc[6] = (int32_t)r.x;
+        sc[7] = (int32_t)r.y;
+        mvslot[(it + 1) & 1] = -1;
+      }
       __syncthreads();
     }
     if (sc[4] == 3) {  // given up: the u16 pass searches it from its start colouring
