@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--mem-seeds", type=int, default=10)
     ap.add_argument("--wvcp-entry-bits", type=int, default=0, choices=(0, 8, 16),
                     help="--workload wvcp: conflict-table entry size (0: the library's choice)")
+    ap.add_argument("--wvcp-pop", type=int, default=8192, help="--workload wvcp: population (small cases for ncu)")
+    ap.add_argument("--wvcp-iters", type=int, default=10000, help="--workload wvcp: iterations per individual")
     ap.add_argument("--mem-log", default=None,
                     help="append one JSON line per generation (mode, seed, generation, elapsed s, best, the "
                          "dlm_memetic_stats diagnostics) to this file (memetic and wvcp_memetic workloads)")
@@ -733,7 +735,7 @@ def run_wvcp(args):
     libbuild.build()
     torch.cuda.set_device(0)
     ctx = dlmcol.Context(0)
-    n, pop, iters = 1000, 8192, 10 * 1000
+    n, pop, iters = 1000, args.wvcp_pop, args.wvcp_iters
     e = inputs.gnp(n, 0.5, 0)
     w = inputs.weights(n, 0)
     g = dlmcol.Graph(ctx, n, torch.from_numpy(e).cuda(), torch.from_numpy(w).cuda())
