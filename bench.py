@@ -97,6 +97,12 @@ def parse():
     ap.add_argument("--mem-seeds", type=int, default=10)
     ap.add_argument("--wvcp-entry-bits", type=int, default=0, choices=(0, 8, 16),
                     help="--workload wvcp: conflict-table entry size (0: the library's choice)")
+    ap.add_argument("--scorer-k", type=int, default=48,
+                    help="--workload scorer: colours (48: the planted learned workload; 145: the weighted one)")
+    ap.add_argument("--scorer-epochs", type=int, default=5, help="--workload scorer: training epochs")
+    ap.add_argument("--scorer-split", type=int, default=1, choices=(0, 1),
+                    help="--workload scorer: scoring activations bf16 hi + lo (1) or bf16 alone (0, the memetic "
+                         "selection's setting)")
     ap.add_argument("--wvcp-pop", type=int, default=8192, help="--workload wvcp: population (small cases for ncu)")
     ap.add_argument("--wvcp-iters", type=int, default=10000, help="--workload wvcp: iterations per individual")
     ap.add_argument("--mem-log", default=None,
@@ -1076,9 +1082,9 @@ def run_scorer(args):
     libbuild.build()
     torch.cuda.set_device(0)
     ctx = dlmcol.Context(0)
-    n, k, p, Kc, epochs, b = 1000, 48, 8192, 32, 5, 100
+    n, k, p, Kc, epochs, b = 1000, args.scorer_k, 8192, 32, args.scorer_epochs, 100
     C = p * Kc
-    e, _ = inputs.planted(n, k, 0.5, seed=0)
+    e = inputs.planted(n, k, 0.5, seed=0)[0] if k == 48 else inputs.gnp(n, 0.5, 0)
     g = dlmcol.Graph(ctx, n, torch.from_numpy(e).cuda())
     cand = torch.empty((C, n), dtype=torch.int16, device="cuda")
     dlmcol.dlm_init_colors(ctx, n, k, C, SEED, 0, cand)
@@ -1087,6 +1093,8 @@ def run_scorer(args):
     dlmcol.dlm_gamma(ctx, g, k, p, samples, None, fvals)
     out = torch.empty(C, dtype=torch.float32, device="cuda")
     sc = dlmcol.Scorer(ctx, n, k, SEED)
+    if args.scorer_split == 0:
+        dlmcol.dlm_scorer_set_scoring_precision(ctx, sc, 0)
     stream = torch.cuda.current_stream()
 
     prof = {"fwd": [0.0, 0.0, 0], "train": [0.0, 0.0, 0]}
@@ -1145,15 +1153,17 @@ def run_scorer(args):
             "kernel_ms_per_launch": fms / max(1, fn_), "launches": fn_,
             "executed_tflops": ffl / (fms / 1e3) / 1e12, "executed_over_algorithmic": ffl / alg_fwd,
             "gemm_share_of_scoring": fms / fwd_ms}
-    res = {"metric": "scorer candidates/s, n=1000, k=48", "workload": "scorer", "value": C * args.steps / (fwd_ms / 1e3),
+    res = {"metric": f"scorer candidates/s, n=1000, k={k}", "workload": "scorer", "value": C * args.steps / (fwd_ms / 1e3),
            "unit": "candidates/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": (fwd_ms + trn_ms) / args.steps, "forward_ms_per_step": fwd_ms / args.steps,
            "train_ms_per_step": trn_ms / args.steps,
            "train_samples_per_s": p * epochs * args.steps / (trn_ms / 1e3), "dtype": "bf16 (fp32 accumulate)",
            "gpu_launches": None, "clocks": ck, "roofline": roof, "data": "synthetic",
-           "config": {"workload": f"planted 48-colourable n={n}, {C} candidates ({p} x {Kc}) scored, training on "
+           "config": {"workload": (f"planted 48-colourable n={n}" if k == 48 else f"G(n={n}, 0.5), k={k}") +
+                                  f", {C} candidates ({p} x {Kc}) scored, training on "
                                   f"{p} samples, {epochs} epochs, batch {b}, scorer 64-d embedding + 3 x 256 "
-                                  f"invariant layers (weights split hi/lo; training activations split)"}}
+                                  f"invariant layers (weights split hi/lo; training activations split; scoring "
+                                  f"activations {'split' if args.scorer_split else 'bf16 alone'})"}}
     print(json.dumps(res), flush=True)
     sc.close()
     g.close()

@@ -881,6 +881,10 @@ dlm_status make_map_bf16(dlm_ctx* ctx, CUtensorMap* map, const void* base, uint6
 // of split operands (or null); kc = 64-wide K chunks per CTA (split-K along grid z)
 // ST = 0: two pipeline stages (split operands) or four; ST > 0: that many (one keeps the shared
 // memory of a 128 x 64 tile at about 50 KB)
+// training batches of at least this many class rows (100 samples at k > 64) run their GEMMs as
+// 128 x 256 tiles with two pipeline stages, as the scoring pass does
+constexpr int kWideRows = 12288;
+
 template <int BN, int ST = 0, class Epi>
 static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K, int lda, const bf16* B, const bf16* B2,
                        int N, int ldb, int kc, Epi epi) {
@@ -1005,12 +1009,13 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       }
     }
     const bool last = l == kNL;
-    // a training batch runs its layer GEMMs as 128 x 64 tiles with one pipeline stage: four
-    // times the CTAs of a 128 x 256 tile for a few thousand rows, and about 50 KB of shared
-    // memory each instead of 193 KB
+    // a training batch of a few thousand rows runs its layer GEMMs as 128 x 64 tiles with one
+    // pipeline stage: four times the CTAs of a 128 x 256 tile, and about 50 KB of shared memory
+    // each instead of 193 KB; from kWideRows rows on (k > 64) 128 x 256 tiles fill the SMs
+    const bool narrow = train && rows < kWideRows;
     EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, s->R, G[l],
-               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, train ? 32 : 128, 0};
-    if (train)
+               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, narrow ? 32 : 128, 0};
+    if (narrow)
       DLM_TRY((gemm<64, 1>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din,
                           0, e)));
     else
@@ -1026,8 +1031,9 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
-  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, s->R, rowdot, train ? kD / 32 : kD / 128, s->theta, s->obh,
-                                                       out);
+  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, s->R, rowdot,
+                                                       (train && rows < kWideRows) ? kD / 32 : kD / 128, s->theta,
+                                                       s->obh, out);
   return launch_check(ctx, "k_head_out");
 }
 
@@ -1053,10 +1059,14 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
         B, s->k, s->R, rows, din, s->dZ[l], s->S[l], s->dZT[l], s->Hb[l - 1], s->Hblo[l - 1], s->HT[l - 1],
         s->HTlo[l - 1]);
     DLM_TRY(launch_check(ctx, "k_bwd_prep"));
-    // dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction)
+    // dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction; the tile width does
+    // not change any sum)
     const int nchunks = rows / tc::BK, kc = 4, splits = (nchunks + kc - 1) / kc;
-    DLM_TRY((gemm<64, 1>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc,
-                        EpiPartial{s->part, kD, din, (size_t)din * kD})));
+    const EpiPartial ep{s->part, kD, din, (size_t)din * kD};
+    if (rows < kWideRows)
+      DLM_TRY((gemm<64, 1>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc, ep)));
+    else
+      DLM_TRY((gemm<256>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc, ep)));
     // the split sums into dLambda_l, dGamma_l and dbeta_l, and the per-candidate term of dH_{l-1}
     const int64_t cnt = (int64_t)din * kD;
     k_bwd_grads<<<(unsigned)((cnt + 255) / 256 + din + B), kD, 0, ctx->stream>>>(
@@ -1065,7 +1075,10 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
     DLM_TRY(launch_check(ctx, "k_bwd_grads"));
     // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
     EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->R, s->Gb, s->Hb[l - 1]};
-    DLM_TRY((gemm<64, 1>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
+    if (rows < kWideRows || din % 256)
+      DLM_TRY((gemm<64, 1>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
+    else
+      DLM_TRY((gemm<256>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
   }
   k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, s->R, 1.f, s->S[0], nullptr, nullptr);
   k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, s->R, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);

@@ -153,7 +153,10 @@ def test_scorer_permutation_invariant_on_gpu(ctx):
     s.close()
 
 
-@pytest.mark.parametrize("n,k,B", [(120, 17, 100), (300, 48, 33), (200, 146, 40), (260, 256, 17)])
+# the last two batches hold at least 12 288 class rows (100 x 192, 60 x 256): their GEMMs run as
+# 128 x 256 tiles, the others as 128 x 64 tiles
+@pytest.mark.parametrize("n,k,B", [(120, 17, 100), (300, 48, 33), (200, 146, 40), (260, 256, 17), (150, 146, 100),
+                                   (90, 200, 60)])
 def test_scorer_gradients_match_oracle(ctx, n, k, B):
     dims = oracle.ScorerDims(n)
     th = _params(dims, seed=k, scale=3.0)
