@@ -364,7 +364,8 @@ def run_memetic(args):
             dlmcol.dlm_memetic_profile(ctx, mm, True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            traj, diag, hit = [], [], None
+            traj, diag, hit, found = [], [], None, None
+            el_prev = 0.0
             for gen in range(args.mem_max_gens):
                 best = dlmcol.dlm_memetic_step(ctx, mm)
                 el = time.perf_counter() - t0
@@ -373,18 +374,25 @@ def run_memetic(args):
                 st = dlmcol.dlm_memetic_stats(ctx, mm)
                 diag.append({key: (None if v != v else round(v, 4)) for key, v in st.items()})
                 log_generation(args.mem_log, "memetic", mode, 1000 + seed, gen, el, best, diag[-1])
-                t0 += time.perf_counter() - t0 - el  # the diagnostics' read is not search time
                 if best <= args.mem_target:
                     hit = el
+                    # the moment S* reached the target: the generation's start plus the device
+                    # time to the end of its best-so-far update (Algorithm 1 records S* after
+                    # the local search)
+                    found = el_prev + dlmcol.dlm_memetic_found_ms(ctx, mm) / 1e3
                     break
+                t0 += time.perf_counter() - t0 - el  # the diagnostics' read is not search time
+                el_prev = el
                 if el > args.mem_time_limit:
                     break
             stages = dlmcol.dlm_memetic_profile(ctx, mm, False)
-            runs[mode].append({"seed": 1000 + seed, "time_to_target_s": hit, "generations": len(traj),
+            runs[mode].append({"seed": 1000 + seed, "time_to_target_s": hit, "time_to_best_found_s": found,
+                               "generations": len(traj),
                                "best": traj[-1][1], "trajectory": traj, "diagnostics": diag,
                                "stage_ms_per_generation": {key: round(v, 2) for key, v in stages.items()
                                                            if key != "generations"}})
             print(json.dumps({"progress": mode, "seed": 1000 + seed, "time_to_target_s": hit,
+                              "time_to_best_found_s": found,
                               "generations": len(traj), "best": traj[-1][1]}), file=sys.stderr, flush=True)
             mm.close()
 
@@ -414,9 +422,15 @@ def memetic_compare(args):
         d = json.loads(r.stdout.strip().splitlines()[-1])
     except Exception as exc:  # reported, never fatal to the headline
         return {"error": f"{type(exc).__name__}: {exc}"}
+    sm = d["summary"]
     return {"metric": d["metric"], "unit": d["unit"], "higher_is_better": False, "learned_median_s": d["value"],
             "random_gpx_median_s": d["random_gpx"], "learned_over_random": d["learned_over_random"],
-            "config": d["config"], "summary": d["summary"],
+            "best_found": {"learned_median_s": sm["learned"]["median_time_to_best_found_s"],
+                           "random_gpx_median_s": sm["random"]["median_time_to_best_found_s"],
+                           "learned_over_random": d.get("found_learned_over_random"),
+                           "per_seed_s": {m: [x.get("time_to_best_found_s") for x in d["runs"][m]]
+                                          for m in d["runs"]}},
+            "config": d["config"], "summary": sm,
             "per_seed_s": {m: [x["time_to_target_s"] for x in d["runs"][m]] for m in d["runs"]}}
 
 
@@ -471,17 +485,23 @@ def memetic_summary(runs, wall_points=(0.5, 1.0, 1.5, 2.0)):
         pear = [statistics.median([r["diagnostics"][i]["pred_pearson"] for r in rs
                                    if len(r["diagnostics"]) > i and r["diagnostics"][i]["pred_pearson"] is not None]
                                   or [float("nan")]) for i in range(gmax)]
+        fs = [r["time_to_best_found_s"] for r in rs if r.get("time_to_best_found_s") is not None]
         res[mode] = {"reached": len(ts), "runs": len(rs),
                      "median_time_to_target_s": statistics.median(ts) if len(ts) == len(rs) else None,
                      "mean_time_to_target_s": statistics.mean(ts) if len(ts) == len(rs) else None,
                      "mean_ci95_s": boot(ts) if len(ts) == len(rs) else None,
+                     "median_time_to_best_found_s": statistics.median(fs) if fs and len(fs) == len(rs) else None,
+                     "mean_time_to_best_found_s": statistics.mean(fs) if fs and len(fs) == len(rs) else None,
+                     "found_mean_ci95_s": boot(fs) if fs and len(fs) == len(rs) else None,
                      "median_generations": statistics.median(r["generations"] for r in rs),
                      "median_best_at_wall_s": at,
                      "median_offspring_f_mean_by_generation": [round(x, 1) for x in fmean],
                      "median_prediction_pearson_by_generation": [None if x != x else round(x, 3) for x in pear]}
     lm, rm = res["learned"]["median_time_to_target_s"], res["random"]["median_time_to_target_s"]
+    lf, rf = res["learned"]["median_time_to_best_found_s"], res["random"]["median_time_to_best_found_s"]
     return {"value": lm, "random_gpx": rm, "summary": res,
-            "learned_over_random": (lm / rm) if lm and rm else None}
+            "learned_over_random": (lm / rm) if lm and rm else None,
+            "found_learned_over_random": (lf / rf) if lf and rf else None}
 
 
 def run_wvcp_memetic(args):

@@ -433,6 +433,12 @@ dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const v
  * overlapping 2-4), and 7 the number of generations averaged; then clears them and sets the
  * recording state to enable. */
 dlm_status dlm_memetic_profile(dlm_ctx* ctx, dlm_memetic* mm, int32_t enable, double* stage_ms);
+/* Measurement utility: host *ms = device time from the start of the last dlm_memetic_step to the
+ * end of its best-so-far update (Algorithm 1 records S* right after the local search), i.e. how
+ * far into that generation its best colouring was known; the rest of the generation (training,
+ * distances, pool update, offspring) prepares the next one. Waits for that point of the stream;
+ * DLM_EINVAL before the first generation. */
+dlm_status dlm_memetic_found_ms(dlm_ctx* ctx, dlm_memetic* mm, double* ms);
 
 /* The vertex colouring problem (section "Adaptations of the algorithm for the vertex coloring
  * problem"): k-COL with decreasing k. Starting at k = prm->k, a memetic search (fresh random

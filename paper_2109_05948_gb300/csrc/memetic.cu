@@ -37,6 +37,8 @@ struct dlm_memetic {
   // the scorer trains on a side stream while the distances and the pool update run
   cudaStream_t side = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_trained = nullptr;
+  // the start of the last generation and the end of its best-so-far update (dlm_memetic_found_ms)
+  cudaEvent_t ev_gen = nullptr, ev_found = nullptr;
   // optional stage timing (dlm_memetic_profile): events at the stage boundaries of the main
   // stream (tabu, best-so-far, distances, pool update, matching, offspring) and around training
   bool prof = false;
@@ -304,6 +306,8 @@ extern "C" void dlm_memetic_destroy(dlm_memetic* mm) {
   for (auto e : mm->tev) if (e) cudaEventDestroy(e);
   if (mm->ev_ready) cudaEventDestroy(mm->ev_ready);
   if (mm->ev_trained) cudaEventDestroy(mm->ev_trained);
+  if (mm->ev_gen) cudaEventDestroy(mm->ev_gen);
+  if (mm->ev_found) cudaEventDestroy(mm->ev_found);
   if (mm->side) cudaStreamDestroy(mm->side);
   delete mm;
 }
@@ -359,6 +363,10 @@ extern "C" dlm_status dlm_memetic_create(dlm_ctx* ctx, const dlm_graph* g, const
        cudaEventCreateWithFlags(&mm->ev_trained, cudaEventDisableTiming) != cudaSuccess)) {
     cudaGetLastError();
     st = fail(ctx, DLM_ECUDA, "memetic_create: side stream");
+  }
+  if (st == DLM_OK && (cudaEventCreate(&mm->ev_gen) != cudaSuccess || cudaEventCreate(&mm->ev_found) != cudaSuccess)) {
+    cudaGetLastError();
+    st = fail(ctx, DLM_ECUDA, "memetic_create: events");
   }
   if (st != DLM_OK) { dlm_memetic_destroy(mm); return st; }
   // fingerprint (FNV-1a, 64 bits) of the graph's bit rows and of the parameters: a checkpoint
@@ -429,6 +437,7 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
   const size_t pn = (size_t)p * n;
   cudaStream_t s = ctx->stream;
   auto mark = [&](int i) { if (mm->prof) cudaEventRecord(mm->pev[i], s); };
+  DLM_CUDA(ctx, cudaEventRecord(mm->ev_gen, s));
   mark(0);
   // 1. local search of every offspring: S'_i <- TabuCol(S^O_i) (k-COL), or the iterated feasible
   //    and infeasible tabu search from S^O_i (WVCP; Pn, free until the gather, holds its running
@@ -447,6 +456,7 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
   // 2. best so far
   k_best_of<<<1, 1024, 0, s>>>(p, n, mm->fSp, mm->Sp, mm->best_f, mm->best_col);
   DLM_TRY(launch_check(ctx, "k_best_of"));
+  DLM_CUDA(ctx, cudaEventRecord(mm->ev_found, s));
   // diagnostics: the last selection's predictions against the conflicts its offspring reached
   k_gen_stats<<<1, 1024, 0, s>>>(p, mm->gen, (q.use_scorer && mm->gen > 0) ? 1 : 0, q.use_scorer ? 1 : 0, mm->pred,
                                  mm->fSp, mm->dstat);
@@ -708,6 +718,16 @@ extern "C" dlm_status dlm_col_descend(dlm_ctx* ctx, const dlm_graph* g, const dl
     if (!solved) break;
     *k_best = k;
   }
+  return DLM_OK;
+}
+
+extern "C" dlm_status dlm_memetic_found_ms(dlm_ctx* ctx, dlm_memetic* mm, double* ms) {
+  if (!ctx || !mm || !ms) return fail(ctx, DLM_EINVAL, "memetic_found_ms: null argument");
+  if (mm->gen == 0) return fail(ctx, DLM_EINVAL, "memetic_found_ms: no generation has run");
+  DLM_CUDA(ctx, cudaEventSynchronize(mm->ev_found));
+  float e = 0.f;
+  DLM_CUDA(ctx, cudaEventElapsedTime(&e, mm->ev_gen, mm->ev_found));
+  *ms = (double)e;
   return DLM_OK;
 }
 

@@ -72,7 +72,16 @@ struct dlm_scorer {
   bf16* dZT[4] = {};
   float* S[4] = {};
   float* Gb = nullptr;
-  float* part = nullptr;  // split-K partial sums
+  float* part[4] = {};  // split-K partial sums of dLambda_l, one buffer per layer
+  // the weight gradients of layer l (dLambda_l GEMM, its split-K sum, dGamma_l, dbeta_l) run on a
+  // side branch forked after the layer's transposes and joined before the Adam step, off the
+  // chain dZ_l -> dZ_{l-1} of the backward pass
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork[4] = {}, ev_join[4] = {};
+  // Adam's bias corrections of the coming step, formed on the side branch ([0] 1 - 0.9^t,
+  // [1] sqrt(1 - 0.999^t))
+  float* d_bc = nullptr;
+  cudaEvent_t ev_bc_fork = nullptr, ev_bc_join = nullptr;
   float* rowdotb = nullptr;
   float* outb = nullptr;
   float* dout = nullptr;
@@ -144,15 +153,15 @@ __global__ void k_convert(ConvArgs a) {
 }
 
 // G[o] = beta[o] + sum_f m[f] Gamma[f][o] for the 256 threads o of a block (m in shared memory,
-// f ascending; sixteen Gamma loads in flight; din a multiple of 16)
+// f ascending; thirty-two Gamma loads in flight; din a multiple of 32)
 __device__ __forceinline__ float gterm_col(const float* m, int din, const float* gam, const float* beta, int o) {
   float acc = 0.f;
-  for (int f = 0; f < din; f += 16) {
-    float g[16];
+  for (int f = 0; f < din; f += 32) {
+    float g[32];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) g[u] = gam[(size_t)(f + u) * kD + o];
+    for (int u = 0; u < 32; ++u) g[u] = gam[(size_t)(f + u) * kD + o];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc += m[f + u] * g[u];
+    for (int u = 0; u < 32; ++u) acc += m[f + u] * g[u];
   }
   return acc + beta[o];
 }
@@ -230,10 +239,20 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, int R, const int16_t
     for (int q = warp; q < R; q += 8) {
       float2 acc = make_float2(0.f, 0.f);
       if (q < k) {
-        // members in ascending order; eight embedding rows are loaded before they are added (the
+        // members in ascending order; sixteen (then eight) embedding rows are loaded before they are added (the
         // rows come from L2, so the loads of a class overlap), the sum keeps the member order
         int j = off[q];
         const int je = off[q + 1];
+        for (; j + 16 <= je; j += 16) {
+          float2 ef[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) ef[u] = *reinterpret_cast<const float2*>(E + (size_t)mem[j + u] * kD0 + 2 * lane);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            acc.x += ef[u].x;
+            acc.y += ef[u].y;
+          }
+        }
         for (; j + 8 <= je; j += 8) {
           float2 ef[8];
 #pragma unroll
@@ -339,19 +358,23 @@ __global__ void __launch_bounds__(kD) k_mean_gterm(const bf16* X, const bf16* Xl
 }
 
 // output = head bias + mean over the k class rows of the head dot, whose row values come in
-// `parts` column slices of M = c * R rows each (summed in slice order)
-__global__ void k_head_out(int c, int k, int R, const float* rowdot, int parts, const float* theta, size_t obh,
-                           float* out) {
-  const int cand = blockIdx.x * blockDim.x + threadIdx.x;
+// `parts` column slices of M = c * R rows each (summed in slice order). One warp per candidate:
+// lane l sums rows l, l + 32, ... in order, then a fixed butterfly over the lanes.
+constexpr int kHeadOutWarps = 8;
+__global__ void __launch_bounds__(32 * kHeadOutWarps) k_head_out(int c, int k, int R, const float* rowdot, int parts,
+                                                                 const float* theta, size_t obh, float* out) {
+  const int cand = blockIdx.x * kHeadOutWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (cand >= c) return;
   const size_t M = (size_t)c * R;
   float s = 0.f;
-  for (int r = 0; r < k; ++r) {
+  for (int r = lane; r < k; r += 32) {
     float t = rowdot[(size_t)cand * R + r];
     for (int q = 1; q < parts; ++q) t += rowdot[q * M + (size_t)cand * R + r];
     s += t;
   }
-  out[cand] = theta[obh] + s / (float)k;
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
+  if (lane == 0) out[cand] = theta[obh] + s / (float)k;
 }
 
 // 32x32 tile (bx, by) of the transpose of a bf16 [rows][cols] matrix into [cols][rows]; 256
@@ -593,13 +616,21 @@ __device__ __forceinline__ void head_grad_col(int B, const float* dout, const fl
   }
 }
 
-// blocks 0 .. rows - 1: dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows (thread = column);
-// block rows: the head's gradient (wh[o] = sum_cand dout * mean(H3)[cand][o], bh = sum dout)
+// blocks 0 .. ceil(rows / kHeadRows) - 1: dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows
+// (thread = column, kHeadRows rows a block); the last block: the head's gradient
+// (wh[o] = sum_cand dout * mean(H3)[cand][o], bh = sum dout)
+constexpr int kHeadRows = 8;
 __global__ void __launch_bounds__(kD) k_head_bwd(int B, int k, int R, int rows, const float* dout, const float* theta,
                                                  size_t owh, size_t obh, const bf16* H3, const float* Mf3, bf16* dZ3,
                                                  float* grad) {
-  if ((int)blockIdx.x < rows) head_back_row(k, R, dout, theta, owh, H3, dZ3, blockIdx.x, threadIdx.x);
-  else head_grad_col(B, dout, Mf3, grad, owh, obh, threadIdx.x);
+  const int rb = (int)blockIdx.x * kHeadRows;
+  if (rb < rows) {
+#pragma unroll
+    for (int i = 0; i < kHeadRows; ++i)
+      if (rb + i < rows) head_back_row(k, R, dout, theta, owh, H3, dZ3, rb + i, threadIdx.x);
+  } else {
+    head_grad_col(B, dout, Mf3, grad, owh, obh, threadIdx.x);
+  }
 }
 
 // dGamma[f][o] = sum_cand Mprev[cand][f] * S[cand][o]; dbeta[o] = sum_cand S[cand][o]
@@ -654,17 +685,18 @@ __device__ __forceinline__ void gb_cand(int din, int k, const float* S, const fl
   }
 }
 
-// grad[dst + i] = sum_z part[z][i]
-// backward layer l, after its weight-gradient GEMM (256 threads a block):
+// backward layer l (256 threads a block), with grads set (after its weight-gradient GEMM):
 //   blocks [0, cnt / 256)   dLambda = sum of the split-K slices (fixed slice order)
 //   next din blocks         dGamma row f and (f = 0) dbeta
-//   next B blocks           the per-candidate term Gb of dH_{l-1}
+// and then, with gb set, B blocks: the per-candidate term Gb of dH_{l-1} (it needs only the
+// column sums S, so it runs before the weight gradients are done)
 __global__ void __launch_bounds__(kD) k_bwd_grads(int B, int din, int k, int64_t cnt, int splits, const float* part,
                                                   float* dlam, const float* Mprev, const float* S, float* grad,
-                                                  const float* theta, size_t ogam, size_t ob, float* Gb) {
+                                                  const float* theta, size_t ogam, size_t ob, float* Gb, int grads) {
   __shared__ float ss[kD];
-  const int64_t nr = (cnt + 255) / 256;
+  const int64_t nr = grads ? (cnt + 255) / 256 : 0;
   int64_t t = blockIdx.x;
+  if (!grads) t += din;
   if (t < nr) {
     const int64_t i = t * 256 + threadIdx.x;
     if (i >= cnt) return;
@@ -674,7 +706,7 @@ __global__ void __launch_bounds__(kD) k_bwd_grads(int B, int din, int k, int64_t
     return;
   }
   t -= nr;
-  if (t < din) {
+  if (t < din) {  // (grads only: without, t starts at din)
     dgamma_col(B, din, Mprev, S, grad, ogam, ob, (int)t, threadIdx.x);
     return;
   }
@@ -682,15 +714,22 @@ __global__ void __launch_bounds__(kD) k_bwd_grads(int B, int din, int k, int64_t
 }
 
 // embedding gradient: dE[v][f] = sum_cand dZ0[cand*R + col_cand[v]][f]; db0[f] = sum_cand S0[cand][f]
-// (with perm, candidate c of the batch is sample perm[step[0] + c] of cols)
-__global__ void k_demb(int n, int B, int R, const int16_t* cols, const int32_t* perm, const int32_t* step,
-                       const bf16* dZ0, const float* S0, float* grad, size_t oE, size_t ob0) {
-  const int v = blockIdx.x, f = threadIdx.x;  // 64 threads
+// (with perm, candidate c of the batch is sample perm[step[0] + c] of cols). Block v (256
+// threads = kDembGroups groups of kD0 features): group g sums the candidates of its contiguous
+// share in order, eight loads in flight, then the groups' sums are added in group order.
+constexpr int kDembGroups = 256 / kD0;
+__global__ void __launch_bounds__(256) k_demb(int n, int B, int R, const int16_t* cols, const int32_t* perm,
+                                              const int32_t* step, const bf16* dZ0, const float* S0, float* grad,
+                                              size_t oE, size_t ob0) {
+  __shared__ float ps[kDembGroups][kD0];
+  const int v = blockIdx.x, f = threadIdx.x % kD0, grp = threadIdx.x / kD0;
+  const int share = (B + kDembGroups - 1) / kDembGroups;
+  const int c0 = min(B, grp * share), c1 = min(B, c0 + share);
   auto row = [&](int c) -> size_t { return (size_t)(perm ? perm[step[0] + c] : c) * n; };
+  float s = 0.f;
   if (v < n) {
-    float s = 0.f;
-    int c = 0;
-    for (; c + 8 <= B; c += 8) {  // eight candidates' colour and gradient loads in flight
+    int c = c0;
+    for (; c + 8 <= c1; c += 8) {  // eight candidates' colour and gradient loads in flight
       int q[8];
       float z[8];
 #pragma unroll
@@ -700,32 +739,40 @@ __global__ void k_demb(int n, int B, int R, const int16_t* cols, const int32_t* 
 #pragma unroll
       for (int u = 0; u < 8; ++u) s += z[u];
     }
-    for (; c < B; ++c) {
+    for (; c < c1; ++c) {
       const int q = cols[row(c) + v];
       s += __bfloat162float(dZ0[((size_t)c * R + q) * kD0 + f]);
     }
-    grad[oE + (size_t)v * kD0 + f] = s;
   } else {
-    float b = 0.f;
-    for (int c = 0; c < B; ++c) b += S0[(size_t)c * kD0 + f];
-    grad[ob0 + f] = b;
+    for (int c = c0; c < c1; ++c) s += S0[(size_t)c * kD0 + f];
+  }
+  ps[grp][f] = s;
+  __syncthreads();
+  if (grp == 0) {
+    float t = ps[0][f];
+#pragma unroll
+    for (int g = 1; g < kDembGroups; ++g) t += ps[g][f];
+    grad[(v < n ? oE + (size_t)v * kD0 : ob0) + f] = t;
   }
 }
 
-// Adam step t + 1 (t = step[1]) of every parameter, then the parameter's bf16 operand copies
-// (those k_convert writes). Bias corrections 1 - 0.9^t and sqrt(1 - 0.999^t) in double.
-__global__ void __launch_bounds__(256) k_adam_convert(int64_t np, float* th, float* m, float* v, const float* g,
-                                                      float lr, const int32_t* step, ConvArgs a) {
-  __shared__ float bc[2];
-  if (threadIdx.x == 0) {
+// Adam's bias corrections of step t + 1 (t = step[1]) in double, by one thread: 1 - 0.9^(t+1) and
+// sqrt(1 - 0.999^(t+1)), rounded to float
+__global__ void k_adam_bias(const int32_t* step, float* bc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
     const double t = (double)(step[1] + 1);
     bc[0] = (float)(1.0 - pow(0.9, t));
     bc[1] = (float)sqrt(1.0 - pow(0.999, t));
   }
-  __syncthreads();
+}
+
+// Adam step t + 1 (t = step[1]) of every parameter with the bias corrections bc of k_adam_bias,
+// then the parameter's bf16 operand copies (those k_convert writes).
+__global__ void __launch_bounds__(256) k_adam_convert(int64_t np, float* th, float* m, float* v, const float* g,
+                                                      float lr, const float* bc, ConvArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
-  const float bc1 = bc[0], sbc2 = bc[1];
+  const float bc1 = bc[0], sbc2 = bc[1];  // the same two words for every thread (L1 broadcast)
   const float gi = g[i];
   const float mi = 0.9f * m[i] + 0.1f * gi;
   const float vi = 0.999f * v[i] + 0.001f * gi * gi;
@@ -1031,7 +1078,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
-  k_head_out<<<(c + 127) / 128, 128, 0, ctx->stream>>>(c, s->k, s->R, rowdot,
+  k_head_out<<<(c + kHeadOutWarps - 1) / kHeadOutWarps, 32 * kHeadOutWarps, 0, ctx->stream>>>(c, s->k, s->R, rowdot,
                                                        (train && rows < kWideRows) ? kD / 32 : kD / 128, s->theta,
                                                        s->obh, out);
   return launch_check(ctx, "k_head_out");
@@ -1047,9 +1094,10 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
   const int rows = B * s->R;
   k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, perm, step, s->dout, s->lossd);
   DLM_TRY(launch_check(ctx, "k_loss"));
-  k_head_bwd<<<rows + 1, kD, 0, ctx->stream>>>(B, s->k, s->R, rows, s->dout, s->theta, s->owh, s->obh, s->Hb[kNL],
+  k_head_bwd<<<(rows + kHeadRows - 1) / kHeadRows + 1, kD, 0, ctx->stream>>>(B, s->k, s->R, rows, s->dout, s->theta, s->owh, s->obh, s->Hb[kNL],
                                                s->Mfb[kNL], s->dZ[kNL], s->grad);
   DLM_TRY(launch_check(ctx, "k_head_bwd"));
+  cudaStream_t main_stream = ctx->stream;
   for (int l = kNL; l >= 1; --l) {
     const int din = din_of(l);
     // column sums of dZ_l per candidate (valid rows are the only nonzero ones) and the
@@ -1059,19 +1107,35 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
         B, s->k, s->R, rows, din, s->dZ[l], s->S[l], s->dZT[l], s->Hb[l - 1], s->Hblo[l - 1], s->HT[l - 1],
         s->HTlo[l - 1]);
     DLM_TRY(launch_check(ctx, "k_bwd_prep"));
-    // dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction; the tile width does
-    // not change any sum)
+    // side branch: dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction; the tile
+    // width does not change any sum), then the split sums into dLambda_l, dGamma_l and dbeta_l.
+    // It reads the transposes, S_l and the activations of this step, and writes only layer l's
+    // gradient blocks and its own partial-sum buffer.
     const int nchunks = rows / tc::BK, kc = 4, splits = (nchunks + kc - 1) / kc;
-    const EpiPartial ep{s->part, kD, din, (size_t)din * kD};
-    if (rows < kWideRows)
-      DLM_TRY((gemm<64, 1>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc, ep)));
-    else
-      DLM_TRY((gemm<256>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows, kc, ep)));
-    // the split sums into dLambda_l, dGamma_l and dbeta_l, and the per-candidate term of dH_{l-1}
     const int64_t cnt = (int64_t)din * kD;
-    k_bwd_grads<<<(unsigned)((cnt + 255) / 256 + din + B), kD, 0, ctx->stream>>>(
-        B, din, s->k, cnt, splits, s->part, s->grad + s->olam[l], s->Mfb[l - 1], s->S[l], s->grad, s->theta,
-        s->ogam[l], s->ob[l], s->Gb);
+    DLM_CUDA(ctx, cudaEventRecord(s->ev_fork[l], main_stream));
+    DLM_CUDA(ctx, cudaStreamWaitEvent(s->side, s->ev_fork[l], 0));
+    ctx->stream = s->side;
+    {
+      const EpiPartial ep{s->part[l], kD, din, (size_t)din * kD};
+      dlm_status st = rows < kWideRows
+                          ? gemm<64, 1>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD,
+                                        rows, kc, ep)
+                          : gemm<256>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows,
+                                      kc, ep);
+      if (st == DLM_OK) {
+        k_bwd_grads<<<(unsigned)((cnt + 255) / 256 + din), kD, 0, ctx->stream>>>(
+            B, din, s->k, cnt, splits, s->part[l], s->grad + s->olam[l], s->Mfb[l - 1], s->S[l], s->grad, s->theta,
+            s->ogam[l], s->ob[l], nullptr, 1);
+        st = launch_check(ctx, "k_bwd_grads");
+      }
+      if (st == DLM_OK) st = cuda_check(ctx, cudaEventRecord(s->ev_join[l], s->side), "event");
+      ctx->stream = main_stream;
+      DLM_TRY(st);
+    }
+    // the per-candidate term of dH_{l-1} (from S_l and Gamma_l) on the main chain
+    k_bwd_grads<<<(unsigned)B, kD, 0, ctx->stream>>>(B, din, s->k, cnt, splits, nullptr, nullptr, nullptr, s->S[l],
+                                                     nullptr, s->theta, s->ogam[l], s->ob[l], s->Gb, 0);
     DLM_TRY(launch_check(ctx, "k_bwd_grads"));
     // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
     EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->R, s->Gb, s->Hb[l - 1]};
@@ -1081,8 +1145,10 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
       DLM_TRY((gemm<256>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
   }
   k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, s->R, 1.f, s->S[0], nullptr, nullptr);
-  k_demb<<<s->n + 1, kD0, 0, ctx->stream>>>(s->n, B, s->R, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
-  return launch_check(ctx, "k_demb");
+  k_demb<<<s->n + 1, 256, 0, ctx->stream>>>(s->n, B, s->R, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
+  DLM_TRY(launch_check(ctx, "k_demb"));
+  for (int l = 1; l <= kNL; ++l) DLM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_join[l], 0));
+  return DLM_OK;
 }
 
 static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
@@ -1104,7 +1170,25 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
     DLM_TRY(dalloc(ctx, &s->S[l], (size_t)cb * w));
   }
   DLM_TRY(dalloc(ctx, &s->Gb, (size_t)cb * kD));
-  DLM_TRY(dalloc(ctx, &s->part, (size_t)(rows / tc::BK / 4 + 1) * kD * kD));
+  for (int l = 1; l <= kNL; ++l) DLM_TRY(dalloc(ctx, &s->part[l], (size_t)(rows / tc::BK / 4 + 1) * kD * kD));
+  if (!s->side) {
+    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, DLM_ECUDA, "scorer: side stream");
+    }
+    for (int l = 1; l <= kNL; ++l)
+      if (cudaEventCreateWithFlags(&s->ev_fork[l], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s->ev_join[l], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, DLM_ECUDA, "scorer: events");
+      }
+    if (cudaEventCreateWithFlags(&s->ev_bc_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_bc_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, DLM_ECUDA, "scorer: events");
+    }
+    DLM_TRY(dalloc(ctx, &s->d_bc, 2));
+  }
   DLM_TRY(dalloc(ctx, &s->rowdotb, (size_t)rows * (kD / 32)));
   DLM_TRY(dalloc(ctx, &s->outb, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->dout, (size_t)cb));
@@ -1133,9 +1217,16 @@ static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
 // one Adam step of batch size B (batch offset and step counter on the device): the batch is read
 // through the epoch permutation, the Adam update writes the bf16 operand copies too
 static dlm_status train_step(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int B, int b, float lr) {
+  // the bias corrections (a short double-precision chain) on the side branch, off the critical path
+  DLM_CUDA(ctx, cudaEventRecord(s->ev_bc_fork, ctx->stream));
+  DLM_CUDA(ctx, cudaStreamWaitEvent(s->side, s->ev_bc_fork, 0));
+  k_adam_bias<<<1, 32, 0, s->side>>>(s->d_step, s->d_bc);
+  DLM_TRY(launch_check(ctx, "k_adam_bias"));
+  DLM_CUDA(ctx, cudaEventRecord(s->ev_bc_join, s->side));
   DLM_TRY(loss_grad(ctx, s, cols, s->y, B, s->perm, s->d_step));
+  DLM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_bc_join, 0));
   k_adam_convert<<<(unsigned)((s->np + 255) / 256), 256, 0, ctx->stream>>>(s->np, s->theta, s->am, s->av, s->grad, lr,
-                                                                          s->d_step, conv_args(s, nullptr));
+                                                                          s->d_bc, conv_args(s, nullptr));
   DLM_TRY(launch_check(ctx, "k_adam_convert"));
   k_step_end<<<1, 1, 0, ctx->stream>>>(s->d_step, b);
   return launch_check(ctx, "k_step_end");
@@ -1186,6 +1277,15 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
   for (auto& g : s->sg)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  for (int l = 0; l < 4; ++l) {
+    cudaFree(s->part[l]);
+    if (s->ev_fork[l]) cudaEventDestroy(s->ev_fork[l]);
+    if (s->ev_join[l]) cudaEventDestroy(s->ev_join[l]);
+  }
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->ev_bc_fork) cudaEventDestroy(s->ev_bc_fork);
+  if (s->ev_bc_join) cudaEventDestroy(s->ev_bc_join);
+  cudaFree(s->d_bc);
   cudaFree(s->d_step);
   cudaFree(s->theta); cudaFree(s->am); cudaFree(s->av); cudaFree(s->grad); cudaFree(s->E16);
   for (int l = 0; l <= kNL; ++l) {
@@ -1195,7 +1295,7 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
     cudaFree(s->Hb[l]); cudaFree(s->Hblo[l]); cudaFree(s->HT[l]); cudaFree(s->HTlo[l]); cudaFree(s->Mbb[l]); cudaFree(s->Mfb[l]); cudaFree(s->Gbf[l]);
     cudaFree(s->dZ[l]); cudaFree(s->dZT[l]); cudaFree(s->S[l]);
   }
-  cudaFree(s->rowdot); cudaFree(s->Gb); cudaFree(s->part); cudaFree(s->rowdotb); cudaFree(s->outb); cudaFree(s->dout);
+  cudaFree(s->rowdot); cudaFree(s->Gb); cudaFree(s->rowdotb); cudaFree(s->outb); cudaFree(s->dout);
   cudaFree(s->lossd); cudaFree(s->y); cudaFree(s->perm);
   delete s;
 }

@@ -108,6 +108,7 @@ _SIGS = {
     "dlm_memetic_set": (_i32, [_P, _P, _i32, _P]),
     "dlm_col_descend": (_i32, [_P, _P, _P, _i32, _P, _P, _P]),
     "dlm_memetic_profile": (_i32, [_P, _P, _i32, _P]),
+    "dlm_memetic_found_ms": (_i32, [_P, _P, _P]),
     "dlm_memetic_state_bytes": (_i64, [_P]),
     "dlm_memetic_save": (_i32, [_P, _P, _P]),
     "dlm_memetic_load": (_i32, [_P, _P, _P]),
@@ -454,6 +455,13 @@ def dlm_memetic_step(ctx, mm):
     best = ctypes.c_int64(0)
     ctx.check(lib().dlm_memetic_step(ctx.h, mm.h, ctypes.byref(best)), "dlm_memetic_step")
     return best.value
+
+
+def dlm_memetic_found_ms(ctx, mm):
+    """ms from the start of the last generation to the end of its best-so-far update."""
+    out = ctypes.c_double(0.0)
+    ctx.check(lib().dlm_memetic_found_ms(ctx.h, mm.h, ctypes.byref(out)), "dlm_memetic_found_ms")
+    return out.value
 
 
 def dlm_memetic_get(ctx, mm, which, dst):

@@ -73,3 +73,24 @@ def test_generation_log_lines(tmp_path):
     lines = [json.loads(x) for x in path.read_text().splitlines()]
     assert [x["generation"] for x in lines] == [0, 1]
     assert lines[0]["elapsed_s"] == 0.5123 and lines[1]["pred_pearson"] == 0.7 and lines[0]["best"] == 17
+
+
+def test_memetic_summary_reports_both_times():
+    """The summary gives the time at the end of the generation that reached the target and the
+    earlier time at which its best-so-far update recorded the target (per mode, with medians)."""
+    def run(seed, hit, found, gens):
+        traj = [[round(hit * (g + 1) / gens, 3), 0 if g == gens - 1 else 5] for g in range(gens)]
+        return {"seed": seed, "time_to_target_s": hit, "time_to_best_found_s": found, "generations": gens,
+                "best": 0, "trajectory": traj,
+                "diagnostics": [{"f_mean": 1.0, "pred_pearson": None} for _ in range(gens)]}
+
+    runs = {"learned": [run(0, 1.4, 1.1, 3), run(1, 1.4, 1.2, 3), run(2, 1.8, 1.5, 4)],
+            "random": [run(0, 1.3, 1.2, 4), run(1, 1.0, 0.9, 3), run(2, 1.3, 1.25, 4)]}
+    out = bench.memetic_summary(runs)
+    assert out["value"] == 1.4 and out["random_gpx"] == 1.3
+    assert out["summary"]["learned"]["median_time_to_best_found_s"] == 1.2
+    assert out["summary"]["random"]["median_time_to_best_found_s"] == 1.2
+    assert out["found_learned_over_random"] == 1.0
+    assert out["summary"]["learned"]["mean_time_to_best_found_s"] == pytest.approx((1.1 + 1.2 + 1.5) / 3)
+    runs["random"][0]["time_to_best_found_s"] = None  # a run that never reached the target
+    assert bench.memetic_summary(runs)["summary"]["random"]["median_time_to_best_found_s"] is None

@@ -1,6 +1,8 @@
 """GPU parity of whole memetic generations (Algorithm 1) against the oracle, through the C-ABI.
 Random-GPX generations are integer work and must match bit for bit; learned generations match bit
 for bit when the oracle selects offspring with the GPU's scores."""
+import time
+
 import numpy as np
 import pytest
 
@@ -51,8 +53,14 @@ def test_memetic_random_gpx_bitexact(ctx, n, k, p, K, iters, gens, seed):
     mm = dlmcol.Memetic(ctx, g, prm)
     st = oracle.MemeticState(adj, k, p, K, seed=seed, iters=iters, use_scorer=0)
     _compare(ctx, mm, st, p, n, K, -1)
+    with pytest.raises(dlmcol.DlmError):  # no generation has run yet
+        dlmcol.dlm_memetic_found_ms(ctx, mm)
     for gen in range(gens):
+        t0 = time.perf_counter()
         best = dlmcol.dlm_memetic_step(ctx, mm)
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        # the best-so-far update ends inside the generation, after its local search
+        assert 0.0 < dlmcol.dlm_memetic_found_ms(ctx, mm) <= wall_ms
         fprime, pick = st.generation()
         assert np.array_equal(_get(ctx, mm, 5, (p,), torch.int64), fprime)
         assert np.array_equal(_get(ctx, mm, 6, (p,), torch.int32), pick)
