@@ -427,11 +427,12 @@ dlm_status dlm_memetic_set(dlm_ctx* ctx, dlm_memetic* mm, int32_t which, const v
 
 /* Measurement utility (no counterpart in the paper): while enabled, dlm_memetic_step records CUDA
  * events at its stage boundaries (and waits for its last one). dlm_memetic_profile returns in
- * stage_ms (host [8] double, or NULL) the mean ms per generation since the previous call of:
+ * stage_ms (host [11] double, or NULL) the mean ms per generation since the previous call of:
  * 0 tabu search, 1 best so far, 2 distances, 3 pool update and gathers, 4 matching, 5 offspring
  * (GPX, and scoring and selection with the scorer), 6 scorer training (on its side stream,
- * overlapping 2-4), and 7 the number of generations averaged; then clears them and sets the
- * recording state to enable. */
+ * overlapping 2-4), 7 the number of generations averaged, and with the scorer the parts of
+ * stage 5: 8 GPX of the K candidates, 9 the wait for the training, 10 scoring and selection;
+ * then clears them and sets the recording state to enable. */
 dlm_status dlm_memetic_profile(dlm_ctx* ctx, dlm_memetic* mm, int32_t enable, double* stage_ms);
 /* Measurement utility: host *ms = device time from the start of the last dlm_memetic_step to the
  * end of its best-so-far update (Algorithm 1 records S* right after the local search), i.e. how

@@ -42,8 +42,10 @@ struct dlm_memetic {
   // optional stage timing (dlm_memetic_profile): events at the stage boundaries of the main
   // stream (tabu, best-so-far, distances, pool update, matching, offspring) and around training
   bool prof = false;
-  cudaEvent_t pev[8] = {}, tev[2] = {};
-  double stage_ms[7] = {};
+  // (pev[7], pev[8]: the offspring stage's GPX end and, with the scorer, the end of its wait for
+  // the training)
+  cudaEvent_t pev[9] = {}, tev[2] = {};
+  double stage_ms[10] = {};
   int64_t prof_gens = 0;
 };
 
@@ -511,7 +513,9 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     k_pairs_all<<<(p * K + 255) / 256, 256, 0, s>>>(p, K, mm->nbr, mm->pairs, mm->cid);
     DLM_TRY(launch_check(ctx, "k_pairs_all"));
     DLM_TRY(dlm_gpx_batch(ctx, n, k, mm->P, p, mm->pairs, mm->cid, p * K, mm->kids, q.seed, mm->gen));
+    mark(7);
     DLM_CUDA(ctx, cudaStreamWaitEvent(s, mm->ev_trained, 0));
+    mark(8);
     if (mm->deep) DLM_TRY(dlm_deepnet_forward(ctx, mm->deep, mm->kids, p * K, 0, mm->scores));
     else DLM_TRY(dlm_score_offspring(ctx, mm->scorer, mm->kids, p * K, mm->scores));
     k_select_best<<<p, 128, 0, s>>>(p, K, n, mm->scores, mm->kids, mm->SO, mm->pick, mm->pred);
@@ -530,6 +534,11 @@ extern "C" dlm_status dlm_memetic_step(dlm_ctx* ctx, dlm_memetic* mm, int64_t* b
     }
     float e = 0.f;
     if (q.use_scorer && cudaEventElapsedTime(&e, mm->tev[0], mm->tev[1]) == cudaSuccess) mm->stage_ms[6] += e;
+    if (q.use_scorer) {  // the offspring stage in three parts: GPX, the wait for training, scoring and selection
+      if (cudaEventElapsedTime(&e, mm->pev[5], mm->pev[7]) == cudaSuccess) mm->stage_ms[7] += e;
+      if (cudaEventElapsedTime(&e, mm->pev[7], mm->pev[8]) == cudaSuccess) mm->stage_ms[8] += e;
+      if (cudaEventElapsedTime(&e, mm->pev[8], mm->pev[6]) == cudaSuccess) mm->stage_ms[9] += e;
+    }
     ++mm->prof_gens;
   }
   mm->gen++;
@@ -736,6 +745,7 @@ extern "C" dlm_status dlm_memetic_profile(dlm_ctx* ctx, dlm_memetic* mm, int32_t
   if (stage_ms) {
     for (int i = 0; i < 7; ++i) stage_ms[i] = mm->prof_gens ? mm->stage_ms[i] / (double)mm->prof_gens : 0.0;
     stage_ms[7] = (double)mm->prof_gens;
+    for (int i = 7; i < 10; ++i) stage_ms[i + 1] = mm->prof_gens ? mm->stage_ms[i] / (double)mm->prof_gens : 0.0;
   }
   for (auto& x : mm->stage_ms) x = 0.0;
   mm->prof_gens = 0;

@@ -76,7 +76,7 @@ struct dlm_scorer {
   // the weight gradients of layer l (dLambda_l GEMM, its split-K sum, dGamma_l, dbeta_l) run on a
   // side branch forked after the layer's transposes and joined before the Adam step, off the
   // chain dZ_l -> dZ_{l-1} of the backward pass
-  cudaStream_t side = nullptr;
+  cudaStream_t side[4] = {};  // one branch stream per layer (the branches of a step overlap)
   cudaEvent_t ev_fork[4] = {}, ev_join[4] = {};
   // Adam's bias corrections of the coming step, formed on the side branch ([0] 1 - 0.9^t,
   // [1] sqrt(1 - 0.999^t))
@@ -345,16 +345,67 @@ __global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, i
   segment_col(X, Xlo, w, k, R, scale, outf, outb, outblo, blockIdx.x, threadIdx.x);
 }
 
-// a training batch between layers l and l + 1: the class mean of H_l (written as above), then
-// the next layer's per-candidate term G = beta + mean Gamma (block = 256 threads, one candidate)
-__global__ void __launch_bounds__(kD) k_mean_gterm(const bf16* X, const bf16* Xlo, int k, int R, float* outf,
-                                                   bf16* outb, bf16* outblo, const float* gam, const float* beta,
-                                                   float* G) {
+// a training batch between layers l and l + 1: the class mean of H_l (written as segment_col
+// writes it), then the next layer's per-candidate term G = beta + mean Gamma. One candidate per
+// block of kMgGroups x kD threads: group g sums its contiguous share of the k rows (in row order)
+// and then its quarter of the rows f of Gamma; the groups' parts are added in group order.
+constexpr int kMgGroups = 4;
+__global__ void __launch_bounds__(kMgGroups * kD) k_mean_gterm(const bf16* X, const bf16* Xlo, int k, int R,
+                                                               float* outf, bf16* outb, bf16* outblo, const float* gam,
+                                                               const float* beta, float* G) {
   __shared__ float ms[kD];
-  const int cand = blockIdx.x, o = threadIdx.x;
-  ms[o] = segment_col(X, Xlo, kD, k, R, 1.f / k, outf, outb, outblo, cand, o);
+  __shared__ float part[kMgGroups][kD];
+  const int cand = blockIdx.x, o = threadIdx.x % kD, grp = threadIdx.x / kD;
+  {  // class mean: rows [r0, r1) of this group, eight loads in flight
+    const int share = (k + kMgGroups - 1) / kMgGroups;
+    const int r0 = min(k, grp * share), r1 = min(k, r0 + share);
+    const bf16* x = X + (size_t)cand * R * kD + o;
+    const bf16* xl = Xlo ? Xlo + (size_t)cand * R * kD + o : nullptr;
+    float sum = 0.f;
+    int r = r0;
+    for (; r + 8 <= r1; r += 8) {
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        t[u] = __bfloat162float(x[(size_t)(r + u) * kD]) + (xl ? __bfloat162float(xl[(size_t)(r + u) * kD]) : 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sum += t[u];
+    }
+    for (; r < r1; ++r) sum += __bfloat162float(x[(size_t)r * kD]) + (xl ? __bfloat162float(xl[(size_t)r * kD]) : 0.f);
+    part[grp][o] = sum;
+  }
   __syncthreads();
-  G[(size_t)cand * kD + o] = gterm_col(ms, kD, gam, beta, o);
+  if (grp == 0) {
+    float m = part[0][o];
+#pragma unroll
+    for (int g = 1; g < kMgGroups; ++g) m += part[g][o];
+    m *= 1.f / (float)k;
+    ms[o] = m;
+    outf[(size_t)cand * kD + o] = m;
+    const bf16 hi = __float2bfloat16_rn(m);
+    outb[(size_t)cand * kD + o] = hi;
+    outblo[(size_t)cand * kD + o] = __float2bfloat16_rn(m - __bfloat162float(hi));
+  }
+  __syncthreads();
+  {  // this group's rows f of Gamma, thirty-two loads in flight
+    constexpr int FQ = kD / kMgGroups;
+    float acc = 0.f;
+    for (int f = grp * FQ; f < (grp + 1) * FQ; f += 32) {
+      float g[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) g[u] = gam[(size_t)(f + u) * kD + o];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) acc += ms[f + u] * g[u];
+    }
+    part[grp][o] = acc;
+  }
+  __syncthreads();
+  if (grp == 0) {
+    float acc = part[0][o];
+#pragma unroll
+    for (int g = 1; g < kMgGroups; ++g) acc += part[g][o];
+    G[(size_t)cand * kD + o] = acc + beta[o];
+  }
 }
 
 // output = head bias + mean over the k class rows of the head dot, whose row values come in
@@ -401,7 +452,7 @@ __global__ void __launch_bounds__(256) k_bwd_prep(int B, int k, int R, int rows,
                                                   bf16* dZT, const bf16* H, const bf16* Hlo, bf16* HT, bf16* HTlo) {
   __shared__ bf16 tile[32][33];
   int t = blockIdx.x;
-  if (t < B) {
+  if (t < B) {  // (B = 0: the transposes alone)
     segment_col(dZ, nullptr, kD, k, R, 1.f, S, nullptr, nullptr, t, threadIdx.x);
     return;
   }
@@ -657,46 +708,14 @@ __device__ __forceinline__ void dgamma_col(int B, int din, const float* Mprev, c
   }
 }
 
-// Gb[cand][f] = (1/k) sum_o S[cand][o] * Gamma[f][o]; one block of kD threads per candidate,
-// warp w takes rows f = w, w + 8, ...: its lanes read a Gamma row contiguously and reduce by a
-// fixed butterfly
-__device__ __forceinline__ void gb_cand(int din, int k, const float* S, const float* theta, size_t ogam, float* Gb,
-                                        int cand, float (&ss)[kD]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ss[threadIdx.x] = S[(size_t)cand * kD + threadIdx.x];
-  __syncthreads();
-  const float* gam = theta + ogam;
-  constexpr int kStep = kD / 32;  // rows f = warp, warp + 8, ...; four of them in flight (din % 32 == 0)
-  for (int f0 = warp; f0 < din; f0 += 4 * kStep) {
-    float gv[4][kD / 32];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int i = 0; i < kD / 32; ++i) gv[q][i] = gam[(size_t)(f0 + q * kStep) * kD + lane + 32 * i];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int i = 0; i < kD / 32; ++i) acc += ss[lane + 32 * i] * gv[q][i];
-#pragma unroll
-      for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, d);
-      if (lane == 0) Gb[(size_t)cand * din + f0 + q * kStep] = acc / (float)k;
-    }
-  }
-}
-
-// backward layer l (256 threads a block), with grads set (after its weight-gradient GEMM):
+// backward layer l, after its weight-gradient GEMM (256 threads a block):
 //   blocks [0, cnt / 256)   dLambda = sum of the split-K slices (fixed slice order)
 //   next din blocks         dGamma row f and (f = 0) dbeta
-// and then, with gb set, B blocks: the per-candidate term Gb of dH_{l-1} (it needs only the
-// column sums S, so it runs before the weight gradients are done)
-__global__ void __launch_bounds__(kD) k_bwd_grads(int B, int din, int k, int64_t cnt, int splits, const float* part,
+__global__ void __launch_bounds__(kD) k_bwd_grads(int B, int din, int64_t cnt, int splits, const float* part,
                                                   float* dlam, const float* Mprev, const float* S, float* grad,
-                                                  const float* theta, size_t ogam, size_t ob, float* Gb, int grads) {
-  __shared__ float ss[kD];
-  const int64_t nr = grads ? (cnt + 255) / 256 : 0;
-  int64_t t = blockIdx.x;
-  if (!grads) t += din;
+                                                  size_t ogam, size_t ob) {
+  const int64_t nr = (cnt + 255) / 256;
+  const int64_t t = blockIdx.x;
   if (t < nr) {
     const int64_t i = t * 256 + threadIdx.x;
     if (i >= cnt) return;
@@ -705,12 +724,65 @@ __global__ void __launch_bounds__(kD) k_bwd_grads(int B, int din, int k, int64_t
     dlam[i] = s;
     return;
   }
-  t -= nr;
-  if (t < din) {  // (grads only: without, t starts at din)
-    dgamma_col(B, din, Mprev, S, grad, ogam, ob, (int)t, threadIdx.x);
-    return;
+  dgamma_col(B, din, Mprev, S, grad, ogam, ob, (int)(t - nr), threadIdx.x);
+}
+
+// backward layer l on the chain dZ_l -> dZ_{l-1}, one candidate per block of kMgGroups x kD
+// threads: the column sums S of its k valid rows of dZ_l (group g sums its contiguous share of the
+// rows in order, the groups' parts are added in group order; written out for dGamma_l and
+// dbeta_l), then the per-candidate term Gb[cand][f] = (1/k) sum_o S[o] Gamma[f][o] of dH_{l-1}:
+// warp w takes rows f = w, w + 32, ..., its lanes read a Gamma row contiguously and reduce by a
+// fixed butterfly
+__global__ void __launch_bounds__(kMgGroups * kD) k_bwd_sums_gb(int din, int k, int R, const bf16* dZ, float* S,
+                                                                const float* theta, size_t ogam, float* Gb) {
+  __shared__ float ss[kD];
+  __shared__ float part[kMgGroups][kD];
+  const int cand = blockIdx.x, o = threadIdx.x % kD, grp = threadIdx.x / kD;
+  {
+    const int share = (k + kMgGroups - 1) / kMgGroups;
+    const int r0 = min(k, grp * share), r1 = min(k, r0 + share);
+    const bf16* x = dZ + (size_t)cand * R * kD + o;
+    float sum = 0.f;
+    int r = r0;
+    for (; r + 8 <= r1; r += 8) {
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = __bfloat162float(x[(size_t)(r + u) * kD]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sum += t[u];
+    }
+    for (; r < r1; ++r) sum += __bfloat162float(x[(size_t)r * kD]);
+    part[grp][o] = sum;
   }
-  gb_cand(din, k, S, theta, ogam, Gb, (int)(t - din), ss);
+  __syncthreads();
+  if (grp == 0) {
+    float m = part[0][o];
+#pragma unroll
+    for (int g = 1; g < kMgGroups; ++g) m += part[g][o];
+    ss[o] = m;
+    S[(size_t)cand * kD + o] = m;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kMgGroups * kD / 32;  // warps of the block
+  const float* gam = theta + ogam;
+  for (int f0 = warp; f0 < din; f0 += 4 * NW) {  // four rows in flight
+    float gv[4][kD / 32];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int i = 0; i < kD / 32; ++i)
+        gv[q][i] = f0 + q * NW < din ? gam[(size_t)(f0 + q * NW) * kD + lane + 32 * i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int i = 0; i < kD / 32; ++i) acc += ss[lane + 32 * i] * gv[q][i];
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, d);
+      if (lane == 0 && f0 + q * NW < din) Gb[(size_t)cand * din + f0 + q * NW] = acc / (float)k;
+    }
+  }
 }
 
 // embedding gradient: dE[v][f] = sum_cand dZ0[cand*R + col_cand[v]][f]; db0[f] = sum_cand S0[cand][f]
@@ -931,6 +1003,11 @@ dlm_status make_map_bf16(dlm_ctx* ctx, CUtensorMap* map, const void* base, uint6
 // training batches of at least this many class rows (100 samples at k > 64) run their GEMMs as
 // 128 x 256 tiles with two pipeline stages, as the scoring pass does
 constexpr int kWideRows = 12288;
+// below that, the training GEMMs run as 128 x 128 tiles with one pipeline stage: one tile per CTA
+// for a batch of 100 samples at k <= 64 (100 CTAs), where 128 x 64 tiles give some CTAs two tiles
+// in sequence; about 66 KB of shared memory each, so that the CTAs also find room beside the
+// distance kernel that runs at the same time in a memetic generation
+constexpr int kTrainBN = 128;
 
 template <int BN, int ST = 0, class Epi>
 static dlm_status gemm(dlm_ctx* ctx, const bf16* A, const bf16* A2, int M, int K, int lda, const bf16* B, const bf16* B2,
@@ -1056,20 +1133,20 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       }
     }
     const bool last = l == kNL;
-    // a training batch of a few thousand rows runs its layer GEMMs as 128 x 64 tiles with one
-    // pipeline stage: four times the CTAs of a 128 x 256 tile, and about 50 KB of shared memory
-    // each instead of 193 KB; from kWideRows rows on (k > 64) 128 x 256 tiles fill the SMs
+    // a training batch of a few thousand rows runs its layer GEMMs as 128 x kTrainBN tiles with
+    // one pipeline stage (twice the CTAs of a 128 x 256 tile, and a third of its shared memory);
+    // from kWideRows rows on (k > 64) 128 x 256 tiles fill the SMs
     const bool narrow = train && rows < kWideRows;
     EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, s->R, G[l],
-               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, narrow ? 32 : 128, 0};
+               last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, narrow ? kTrainBN / 2 : 128, 0};
     if (narrow)
-      DLM_TRY((gemm<64, 1>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din,
+      DLM_TRY((gemm<kTrainBN, 1>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din,
                           0, e)));
     else
       DLM_TRY(gemm<256>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din, 0,
                         e));
     if (train && !last) {
-      k_mean_gterm<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, s->k, s->R, Mf[l], Mb[l], Mblo[l],
+      k_mean_gterm<<<c, kMgGroups * kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, s->k, s->R, Mf[l], Mb[l], Mblo[l],
                                               s->theta + s->ogam[l + 1], s->theta + s->ob[l + 1], G[l + 1]);
       DLM_TRY(launch_check(ctx, "k_mean_gterm"));
     } else if (!last || train) {
@@ -1079,7 +1156,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
     }
   }
   k_head_out<<<(c + kHeadOutWarps - 1) / kHeadOutWarps, 32 * kHeadOutWarps, 0, ctx->stream>>>(c, s->k, s->R, rowdot,
-                                                       (train && rows < kWideRows) ? kD / 32 : kD / 128, s->theta,
+                                                       (train && rows < kWideRows) ? kD / (kTrainBN / 2) : kD / 128, s->theta,
                                                        s->obh, out);
   return launch_check(ctx, "k_head_out");
 }
@@ -1100,46 +1177,46 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
   cudaStream_t main_stream = ctx->stream;
   for (int l = kNL; l >= 1; --l) {
     const int din = din_of(l);
-    // column sums of dZ_l per candidate (valid rows are the only nonzero ones) and the
-    // transposes of dZ_l and H_{l-1} (hi and lo) for the weight-gradient GEMM, in one launch
+    // main chain: the column sums S_l of dZ_l per candidate (valid rows are the only nonzero ones)
+    // and the per-candidate term Gb of dH_{l-1} (from S_l and Gamma_l), in one launch
+    k_bwd_sums_gb<<<(unsigned)B, kMgGroups * kD, 0, ctx->stream>>>(din, s->k, s->R, s->dZ[l], s->S[l], s->theta, s->ogam[l], s->Gb);
+    DLM_TRY(launch_check(ctx, "k_bwd_sums_gb"));
+    // side branch: the transposes of dZ_l and H_{l-1} (hi and lo), dLambda_l = H_{l-1}^T dZ_l
+    // (split-K over rows, fixed-order reduction; the tile width does not change any sum), then the
+    // split sums into dLambda_l, dGamma_l and dbeta_l. It reads dZ_l, S_l and this step's
+    // activations, and writes only layer l's gradient blocks, transposes and partial sums.
     const int ty = (rows + 31) / 32;
-    k_bwd_prep<<<B + ty * (kD / 32) + 2 * ty * (din / 32), 256, 0, ctx->stream>>>(
-        B, s->k, s->R, rows, din, s->dZ[l], s->S[l], s->dZT[l], s->Hb[l - 1], s->Hblo[l - 1], s->HT[l - 1],
-        s->HTlo[l - 1]);
-    DLM_TRY(launch_check(ctx, "k_bwd_prep"));
-    // side branch: dLambda_l = H_{l-1}^T dZ_l (split-K over rows, fixed-order reduction; the tile
-    // width does not change any sum), then the split sums into dLambda_l, dGamma_l and dbeta_l.
-    // It reads the transposes, S_l and the activations of this step, and writes only layer l's
-    // gradient blocks and its own partial-sum buffer.
     const int nchunks = rows / tc::BK, kc = 4, splits = (nchunks + kc - 1) / kc;
     const int64_t cnt = (int64_t)din * kD;
     DLM_CUDA(ctx, cudaEventRecord(s->ev_fork[l], main_stream));
-    DLM_CUDA(ctx, cudaStreamWaitEvent(s->side, s->ev_fork[l], 0));
-    ctx->stream = s->side;
+    DLM_CUDA(ctx, cudaStreamWaitEvent(s->side[l], s->ev_fork[l], 0));
+    ctx->stream = s->side[l];
     {
+      k_bwd_prep<<<ty * (kD / 32) + 2 * ty * (din / 32), 256, 0, ctx->stream>>>(
+          0, s->k, s->R, rows, din, s->dZ[l], nullptr, s->dZT[l], s->Hb[l - 1], s->Hblo[l - 1], s->HT[l - 1],
+          s->HTlo[l - 1]);
+      dlm_status st = launch_check(ctx, "k_bwd_prep");
       const EpiPartial ep{s->part[l], kD, din, (size_t)din * kD};
-      dlm_status st = rows < kWideRows
-                          ? gemm<64, 1>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD,
-                                        rows, kc, ep)
-                          : gemm<256>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD, rows,
-                                      kc, ep);
+      if (st == DLM_OK)
+        st = rows < kWideRows ? gemm<kTrainBN, 1>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD,
+                                            rows, kc, ep)
+                              : gemm<256>(ctx, s->HT[l - 1], s->HTlo[l - 1], din, rows, rows, s->dZT[l], nullptr, kD,
+                                          rows, kc, ep);
       if (st == DLM_OK) {
         k_bwd_grads<<<(unsigned)((cnt + 255) / 256 + din), kD, 0, ctx->stream>>>(
-            B, din, s->k, cnt, splits, s->part[l], s->grad + s->olam[l], s->Mfb[l - 1], s->S[l], s->grad, s->theta,
-            s->ogam[l], s->ob[l], nullptr, 1);
+            B, din, cnt, splits, s->part[l], s->grad + s->olam[l], s->Mfb[l - 1], s->S[l], s->grad, s->ogam[l],
+            s->ob[l]);
         st = launch_check(ctx, "k_bwd_grads");
       }
-      if (st == DLM_OK) st = cuda_check(ctx, cudaEventRecord(s->ev_join[l], s->side), "event");
+      if (st == DLM_OK) st = cuda_check(ctx, cudaEventRecord(s->ev_join[l], s->side[l]), "event");
       ctx->stream = main_stream;
       DLM_TRY(st);
     }
-    // the per-candidate term of dH_{l-1} (from S_l and Gamma_l) on the main chain
-    k_bwd_grads<<<(unsigned)B, kD, 0, ctx->stream>>>(B, din, s->k, cnt, splits, nullptr, nullptr, nullptr, s->S[l],
-                                                     nullptr, s->theta, s->ogam[l], s->ob[l], s->Gb, 0);
-    DLM_TRY(launch_check(ctx, "k_bwd_grads"));
     // dZ_{l-1} = (dZ_l Lambda_l^T + Gb) * LeakyReLU'(H_{l-1})
     EpiBwd e{s->dZ[l - 1], din, rows, s->k, s->R, s->Gb, s->Hb[l - 1]};
-    if (rows < kWideRows || din % 256)
+    if (rows < kWideRows && din % kTrainBN == 0)
+      DLM_TRY((gemm<kTrainBN, 1>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
+    else if (rows < kWideRows || din % 256)
       DLM_TRY((gemm<64, 1>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
     else
       DLM_TRY((gemm<256>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
@@ -1171,11 +1248,12 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
   }
   DLM_TRY(dalloc(ctx, &s->Gb, (size_t)cb * kD));
   for (int l = 1; l <= kNL; ++l) DLM_TRY(dalloc(ctx, &s->part[l], (size_t)(rows / tc::BK / 4 + 1) * kD * kD));
-  if (!s->side) {
-    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, DLM_ECUDA, "scorer: side stream");
-    }
+  if (!s->side[1]) {
+    for (int l = 1; l <= kNL; ++l)
+      if (cudaStreamCreateWithFlags(&s->side[l], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, DLM_ECUDA, "scorer: side stream");
+      }
     for (int l = 1; l <= kNL; ++l)
       if (cudaEventCreateWithFlags(&s->ev_fork[l], cudaEventDisableTiming) != cudaSuccess ||
           cudaEventCreateWithFlags(&s->ev_join[l], cudaEventDisableTiming) != cudaSuccess) {
@@ -1219,10 +1297,10 @@ static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
 static dlm_status train_step(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int B, int b, float lr) {
   // the bias corrections (a short double-precision chain) on the side branch, off the critical path
   DLM_CUDA(ctx, cudaEventRecord(s->ev_bc_fork, ctx->stream));
-  DLM_CUDA(ctx, cudaStreamWaitEvent(s->side, s->ev_bc_fork, 0));
-  k_adam_bias<<<1, 32, 0, s->side>>>(s->d_step, s->d_bc);
+  DLM_CUDA(ctx, cudaStreamWaitEvent(s->side[1], s->ev_bc_fork, 0));
+  k_adam_bias<<<1, 32, 0, s->side[1]>>>(s->d_step, s->d_bc);
   DLM_TRY(launch_check(ctx, "k_adam_bias"));
-  DLM_CUDA(ctx, cudaEventRecord(s->ev_bc_join, s->side));
+  DLM_CUDA(ctx, cudaEventRecord(s->ev_bc_join, s->side[1]));
   DLM_TRY(loss_grad(ctx, s, cols, s->y, B, s->perm, s->d_step));
   DLM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_bc_join, 0));
   k_adam_convert<<<(unsigned)((s->np + 255) / 256), 256, 0, ctx->stream>>>(s->np, s->theta, s->am, s->av, s->grad, lr,
@@ -1282,7 +1360,8 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
     if (s->ev_fork[l]) cudaEventDestroy(s->ev_fork[l]);
     if (s->ev_join[l]) cudaEventDestroy(s->ev_join[l]);
   }
-  if (s->side) cudaStreamDestroy(s->side);
+  for (auto st : s->side)
+    if (st) cudaStreamDestroy(st);
   if (s->ev_bc_fork) cudaEventDestroy(s->ev_bc_fork);
   if (s->ev_bc_join) cudaEventDestroy(s->ev_bc_join);
   cudaFree(s->d_bc);

@@ -616,12 +616,15 @@ def dlm_col_descend(ctx, g, params, max_gens, best_col):
 
 
 MEMETIC_STAGES = ("tabu", "best_of", "distances", "pool_update", "matching", "offspring", "training")
+MEMETIC_OFFSPRING_PARTS = ("offspring_gpx", "offspring_wait_training", "offspring_scoring")
 
 
 def dlm_memetic_profile(ctx, mm, enable):
     """Mean ms per generation of each stage since the last call (dict), then (re)sets recording."""
     import numpy as np
 
-    out = np.zeros(8, np.float64)
+    out = np.zeros(11, np.float64)
     ctx.check(lib().dlm_memetic_profile(ctx.h, mm.h, 1 if enable else 0, _ptr(out)), "dlm_memetic_profile")
-    return dict(zip(MEMETIC_STAGES, out[:7].tolist()), generations=int(out[7]))
+    d = dict(zip(MEMETIC_STAGES, out[:7].tolist()), generations=int(out[7]))
+    d.update(zip(MEMETIC_OFFSPRING_PARTS, out[8:11].tolist()))
+    return d
