@@ -40,7 +40,9 @@ constexpr int kD0 = 64, kD = 256, kNL = 3, kRMax = 256;  // rows per candidate: 
 
 struct dlm_scorer {
   int n = 0, k = 0;
-  int R = 64;  // rows per candidate in the layer matrices: k rounded up to a multiple of 64
+  int R = 64;  // rows per candidate in the training layer matrices: k rounded up to a multiple of 64
+  int Rs = 64;  // rows per candidate when scoring: k (no padding rows; rows are independent in every
+                // layer GEMM, so the scores are the same)
   int64_t np = 0;
   int64_t t = 0;  // Adam step counter
   size_t oE = 0, ob0 = 0, olam[4] = {}, ogam[4] = {}, ob[4] = {}, owh = 0, obh = 0;
@@ -1106,17 +1108,17 @@ static size_t pool_smem(int n) {
 
 // forward over c candidates with the given buffers; train = a training batch: keep every
 // activation (and H3), candidate b being sample perm[step[0] + b] of cols when perm is given
-static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int c, float* out, bf16** H, bf16** Hlo,
-                          bf16** Mb, bf16** Mblo, float** Mf, float** G, float* rowdot, bool train,
+static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int c, int R, float* out, bf16** H,
+                          bf16** Hlo, bf16** Mb, bf16** Mblo, float** Mf, float** G, float* rowdot, bool train,
                           const int32_t* perm = nullptr, const int32_t* step = nullptr) {
-  const int rows = c * s->R;
+  const int rows = c * R;
   const size_t psm = pool_smem(s->n);  // < 10 KB for n <= 2048
   const int pgrid = std::min(c, ctx->num_sms * 4);
   // per-candidate term rho(H_{l-1}) Gamma_l + beta_l: on the tensor cores for a scoring chunk,
   // both operands split into bf16 hi + lo (three MMA passes, about 16 mantissa bits each); in
   // FP32 on CUDA cores for a small batch, for a training batch fused into the kernel that forms
   // the class means (k_pool for layer 1, k_mean_gterm for layers 2 and 3)
-  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, s->R, cols, c, perm, step, s->theta + s->oE, s->theta + s->ob0, H[0],
+  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, R, cols, c, perm, step, s->theta + s->oE, s->theta + s->ob0, H[0],
                                            Hlo ? Hlo[0] : nullptr, Mf[0], Mb[0], Mblo[0],
                                            s->theta + s->ogam[1], s->theta + s->ob[1], train ? G[1] : nullptr,
                                            ctx->d_status);
@@ -1137,7 +1139,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
     // one pipeline stage (twice the CTAs of a 128 x 256 tile, and a third of its shared memory);
     // from kWideRows rows on (k > 64) 128 x 256 tiles fill the SMs
     const bool narrow = train && rows < kWideRows;
-    EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, s->R, G[l],
+    EpiLayer e{(last && !train) ? nullptr : H[l], Hlo ? Hlo[l] : nullptr, rows, s->k, R, G[l],
                last ? s->theta + s->owh : nullptr, last ? rowdot : nullptr, 0.f, narrow ? kTrainBN / 2 : 128, 0};
     if (narrow)
       DLM_TRY((gemm<kTrainBN, 1>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din,
@@ -1146,16 +1148,16 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       DLM_TRY(gemm<256>(ctx, H[l - 1], Hlo ? Hlo[l - 1] : nullptr, rows, din, din, s->LamT[l], s->LamTlo[l], kD, din, 0,
                         e));
     if (train && !last) {
-      k_mean_gterm<<<c, kMgGroups * kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, s->k, s->R, Mf[l], Mb[l], Mblo[l],
+      k_mean_gterm<<<c, kMgGroups * kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, s->k, R, Mf[l], Mb[l], Mblo[l],
                                               s->theta + s->ogam[l + 1], s->theta + s->ob[l + 1], G[l + 1]);
       DLM_TRY(launch_check(ctx, "k_mean_gterm"));
     } else if (!last || train) {
-      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, s->R, 1.f / s->k, Mf[l], Mb[l],
+      k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, R, 1.f / s->k, Mf[l], Mb[l],
                                                   Mblo[l]);
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
-  k_head_out<<<(c + kHeadOutWarps - 1) / kHeadOutWarps, 32 * kHeadOutWarps, 0, ctx->stream>>>(c, s->k, s->R, rowdot,
+  k_head_out<<<(c + kHeadOutWarps - 1) / kHeadOutWarps, 32 * kHeadOutWarps, 0, ctx->stream>>>(c, s->k, R, rowdot,
                                                        (train && rows < kWideRows) ? kD / (kTrainBN / 2) : kD / 128, s->theta,
                                                        s->obh, out);
   return launch_check(ctx, "k_head_out");
@@ -1166,7 +1168,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
 // sample); otherwise cols and y hold the batch itself.
 static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, const float* y, int B,
                             const int32_t* perm = nullptr, const int32_t* step = nullptr) {
-  DLM_TRY(forward(ctx, s, cols, B, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mbblo, s->Mfb, s->Gbf, s->rowdotb, true, perm,
+  DLM_TRY(forward(ctx, s, cols, B, s->R, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mbblo, s->Mfb, s->Gbf, s->rowdotb, true, perm,
                   step));
   const int rows = B * s->R;
   k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, perm, step, s->dout, s->lossd);
@@ -1277,7 +1279,7 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
 
 static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
   if (s->cap) return DLM_OK;
-  const int cap = 8192 * 64 / s->R, rows = cap * s->R;  // the same bytes for every k
+  const int cap = 8192 * 64 / s->Rs, rows = cap * s->Rs;  // about the same bytes for every k
   for (int l = 0; l <= kNL; ++l) {
     const int w = l == 0 ? kD0 : kD;
     if (l < kNL) DLM_TRY(dalloc(ctx, &s->H[l], (size_t)rows * w));
@@ -1388,6 +1390,7 @@ extern "C" dlm_status dlm_scorer_create(dlm_ctx* ctx, int32_t n, int32_t k, uint
   s->n = n;
   s->k = k;
   s->R = 64 * ((k + 63) / 64);
+  s->Rs = k;
   size_t o = 0;
   s->oE = o; o += (size_t)n * kD0;
   s->ob0 = o; o += kD0;
@@ -1468,7 +1471,7 @@ extern "C" dlm_status dlm_score_offspring(dlm_ctx* ctx, dlm_scorer* s, const int
   DLM_TRY(ensure_fwd_buffers(ctx, s));
   for (int c0 = 0; c0 < c; c0 += s->cap) {
     const int cc = std::min(s->cap, c - c0);
-    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, out + c0, s->H, s->split_act ? s->Hlo : nullptr, s->Mb,
+    DLM_TRY(forward(ctx, s, col + (size_t)c0 * s->n, cc, s->Rs, out + c0, s->H, s->split_act ? s->Hlo : nullptr, s->Mb,
                     s->Mblo, s->Mf, s->G, s->rowdot, false));
   }
   return DLM_OK;
