@@ -78,8 +78,13 @@ struct dlm_scorer {
   // the weight gradients of layer l (dLambda_l GEMM, its split-K sum, dGamma_l, dbeta_l) run on a
   // side branch forked after the layer's transposes and joined before the Adam step, off the
   // chain dZ_l -> dZ_{l-1} of the backward pass
-  cudaStream_t side[4] = {};  // one branch stream per layer (the branches of a step overlap)
-  cudaEvent_t ev_fork[4] = {}, ev_join[4] = {};
+  // branch streams: [1..3] one per layer (the branches of a step overlap), [0] the head's gradient
+  // and the loss, then the embedding bias gradient
+  cudaStream_t side[4] = {};
+  // fork / join events: [1..3] the layers' weight gradients, [4] the head's gradient and the loss,
+  // [5] the embedding bias gradient
+  cudaEvent_t ev_fork[6] = {}, ev_join[6] = {};
+  float* sqerr = nullptr;  // squared error of each candidate of a training batch
   // Adam's bias corrections of the coming step, formed on the side branch ([0] 1 - 0.9^t,
   // [1] sqrt(1 - 0.999^t))
   float* d_bc = nullptr;
@@ -169,14 +174,16 @@ __device__ __forceinline__ float gterm_col(const float* m, int din, const float*
 }
 
 // ------------------------------------------------------------------------------------------------
-// layer 0: class pooling. One CTA per candidate (grid-stride): a stable counting sort puts the
-// vertices of each class in ascending order, then warp w sums the FP32 embedding rows of classes
-// w, w+8, ... with lane = feature pair (fixed summation order; E is read through L1/L2).
+// layer 0: class pooling. One CTA of kPoolWarps warps per candidate (grid-stride): a stable
+// counting sort puts the vertices of each class in ascending order, then warp w sums the FP32
+// embedding rows of classes w, w + kPoolWarps, ... with lane = feature pair (fixed summation order;
+// E is read through L1/L2).
 // A training batch reads its candidates through the epoch permutation (candidate b = sample
 // perm[step[0] + b]) and, with G1 set, ends with layer 1's per-candidate term
 // G1 = beta_1 + mean_c(H0) Gamma_1.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pool(int n, int k, int R, const int16_t* cols, int c, const int32_t* perm,
+constexpr int kPoolWarps = 8;
+__global__ void __launch_bounds__(32 * kPoolWarps) k_pool(int n, int k, int R, const int16_t* cols, int c, const int32_t* perm,
                                               const int32_t* step, const float* E, const float* b0, bf16* H0,
                                               bf16* H0lo, float* Mf0, bf16* Mb0, bf16* Mb0lo, const float* gam1,
                                               const float* beta1, float* G1, int32_t* status) {
@@ -186,15 +193,15 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, int R, const int16_t
   int* cnt = (int*)(mem + ((n + 7) & ~7));                  // [256]
   int* off = cnt + kRMax;                                   // [257]
   int* cur = off + kRMax + 1;                               // [256]
-  float* part = (float*)(cur + kRMax);                      // [8][64]
-  float* mvec = part + 8 * 64;                              // [64]
+  float* part = (float*)(cur + kRMax);                      // [kPoolWarps][64]
+  float* mvec = part + kPoolWarps * 64;                     // [64]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int cand = blockIdx.x; cand < c; cand += gridDim.x) {
     const int srow = perm ? perm[step[0] + cand] : cand;
     const int16_t* cc = cols + (size_t)srow * n;
-    cnt[tid] = 0;  // 256 threads: every class counter
+    if (tid < kRMax) cnt[tid] = 0;  // every class counter
     __syncthreads();
-    for (int v = tid; v < n; v += 256) {
+    for (int v = tid; v < n; v += 32 * kPoolWarps) {
       int q = cc[v];
       if (q < 0 || q >= k) { raise_status(status, DLM_EINVAL); q = 0; }
       col[v] = (uint8_t)q;
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, int R, const int16_t
     __syncthreads();
     float2 msum = make_float2(0.f, 0.f);
     const float2 bb = make_float2(b0[2 * lane], b0[2 * lane + 1]);
-    for (int q = warp; q < R; q += 8) {
+    for (int q = warp; q < R; q += kPoolWarps) {
       float2 acc = make_float2(0.f, 0.f);
       if (q < k) {
         // members in ascending order; sixteen (then eight) embedding rows are loaded before they are added (the
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, int R, const int16_t
     __syncthreads();
     if (tid < 64) {
       float s = 0.f;
-      for (int w = 0; w < 8; ++w) s += part[w * 64 + tid];
+      for (int w = 0; w < kPoolWarps; ++w) s += part[w * 64 + tid];
       s /= (float)k;
       Mf0[(size_t)cand * kD0 + tid] = s;
       mvec[tid] = s;
@@ -298,7 +305,7 @@ __global__ void __launch_bounds__(256) k_pool(int n, int k, int R, const int16_t
       Mb0lo[(size_t)cand * kD0 + tid] = __float2bfloat16_rn(s - __bfloat162float(hi));
     }
     __syncthreads();
-    if (G1) G1[(size_t)cand * kD + tid] = gterm_col(mvec, kD0, gam1, beta1, tid);
+    if (G1 && tid < kD) G1[(size_t)cand * kD + tid] = gterm_col(mvec, kD0, gam1, beta1, tid);
   }
 }
 
@@ -616,22 +623,34 @@ struct EpiBwd {  // dZprev[row][col] = mask((acc + Gb[cand][col]) * LeakyReLU'(H
 // ------------------------------------------------------------------------------------------------
 // backward helpers (batch of B candidates)
 // ------------------------------------------------------------------------------------------------
-// MSE loss of the batch; with perm, candidate i is sample perm[step[0] + i] (target y of that sample)
-__global__ void k_loss(int B, const float* out, const float* y, const int32_t* perm, const int32_t* step, float* dout,
-                       float* loss) {
-  __shared__ float s[256];
-  float l = 0.f;
-  for (int i = threadIdx.x; i < B; i += blockDim.x) {
-    const float e = out[i] - y[perm ? perm[step[0] + i] : i];
-    dout[i] = 2.f * e / (float)B;
-    l += e * e;
-  }
-  s[threadIdx.x] = l;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.f;
-    for (int i = 0; i < (int)blockDim.x; ++i) t += s[i];
-    *loss = t / (float)B;
+// end of a training batch's forward pass, one candidate per block of kD threads: the class mean of
+// H3 (Mf3 and its bf16 hi / lo, as segment_col writes them), the output out = head bias + mean over
+// the k class rows of the head dot (warp 0, in the order of k_head_out), the loss gradient
+// dout = 2 (out - y) / B and the squared error; with perm, candidate i is sample perm[step[0] + i]
+// (target y of that sample)
+__global__ void __launch_bounds__(kD) k_head_fwd(int B, int k, int R, const bf16* H3, const bf16* H3lo, float* Mf3,
+                                                 bf16* Mb3, bf16* Mb3lo, const float* rowdot, int parts,
+                                                 const float* theta, size_t obh, const float* y, const int32_t* perm,
+                                                 const int32_t* step, float* out, float* dout, float* sqerr) {
+  const int cand = blockIdx.x, o = threadIdx.x;
+  segment_col(H3, H3lo, kD, k, R, 1.f / k, Mf3, Mb3, Mb3lo, cand, o);
+  if (o < 32) {
+    const size_t M = (size_t)B * R;
+    float sum = 0.f;
+    for (int r = o; r < k; r += 32) {
+      float t = rowdot[(size_t)cand * R + r];
+      for (int q = 1; q < parts; ++q) t += rowdot[q * M + (size_t)cand * R + r];
+      sum += t;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, d);
+    if (o == 0) {
+      const float ov = theta[obh] + sum / (float)k;
+      out[cand] = ov;
+      const float e = ov - y[perm ? perm[step[0] + cand] : cand];
+      dout[cand] = 2.f * e / (float)B;
+      sqerr[cand] = e * e;
+    }
   }
 }
 
@@ -669,20 +688,28 @@ __device__ __forceinline__ void head_grad_col(int B, const float* dout, const fl
   }
 }
 
-// blocks 0 .. ceil(rows / kHeadRows) - 1: dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows
-// (thread = column, kHeadRows rows a block); the last block: the head's gradient
-// (wh[o] = sum_cand dout * mean(H3)[cand][o], bh = sum dout)
+// dZ3 = (dout/k * wh) * LeakyReLU'(H3) on valid rows (thread = column, kHeadRows rows a block)
 constexpr int kHeadRows = 8;
-__global__ void __launch_bounds__(kD) k_head_bwd(int B, int k, int R, int rows, const float* dout, const float* theta,
-                                                 size_t owh, size_t obh, const bf16* H3, const float* Mf3, bf16* dZ3,
-                                                 float* grad) {
+__global__ void __launch_bounds__(kD) k_head_bwd(int k, int R, int rows, const float* dout, const float* theta,
+                                                 size_t owh, const bf16* H3, bf16* dZ3) {
   const int rb = (int)blockIdx.x * kHeadRows;
-  if (rb < rows) {
 #pragma unroll
-    for (int i = 0; i < kHeadRows; ++i)
-      if (rb + i < rows) head_back_row(k, R, dout, theta, owh, H3, dZ3, rb + i, threadIdx.x);
-  } else {
-    head_grad_col(B, dout, Mf3, grad, owh, obh, threadIdx.x);
+  for (int i = 0; i < kHeadRows; ++i)
+    if (rb + i < rows) head_back_row(k, R, dout, theta, owh, H3, dZ3, rb + i, threadIdx.x);
+}
+
+// the head's gradient (wh[o] = sum_cand dout * mean(H3)[cand][o], bh = sum dout) and the batch's
+// MSE loss; one block of kD threads, on a side branch
+__global__ void __launch_bounds__(kD) k_head_grad(int B, const float* dout, const float* Mf3, float* grad, size_t owh,
+                                                  size_t obh, const float* sqerr, float* loss) {
+  head_grad_col(B, dout, Mf3, grad, owh, obh, threadIdx.x);
+  if (threadIdx.x >= 32 && threadIdx.x < 64) {  // warp 1: lane-strided sums, then a fixed butterfly
+    const int lane = threadIdx.x - 32;
+    float t = 0.f;
+    for (int i = lane; i < B; i += 32) t += sqerr[i];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, d);
+    if (lane == 0) *loss = t / (float)B;
   }
 }
 
@@ -788,15 +815,15 @@ __global__ void __launch_bounds__(kMgGroups * kD) k_bwd_sums_gb(int din, int k, 
 }
 
 // embedding gradient: dE[v][f] = sum_cand dZ0[cand*R + col_cand[v]][f]; db0[f] = sum_cand S0[cand][f]
-// (with perm, candidate c of the batch is sample perm[step[0] + c] of cols). Block v (256
+// (with perm, candidate c of the batch is sample perm[step[0] + c] of cols). Block v - vbase (256
 // threads = kDembGroups groups of kD0 features): group g sums the candidates of its contiguous
 // share in order, eight loads in flight, then the groups' sums are added in group order.
 constexpr int kDembGroups = 256 / kD0;
 __global__ void __launch_bounds__(256) k_demb(int n, int B, int R, const int16_t* cols, const int32_t* perm,
                                               const int32_t* step, const bf16* dZ0, const float* S0, float* grad,
-                                              size_t oE, size_t ob0) {
+                                              size_t oE, size_t ob0, int vbase) {
   __shared__ float ps[kDembGroups][kD0];
-  const int v = blockIdx.x, f = threadIdx.x % kD0, grp = threadIdx.x / kD0;
+  const int v = vbase + (int)blockIdx.x, f = threadIdx.x % kD0, grp = threadIdx.x / kD0;
   const int share = (B + kDembGroups - 1) / kDembGroups;
   const int c0 = min(B, grp * share), c1 = min(B, c0 + share);
   auto row = [&](int c) -> size_t { return (size_t)(perm ? perm[step[0] + c] : c) * n; };
@@ -841,10 +868,15 @@ __global__ void k_adam_bias(const int32_t* step, float* bc) {
 }
 
 // Adam step t + 1 (t = step[1]) of every parameter with the bias corrections bc of k_adam_bias,
-// then the parameter's bf16 operand copies (those k_convert writes).
+// then the parameter's bf16 operand copies (those k_convert writes); thread 0 then advances the
+// batch offset step[0] by b and Adam's counter step[1] (nothing of this step reads them any more).
 __global__ void __launch_bounds__(256) k_adam_convert(int64_t np, float* th, float* m, float* v, const float* g,
-                                                      float lr, const float* bc, ConvArgs a) {
+                                                      float lr, const float* bc, ConvArgs a, int32_t* step, int b) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && step) {  // the step's end: the next batch starts b samples later, Adam's counter advances
+    step[0] += b;
+    step[1] += 1;
+  }
   if (i >= np) return;
   const float bc1 = bc[0], sbc2 = bc[1];  // the same two words for every thread (L1 broadcast)
   const float gi = g[i];
@@ -885,11 +917,6 @@ __global__ void __launch_bounds__(256) k_adam_convert(int64_t np, float* th, flo
   }
 }
 
-// after a step: the next batch starts b samples later, Adam's counter advances
-__global__ void k_step_end(int32_t* step, int b) {
-  step[0] += b;
-  step[1] += 1;
-}
 
 __global__ void k_init_params(int64_t np, uint64_t seed, float* th, const float* bound_of, const int64_t* seg_end, int nseg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1103,7 +1130,7 @@ static dlm_status convert_params(dlm_ctx* ctx, dlm_scorer* s) {
 }
 
 static size_t pool_smem(int n) {
-  return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + (3 * kRMax + 1) * 4 + 9 * 64 * 4 + 64;
+  return ((n + 15) & ~15) + ((n + 7) & ~7) * 2 + (3 * kRMax + 1) * 4 + (kPoolWarps + 1) * 64 * 4 + 64;
 }
 
 // forward over c candidates with the given buffers; train = a training batch: keep every
@@ -1118,7 +1145,7 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
   // both operands split into bf16 hi + lo (three MMA passes, about 16 mantissa bits each); in
   // FP32 on CUDA cores for a small batch, for a training batch fused into the kernel that forms
   // the class means (k_pool for layer 1, k_mean_gterm for layers 2 and 3)
-  k_pool<<<pgrid, 256, psm, ctx->stream>>>(s->n, s->k, R, cols, c, perm, step, s->theta + s->oE, s->theta + s->ob0, H[0],
+  k_pool<<<pgrid, 32 * kPoolWarps, psm, ctx->stream>>>(s->n, s->k, R, cols, c, perm, step, s->theta + s->oE, s->theta + s->ob0, H[0],
                                            Hlo ? Hlo[0] : nullptr, Mf[0], Mb[0], Mblo[0],
                                            s->theta + s->ogam[1], s->theta + s->ob[1], train ? G[1] : nullptr,
                                            ctx->d_status);
@@ -1151,15 +1178,16 @@ static dlm_status forward(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int 
       k_mean_gterm<<<c, kMgGroups * kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, s->k, R, Mf[l], Mb[l], Mblo[l],
                                               s->theta + s->ogam[l + 1], s->theta + s->ob[l + 1], G[l + 1]);
       DLM_TRY(launch_check(ctx, "k_mean_gterm"));
-    } else if (!last || train) {
+    } else if (!last) {
       k_segment_reduce<<<c, kD, 0, ctx->stream>>>(H[l], Hlo ? Hlo[l] : nullptr, kD, s->k, R, 1.f / s->k, Mf[l], Mb[l],
                                                   Mblo[l]);
       DLM_TRY(launch_check(ctx, "k_segment_reduce"));
     }
   }
+  if (train) return DLM_OK;  // the training batch's class means of H3 and output: k_head_fwd
   k_head_out<<<(c + kHeadOutWarps - 1) / kHeadOutWarps, 32 * kHeadOutWarps, 0, ctx->stream>>>(c, s->k, R, rowdot,
-                                                       (train && rows < kWideRows) ? kD / (kTrainBN / 2) : kD / 128, s->theta,
-                                                       s->obh, out);
+                                                                                             kD / 128, s->theta, s->obh,
+                                                                                             out);
   return launch_check(ctx, "k_head_out");
 }
 
@@ -1171,12 +1199,21 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
   DLM_TRY(forward(ctx, s, cols, B, s->R, s->outb, s->Hb, s->Hblo, s->Mbb, s->Mbblo, s->Mfb, s->Gbf, s->rowdotb, true, perm,
                   step));
   const int rows = B * s->R;
-  k_loss<<<1, 256, 0, ctx->stream>>>(B, s->outb, y, perm, step, s->dout, s->lossd);
-  DLM_TRY(launch_check(ctx, "k_loss"));
-  k_head_bwd<<<(rows + kHeadRows - 1) / kHeadRows + 1, kD, 0, ctx->stream>>>(B, s->k, s->R, rows, s->dout, s->theta, s->owh, s->obh, s->Hb[kNL],
-                                               s->Mfb[kNL], s->dZ[kNL], s->grad);
-  DLM_TRY(launch_check(ctx, "k_head_bwd"));
+  const int parts = rows < kWideRows ? kD / (kTrainBN / 2) : kD / 128;  // head-dot slices of the layer-3 GEMM
+  k_head_fwd<<<(unsigned)B, kD, 0, ctx->stream>>>(B, s->k, s->R, s->Hb[kNL], s->Hblo[kNL], s->Mfb[kNL], s->Mbb[kNL],
+                                                  s->Mbblo[kNL], s->rowdotb, parts, s->theta, s->obh, y, perm, step,
+                                                  s->outb, s->dout, s->sqerr);
+  DLM_TRY(launch_check(ctx, "k_head_fwd"));
   cudaStream_t main_stream = ctx->stream;
+  // side branch: the head's gradient and the loss
+  DLM_CUDA(ctx, cudaEventRecord(s->ev_fork[4], main_stream));
+  DLM_CUDA(ctx, cudaStreamWaitEvent(s->side[0], s->ev_fork[4], 0));
+  k_head_grad<<<1, kD, 0, s->side[0]>>>(B, s->dout, s->Mfb[kNL], s->grad, s->owh, s->obh, s->sqerr, s->lossd);
+  DLM_TRY(launch_check(ctx, "k_head_grad"));
+  DLM_CUDA(ctx, cudaEventRecord(s->ev_join[4], s->side[0]));
+  k_head_bwd<<<(unsigned)((rows + kHeadRows - 1) / kHeadRows), kD, 0, ctx->stream>>>(s->k, s->R, rows, s->dout, s->theta,
+                                                                                     s->owh, s->Hb[kNL], s->dZ[kNL]);
+  DLM_TRY(launch_check(ctx, "k_head_bwd"));
   for (int l = kNL; l >= 1; --l) {
     const int din = din_of(l);
     // main chain: the column sums S_l of dZ_l per candidate (valid rows are the only nonzero ones)
@@ -1223,10 +1260,18 @@ static dlm_status loss_grad(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, co
     else
       DLM_TRY((gemm<256>(ctx, s->dZ[l], nullptr, rows, kD, kD, s->Lam[l], s->Lamlo[l], din, kD, 0, e)));
   }
-  k_segment_reduce<<<B, kD0, 0, ctx->stream>>>(s->dZ[0], nullptr, kD0, s->k, s->R, 1.f, s->S[0], nullptr, nullptr);
-  k_demb<<<s->n + 1, 256, 0, ctx->stream>>>(s->n, B, s->R, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0);
+  // side branch: the embedding bias gradient db0 = sum over candidates of the column sums of dZ0
+  DLM_CUDA(ctx, cudaEventRecord(s->ev_fork[5], main_stream));
+  DLM_CUDA(ctx, cudaStreamWaitEvent(s->side[0], s->ev_fork[5], 0));
+  k_segment_reduce<<<B, kD0, 0, s->side[0]>>>(s->dZ[0], nullptr, kD0, s->k, s->R, 1.f, s->S[0], nullptr, nullptr);
+  k_demb<<<1, 256, 0, s->side[0]>>>(s->n, B, s->R, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE, s->ob0, s->n);
   DLM_TRY(launch_check(ctx, "k_demb"));
-  for (int l = 1; l <= kNL; ++l) DLM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_join[l], 0));
+  DLM_CUDA(ctx, cudaEventRecord(s->ev_join[5], s->side[0]));
+  // the embedding gradient dE on the main chain
+  k_demb<<<(unsigned)s->n, 256, 0, ctx->stream>>>(s->n, B, s->R, cols, perm, step, s->dZ[0], s->S[0], s->grad, s->oE,
+                                                  s->ob0, 0);
+  DLM_TRY(launch_check(ctx, "k_demb"));
+  for (int l = 1; l < 6; ++l) DLM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_join[l], 0));
   return DLM_OK;
 }
 
@@ -1250,13 +1295,13 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
   }
   DLM_TRY(dalloc(ctx, &s->Gb, (size_t)cb * kD));
   for (int l = 1; l <= kNL; ++l) DLM_TRY(dalloc(ctx, &s->part[l], (size_t)(rows / tc::BK / 4 + 1) * kD * kD));
-  if (!s->side[1]) {
-    for (int l = 1; l <= kNL; ++l)
+  if (!s->side[0]) {
+    for (int l = 0; l <= kNL; ++l)
       if (cudaStreamCreateWithFlags(&s->side[l], cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, DLM_ECUDA, "scorer: side stream");
       }
-    for (int l = 1; l <= kNL; ++l)
+    for (int l = 0; l < 6; ++l)
       if (cudaEventCreateWithFlags(&s->ev_fork[l], cudaEventDisableTiming) != cudaSuccess ||
           cudaEventCreateWithFlags(&s->ev_join[l], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -1269,6 +1314,7 @@ static dlm_status ensure_train_buffers(dlm_ctx* ctx, dlm_scorer* s, int B) {
     }
     DLM_TRY(dalloc(ctx, &s->d_bc, 2));
   }
+  DLM_TRY(dalloc(ctx, &s->sqerr, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->rowdotb, (size_t)rows * (kD / 32)));
   DLM_TRY(dalloc(ctx, &s->outb, (size_t)cb));
   DLM_TRY(dalloc(ctx, &s->dout, (size_t)cb));
@@ -1299,17 +1345,15 @@ static dlm_status ensure_fwd_buffers(dlm_ctx* ctx, dlm_scorer* s) {
 static dlm_status train_step(dlm_ctx* ctx, dlm_scorer* s, const int16_t* cols, int B, int b, float lr) {
   // the bias corrections (a short double-precision chain) on the side branch, off the critical path
   DLM_CUDA(ctx, cudaEventRecord(s->ev_bc_fork, ctx->stream));
-  DLM_CUDA(ctx, cudaStreamWaitEvent(s->side[1], s->ev_bc_fork, 0));
-  k_adam_bias<<<1, 32, 0, s->side[1]>>>(s->d_step, s->d_bc);
+  DLM_CUDA(ctx, cudaStreamWaitEvent(s->side[0], s->ev_bc_fork, 0));
+  k_adam_bias<<<1, 32, 0, s->side[0]>>>(s->d_step, s->d_bc);
   DLM_TRY(launch_check(ctx, "k_adam_bias"));
-  DLM_CUDA(ctx, cudaEventRecord(s->ev_bc_join, s->side[1]));
+  DLM_CUDA(ctx, cudaEventRecord(s->ev_bc_join, s->side[0]));
   DLM_TRY(loss_grad(ctx, s, cols, s->y, B, s->perm, s->d_step));
   DLM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_bc_join, 0));
   k_adam_convert<<<(unsigned)((s->np + 255) / 256), 256, 0, ctx->stream>>>(s->np, s->theta, s->am, s->av, s->grad, lr,
-                                                                          s->d_bc, conv_args(s, nullptr));
-  DLM_TRY(launch_check(ctx, "k_adam_convert"));
-  k_step_end<<<1, 1, 0, ctx->stream>>>(s->d_step, b);
-  return launch_check(ctx, "k_step_end");
+                                                                          s->d_bc, conv_args(s, nullptr), s->d_step, b);
+  return launch_check(ctx, "k_adam_convert");
 }
 
 // the training step of batch size B as an instantiated CUDA graph (captured on a private stream,
@@ -1357,11 +1401,12 @@ extern "C" void dlm_scorer_destroy(dlm_scorer* s) {
   for (auto& g : s->sg)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
-  for (int l = 0; l < 4; ++l) {
-    cudaFree(s->part[l]);
+  for (int l = 0; l < 4; ++l) cudaFree(s->part[l]);
+  for (int l = 0; l < 6; ++l) {
     if (s->ev_fork[l]) cudaEventDestroy(s->ev_fork[l]);
     if (s->ev_join[l]) cudaEventDestroy(s->ev_join[l]);
   }
+  cudaFree(s->sqerr);
   for (auto st : s->side)
     if (st) cudaStreamDestroy(st);
   if (s->ev_bc_fork) cudaEventDestroy(s->ev_bc_fork);
