@@ -357,8 +357,10 @@ __global__ void k_segment_reduce(const bf16* X, const bf16* Xlo, int w, int k, i
 // a training batch between layers l and l + 1: the class mean of H_l (written as segment_col
 // writes it), then the next layer's per-candidate term G = beta + mean Gamma. One candidate per
 // block of kMgGroups x kD threads: group g sums its contiguous share of the k rows (in row order)
-// and then its quarter of the rows f of Gamma; the groups' parts are added in group order.
-constexpr int kMgGroups = 4;
+// and then its share of the rows f of Gamma; the groups' parts are added in group order. Two
+// groups (512 threads): in a memetic generation the training runs beside the distance kernel, whose
+// CTAs leave about 768 threads of an SM free, so a 1024-thread block would wait for one to finish.
+constexpr int kMgGroups = 2;
 __global__ void __launch_bounds__(kMgGroups * kD) k_mean_gterm(const bf16* X, const bf16* Xlo, int k, int R,
                                                                float* outf, bf16* outb, bf16* outblo, const float* gam,
                                                                const float* beta, float* G) {
