@@ -85,6 +85,33 @@ def test_distance_matches_oracle(ctx, n, k, a, b, method):
     assert np.all(got[:, b:] == -1)
 
 
+@pytest.mark.parametrize("method", [None, 1])
+def test_distance_large_classes(ctx, method):
+    """Rows of X with a class above 255 vertices (their overlap counts need more than a byte) beside
+    rows without, in one launch and in the upper-triangle form."""
+    n, k, a, b = 1000, 48, 12, 140
+    X = inputs.random_colorings(a, n, k, seed=5)
+    X[1] = 0  # one class of n vertices
+    X[4] = X[4] % 3  # three classes of about 333
+    X[7, :600] = 5  # one class of at least 600
+    X[10, :256] = 9  # one class of at least 256
+    Y = inputs.random_colorings(b, n, k, seed=6)
+    Y[0], Y[1], Y[2], Y[3] = X[1], X[4], 0, X[7]
+    D = torch.full((a, b), -1, dtype=torch.int16, device="cuda")
+    dlmcol.dlm_distance_batch(ctx, n, k, _cuda(X), a, _cuda(Y), b, D, b, 0, method=method)
+    ctx.sync()
+    assert np.array_equal(D.cpu().numpy(), oracle.distance_matrix(k, X, Y))
+    Z = inputs.random_colorings(70, 600, 2, seed=7)  # two classes of about 300 in every row
+    Z[5:9] = np.arange(600) % 2  # rows at distance 0 from each other
+    D2 = torch.full((70, 70), -1, dtype=torch.int16, device="cuda")
+    dlmcol.dlm_distance_batch(ctx, 600, 2, _cuda(Z), 70, _cuda(Z), 70, D2, 70, 1, method=method)
+    ctx.sync()
+    got, ref = D2.cpu().numpy(), oracle.distance_matrix(2, Z, Z)
+    iu = np.triu_indices(70, 1)
+    assert np.array_equal(got[iu], ref[iu])
+    assert np.all(got[np.tril_indices(70)] == -1)
+
+
 @pytest.mark.parametrize("method", [1, 2, 3])
 @pytest.mark.parametrize("n,k,a", [(200, 12, 50), (300, 120, 70)])
 def test_distance_upper_triangle(ctx, n, k, a, method):
