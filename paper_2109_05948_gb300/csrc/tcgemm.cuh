@@ -149,8 +149,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   const int zt = (nchunks + kpc - 1) / kpc;
   const int tiles = mt * nt * zt;
   auto tile_of = [&](int t, int& m0, int& n0, int& kc0, int& nk) {
+    // N tiles fastest: the N tiles of one M tile run on consecutive CTAs, close in time, so the
+    // A tile is read from DRAM once and from L2 for the others
     const int z = t / (mt * nt), r = t - z * mt * nt;
-    const int ny = r / mt, mx = r - ny * mt;
+    const int mx = r / nt, ny = r - mx * nt;
     m0 = mx * BM;
     n0 = ny * BN;
     kc0 = z * kpc;
