@@ -542,12 +542,25 @@ struct EpiLayer {  // H[row][col] = mask(LeakyReLU(acc + G[cand][col])); optiona
   float dot;
   int pbn;        // half the GEMM's N tile width
   int part;
+  // G[cand][gnext - 1 ..] for the next call, loaded during this one (gnext = 0: nothing loaded)
+  float4 gq[4];
+  int gnext;
   __device__ void tile(int, int n0) { part = n0 / pbn; }
   __device__ void operator()(int row, int col0, const float (&v)[16]) {
     if (row >= M) return;
     const int cand = row / R;
     const bool valid = row - cand * R < kv;
-    const float* g = G + (size_t)cand * kD + col0;
+    const float4* gsrc = reinterpret_cast<const float4*>(G + (size_t)cand * kD);
+    float4 gc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) gc[i] = gnext == col0 + 1 ? gq[i] : gsrc[col0 / 4 + i];
+    gnext = 0;
+    if (col0 + 16 < kD) {  // the next 16 columns of this row's G (the call after this one)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) gq[i] = gsrc[(col0 + 16) / 4 + i];
+      gnext = col0 + 17;
+    }
+    const float* g = reinterpret_cast<const float*>(gc);
     float h[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -857,6 +870,12 @@ __global__ void __launch_bounds__(256) k_demb(int n, int B, int R, const int16_t
     for (int g = 1; g < kDembGroups; ++g) t += ps[g][f];
     grad[(v < n ? oE + (size_t)v * kD0 : ob0) + f] = t;
   }
+}
+
+// the batch offset and Adam's step counter at the start of a training call
+__global__ void k_set_step(int32_t* step, int32_t t) {
+  step[0] = 0;
+  step[1] = t;
 }
 
 // Adam's bias corrections of step t + 1 (t = step[1]) in double, by one thread: 1 - 0.9^(t+1) and
@@ -1580,10 +1599,10 @@ extern "C" dlm_status dlm_scorer_train(dlm_ctx* ctx, dlm_scorer* s, const int16_
   if (!s->d_step) {
     DLM_TRY(dalloc(ctx, &s->d_step, 2));
   }
-  // the device counters start from the host mirror of Adam's step counter
-  int32_t init[2] = {0, (int32_t)s->t};
-  DLM_CUDA(ctx, cudaMemcpyAsync(s->d_step, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
-  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // init lives on the host stack
+  // the device counters start from the host mirror of Adam's step counter (written by a kernel, so
+  // the call does not wait for the stream)
+  k_set_step<<<1, 1, 0, ctx->stream>>>(s->d_step, (int32_t)s->t);
+  DLM_TRY(launch_check(ctx, "k_set_step"));
   for (int ep = 0; ep < epochs; ++ep) {
     k_epoch_perm<<<1, 1024, (size_t)mp * 8, ctx->stream>>>(p, seed, (uint32_t)ep, generation, s->perm);
     DLM_TRY(launch_check(ctx, "k_epoch_perm"));

@@ -104,6 +104,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// the same load without its wait: the registers are valid only after tmem_wait16 on them
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+// waits for the thread's TMEM loads; the registers pass through the statement, so no use of them
+// is scheduled before it
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -252,11 +271,23 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         break;
       }
       const uint32_t tbase = tmem + (uint32_t)(b * BN) + ((uint32_t)(q * 32) << 16);
+      // the next 16 columns' TMEM load is in flight while the functor handles the current ones
+      uint32_t cur[16], nxt[16];
+      tmem_ld16_issue(tbase + (uint32_t)c0, cur);
+      tmem_wait16(cur);
 #pragma unroll 1
       for (int c = c0; c < c0 + HALF; c += 16) {
+        const bool more = c + 16 < c0 + HALF;  // uniform over the warp
+        if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), nxt);
         float v[16];
-        tmem_ld16(tbase + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(cur[i]);
         e(row, n0 + c, v);
+        if (more) {
+          tmem_wait16(nxt);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
+        }
       }
       e.finish(row);
       fence_before_sync();
