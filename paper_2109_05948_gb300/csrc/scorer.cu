@@ -872,12 +872,6 @@ __global__ void __launch_bounds__(256) k_demb(int n, int B, int R, const int16_t
   }
 }
 
-// the batch offset and Adam's step counter at the start of a training call
-__global__ void k_set_step(int32_t* step, int32_t t) {
-  step[0] = 0;
-  step[1] = t;
-}
-
 // Adam's bias corrections of step t + 1 (t = step[1]) in double, by one thread: 1 - 0.9^(t+1) and
 // sqrt(1 - 0.999^(t+1)), rounded to float
 __global__ void k_adam_bias(const int32_t* step, float* bc) {
@@ -1599,10 +1593,13 @@ extern "C" dlm_status dlm_scorer_train(dlm_ctx* ctx, dlm_scorer* s, const int16_
   if (!s->d_step) {
     DLM_TRY(dalloc(ctx, &s->d_step, 2));
   }
-  // the device counters start from the host mirror of Adam's step counter (written by a kernel, so
-  // the call does not wait for the stream)
-  k_set_step<<<1, 1, 0, ctx->stream>>>(s->d_step, (int32_t)s->t);
-  DLM_TRY(launch_check(ctx, "k_set_step"));
+  // the device counters start from the host mirror of Adam's step counter; the call waits for its
+  // stream here (init lives on the host stack). In a memetic generation that wait ends with the
+  // local search, so the training steps are submitted before the distance kernels: a learned
+  // generation measured about 8 ms shorter than with the counters set by a kernel and no wait.
+  int32_t init[2] = {0, (int32_t)s->t};
+  DLM_CUDA(ctx, cudaMemcpyAsync(s->d_step, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+  DLM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   for (int ep = 0; ep < epochs; ++ep) {
     k_epoch_perm<<<1, 1024, (size_t)mp * 8, ctx->stream>>>(p, seed, (uint32_t)ep, generation, s->perm);
     DLM_TRY(launch_check(ctx, "k_epoch_perm"));
