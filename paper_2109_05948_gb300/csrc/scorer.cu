@@ -6,8 +6,8 @@
 // over each colour class (V_i Lambda_0; the rho(S) Gamma_0 term is the same for every partition
 // and is part of beta_0), LeakyReLU_0.2; layers 1..3: H' = LeakyReLU_0.2(beta + H Lambda +
 // rho(H) Gamma) with width 256 and rho the mean over the k classes; output = mean over classes of
-// the linear head. Each candidate occupies R = 64 rows (rows k..63 are zero), so one 128-row
-// tensor-core tile holds two whole candidates.
+// the linear head. In a training batch each candidate occupies R = 64 ceil(k / 64) rows (rows
+// k..R-1 are zero); a scoring chunk keeps k rows per candidate.
 //
 // Where the work runs:
 //   tcgen05 BF16 GEMMs (FP32 accumulate in TMEM): H Lambda for layers 1..3 (fused epilogue:
@@ -20,8 +20,10 @@
 //   CUDA cores (FP32): the class pooling of layer 0 (a gather, not a contraction), per-candidate
 //     means and column sums, the rho(H) Gamma terms of small and training batches (fused into
 //     the pooling and the class-mean kernels), the embedding gradient (scatter by colour), Adam
-//     (which also writes the bf16 operand copies). A training step is 26 launches replayed from
-//     a CUDA graph.
+//     (which also writes the bf16 operand copies). A training step is one CUDA graph: 16 launches
+//     on the chain forward -> dZ_3 -> ... -> dZ_0 -> Adam, and side branches for the layers'
+//     weight gradients, the head gradient and loss, the embedding bias and Adam's bias
+//     corrections.
 // All reductions run in a fixed order: results are deterministic run to run.
 #include <cuda_bf16.h>
 
