@@ -29,11 +29,22 @@ def test_binding_declares_signatures_for_every_symbol(lib):
     assert [s for s in dlmcol.header_symbols() if s not in dlmcol._SIGS] == []
 
 
-def test_library_has_no_torch_or_oracle_dependency():
+def test_library_has_no_torch_or_oracle_dependency(lib):
+    """The library's dynamic dependencies (ELF NEEDED entries) and exported symbols name neither
+    torch nor the oracle."""
+    import shutil
+    import subprocess
+
+    if not shutil.which("readelf") or not shutil.which("nm"):
+        pytest.skip("readelf / nm not available")
     so = dlmcol.LIB_PATH
-    data = open(so, "rb").read()
-    assert b"liboracle" not in data and b"oracle_tabucol" not in data
-    assert b"libtorch" not in data and b"libc10" not in data
+    dyn = subprocess.run(["readelf", "-d", so], capture_output=True, text=True, check=True).stdout
+    needed = [ln.split("[", 1)[1].rstrip("]") for ln in dyn.splitlines() if "(NEEDED)" in ln]
+    assert needed and not [x for x in needed if "torch" in x or "c10" in x or "oracle" in x], needed
+    syms = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    names = [ln.split()[-1] for ln in syms.splitlines() if ln.strip()]
+    assert "dlm_tabucol_batch" in names
+    assert not [x for x in names if x.startswith("oracle_")]
 
 
 def test_create_without_gpu_fails_cleanly(lib):
